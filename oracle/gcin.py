@@ -1,0 +1,128 @@
+"""GCIN coefficient network (Sec. 3.2, App. A.1) in plain FP64 torch ops.
+
+Test infrastructure only.  Gradients are taken by autograd on this forward.
+
+Per level graph G = (V, E) of a matrix A (Sec. 3.2, Algorithm 1 steps 3-5):
+node features x_i^(0) = [a_ii, deg(v_i)] with deg = number of off-diagonal
+pattern entries of row i; edge weights w_ij = a_ij; the self-loop of
+A_hat carries w_ii = a_ii (reading: A_hat = A).
+
+Layer l = 1..4 (Eq. GCN + App. A.1):
+    h_i = sum_{j in N(i) u {i}} w_ij x_j^(l-1)      (no GCN normalisation)
+    y   = h Theta^(l) + b^(l)                         (MLP^(l) = one Linear)
+    x^(l) = ReLU(InstanceNorm_graph(y))               (eps 1e-5, biased var, affine)
+Readout (JK-like, Sec. 3.2 readout equations; App. A.1):
+    g^(l) = Linear_{128->32}([mean_i x_i^(l), max_i x_i^(l)])   for l = 1..4
+    z = sigmoid(LayerNorm_128(concat_l g^(l)))                  (eps 1e-5)
+    c = Linear_{64->5}(ReLU(Linear_{128->64}(ReLU(Linear_{128->128}(z)))))
+This layout has exactly 55,045 trainable parameters (App. A.1).
+Readings: no activation after the readout linears, linear output on the five
+coefficients, max-pooling after the ReLU, readout over layers 1..L only.
+
+Flat parameter order (weights stored [in][out], row-major; then bias):
+conv1 W(2x64) b(64); conv2..4 W(64x64) b(64); IN1..4 gamma(64) beta(64);
+readout1..4 W(128x32) b(32); LN gamma(128) beta(128);
+head W(128x128) b(128), W(128x64) b(64), W(64x5) b(5).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from workloads import CSR
+
+DT = torch.float64
+HIDDEN = 64
+N_LAYERS = 4
+EPS = 1e-5
+
+
+def param_shapes():
+    shapes = [("conv1.W", (2, HIDDEN)), ("conv1.b", (HIDDEN,))]
+    for l in range(2, N_LAYERS + 1):
+        shapes += [(f"conv{l}.W", (HIDDEN, HIDDEN)), (f"conv{l}.b", (HIDDEN,))]
+    for l in range(1, N_LAYERS + 1):
+        shapes += [(f"in{l}.gamma", (HIDDEN,)), (f"in{l}.beta", (HIDDEN,))]
+    for l in range(1, N_LAYERS + 1):
+        shapes += [(f"ro{l}.W", (2 * HIDDEN, 32)), (f"ro{l}.b", (32,))]
+    shapes += [("ln.gamma", (128,)), ("ln.beta", (128,))]
+    shapes += [("h1.W", (128, 128)), ("h1.b", (128,)), ("h2.W", (128, 64)), ("h2.b", (64,)),
+               ("h3.W", (64, 5)), ("h3.b", (5,))]
+    return shapes
+
+
+def n_params() -> int:
+    return sum(int(np.prod(s)) for _, s in param_shapes())
+
+
+def unpack(theta: torch.Tensor) -> dict:
+    out, off = {}, 0
+    for name, shape in param_shapes():
+        k = int(np.prod(shape))
+        out[name] = theta[off:off + k].reshape(shape)
+        off += k
+    assert off == theta.numel(), (off, theta.numel())
+    return out
+
+
+class Graph:
+    """One level's matrix as a graph (Algorithm 1 steps 3-4)."""
+
+    def __init__(self, A: CSR):
+        self.n = A.n_rows
+        self.row = torch.from_numpy(np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr)).astype(np.int64))
+        self.col = torch.from_numpy(A.col.astype(np.int64))
+        self.w = torch.from_numpy(A.val.astype(np.float64))
+        on = self.row == self.col
+        self.diag = torch.zeros(self.n, dtype=DT).index_add(0, self.row[on], self.w[on])
+        self.deg = torch.zeros(self.n, dtype=DT).index_add(0, self.row[~on], torch.ones(int((~on).sum()), dtype=DT))
+
+    def features(self) -> torch.Tensor:
+        return torch.stack([self.diag, self.deg], dim=1)
+
+    def aggregate(self, x: torch.Tensor) -> torch.Tensor:
+        """h_i = sum_j w_ij x_j over row i of A_hat (diagonal = self-loop)."""
+        return torch.zeros(self.n, x.shape[1], dtype=DT).index_add(0, self.row, self.w[:, None] * x[self.col])
+
+
+def instance_norm(y: torch.Tensor, gamma, beta) -> torch.Tensor:
+    mu = y.mean(dim=0)
+    var = ((y - mu) ** 2).mean(dim=0)
+    return (y - mu) / torch.sqrt(var + EPS) * gamma + beta
+
+
+def layer_norm(z: torch.Tensor, gamma, beta) -> torch.Tensor:
+    mu = z.mean()
+    var = ((z - mu) ** 2).mean()
+    return (z - mu) / torch.sqrt(var + EPS) * gamma + beta
+
+
+def forward_graph(p: dict, g: Graph, keep=None) -> torch.Tensor:
+    """Coefficients c (5,) for one graph."""
+    x = g.features()
+    pooled = []
+    for l in range(1, N_LAYERS + 1):
+        h = g.aggregate(x)
+        y = h @ p[f"conv{l}.W"] + p[f"conv{l}.b"]
+        x = torch.relu(instance_norm(y, p[f"in{l}.gamma"], p[f"in{l}.beta"]))
+        if keep is not None:
+            keep.append((h, y, x))
+        gl = torch.cat([x.mean(dim=0), x.max(dim=0).values])
+        pooled.append(gl @ p[f"ro{l}.W"] + p[f"ro{l}.b"])
+    z = torch.sigmoid(layer_norm(torch.cat(pooled), p["ln.gamma"], p["ln.beta"]))
+    z = torch.relu(z @ p["h1.W"] + p["h1.b"])
+    z = torch.relu(z @ p["h2.W"] + p["h2.b"])
+    return z @ p["h3.W"] + p["h3.b"]
+
+
+def forward(theta, graphs) -> torch.Tensor:
+    """Batched inference (Algorithm 1 step 6): c[g] for every graph, shape (G, 5)."""
+    theta = torch.as_tensor(theta, dtype=DT) if not isinstance(theta, torch.Tensor) else theta
+    p = unpack(theta)
+    return torch.stack([forward_graph(p, g) for g in graphs])
+
+
+def predict(theta, matrices) -> np.ndarray:
+    """Coefficients for a list of CSR matrices (no gradient)."""
+    with torch.no_grad():
+        return forward(torch.as_tensor(np.asarray(theta, dtype=np.float64)), [Graph(A) for A in matrices]).numpy()

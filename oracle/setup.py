@@ -1,0 +1,195 @@
+"""AMG setup phase (Sec. 2.2): Ruge-Stueben coarsening, direct interpolation,
+Galerkin coarse operators.  Plain FP64, Python loops; test infrastructure only.
+
+Readings where the paper is silent (it names only "classical Ruge-Stueben,
+theta = 0.25", Sec. 4, and "at most 10 levels", Table train_hyper):
+
+* strength: j is a strong dependency of i iff j != i and
+  -a_ij >= theta * max_{k != i} (-a_ik), with that maximum > 0;
+* C/F splitting: the classical first pass only.  Points with no strong
+  connection in either direction become F.  Then repeatedly the undecided
+  point with the largest measure lambda becomes C (ties: lowest index) and
+  its undecided strong dependents become F.  lambda_k starts at |S_k^T|;
+  each time an undecided point that strongly depends on k becomes C,
+  lambda_k drops by 1, and each time one becomes F it rises by 1
+  (lambda = |S^T cap U| + 2 |S^T cap F|).  No second pass;
+* direct interpolation (C rows identity): for an F point i with strong
+  C-neighbours C_i, w_ij = -alpha_i a_ij / d_i with
+  alpha_i = sum_{k != i, a_ik < 0} a_ik / sum_{k in C_i} a_ik and
+  d_i = a_ii + sum_{k != i, a_ik > 0} a_ik (positive couplings lumped onto
+  the diagonal; strong couplings are always negative).  An F point with no
+  strong C-neighbour gets an empty row;
+* Galerkin product keeps the structural pattern of P^T A P (entries that
+  cancel to 0.0 stay in the pattern);
+* stop coarsening when n <= max_coarse, when the hierarchy has max_levels
+  levels, or when a coarse level would keep more than 90% of the points (or
+  none).
+"""
+from __future__ import annotations
+
+import heapq
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+from workloads import CSR
+
+F_PT, C_PT, U_PT = 0, 1, -1
+
+
+def _rows(A: CSR) -> np.ndarray:
+    return np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr))
+
+
+def strength(A: CSR, theta: float):
+    """S[i] = sorted strong dependencies of i; ST[i] = points strongly depending on i."""
+    n = A.n_rows
+    S = []
+    for i in range(n):
+        lo, hi = A.row_ptr[i], A.row_ptr[i + 1]
+        cols = A.col[lo:hi]
+        neg = -A.val[lo:hi]
+        off = cols != i
+        if not off.any():
+            S.append(np.zeros(0, dtype=np.int64))
+            continue
+        m = neg[off].max()
+        if m <= 0.0:
+            S.append(np.zeros(0, dtype=np.int64))
+            continue
+        S.append(cols[off & (neg >= theta * m)].astype(np.int64))
+    ST = [[] for _ in range(n)]
+    for i in range(n):
+        for j in S[i]:
+            ST[j].append(i)
+    ST = [np.array(t, dtype=np.int64) for t in ST]
+    return S, ST
+
+
+def rs_split(n: int, S, ST) -> np.ndarray:
+    """Classical Ruge-Stueben first pass; returns 1 for C points, 0 for F."""
+    state = np.full(n, U_PT, dtype=np.int64)
+    lam = np.array([len(t) for t in ST], dtype=np.int64)
+    for i in range(n):
+        if len(S[i]) == 0 and len(ST[i]) == 0:
+            state[i] = F_PT
+    heap = [(-int(lam[i]), i) for i in range(n) if state[i] == U_PT]
+    heapq.heapify(heap)
+    while heap:
+        neg_l, i = heapq.heappop(heap)
+        if state[i] != U_PT or -neg_l != lam[i]:
+            continue  # stale entry
+        state[i] = C_PT
+        for j in ST[i]:
+            if state[j] == U_PT:
+                state[j] = F_PT
+                for k in S[j]:
+                    if state[k] == U_PT:
+                        lam[k] += 1
+                        heapq.heappush(heap, (-int(lam[k]), int(k)))
+        for k in S[i]:
+            if state[k] == U_PT:
+                lam[k] -= 1
+                heapq.heappush(heap, (-int(lam[k]), int(k)))
+    return (state == C_PT).astype(np.int64)
+
+
+def direct_interpolation(A: CSR, S, split: np.ndarray) -> CSR:
+    """Direct interpolation P (n x n_c); C points map to themselves."""
+    n = A.n_rows
+    cidx = np.cumsum(split) - 1
+    nc = int(split.sum())
+    rp, cols, vals = [0], [], []
+    for i in range(n):
+        if split[i] == C_PT:
+            cols.append(int(cidx[i]))
+            vals.append(1.0)
+            rp.append(len(cols))
+            continue
+        lo, hi = A.row_ptr[i], A.row_ptr[i + 1]
+        strong_c = set(int(j) for j in S[i] if split[j] == C_PT)
+        if not strong_c:
+            rp.append(len(cols))
+            continue
+        a_ii = 0.0
+        neg_all = 0.0
+        pos_all = 0.0
+        neg_c = 0.0
+        for p in range(lo, hi):
+            j, a = int(A.col[p]), float(A.val[p])
+            if j == i:
+                a_ii += a
+            elif a < 0.0:
+                neg_all += a
+                if j in strong_c:
+                    neg_c += a
+            elif a > 0.0:
+                pos_all += a
+        d = a_ii + pos_all
+        alpha = neg_all / neg_c
+        for p in range(lo, hi):
+            j = int(A.col[p])
+            if j in strong_c:
+                cols.append(int(cidx[j]))
+                vals.append(-alpha * float(A.val[p]) / d)
+        rp.append(len(cols))
+    return CSR(n, nc, np.array(rp, dtype=np.int32), np.array(cols, dtype=np.int32),
+               np.array(vals, dtype=np.float64))
+
+
+def _to_scipy(M: CSR):
+    return sp.csr_matrix((M.val, M.col, M.row_ptr), shape=(M.n_rows, M.n_cols))
+
+
+def _from_scipy(M) -> CSR:
+    M = M.tocsr()
+    M.sort_indices()
+    return CSR(M.shape[0], M.shape[1], M.indptr.astype(np.int32), M.indices.astype(np.int32),
+               M.data.astype(np.float64))
+
+
+def transpose(M: CSR) -> CSR:
+    return _from_scipy(_to_scipy(M).T)
+
+
+def galerkin(A: CSR, P: CSR) -> CSR:
+    """A_c = P^T A P on the structural pattern of the product."""
+    As, Ps = _to_scipy(A), _to_scipy(P)
+    ones = lambda M: sp.csr_matrix((np.ones_like(M.data), M.indices, M.indptr), shape=M.shape)
+    pattern = (ones(Ps).T @ ones(As) @ ones(Ps)).tocsr()
+    pattern.sort_indices()
+    numeric = (Ps.T @ As @ Ps).tocoo()
+    prow = np.repeat(np.arange(pattern.shape[0], dtype=np.int64), np.diff(pattern.indptr))
+    pkey = prow * pattern.shape[1] + pattern.indices
+    nkey = numeric.row.astype(np.int64) * pattern.shape[1] + numeric.col
+    vals = np.zeros(pattern.nnz)
+    np.add.at(vals, np.searchsorted(pkey, nkey), numeric.data)
+    return CSR(pattern.shape[0], pattern.shape[1], pattern.indptr.astype(np.int32),
+               pattern.indices.astype(np.int32), vals)
+
+
+@dataclass
+class Level:
+    A: CSR
+    P: CSR | None = None   # n_l x n_{l+1}
+    R: CSR | None = None   # n_{l+1} x n_l, R = P^T
+    split: np.ndarray | None = None
+
+
+def build_hierarchy(A: CSR, theta: float = 0.25, max_levels: int = 10, max_coarse: int = 64):
+    """Setup-AMG-Hierarchy of Algorithm 1: list of Level, finest first."""
+    levels = [Level(A)]
+    while len(levels) < max_levels and levels[-1].A.n_rows > max_coarse:
+        Al = levels[-1].A
+        S, ST = strength(Al, theta)
+        split = rs_split(Al.n_rows, S, ST)
+        nc = int(split.sum())
+        if nc == 0 or nc > 0.9 * Al.n_rows:
+            break
+        P = direct_interpolation(Al, S, split)
+        levels[-1].P = P
+        levels[-1].R = transpose(P)
+        levels[-1].split = split
+        levels.append(Level(galerkin(Al, P)))
+    return levels

@@ -1,0 +1,250 @@
+"""AMG solve phase in plain FP64 (torch CPU ops, differentiable).
+
+Test infrastructure only.  Every sparse product is written out as its
+definition, y_i = sum_j m_ij x_j, with a gather and an index_add, so that
+autograd can differentiate through the smoother's values (Sec. 3.3).
+
+* Sec. 2.1: stationary correction u <- u + Q^-1 (f - A u).
+* Sec. 2.3: relaxed Jacobi, Q^-1 = omega D^-1.
+* Sec. 3.1: sparse pseudo-inverse smoother with A's pattern,
+  q_ii^-1 = f_d(a_ii/s)/a_ii, q_ij^-1 = f_o(a_ij/s)/(a_ii + a_jj),
+  s = max |A - D|, f_d(x) = c0 + c1 x + c2 x^2, f_o(x) = c3 x + c4 x^2
+  (coefficient order (d0, d1, d2, o1, o2) is a reading; the paper fixes
+  only "3 for f_d, 2 for f_o").
+* Sec. 2.2: V-cycle: nu1 pre-sweeps, restriction of the residual with R,
+  recursion with a zero initial guess, prolongation with P, nu2 post-sweeps;
+  the coarsest level is solved by a dense Cholesky factorisation.
+* Sec. 4: stop when ||f - A u||_2 / ||f||_2 <= tol (relative to ||f||: a
+  reading) or after max_iter cycles; diverged when a norm is not finite or
+  exceeds 1e3 times the initial one; stagnated when 10 cycles reduce the
+  norm by less than 1%.
+* Sec. 3.3: the relative validation metric
+  log10(||r_{n+1}|| / ||r^{omega-J}_{n+1}||) after one cycle from the same
+  state.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from workloads import CSR
+
+DT = torch.float64
+
+OK, DIVERGED, STAGNATED, MAXITER = 0, -4, -5, -6
+
+
+@dataclass
+class TMat:
+    """A sparse matrix as (row, col, val) triples in torch FP64."""
+    n_rows: int
+    n_cols: int
+    row: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+
+    @staticmethod
+    def of(M: CSR) -> "TMat":
+        row = torch.from_numpy(np.repeat(np.arange(M.n_rows), np.diff(M.row_ptr)).astype(np.int64))
+        return TMat(M.n_rows, M.n_cols, row, torch.from_numpy(M.col.astype(np.int64)),
+                    torch.from_numpy(M.val.astype(np.float64)))
+
+    def diag(self) -> torch.Tensor:
+        d = torch.zeros(self.n_rows, dtype=DT)
+        on = self.row == self.col
+        return d.index_add(0, self.row[on], self.val[on])
+
+
+def matvec(row, col, val, x, n_rows) -> torch.Tensor:
+    """y_i = sum_j m_ij x_j."""
+    return torch.zeros(n_rows, dtype=DT).index_add(0, row, val * x[col])
+
+
+def mv(M: TMat, x: torch.Tensor) -> torch.Tensor:
+    return matvec(M.row, M.col, M.val, x, M.n_rows)
+
+
+# ----------------------------------------------------------------------------
+# smoothers (Sec. 2.3, Sec. 3.1)
+# ----------------------------------------------------------------------------
+def smoother_scale(A: TMat) -> float:
+    """s = max |A - D| (largest off-diagonal magnitude)."""
+    off = A.row != A.col
+    return float(A.val[off].abs().max()) if bool(off.any()) else 1.0
+
+
+def pseudo_inverse_values(A: TMat, c, s: float | None = None) -> torch.Tensor:
+    """Values of Q^-1 on A's pattern for coefficients c = (d0, d1, d2, o1, o2)."""
+    if s is None:
+        s = smoother_scale(A)
+    d = A.diag()
+    x = A.val / s
+    on = A.row == A.col
+    f_d = c[0] + c[1] * x + c[2] * x * x
+    f_o = c[3] * x + c[4] * x * x
+    q_diag = f_d / d[A.row]
+    q_off = f_o / (d[A.row] + d[A.col])
+    return torch.where(on, q_diag, q_off)
+
+
+def jacobi_values(A: TMat, omega: float) -> torch.Tensor:
+    """Values of omega D^-1 on A's pattern (zero off the diagonal)."""
+    d = A.diag()
+    on = A.row == A.col
+    return torch.where(on, torch.full_like(A.val, omega) / d[A.row], torch.zeros_like(A.val))
+
+
+# ----------------------------------------------------------------------------
+# coarsest level: dense Cholesky
+# ----------------------------------------------------------------------------
+def cholesky(Ad: np.ndarray) -> np.ndarray:
+    """Lower-triangular L with L L^T = Ad, column by column."""
+    n = Ad.shape[0]
+    L = np.zeros_like(Ad)
+    for j in range(n):
+        djj = Ad[j, j] - L[j, :j] @ L[j, :j]
+        if not djj > 0.0:
+            raise np.linalg.LinAlgError("coarsest matrix is not positive definite")
+        L[j, j] = math.sqrt(djj)
+        L[j + 1:, j] = (Ad[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return L
+
+
+def cholesky_solve(L: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """Solve L L^T x = b by forward then backward substitution."""
+    n = L.shape[0]
+    y = []
+    for i in range(n):
+        acc = b[i] - (L[i, :i] @ torch.stack(y) if i else 0.0)
+        y.append(acc / L[i, i])
+    y = torch.stack(y)
+    x = [None] * n
+    for i in reversed(range(n)):
+        acc = y[i] - (L[i + 1:, i] @ torch.stack(x[i + 1:]) if i < n - 1 else 0.0)
+        x[i] = acc / L[i, i]
+    return torch.stack(x)
+
+
+# ----------------------------------------------------------------------------
+# hierarchy with smoothers
+# ----------------------------------------------------------------------------
+@dataclass
+class OLevel:
+    A: TMat
+    P: TMat | None
+    R: TMat | None
+    M: torch.Tensor | None = None      # smoother values on A's pattern
+    L: torch.Tensor | None = None      # Cholesky factor on the coarsest level
+    s: float = 1.0
+
+
+@dataclass
+class OHierarchy:
+    levels: list = field(default_factory=list)
+
+    @staticmethod
+    def of(setup_levels) -> "OHierarchy":
+        h = OHierarchy()
+        for k, lv in enumerate(setup_levels):
+            A = TMat.of(lv.A)
+            P = TMat.of(lv.P) if lv.P is not None else None
+            R = TMat.of(lv.R) if lv.R is not None else None
+            ol = OLevel(A, P, R, s=smoother_scale(A))
+            if k == len(setup_levels) - 1:
+                ol.L = torch.from_numpy(cholesky(lv.A.to_dense()))
+            h.levels.append(ol)
+        return h
+
+    def set_jacobi(self, omega: float = 2.0 / 3.0):
+        for lv in self.levels[:-1]:
+            lv.M = jacobi_values(lv.A, omega)
+
+    def set_pseudo_inverse(self, coeffs):
+        """coeffs[l] = (d0, d1, d2, o1, o2) for level l (rows past the last smoothed level unused)."""
+        for l, lv in enumerate(self.levels[:-1]):
+            lv.M = pseudo_inverse_values(lv.A, coeffs[l], lv.s)
+
+
+def sweep(lv: OLevel, b: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+    """One stationary smoothing step u + Q^-1 (b - A u)."""
+    r = b - mv(lv.A, u)
+    return u + matvec(lv.A.row, lv.A.col, lv.M, r, lv.A.n_rows)
+
+
+def vcycle(h: OHierarchy, b: torch.Tensor, u: torch.Tensor, nu1: int = 2, nu2: int = 2, l: int = 0):
+    """One V-cycle on level l for A_l u = b starting from u."""
+    lv = h.levels[l]
+    if l == len(h.levels) - 1:
+        return cholesky_solve(lv.L, b)
+    for _ in range(nu1):
+        u = sweep(lv, b, u)
+    r = b - mv(lv.A, u)
+    bc = mv(lv.R, r)
+    ec = vcycle(h, bc, torch.zeros(lv.R.n_rows, dtype=DT), nu1, nu2, l + 1)
+    u = u + mv(lv.P, ec)
+    for _ in range(nu2):
+        u = sweep(lv, b, u)
+    return u
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    history: list
+    n_vcycles: int
+    status: int
+
+
+def solve(h: OHierarchy, f, tol: float = 1e-8, max_iter: int = 500, u0=None,
+          nu1: int = 2, nu2: int = 2) -> SolveResult:
+    """Stationary V-cycle iteration to ||f - A u|| / ||f|| <= tol."""
+    f = torch.as_tensor(np.asarray(f, dtype=np.float64))
+    A = h.levels[0].A
+    u = torch.zeros(A.n_rows, dtype=DT) if u0 is None else torch.as_tensor(np.asarray(u0, dtype=np.float64)).clone()
+    fnorm = float(torch.linalg.vector_norm(f))
+    if fnorm == 0.0:
+        fnorm = 1.0
+    r0 = float(torch.linalg.vector_norm(f - mv(A, u)))
+    hist = [r0 / fnorm]
+    status = MAXITER
+    if hist[0] <= tol:
+        return SolveResult(u.numpy(), hist, 0, OK)
+    k = 0
+    with torch.no_grad():
+        while k < max_iter:
+            u = vcycle(h, f, u, nu1, nu2)
+            k += 1
+            rn = float(torch.linalg.vector_norm(f - mv(A, u)))
+            hist.append(rn / fnorm)
+            if not math.isfinite(rn) or rn > 1e3 * r0:
+                status = DIVERGED
+                break
+            if hist[-1] <= tol:
+                status = OK
+                break
+            if k >= 10 and hist[-1] > 0.99 * hist[-11]:
+                status = STAGNATED
+                break
+    return SolveResult(u.numpy(), hist, k, status)
+
+
+def vcycle_operator_apply(h: OHierarchy, r, nu1: int = 2, nu2: int = 2) -> np.ndarray:
+    """B r: one V-cycle from a zero initial guess (the preconditioner's action)."""
+    r = torch.as_tensor(np.asarray(r, dtype=np.float64))
+    with torch.no_grad():
+        return vcycle(h, r, torch.zeros_like(r), nu1, nu2).numpy()
+
+
+def relative_metric(h_gnn: OHierarchy, h_jac: OHierarchy, f, u0=None, nu1=2, nu2=2) -> float:
+    """log10(||r_{n+1}|| / ||r^{omega-J}_{n+1}||) after one cycle from u0."""
+    f = torch.as_tensor(np.asarray(f, dtype=np.float64))
+    u = torch.zeros_like(f) if u0 is None else torch.as_tensor(np.asarray(u0, dtype=np.float64))
+    with torch.no_grad():
+        ug = vcycle(h_gnn, f, u.clone(), nu1, nu2)
+        uj = vcycle(h_jac, f, u.clone(), nu1, nu2)
+        rg = torch.linalg.vector_norm(f - mv(h_gnn.levels[0].A, ug))
+        rj = torch.linalg.vector_norm(f - mv(h_jac.levels[0].A, uj))
+    return float(torch.log10(rg / rj))

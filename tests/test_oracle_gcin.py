@@ -1,0 +1,146 @@
+"""Pins for the oracle's GCIN network (Sec. 3.2, App. A.1) and training
+objective (Sec. 3.3).  The forward is checked against an independent build
+from torch.nn.functional library layers on a dense adjacency; gradients are
+checked against FP64 central finite differences; the optimiser against
+torch.optim.Adam and torch.nn.utils.clip_grad_norm_."""
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as Fn
+
+import workloads as W
+from oracle import gcin as G
+from oracle import setup as S
+from oracle import solve as O
+from oracle import train as T
+
+
+def test_parameter_count_matches_paper():
+    assert G.n_params() == 55045          # App. A.1
+    assert sum(s for s, _ in W.GCIN_PARAM_SIZES) == 55045
+
+
+def _library_forward(theta, A):
+    """Same network from library layers: dense A_hat, F.linear, F.instance_norm, F.layer_norm."""
+    p = G.unpack(torch.from_numpy(theta))
+    Ad = torch.from_numpy(A.to_dense())
+    n = A.n_rows
+    deg = torch.from_numpy((np.diff(A.row_ptr) - 1).astype(np.float64))
+    x = torch.stack([torch.diagonal(Ad), deg], 1)
+    pooled = []
+    for l in range(1, 5):
+        y = Fn.linear(Ad @ x, p[f"conv{l}.W"].T, p[f"conv{l}.b"])
+        y = Fn.instance_norm(y.T.unsqueeze(0), weight=p[f"in{l}.gamma"], bias=p[f"in{l}.beta"], eps=1e-5)[0].T
+        x = Fn.relu(y)
+        g = torch.cat([x.mean(0), x.amax(0)])
+        pooled.append(Fn.linear(g, p[f"ro{l}.W"].T, p[f"ro{l}.b"]))
+    z = torch.sigmoid(Fn.layer_norm(torch.cat(pooled), (128,), p["ln.gamma"], p["ln.beta"], eps=1e-5))
+    z = Fn.relu(Fn.linear(z, p["h1.W"].T, p["h1.b"]))
+    z = Fn.relu(Fn.linear(z, p["h2.W"].T, p["h2.b"]))
+    return Fn.linear(z, p["h3.W"].T, p["h3.b"])
+
+
+@pytest.mark.parametrize("kind", ["uniform", "band"])
+def test_forward_equals_library_layers(kind):
+    A = W.fv_mesh(kind, 600, 3, max_aspect=100.0)[0]
+    levels = S.build_hierarchy(A, max_coarse=20)
+    theta = W.gcin_init_params(1, last_scale=1.0)
+    c = G.predict(theta, [l.A for l in levels])
+    for k, lv in enumerate(levels):
+        ref = _library_forward(theta, lv.A).numpy()
+        np.testing.assert_allclose(c[k], ref, rtol=1e-10, atol=1e-12)
+
+
+def test_permutation_invariance():
+    A = W.fv_mesh("graded", 800, 6)[0]
+    perm = np.argsort(W.uniform01(99, A.n_rows))
+    Ad = A.to_dense()[np.ix_(perm, perm)]
+    r, c = np.nonzero(Ad != 0)
+    Ap = W._coo_to_csr(A.n_rows, A.n_rows, r, c, Ad[r, c])
+    theta = W.gcin_init_params(2, last_scale=1.0)
+    np.testing.assert_allclose(G.predict(theta, [A])[0], G.predict(theta, [Ap])[0], rtol=1e-11, atol=1e-13)
+
+
+def test_instance_norm_statistics():
+    A = W.fv_mesh("uniform", 500, 8)[0]
+    theta = W.gcin_init_params(3)
+    p = G.unpack(torch.from_numpy(theta))
+    keep = []
+    with torch.no_grad():
+        G.forward_graph(p, G.Graph(A), keep)
+    for h, y, x in keep:
+        z = (y - y.mean(0)) / torch.sqrt(y.var(0, unbiased=False) + 1e-5)
+        np.testing.assert_allclose(z.mean(0).numpy(), 0, atol=1e-12)
+        assert torch.all(x >= 0)
+
+
+def _small_problem(seed, n_pts=400):
+    A = W.fv_mesh(["uniform", "graded", "band"][seed % 3], n_pts, seed, max_aspect=100.0)[0]
+    levels = S.build_hierarchy(A, max_coarse=16)
+    return levels, O.OHierarchy.of(levels), W.rhs_uniform(seed, A.n_rows)
+
+
+def test_coefficient_gradient_matches_finite_differences():
+    levels, h, f = _small_problem(1)
+    c = np.array([[0.6, 0.02, -0.01, 0.15, 0.02]] * len(levels))
+    L, dc = T.loss_and_coeff_grad(h, c, f)
+    eps = 1e-6
+    for l in range(len(levels) - 1):
+        for k in range(5):
+            cp, cm = c.copy(), c.copy()
+            cp[l, k] += eps
+            cm[l, k] -= eps
+            with torch.no_grad():
+                fd = (float(T.problem_loss(h, torch.from_numpy(cp), f)) -
+                      float(T.problem_loss(h, torch.from_numpy(cm), f))) / (2 * eps)
+            assert abs(fd - dc[l, k]) <= 1e-6 * max(1.0, abs(fd)), (l, k, fd, dc[l, k])
+    assert np.all(dc[-1] == 0)   # the coarsest level has no smoother
+
+
+def test_network_gradient_matches_finite_differences():
+    probs = [_small_problem(s) for s in (0, 2)]
+    hs = [p[1] for p in probs]
+    gs = [[G.Graph(l.A) for l in p[0]] for p in probs]
+    fs = [p[2] for p in probs]
+    theta = W.gcin_init_params(4)
+    L, g = T.batch_loss_and_grad(theta, hs, gs, fs)
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        d = rng.standard_normal(theta.size)
+        d /= np.linalg.norm(d)
+        eps = 1e-5
+        with torch.no_grad():
+            lp = float(T.batch_loss(torch.from_numpy(theta + eps * d), hs, gs, fs))
+            lm = float(T.batch_loss(torch.from_numpy(theta - eps * d), hs, gs, fs))
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - g @ d) <= 1e-6 * max(1.0, abs(fd)), (fd, g @ d)
+
+
+def test_adam_and_clip_match_library():
+    rng = np.random.default_rng(1)
+    theta = rng.standard_normal(50)
+    t = torch.tensor(theta.copy(), requires_grad=True)
+    opt = torch.optim.Adam([t], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    m = np.zeros(50)
+    v = np.zeros(50)
+    for step in range(1, 6):
+        g = rng.standard_normal(50) * (10.0 if step % 2 else 0.1)
+        t.grad = torch.tensor(g.copy())
+        torch.nn.utils.clip_grad_norm_([t], 1.0)
+        gc = T.clip_grad(g, 1.0)
+        np.testing.assert_allclose(t.grad.numpy(), gc, rtol=1e-12)
+        opt.step()
+        theta, m, v = T.adam_step(theta, gc, m, v, step)
+        np.testing.assert_allclose(t.detach().numpy(), theta, rtol=1e-12, atol=1e-15)
+
+
+def test_jacobi_loss_equals_first_cycle_reduction():
+    # with c = (omega, 0, 0, 0, 0) the loss is log10 of the first entry of the
+    # Jacobi solve's relative residual history
+    levels, h, f = _small_problem(5)
+    c = np.array([[2.0 / 3.0, 0, 0, 0, 0]] * len(levels))
+    L, _ = T.loss_and_coeff_grad(h, c, f)
+    hj = O.OHierarchy.of(levels)
+    hj.set_jacobi()
+    res = O.solve(hj, f, tol=0.0, max_iter=1)
+    assert abs(L - np.log10(res.history[1])) < 1e-12

@@ -1,0 +1,160 @@
+"""Pins for the oracle's solve phase: SpMV, Jacobi, pseudo-inverse smoother,
+Cholesky, V-cycle, stopping rule.  Closed forms (5-point eigenpairs),
+hand-worked values (tests/golden), library routines (numpy LU) and algebraic
+invariants (symmetry, linearity)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import setup as S
+from oracle import solve as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def eigvec(m, j, k):
+    h = 1.0 / (m + 1)
+    x = np.arange(1, m + 1) * h
+    return np.outer(np.sin(j * np.pi * x), np.sin(k * np.pi * x)).ravel(), 4 - 2 * np.cos(j * np.pi * h) - 2 * np.cos(k * np.pi * h)
+
+
+@pytest.mark.parametrize("j,k", [(1, 1), (3, 7), (32, 5), (64, 64)])
+def test_spmv_5point_eigenpairs(j, k):
+    m = 64
+    A = O.TMat.of(W.poisson5(m))
+    v, lam = eigvec(m, j, k)
+    Av = O.mv(A, torch.from_numpy(v)).numpy()
+    np.testing.assert_allclose(Av, lam * v, atol=1e-13)
+
+
+@pytest.mark.parametrize("j,k", [(1, 1), (20, 40), (64, 64)])
+def test_jacobi_damps_eigenvector_by_closed_form(j, k):
+    # one relaxed-Jacobi step on A u = 0 multiplies an eigenvector by 1 - omega*lambda/4
+    m, omega = 64, 2.0 / 3.0
+    A = O.TMat.of(W.poisson5(m))
+    lv = O.OLevel(A, None, None, M=O.jacobi_values(A, omega))
+    v, lam = eigvec(m, j, k)
+    u1 = O.sweep(lv, torch.zeros(m * m, dtype=torch.float64), torch.from_numpy(v)).numpy()
+    np.testing.assert_allclose(u1, (1 - omega * lam / 4) * v, atol=1e-14)
+
+
+def test_pseudo_inverse_hand_worked():
+    A = W._coo_to_csr(3, 3, np.array([0, 0, 1, 1, 1, 2, 2]), np.array([0, 1, 0, 1, 2, 1, 2]),
+                      np.array([2.0, -1, -1, 3, -2, -2, 4]))
+    T = O.TMat.of(A)
+    assert O.smoother_scale(T) == 2.0
+    q = O.pseudo_inverse_values(T, [1.0, 0.5, 0.25, 0.3, 0.1]).numpy()
+    rows = np.loadtxt(os.path.join(GOLDEN, "pinv_3x3.txt"), comments="#")
+    got = {(int(r), int(c)): v for r, c, v in zip(T.row.numpy(), T.col.numpy(), q)}
+    for r, c, v in rows:
+        assert abs(got[(int(r), int(c))] - v) < 1e-15
+
+
+def test_degree_one_coefficients_reproduce_jacobi():
+    A = O.TMat.of(W.fv_mesh("graded", 3000, 1)[0])
+    omega = 2.0 / 3.0
+    np.testing.assert_array_equal(O.pseudo_inverse_values(A, [omega, 0, 0, 0, 0]).numpy(),
+                                  O.jacobi_values(A, omega).numpy())
+
+
+def test_pseudo_inverse_symmetric_and_pattern():
+    Acsr = W.fv_mesh("band", 2000, 4, max_aspect=100.0)[0]
+    A = O.TMat.of(Acsr)
+    q = O.pseudo_inverse_values(A, [0.7, -0.1, 0.02, 0.3, -0.05])
+    Q = W.CSR(Acsr.n_rows, Acsr.n_cols, Acsr.row_ptr, Acsr.col, q.numpy()).to_dense()
+    np.testing.assert_allclose(Q, Q.T, rtol=0, atol=1e-15)
+    # f_o(0) = 0: entries where a_ij = 0 stay zero
+    Ad = Acsr.to_dense()
+    assert np.all(Q[Ad == 0] == 0)
+
+
+def test_cholesky_against_library_solve():
+    A = W.fv_mesh("uniform", 200, 9)[0]
+    Ad = A.to_dense()
+    L = O.cholesky(Ad)
+    np.testing.assert_allclose(L @ L.T, Ad, atol=1e-13 * np.abs(Ad).max())
+    assert np.all(np.triu(L, 1) == 0)
+    b = W.rhs_uniform(3, A.n_rows)
+    x = O.cholesky_solve(torch.from_numpy(L), torch.from_numpy(b)).numpy()
+    np.testing.assert_allclose(x, np.linalg.solve(Ad, b), rtol=1e-11, atol=1e-12)
+
+
+def _hier(A, smoother="jacobi", coeffs=None, **kw):
+    lv = S.build_hierarchy(A, **kw)
+    h = O.OHierarchy.of(lv)
+    if smoother == "jacobi":
+        h.set_jacobi()
+    else:
+        h.set_pseudo_inverse([coeffs] * len(lv))
+    return h
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "pinv"])
+def test_vcycle_operator_is_symmetric(smoother):
+    # nu1 = nu2 with a symmetric smoother makes the V-cycle preconditioner B
+    # symmetric: <B x, y> = <x, B y>.
+    A = W.fv_mesh("graded", 3000, 2)[0]
+    h = _hier(A, smoother, [0.6, 0.05, -0.01, 0.2, 0.03])
+    x = W.rhs_uniform(1, A.n_rows)
+    y = W.rhs_uniform(2, A.n_rows)
+    Bx, By = O.vcycle_operator_apply(h, x), O.vcycle_operator_apply(h, y)
+    lhs, rhs = Bx @ y, x @ By
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_vcycle_is_linear_in_b():
+    A = W.poisson5(32)
+    h = _hier(A, "pinv", [0.6, 0.05, -0.01, 0.2, 0.03])
+    x, y = W.rhs_uniform(1, A.n_rows), W.rhs_uniform(2, A.n_rows)
+    lhs = O.vcycle_operator_apply(h, 2.5 * x - 0.75 * y)
+    rhs = 2.5 * O.vcycle_operator_apply(h, x) - 0.75 * O.vcycle_operator_apply(h, y)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-12 * np.abs(rhs).max())
+
+
+@pytest.mark.parametrize("case", ["grid16", "delaunay300"])
+def test_converged_solution_equals_dense_direct_solve(case):
+    A = W.poisson5(16) if case == "grid16" else W.fv_mesh("graded", 300, 7)[0]
+    h = _hier(A, max_coarse=8)
+    assert len(h.levels) >= 3
+    b = W.rhs_uniform(4, A.n_rows)
+    res = O.solve(h, b, tol=1e-13, max_iter=200)
+    assert res.status == O.OK
+    np.testing.assert_allclose(res.x, np.linalg.solve(A.to_dense(), b), rtol=0,
+                               atol=1e-11 * np.abs(np.linalg.solve(A.to_dense(), b)).max())
+
+
+def test_single_level_vcycle_is_exact():
+    A = W.poisson5(6)
+    h = _hier(A)
+    assert len(h.levels) == 1
+    b = W.rhs_uniform(5, A.n_rows)
+    res = O.solve(h, b, tol=1e-12)
+    assert res.n_vcycles == 1 and res.history[-1] < 1e-14
+
+
+def test_c1_jacobi_amg_converges_fast():
+    # RS AMG with omega-Jacobi (2+2 sweeps) on the 5-point Laplacian is a
+    # textbook fast solver: 1e-8 in well under 15 cycles.
+    A = W.poisson5(64)
+    h = _hier(A)
+    res = O.solve(h, W.rhs_uniform(0, A.n_rows), tol=1e-8)
+    assert res.status == O.OK and res.n_vcycles <= 12
+    assert np.all(np.diff(res.history) < 0)
+
+
+def test_status_codes():
+    A = W.poisson5(32)
+    b = W.rhs_uniform(0, A.n_rows)
+    assert O.solve(_hier(A, "pinv", [5.0, 0, 0, 0, 0]), b).status == O.DIVERGED
+    assert O.solve(_hier(A), b, max_iter=2).status == O.MAXITER
+    assert O.solve(_hier(A, "pinv", [1e-6, 0, 0, 0, 0]), b).status == O.STAGNATED
+
+
+def test_relative_metric_zero_for_identical_smoothers():
+    A = W.poisson5(16)
+    hg = _hier(A, "pinv", [2.0 / 3.0, 0, 0, 0, 0], max_coarse=8)
+    hj = _hier(A, max_coarse=8)
+    assert abs(O.relative_metric(hg, hj, W.rhs_uniform(1, A.n_rows))) < 1e-12

@@ -1,0 +1,330 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module only generates inputs: counter-based random numbers (splitmix64),
+point sets, Delaunay meshes, the finite-volume Poisson matrix those meshes
+define, right-hand sides and random initial network parameters.  It holds none
+of the solver's arithmetic (no coarsening, smoothing, V-cycle or network
+evaluation), so both sides of every parity check can consume it.
+
+Sign convention: every matrix produced here is the symmetric positive
+(semi-)definite form of the Poisson operator (positive diagonal, non-positive
+off-diagonals), i.e. minus the negative semi-definite operator of Sec. 2.1.
+
+Workload recipes (all seeded; sizes follow the paper's workloads, the paper's
+own datasets are not available and these stand in for them):
+
+* ``poisson5(m)``: 5-point finite-difference Laplacian, unscaled stencil
+  (4, -1, -1, -1, -1), Dirichlet boundary eliminated, n = m*m.
+* ``fv_mesh(kind, n_points, seed)``: vertex-centred finite volumes on a
+  Delaunay triangulation of the unit square.  Edge coupling
+  w_ij = (cot a + cot b)/2 over the one or two triangles sharing edge ij
+  (the Voronoi-dual two-point flux); couplings that come out non-positive
+  (obtuse pairs) are clipped to zero and counted.  Dirichlet on x = 1
+  (those nodes eliminated, their couplings kept on the diagonal), Neumann
+  elsewhere.  Point-set kinds:
+    - "uniform": stratified jittered points, uniform density;
+    - "graded":  x-density proportional to (10 - 9x) (10:1 toward x = 0);
+    - "band":    graded points plus a horizontal band of anisotropic
+                 lattice rows centred on y = 0.5, cell aspect ratio growing
+                 geometrically (row height x1.1 per row) from
+                 ``max_aspect`` at the centre toward 1, the band kept
+                 inside 0.45 <= y <= 0.55.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "CSR", "splitmix64", "uniform01", "uniform_pm1", "poisson5", "fv_mesh",
+    "rhs_uniform", "rhs_zero_mean", "gcin_init_params", "c2_matrix",
+    "c3_batch", "c4_matrix", "GCIN_PARAM_SIZES",
+]
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+@dataclass
+class CSR:
+    """Square or rectangular CSR matrix: int32 row_ptr/col, float64 val."""
+    n_rows: int
+    n_cols: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n_rows, self.n_cols))
+        rows = np.repeat(np.arange(self.n_rows), np.diff(self.row_ptr))
+        np.add.at(d, (rows, self.col), self.val)
+        return d
+
+
+# ----------------------------------------------------------------------------
+# counter-based random numbers
+# ----------------------------------------------------------------------------
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Outputs offset+1 .. offset+n of the splitmix64 sequence started at seed."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of splitmix64."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform_pm1(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [-1, 1)."""
+    return 2.0 * uniform01(seed, n, offset) - 1.0
+
+
+def _sub_seed(seed: int, tag: int) -> int:
+    return int(splitmix64(seed * 1000003 + tag, 1)[0])
+
+
+# ----------------------------------------------------------------------------
+# structured 5-point Laplacian (64x64 is the small parity case)
+# ----------------------------------------------------------------------------
+def poisson5(m: int) -> CSR:
+    """5-point Laplacian on an m x m interior grid, Dirichlet eliminated."""
+    n = m * m
+    rows, cols, vals = [], [], []
+    idx = np.arange(n).reshape(m, m)
+    for di, dj, v in ((0, 0, 4.0), (-1, 0, -1.0), (1, 0, -1.0), (0, -1, -1.0), (0, 1, -1.0)):
+        i0, i1 = max(0, -di), m - max(0, di)
+        j0, j1 = max(0, -dj), m - max(0, dj)
+        src = idx[i0:i1, j0:j1].ravel()
+        dst = idx[i0 + di:i1 + di, j0 + dj:j1 + dj].ravel()
+        rows.append(src)
+        cols.append(dst)
+        vals.append(np.full(src.size, v))
+    return _coo_to_csr(n, n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def _coo_to_csr(nr, nc, r, c, v) -> CSR:
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    row_ptr = np.zeros(nr + 1, dtype=np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    return CSR(nr, nc, row_ptr.astype(np.int32), c.astype(np.int32), v.astype(np.float64))
+
+
+# ----------------------------------------------------------------------------
+# point sets
+# ----------------------------------------------------------------------------
+def _graded_x(u: np.ndarray) -> np.ndarray:
+    """Inverse CDF of the density (10 - 9x)/5.5 on [0, 1]."""
+    return (10.0 - np.sqrt(100.0 - 99.0 * u)) / 9.0
+
+
+def _stratified(n: int, seed: int, graded: bool) -> np.ndarray:
+    """About n jittered stratified points strictly inside the unit square."""
+    ny = max(2, int(round(np.sqrt(n))))
+    nx = max(2, int(round(n / ny)))
+    gx, gy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    gx, gy = gx.ravel().astype(np.float64), gy.ravel().astype(np.float64)
+    j = uniform_pm1(_sub_seed(seed, 1), 2 * gx.size).reshape(2, -1)
+    u = (gx + 0.5 + 0.35 * j[0]) / nx
+    v = (gy + 0.5 + 0.35 * j[1]) / ny
+    x = _graded_x(u) if graded else u
+    return np.stack([x, v], axis=1)
+
+
+def _boundary_points(per_side: int, graded: bool) -> tuple[np.ndarray, np.ndarray]:
+    """Points on the square's boundary; returns (points, on_dirichlet_side)."""
+    t = np.arange(per_side, dtype=np.float64) / per_side
+    xs = _graded_x(t) if graded else t
+    bottom = np.stack([xs, np.zeros_like(t)], 1)               # (x, 0), x in [0,1)
+    right = np.stack([np.ones_like(t), t], 1)                   # (1, y), y in [0,1)
+    top = np.stack([_graded_x(1.0 - t) if graded else 1.0 - t, np.ones_like(t)], 1)  # (x, 1), x in (0,1]
+    left = np.stack([np.zeros_like(t), 1.0 - t], 1)             # (0, y), y in (0,1]
+    pts = np.concatenate([bottom, right, top, left])
+    dir_mask = np.isclose(pts[:, 0], 1.0)
+    return pts, dir_mask
+
+
+def _band_rows(max_aspect: float, h: float) -> np.ndarray:
+    """y offsets (from 0.5) of anisotropic lattice rows, aspect 1 -> max_aspect."""
+    hy = h / max_aspect
+    ys, y = [0.0], 0.0
+    while hy < h and y + hy < 0.05:
+        y += hy
+        ys.append(y)
+        hy *= 1.1
+    ys = np.array(ys)
+    return np.concatenate([-ys[:0:-1], ys])
+
+
+def fv_points(kind: str, n_points: int, seed: int, max_aspect: float = 1000.0):
+    """Point set of the requested kind and its Dirichlet mask."""
+    graded = kind in ("graded", "band")
+    per_side = max(8, int(round(np.sqrt(n_points))))
+    bnd, bnd_dir = _boundary_points(per_side, graded)
+    n_int = max(16, n_points - bnd.shape[0])
+    if kind == "band":
+        h = 1.0 / per_side
+        rows = _band_rows(max_aspect, h)
+        half = rows.max() + 0.5 * h
+        n_cols = per_side
+        cu = (np.arange(n_cols) + 0.5) / n_cols
+        cx = _graded_x(cu)
+        BX, BY = np.meshgrid(cx, 0.5 + rows, indexing="ij")
+        # jitter of 1% of the local row spacing breaks cocircular quadruples
+        gaps = np.diff(rows)
+        dy = np.minimum(np.concatenate([[gaps[0]], gaps]), np.concatenate([gaps, [gaps[-1]]]))
+        DY = np.broadcast_to(dy[None, :], BX.shape).ravel()
+        jit = uniform_pm1(_sub_seed(seed, 2), 2 * BX.size).reshape(2, -1)
+        band = np.stack([BX.ravel() + 0.01 * DY * jit[0], BY.ravel() + 0.01 * DY * jit[1]], 1)
+        n_iso = max(16, n_int - band.shape[0])
+        iso = _stratified(int(n_iso / (1.0 - 2 * half)), seed, True)
+        iso = iso[np.abs(iso[:, 1] - 0.5) > half + 0.35 * h]
+        interior = np.concatenate([iso, band])
+    else:
+        interior = _stratified(n_int, seed, graded)
+    pts = np.concatenate([bnd, interior])
+    dmask = np.concatenate([bnd_dir, np.zeros(interior.shape[0], dtype=bool)])
+    return pts, dmask
+
+
+# ----------------------------------------------------------------------------
+# vertex-centred finite-volume assembly on a Delaunay triangulation
+# ----------------------------------------------------------------------------
+def delaunay_fv(points: np.ndarray, dirichlet: np.ndarray):
+    """Assemble the SPD FV Laplacian; returns (CSR, stats dict)."""
+    from scipy.spatial import Delaunay
+
+    tri = Delaunay(points).simplices.astype(np.int64)
+    n_all = points.shape[0]
+    ea, eb, ew = [], [], []
+    for k in range(3):
+        p0 = tri[:, k]
+        pa = tri[:, (k + 1) % 3]
+        pb = tri[:, (k + 2) % 3]
+        e1 = points[pa] - points[p0]
+        e2 = points[pb] - points[p0]
+        cross = np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+        dot = e1[:, 0] * e2[:, 0] + e1[:, 1] * e2[:, 1]
+        ok = cross > 1e-300
+        cot = np.where(ok, dot / np.where(ok, cross, 1.0), 0.0)
+        ea.append(np.minimum(pa, pb))
+        eb.append(np.maximum(pa, pb))
+        ew.append(0.5 * cot)
+    ea, eb, ew = np.concatenate(ea), np.concatenate(eb), np.concatenate(ew)
+    key = ea * n_all + eb
+    uk, inv = np.unique(key, return_inverse=True)
+    w = np.bincount(inv, weights=ew)
+    ia, ib = uk // n_all, uk % n_all
+    n_clipped = int(np.count_nonzero(w <= 0.0))
+    wmax_node = np.zeros(n_all)
+    np.maximum.at(wmax_node, ia, np.maximum(w, 0))
+    np.maximum.at(wmax_node, ib, np.maximum(w, 0))
+    keep = w > 1e-12 * np.maximum(wmax_node[ia], wmax_node[ib])
+    ia, ib, w = ia[keep], ib[keep], w[keep]
+    diag = np.zeros(n_all)
+    np.add.at(diag, ia, w)
+    np.add.at(diag, ib, w)
+    live = ~dirichlet
+    newid = -np.ones(n_all, dtype=np.int64)
+    newid[live] = np.arange(int(live.sum()))
+    both = live[ia] & live[ib]
+    ra, rb, rw = newid[ia[both]], newid[ib[both]], w[both]
+    n = int(live.sum())
+    rows = np.concatenate([ra, rb, np.arange(n)])
+    cols = np.concatenate([rb, ra, np.arange(n)])
+    vals = np.concatenate([-rw, -rw, diag[live]])
+    A = _coo_to_csr(n, n, rows, cols, vals)
+    stats = {"n_points": n_all, "n_triangles": int(tri.shape[0]), "n_clipped": n_clipped,
+             "n_dirichlet": int(dirichlet.sum()), "n": n, "nnz": A.nnz}
+    return A, stats
+
+
+def fv_mesh(kind: str, n_points: int, seed: int, max_aspect: float = 1000.0):
+    pts, dmask = fv_points(kind, n_points, seed, max_aspect)
+    return delaunay_fv(pts, dmask)
+
+
+# ----------------------------------------------------------------------------
+# the named workloads
+# ----------------------------------------------------------------------------
+def c2_matrix(seed: int = 0) -> CSR:
+    """50k-point graded (10:1) Delaunay FV Laplacian."""
+    return fv_mesh("graded", 50_000, seed)[0]
+
+
+def c3_batch(n_meshes: int = 64, seed: int = 0, n_min: int = 2000, n_max: int = 20000):
+    """Training batch: meshes of uneven size cycling uniform/graded/band kinds."""
+    kinds = ("uniform", "graded", "band")
+    sizes = n_min + (splitmix64(_sub_seed(seed, 7), n_meshes) % np.uint64(n_max - n_min + 1)).astype(np.int64)
+    out = []
+    for m in range(n_meshes):
+        kind = kinds[m % 3]
+        out.append(fv_mesh(kind, int(sizes[m]), seed * 1000 + m, max_aspect=100.0)[0])
+    return out
+
+
+def c4_matrix(seed: int = 0, n_points: int = 2_500_000) -> CSR:
+    """2.5M-point graded mesh with an anisotropic band (aspect up to 1000)."""
+    return fv_mesh("band", n_points, seed, max_aspect=1000.0)[0]
+
+
+def rhs_uniform(seed: int, n: int) -> np.ndarray:
+    """b ~ U[-1, 1)."""
+    return uniform_pm1(_sub_seed(seed, 11), n)
+
+
+def rhs_zero_mean(seed: int, n: int) -> np.ndarray:
+    """b = xi - mean(xi), xi ~ U[-1, 1)."""
+    xi = uniform_pm1(_sub_seed(seed, 13), n)
+    return xi - xi.mean()
+
+
+# ----------------------------------------------------------------------------
+# random initial network parameters
+# ----------------------------------------------------------------------------
+# (size, fan_in) of each parameter tensor in flat order.  The order is the
+# parameter-vector interface of the coefficient network: conv linears
+# (weight [in][out] then bias) for 4 layers, instance-norm affine (gamma, beta)
+# for 4 layers, per-layer readout linears 128->32, layer norm (gamma, beta),
+# head linears 128->128, 128->64, 64->5.  fan_in = 0 marks gamma (init 1) and
+# -1 marks beta (init 0).
+GCIN_PARAM_SIZES = (
+    [(2 * 64, 2), (64, 2)]
+    + [(64 * 64, 64), (64, 64)] * 3
+    + [(64, 0), (64, -1)] * 4
+    + [(128 * 32, 128), (32, 128)] * 4
+    + [(128, 0), (128, -1)]
+    + [(128 * 128, 128), (128, 128), (128 * 64, 128), (64, 128), (64 * 5, 64), (5, 64)]
+)
+
+
+def gcin_init_params(seed: int, last_bias=(2.0 / 3.0, 0.0, 0.0, 0.0, 0.0), last_scale: float = 0.1) -> np.ndarray:
+    """Flat float64 parameter vector: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights.
+
+    The last layer's weights are scaled by ``last_scale`` and its bias set to
+    ``last_bias`` so that an untrained network starts near weighted Jacobi.
+    """
+    parts = []
+    for t, (size, fan_in) in enumerate(GCIN_PARAM_SIZES):
+        if fan_in == 0:
+            parts.append(np.ones(size))
+        elif fan_in == -1:
+            parts.append(np.zeros(size))
+        else:
+            parts.append(uniform_pm1(_sub_seed(seed, 100 + t), size) / np.sqrt(fan_in))
+    parts[-2] = parts[-2] * last_scale
+    parts[-1] = np.asarray(last_bias, dtype=np.float64).copy()
+    return np.concatenate(parts)
