@@ -1,0 +1,240 @@
+/*
+ * amg_gnn.h -- C ABI of the GB300 (sm_103a) GNN-smoothed algebraic multigrid
+ * pressure solver ("Acceleration of an algebraic multigrid pressure solver
+ * using graph neural networks").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices follow the symmetric positive definite sign convention: positive
+ *   diagonal, non-positive off-diagonal couplings (the negative of the
+ *   negative semi-definite operator of Sec. 2.1).  A must be symmetric with
+ *   every diagonal entry present in its pattern.
+ * - CSR arrays are 0-based, int32 row pointers and column indices with
+ *   ascending columns inside each row, float64 values.
+ * - Host pointers are read during the call only; the library copies what it
+ *   keeps.  Device pointers ("d_" prefix) are caller-owned device memory on
+ *   the context's device and must stay valid until the work enqueued on the
+ *   given stream has finished.  A NULL stream means the legacy default stream.
+ * - Every int-returning call returns AMG_OK (0) or a negative AMG_ERR_* code;
+ *   amg_last_error() then describes the failure.  Errors from argument checks
+ *   leave the context unchanged.  A context is not thread-safe.
+ */
+#ifndef AMG_GNN_H
+#define AMG_GNN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMG_OK               0
+#define AMG_ERR_ARG         -1  /* invalid argument or size                         */
+#define AMG_ERR_CUDA        -2  /* a CUDA runtime call failed                       */
+#define AMG_ERR_NOT_SPD     -3  /* coarsest matrix not positive definite            */
+#define AMG_ERR_DIVERGED    -4  /* residual not finite or > 1e3 x initial residual  */
+#define AMG_ERR_STAGNATED   -5  /* < 1% residual reduction over 10 V-cycles         */
+#define AMG_ERR_MAXITER     -6  /* max_iter V-cycles without reaching the tolerance */
+#define AMG_ERR_DEVICE_FLAG -7  /* a kernel reported an invalid index or value      */
+#define AMG_ERR_STATE       -8  /* call made in the wrong order (e.g. no hierarchy) */
+
+/* precision of the V-cycle (the outer residual/update are always FP64) */
+#define AMG_FP64         0
+#define AMG_FP32_IN_FP64 1
+
+/* smoother of the V-cycle */
+#define AMG_SMOOTHER_JACOBI 0   /* relaxed Jacobi, Q^-1 = omega D^-1 (Sec. 2.3)          */
+#define AMG_SMOOTHER_GNN    1   /* sparse pseudo-inverse from coefficients (Sec. 3.1)    */
+
+#define AMG_GCIN_NUM_PARAMS 55045   /* App. A.1 */
+
+typedef struct amg_ctx amg_ctx;
+
+typedef struct {
+    int n_rows;
+    int n_cols;
+    long long nnz;
+    const int *row_ptr;   /* n_rows + 1 */
+    const int *col;       /* nnz        */
+    const double *val;    /* nnz        */
+} amg_csr;
+
+typedef struct {
+    int nu1;          /* pre-smoothing sweeps per level  (Sec. 4: 2)                 */
+    int nu2;          /* post-smoothing sweeps per level (Sec. 4: 2)                 */
+    int max_levels;   /* hierarchy depth cap (Table train_hyper: 10)                 */
+    int max_coarse;   /* stop coarsening at n <= max_coarse (64)                     */
+    int max_iter;     /* V-cycle cap of a solve (Sec. 4: 500)                        */
+    int precision;    /* AMG_FP64 or AMG_FP32_IN_FP64                                */
+    int smoother;     /* AMG_SMOOTHER_JACOBI or AMG_SMOOTHER_GNN                     */
+    double omega;     /* Jacobi relaxation (Sec. 4: 2/3)                             */
+    double theta;     /* Ruge-Stueben strength threshold (Sec. 4: 0.25)              */
+    int device;       /* CUDA device ordinal                                         */
+} amg_options;
+
+/* Fill *opt with the paper's settings: nu1 = nu2 = 2, max_levels = 10,
+ * max_coarse = 64, max_iter = 500, FP32 V-cycle in FP64 refinement, Jacobi,
+ * omega = 2/3, theta = 0.25, device 0 (Sec. 4, Table train_hyper). */
+void amg_default_options(amg_options *opt);
+
+/* Create a context bound to opt->device.  *ctx receives the handle (NULL on
+ * error).  Errors: AMG_ERR_ARG for out-of-range options, AMG_ERR_CUDA. */
+int amg_create(amg_ctx **ctx, const amg_options *opt);
+
+/* Release every host and device resource of ctx (NULL is allowed). */
+void amg_destroy(amg_ctx *ctx);
+
+/* Message of the last failing call on ctx (never NULL; "" after success).
+ * With ctx == NULL: the message of the last failing amg_create. */
+const char *amg_last_error(const amg_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Setup phase (Sec. 2.2; Algorithm 1 step 2), host C++ -- off the hot path.
+ * ------------------------------------------------------------------------ */
+
+/* Setup-AMG-Hierarchy: build {A_l, P_l, R_l} from A by classical
+ * Ruge-Stueben coarsening (strength theta), direct interpolation, R = P^T and
+ * the Galerkin product A_c = R A P (Sec. 2.2), until n <= max_coarse, the
+ * level cap, or a coarse level keeping > 90% of the points; then upload it to
+ * the device and factor the coarsest level (as amg_load_hierarchy).
+ * Replaces any previous hierarchy and resets the smoother to Jacobi.
+ * Errors: AMG_ERR_ARG (non-square, bad CSR), AMG_ERR_NOT_SPD, AMG_ERR_CUDA. */
+int amg_setup(amg_ctx *ctx, const amg_csr *A);
+
+/* Load a caller-built hierarchy: A[0..n_levels-1] (finest first),
+ * P[0..n_levels-2] (n_l x n_{l+1}) and R[0..n_levels-2] (n_{l+1} x n_l);
+ * R may be NULL, then R = P^T is formed.  Copies everything to the device,
+ * computes s_l = max|A_l - D_l| for every level (Sec. 3.1) and factors the
+ * coarsest A by dense Cholesky on the device (FP64).
+ * Errors: AMG_ERR_ARG (sizes disagree), AMG_ERR_NOT_SPD, AMG_ERR_CUDA. */
+int amg_load_hierarchy(amg_ctx *ctx, int n_levels, const amg_csr *A, const amg_csr *P, const amg_csr *R);
+
+/* Number of levels of the loaded hierarchy (0 if none). */
+int amg_num_levels(const amg_ctx *ctx);
+
+/* Sizes of level `level`: rows, nnz of A_l and nnz of P_l (0 on the
+ * coarsest level).  Any output pointer may be NULL. */
+int amg_level_info(const amg_ctx *ctx, int level, int *n, long long *nnz_A, long long *nnz_P);
+
+/* Copy level `level`'s A_l and P_l (host hierarchy) into caller buffers
+ * sized by amg_level_info; the P buffers are ignored (may be NULL) on the
+ * coarsest level.  Errors: AMG_ERR_ARG, AMG_ERR_STATE. */
+int amg_get_level(const amg_ctx *ctx, int level, int *A_row_ptr, int *A_col, double *A_val,
+                  int *P_row_ptr, int *P_col, double *P_val);
+
+/* Smoother scale s_l = max |A_l - D_l| of every level as computed on the
+ * device (Sec. 3.1); s_out has amg_num_levels() entries. */
+int amg_get_scales(const amg_ctx *ctx, double *s_out);
+
+/* ------------------------------------------------------------------------
+ * Smoother selection (Sec. 2.3, Sec. 3.1)
+ * ------------------------------------------------------------------------ */
+
+/* Relaxed Jacobi on every level: Q^-1 = omega D^-1 (Sec. 2.3). */
+int amg_set_jacobi(amg_ctx *ctx, double omega);
+
+/* Sparse pseudo-inverse smoother (Sec. 3.1) on every smoothed level l from
+ * c[5 l .. 5 l + 4] = (d0, d1, d2, o1, o2):
+ *   q_ii^-1 = (d0 + d1 x + d2 x^2) / a_ii,        x = a_ii / s_l
+ *   q_ij^-1 = (o1 x + o2 x^2) / (a_ii + a_jj),    x = a_ij / s_l.
+ * c holds n_rows >= amg_num_levels() - 1 rows (extra rows ignored).
+ * The Q^-1 values are assembled on the device once, in FP64 and in the
+ * V-cycle precision.  c = (omega, 0, 0, 0, 0) reproduces weighted Jacobi. */
+int amg_set_coeffs(amg_ctx *ctx, const double *c, int n_rows);
+
+/* Read back the smoother values of level `level` on A_l's pattern (nnz_A
+ * entries, FP64 copy).  Jacobi leaves zeros off the diagonal. */
+int amg_get_smoother(const amg_ctx *ctx, int level, double *q_out);
+
+/* ------------------------------------------------------------------------
+ * Coefficient network (Sec. 3.2, App. A.1; Algorithm 1 steps 3-6)
+ * ------------------------------------------------------------------------ */
+
+/* Load the GCIN parameters: n == AMG_GCIN_NUM_PARAMS floats in the flat
+ * order conv1 W(2x64) b(64); conv2..4 W(64x64) b(64); IN1..4 gamma(64)
+ * beta(64); readout1..4 W(128x32) b(32); LN gamma(128) beta(128); head
+ * W(128x128) b(128), W(128x64) b(64), W(64x5) b(5); weights [in][out]
+ * row-major.  Errors: AMG_ERR_ARG (wrong n), AMG_ERR_CUDA. */
+int gnn_load_params(amg_ctx *ctx, const float *theta, long long n);
+
+/* Batched GCIN inference over every level graph of the loaded hierarchy
+ * (node features [a_ii, deg_i], edge weights a_ij, self-loop weight a_ii),
+ * then amg_set_coeffs with the result.  c_out (host, may be NULL) receives
+ * amg_num_levels() rows of 5.  Errors: AMG_ERR_STATE (no hierarchy or no
+ * parameters), AMG_ERR_CUDA. */
+int gnn_predict_coeffs(amg_ctx *ctx, double *c_out);
+
+/* ------------------------------------------------------------------------
+ * Solve phase (Sec. 2.1, 2.2; Algorithm 1 step 9) -- the hot path
+ * ------------------------------------------------------------------------ */
+
+/* Solve A x = b.  x holds the initial guess on entry and the last iterate on
+ * return.  Each V-cycle runs in the context's precision as a preconditioner
+ * of an FP64 iterative refinement x <- x + V(b - A x) (identical to the
+ * stationary V-cycle iteration of Sec. 2.1 in exact arithmetic).  Stops when
+ * ||b - A x||_2 / ||b||_2 <= rtol or after max_iter cycles.
+ * n_vcycles (may be NULL) receives the number of V-cycles; res_hist (may be
+ * NULL, max_iter + 1 entries) the relative residual before cycle 0 and after
+ * every cycle.  Returns AMG_OK, AMG_ERR_DIVERGED, AMG_ERR_STAGNATED or
+ * AMG_ERR_MAXITER (x and res_hist are filled in every case), AMG_ERR_STATE,
+ * AMG_ERR_CUDA.  Host vectors of n_0 doubles. */
+int amg_solve(amg_ctx *ctx, const double *b, double *x, double rtol, int *n_vcycles, double *res_hist);
+
+/* amg_solve with device vectors d_b, d_x (n_0 doubles each) enqueued on
+ * `stream` (a cudaStream_t); n_vcycles/res_hist are host outputs and the
+ * call returns after the solve has finished on the stream. */
+int amg_solve_device(amg_ctx *ctx, const double *d_b, double *d_x, double rtol, void *stream,
+                     int *n_vcycles, double *res_hist);
+
+/* One V-cycle from a zero initial guess: d_e = B d_r (Sec. 2.2), in the
+ * context's precision (inputs/outputs FP64, n_0 each).  Asynchronous. */
+int amg_vcycle_device(amg_ctx *ctx, const double *d_r, double *d_e, void *stream);
+
+/* n_sweeps smoothing steps u <- u + Q_l^-1 (b - A_l u) on level `level`
+ * (d_b, d_u: n_l doubles; d_u is updated in place).  Asynchronous. */
+int amg_smooth_device(amg_ctx *ctx, int level, const double *d_b, double *d_u, int n_sweeps, void *stream);
+
+/* d_y = A_l d_x on level `level` in the context's precision.  Asynchronous. */
+int amg_spmv_device(amg_ctx *ctx, int level, const double *d_x, double *d_y, void *stream);
+
+/* Relative validation metric of Sec. 3.3 on right-hand side b (host, n_0):
+ * log10(||r_1^GNN|| / ||r_1^omega-J||) after one V-cycle from x = 0 with the
+ * current pseudo-inverse smoother and with omega-Jacobi.  A value >= 0 means
+ * the learned smoother does not beat Jacobi on this matrix. */
+int amg_judge(amg_ctx *ctx, const double *b, double *metric);
+
+/* ------------------------------------------------------------------------
+ * Training (Sec. 3.3, Algorithm 1, Table train_hyper)
+ * ------------------------------------------------------------------------ */
+
+typedef struct gcin_trainer gcin_trainer;
+
+/* Trainer owning the parameters, their gradient and Adam moments on
+ * `device`.  theta0: AMG_GCIN_NUM_PARAMS floats (copied). */
+int gcin_trainer_create(gcin_trainer **tr, int device, const float *theta0);
+void gcin_trainer_destroy(gcin_trainer *tr);
+const char *gcin_trainer_last_error(const gcin_trainer *tr);
+int gcin_trainer_get_params(const gcin_trainer *tr, float *theta_out);
+
+/* Batched inference over every level of every problem (Algorithm 1 step 6),
+ * keeping the activations for gcin_trainer_backward.  c_out (host) receives
+ * sum_m amg_num_levels(problems[m]) rows of 5, problem by problem. */
+int gcin_trainer_forward(gcin_trainer *tr, int n_problems, amg_ctx *const *problems, double *c_out);
+
+/* Backward of the last forward: dc (host, same layout as c_out) -> the
+ * parameter gradient (kept on the device; dtheta_out, host, may be NULL). */
+int gcin_trainer_backward(gcin_trainer *tr, const double *dc, double *dtheta_out);
+
+/* Clip the kept gradient to global norm max_norm, then one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr. */
+int gcin_trainer_adam_step(gcin_trainer *tr, double lr, double max_norm);
+
+/* Loss of one problem (Sec. 3.3, N_vc = 1, u_0 = 0):
+ * L = log10(||f - A u_1|| / ||f||), u_1 = one V-cycle of the pseudo-inverse
+ * smoother with coefficients c (n_levels rows of 5) on f (host, n_0), and its
+ * gradient dL/dc (host, n_levels rows of 5) from the hand-written adjoint of
+ * the V-cycle.  Runs in the context's precision. */
+int amg_loss_grad(amg_ctx *ctx, const double *c, const double *f, double *loss, double *dc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_GNN_H */

@@ -1,0 +1,365 @@
+"""Thin Python binding of the C ABI in include/amg_gnn.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; every step of
+the solve and of the network runs in libamggnn.so's CUDA kernels.  The
+library must have been built (``__graft_entry__.build()``); importing this
+module without it raises immediately -- there is no fallback.
+
+Matrices are passed as any object with ``n_rows, n_cols, row_ptr, col, val``
+(e.g. ``workloads.CSR``).  Device vectors are torch CUDA tensors (float64);
+streams default to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+AMG_OK = 0
+AMG_ERR_ARG = -1
+AMG_ERR_CUDA = -2
+AMG_ERR_NOT_SPD = -3
+AMG_ERR_DIVERGED = -4
+AMG_ERR_STAGNATED = -5
+AMG_ERR_MAXITER = -6
+AMG_ERR_DEVICE_FLAG = -7
+AMG_ERR_STATE = -8
+AMG_FP64 = 0
+AMG_FP32_IN_FP64 = 1
+AMG_SMOOTHER_JACOBI = 0
+AMG_SMOOTHER_GNN = 1
+AMG_GCIN_NUM_PARAMS = 55045
+
+SOLVE_STATUSES = (AMG_OK, AMG_ERR_DIVERGED, AMG_ERR_STAGNATED, AMG_ERR_MAXITER)
+
+
+class AmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class amg_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int), ("n_cols", C.c_int), ("nnz", C.c_longlong),
+                ("row_ptr", C.POINTER(C.c_int)), ("col", C.POINTER(C.c_int)), ("val", C.POINTER(C.c_double))]
+
+
+class amg_options(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_levels", C.c_int), ("max_coarse", C.c_int),
+                ("max_iter", C.c_int), ("precision", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
+                ("theta", C.c_double), ("device", C.c_int)]
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded libamggnn.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build it with __graft_entry__.build() "
+                               "(the solver has no CPU fallback)")
+        _LIB = C.CDLL(_build.LIB)
+        _declare(_LIB)
+    return _LIB
+
+
+def _declare(L):
+    P, I, D, LL, V = C.c_void_p, C.c_int, C.c_double, C.c_longlong, None
+    pd, pi, pf = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_float)
+    sig = {
+        "amg_default_options": (V, [C.POINTER(amg_options)]),
+        "amg_create": (I, [C.POINTER(P), C.POINTER(amg_options)]),
+        "amg_destroy": (V, [P]),
+        "amg_last_error": (C.c_char_p, [P]),
+        "amg_setup": (I, [P, C.POINTER(amg_csr)]),
+        "amg_load_hierarchy": (I, [P, I, C.POINTER(amg_csr), C.POINTER(amg_csr), C.POINTER(amg_csr)]),
+        "amg_num_levels": (I, [P]),
+        "amg_level_info": (I, [P, I, pi, C.POINTER(LL), C.POINTER(LL)]),
+        "amg_get_level": (I, [P, I, pi, pi, pd, pi, pi, pd]),
+        "amg_get_scales": (I, [P, pd]),
+        "amg_set_jacobi": (I, [P, D]),
+        "amg_set_coeffs": (I, [P, pd, I]),
+        "amg_get_smoother": (I, [P, I, pd]),
+        "gnn_load_params": (I, [P, pf, LL]),
+        "gnn_predict_coeffs": (I, [P, pd]),
+        "amg_solve": (I, [P, pd, pd, D, pi, pd]),
+        "amg_solve_device": (I, [P, P, P, D, P, pi, pd]),
+        "amg_vcycle_device": (I, [P, P, P, P]),
+        "amg_smooth_device": (I, [P, I, P, P, I, P]),
+        "amg_spmv_device": (I, [P, I, P, P, P]),
+        "amg_judge": (I, [P, pd, pd]),
+        "gcin_trainer_create": (I, [C.POINTER(P), I, pf]),
+        "gcin_trainer_destroy": (V, [P]),
+        "gcin_trainer_last_error": (C.c_char_p, [P]),
+        "gcin_trainer_get_params": (I, [P, pf]),
+        "gcin_trainer_forward": (I, [P, I, C.POINTER(P), pd]),
+        "gcin_trainer_backward": (I, [P, pd, pd]),
+        "gcin_trainer_adam_step": (I, [P, D, D]),
+        "amg_loss_grad": (I, [P, pd, pd, pd, pd]),
+    }
+    for name, (res, args) in sig.items():
+        if not hasattr(L, name):
+            continue
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def exported_symbols():
+    """Names of the C entry points this binding knows about."""
+    return ["amg_default_options", "amg_create", "amg_destroy", "amg_last_error", "amg_setup",
+            "amg_load_hierarchy", "amg_num_levels", "amg_level_info", "amg_get_level", "amg_get_scales",
+            "amg_set_jacobi", "amg_set_coeffs", "amg_get_smoother", "gnn_load_params", "gnn_predict_coeffs",
+            "amg_solve", "amg_solve_device", "amg_vcycle_device", "amg_smooth_device", "amg_spmv_device",
+            "amg_judge", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
+            "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
+            "gcin_trainer_adam_step", "amg_loss_grad"]
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _csr(M, keep):
+    rp = np.ascontiguousarray(M.row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(M.col, dtype=np.int32)
+    val = np.ascontiguousarray(M.val, dtype=np.float64)
+    keep.extend([rp, col, val])
+    return amg_csr(int(M.n_rows), int(M.n_cols), int(rp[-1]), _iptr(rp), _iptr(col), _dptr(val))
+
+
+def _check(ctx, rc, allowed=(AMG_OK,)):
+    if rc not in allowed:
+        raise AmgError(rc, amg_last_error(ctx))
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dev(t):
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def amg_default_options(**overrides) -> amg_options:
+    o = amg_options()
+    lib().amg_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def amg_create(opt: amg_options | None = None, **overrides):
+    if opt is None:
+        opt = amg_default_options(**overrides)
+    h = C.c_void_p()
+    rc = lib().amg_create(C.byref(h), C.byref(opt))
+    if rc != AMG_OK:
+        raise AmgError(rc, amg_last_error(None))
+    return h
+
+
+def amg_destroy(ctx):
+    lib().amg_destroy(ctx)
+
+
+def amg_last_error(ctx) -> str:
+    return lib().amg_last_error(ctx).decode()
+
+
+def amg_setup(ctx, A):
+    keep = []
+    m = _csr(A, keep)
+    return _check(ctx, lib().amg_setup(ctx, C.byref(m)))
+
+
+def amg_load_hierarchy(ctx, A_list, P_list, R_list=None):
+    keep = []
+    nl = len(A_list)
+    As = (amg_csr * nl)(*[_csr(A, keep) for A in A_list])
+    Ps = (amg_csr * max(1, nl - 1))(*[_csr(P, keep) for P in P_list]) if nl > 1 else None
+    Rs = (amg_csr * max(1, nl - 1))(*[_csr(R, keep) for R in R_list]) if (R_list and nl > 1) else None
+    return _check(ctx, lib().amg_load_hierarchy(ctx, nl, As, Ps, Rs))
+
+
+def amg_num_levels(ctx) -> int:
+    return lib().amg_num_levels(ctx)
+
+
+def amg_level_info(ctx, level):
+    n, na, npp = C.c_int(), C.c_longlong(), C.c_longlong()
+    _check(ctx, lib().amg_level_info(ctx, level, C.byref(n), C.byref(na), C.byref(npp)))
+    return n.value, na.value, npp.value
+
+
+def amg_get_level(ctx, level):
+    """Returns (A, P) as dicts of numpy arrays (P is None on the coarsest level)."""
+    n, na, npp = amg_level_info(ctx, level)
+    arp, acol, aval = np.zeros(n + 1, np.int32), np.zeros(na, np.int32), np.zeros(na)
+    coarse = level == amg_num_levels(ctx) - 1
+    if coarse:
+        _check(ctx, lib().amg_get_level(ctx, level, _iptr(arp), _iptr(acol), _dptr(aval), None, None, None))
+        return dict(row_ptr=arp, col=acol, val=aval, n=n), None
+    prp, pcol, pval = np.zeros(n + 1, np.int32), np.zeros(npp, np.int32), np.zeros(npp)
+    _check(ctx, lib().amg_get_level(ctx, level, _iptr(arp), _iptr(acol), _dptr(aval), _iptr(prp), _iptr(pcol),
+                                    _dptr(pval)))
+    nc = amg_level_info(ctx, level + 1)[0]
+    return dict(row_ptr=arp, col=acol, val=aval, n=n), dict(row_ptr=prp, col=pcol, val=pval, n=n, nc=nc)
+
+
+def amg_get_scales(ctx) -> np.ndarray:
+    s = np.zeros(amg_num_levels(ctx))
+    _check(ctx, lib().amg_get_scales(ctx, _dptr(s)))
+    return s
+
+
+def amg_set_jacobi(ctx, omega=2.0 / 3.0):
+    return _check(ctx, lib().amg_set_jacobi(ctx, float(omega)))
+
+
+def amg_set_coeffs(ctx, c):
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, 5))
+    return _check(ctx, lib().amg_set_coeffs(ctx, _dptr(c), c.shape[0]))
+
+
+def amg_get_smoother(ctx, level) -> np.ndarray:
+    q = np.zeros(amg_level_info(ctx, level)[1])
+    _check(ctx, lib().amg_get_smoother(ctx, level, _dptr(q)))
+    return q
+
+
+def gnn_load_params(ctx, theta):
+    t = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+    return _check(ctx, lib().gnn_load_params(ctx, _fptr(t), t.size))
+
+
+def gnn_predict_coeffs(ctx) -> np.ndarray:
+    c = np.zeros((amg_num_levels(ctx), 5))
+    _check(ctx, lib().gnn_predict_coeffs(ctx, _dptr(c)))
+    return c
+
+
+def amg_solve(ctx, b, x0=None, rtol=1e-8, max_iter=None):
+    """Returns (status, x, history)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    cap = (max_iter if max_iter is not None else 100000) + 1
+    hist = np.zeros(cap)
+    nvc = C.c_int()
+    rc = _check(ctx, lib().amg_solve(ctx, _dptr(b), _dptr(x), float(rtol), C.byref(nvc), _dptr(hist)),
+                SOLVE_STATUSES)
+    return rc, x, hist[:nvc.value + 1].copy()
+
+
+def amg_solve_device(ctx, d_b, d_x, rtol=1e-8, stream=None, hist_cap=100001):
+    """Solve in place on device tensors; returns (status, history)."""
+    hist = np.zeros(hist_cap)
+    nvc = C.c_int()
+    rc = _check(ctx, lib().amg_solve_device(ctx, _dev(d_b), _dev(d_x), float(rtol), _stream(stream),
+                                            C.byref(nvc), _dptr(hist)), SOLVE_STATUSES)
+    return rc, hist[:nvc.value + 1].copy()
+
+
+def amg_vcycle_device(ctx, d_r, d_e, stream=None):
+    return _check(ctx, lib().amg_vcycle_device(ctx, _dev(d_r), _dev(d_e), _stream(stream)))
+
+
+def amg_smooth_device(ctx, level, d_b, d_u, n_sweeps, stream=None):
+    return _check(ctx, lib().amg_smooth_device(ctx, level, _dev(d_b), _dev(d_u), int(n_sweeps), _stream(stream)))
+
+
+def amg_spmv_device(ctx, level, d_x, d_y, stream=None):
+    return _check(ctx, lib().amg_spmv_device(ctx, level, _dev(d_x), _dev(d_y), _stream(stream)))
+
+
+def amg_judge(ctx, b) -> float:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m = C.c_double()
+    _check(ctx, lib().amg_judge(ctx, _dptr(b), C.byref(m)))
+    return m.value
+
+
+def amg_loss_grad(ctx, c, f):
+    """(loss, dL/dc) of one V-cycle from zero (Sec. 3.3)."""
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, 5))
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    loss = C.c_double()
+    dc = np.zeros_like(c)
+    _check(ctx, lib().amg_loss_grad(ctx, _dptr(c), _dptr(f), C.byref(loss), _dptr(dc)))
+    return loss.value, dc
+
+
+# trainer --------------------------------------------------------------------
+def _tcheck(tr, rc):
+    if rc != AMG_OK:
+        raise AmgError(rc, gcin_trainer_last_error(tr))
+    return rc
+
+
+def gcin_trainer_create(theta0, device=0):
+    t = np.ascontiguousarray(np.asarray(theta0, dtype=np.float32))
+    if t.size != AMG_GCIN_NUM_PARAMS:
+        raise ValueError("theta0 must have 55045 entries")
+    h = C.c_void_p()
+    rc = lib().gcin_trainer_create(C.byref(h), int(device), _fptr(t))
+    if rc != AMG_OK:
+        raise AmgError(rc, "gcin_trainer_create failed")
+    return h
+
+
+def gcin_trainer_destroy(tr):
+    lib().gcin_trainer_destroy(tr)
+
+
+def gcin_trainer_last_error(tr) -> str:
+    return lib().gcin_trainer_last_error(tr).decode()
+
+
+def gcin_trainer_get_params(tr) -> np.ndarray:
+    t = np.zeros(AMG_GCIN_NUM_PARAMS, np.float32)
+    _tcheck(tr, lib().gcin_trainer_get_params(tr, _fptr(t)))
+    return t
+
+
+def gcin_trainer_forward(tr, ctxs) -> np.ndarray:
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    rows = sum(amg_num_levels(c) for c in ctxs)
+    out = np.zeros((rows, 5))
+    _tcheck(tr, lib().gcin_trainer_forward(tr, len(ctxs), arr, _dptr(out)))
+    return out
+
+
+def gcin_trainer_backward(tr, dc) -> np.ndarray:
+    dc = np.ascontiguousarray(np.asarray(dc, dtype=np.float64))
+    g = np.zeros(AMG_GCIN_NUM_PARAMS)
+    _tcheck(tr, lib().gcin_trainer_backward(tr, _dptr(dc), _dptr(g)))
+    return g
+
+
+def gcin_trainer_adam_step(tr, lr=1e-3, max_norm=1.0):
+    return _tcheck(tr, lib().gcin_trainer_adam_step(tr, float(lr), float(max_norm)))

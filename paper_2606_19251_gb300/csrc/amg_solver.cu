@@ -1,0 +1,1094 @@
+// Solve phase of the GNN-smoothed AMG (Sec. 2.1, 2.2, 2.3, 3.1) on sm_103a.
+//
+// Every sparse operation is a row-group CSR kernel: TPR consecutive lanes
+// (2..32, picked from the matrix's mean row length) share one row, stream
+// its column/value entries with unit stride and combine with shuffles.  All
+// reductions are fixed-order (no floating-point atomics), so results are
+// bit-reproducible run to run.
+//
+// V-cycle (Sec. 2.2) per level l < L-1, in precision T (float or double):
+//   pre-smoothing   nu1 sweeps from u = 0   (the first sweep needs no A pass)
+//   residual        r = b - A u
+//   restriction     b_{l+1} = R r           (explicit R = P^T, gather form)
+//   recursion
+//   prolongation    u += P u_{l+1}
+//   post-smoothing  nu2 sweeps
+// Sweep of the pseudo-inverse smoother (Sec. 3.1): r = b - A u, u += Q^-1 r.
+// Sweep of relaxed Jacobi (Sec. 2.3): u' = u + omega D^-1 (b - A u).
+// Coarsest level: FP64 dense Cholesky factor L (setup), applied as
+// u = L^-T (L^-1 b) with L^-1 formed once at setup.
+// Outer loop (FP64): r = b - A x, ||r|| / ||b||, x += V(r).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctx.cuh"
+
+using namespace amg;
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+static thread_local std::string g_create_err;
+
+namespace amg {
+bool ctx_fail(amg_ctx *c, const std::string &msg) {
+    if (c) c->err = msg;
+    return false;
+}
+int ctx_cuda_check(amg_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return AMG_OK;
+    if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return AMG_ERR_CUDA;
+}
+}  // namespace amg
+
+#define CK(expr)                                                        \
+    do {                                                                \
+        int _rc = ctx_cuda_check(c, (expr), #expr);                     \
+        if (_rc != AMG_OK) return _rc;                                  \
+    } while (0)
+#define CKL(what)                                                       \
+    do {                                                                \
+        int _rc = ctx_cuda_check(c, cudaGetLastError(), what);          \
+        if (_rc != AMG_OK) return _rc;                                  \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// kernels: row-group CSR family
+// ---------------------------------------------------------------------------
+// r = b - A u
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_resid(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                  const T *__restrict__ a, const T *__restrict__ b,
+                                                  const T *__restrict__ u, T *__restrict__ r) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) {
+        const int e = rp[row + 1];
+        for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * u[col[p]];
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) r[row] = b[row] - acc;
+}
+
+// y = M x   (restriction with R, or a plain product)
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                 const T *__restrict__ m, const T *__restrict__ x,
+                                                 T *__restrict__ y) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) {
+        const int e = rp[row + 1];
+        for (int p = rp[row] + lane; p < e; p += TPR) acc += m[p] * x[col[p]];
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) y[row] = acc;
+}
+
+// u = (add ? u : 0) + M r   (pseudo-inverse application, Sec. 3.1;
+// also prolongation-correction u += P e with add = 1)
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_apply(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                  const T *__restrict__ m, const T *__restrict__ r,
+                                                  T *__restrict__ u, int add) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) {
+        const int e = rp[row + 1];
+        for (int p = rp[row] + lane; p < e; p += TPR) acc += m[p] * r[col[p]];
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) u[row] = (add ? u[row] : T(0)) + acc;
+}
+
+// u_out = u_in + (omega/a_ii) (b - A u_in)   (relaxed Jacobi, Sec. 2.3)
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                   const T *__restrict__ a, const T *__restrict__ jac,
+                                                   const T *__restrict__ b, const T *__restrict__ uin,
+                                                   T *__restrict__ uout) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) {
+        const int e = rp[row + 1];
+        for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * uin[col[p]];
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) uout[row] = uin[row] + jac[row] * (b[row] - acc);
+}
+
+// u = (omega/a_ii) b  (first Jacobi sweep from u = 0)
+template <class T>
+__global__ void k_scale(int n, const T *__restrict__ jac, const T *__restrict__ b, T *__restrict__ u) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n) u[i] = jac[i] * b[i];
+}
+
+template <class S, class D>
+__global__ void k_convert(int n, const S *__restrict__ s, D *__restrict__ d) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n) d[i] = static_cast<D>(s[i]);
+}
+
+// x += e  (outer FP64 update)
+template <class T>
+__global__ void k_axpy(int n, double *__restrict__ x, const T *__restrict__ e) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n) x[i] += static_cast<double>(e[i]);
+}
+
+// Coarsest level: u = L^-T (L^-1 b) in FP64 (one block; dynamic smem 2n doubles).
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_coarse(int n, const double *__restrict__ Linv,
+                                                   const double *__restrict__ LinvT, const T *__restrict__ b,
+                                                   T *__restrict__ u) {
+    extern __shared__ double sm[];
+    double *sb = sm, *sy = sm + n;
+    for (int i = threadIdx.x; i < n; i += kBlock) sb[i] = static_cast<double>(b[i]);
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = kBlock / 32;
+    for (int i = warp; i < n; i += nw) {
+        double acc = 0.0;
+        const double *row = Linv + static_cast<size_t>(i) * n;
+        for (int k = lane; k <= i; k += 32) acc += row[k] * sb[k];
+        acc = warp_sum(acc);
+        if (lane == 0) sy[i] = acc;
+    }
+    __syncthreads();
+    for (int i = warp; i < n; i += nw) {
+        double acc = 0.0;
+        const double *row = LinvT + static_cast<size_t>(i) * n;
+        for (int k = i + lane; k < n; k += 32) acc += row[k] * sy[k];
+        acc = warp_sum(acc);
+        if (lane == 0) u[i] = static_cast<T>(acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernels: FP64 outer loop with deterministic norms
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_partial(double v, double *out) {
+    __shared__ double red[kBlock / 32];
+    v = warp_sum(v);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : 0.0;
+        w = warp_sum(w);
+        if (threadIdx.x == 0) out[blockIdx.x] = w;
+    }
+}
+
+// r = b - A x (FP64), rT = (T) r, partial[block] = sum r^2 over the block's rows
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_outer_resid(int n, const int *__restrict__ rp,
+                                                        const int *__restrict__ col, const double *__restrict__ a,
+                                                        const double *__restrict__ b, const double *__restrict__ x,
+                                                        T *__restrict__ rT, double *__restrict__ partial) {
+    constexpr int RPB = kBlock / TPR;
+    const int lane = threadIdx.x % TPR;
+    double sq = 0.0;
+    for (int base = blockIdx.x * RPB; base < n; base += gridDim.x * RPB) {
+        const int row = base + threadIdx.x / TPR;
+        double acc = 0.0;
+        if (row < n) {
+            const int e = rp[row + 1];
+            for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * x[col[p]];
+        }
+        acc = group_sum<TPR>(acc);
+        if (row < n && lane == 0) {
+            const double r = b[row] - acc;
+            rT[row] = static_cast<T>(r);
+            sq += r * r;
+        }
+    }
+    block_partial(sq, partial);
+}
+
+__global__ void __launch_bounds__(kBlock) k_sqnorm_partial(int n, const double *__restrict__ v,
+                                                           double *__restrict__ partial) {
+    double sq = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) sq += v[i] * v[i];
+    block_partial(sq, partial);
+}
+
+__global__ void k_state_init(SolveState *st, double tol, int max_iter) {
+    st->k = 0;
+    st->status = kRunning;
+    st->max_iter = max_iter;
+    st->tol = tol;
+    st->bnorm = 1.0;
+    st->r0 = 0.0;
+}
+
+// Sum the partials in a fixed order.  mode 0: ||b||.  mode 1: residual
+// history entry k and the stopping rule (Sec. 4 tolerance, divergence,
+// stagnation, iteration cap).
+__global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ partial, int np, SolveState *st,
+                                                     double *__restrict__ hist, int mode) {
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < np; i += 1024) v += partial[i];
+    v = warp_sum(v);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    v = warp_sum(red[threadIdx.x]);
+    if (threadIdx.x != 0) return;
+    const double nrm = sqrt(v);
+    if (mode == 0) {
+        st->bnorm = nrm > 0.0 ? nrm : 1.0;
+        return;
+    }
+    const int k = st->k;
+    const double rel = nrm / st->bnorm;
+    hist[k] = rel;
+    int status = kRunning;
+    if (k == 0) {
+        st->r0 = nrm;
+        if (!isfinite(nrm)) status = AMG_ERR_DIVERGED;
+        else if (rel <= st->tol) status = AMG_OK;
+        else if (st->max_iter <= 0) status = AMG_ERR_MAXITER;
+    } else {
+        if (!isfinite(nrm) || nrm > 1e3 * st->r0) status = AMG_ERR_DIVERGED;
+        else if (rel <= st->tol) status = AMG_OK;
+        else if (k >= 10 && rel > 0.99 * hist[k - 10]) status = AMG_ERR_STAGNATED;
+        else if (k >= st->max_iter) status = AMG_ERR_MAXITER;
+    }
+    st->status = status;
+    st->k = k + 1;
+}
+
+// ---------------------------------------------------------------------------
+// kernels: setup (s_l, smoother values, coarsest factorisation)
+// ---------------------------------------------------------------------------
+__global__ void k_extract_diag(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                               const double *__restrict__ a, double *__restrict__ d) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    double v = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (col[p] == i) v += a[p];
+    d[i] = v;
+}
+
+// s = max_{i != j} |a_ij| (Sec. 3.1): per-block maxima, then one block.
+__global__ void __launch_bounds__(kBlock) k_offdiag_absmax(int n, const int *__restrict__ rp,
+                                                           const int *__restrict__ col,
+                                                           const double *__restrict__ a,
+                                                           double *__restrict__ partial) {
+    __shared__ double red[kBlock / 32];
+    double m = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+        for (int p = rp[i]; p < rp[i + 1]; ++p)
+            if (col[p] != i) m = fmax(m, fabs(a[p]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double w = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) w = fmax(w, red[k]);
+        partial[blockIdx.x] = w;
+    }
+}
+
+__global__ void k_max_final(const double *__restrict__ partial, int np, double *__restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double m = 0.0;
+    for (int i = 0; i < np; ++i) m = fmax(m, partial[i]);
+    *out = m > 0.0 ? m : 1.0;
+}
+
+// Q^-1 values on A's pattern from c = (d0, d1, d2, o1, o2) (Sec. 3.1), in
+// FP64 with the polynomial evaluated as d0 + d1 x + (d2 x) x, uncontracted.
+__global__ void k_assemble_q(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ a, const double *__restrict__ d,
+                             const double *__restrict__ s_ptr, double c0, double c1, double c2, double c3,
+                             double c4, double *__restrict__ q64, float *__restrict__ q32) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const double s = *s_ptr;
+    const double di = d[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = col[p];
+        const double x = __ddiv_rn(a[p], s);
+        double q;
+        if (j == i) {
+            double f = __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x));
+            q = __ddiv_rn(f, di);
+        } else {
+            double f = __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
+            q = __ddiv_rn(f, __dadd_rn(di, d[j]));
+        }
+        q64[p] = q;
+        q32[p] = static_cast<float>(q);
+    }
+}
+
+__global__ void k_jacobi_vals(int n, const double *__restrict__ d, double omega, double *__restrict__ j64,
+                              float *__restrict__ j32) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    double v = __ddiv_rn(omega, d[i]);
+    j64[i] = v;
+    j32[i] = static_cast<float>(v);
+}
+
+__global__ void k_csr_to_dense(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                               const double *__restrict__ a, double *__restrict__ dense) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) dense[static_cast<size_t>(i) * n + col[p]] += a[p];
+}
+
+// Right-looking dense Cholesky in place (lower triangle), one block.
+__global__ void __launch_bounds__(1024) k_cholesky(int n, double *__restrict__ a, int *__restrict__ flag) {
+    __shared__ double piv;
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double d = a[static_cast<size_t>(j) * n + j];
+            if (!(d > 0.0)) {
+                *flag = 1;
+                d = 1.0;
+            }
+            piv = sqrt(d);
+            a[static_cast<size_t>(j) * n + j] = piv;
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) a[static_cast<size_t>(i) * n + j] /= piv;
+        __syncthreads();
+        const int m = n - j - 1;
+        for (long long idx = threadIdx.x; idx < static_cast<long long>(m) * m; idx += blockDim.x) {
+            const int i = j + 1 + static_cast<int>(idx / m);
+            const int k = j + 1 + static_cast<int>(idx % m);
+            if (k <= i)
+                a[static_cast<size_t>(i) * n + k] -=
+                    a[static_cast<size_t>(i) * n + j] * a[static_cast<size_t>(k) * n + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Column j of L^-1 by forward substitution (one thread per column).
+__global__ void k_tri_inverse(int n, const double *__restrict__ L, double *__restrict__ Linv,
+                              double *__restrict__ LinvT) {
+    const int j = blockIdx.x * kBlock + threadIdx.x;
+    if (j >= n) return;
+    Linv[static_cast<size_t>(j) * n + j] = 1.0 / L[static_cast<size_t>(j) * n + j];
+    LinvT[static_cast<size_t>(j) * n + j] = Linv[static_cast<size_t>(j) * n + j];
+    for (int i = j + 1; i < n; ++i) {
+        double s = 0.0;
+        for (int k = j; k < i; ++k) s += L[static_cast<size_t>(i) * n + k] * Linv[static_cast<size_t>(k) * n + j];
+        const double v = -s / L[static_cast<size_t>(i) * n + i];
+        Linv[static_cast<size_t>(i) * n + j] = v;
+        LinvT[static_cast<size_t>(j) * n + i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers (dispatch on threads-per-row)
+// ---------------------------------------------------------------------------
+template <class T> static const T *mvals(const DevMat &m);
+template <> const double *mvals<double>(const DevMat &m) { return m.v64; }
+template <> const float *mvals<float>(const DevMat &m) { return m.v32; }
+template <class T> static const T *qvals(const DevLevel &L);
+template <> const double *qvals<double>(const DevLevel &L) { return L.q64; }
+template <> const float *qvals<float>(const DevLevel &L) { return L.q32; }
+template <class T> static const T *jvals(const DevLevel &L);
+template <> const double *jvals<double>(const DevLevel &L) { return L.j64; }
+template <> const float *jvals<float>(const DevLevel &L) { return L.j32; }
+
+#define TPR_DISPATCH(tpr, KERNEL, ...)                    \
+    switch (tpr) {                                        \
+        case 2: KERNEL<2>(__VA_ARGS__); break;            \
+        case 4: KERNEL<4>(__VA_ARGS__); break;            \
+        case 8: KERNEL<8>(__VA_ARGS__); break;            \
+        case 16: KERNEL<16>(__VA_ARGS__); break;          \
+        default: KERNEL<32>(__VA_ARGS__); break;          \
+    }
+
+template <class T> struct Launch {
+    template <int TPR>
+    static void resid(const DevMat &A, const T *b, const T *u, T *r, cudaStream_t s) {
+        k_resid<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(A.nr, A.rp, A.col,
+                                                                                         mvals<T>(A), b, u, r);
+    }
+    template <int TPR>
+    static void spmv(const DevMat &M, const T *x, T *y, cudaStream_t s) {
+        k_spmv<T, TPR><<<grid_for(static_cast<long long>(M.nr) * TPR), kBlock, 0, s>>>(M.nr, M.rp, M.col,
+                                                                                        mvals<T>(M), x, y);
+    }
+    template <int TPR>
+    static void apply(const DevMat &M, const T *m, const T *r, T *u, int add, cudaStream_t s) {
+        k_apply<T, TPR><<<grid_for(static_cast<long long>(M.nr) * TPR), kBlock, 0, s>>>(M.nr, M.rp, M.col, m,
+                                                                                         r, u, add);
+    }
+    template <int TPR>
+    static void jacobi(const DevMat &A, const T *jac, const T *b, const T *uin, T *uout, cudaStream_t s) {
+        k_jacobi<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(
+            A.nr, A.rp, A.col, mvals<T>(A), jac, b, uin, uout);
+    }
+    template <int TPR>
+    static void outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nblk,
+                      cudaStream_t s) {
+        k_outer_resid<T, TPR><<<nblk, kBlock, 0, s>>>(A.nr, A.rp, A.col, A.v64, b, x, rT, partial);
+    }
+};
+
+template <class T> static void L_resid(const DevMat &A, const T *b, const T *u, T *r, cudaStream_t s) {
+    TPR_DISPATCH(A.tpr, Launch<T>::template resid, A, b, u, r, s);
+}
+template <class T> static void L_spmv(const DevMat &M, const T *x, T *y, cudaStream_t s) {
+    TPR_DISPATCH(M.tpr, Launch<T>::template spmv, M, x, y, s);
+}
+template <class T> static void L_apply(const DevMat &M, const T *m, const T *r, T *u, int add, cudaStream_t s) {
+    TPR_DISPATCH(M.tpr, Launch<T>::template apply, M, m, r, u, add, s);
+}
+template <class T>
+static void L_jacobi(const DevMat &A, const T *jac, const T *b, const T *uin, T *uout, cudaStream_t s) {
+    TPR_DISPATCH(A.tpr, Launch<T>::template jacobi, A, jac, b, uin, uout, s);
+}
+
+static int outer_blocks(const DevMat &A) {
+    long long need = (static_cast<long long>(A.nr) * A.tpr + kBlock - 1) / kBlock;
+    long long cap = static_cast<long long>(kNumSMs) * 8;
+    return static_cast<int>(std::max(1LL, std::min(need, cap)));
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle driver
+// ---------------------------------------------------------------------------
+// Smoothing sweeps on level l; returns the buffer holding the result (Jacobi
+// alternates between cur and alt).
+template <class T>
+static T *smooth(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *alt, T *r, int nsweeps,
+                 bool zero_init) {
+    const DevLevel &L = c->lev[l];
+    const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
+    if (nsweeps == 0 && zero_init) cudaMemsetAsync(cur, 0, sizeof(T) * L.n, s);
+    for (int k = 0; k < nsweeps; ++k) {
+        const bool first = (k == 0 && zero_init);
+        if (gnn) {
+            if (first) {
+                L_apply<T>(L.A, qvals<T>(L), b, cur, 0, s);
+            } else {
+                L_resid<T>(L.A, b, cur, r, s);
+                L_apply<T>(L.A, qvals<T>(L), r, cur, 1, s);
+            }
+        } else {
+            if (first) {
+                k_scale<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, jvals<T>(L), b, cur);
+            } else {
+                L_jacobi<T>(L.A, jvals<T>(L), b, cur, alt, s);
+                std::swap(cur, alt);
+            }
+        }
+    }
+    return cur;
+}
+
+// One V-cycle on level l with right-hand side lev[l].vb; returns the result buffer.
+template <class T>
+static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
+    DevLevel &L = c->lev[l];
+    T *b = reinterpret_cast<T *>(L.vb);
+    T *u = reinterpret_cast<T *>(L.vu);
+    T *r = reinterpret_cast<T *>(L.vr);
+    T *t = reinterpret_cast<T *>(L.vt);
+    const int nlev = static_cast<int>(c->lev.size());
+    if (l == nlev - 1) {
+        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u);
+        return u;
+    }
+    T *cur = smooth<T>(c, l, s, b, u, t, r, c->opt.nu1, true);
+    T *alt = (cur == u) ? t : u;
+    L_resid<T>(L.A, b, cur, r, s);
+    L_spmv<T>(L.R, r, reinterpret_cast<T *>(c->lev[l + 1].vb), s);
+    T *ec = vcycle_level<T>(c, l + 1, s);
+    L_apply<T>(L.P, mvals<T>(L.P), ec, cur, 1, s);
+    return smooth<T>(c, l, s, b, cur, alt, r, c->opt.nu2, false);
+}
+
+template <class T>
+static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s) {
+    const DevMat &A = c->lev[0].A;
+    const int nb = outer_blocks(A);
+    TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb),
+                 c->partials, nb, s);
+    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 1);
+}
+
+template <class T>
+static void enqueue_init(amg_ctx *c, cudaStream_t s, double tol, int max_iter) {
+    const int n0 = c->lev[0].n;
+    const int nb = std::min(grid_for(n0), kNumSMs * 8);
+    k_state_init<<<1, 1, 0, s>>>(c->state, tol, max_iter);
+    k_sqnorm_partial<<<nb, kBlock, 0, s>>>(n0, c->db, c->partials);
+    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 0);
+    enqueue_outer_residual<T>(c, s);
+}
+
+template <class T>
+static void enqueue_iteration(amg_ctx *c, cudaStream_t s) {
+    T *e = vcycle_level<T>(c, 0, s);
+    k_axpy<T><<<grid_for(c->lev[0].n), kBlock, 0, s>>>(c->lev[0].n, c->dx, e);
+    enqueue_outer_residual<T>(c, s);
+}
+
+// Solve on the staging buffers c->db / c->dx.
+template <class T>
+static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, double *hist) {
+    const int max_iter = c->opt.max_iter;
+    enqueue_init<T>(c, s, tol, max_iter);
+    CKL("solve init launch");
+    CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    while (c->h_state->status == kRunning) {
+        enqueue_iteration<T>(c, s);
+        CKL("V-cycle launch");
+        CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    const int nh = c->h_state->k;
+    if (n_vc) *n_vc = nh - 1;
+    if (hist) CK(cudaMemcpyAsync(hist, c->hist, sizeof(double) * nh, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return c->h_state->status;
+}
+
+// ---------------------------------------------------------------------------
+// hierarchy upload
+// ---------------------------------------------------------------------------
+static const int kMaxCoarseDense = 4096;
+
+static void free_device(amg_ctx *c) {
+    if (c->arena) cudaFree(c->arena);
+    c->arena = nullptr;
+    c->arena_bytes = 0;
+    c->lev.clear();
+    c->nL = 0;
+    c->have_q = false;
+}
+
+static void layout_mat(Planner &pl, DevMat &m, const HostCSR &h) {
+    m.nr = h.n_rows;
+    m.nc = h.n_cols;
+    m.nnz = static_cast<int>(h.nnz());
+    m.tpr = pick_tpr(h.nnz(), h.n_rows);
+    m.rp = pl.take<int>(h.n_rows + 1);
+    m.col = pl.take<int>(std::max<long long>(1, h.nnz()));
+    m.v64 = pl.take<double>(std::max<long long>(1, h.nnz()));
+    m.v32 = pl.take<float>(std::max<long long>(1, h.nnz()));
+}
+
+static void layout(amg_ctx *c, Planner &pl) {
+    const int nlev = static_cast<int>(c->host.size());
+    c->lev.assign(nlev, DevLevel{});
+    for (int l = 0; l < nlev; ++l) {
+        DevLevel &L = c->lev[l];
+        const HostLevel &H = c->host[l];
+        L.n = H.A.n_rows;
+        layout_mat(pl, L.A, H.A);
+        if (l < nlev - 1) {
+            layout_mat(pl, L.P, H.P);
+            layout_mat(pl, L.R, H.R);
+        }
+        L.diag = pl.take<double>(L.n);
+        L.q64 = pl.take<double>(std::max(1, L.A.nnz));
+        L.q32 = pl.take<float>(std::max(1, L.A.nnz));
+        L.j64 = pl.take<double>(L.n);
+        L.j32 = pl.take<float>(L.n);
+        L.vb = pl.take<double>(L.n);
+        L.vu = pl.take<double>(L.n);
+        L.vr = pl.take<double>(L.n);
+        L.vt = pl.take<double>(L.n);
+    }
+    const int nL = c->host.back().A.n_rows;
+    c->nL = nL;
+    c->Ldense = pl.take<double>(static_cast<size_t>(nL) * nL);
+    c->Linv = pl.take<double>(static_cast<size_t>(nL) * nL);
+    c->LinvT = pl.take<double>(static_cast<size_t>(nL) * nL);
+    const int n0 = c->host[0].A.n_rows;
+    c->db = pl.take<double>(n0);
+    c->dx = pl.take<double>(n0);
+    c->n_partials = kNumSMs * 8;
+    c->partials = pl.take<double>(c->n_partials);
+    c->scal = pl.take<double>(nlev);
+    c->state = pl.take<SolveState>(1);
+    c->hist = pl.take<double>(c->opt.max_iter + 1);
+    c->dflag = pl.take<int>(4);
+}
+
+static int upload_mat(amg_ctx *c, const DevMat &m, const HostCSR &h, cudaStream_t s) {
+    CK(cudaMemcpyAsync(m.rp, h.rp.data(), sizeof(int) * (h.n_rows + 1), cudaMemcpyHostToDevice, s));
+    if (h.nnz() > 0) {
+        CK(cudaMemcpyAsync(m.col, h.col.data(), sizeof(int) * h.nnz(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.v64, h.val.data(), sizeof(double) * h.nnz(), cudaMemcpyHostToDevice, s));
+        k_convert<double, float><<<grid_for(h.nnz()), kBlock, 0, s>>>(m.nnz, m.v64, m.v32);
+    }
+    return AMG_OK;
+}
+
+static int upload(amg_ctx *c) {
+    free_device(c);
+    ++c->hier_version;
+    Planner pl;
+    layout(c, pl);
+    c->arena_bytes = pl.off;
+    CK(cudaMalloc(&c->arena, c->arena_bytes));
+    pl = Planner{};
+    pl.base = c->arena;
+    layout(c, pl);
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->arena, 0, c->arena_bytes, s));
+    const int nlev = static_cast<int>(c->host.size());
+    c->scales.assign(nlev, 1.0);
+    for (int l = 0; l < nlev; ++l) {
+        DevLevel &L = c->lev[l];
+        const HostLevel &H = c->host[l];
+        int rc = upload_mat(c, L.A, H.A, s);
+        if (rc) return rc;
+        if (l < nlev - 1) {
+            if ((rc = upload_mat(c, L.P, H.P, s))) return rc;
+            if ((rc = upload_mat(c, L.R, H.R, s))) return rc;
+        }
+        k_extract_diag<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag);
+        const int nb = std::min(grid_for(L.n), kNumSMs * 8);
+        k_offdiag_absmax<<<nb, kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, c->partials);
+        k_max_final<<<1, 32, 0, s>>>(c->partials, nb, c->scal + l);
+        k_jacobi_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, c->opt.omega, L.j64, L.j32);
+    }
+    c->jac_omega = c->opt.omega;
+    // coarsest level: dense FP64 Cholesky and the inverse factor
+    const DevLevel &Lc = c->lev.back();
+    const int nL = c->nL;
+    k_csr_to_dense<<<grid_for(nL), kBlock, 0, s>>>(nL, Lc.A.rp, Lc.A.col, Lc.A.v64, c->Ldense);
+    k_cholesky<<<1, 1024, 0, s>>>(nL, c->Ldense, c->dflag);
+    CK(cudaFuncSetAttribute(k_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8 * kMaxCoarseDense));
+    CK(cudaFuncSetAttribute(k_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8 * kMaxCoarseDense));
+    k_tri_inverse<<<grid_for(nL), kBlock, 0, s>>>(nL, c->Ldense, c->Linv, c->LinvT);
+    CKL("hierarchy setup kernels");
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->scales.data(), c->scal, sizeof(double) * nlev, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (flag) {
+        c->err = "coarsest-level matrix is not positive definite";
+        free_device(c);
+        return AMG_ERR_NOT_SPD;
+    }
+    c->smoother = AMG_SMOOTHER_JACOBI;
+    return AMG_OK;
+}
+
+static bool to_host(const amg_csr *m, HostCSR &h, std::string &why) {
+    if (!m || !m->row_ptr || (m->nnz > 0 && (!m->col || !m->val)) || m->n_rows < 0 || m->n_cols < 0 ||
+        m->nnz < 0 || m->nnz > 2000000000LL) {
+        why = "null or invalid CSR";
+        return false;
+    }
+    h.n_rows = m->n_rows;
+    h.n_cols = m->n_cols;
+    h.rp.assign(m->row_ptr, m->row_ptr + m->n_rows + 1);
+    if (h.rp.back() != m->nnz) {
+        why = "row_ptr[n] != nnz";
+        return false;
+    }
+    h.col.assign(m->col, m->col + m->nnz);
+    h.val.assign(m->val, m->val + m->nnz);
+    return true;
+}
+
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void amg_default_options(amg_options *o) {
+    if (!o) return;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->max_levels = 10;
+    o->max_coarse = 64;
+    o->max_iter = 500;
+    o->precision = AMG_FP32_IN_FP64;
+    o->smoother = AMG_SMOOTHER_JACOBI;
+    o->omega = 2.0 / 3.0;
+    o->theta = 0.25;
+    o->device = 0;
+}
+
+int amg_create(amg_ctx **ctx, const amg_options *opt) {
+    if (!ctx) {
+        g_create_err = "ctx is NULL";
+        return AMG_ERR_ARG;
+    }
+    *ctx = nullptr;
+    amg_options o;
+    amg_default_options(&o);
+    if (opt) o = *opt;
+    if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 64 || o.nu2 > 64 || o.max_levels < 1 || o.max_levels > 32 ||
+        o.max_coarse < 1 || o.max_iter < 0 || o.max_iter > 100000 ||
+        (o.precision != AMG_FP64 && o.precision != AMG_FP32_IN_FP64) ||
+        (o.smoother != AMG_SMOOTHER_JACOBI && o.smoother != AMG_SMOOTHER_GNN) || !(o.theta >= 0.0) ||
+        !(o.theta <= 1.0) || !std::isfinite(o.omega)) {
+        g_create_err = "invalid amg_options";
+        return AMG_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) {
+        g_create_err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        return AMG_ERR_CUDA;
+    }
+    amg_ctx *c = new (std::nothrow) amg_ctx();
+    if (!c) {
+        g_create_err = "out of host memory";
+        return AMG_ERR_ARG;
+    }
+    c->opt = o;
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_state, sizeof(SolveState));
+    if (e != cudaSuccess) {
+        g_create_err = std::string("stream/pinned allocation: ") + cudaGetErrorString(e);
+        if (c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return AMG_ERR_CUDA;
+    }
+    g_create_err.clear();
+    *ctx = c;
+    return AMG_OK;
+}
+
+void amg_destroy(amg_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->opt.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gnn) gcin_engine_free(c->gnn);
+    free_device(c);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *amg_last_error(const amg_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int amg_load_hierarchy(amg_ctx *c, int n_levels, const amg_csr *A, const amg_csr *P, const amg_csr *R) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (n_levels < 1 || !A || (n_levels > 1 && !P)) return ctx_fail(c, "bad n_levels or NULL arrays"), AMG_ERR_ARG;
+    std::vector<HostLevel> h(n_levels);
+    std::string why;
+    for (int l = 0; l < n_levels; ++l) {
+        if (!to_host(&A[l], h[l].A, why) || !validate_csr(h[l].A, true, why))
+            return ctx_fail(c, "A[" + std::to_string(l) + "]: " + why), AMG_ERR_ARG;
+        if (l < n_levels - 1) {
+            if (!to_host(&P[l], h[l].P, why) || !validate_csr(h[l].P, false, why))
+                return ctx_fail(c, "P[" + std::to_string(l) + "]: " + why), AMG_ERR_ARG;
+            if (R) {
+                if (!to_host(&R[l], h[l].R, why) || !validate_csr(h[l].R, false, why))
+                    return ctx_fail(c, "R[" + std::to_string(l) + "]: " + why), AMG_ERR_ARG;
+            } else {
+                h[l].R = transpose(h[l].P);
+            }
+        }
+    }
+    for (int l = 0; l + 1 < n_levels; ++l) {
+        const int n = h[l].A.n_rows, nc = h[l + 1].A.n_rows;
+        if (h[l].P.n_rows != n || h[l].P.n_cols != nc || h[l].R.n_rows != nc || h[l].R.n_cols != n)
+            return ctx_fail(c, "P/R dimensions disagree with A at level " + std::to_string(l)), AMG_ERR_ARG;
+    }
+    if (h.back().A.n_rows > kMaxCoarseDense)
+        return ctx_fail(c, "coarsest level larger than 4096 rows: dense Cholesky refused"), AMG_ERR_ARG;
+    if (h[0].A.n_rows < 1) return ctx_fail(c, "empty matrix"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    c->host = std::move(h);
+    return upload(c);
+}
+
+int amg_setup(amg_ctx *c, const amg_csr *A) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    HostCSR h;
+    std::string why;
+    if (!to_host(A, h, why) || !validate_csr(h, true, why)) return ctx_fail(c, "A: " + why), AMG_ERR_ARG;
+    if (h.n_rows < 1) return ctx_fail(c, "empty matrix"), AMG_ERR_ARG;
+    std::vector<HostLevel> levels;
+    build_hierarchy(h, c->opt.theta, c->opt.max_levels, c->opt.max_coarse, levels);
+    if (levels.back().A.n_rows > kMaxCoarseDense)
+        return ctx_fail(c, "coarsening stalled above 4096 rows: dense Cholesky refused"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    c->host = std::move(levels);
+    return upload(c);
+}
+
+int amg_num_levels(const amg_ctx *c) { return c ? static_cast<int>(c->lev.size()) : 0; }
+
+int amg_level_info(const amg_ctx *c, int level, int *n, long long *nnz_A, long long *nnz_P) {
+    if (!c || level < 0 || level >= static_cast<int>(c->host.size())) return AMG_ERR_ARG;
+    const HostLevel &H = c->host[level];
+    if (n) *n = H.A.n_rows;
+    if (nnz_A) *nnz_A = H.A.nnz();
+    if (nnz_P) *nnz_P = (level + 1 < static_cast<int>(c->host.size())) ? H.P.nnz() : 0;
+    return AMG_OK;
+}
+
+int amg_get_level(const amg_ctx *c, int level, int *A_rp, int *A_col, double *A_val, int *P_rp, int *P_col,
+                  double *P_val) {
+    if (!c || level < 0 || level >= static_cast<int>(c->host.size())) return AMG_ERR_ARG;
+    const HostLevel &H = c->host[level];
+    if (!A_rp || !A_col || !A_val) return AMG_ERR_ARG;
+    std::copy(H.A.rp.begin(), H.A.rp.end(), A_rp);
+    std::copy(H.A.col.begin(), H.A.col.end(), A_col);
+    std::copy(H.A.val.begin(), H.A.val.end(), A_val);
+    if (level + 1 < static_cast<int>(c->host.size()) && P_rp && P_col && P_val) {
+        std::copy(H.P.rp.begin(), H.P.rp.end(), P_rp);
+        std::copy(H.P.col.begin(), H.P.col.end(), P_col);
+        std::copy(H.P.val.begin(), H.P.val.end(), P_val);
+    }
+    return AMG_OK;
+}
+
+int amg_get_scales(const amg_ctx *c, double *s_out) {
+    if (!c || !s_out) return AMG_ERR_ARG;
+    if (c->lev.empty()) return AMG_ERR_STATE;
+    std::copy(c->scales.begin(), c->scales.end(), s_out);
+    return AMG_OK;
+}
+
+int amg_set_jacobi(amg_ctx *c, double omega) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (!std::isfinite(omega)) return ctx_fail(c, "omega not finite"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    if (omega != c->jac_omega) {
+        for (auto &L : c->lev)
+            k_jacobi_vals<<<grid_for(L.n), kBlock, 0, c->stream>>>(L.n, L.diag, omega, L.j64, L.j32);
+        CKL("jacobi values");
+        CK(cudaStreamSynchronize(c->stream));
+        c->jac_omega = omega;
+    }
+    c->smoother = AMG_SMOOTHER_JACOBI;
+    return AMG_OK;
+}
+}  // extern "C"
+
+namespace amg {
+int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s) {
+    const int nlev = static_cast<int>(c->lev.size());
+    for (int l = 0; l < nlev - 1; ++l) {
+        const DevLevel &L = c->lev[l];
+        const double *q = coef + 5 * l;
+        for (int k = 0; k < 5; ++k)
+            if (!std::isfinite(q[k])) return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
+        k_assemble_q<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag, c->scal + l, q[0],
+                                                      q[1], q[2], q[3], q[4], L.q64, L.q32);
+    }
+    (void)n_rows;
+    CKL("assemble pseudo-inverse");
+    c->have_q = true;
+    c->smoother = AMG_SMOOTHER_GNN;
+    return AMG_OK;
+}
+}  // namespace amg
+
+extern "C" {
+
+int amg_set_coeffs(amg_ctx *c, const double *coef, int n_rows) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (!coef || n_rows < static_cast<int>(c->lev.size()) - 1)
+        return ctx_fail(c, "need one coefficient row per smoothed level"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    int rc = set_coeffs_device(c, coef, n_rows, c->stream);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return AMG_OK;
+}
+
+int amg_get_smoother(const amg_ctx *cc, int level, double *q_out) {
+    amg_ctx *c = const_cast<amg_ctx *>(cc);
+    if (!c || !q_out || level < 0 || level >= static_cast<int>(c->lev.size()) - 1) return AMG_ERR_ARG;
+    const DevLevel &L = c->lev[level];
+    CK(cudaSetDevice(c->opt.device));
+    if (c->smoother == AMG_SMOOTHER_GNN) {
+        CK(cudaMemcpyAsync(q_out, L.q64, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<double> j(L.n);
+        CK(cudaMemcpyAsync(j.data(), L.j64, sizeof(double) * L.n, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const HostCSR &A = c->host[level].A;
+        for (int i = 0; i < A.n_rows; ++i)
+            for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) q_out[p] = (A.col[p] == i) ? j[i] : 0.0;
+    }
+    return AMG_OK;
+}
+
+static int solve_dispatch(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, double *hist) {
+    if (c->opt.precision == AMG_FP64) return solve_staged<double>(c, s, tol, n_vc, hist);
+    return solve_staged<float>(c, s, tol, n_vc, hist);
+}
+
+static int check_ready(amg_ctx *c) {
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (c->smoother == AMG_SMOOTHER_GNN && !c->have_q)
+        return ctx_fail(c, "pseudo-inverse smoother selected without coefficients"), AMG_ERR_STATE;
+    return AMG_OK;
+}
+
+int amg_solve(amg_ctx *c, const double *b, double *x, double rtol, int *n_vc, double *hist) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (!b || !x || !(rtol >= 0.0)) return ctx_fail(c, "NULL vector or negative tolerance"), AMG_ERR_ARG;
+    int rc = check_ready(c);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->opt.device));
+    const int n0 = c->lev[0].n;
+    cudaStream_t s = c->stream;
+    CK(cudaMemcpyAsync(c->db, b, sizeof(double) * n0, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->dx, x, sizeof(double) * n0, cudaMemcpyHostToDevice, s));
+    rc = solve_dispatch(c, s, rtol, n_vc, hist);
+    if (rc == AMG_ERR_CUDA) return rc;
+    CK(cudaMemcpyAsync(x, c->dx, sizeof(double) * n0, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (rc != AMG_OK) c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
+    return rc;
+}
+
+int amg_solve_device(amg_ctx *c, const double *d_b, double *d_x, double rtol, void *stream, int *n_vc,
+                     double *hist) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (!d_b || !d_x || !(rtol >= 0.0)) return ctx_fail(c, "NULL vector or negative tolerance"), AMG_ERR_ARG;
+    int rc = check_ready(c);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->opt.device));
+    const int n0 = c->lev[0].n;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(c->db, d_b, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->dx, d_x, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
+    rc = solve_dispatch(c, s, rtol, n_vc, hist);
+    if (rc == AMG_ERR_CUDA) return rc;
+    CK(cudaMemcpyAsync(d_x, c->dx, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (rc != AMG_OK) c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
+    return rc;
+}
+
+int amg_vcycle_device(amg_ctx *c, const double *d_r, double *d_e, void *stream) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (!d_r || !d_e) return ctx_fail(c, "NULL vector"), AMG_ERR_ARG;
+    int rc = check_ready(c);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->opt.device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n0 = c->lev[0].n;
+    if (c->opt.precision == AMG_FP64) {
+        CK(cudaMemcpyAsync(c->lev[0].vb, d_r, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
+        double *e = vcycle_level<double>(c, 0, s);
+        CK(cudaMemcpyAsync(d_e, e, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_convert<double, float><<<grid_for(n0), kBlock, 0, s>>>(n0, d_r, reinterpret_cast<float *>(c->lev[0].vb));
+        float *e = vcycle_level<float>(c, 0, s);
+        k_convert<float, double><<<grid_for(n0), kBlock, 0, s>>>(n0, e, d_e);
+    }
+    CKL("vcycle");
+    return AMG_OK;
+}
+
+}  // extern "C"
+
+template <class T>
+static void smooth_level_device(amg_ctx *c, int l, const double *d_b, double *d_u, int nsw, cudaStream_t s) {
+    DevLevel &L = c->lev[l];
+    const int n = L.n;
+    T *b = reinterpret_cast<T *>(L.vb), *u = reinterpret_cast<T *>(L.vu);
+    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_b, b);
+    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_u, u);
+    T *res = smooth<T>(c, l, s, b, u, reinterpret_cast<T *>(L.vt), reinterpret_cast<T *>(L.vr), nsw, false);
+    k_convert<T, double><<<grid_for(n), kBlock, 0, s>>>(n, res, d_u);
+}
+
+extern "C" {
+
+int amg_smooth_device(amg_ctx *c, int level, const double *d_b, double *d_u, int n_sweeps, void *stream) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!d_b || !d_u || n_sweeps < 0 || level < 0 || level >= static_cast<int>(c->lev.size()) - 1)
+        return ctx_fail(c, "bad level, sweep count or vector"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->opt.precision == AMG_FP64) smooth_level_device<double>(c, level, d_b, d_u, n_sweeps, s);
+    else smooth_level_device<float>(c, level, d_b, d_u, n_sweeps, s);
+    CKL("smooth");
+    return AMG_OK;
+}
+
+int amg_spmv_device(amg_ctx *c, int level, const double *d_x, double *d_y, void *stream) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (!d_x || !d_y || level < 0 || level >= static_cast<int>(c->lev.size()))
+        return ctx_fail(c, "bad level or vector"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevLevel &L = c->lev[level];
+    const int n = L.n;
+    if (c->opt.precision == AMG_FP64) {
+        L_spmv<double>(L.A, d_x, d_y, s);
+    } else {
+        float *x = reinterpret_cast<float *>(L.vu), *y = reinterpret_cast<float *>(L.vr);
+        k_convert<double, float><<<grid_for(n), kBlock, 0, s>>>(n, d_x, x);
+        L_spmv<float>(L.A, x, y, s);
+        k_convert<float, double><<<grid_for(n), kBlock, 0, s>>>(n, y, d_y);
+    }
+    CKL("spmv");
+    return AMG_OK;
+}
+
+int amg_judge(amg_ctx *c, const double *b, double *metric) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (!b || !metric) return ctx_fail(c, "NULL argument"), AMG_ERR_ARG;
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (!c->have_q) return ctx_fail(c, "no pseudo-inverse coefficients set"), AMG_ERR_STATE;
+    CK(cudaSetDevice(c->opt.device));
+    const int n0 = c->lev[0].n;
+    cudaStream_t s = c->stream;
+    const int saved_iter = c->opt.max_iter;
+    const int saved_sm = c->smoother;
+    double h_gnn[2] = {0, 0}, h_jac[2] = {0, 0};
+    int rc = AMG_OK;
+    c->opt.max_iter = 1;
+    for (int pass = 0; pass < 2 && rc != AMG_ERR_CUDA; ++pass) {
+        c->smoother = pass == 0 ? AMG_SMOOTHER_GNN : AMG_SMOOTHER_JACOBI;
+        CK(cudaMemcpyAsync(c->db, b, sizeof(double) * n0, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(c->dx, 0, sizeof(double) * n0, s));
+        rc = solve_dispatch(c, s, 0.0, nullptr, pass == 0 ? h_gnn : h_jac);
+    }
+    c->opt.max_iter = saved_iter;
+    c->smoother = saved_sm;
+    if (rc == AMG_ERR_CUDA) return rc;
+    *metric = std::log10(h_gnn[1] / h_jac[1]);
+    return AMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,42 @@
+// Host-side AMG setup (Sec. 2.2): Ruge-Stueben coarsening, direct
+// interpolation, Galerkin coarse operators.  Runs once per matrix, off the
+// solve path; its output is uploaded by the device code.
+#pragma once
+#include <string>
+#include <vector>
+
+namespace amg {
+
+struct HostCSR {
+    int n_rows = 0, n_cols = 0;
+    std::vector<int> rp, col;
+    std::vector<double> val;
+    long long nnz() const { return static_cast<long long>(col.size()); }
+};
+
+struct HostLevel {
+    HostCSR A;   // n_l x n_l
+    HostCSR P;   // n_l x n_{l+1}   (empty on the coarsest level)
+    HostCSR R;   // n_{l+1} x n_l, R = P^T
+};
+
+// Checks CSR structure; square/diag requirements only when asked.
+bool validate_csr(const HostCSR& M, bool square_with_diag, std::string& why);
+
+HostCSR transpose(const HostCSR& M);
+
+// Classical RS first pass with strength threshold theta; split[i] = 1 for C.
+void rs_split(const HostCSR& A, double theta, std::vector<int>& split,
+              std::vector<int>& S_rp, std::vector<int>& S_col);
+
+HostCSR direct_interpolation(const HostCSR& A, const std::vector<int>& S_rp,
+                             const std::vector<int>& S_col, const std::vector<int>& split);
+
+// A_c = P^T A P on the structural pattern of the product.
+HostCSR galerkin(const HostCSR& A, const HostCSR& P, const HostCSR& R);
+
+// Setup-AMG-Hierarchy of Algorithm 1 (finest level first).
+void build_hierarchy(const HostCSR& A0, double theta, int max_levels, int max_coarse,
+                     std::vector<HostLevel>& levels);
+
+}  // namespace amg

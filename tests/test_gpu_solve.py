@@ -1,0 +1,265 @@
+"""GPU parity of the solve path against the FP64 oracle, through the C ABI.
+
+Bars: FP64 path within 1e-12 relative of the oracle (only the summation
+order inside a row differs); FP32 V-cycle inside FP64 refinement reaches the
+same tolerance with the V-cycle count within +-1 of the oracle's; integer
+work (setup splitting and patterns) bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_19251_gb300 as P
+import workloads as W
+from oracle import setup as OS
+from oracle import solve as O
+from tests.gpu_helpers import CASES, ctx_from_oracle, ctx_setup, library_levels, oracle_hier, rel_err
+
+pytestmark = pytest.mark.gpu
+
+COEFFS = [0.62, 0.03, -0.01, -0.18, 0.02]
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for name, make in CASES.items():
+        A = make()
+        out[name] = (A, OS.build_hierarchy(A))
+    return out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_matches_oracle(cases, name):
+    A, levels = cases[name]
+    ctx = ctx_setup(A)
+    try:
+        lib = library_levels(ctx)
+        assert len(lib) == len(levels)
+        for (a, p), lv in zip(lib, levels):
+            assert np.array_equal(a.row_ptr, lv.A.row_ptr) and np.array_equal(a.col, lv.A.col)
+            assert rel_err(a.val, lv.A.val) < 1e-13
+            if lv.P is not None:
+                assert np.array_equal(p.row_ptr, lv.P.row_ptr) and np.array_equal(p.col, lv.P.col)
+                assert rel_err(p.val, lv.P.val) < 1e-14
+        s = P.amg_get_scales(ctx)
+        for l, lv in enumerate(levels):
+            assert abs(s[l] - O.smoother_scale(O.TMat.of(lv.A))) <= 1e-13 * s[l]
+    finally:
+        P.amg_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,tol", [(P.AMG_FP64, 1e-14), (P.AMG_FP32_IN_FP64, 2e-6)])
+@pytest.mark.parametrize("name", ["c1_64", "band_4k"])
+def test_spmv_parity(cases, name, prec, tol):
+    A, levels = cases[name]
+    ctx = ctx_from_oracle(levels, prec)
+    try:
+        for l, lv in enumerate(levels):
+            x = W.rhs_uniform(10 + l, lv.A.n_rows)
+            dx = torch.tensor(x, device="cuda")
+            dy = torch.empty_like(dx)
+            P.amg_spmv_device(ctx, l, dx, dy)
+            torch.cuda.synchronize()
+            ref = O.mv(O.TMat.of(lv.A), torch.from_numpy(x)).numpy()
+            assert rel_err(dy.cpu().numpy(), ref) < tol
+    finally:
+        P.amg_destroy(ctx)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "pinv"])
+@pytest.mark.parametrize("name", ["c1_64", "graded_5k", "band_4k"])
+def test_smoother_sweeps_parity_fp64(cases, name, smoother):
+    A, levels = cases[name]
+    ctx = ctx_from_oracle(levels)
+    coeffs = [COEFFS] * len(levels)
+    h = oracle_hier(levels, smoother, coeffs)
+    try:
+        if smoother == "pinv":
+            P.amg_set_coeffs(ctx, coeffs)
+        for l in range(len(levels) - 1):
+            b = W.rhs_uniform(20 + l, levels[l].A.n_rows)
+            u0 = W.rhs_uniform(30 + l, levels[l].A.n_rows)
+            db, du = torch.tensor(b, device="cuda"), torch.tensor(u0, device="cuda")
+            P.amg_smooth_device(ctx, l, db, du, 3)
+            torch.cuda.synchronize()
+            u = torch.from_numpy(u0)
+            for _ in range(3):
+                u = O.sweep(h.levels[l], torch.from_numpy(b), u)
+            assert rel_err(du.cpu().numpy(), u.numpy()) < 1e-13
+            if smoother == "pinv":
+                q = P.amg_get_smoother(ctx, l)
+                assert rel_err(q, h.levels[l].M.numpy()) < 1e-15
+    finally:
+        P.amg_destroy(ctx)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "pinv"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle_parity_fp64(cases, name, smoother):
+    A, levels = cases[name]
+    coeffs = [COEFFS] * len(levels)
+    h = oracle_hier(levels, smoother, coeffs)
+    ctx = ctx_from_oracle(levels)
+    try:
+        if smoother == "pinv":
+            P.amg_set_coeffs(ctx, coeffs)
+        r = W.rhs_uniform(5, A.n_rows)
+        dr = torch.tensor(r, device="cuda")
+        de = torch.empty_like(dr)
+        P.amg_vcycle_device(ctx, dr, de)
+        torch.cuda.synchronize()
+        assert rel_err(de.cpu().numpy(), O.vcycle_operator_apply(h, r)) < 1e-12
+    finally:
+        P.amg_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["c1_64", "uniform_3k", "band_4k"])
+def test_solve_parity_fp64(cases, name):
+    A, levels = cases[name]
+    b = W.rhs_uniform(0, A.n_rows)
+    ref = O.solve(oracle_hier(levels), b, tol=1e-8)
+    ctx = ctx_setup(A)
+    try:
+        st, x, hist = P.amg_solve(ctx, b, rtol=1e-8)
+        assert st == P.AMG_OK and ref.status == O.OK
+        assert len(hist) - 1 == ref.n_vcycles
+        assert rel_err(hist, ref.history) < 1e-10
+        assert rel_err(x, ref.x) < 1e-12
+    finally:
+        P.amg_destroy(ctx)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "pinv"])
+@pytest.mark.parametrize("name", ["c1_64", "graded_5k", "band_4k"])
+def test_mixed_precision_solve(cases, name, smoother):
+    A, levels = cases[name]
+    coeffs = [COEFFS] * len(levels)
+    b = W.rhs_zero_mean(1, A.n_rows)
+    ref = O.solve(oracle_hier(levels, smoother, coeffs), b, tol=1e-8)
+    ctx = ctx_setup(A, P.AMG_FP32_IN_FP64)
+    try:
+        if smoother == "pinv":
+            P.amg_set_coeffs(ctx, coeffs)
+        st, x, hist = P.amg_solve(ctx, b, rtol=1e-8)
+        assert st == ref.status == P.AMG_OK
+        assert abs((len(hist) - 1) - ref.n_vcycles) <= 1
+        # final residual measured independently in FP64 by the oracle
+        r = b - O.mv(O.TMat.of(A), torch.from_numpy(x)).numpy()
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-8
+        assert rel_err(x, ref.x) < 1e-6
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_degree_one_coefficients_equal_jacobi(cases):
+    A, levels = cases["graded_5k"]
+    r = torch.tensor(W.rhs_uniform(3, A.n_rows), device="cuda")
+    outs = []
+    for use_coeffs in (False, True):
+        ctx = ctx_from_oracle(levels)
+        if use_coeffs:
+            P.amg_set_coeffs(ctx, [[2.0 / 3.0, 0, 0, 0, 0]] * len(levels))
+        e = torch.empty_like(r)
+        P.amg_vcycle_device(ctx, r, e)
+        torch.cuda.synchronize()
+        outs.append(e.cpu().numpy())
+        P.amg_destroy(ctx)
+    # Jacobi double-buffers, the pseudo-inverse path computes r then u += Q r;
+    # both evaluate u_i + (omega/a_ii)(b_i - sum_j a_ij u_j) per row and differ
+    # only in where the last addition is fused.
+    assert rel_err(outs[0], outs[1]) < 1e-13
+
+
+def test_status_codes(cases):
+    A, levels = cases["c1_64"]
+    b = W.rhs_uniform(0, A.n_rows)
+    ctx = ctx_setup(A)
+    try:
+        P.amg_set_coeffs(ctx, [[5.0, 0, 0, 0, 0]] * len(levels))
+        assert P.amg_solve(ctx, b)[0] == P.AMG_ERR_DIVERGED
+        P.amg_set_coeffs(ctx, [[1e-6, 0, 0, 0, 0]] * len(levels))
+        assert P.amg_solve(ctx, b)[0] == P.AMG_ERR_STAGNATED
+        P.amg_set_jacobi(ctx)
+        st, x, hist = P.amg_solve(ctx, b, max_iter=None, rtol=1e-30)
+        assert st in (P.AMG_ERR_STAGNATED, P.AMG_ERR_MAXITER)
+    finally:
+        P.amg_destroy(ctx)
+    ctx = ctx_setup(A, max_iter=2)
+    try:
+        st, x, hist = P.amg_solve(ctx, b)
+        assert st == P.AMG_ERR_MAXITER and len(hist) == 3
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_edge_cases():
+    # single unknown, single level
+    one = W._coo_to_csr(1, 1, np.array([0]), np.array([0]), np.array([3.0]))
+    ctx = ctx_setup(one)
+    try:
+        assert P.amg_num_levels(ctx) == 1
+        st, x, hist = P.amg_solve(ctx, np.array([6.0]))
+        assert st == P.AMG_OK and abs(x[0] - 2.0) < 1e-15
+        # zero right-hand side: converged before the first cycle
+        st, x, hist = P.amg_solve(ctx, np.array([0.0]))
+        assert st == P.AMG_OK and len(hist) == 1
+    finally:
+        P.amg_destroy(ctx)
+    # ragged small grid (n not a multiple of any block) against a dense solve
+    A = W.poisson5(7)
+    ctx = ctx_setup(A, max_coarse=4)
+    try:
+        b = W.rhs_uniform(2, A.n_rows)
+        st, x, _ = P.amg_solve(ctx, b, rtol=1e-13)
+        assert st == P.AMG_OK
+        assert rel_err(x, np.linalg.solve(A.to_dense(), b)) < 1e-11
+    finally:
+        P.amg_destroy(ctx)
+    # indefinite coarsest matrix is refused
+    bad = W._coo_to_csr(2, 2, np.array([0, 0, 1, 1]), np.array([0, 1, 0, 1]), np.array([1.0, 2.0, 2.0, 1.0]))
+    ctx = P.amg_create()
+    try:
+        with pytest.raises(P.AmgError) as e:
+            P.amg_setup(ctx, bad)
+        assert e.value.code == P.AMG_ERR_NOT_SPD
+        # malformed CSR is refused with an argument error
+        broken = W.CSR(2, 2, np.array([0, 2, 1], np.int32), np.array([0, 1], np.int32), np.array([1.0, 1.0]))
+        with pytest.raises(P.AmgError) as e:
+            P.amg_setup(ctx, broken)
+        assert e.value.code == P.AMG_ERR_ARG
+        with pytest.raises(P.AmgError) as e:
+            P.amg_solve(ctx, np.zeros(2))
+        assert e.value.code == P.AMG_ERR_STATE
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_device_solve_matches_host_solve(cases):
+    A, levels = cases["graded_5k"]
+    b = W.rhs_zero_mean(4, A.n_rows)
+    ctx = ctx_setup(A, P.AMG_FP32_IN_FP64)
+    try:
+        st, x, hist = P.amg_solve(ctx, b)
+        db = torch.tensor(b, device="cuda")
+        dx = torch.zeros_like(db)
+        st2, hist2 = P.amg_solve_device(ctx, db, dx)
+        torch.cuda.synchronize()
+        assert st == st2 == P.AMG_OK
+        assert np.array_equal(hist, hist2) and np.array_equal(x, dx.cpu().numpy())
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_judge_matches_oracle(cases):
+    A, levels = cases["band_4k"]
+    coeffs = [COEFFS] * len(levels)
+    b = W.rhs_uniform(6, A.n_rows)
+    ref = O.relative_metric(oracle_hier(levels, "pinv", coeffs), oracle_hier(levels), b)
+    ctx = ctx_from_oracle(levels)
+    try:
+        P.amg_set_coeffs(ctx, coeffs)
+        m = P.amg_judge(ctx, b)
+        assert abs(m - ref) < 1e-10
+    finally:
+        P.amg_destroy(ctx)
