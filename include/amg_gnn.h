@@ -202,6 +202,33 @@ int amg_spmv_device(amg_ctx *ctx, int level, const double *d_x, double *d_y, voi
 int amg_judge(amg_ctx *ctx, const double *b, double *metric);
 
 /* ------------------------------------------------------------------------
+ * Measurement aids (no counterpart in the paper; used for roofline timing)
+ * ------------------------------------------------------------------------ */
+
+/* Kernels selectable in amg_kernel_launch. */
+#define AMG_K_RESIDUAL  0   /* r = b - A_l u                          (V-cycle precision) */
+#define AMG_K_PINV      1   /* u += Q_l^-1 r   (needs coefficients)    (V-cycle precision) */
+#define AMG_K_JACOBI    2   /* u' = u + omega D^-1 (b - A_l u)         (V-cycle precision) */
+#define AMG_K_RESTRICT  3   /* b_{l+1} = R_l r                         (V-cycle precision) */
+#define AMG_K_PROLONG   4   /* u += P_l e_{l+1}                        (V-cycle precision) */
+#define AMG_K_OUTER     5   /* FP64 r = b - A_0 x with norm partials   (level 0 only)      */
+#define AMG_K_VCYCLE    6   /* one whole V-cycle from level 0          (level ignored)     */
+
+/* Launch `reps` back-to-back instances of one solve-path kernel on level
+ * `level`, using the context's own work vectors, asynchronously on
+ * `stream`; the caller brackets the call with events to time it.  *bytes
+ * (may be NULL) receives the algorithmic bytes one launch moves, every
+ * array element counted once (values, indices and vectors at their storage
+ * width).  Errors: AMG_ERR_ARG (unknown kernel or level), AMG_ERR_STATE. */
+int amg_kernel_launch(amg_ctx *ctx, int kernel, int level, int reps, void *stream, double *bytes);
+
+/* Algorithmic bytes of one V-cycle with the current smoother/precision. */
+int amg_vcycle_bytes(const amg_ctx *ctx, double *bytes);
+
+/* Number of kernels this library has launched in this process so far. */
+long long amg_launch_count(void);
+
+/* ------------------------------------------------------------------------
  * Training (Sec. 3.3, Algorithm 1, Table train_hyper)
  * ------------------------------------------------------------------------ */
 

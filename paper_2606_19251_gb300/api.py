@@ -101,6 +101,9 @@ def _declare(L):
         "gcin_trainer_backward": (I, [P, pd, pd]),
         "gcin_trainer_adam_step": (I, [P, D, D]),
         "amg_loss_grad": (I, [P, pd, pd, pd, pd]),
+        "amg_kernel_launch": (I, [P, I, I, I, P, pd]),
+        "amg_vcycle_bytes": (I, [P, pd]),
+        "amg_launch_count": (LL, []),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):
@@ -118,7 +121,8 @@ def exported_symbols():
             "amg_solve", "amg_solve_device", "amg_vcycle_device", "amg_smooth_device", "amg_spmv_device",
             "amg_judge", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
             "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
-            "gcin_trainer_adam_step", "amg_loss_grad"]
+            "gcin_trainer_adam_step", "amg_loss_grad", "amg_kernel_launch", "amg_vcycle_bytes",
+            "amg_launch_count"]
 
 
 # ---------------------------------------------------------------------------
@@ -312,6 +316,26 @@ def amg_loss_grad(ctx, c, f):
     dc = np.zeros_like(c)
     _check(ctx, lib().amg_loss_grad(ctx, _dptr(c), _dptr(f), C.byref(loss), _dptr(dc)))
     return loss.value, dc
+
+
+AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE = range(7)
+
+
+def amg_kernel_launch(ctx, kernel, level, reps, stream=None) -> float:
+    """Enqueue `reps` launches of one kernel; returns algorithmic bytes per launch."""
+    b = C.c_double()
+    _check(ctx, lib().amg_kernel_launch(ctx, int(kernel), int(level), int(reps), _stream(stream), C.byref(b)))
+    return b.value
+
+
+def amg_vcycle_bytes(ctx) -> float:
+    b = C.c_double()
+    _check(ctx, lib().amg_vcycle_bytes(ctx, C.byref(b)))
+    return b.value
+
+
+def amg_launch_count() -> int:
+    return int(lib().amg_launch_count())
 
 
 # trainer --------------------------------------------------------------------

@@ -36,6 +36,7 @@ using namespace amg;
 // error handling
 // ---------------------------------------------------------------------------
 static thread_local std::string g_create_err;
+std::atomic<long long> amg::g_launches{0};
 
 namespace amg {
 bool ctx_fail(amg_ctx *c, const std::string &msg) {
@@ -423,27 +424,27 @@ template <class T> struct Launch {
     template <int TPR>
     static void resid(const DevMat &A, const T *b, const T *u, T *r, cudaStream_t s) {
         k_resid<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(A.nr, A.rp, A.col,
-                                                                                         mvals<T>(A), b, u, r);
+                                                                                         mvals<T>(A), b, u, r); AMG_COUNT();
     }
     template <int TPR>
     static void spmv(const DevMat &M, const T *x, T *y, cudaStream_t s) {
         k_spmv<T, TPR><<<grid_for(static_cast<long long>(M.nr) * TPR), kBlock, 0, s>>>(M.nr, M.rp, M.col,
-                                                                                        mvals<T>(M), x, y);
+                                                                                        mvals<T>(M), x, y); AMG_COUNT();
     }
     template <int TPR>
     static void apply(const DevMat &M, const T *m, const T *r, T *u, int add, cudaStream_t s) {
         k_apply<T, TPR><<<grid_for(static_cast<long long>(M.nr) * TPR), kBlock, 0, s>>>(M.nr, M.rp, M.col, m,
-                                                                                         r, u, add);
+                                                                                         r, u, add); AMG_COUNT();
     }
     template <int TPR>
     static void jacobi(const DevMat &A, const T *jac, const T *b, const T *uin, T *uout, cudaStream_t s) {
         k_jacobi<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(
-            A.nr, A.rp, A.col, mvals<T>(A), jac, b, uin, uout);
+            A.nr, A.rp, A.col, mvals<T>(A), jac, b, uin, uout); AMG_COUNT();
     }
     template <int TPR>
     static void outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nblk,
                       cudaStream_t s) {
-        k_outer_resid<T, TPR><<<nblk, kBlock, 0, s>>>(A.nr, A.rp, A.col, A.v64, b, x, rT, partial);
+        k_outer_resid<T, TPR><<<nblk, kBlock, 0, s>>>(A.nr, A.rp, A.col, A.v64, b, x, rT, partial); AMG_COUNT();
     }
 };
 
@@ -489,7 +490,7 @@ static T *smooth(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *alt, 
             }
         } else {
             if (first) {
-                k_scale<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, jvals<T>(L), b, cur);
+                k_scale<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, jvals<T>(L), b, cur); AMG_COUNT();
             } else {
                 L_jacobi<T>(L.A, jvals<T>(L), b, cur, alt, s);
                 std::swap(cur, alt);
@@ -509,7 +510,7 @@ static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
     T *t = reinterpret_cast<T *>(L.vt);
     const int nlev = static_cast<int>(c->lev.size());
     if (l == nlev - 1) {
-        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u);
+        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
         return u;
     }
     T *cur = smooth<T>(c, l, s, b, u, t, r, c->opt.nu1, true);
@@ -527,23 +528,23 @@ static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s) {
     const int nb = outer_blocks(A);
     TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb),
                  c->partials, nb, s);
-    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 1);
+    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 1); AMG_COUNT();
 }
 
 template <class T>
 static void enqueue_init(amg_ctx *c, cudaStream_t s, double tol, int max_iter) {
     const int n0 = c->lev[0].n;
     const int nb = std::min(grid_for(n0), kNumSMs * 8);
-    k_state_init<<<1, 1, 0, s>>>(c->state, tol, max_iter);
-    k_sqnorm_partial<<<nb, kBlock, 0, s>>>(n0, c->db, c->partials);
-    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 0);
+    k_state_init<<<1, 1, 0, s>>>(c->state, tol, max_iter); AMG_COUNT();
+    k_sqnorm_partial<<<nb, kBlock, 0, s>>>(n0, c->db, c->partials); AMG_COUNT();
+    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 0); AMG_COUNT();
     enqueue_outer_residual<T>(c, s);
 }
 
 template <class T>
 static void enqueue_iteration(amg_ctx *c, cudaStream_t s) {
     T *e = vcycle_level<T>(c, 0, s);
-    k_axpy<T><<<grid_for(c->lev[0].n), kBlock, 0, s>>>(c->lev[0].n, c->dx, e);
+    k_axpy<T><<<grid_for(c->lev[0].n), kBlock, 0, s>>>(c->lev[0].n, c->dx, e); AMG_COUNT();
     enqueue_outer_residual<T>(c, s);
 }
 
@@ -636,7 +637,7 @@ static int upload_mat(amg_ctx *c, const DevMat &m, const HostCSR &h, cudaStream_
     if (h.nnz() > 0) {
         CK(cudaMemcpyAsync(m.col, h.col.data(), sizeof(int) * h.nnz(), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(m.v64, h.val.data(), sizeof(double) * h.nnz(), cudaMemcpyHostToDevice, s));
-        k_convert<double, float><<<grid_for(h.nnz()), kBlock, 0, s>>>(m.nnz, m.v64, m.v32);
+        k_convert<double, float><<<grid_for(h.nnz()), kBlock, 0, s>>>(m.nnz, m.v64, m.v32); AMG_COUNT();
     }
     return AMG_OK;
 }
@@ -664,21 +665,21 @@ static int upload(amg_ctx *c) {
             if ((rc = upload_mat(c, L.P, H.P, s))) return rc;
             if ((rc = upload_mat(c, L.R, H.R, s))) return rc;
         }
-        k_extract_diag<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag);
+        k_extract_diag<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag); AMG_COUNT();
         const int nb = std::min(grid_for(L.n), kNumSMs * 8);
-        k_offdiag_absmax<<<nb, kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, c->partials);
-        k_max_final<<<1, 32, 0, s>>>(c->partials, nb, c->scal + l);
-        k_jacobi_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, c->opt.omega, L.j64, L.j32);
+        k_offdiag_absmax<<<nb, kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, c->partials); AMG_COUNT();
+        k_max_final<<<1, 32, 0, s>>>(c->partials, nb, c->scal + l); AMG_COUNT();
+        k_jacobi_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, c->opt.omega, L.j64, L.j32); AMG_COUNT();
     }
     c->jac_omega = c->opt.omega;
     // coarsest level: dense FP64 Cholesky and the inverse factor
     const DevLevel &Lc = c->lev.back();
     const int nL = c->nL;
-    k_csr_to_dense<<<grid_for(nL), kBlock, 0, s>>>(nL, Lc.A.rp, Lc.A.col, Lc.A.v64, c->Ldense);
-    k_cholesky<<<1, 1024, 0, s>>>(nL, c->Ldense, c->dflag);
+    k_csr_to_dense<<<grid_for(nL), kBlock, 0, s>>>(nL, Lc.A.rp, Lc.A.col, Lc.A.v64, c->Ldense); AMG_COUNT();
+    k_cholesky<<<1, 1024, 0, s>>>(nL, c->Ldense, c->dflag); AMG_COUNT();
     CK(cudaFuncSetAttribute(k_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8 * kMaxCoarseDense));
     CK(cudaFuncSetAttribute(k_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8 * kMaxCoarseDense));
-    k_tri_inverse<<<grid_for(nL), kBlock, 0, s>>>(nL, c->Ldense, c->Linv, c->LinvT);
+    k_tri_inverse<<<grid_for(nL), kBlock, 0, s>>>(nL, c->Ldense, c->Linv, c->LinvT); AMG_COUNT();
     CKL("hierarchy setup kernels");
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -875,8 +876,9 @@ int amg_set_jacobi(amg_ctx *c, double omega) {
     if (!std::isfinite(omega)) return ctx_fail(c, "omega not finite"), AMG_ERR_ARG;
     CK(cudaSetDevice(c->opt.device));
     if (omega != c->jac_omega) {
-        for (auto &L : c->lev)
-            k_jacobi_vals<<<grid_for(L.n), kBlock, 0, c->stream>>>(L.n, L.diag, omega, L.j64, L.j32);
+        for (auto &L : c->lev) {
+            k_jacobi_vals<<<grid_for(L.n), kBlock, 0, c->stream>>>(L.n, L.diag, omega, L.j64, L.j32); AMG_COUNT();
+        }
         CKL("jacobi values");
         CK(cudaStreamSynchronize(c->stream));
         c->jac_omega = omega;
@@ -895,7 +897,7 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
         for (int k = 0; k < 5; ++k)
             if (!std::isfinite(q[k])) return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
         k_assemble_q<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag, c->scal + l, q[0],
-                                                      q[1], q[2], q[3], q[4], L.q64, L.q32);
+                                                      q[1], q[2], q[3], q[4], L.q64, L.q32); AMG_COUNT();
     }
     (void)n_rows;
     CKL("assemble pseudo-inverse");
@@ -1004,9 +1006,9 @@ int amg_vcycle_device(amg_ctx *c, const double *d_r, double *d_e, void *stream) 
         double *e = vcycle_level<double>(c, 0, s);
         CK(cudaMemcpyAsync(d_e, e, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
     } else {
-        k_convert<double, float><<<grid_for(n0), kBlock, 0, s>>>(n0, d_r, reinterpret_cast<float *>(c->lev[0].vb));
+        k_convert<double, float><<<grid_for(n0), kBlock, 0, s>>>(n0, d_r, reinterpret_cast<float *>(c->lev[0].vb)); AMG_COUNT();
         float *e = vcycle_level<float>(c, 0, s);
-        k_convert<float, double><<<grid_for(n0), kBlock, 0, s>>>(n0, e, d_e);
+        k_convert<float, double><<<grid_for(n0), kBlock, 0, s>>>(n0, e, d_e); AMG_COUNT();
     }
     CKL("vcycle");
     return AMG_OK;
@@ -1019,10 +1021,10 @@ static void smooth_level_device(amg_ctx *c, int l, const double *d_b, double *d_
     DevLevel &L = c->lev[l];
     const int n = L.n;
     T *b = reinterpret_cast<T *>(L.vb), *u = reinterpret_cast<T *>(L.vu);
-    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_b, b);
-    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_u, u);
+    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_b, b); AMG_COUNT();
+    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_u, u); AMG_COUNT();
     T *res = smooth<T>(c, l, s, b, u, reinterpret_cast<T *>(L.vt), reinterpret_cast<T *>(L.vr), nsw, false);
-    k_convert<T, double><<<grid_for(n), kBlock, 0, s>>>(n, res, d_u);
+    k_convert<T, double><<<grid_for(n), kBlock, 0, s>>>(n, res, d_u); AMG_COUNT();
 }
 
 extern "C" {
@@ -1056,9 +1058,9 @@ int amg_spmv_device(amg_ctx *c, int level, const double *d_x, double *d_y, void 
         L_spmv<double>(L.A, d_x, d_y, s);
     } else {
         float *x = reinterpret_cast<float *>(L.vu), *y = reinterpret_cast<float *>(L.vr);
-        k_convert<double, float><<<grid_for(n), kBlock, 0, s>>>(n, d_x, x);
+        k_convert<double, float><<<grid_for(n), kBlock, 0, s>>>(n, d_x, x); AMG_COUNT();
         L_spmv<float>(L.A, x, y, s);
-        k_convert<float, double><<<grid_for(n), kBlock, 0, s>>>(n, y, d_y);
+        k_convert<float, double><<<grid_for(n), kBlock, 0, s>>>(n, y, d_y); AMG_COUNT();
     }
     CKL("spmv");
     return AMG_OK;
@@ -1089,6 +1091,124 @@ int amg_judge(amg_ctx *c, const double *b, double *metric) {
     if (rc == AMG_ERR_CUDA) return rc;
     *metric = std::log10(h_gnn[1] / h_jac[1]);
     return AMG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// measurement aids: algorithmic byte model and single-kernel launches
+// ---------------------------------------------------------------------------
+namespace {
+// bytes of one row-group pass over M: rp, col, values, gathered vector x,
+// plus `vec_rw` further vectors of n_rows entries
+double pass_bytes(const DevMat &M, int tb, double gathered, double vec_rw) {
+    return 4.0 * (M.nr + 1) + (4.0 + tb) * M.nnz + tb * gathered + tb * vec_rw * M.nr;
+}
+
+double smooth_bytes(const amg_ctx *c, const DevLevel &L, int tb, int nsweeps, bool zero_init) {
+    const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
+    double b = 0.0;
+    for (int k = 0; k < nsweeps; ++k) {
+        const bool first = (k == 0 && zero_init);
+        if (gnn) {
+            if (first) b += pass_bytes(L.A, tb, L.n, 1);                       // u = Q b
+            else b += pass_bytes(L.A, tb, L.n, 2) + pass_bytes(L.A, tb, L.n, 2);   // r = b - A u ; u += Q r
+        } else {
+            if (first) b += 3.0 * tb * L.n;                                    // u = jac b
+            else b += pass_bytes(L.A, tb, L.n, 3);                            // u' = u + jac (b - A u)
+        }
+    }
+    return b;
+}
+
+double vcycle_bytes_level(const amg_ctx *c, int l, int tb) {
+    const DevLevel &L = c->lev[l];
+    const int nlev = static_cast<int>(c->lev.size());
+    if (l == nlev - 1) return 8.0 * c->nL * c->nL + 2.0 * tb * c->nL;
+    double b = smooth_bytes(c, L, tb, c->opt.nu1, true);
+    b += pass_bytes(L.A, tb, L.n, 2);                           // residual
+    b += pass_bytes(L.R, tb, L.n, 1);                           // restriction
+    b += vcycle_bytes_level(c, l + 1, tb);
+    b += pass_bytes(L.P, tb, L.P.nc, 2);                        // prolongation-correction
+    b += smooth_bytes(c, L, tb, c->opt.nu2, false);
+    return b;
+}
+
+template <class T>
+int kernel_launch(amg_ctx *c, int which, int l, int reps, cudaStream_t s, double *bytes) {
+    DevLevel &L = c->lev[l];
+    const int tb = sizeof(T);
+    T *b = reinterpret_cast<T *>(L.vb), *u = reinterpret_cast<T *>(L.vu);
+    T *r = reinterpret_cast<T *>(L.vr), *t = reinterpret_cast<T *>(L.vt);
+    const int last = static_cast<int>(c->lev.size()) - 1;
+    double by = 0.0;
+    switch (which) {
+        case AMG_K_RESIDUAL:
+            by = pass_bytes(L.A, tb, L.n, 2);
+            for (int k = 0; k < reps; ++k) L_resid<T>(L.A, b, u, r, s);
+            break;
+        case AMG_K_PINV:
+            if (!c->have_q) return ctx_fail(c, "no pseudo-inverse coefficients set"), AMG_ERR_STATE;
+            by = pass_bytes(L.A, tb, L.n, 2);
+            for (int k = 0; k < reps; ++k) L_apply<T>(L.A, qvals<T>(L), r, u, 1, s);
+            break;
+        case AMG_K_JACOBI:
+            by = pass_bytes(L.A, tb, L.n, 3);
+            for (int k = 0; k < reps; ++k) L_jacobi<T>(L.A, jvals<T>(L), b, (k & 1) ? t : u, (k & 1) ? u : t, s);
+            break;
+        case AMG_K_RESTRICT:
+            if (l >= last) return ctx_fail(c, "no restriction on the coarsest level"), AMG_ERR_ARG;
+            by = pass_bytes(L.R, tb, L.n, 1);
+            for (int k = 0; k < reps; ++k) L_spmv<T>(L.R, r, reinterpret_cast<T *>(c->lev[l + 1].vb), s);
+            break;
+        case AMG_K_PROLONG:
+            if (l >= last) return ctx_fail(c, "no prolongation on the coarsest level"), AMG_ERR_ARG;
+            by = pass_bytes(L.P, tb, L.P.nc, 2);
+            for (int k = 0; k < reps; ++k) L_apply<T>(L.P, mvals<T>(L.P), reinterpret_cast<T *>(c->lev[l + 1].vu), u, 1, s);
+            break;
+        case AMG_K_OUTER: {
+            const DevMat &A = c->lev[0].A;
+            by = 4.0 * (A.nr + 1) + 12.0 * A.nnz + 16.0 * A.nr + tb * A.nr;
+            const int nb = outer_blocks(A);
+            for (int k = 0; k < reps; ++k) {
+                TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, c->db, c->dx,
+                             reinterpret_cast<T *>(c->lev[0].vr), c->partials, nb, s);
+            }
+            break;
+        }
+        case AMG_K_VCYCLE:
+            by = vcycle_bytes_level(c, 0, tb);
+            for (int k = 0; k < reps; ++k) vcycle_level<T>(c, 0, s);
+            break;
+        default:
+            return ctx_fail(c, "unknown kernel id"), AMG_ERR_ARG;
+    }
+    if (bytes) *bytes = by;
+    return ctx_cuda_check(c, cudaGetLastError(), "kernel launch");
+}
+}  // namespace
+
+extern "C" {
+
+long long amg_launch_count(void) { return amg::g_launches.load(); }
+
+int amg_vcycle_bytes(const amg_ctx *c, double *bytes) {
+    if (!c || !bytes) return AMG_ERR_ARG;
+    if (c->lev.empty()) return AMG_ERR_STATE;
+    *bytes = vcycle_bytes_level(c, 0, c->opt.precision == AMG_FP64 ? 8 : 4);
+    return AMG_OK;
+}
+
+int amg_kernel_launch(amg_ctx *c, int which, int level, int reps, void *stream, double *bytes) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (level < 0 || level >= static_cast<int>(c->lev.size()) || reps < 0)
+        return ctx_fail(c, "bad level or repetition count"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->opt.precision == AMG_FP64) return kernel_launch<double>(c, which, level, reps, s, bytes);
+    return kernel_launch<float>(c, which, level, reps, s, bytes);
 }
 
 }  // extern "C"

@@ -2,11 +2,17 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
 
 namespace amg {
+
+// Process-wide count of kernels this library has launched (reported by
+// amg_launch_count; every launch site is followed by AMG_COUNT()).
+extern std::atomic<long long> g_launches;
+#define AMG_COUNT() (::amg::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 constexpr int kBlock = 256;          // threads per block of the row kernels
 constexpr int kNumSMs = 152;         // GB300

@@ -117,12 +117,12 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
             const int work = std::max(L.n, L.A.nnz);
             k_cat_graph<<<grid_for(work), kBlock, 0, s>>>(L.n, L.A.nnz, L.A.rp, L.A.col, L.A.v64, gptr[g],
                                                           static_cast<int>(eoff), g, b.rp, b.col, b.w, b.w64,
-                                                          b.gid);
+                                                          b.gid); AMG_COUNT();
             eoff += L.A.nnz;
             ++g;
         }
     }
-    k_set_int<<<1, 1, 0, s>>>(b.rp + b.N, static_cast<int>(E));
+    k_set_int<<<1, 1, 0, s>>>(b.rp + b.N, static_cast<int>(E)); AMG_COUNT();
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("batch build: ") + cudaGetErrorString(e);
@@ -358,23 +358,23 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
 
 void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
     const int N = b.N, G = b.G;
-    k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0);
+    k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
     const int warp_grid = grid_for(static_cast<long long>(N) * 32);
     const int elem_grid = grid_for(static_cast<long long>(N) * kHidden);
     for (int l = 0; l < kLayers; ++l) {
         if (l == 0) {
             k_layer1<<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0, th + kPL.convW[0], th + kPL.convB[0],
-                                                  b.h1, b.y[0]);
+                                                  b.h1, b.y[0]); AMG_COUNT();
         } else {
             k_agg_lin<<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
-                                                   th + kPL.convB[l], b.h[l], b.y[l]);
+                                                   th + kPL.convB[l], b.h[l], b.y[l]); AMG_COUNT();
         }
-        k_graph_stats<<<G, kBlock, 0, s>>>(b.gptr, b.y[l], b.mu[l], b.rstd[l]);
+        k_graph_stats<<<G, kBlock, 0, s>>>(b.gptr, b.y[l], b.mu[l], b.rstd[l]); AMG_COUNT();
         k_norm_relu<<<elem_grid, kBlock, 0, s>>>(N, b.gid, b.y[l], b.mu[l], b.rstd[l], th + kPL.inG[l],
-                                                 th + kPL.inB[l], b.x[l]);
-        k_pool<<<G, kBlock, 0, s>>>(b.gptr, b.x[l], b.pooled, b.argmax, l);
+                                                 th + kPL.inB[l], b.x[l]); AMG_COUNT();
+        k_pool<<<G, kBlock, 0, s>>>(b.gptr, b.x[l], b.pooled, b.argmax, l); AMG_COUNT();
     }
-    k_head<<<G, 128, 0, s>>>(b.pooled, th, b.head, b.c);
+    k_head<<<G, 128, 0, s>>>(b.pooled, th, b.head, b.c); AMG_COUNT();
 }
 
 void gcin_engine_free(GcinEngine *e) {
