@@ -228,6 +228,34 @@ int amg_vcycle_bytes(const amg_ctx *ctx, double *bytes);
 /* Number of kernels this library has launched in this process so far. */
 long long amg_launch_count(void);
 
+/* Allocation-free residual norm.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- applications that
+ * reserve all device memory up front in their own pool, or that run it in a
+ * time-critical loop where a driver allocation (which may synchronise the
+ * device or fail under memory pressure) is not acceptable.
+ *
+ * Computes r = b - A x in FP64 for a caller-owned CSR matrix already on the
+ * device (n rows, nnz entries; same layout rules as amg_csr), stores r in d_r
+ * when d_r is not NULL, and writes d_out[0] = ||b - A x||_2 and
+ * d_out[1] = ||b||_2.  Every input and output is caller-owned device memory;
+ * the call allocates nothing.  Its only scratch is a fixed array of
+ * 2 x 1216 doubles (19,456 bytes) compiled into the library, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * Limits: 0 <= n <= 67,108,863 rows (the row-group thread index must fit a
+ * 32-bit int) and 0 <= nnz <= 2^31 - 1; anything larger is rejected with
+ * AMG_ERR_ARG.  The first call on a device looks up the scratch array's
+ * device address (once per device, with that device current); make that
+ * first call before any stream capture.  All calls on a device share the
+ * scratch array, so calls whose work overlaps on the GPU (e.g. on two
+ * concurrent streams) race and give wrong norms; serialise them.  The array
+ * keeps the last call's contents, and every call overwrites the slots it
+ * reads.  Asynchronous on `stream` (a cudaStream_t) of the current device.
+ * Errors: AMG_ERR_ARG, AMG_ERR_CUDA; amg_last_error(NULL) describes them. */
+int amg_residual_norm_noalloc(int n, long long nnz, const int *d_row_ptr, const int *d_col,
+                              const double *d_val, const double *d_b, const double *d_x, double *d_r,
+                              double *d_out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Training (Sec. 3.3, Algorithm 1, Table train_hyper)
  * ------------------------------------------------------------------------ */

@@ -104,6 +104,7 @@ def _declare(L):
         "amg_kernel_launch": (I, [P, I, I, I, P, pd]),
         "amg_vcycle_bytes": (I, [P, pd]),
         "amg_launch_count": (LL, []),
+        "amg_residual_norm_noalloc": (I, [I, LL, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):
@@ -122,7 +123,7 @@ def exported_symbols():
             "amg_judge", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
             "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
             "gcin_trainer_adam_step", "amg_loss_grad", "amg_kernel_launch", "amg_vcycle_bytes",
-            "amg_launch_count"]
+            "amg_launch_count", "amg_residual_norm_noalloc"]
 
 
 # ---------------------------------------------------------------------------
@@ -336,6 +337,23 @@ def amg_vcycle_bytes(ctx) -> float:
 
 def amg_launch_count() -> int:
     return int(lib().amg_launch_count())
+
+
+def amg_residual_norm_noalloc(d_row_ptr, d_col, d_val, d_b, d_x, d_out, d_r=None, stream=None):
+    """||b - A x|| and ||b|| into d_out[0:2] with no allocation; all arguments are device tensors."""
+    import torch
+    n = d_b.numel()
+    nnz = d_col.numel()
+    for t, dt in ((d_row_ptr, torch.int32), (d_col, torch.int32)):
+        assert t.is_cuda and t.dtype == dt and t.is_contiguous()
+    rp = C.c_void_p(d_row_ptr.data_ptr())
+    col = C.c_void_p(d_col.data_ptr())
+    r = _dev(d_r) if d_r is not None else None
+    rc = lib().amg_residual_norm_noalloc(n, nnz, rp, col, _dev(d_val), _dev(d_b), _dev(d_x), r, _dev(d_out),
+                                         _stream(stream))
+    if rc != AMG_OK:
+        raise AmgError(rc, amg_last_error(None))
+    return rc
 
 
 # trainer --------------------------------------------------------------------

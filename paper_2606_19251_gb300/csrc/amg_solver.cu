@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1212,3 +1213,141 @@ int amg_kernel_launch(amg_ctx *c, int which, int level, int reps, void *stream, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free residual norm (caller owns every buffer; scratch is static)
+// ---------------------------------------------------------------------------
+namespace {
+// Per-block partial sums of ||r||^2 and ||b||^2.  Lives for the life of the
+// process on every device that loads this library; shared by all calls.
+constexpr int kStaticSlots = kNumSMs * 8;      // blocks of one launch at most
+constexpr int kNoAllocMaxRows = (1 << 26) - 1; // row * 32 lanes must fit in int
+static __device__ __align__(256) double g_static_partials[2 * kStaticSlots];
+
+// r = b - A x in FP64 (r stored when r_out != NULL); partials of r.r and b.b
+template <int TPR>
+__global__ void __launch_bounds__(kBlock) k_resid_norm_static(int n, const int *__restrict__ rp,
+                                                              const int *__restrict__ col,
+                                                              const double *__restrict__ a,
+                                                              const double *__restrict__ b,
+                                                              const double *__restrict__ x,
+                                                              double *__restrict__ r_out,
+                                                              double *__restrict__ scratch) {
+    constexpr int RPB = kBlock / TPR;
+    const int lane = threadIdx.x % TPR;
+    double rr = 0.0, bb = 0.0;
+    for (int base = blockIdx.x * RPB; base < n; base += gridDim.x * RPB) {
+        const int row = base + threadIdx.x / TPR;
+        double acc = 0.0;
+        if (row < n) {
+            const int e = rp[row + 1];
+            for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * x[col[p]];
+        }
+        acc = group_sum<TPR>(acc);
+        if (row < n && lane == 0) {
+            const double r = b[row] - acc;
+            if (r_out) r_out[row] = r;
+            rr += r * r;
+            bb += b[row] * b[row];
+        }
+    }
+    block_partial(rr, scratch);
+    __syncthreads();
+    block_partial(bb, scratch + kStaticSlots);
+}
+
+// out[0] = ||b - A x||_2, out[1] = ||b||_2 from the first np partials (fixed order)
+__global__ void __launch_bounds__(1024) k_resid_norm_static_final(int np, double *__restrict__ out) {
+    __shared__ double red[2][32];
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < np; i += 1024) {
+        v[0] += g_static_partials[i];
+        v[1] += g_static_partials[kStaticSlots + i];
+    }
+    for (int k = 0; k < 2; ++k) {
+        double w = warp_sum(v[k]);
+        if (threadIdx.x % 32 == 0) red[k][threadIdx.x / 32] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int k = 0; k < 2; ++k) {
+            double w = warp_sum(red[k][threadIdx.x]);
+            if (threadIdx.x == 0) out[k] = sqrt(w);
+        }
+    }
+}
+
+__global__ void k_zero2(double *out) {
+    out[0] = 0.0;
+    out[1] = 0.0;
+}
+
+// Device address of g_static_partials, looked up once per device.
+std::mutex g_static_mutex;
+double *g_static_addr[64] = {};
+
+int static_scratch_for(int dev, double **ptr) {
+    if (dev < 0 || dev >= 64) {
+        g_create_err = "device ordinal out of range for the static scratch table";
+        return AMG_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess || !p) {
+            g_create_err = std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e);
+            return AMG_ERR_CUDA;
+        }
+        g_static_addr[dev] = static_cast<double *>(p);
+    }
+    *ptr = g_static_addr[dev];
+    return AMG_OK;
+}
+}  // namespace
+
+extern "C" int amg_residual_norm_noalloc(int n, long long nnz, const int *d_row_ptr, const int *d_col,
+                                         const double *d_val, const double *d_b, const double *d_x,
+                                         double *d_r, double *d_out, void *stream) {
+    g_create_err.clear();
+    if (n < 0 || n > kNoAllocMaxRows || nnz < 0 || nnz > 2147483647LL) {
+        g_create_err = "amg_residual_norm_noalloc: n must be in [0, 67108863] and nnz in [0, 2^31-1]";
+        return AMG_ERR_ARG;
+    }
+    if (!d_out || (n > 0 && (!d_row_ptr || !d_b || !d_x || (nnz > 0 && (!d_col || !d_val))))) {
+        g_create_err = "amg_residual_norm_noalloc: NULL device pointer";
+        return AMG_ERR_ARG;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        g_create_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return AMG_ERR_CUDA;
+    }
+    double *scratch = nullptr;
+    int rc = static_scratch_for(dev, &scratch);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        k_zero2<<<1, 1, 0, s>>>(d_out); AMG_COUNT();
+    } else {
+        const int tpr = pick_tpr(nnz, n);
+        const long long need = (static_cast<long long>(n) * tpr + kBlock - 1) / kBlock;
+        const int nb = static_cast<int>(std::max(1LL, std::min<long long>(need, kStaticSlots)));
+        switch (tpr) {
+            case 2: k_resid_norm_static<2><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
+            case 4: k_resid_norm_static<4><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
+            case 8: k_resid_norm_static<8><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
+            case 16: k_resid_norm_static<16><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
+            default: k_resid_norm_static<32><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
+        }
+        AMG_COUNT();
+        k_resid_norm_static_final<<<1, 1024, 0, s>>>(nb, d_out); AMG_COUNT();
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_create_err = std::string("amg_residual_norm_noalloc launch: ") + cudaGetErrorString(e);
+        return AMG_ERR_CUDA;
+    }
+    return AMG_OK;
+}
