@@ -576,6 +576,7 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
 static const int kMaxCoarseDense = 4096;
 
 static void free_device(amg_ctx *c) {
+    train_bufs_free(c);
     if (c->arena) cudaFree(c->arena);
     c->arena = nullptr;
     c->arena_bytes = 0;
@@ -625,8 +626,8 @@ static void layout(amg_ctx *c, Planner &pl) {
     const int n0 = c->host[0].A.n_rows;
     c->db = pl.take<double>(n0);
     c->dx = pl.take<double>(n0);
-    c->n_partials = kNumSMs * 8;
-    c->partials = pl.take<double>(c->n_partials);
+    c->n_partials = kNumSMs * 8;                       // blocks of a capped grid
+    c->partials = pl.take<double>(5 * c->n_partials);  // up to 5 partial sums per block
     c->scal = pl.take<double>(nlev);
     c->state = pl.take<SolveState>(1);
     c->hist = pl.take<double>(c->opt.max_iter + 1);
@@ -1351,3 +1352,317 @@ extern "C" int amg_residual_norm_noalloc(int n, long long nnz, const int *d_row_
     }
     return AMG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Training loss and the hand-written V-cycle adjoint (Sec. 3.3, N_vc = 1)
+// ---------------------------------------------------------------------------
+// Forward: one V-cycle from u = 0 with the pseudo-inverse smoother, keeping
+// every sweep's input residual r_k per level (the checkpoints).  A sweep is
+// u' = u + M r, r = b - A u, M = Q^-1(c) symmetric, so its adjoint is
+//   dL/dM_ij += ubar'_i r_j,  rbar = M ubar',  ubar = ubar' - A rbar,  bbar += rbar,
+// restriction and prolongation swap (R^T = P), and the coarse solve is
+// self-adjoint.  dL/dc_k = sum_ij dL/dM_ij dM_ij/dc_k with
+//   dM_ii/d(d0, d1, d2) = (1, x, x^2) / a_ii,          x = a_ii / s
+//   dM_ij/d(o1, o2)     = (x, x^2) / (a_ii + a_jj),    x = a_ij / s.
+namespace {
+
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_coef_grad(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                      const double *__restrict__ a, const double *__restrict__ d,
+                                                      const double *__restrict__ s_ptr, const T *__restrict__ ubar,
+                                                      const T *__restrict__ r, double *__restrict__ partial) {
+    constexpr int RPB = kBlock / TPR;
+    const int lane = threadIdx.x % TPR;
+    const double s = *s_ptr;
+    double g[5] = {0, 0, 0, 0, 0};
+    for (int base = blockIdx.x * RPB; base < n; base += gridDim.x * RPB) {
+        const int row = base + threadIdx.x / TPR;
+        double acc[5] = {0, 0, 0, 0, 0};
+        if (row < n) {
+            const double ui = static_cast<double>(ubar[row]), di = d[row];
+            for (int p = rp[row] + lane; p < rp[row + 1]; p += TPR) {
+                const int j = col[p];
+                const double x = a[p] / s;
+                if (j == row) {
+                    const double w = ui * static_cast<double>(r[j]) / di;
+                    acc[0] += w;
+                    acc[1] += w * x;
+                    acc[2] += w * x * x;
+                } else {
+                    const double w = ui * static_cast<double>(r[j]) / (di + d[j]);
+                    acc[3] += w * x;
+                    acc[4] += w * x * x;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) g[k] += group_sum<TPR>(acc[k]);
+    }
+    __shared__ double red[5][kBlock / 32];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double v = (lane == 0) ? g[k] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x % 32 == 0) red[k][threadIdx.x / 32] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) t += red[threadIdx.x][w];
+        partial[blockIdx.x * 5 + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_coef_grad_final(int np, const double *__restrict__ partial, double *__restrict__ dc) {
+    if (threadIdx.x >= 5) return;
+    double t = 0.0;
+    for (int b = 0; b < np; ++b) t += partial[b * 5 + threadIdx.x];
+    dc[threadIdx.x] += t;
+}
+
+template <class T>
+__global__ void k_add(int n, T *__restrict__ y, const T *__restrict__ x) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n) y[i] += x[i];
+}
+
+template <class T>
+__global__ void k_scale_copy(int n, T *__restrict__ y, const T *__restrict__ x, double a) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n) y[i] = static_cast<T>(a * static_cast<double>(x[i]));
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_dot_partial(int n, const T *__restrict__ x, const T *__restrict__ y,
+                                                        double *__restrict__ partial) {
+    double s = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+        s += static_cast<double>(x[i]) * static_cast<double>(y[i]);
+    block_partial(s, partial);
+}
+
+__global__ void k_sum_final(int np, const double *__restrict__ partial, double *__restrict__ out) {
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < np; i += 1024) v += partial[i];
+    v = warp_sum(v);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = warp_sum(red[threadIdx.x]);
+        if (threadIdx.x == 0) *out = v;
+    }
+}
+
+struct TrainBufs {
+    std::vector<double *> ck;      // per level: (nu1 + nu2) checkpoint vectors
+    std::vector<double *> ubar, tmp, bbar, zero;
+    double *dcoef = nullptr;       // n_levels x 5
+    double *scal = nullptr;        // 4 doubles
+    char *arena = nullptr;
+};
+
+int train_bufs(amg_ctx *c, TrainBufs &tb) {
+    const int nlev = static_cast<int>(c->lev.size());
+    const int nsw = c->opt.nu1 + c->opt.nu2;
+    auto lay = [&](Planner &pl) {
+        tb.ck.assign(static_cast<size_t>(nlev) * std::max(1, nsw), nullptr);
+        tb.ubar.assign(nlev, nullptr);
+        tb.tmp.assign(nlev, nullptr);
+        tb.bbar.assign(nlev, nullptr);
+        tb.zero.assign(nlev, nullptr);
+        for (int l = 0; l < nlev; ++l) {
+            const int n = c->lev[l].n;
+            for (int k = 0; k < nsw; ++k) tb.ck[static_cast<size_t>(l) * nsw + k] = pl.take<double>(n);
+            tb.ubar[l] = pl.take<double>(n);
+            tb.tmp[l] = pl.take<double>(n);
+            tb.bbar[l] = pl.take<double>(n);
+            tb.zero[l] = pl.take<double>(n);
+        }
+        tb.dcoef = pl.take<double>(static_cast<size_t>(nlev) * 5);
+        tb.scal = pl.take<double>(4);
+    };
+    Planner pl;
+    lay(pl);
+    cudaError_t e = cudaMalloc(&tb.arena, pl.off);
+    if (e != cudaSuccess) return ctx_cuda_check(c, e, "cudaMalloc training buffers");
+    const size_t bytes = pl.off;
+    pl = Planner{};
+    pl.base = tb.arena;
+    lay(pl);
+    return ctx_cuda_check(c, cudaMemsetAsync(tb.arena, 0, bytes, c->stream), "memset training buffers");
+}
+
+template <class T>
+T *fwd_level_ckpt(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
+    DevLevel &L = c->lev[l];
+    T *b = reinterpret_cast<T *>(L.vb), *u = reinterpret_cast<T *>(L.vu), *r = reinterpret_cast<T *>(L.vr);
+    const int nlev = static_cast<int>(c->lev.size());
+    const int nu1 = c->opt.nu1, nu2 = c->opt.nu2, nsw = nu1 + nu2;
+    if (l == nlev - 1) {
+        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
+        return u;
+    }
+    auto ck = [&](int k) { return reinterpret_cast<T *>(tb.ck[static_cast<size_t>(l) * nsw + k]); };
+    if (nu1 == 0) cudaMemsetAsync(u, 0, sizeof(T) * L.n, s);
+    for (int k = 0; k < nu1; ++k) {
+        if (k == 0) {
+            L_apply<T>(L.A, qvals<T>(L), b, u, 0, s);
+        } else {
+            L_resid<T>(L.A, b, u, ck(k), s);
+            L_apply<T>(L.A, qvals<T>(L), ck(k), u, 1, s);
+        }
+    }
+    L_resid<T>(L.A, b, u, r, s);
+    L_spmv<T>(L.R, r, reinterpret_cast<T *>(c->lev[l + 1].vb), s);
+    T *e = fwd_level_ckpt<T>(c, tb, l + 1, s);
+    L_apply<T>(L.P, mvals<T>(L.P), e, u, 1, s);
+    for (int k = nu1; k < nsw; ++k) {
+        L_resid<T>(L.A, b, u, ck(k), s);
+        L_apply<T>(L.A, qvals<T>(L), ck(k), u, 1, s);
+    }
+    return u;
+}
+
+template <class T>
+void coef_grad(amg_ctx *c, TrainBufs &tb, int l, const T *ubar, const T *r, cudaStream_t s) {
+    const DevLevel &L = c->lev[l];
+    const DevMat &A = L.A;
+    const int nb = outer_blocks(A);
+#define CG_LAUNCH(TP)                                                                                          \
+    k_coef_grad<T, TP><<<nb, kBlock, 0, s>>>(A.nr, A.rp, A.col, A.v64, L.diag, c->scal + l, ubar, r, c->partials); \
+    AMG_COUNT();
+    switch (A.tpr) {
+        case 2: CG_LAUNCH(2) break;
+        case 4: CG_LAUNCH(4) break;
+        case 8: CG_LAUNCH(8) break;
+        case 16: CG_LAUNCH(16) break;
+        default: CG_LAUNCH(32) break;
+    }
+#undef CG_LAUNCH
+    k_coef_grad_final<<<1, 32, 0, s>>>(nb, c->partials, tb.dcoef + 5 * l); AMG_COUNT();
+}
+
+// Backward of one sweep u' = u + M r (r = b - A u): accumulate dL/dc, then
+// ubar <- ubar - A (M ubar) into `spare`, bbar += M ubar.  Returns the new ubar.
+template <class T>
+T *sweep_adjoint(amg_ctx *c, TrainBufs &tb, int l, T *ubar, T *spare, const T *r, T *bbar, cudaStream_t s) {
+    const DevLevel &L = c->lev[l];
+    coef_grad<T>(c, tb, l, ubar, r, s);
+    T *rbar = reinterpret_cast<T *>(L.vt);            // free during the backward pass
+    L_apply<T>(L.A, qvals<T>(L), ubar, rbar, 0, s);   // rbar = M ubar
+    L_resid<T>(L.A, ubar, rbar, spare, s);            // spare = ubar - A rbar
+    k_add<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, bbar, rbar); AMG_COUNT();
+    return spare;
+}
+
+// Backward of the V-cycle on level l: tb.ubar[l] = dL/d(level output) in,
+// tb.bbar[l] = dL/d(level right-hand side) out.
+template <class T>
+void bwd_level(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
+    DevLevel &L = c->lev[l];
+    const int nlev = static_cast<int>(c->lev.size());
+    const int nu1 = c->opt.nu1, nu2 = c->opt.nu2, nsw = nu1 + nu2;
+    T *ub = reinterpret_cast<T *>(tb.ubar[l]), *sp = reinterpret_cast<T *>(tb.tmp[l]);
+    T *bb = reinterpret_cast<T *>(tb.bbar[l]);
+    if (l == nlev - 1) {   // u = A_L^-1 b is self-adjoint
+        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, ub, bb); AMG_COUNT();
+        return;
+    }
+    auto ck = [&](int k) { return reinterpret_cast<const T *>(tb.ck[static_cast<size_t>(l) * nsw + k]); };
+    cudaMemsetAsync(bb, 0, sizeof(T) * L.n, s);
+    for (int k = nsw - 1; k >= nu1; --k) {
+        T *nu = sweep_adjoint<T>(c, tb, l, ub, sp, ck(k), bb, s);
+        sp = ub;
+        ub = nu;
+    }
+    // prolongation u += P e: ebar = P^T ubar = R ubar
+    L_spmv<T>(L.R, ub, reinterpret_cast<T *>(tb.ubar[l + 1]), s);
+    bwd_level<T>(c, tb, l + 1, s);
+    // restriction b_{l+1} = R (b - A u): rhobar = R^T bbar_{l+1} = P bbar_{l+1}
+    T *rhobar = reinterpret_cast<T *>(L.vt);
+    L_spmv<T>(L.P, reinterpret_cast<const T *>(tb.bbar[l + 1]), rhobar, s);
+    k_add<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, bb, rhobar); AMG_COUNT();
+    L_resid<T>(L.A, ub, rhobar, sp, s);
+    std::swap(ub, sp);
+    for (int k = nu1 - 1; k >= 1; --k) {
+        T *nu = sweep_adjoint<T>(c, tb, l, ub, sp, ck(k), bb, s);
+        sp = ub;
+        ub = nu;
+    }
+    if (nu1 >= 1) {        // first sweep from zero: u = M b
+        coef_grad<T>(c, tb, l, ub, reinterpret_cast<const T *>(L.vb), s);
+        L_apply<T>(L.A, qvals<T>(L), ub, reinterpret_cast<T *>(L.vt), 0, s);
+        k_add<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, bb, reinterpret_cast<const T *>(L.vt)); AMG_COUNT();
+    }
+}
+
+template <class T>
+int loss_grad(amg_ctx *c, TrainBufs &tb, const double *f, double *loss, double *dc) {
+    cudaStream_t s = c->stream;
+    DevLevel &L0 = c->lev[0];
+    const int n0 = L0.n, nlev = static_cast<int>(c->lev.size());
+    CK(cudaMemcpyAsync(c->db, f, sizeof(double) * n0, cudaMemcpyHostToDevice, s));
+    k_convert<double, T><<<grid_for(n0), kBlock, 0, s>>>(n0, c->db, reinterpret_cast<T *>(L0.vb)); AMG_COUNT();
+    T *u = fwd_level_ckpt<T>(c, tb, 0, s);
+    T *fT = reinterpret_cast<T *>(L0.vb), *r1 = reinterpret_cast<T *>(tb.tmp[0]);
+    L_resid<T>(L0.A, fT, u, r1, s);
+    const int nb = std::min(grid_for(n0), kNumSMs * 8);
+    k_dot_partial<T><<<nb, kBlock, 0, s>>>(n0, r1, r1, c->partials); AMG_COUNT();
+    k_sum_final<<<1, 1024, 0, s>>>(nb, c->partials, tb.scal); AMG_COUNT();
+    k_dot_partial<T><<<nb, kBlock, 0, s>>>(n0, fT, fT, c->partials); AMG_COUNT();
+    k_sum_final<<<1, 1024, 0, s>>>(nb, c->partials, tb.scal + 1); AMG_COUNT();
+    double h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, tb.scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double rr = h[0], ff = h[1];
+    if (!(rr > 0.0) || !(ff > 0.0) || !std::isfinite(rr))
+        return ctx_fail(c, "loss undefined: zero or non-finite residual"), AMG_ERR_DIVERGED;
+    *loss = 0.5 * std::log10(rr / ff);
+    // dL/du = -A^T r1 / (ln10 ||r1||^2)
+    T *seed = reinterpret_cast<T *>(L0.vt);
+    k_scale_copy<T><<<grid_for(n0), kBlock, 0, s>>>(n0, seed, r1, 1.0 / (std::log(10.0) * rr)); AMG_COUNT();
+    L_resid<T>(L0.A, reinterpret_cast<const T *>(tb.zero[0]), seed, reinterpret_cast<T *>(tb.ubar[0]), s);
+    CK(cudaMemsetAsync(tb.dcoef, 0, sizeof(double) * 5 * nlev, s));
+    bwd_level<T>(c, tb, 0, s);
+    CKL("V-cycle adjoint");
+    CK(cudaMemcpyAsync(dc, tb.dcoef, sizeof(double) * 5 * nlev, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+}  // namespace
+
+extern "C" int amg_loss_grad(amg_ctx *c, const double *coef, const double *f, double *loss, double *dc) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (!coef || !f || !loss || !dc) return ctx_fail(c, "NULL argument"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    const int nlev = static_cast<int>(c->lev.size());
+    int rc = set_coeffs_device(c, coef, nlev, c->stream);
+    if (rc) return rc;
+    if (!c->train) {
+        TrainBufs *tb = new TrainBufs();
+        rc = train_bufs(c, *tb);
+        if (rc) {
+            if (tb->arena) cudaFree(tb->arena);
+            delete tb;
+            return rc;
+        }
+        c->train = tb;
+    }
+    TrainBufs &tb = *static_cast<TrainBufs *>(c->train);
+    if (c->opt.precision == AMG_FP64) return loss_grad<double>(c, tb, f, loss, dc);
+    return loss_grad<float>(c, tb, f, loss, dc);
+}
+
+namespace amg {
+void train_bufs_free(amg_ctx *c) {
+    if (!c->train) return;
+    TrainBufs *tb = static_cast<TrainBufs *>(c->train);
+    if (tb->arena) cudaFree(tb->arena);
+    delete tb;
+    c->train = nullptr;
+}
+}  // namespace amg

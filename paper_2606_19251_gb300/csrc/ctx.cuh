@@ -70,6 +70,7 @@ struct amg_ctx {
     double jac_omega = 2.0 / 3.0;
     amg::GcinEngine *gnn = nullptr;
     long long hier_version = 0;                // bumped by every hierarchy upload
+    void *train = nullptr;                     // training (adjoint) buffers, created on demand
 };
 
 namespace amg {
@@ -77,4 +78,5 @@ namespace amg {
 bool ctx_fail(amg_ctx *c, const std::string &msg);
 int ctx_cuda_check(amg_ctx *c, cudaError_t e, const char *what);
 int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s);
+void train_bufs_free(amg_ctx *c);
 }  // namespace amg

@@ -1,17 +1,22 @@
-// GCIN coefficient network, forward pass (Sec. 3.2, App. A.1; Algorithm 1
-// steps 1-6) on sm_103a.
+// GCIN coefficient network (Sec. 3.2, App. A.1; Algorithm 1 steps 1-6 and
+// the network half of step 13) on sm_103a: forward, backward and Adam.
 //
 // The batch is the disjoint union of every level graph (Algorithm 1 step 5):
 // one concatenated CSR whose entries are the edges (weight a_ij; the
-// diagonal entry is the self-loop of A_hat with weight a_ii) plus the node
-// range of every graph.  Per layer:
-//   aggregation  h_i = sum_j w_ij x_j         warp per node, lanes own 2 features
-//   linear       y = h Theta + b              fused into the aggregation kernel
-//   statistics   per graph mean/rstd of y     block per graph, FP64 sums
-//   normalise    x = ReLU((y - mu) rstd gamma + beta)
-//   pooling      per graph mean / max (+argmax) of x
+// diagonal entry is the self-loop of A_hat with weight a_ii).  Nodes are cut
+// into tiles of <= 64 consecutive nodes inside one graph; one block owns a
+// tile.  Per layer (forward):
+//   aggregation + linear   h_i = sum_j w_ij x_j, y = h Theta + b   (warp per
+//                          node, lanes own feature pairs) and, in the same
+//                          kernel, the tile's mean / M2 of y per feature
+//   statistics             per graph: Chan combination of tile partials
+//   normalise + pool       x = ReLU((y - mu) rstd gamma + beta) and the
+//                          tile's sum / max / argmax of x
+//   pooling                per graph: combination of tile partials
 // Head (block per graph): 4 readout linears 128->32, LayerNorm(128),
 // sigmoid, Linear 128->128 + ReLU, Linear 128->64 + ReLU, Linear 64->5.
+// Backward mirrors these steps; every parameter gradient is a fixed-order
+// sum of per-tile or per-graph partials, so gradients are bit-reproducible.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,14 +57,17 @@ void gcin_batch_free(GcinBatch &b) {
     b = GcinBatch{};
 }
 
-static void batch_layout(GcinBatch &b, Planner &pl) {
-    const size_t N = b.N, G = b.G, E = std::max<long long>(1, b.E);
+static void batch_layout(GcinBatch &b, Planner &pl, bool backward) {
+    const size_t N = b.N, G = b.G, NT = b.NT, E = std::max<long long>(1, b.E);
     b.rp = pl.take<int>(N + 1);
     b.col = pl.take<int>(E);
     b.w = pl.take<float>(E);
     b.w64 = pl.take<double>(E);
     b.gptr = pl.take<int>(G + 1);
     b.gid = pl.take<int>(N);
+    b.tstart = pl.take<int>(NT + 1);
+    b.tgraph = pl.take<int>(NT);
+    b.gtile = pl.take<int>(G + 1);
     b.x0 = pl.take<double>(N * 2);
     b.h1 = pl.take<float>(N * 2);
     for (int l = 0; l < kLayers; ++l) {
@@ -69,15 +77,33 @@ static void batch_layout(GcinBatch &b, Planner &pl) {
         b.mu[l] = pl.take<float>(G * kHidden);
         b.rstd[l] = pl.take<float>(G * kHidden);
     }
+    b.tmean = pl.take<float>(NT * kHidden);
+    b.tm2 = pl.take<float>(NT * kHidden);
+    b.tsum = pl.take<double>(NT * kHidden);
+    b.tsum2 = pl.take<double>(NT * kHidden);
+    b.tmax = pl.take<float>(NT * kHidden);
+    b.targ = pl.take<int>(NT * kHidden);
     b.pooled = pl.take<float>(G * kLayers * 2 * kHidden);
     b.argmax = pl.take<int>(G * kLayers * kHidden);
     b.head = pl.take<float>(G * kHeadScratch);
     b.c = pl.take<float>(G * 5);
+    if (backward) {
+        b.dc = pl.take<float>(G * 5);
+        b.dhead = pl.take<float>(G * kHeadGrad);
+        b.dpooled = pl.take<float>(G * kLayers * 2 * kHidden);
+        b.dx = pl.take<float>(N * kHidden);
+        b.dh = pl.take<float>(N * kHidden);
+        b.dy = pl.take<float>(N * kHidden);
+        b.gS1 = pl.take<double>(G * kHidden);
+        b.gS2 = pl.take<double>(G * kHidden);
+        b.dWt = pl.take<float>(NT * (kHidden * kHidden + kHidden));
+    }
 }
 
-int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cudaStream_t s, std::string &err) {
+int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cudaStream_t s, std::string &err,
+                     bool backward) {
     gcin_batch_free(b);
-    std::vector<int> gptr(1, 0);
+    std::vector<int> gptr(1, 0), tstart, tgraph, gtile;
     long long E = 0;
     for (int m = 0; m < n_problems; ++m) {
         const amg_ctx *c = problems[m];
@@ -86,19 +112,28 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
             return AMG_ERR_STATE;
         }
         for (const auto &L : c->lev) {
+            const int g = static_cast<int>(gptr.size()) - 1;
+            gtile.push_back(static_cast<int>(tstart.size()));
+            for (int a = gptr.back(); a < gptr.back() + L.n; a += kTile) {
+                tstart.push_back(a);
+                tgraph.push_back(g);
+            }
             gptr.push_back(gptr.back() + L.n);
             E += L.A.nnz;
         }
     }
-    if (E > 2000000000LL || gptr.back() <= 0) {
+    if (E > 2000000000LL || gptr.back() <= 0 || gptr.back() > 200000000) {
         err = "batch graph too large or empty";
         return AMG_ERR_ARG;
     }
     b.G = static_cast<int>(gptr.size()) - 1;
     b.N = gptr.back();
+    b.NT = static_cast<int>(tstart.size());
     b.E = E;
+    tstart.push_back(b.N);
+    gtile.push_back(b.NT);
     Planner pl;
-    batch_layout(b, pl);
+    batch_layout(b, pl, backward);
     cudaError_t e = cudaMalloc(&b.arena, pl.off);
     if (e != cudaSuccess) {
         err = std::string("cudaMalloc batch: ") + cudaGetErrorString(e);
@@ -108,8 +143,11 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
     b.bytes = pl.off;
     pl = Planner{};
     pl.base = b.arena;
-    batch_layout(b, pl);
+    batch_layout(b, pl, backward);
     cudaMemcpyAsync(b.gptr, gptr.data(), sizeof(int) * gptr.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b.tstart, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b.tgraph, tgraph.data(), sizeof(int) * tgraph.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b.gtile, gtile.data(), sizeof(int) * gtile.size(), cudaMemcpyHostToDevice, s);
     int g = 0;
     long long eoff = 0;
     for (int m = 0; m < n_problems; ++m) {
@@ -123,7 +161,8 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
         }
     }
     k_set_int<<<1, 1, 0, s>>>(b.rp + b.N, static_cast<int>(E)); AMG_COUNT();
-    e = cudaGetLastError();
+    e = cudaStreamSynchronize(s);   // host vectors above must outlive the async copies
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("batch build: ") + cudaGetErrorString(e);
         return AMG_ERR_CUDA;
@@ -149,150 +188,191 @@ __global__ void k_feat0(int N, const int *__restrict__ rp, const int *__restrict
     x0[2 * i + 1] = static_cast<double>(deg);
 }
 
-// Layer 1: h = A_hat x0 (2 features, FP64 sums of the raw features), y = h W + b.
-__global__ void __launch_bounds__(kBlock) k_layer1(int N, const int *__restrict__ rp, const int *__restrict__ col,
-                                                   const double *__restrict__ w64, const double *__restrict__ x0,
-                                                   const float *__restrict__ W, const float *__restrict__ bias,
-                                                   float *__restrict__ h1, float *__restrict__ y) {
-    const int warp = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32;
-    const int i = warp;
-    double a0 = 0.0, a1 = 0.0;
-    if (i < N) {
+// mean and M2 (sum of squared deviations) per feature of the tile's y rows
+__device__ __forceinline__ void tile_stats(const float (*sY)[kHidden + 1], int nn, float *tmean, float *tm2) {
+    __shared__ float red[4][kHidden];
+    __shared__ float smean[kHidden];
+    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+    float s = 0.f;
+    for (int k = q; k < nn; k += 4) s += sY[k][f];
+    red[q][f] = s;
+    __syncthreads();
+    if (q == 0) smean[f] = (red[0][f] + red[1][f] + red[2][f] + red[3][f]) / nn;
+    __syncthreads();
+    const float m = smean[f];
+    float v = 0.f;
+    for (int k = q; k < nn; k += 4) {
+        const float d = sY[k][f] - m;
+        v = fmaf(d, d, v);
+    }
+    __syncthreads();
+    red[q][f] = v;
+    __syncthreads();
+    if (q == 0) {
+        tmean[f] = m;
+        tm2[f] = red[0][f] + red[1][f] + red[2][f] + red[3][f];
+    }
+}
+
+// Layer 1: h = A_hat x0 (FP64 sums of the raw features), y = h W + b; tile stats.
+__global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ rp, const int *__restrict__ col,
+                                                        const double *__restrict__ w64, const double *__restrict__ x0,
+                                                        const float *__restrict__ W, const float *__restrict__ bias,
+                                                        const int *__restrict__ tstart, float *__restrict__ h1,
+                                                        float *__restrict__ y, float *__restrict__ tmean,
+                                                        float *__restrict__ tm2) {
+    __shared__ float sY[kTile][kHidden + 1];
+    const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int k = warp; k < nn; k += kBlock / 32) {
+        const int i = a + k;
+        double a0 = 0.0, a1 = 0.0;
         for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
             const double wv = w64[p];
             const int j = col[p];
             a0 += wv * x0[2 * j];
             a1 += wv * x0[2 * j + 1];
         }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane == 0) {
+            h1[2 * i] = static_cast<float>(a0);
+            h1[2 * i + 1] = static_cast<float>(a1);
+        }
+        const int f = 2 * lane;
+        const float y0 = static_cast<float>(a0 * W[f] + a1 * W[kHidden + f] + bias[f]);
+        const float y1 = static_cast<float>(a0 * W[f + 1] + a1 * W[kHidden + f + 1] + bias[f + 1]);
+        reinterpret_cast<float2 *>(y)[static_cast<size_t>(i) * 32 + lane] = make_float2(y0, y1);
+        sY[k][f] = y0;
+        sY[k][f + 1] = y1;
     }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    if (i >= N) return;
-    if (lane == 0) {
-        h1[2 * i] = static_cast<float>(a0);
-        h1[2 * i + 1] = static_cast<float>(a1);
-    }
-    const int k = 2 * lane;
-    const double y0 = a0 * W[k] + a1 * W[kHidden + k] + bias[k];
-    const double y1 = a0 * W[k + 1] + a1 * W[kHidden + k + 1] + bias[k + 1];
-    reinterpret_cast<float2 *>(y)[static_cast<size_t>(i) * 32 + lane] =
-        make_float2(static_cast<float>(y0), static_cast<float>(y1));
+    __syncthreads();
+    tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
 }
 
-// Layers 2..4: h = A_hat x (64 features, lanes own feature pairs), y = h W + b.
-__global__ void __launch_bounds__(kBlock) k_agg_lin(int N, const int *__restrict__ rp, const int *__restrict__ col,
-                                                    const float *__restrict__ w, const float *__restrict__ x,
-                                                    const float *__restrict__ W, const float *__restrict__ bias,
-                                                    float *__restrict__ hout, float *__restrict__ y) {
+// Layers 2..4: h = A_hat x (64 features), y = h W + b; tile stats.
+__global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__ rp, const int *__restrict__ col,
+                                                         const float *__restrict__ w, const float *__restrict__ x,
+                                                         const float *__restrict__ W, const float *__restrict__ bias,
+                                                         const int *__restrict__ tstart, float *__restrict__ hout,
+                                                         float *__restrict__ y, float *__restrict__ tmean,
+                                                         float *__restrict__ tm2) {
     __shared__ float2 sW[kHidden * 32];   // W[m][2 lane .. 2 lane + 1]
-    for (int t = threadIdx.x; t < kHidden * 32; t += kBlock)
-        sW[t] = reinterpret_cast<const float2 *>(W)[t];
+    __shared__ float sY[kTile][kHidden + 1];
+    for (int t2 = threadIdx.x; t2 < kHidden * 32; t2 += kBlock) sW[t2] = reinterpret_cast<const float2 *>(W)[t2];
     __syncthreads();
-    const int i = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32;
-    if (i >= N) return;
+    const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const float2 *x2 = reinterpret_cast<const float2 *>(x);
-    float hx = 0.f, hy = 0.f;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const float wv = w[p];
-        const float2 v = x2[static_cast<size_t>(col[p]) * 32 + lane];
-        hx = fmaf(wv, v.x, hx);
-        hy = fmaf(wv, v.y, hy);
-    }
-    reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = make_float2(hx, hy);
-    float y0 = bias[2 * lane], y1 = bias[2 * lane + 1];
+    const float2 b2 = reinterpret_cast<const float2 *>(bias)[lane];
+    for (int k = warp; k < nn; k += kBlock / 32) {
+        const int i = a + k;
+        float hx = 0.f, hy = 0.f;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            const float wv = w[p];
+            const float2 v = x2[static_cast<size_t>(col[p]) * 32 + lane];
+            hx = fmaf(wv, v.x, hx);
+            hy = fmaf(wv, v.y, hy);
+        }
+        reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = make_float2(hx, hy);
+        float y0 = b2.x, y1 = b2.y;
 #pragma unroll 8
-    for (int m = 0; m < kHidden; ++m) {
-        const float hm = __shfl_sync(0xffffffffu, (m & 1) ? hy : hx, m >> 1);
-        const float2 wm = sW[m * 32 + lane];
-        y0 = fmaf(hm, wm.x, y0);
-        y1 = fmaf(hm, wm.y, y1);
+        for (int m = 0; m < kHidden; ++m) {
+            const float hm = __shfl_sync(0xffffffffu, (m & 1) ? hy : hx, m >> 1);
+            const float2 wm = sW[m * 32 + lane];
+            y0 = fmaf(hm, wm.x, y0);
+            y1 = fmaf(hm, wm.y, y1);
+        }
+        reinterpret_cast<float2 *>(y)[static_cast<size_t>(i) * 32 + lane] = make_float2(y0, y1);
+        sY[k][2 * lane] = y0;
+        sY[k][2 * lane + 1] = y1;
     }
-    reinterpret_cast<float2 *>(y)[static_cast<size_t>(i) * 32 + lane] = make_float2(y0, y1);
+    __syncthreads();
+    tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
 }
 
-// Per-graph instance-norm statistics (biased variance, two passes, FP64 sums).
-__global__ void __launch_bounds__(kBlock) k_graph_stats(const int *__restrict__ gptr, const float *__restrict__ y,
-                                                        float *__restrict__ mu, float *__restrict__ rstd) {
-    __shared__ double red[kBlock];
-    __shared__ double smean[kHidden];
-    const int g = blockIdx.x;
-    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;   // 4 node lanes
-    const int a = gptr[g], e = gptr[g + 1];
-    const int n = e - a;
-    double s = 0.0;
-    for (int i = a + q; i < e; i += kBlock / kHidden) s += y[static_cast<size_t>(i) * kHidden + f];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    if (q == 0) {
-        double t = 0.0;
-        for (int k = 0; k < kBlock / kHidden; ++k) t += red[k * kHidden + f];
-        smean[f] = t / n;
+// Per-graph instance-norm statistics: Chan combination of the tile partials
+// in tile order (biased variance, FP64).
+__global__ void k_stats_combine(const int *__restrict__ gtile, const int *__restrict__ tstart,
+                                const float *__restrict__ tmean, const float *__restrict__ tm2,
+                                float *__restrict__ mu, float *__restrict__ rstd) {
+    const int g = blockIdx.x, f = threadIdx.x;
+    double n = 0.0, mean = 0.0, m2 = 0.0;
+    for (int t = gtile[g]; t < gtile[g + 1]; ++t) {
+        const double nb = tstart[t + 1] - tstart[t];
+        const double mb = tmean[static_cast<size_t>(t) * kHidden + f];
+        const double delta = mb - mean;
+        const double nn = n + nb;
+        mean += delta * nb / nn;
+        m2 += tm2[static_cast<size_t>(t) * kHidden + f] + delta * delta * n * nb / nn;
+        n = nn;
     }
-    __syncthreads();
-    const double m = smean[f];
-    double v = 0.0;
-    for (int i = a + q; i < e; i += kBlock / kHidden) {
-        const double d = y[static_cast<size_t>(i) * kHidden + f] - m;
-        v += d * d;
-    }
-    __syncthreads();
-    red[threadIdx.x] = v;
-    __syncthreads();
-    if (q == 0) {
-        double t = 0.0;
-        for (int k = 0; k < kBlock / kHidden; ++k) t += red[k * kHidden + f];
-        mu[g * kHidden + f] = static_cast<float>(m);
-        rstd[g * kHidden + f] = static_cast<float>(1.0 / sqrt(t / n + static_cast<double>(kEps)));
-    }
+    mu[g * kHidden + f] = static_cast<float>(mean);
+    rstd[g * kHidden + f] = static_cast<float>(1.0 / sqrt(m2 / n + static_cast<double>(kEps)));
 }
 
-// x = ReLU((y - mu) rstd gamma + beta)
-__global__ void k_norm_relu(int N, const int *__restrict__ gid, const float *__restrict__ y,
-                            const float *__restrict__ mu, const float *__restrict__ rstd,
-                            const float *__restrict__ gamma, const float *__restrict__ beta, float *__restrict__ x) {
-    const long long t = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
-    if (t >= static_cast<long long>(N) * kHidden) return;
-    const int i = static_cast<int>(t / kHidden), f = static_cast<int>(t % kHidden);
-    const int g = gid[i];
-    const float z = (y[t] - mu[g * kHidden + f]) * rstd[g * kHidden + f] * gamma[f] + beta[f];
-    x[t] = fmaxf(z, 0.f);
-}
-
-// Per-graph mean and max (first index of the max kept) of x.
-__global__ void __launch_bounds__(kBlock) k_pool(const int *__restrict__ gptr, const float *__restrict__ x,
-                                                 float *__restrict__ pooled, int *__restrict__ argmax, int layer) {
-    __shared__ double rs[kBlock];
-    __shared__ float rm[kBlock];
-    __shared__ int ri[kBlock];
-    const int g = blockIdx.x;
+// x = ReLU((y - mu) rstd gamma + beta); tile sum / max / argmax of x.
+__global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__restrict__ tstart,
+                                                                const int *__restrict__ tgraph,
+                                                                const float *__restrict__ y,
+                                                                const float *__restrict__ mu,
+                                                                const float *__restrict__ rstd,
+                                                                const float *__restrict__ gamma,
+                                                                const float *__restrict__ beta, float *__restrict__ x,
+                                                                double *__restrict__ tsum, float *__restrict__ tmax,
+                                                                int *__restrict__ targ) {
+    __shared__ double rs[4][kHidden];
+    __shared__ float rm[4][kHidden];
+    __shared__ int ri[4][kHidden];
+    const int t = blockIdx.x, a = tstart[t], e = tstart[t + 1], g = tgraph[t];
     const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
-    const int a = gptr[g], e = gptr[g + 1];
+    const float m = mu[g * kHidden + f], r = rstd[g * kHidden + f], ga = gamma[f], be = beta[f];
     double s = 0.0;
     float mx = -INFINITY;
     int mi = a;
-    for (int i = a + q; i < e; i += kBlock / kHidden) {
-        const float v = x[static_cast<size_t>(i) * kHidden + f];
+    for (int i = a + q; i < e; i += 4) {
+        const size_t o = static_cast<size_t>(i) * kHidden + f;
+        const float v = fmaxf((y[o] - m) * r * ga + be, 0.f);
+        x[o] = v;
         s += v;
         if (v > mx) { mx = v; mi = i; }
     }
-    rs[threadIdx.x] = s;
-    rm[threadIdx.x] = mx;
-    ri[threadIdx.x] = mi;
+    rs[q][f] = s;
+    rm[q][f] = mx;
+    ri[q][f] = mi;
     __syncthreads();
     if (q == 0) {
-        double t = 0.0;
+        double ts = 0.0;
         float bm = -INFINITY;
         int bi = a;
-        for (int k = 0; k < kBlock / kHidden; ++k) {
-            const int idx = k * kHidden + f;
-            t += rs[idx];
-            if (rm[idx] > bm || (rm[idx] == bm && ri[idx] < bi)) { bm = rm[idx]; bi = ri[idx]; }
+        for (int k = 0; k < 4; ++k) {
+            ts += rs[k][f];
+            if (rm[k][f] > bm || (rm[k][f] == bm && ri[k][f] < bi)) { bm = rm[k][f]; bi = ri[k][f]; }
         }
-        float *P = pooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
-        P[f] = static_cast<float>(t / (e - a));
-        P[kHidden + f] = bm;
-        argmax[(static_cast<size_t>(g) * kLayers + layer) * kHidden + f] = bi;
+        tsum[static_cast<size_t>(t) * kHidden + f] = ts;
+        tmax[static_cast<size_t>(t) * kHidden + f] = bm;
+        targ[static_cast<size_t>(t) * kHidden + f] = bi;
     }
+}
+
+// Per-graph mean and max (first index of the max kept) from the tile partials.
+__global__ void k_pool_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
+                               const double *__restrict__ tsum, const float *__restrict__ tmax,
+                               const int *__restrict__ targ, float *__restrict__ pooled, int *__restrict__ argmax,
+                               int layer) {
+    const int g = blockIdx.x, f = threadIdx.x;
+    double s = 0.0;
+    float bm = -INFINITY;
+    int bi = gptr[g];
+    for (int t = gtile[g]; t < gtile[g + 1]; ++t) {
+        const size_t o = static_cast<size_t>(t) * kHidden + f;
+        s += tsum[o];
+        if (tmax[o] > bm) { bm = tmax[o]; bi = targ[o]; }
+    }
+    float *P = pooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
+    P[f] = static_cast<float>(s / (gptr[g + 1] - gptr[g]));
+    P[kHidden + f] = bm;
+    argmax[(static_cast<size_t>(g) * kLayers + layer) * kHidden + f] = bi;
 }
 
 __device__ __forceinline__ float block128_sum(float v, float *red) {
@@ -303,6 +383,12 @@ __device__ __forceinline__ float block128_sum(float v, float *red) {
     __syncthreads();
     return t;
 }
+
+// Head scratch layout per graph: z[128] | zh[128] | sig[128] | a1[128] | a2[64] | mean | rstd
+constexpr int kSz = 0, kSzh = kEmb, kSsg = 2 * kEmb, kSa1 = 3 * kEmb, kSa2 = 3 * kEmb + 128,
+              kSmean = 3 * kEmb + 192, kSrs = 3 * kEmb + 193;
+// Head gradient layout per graph: dz1[128] | dz2[64] | dzh[128] | dz[128]
+constexpr int kGdz1 = 0, kGdz2 = 128, kGdzh = 192, kGdz = 192 + kEmb;
 
 // Readout + head for one graph (128 threads).
 __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, const float *__restrict__ th,
@@ -326,12 +412,12 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     const float rs = rsqrtf(var + kEps);
     const float zh = d * rs * th[kPLd.lnG + t] + th[kPLd.lnB + t];
     const float sg = 1.f / (1.f + expf(-zh));
-    S[t] = z;
-    S[kEmb + t] = zh;
-    S[2 * kEmb + t] = sg;
+    S[kSz + t] = z;
+    S[kSzh + t] = zh;
+    S[kSsg + t] = sg;
     if (t == 0) {
-        S[3 * kEmb + 128 + 64] = mean;
-        S[3 * kEmb + 128 + 64 + 1] = rs;
+        S[kSmean] = mean;
+        S[kSrs] = rs;
     }
     ss[t] = sg;
     __syncthreads();
@@ -339,14 +425,14 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     for (int m = 0; m < kEmb; ++m) a1 = fmaf(ss[m], th[kPLd.h1W + m * 128 + t], a1);
     a1 = fmaxf(a1, 0.f);
     sa1[t] = a1;
-    S[3 * kEmb + t] = a1;
+    S[kSa1 + t] = a1;
     __syncthreads();
     if (t < 64) {
         float a2 = th[kPLd.h2B + t];
         for (int m = 0; m < 128; ++m) a2 = fmaf(sa1[m], th[kPLd.h2W + m * 64 + t], a2);
         a2 = fmaxf(a2, 0.f);
         sa2[t] = a2;
-        S[3 * kEmb + 128 + t] = a2;
+        S[kSa2 + t] = a2;
     }
     __syncthreads();
     if (t < 5) {
@@ -357,24 +443,363 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
 }
 
 void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
-    const int N = b.N, G = b.G;
+    const int N = b.N, G = b.G, NT = b.NT;
     k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
-    const int warp_grid = grid_for(static_cast<long long>(N) * 32);
-    const int elem_grid = grid_for(static_cast<long long>(N) * kHidden);
     for (int l = 0; l < kLayers; ++l) {
         if (l == 0) {
-            k_layer1<<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0, th + kPL.convW[0], th + kPL.convB[0],
-                                                  b.h1, b.y[0]); AMG_COUNT();
+            k_layer1_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + kPL.convW[0], th + kPL.convB[0],
+                                                b.tstart, b.h1, b.y[0], b.tmean, b.tm2); AMG_COUNT();
         } else {
-            k_agg_lin<<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
-                                                   th + kPL.convB[l], b.h[l], b.y[l]); AMG_COUNT();
+            k_agg_lin_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
+                                                 th + kPL.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
+                                                 b.tm2); AMG_COUNT();
         }
-        k_graph_stats<<<G, kBlock, 0, s>>>(b.gptr, b.y[l], b.mu[l], b.rstd[l]); AMG_COUNT();
-        k_norm_relu<<<elem_grid, kBlock, 0, s>>>(N, b.gid, b.y[l], b.mu[l], b.rstd[l], th + kPL.inG[l],
-                                                 th + kPL.inB[l], b.x[l]); AMG_COUNT();
-        k_pool<<<G, kBlock, 0, s>>>(b.gptr, b.x[l], b.pooled, b.argmax, l); AMG_COUNT();
+        k_stats_combine<<<G, kHidden, 0, s>>>(b.gtile, b.tstart, b.tmean, b.tm2, b.mu[l], b.rstd[l]); AMG_COUNT();
+        k_norm_relu_pool_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
+                                                    th + kPL.inG[l], th + kPL.inB[l], b.x[l], b.tsum, b.tmax,
+                                                    b.targ); AMG_COUNT();
+        k_pool_combine<<<G, kHidden, 0, s>>>(b.gtile, b.gptr, b.tsum, b.tmax, b.targ, b.pooled, b.argmax, l); AMG_COUNT();
     }
     k_head<<<G, 128, 0, s>>>(b.pooled, th, b.head, b.c); AMG_COUNT();
+}
+
+// ---------------------------------------------------------------------------
+// backward kernels
+// ---------------------------------------------------------------------------
+// Head backward for one graph: dc -> dz2, dz1, dzh, dz (readout outputs) and
+// the pooled-feature gradient dpooled.
+__global__ void __launch_bounds__(128) k_head_bwd(const float *__restrict__ scratch, const float *__restrict__ th,
+                                                  const float *__restrict__ dc, float *__restrict__ dhead,
+                                                  float *__restrict__ dpooled) {
+    __shared__ float sdc[5], sdz2[64], sdz1[128], sdz[kEmb];
+    __shared__ float red[4];
+    const int g = blockIdx.x, t = threadIdx.x;
+    const float *S = scratch + static_cast<size_t>(g) * kHeadScratch;
+    float *D = dhead + static_cast<size_t>(g) * kHeadGrad;
+    if (t < 5) sdc[t] = dc[g * 5 + t];
+    __syncthreads();
+    if (t < 64) {
+        float da2 = 0.f;
+        for (int k = 0; k < 5; ++k) da2 = fmaf(sdc[k], th[kPLd.h3W + t * 5 + k], da2);
+        const float dz2 = S[kSa2 + t] > 0.f ? da2 : 0.f;
+        sdz2[t] = dz2;
+        D[kGdz2 + t] = dz2;
+    }
+    __syncthreads();
+    float da1 = 0.f;
+    for (int k = 0; k < 64; ++k) da1 = fmaf(sdz2[k], th[kPLd.h2W + t * 64 + k], da1);
+    const float dz1 = S[kSa1 + t] > 0.f ? da1 : 0.f;
+    sdz1[t] = dz1;
+    D[kGdz1 + t] = dz1;
+    __syncthreads();
+    float ds = 0.f;
+    for (int k = 0; k < 128; ++k) ds = fmaf(sdz1[k], th[kPLd.h1W + t * 128 + k], ds);
+    const float sg = S[kSsg + t];
+    const float dzh = ds * sg * (1.f - sg);
+    D[kGdzh + t] = dzh;
+    // layer norm backward
+    const float rs = S[kSrs], mean = S[kSmean];
+    const float zn = (S[kSz + t] - mean) * rs;
+    const float dzn = dzh * th[kPLd.lnG + t];
+    const float m1 = block128_sum(dzn, red) / kEmb;
+    const float m2 = block128_sum(dzn * zn, red) / kEmb;
+    const float dz = rs * (dzn - m1 - zn * m2);
+    sdz[t] = dz;
+    D[kGdz + t] = dz;
+    __syncthreads();
+    // readout linears: dpooled_l[m] = sum_k dz[32 l + k] W_l[m][k]
+    for (int j = t; j < kLayers * 2 * kHidden; j += 128) {
+        const int l = j / (2 * kHidden), m = j % (2 * kHidden);
+        const float *W = th + kPLd.roW[l] + m * kRo;
+        float acc = 0.f;
+        for (int k = 0; k < kRo; ++k) acc = fmaf(sdz[l * kRo + k], W[k], acc);
+        dpooled[static_cast<size_t>(g) * kLayers * 2 * kHidden + j] = acc;
+    }
+}
+
+// Gradients of the readout / layer-norm / head parameters: one thread per
+// parameter, sum over graphs in graph order.
+__global__ void k_head_param_grad(int G, const float *__restrict__ pooled, const float *__restrict__ scratch,
+                                  const float *__restrict__ dhead, const float *__restrict__ dc,
+                                  float *__restrict__ grad) {
+    const int p = kPLd.roW[0] + blockIdx.x * kBlock + threadIdx.x;
+    if (p >= kNumParams) return;
+    double acc = 0.0;
+    int l = -1;
+    for (int k = 0; k < kLayers; ++k)
+        if (p >= kPLd.roW[k] && p < kPLd.roB[k] + kRo) l = k;
+    for (int g = 0; g < G; ++g) {
+        const float *S = scratch + static_cast<size_t>(g) * kHeadScratch;
+        const float *D = dhead + static_cast<size_t>(g) * kHeadGrad;
+        double v;
+        if (l >= 0) {
+            if (p < kPLd.roB[l]) {
+                const int o = p - kPLd.roW[l], m = o / kRo, k = o % kRo;
+                v = static_cast<double>(pooled[(static_cast<size_t>(g) * kLayers + l) * 2 * kHidden + m]) *
+                    D[kGdz + l * kRo + k];
+            } else {
+                v = D[kGdz + l * kRo + (p - kPLd.roB[l])];
+            }
+        } else if (p < kPLd.lnB) {
+            const int k = p - kPLd.lnG;
+            v = static_cast<double>(D[kGdzh + k]) * ((S[kSz + k] - S[kSmean]) * S[kSrs]);
+        } else if (p < kPLd.h1W) {
+            v = D[kGdzh + (p - kPLd.lnB)];
+        } else if (p < kPLd.h1B) {
+            const int o = p - kPLd.h1W, m = o / 128, k = o % 128;
+            v = static_cast<double>(S[kSsg + m]) * D[kGdz1 + k];
+        } else if (p < kPLd.h2W) {
+            v = D[kGdz1 + (p - kPLd.h1B)];
+        } else if (p < kPLd.h2B) {
+            const int o = p - kPLd.h2W, m = o / 64, k = o % 64;
+            v = static_cast<double>(S[kSa1 + m]) * D[kGdz2 + k];
+        } else if (p < kPLd.h3W) {
+            v = D[kGdz2 + (p - kPLd.h2B)];
+        } else if (p < kPLd.h3B) {
+            const int o = p - kPLd.h3W, m = o / 5, k = o % 5;
+            v = static_cast<double>(S[kSa2 + m]) * dc[g * 5 + k];
+        } else {
+            v = dc[g * 5 + (p - kPLd.h3B)];
+        }
+        acc += v;
+    }
+    grad[p] = static_cast<float>(acc);
+}
+
+// Layer backward, part 1 (per tile): dX = dx_next + pooling routes; the
+// ReLU mask gives d(yn); tile sums S1 = sum d(yn), S2 = sum d(yn) * yhat.
+__global__ void __launch_bounds__(kBlock) k_bwd_relu_tile(const int *__restrict__ tstart,
+                                                          const int *__restrict__ tgraph, const int *__restrict__ gptr,
+                                                          const float *__restrict__ x, const float *__restrict__ y,
+                                                          const float *__restrict__ mu, const float *__restrict__ rstd,
+                                                          const float *__restrict__ dx, const float *__restrict__ dpooled,
+                                                          const int *__restrict__ argmax, int layer,
+                                                          float *__restrict__ dyn, double *__restrict__ tsum,
+                                                          double *__restrict__ tsum2) {
+    __shared__ double r1[4][kHidden], r2[4][kHidden];
+    const int t = blockIdx.x, a = tstart[t], e = tstart[t + 1], g = tgraph[t];
+    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+    const float *dp = dpooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
+    const float dmean = dp[f] / (gptr[g + 1] - gptr[g]), dmax = dp[kHidden + f];
+    const int am = argmax[(static_cast<size_t>(g) * kLayers + layer) * kHidden + f];
+    const float m = mu[g * kHidden + f], r = rstd[g * kHidden + f];
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = a + q; i < e; i += 4) {
+        const size_t o = static_cast<size_t>(i) * kHidden + f;
+        float dX = dmean + (i == am ? dmax : 0.f);
+        if (dx) dX += dx[o];
+        const float d = x[o] > 0.f ? dX : 0.f;
+        dyn[o] = d;
+        s1 += d;
+        s2 += static_cast<double>(d) * ((y[o] - m) * r);
+    }
+    r1[q][f] = s1;
+    r2[q][f] = s2;
+    __syncthreads();
+    if (q == 0) {
+        tsum[static_cast<size_t>(t) * kHidden + f] = r1[0][f] + r1[1][f] + r1[2][f] + r1[3][f];
+        tsum2[static_cast<size_t>(t) * kHidden + f] = r2[0][f] + r2[1][f] + r2[2][f] + r2[3][f];
+    }
+}
+
+__global__ void k_bwd_combine(const int *__restrict__ gtile, const double *__restrict__ tsum,
+                              const double *__restrict__ tsum2, double *__restrict__ gS1, double *__restrict__ gS2) {
+    const int g = blockIdx.x, f = threadIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    for (int t = gtile[g]; t < gtile[g + 1]; ++t) {
+        s1 += tsum[static_cast<size_t>(t) * kHidden + f];
+        s2 += tsum2[static_cast<size_t>(t) * kHidden + f];
+    }
+    gS1[g * kHidden + f] = s1;
+    gS2[g * kHidden + f] = s2;
+}
+
+// Layer backward, part 2 (per tile): instance-norm backward
+//   dy = rstd (gamma d(yn) - gamma S1/n - yhat gamma S2/n),
+// then dh = dy W^T (layers 2..4) and the tile's partial weight and bias
+// gradients sum_i h_i^T dy_i, sum_i dy_i.
+template <int FIN>
+__global__ void __launch_bounds__(kBlock) k_bwd_in_lin_tile(const int *__restrict__ tstart,
+                                                            const int *__restrict__ tgraph,
+                                                            const int *__restrict__ gptr, const float *__restrict__ y,
+                                                            const float *__restrict__ mu,
+                                                            const float *__restrict__ rstd,
+                                                            const float *__restrict__ gamma,
+                                                            const double *__restrict__ gS1,
+                                                            const double *__restrict__ gS2,
+                                                            const float *__restrict__ W, const float *__restrict__ hin,
+                                                            const float *__restrict__ dyn, float *__restrict__ dh,
+                                                            float *__restrict__ dWt) {
+    __shared__ float2 sWT[FIN == kHidden ? kHidden * 32 : 1];   // (W[2 lane][k], W[2 lane + 1][k])
+    __shared__ float sH[kTile][FIN + 1];
+    __shared__ float sD[kTile][kHidden + 1];
+    if (FIN == kHidden) {
+        for (int e = threadIdx.x; e < kHidden * 32; e += kBlock) {
+            const int k = e / 32, ln = e % 32;
+            sWT[e] = make_float2(W[(2 * ln) * kHidden + k], W[(2 * ln + 1) * kHidden + k]);
+        }
+    }
+    const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a, g = tgraph[t];
+    const float inv_n = 1.f / (gptr[g + 1] - gptr[g]);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int f0 = 2 * lane, f1 = 2 * lane + 1;
+    const float ga0 = gamma[f0], ga1 = gamma[f1];
+    const float m0 = mu[g * kHidden + f0], m1 = mu[g * kHidden + f1];
+    const float r0 = rstd[g * kHidden + f0], r1 = rstd[g * kHidden + f1];
+    const float c10 = ga0 * static_cast<float>(gS1[g * kHidden + f0]) * inv_n;
+    const float c11 = ga1 * static_cast<float>(gS1[g * kHidden + f1]) * inv_n;
+    const float c20 = ga0 * static_cast<float>(gS2[g * kHidden + f0]) * inv_n;
+    const float c21 = ga1 * static_cast<float>(gS2[g * kHidden + f1]) * inv_n;
+    __syncthreads();
+    for (int k = warp; k < nn; k += kBlock / 32) {
+        const int i = a + k;
+        const float2 d2 = reinterpret_cast<const float2 *>(dyn)[static_cast<size_t>(i) * 32 + lane];
+        const float2 y2 = reinterpret_cast<const float2 *>(y)[static_cast<size_t>(i) * 32 + lane];
+        const float yh0 = (y2.x - m0) * r0, yh1 = (y2.y - m1) * r1;
+        const float dy0 = r0 * (ga0 * d2.x - c10 - yh0 * c20);
+        const float dy1 = r1 * (ga1 * d2.y - c11 - yh1 * c21);
+        sD[k][f0] = dy0;
+        sD[k][f1] = dy1;
+        if (FIN == kHidden) {
+            const float2 h2 = reinterpret_cast<const float2 *>(hin)[static_cast<size_t>(i) * 32 + lane];
+            sH[k][f0] = h2.x;
+            sH[k][f1] = h2.y;
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll 8
+            for (int kk = 0; kk < kHidden; ++kk) {
+                const float dk = __shfl_sync(0xffffffffu, (kk & 1) ? dy1 : dy0, kk >> 1);
+                const float2 wk = sWT[kk * 32 + lane];
+                a0 = fmaf(dk, wk.x, a0);
+                a1 = fmaf(dk, wk.y, a1);
+            }
+            reinterpret_cast<float2 *>(dh)[static_cast<size_t>(i) * 32 + lane] = make_float2(a0, a1);
+        } else {
+            if (lane < FIN) sH[k][lane] = hin[static_cast<size_t>(i) * FIN + lane];
+        }
+    }
+    __syncthreads();
+    float *out = dWt + static_cast<size_t>(t) * (kHidden * kHidden + kHidden);
+    for (int e = threadIdx.x; e < FIN * kHidden; e += kBlock) {
+        const int m = e / kHidden, k = e % kHidden;
+        float acc = 0.f;
+        for (int j = 0; j < nn; ++j) acc = fmaf(sH[j][m], sD[j][k], acc);
+        out[e] = acc;
+    }
+    if (threadIdx.x < kHidden) {
+        float acc = 0.f;
+        for (int j = 0; j < nn; ++j) acc += sD[j][threadIdx.x];
+        out[kHidden * kHidden + threadIdx.x] = acc;
+    }
+}
+
+// dx = A_hat dh (A_hat symmetric), 64 features, warp per node.
+__global__ void __launch_bounds__(kBlock) k_agg_plain(int N, const int *__restrict__ rp, const int *__restrict__ col,
+                                                      const float *__restrict__ w, const float *__restrict__ v,
+                                                      float *__restrict__ out) {
+    const int i = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32;
+    if (i >= N) return;
+    const float2 *v2 = reinterpret_cast<const float2 *>(v);
+    float ax = 0.f, ay = 0.f;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const float wv = w[p];
+        const float2 u = v2[static_cast<size_t>(col[p]) * 32 + lane];
+        ax = fmaf(wv, u.x, ax);
+        ay = fmaf(wv, u.y, ay);
+    }
+    reinterpret_cast<float2 *>(out)[static_cast<size_t>(i) * 32 + lane] = make_float2(ax, ay);
+}
+
+// Conv weight/bias gradient (sum of tile partials, tile order) and the
+// instance-norm affine gradients (sum over graphs).
+__global__ void k_layer_param_grad(int NT, int G, int fin, const float *__restrict__ dWt,
+                                   const double *__restrict__ gS1, const double *__restrict__ gS2,
+                                   float *__restrict__ gW, float *__restrict__ gB, float *__restrict__ gG,
+                                   float *__restrict__ gBeta) {
+    const int e = blockIdx.x * kBlock + threadIdx.x;
+    const int nW = fin * kHidden;
+    if (e < nW + kHidden) {
+        const int src = (e < nW) ? e : kHidden * kHidden + (e - nW);
+        double acc = 0.0;
+        for (int t = 0; t < NT; ++t) acc += dWt[static_cast<size_t>(t) * (kHidden * kHidden + kHidden) + src];
+        if (e < nW) gW[e] = static_cast<float>(acc);
+        else gB[e - nW] = static_cast<float>(acc);
+    } else if (e < nW + 2 * kHidden) {
+        const int f = e - nW - kHidden;
+        double s1 = 0.0, s2 = 0.0;
+        for (int g = 0; g < G; ++g) {
+            s1 += gS1[g * kHidden + f];
+            s2 += gS2[g * kHidden + f];
+        }
+        gG[f] = static_cast<float>(s2);
+        gBeta[f] = static_cast<float>(s1);
+    }
+}
+
+void gcin_backward(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
+    const int N = b.N, G = b.G, NT = b.NT;
+    k_head_bwd<<<G, 128, 0, s>>>(b.head, th, b.dc, b.dhead, b.dpooled); AMG_COUNT();
+    const int nhead = kNumParams - kPL.roW[0];
+    k_head_param_grad<<<grid_for(nhead), kBlock, 0, s>>>(G, b.pooled, b.head, b.dhead, b.dc, grad); AMG_COUNT();
+    const int warp_grid = grid_for(static_cast<long long>(N) * 32);
+    for (int l = kLayers - 1; l >= 0; --l) {
+        k_bwd_relu_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.x[l], b.y[l], b.mu[l], b.rstd[l],
+                                              l == kLayers - 1 ? nullptr : b.dx, b.dpooled, b.argmax, l, b.dy,
+                                              b.tsum, b.tsum2); AMG_COUNT();
+        k_bwd_combine<<<G, kHidden, 0, s>>>(b.gtile, b.tsum, b.tsum2, b.gS1, b.gS2); AMG_COUNT();
+        if (l > 0) {
+            k_bwd_in_lin_tile<kHidden><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
+                                                             th + kPL.inG[l], b.gS1, b.gS2, th + kPL.convW[l],
+                                                             b.h[l], b.dy, b.dh, b.dWt); AMG_COUNT();
+            k_agg_plain<<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w, b.dh, b.dx); AMG_COUNT();
+        } else {
+            k_bwd_in_lin_tile<2><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
+                                                       th + kPL.inG[l], b.gS1, b.gS2, th + kPL.convW[l], b.h1, b.dy,
+                                                       nullptr, b.dWt); AMG_COUNT();
+        }
+        const int fin = (l == 0) ? 2 : kHidden;
+        k_layer_param_grad<<<grid_for(fin * kHidden + 2 * kHidden), kBlock, 0, s>>>(
+            NT, G, fin, b.dWt, b.gS1, b.gS2, grad + kPL.convW[l], grad + kPL.convB[l], grad + kPL.inG[l],
+            grad + kPL.inB[l]); AMG_COUNT();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// optimiser: global-norm clipping + Adam (Table train_hyper)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_sq_partial_f(int n, const float *__restrict__ v, double *__restrict__ part) {
+    __shared__ double red[kBlock / 32];
+    double s = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s += static_cast<double>(v[i]) * v[i];
+    s = warp_sum(s);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) t += red[k];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_norm_from_partials(int np, const double *__restrict__ part, double *__restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += part[i];
+    *out = sqrt(s);
+}
+
+// clip to max_norm (scale = min(1, max_norm / (||g|| + 1e-6))), then Adam
+__global__ void k_adam(int n, float *__restrict__ theta, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, const double *__restrict__ gnorm, double max_norm, double lr,
+                       double b1, double b2, double eps, double bc1, double bc2) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const double scale = fmin(1.0, max_norm / (*gnorm + 1e-6));
+    const double gi = g[i] * scale;
+    const double mi = b1 * m[i] + (1.0 - b1) * gi;
+    const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+    m[i] = static_cast<float>(mi);
+    v[i] = static_cast<float>(vi);
+    theta[i] = static_cast<float>(theta[i] - lr * (mi / bc1) / (sqrt(vi / bc2) + eps));
 }
 
 void gcin_engine_free(GcinEngine *e) {
@@ -387,6 +812,31 @@ void gcin_engine_free(GcinEngine *e) {
 }  // namespace amg
 
 using namespace amg;
+
+struct gcin_trainer {
+    int device = 0;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    double *part = nullptr;          // norm partials + the norm
+    long long step = 0;
+    GcinBatch batch;
+    std::vector<const amg_ctx *> key;
+    std::vector<long long> versions;
+    bool have_forward = false;
+};
+
+static int tr_fail(gcin_trainer *t, int rc, const std::string &msg) {
+    if (t) t->err = msg;
+    return rc;
+}
+
+static int tr_cuda(gcin_trainer *t, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return AMG_OK;
+    return tr_fail(t, AMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kNormBlocks = 64;
 
 extern "C" {
 
@@ -424,7 +874,7 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
     if (g->batch_version != c->hier_version || g->batch.G != static_cast<int>(c->lev.size())) {
         std::string err;
         amg_ctx *one[1] = {c};
-        int rc = gcin_batch_build(g->batch, 1, one, s, err);
+        int rc = gcin_batch_build(g->batch, 1, one, s, err, false);
         if (rc) return ctx_fail(c, err), rc;
         g->batch_version = c->hier_version;
     }
@@ -442,6 +892,136 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ctx_cuda_check(c, e, "assemble smoother");
     return AMG_OK;
+}
+
+int gcin_trainer_create(gcin_trainer **out, int device, const float *theta0) {
+    if (!out || !theta0) return AMG_ERR_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return AMG_ERR_CUDA;
+    gcin_trainer *t = new gcin_trainer();
+    t->device = device;
+    cudaError_t e = cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking);
+    const size_t P = kNumParams;
+    const size_t fbytes = ((sizeof(float) * 4 * P + 255) / 256) * 256;
+    if (e == cudaSuccess) e = cudaMalloc(&t->theta, fbytes + sizeof(double) * (kNormBlocks + 1));
+    if (e != cudaSuccess) {
+        if (t->stream) cudaStreamDestroy(t->stream);
+        delete t;
+        return AMG_ERR_CUDA;
+    }
+    t->grad = t->theta + P;
+    t->m = t->grad + P;
+    t->v = t->m + P;
+    t->part = reinterpret_cast<double *>(reinterpret_cast<char *>(t->theta) + fbytes);
+    e = cudaMemcpyAsync(t->theta, theta0, sizeof(float) * P, cudaMemcpyHostToDevice, t->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->grad, 0, sizeof(float) * 3 * P, t->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+    if (e != cudaSuccess) {
+        gcin_trainer_destroy(t);
+        return AMG_ERR_CUDA;
+    }
+    *out = t;
+    return AMG_OK;
+}
+
+void gcin_trainer_destroy(gcin_trainer *t) {
+    if (!t) return;
+    cudaSetDevice(t->device);
+    if (t->stream) cudaStreamSynchronize(t->stream);
+    gcin_batch_free(t->batch);
+    if (t->theta) cudaFree(t->theta);
+    if (t->stream) cudaStreamDestroy(t->stream);
+    delete t;
+}
+
+const char *gcin_trainer_last_error(const gcin_trainer *t) { return t ? t->err.c_str() : "trainer is NULL"; }
+
+int gcin_trainer_get_params(const gcin_trainer *tc, float *theta_out) {
+    gcin_trainer *t = const_cast<gcin_trainer *>(tc);
+    if (!t || !theta_out) return AMG_ERR_ARG;
+    int rc = tr_cuda(t, cudaSetDevice(t->device), "cudaSetDevice");
+    if (rc) return rc;
+    rc = tr_cuda(t, cudaMemcpyAsync(theta_out, t->theta, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, t->stream),
+                 "params download");
+    if (rc) return rc;
+    return tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
+}
+
+int gcin_trainer_forward(gcin_trainer *t, int n_problems, amg_ctx *const *problems, double *c_out) {
+    if (!t) return AMG_ERR_ARG;
+    t->err.clear();
+    if (n_problems < 1 || !problems || !c_out) return tr_fail(t, AMG_ERR_ARG, "need at least one problem and c_out");
+    int rc = tr_cuda(t, cudaSetDevice(t->device), "cudaSetDevice");
+    if (rc) return rc;
+    std::vector<const amg_ctx *> key(problems, problems + n_problems);
+    std::vector<long long> versions;
+    for (int m = 0; m < n_problems; ++m) {
+        if (!problems[m]) return tr_fail(t, AMG_ERR_ARG, "NULL problem");
+        versions.push_back(problems[m]->hier_version);
+    }
+    if (key != t->key || versions != t->versions || !t->batch.arena) {
+        std::string err;
+        rc = gcin_batch_build(t->batch, n_problems, problems, t->stream, err, true);
+        if (rc) return tr_fail(t, rc, err);
+        t->key = key;
+        t->versions = versions;
+    }
+    gcin_forward(t->batch, t->theta, t->stream);
+    std::vector<float> cf(static_cast<size_t>(t->batch.G) * 5);
+    rc = tr_cuda(t, cudaGetLastError(), "GCIN forward");
+    if (!rc) rc = tr_cuda(t, cudaMemcpyAsync(cf.data(), t->batch.c, sizeof(float) * cf.size(), cudaMemcpyDeviceToHost,
+                                             t->stream), "coefficients download");
+    if (!rc) rc = tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
+    if (rc) return rc;
+    std::copy(cf.begin(), cf.end(), c_out);
+    t->have_forward = true;
+    return AMG_OK;
+}
+
+int gcin_trainer_backward(gcin_trainer *t, const double *dc, double *dtheta_out) {
+    if (!t) return AMG_ERR_ARG;
+    t->err.clear();
+    if (!dc) return tr_fail(t, AMG_ERR_ARG, "dc is NULL");
+    if (!t->have_forward) return tr_fail(t, AMG_ERR_STATE, "backward without a forward");
+    int rc = tr_cuda(t, cudaSetDevice(t->device), "cudaSetDevice");
+    if (rc) return rc;
+    std::vector<float> df(dc, dc + static_cast<size_t>(t->batch.G) * 5);
+    rc = tr_cuda(t, cudaMemcpyAsync(t->batch.dc, df.data(), sizeof(float) * df.size(), cudaMemcpyHostToDevice,
+                                    t->stream), "dc upload");
+    if (rc) return rc;
+    gcin_backward(t->batch, t->theta, t->grad, t->stream);
+    rc = tr_cuda(t, cudaGetLastError(), "GCIN backward");
+    if (rc) return rc;
+    std::vector<float> g(kNumParams);
+    if (dtheta_out) {
+        rc = tr_cuda(t, cudaMemcpyAsync(g.data(), t->grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost,
+                                        t->stream), "gradient download");
+        if (rc) return rc;
+    }
+    rc = tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
+    if (rc) return rc;
+    if (dtheta_out) std::copy(g.begin(), g.end(), dtheta_out);
+    return AMG_OK;
+}
+
+int gcin_trainer_adam_step(gcin_trainer *t, double lr, double max_norm) {
+    if (!t) return AMG_ERR_ARG;
+    t->err.clear();
+    if (!(lr >= 0.0) || !(max_norm > 0.0)) return tr_fail(t, AMG_ERR_ARG, "bad lr or max_norm");
+    int rc = tr_cuda(t, cudaSetDevice(t->device), "cudaSetDevice");
+    if (rc) return rc;
+    t->step += 1;
+    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    const double bc1 = 1.0 - std::pow(b1, static_cast<double>(t->step));
+    const double bc2 = 1.0 - std::pow(b2, static_cast<double>(t->step));
+    k_sq_partial_f<<<kNormBlocks, kBlock, 0, t->stream>>>(kNumParams, t->grad, t->part); AMG_COUNT();
+    k_norm_from_partials<<<1, 32, 0, t->stream>>>(kNormBlocks, t->part, t->part + kNormBlocks); AMG_COUNT();
+    k_adam<<<grid_for(kNumParams), kBlock, 0, t->stream>>>(kNumParams, t->theta, t->grad, t->m, t->v,
+                                                           t->part + kNormBlocks, max_norm, lr, b1, b2, eps, bc1,
+                                                           bc2); AMG_COUNT();
+    rc = tr_cuda(t, cudaGetLastError(), "adam");
+    if (rc) return rc;
+    return tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
 }
 
 }  // extern "C"

@@ -57,10 +57,16 @@ static_assert(kPL.total == kNumParams, "GCIN layout must have 55,045 parameters 
 
 // Batch graph (Algorithm 1 steps 1-5): disjoint union of level graphs with
 // node ranges gptr[g] .. gptr[g+1] and edges = the concatenated CSR patterns.
+// Nodes are cut into tiles of at most kTile consecutive nodes that never
+// cross a graph boundary; every reduction over a graph is a fixed-order
+// combination of per-tile partials (deterministic, no atomics).
+constexpr int kTile = 64;
+
 struct GcinBatch {
-    int G = 0, N = 0;
+    int G = 0, N = 0, NT = 0;            // graphs, nodes, tiles
     long long E = 0;
     int *rp = nullptr, *col = nullptr, *gptr = nullptr, *gid = nullptr;
+    int *tstart = nullptr, *tgraph = nullptr, *gtile = nullptr;   // tile -> first node / graph; graph -> first tile
     float *w = nullptr;
     double *w64 = nullptr;
     // activations (kept for the backward pass)
@@ -70,22 +76,39 @@ struct GcinBatch {
     float *y[kLayers] = {};              // N x 64     linear outputs
     float *x[kLayers] = {};              // N x 64     ReLU(IN(y))
     float *mu[kLayers] = {}, *rstd[kLayers] = {};   // G x 64
+    float *tmean = nullptr, *tm2 = nullptr;          // NT x 64 tile statistics of y
+    double *tsum = nullptr;                          // NT x 64 tile sums (pooling / backward)
+    double *tsum2 = nullptr;                         // NT x 64 second tile sums (backward)
+    float *tmax = nullptr;                           // NT x 64
+    int *targ = nullptr;                             // NT x 64
     float *pooled = nullptr;             // G x 4 x 128 (mean | max per layer)
     int *argmax = nullptr;               // G x 4 x 64  node index of each max
     float *head = nullptr;               // G x head scratch
     float *c = nullptr;                  // G x 5
+    // backward work
+    float *dc = nullptr;                 // G x 5
+    float *dhead = nullptr;              // G x (dz1 128 | dz2 64 | dzh 128 | dz 128)
+    float *dpooled = nullptr;            // G x 4 x 128
+    float *dx = nullptr, *dh = nullptr, *dy = nullptr;   // N x 64
+    double *gS1 = nullptr, *gS2 = nullptr;               // G x 64 per-graph sums
+    float *dWt = nullptr;                // NT x (64 x 64 + 64) per-tile weight/bias gradient partials
     char *arena = nullptr;
     size_t bytes = 0;
 };
 
 void gcin_batch_free(GcinBatch &b);
-// Build the batch from every level of every context; allocates device memory.
-int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cudaStream_t s, std::string &err);
+// Build the batch from every level of every context; allocates device memory
+// (with the backward buffers when `backward` is set).
+int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cudaStream_t s, std::string &err,
+                     bool backward);
 // Forward pass on the batch with parameters theta (device, 55,045 floats).
 void gcin_forward(GcinBatch &b, const float *theta, cudaStream_t s);
+// Backward from b.dc (device, G x 5) into grad (device, 55,045 floats, overwritten).
+void gcin_backward(GcinBatch &b, const float *theta, float *grad, cudaStream_t s);
 
 // Per-graph head scratch floats (activations kept for backward).
 constexpr int kHeadScratch = kEmb /*z*/ + kEmb /*zhat*/ + kEmb /*sig*/ + 128 /*a1*/ + 64 /*a2*/ + 4 /*mean,rstd*/;
+constexpr int kHeadGrad = 128 /*dz1*/ + 64 /*dz2*/ + kEmb /*dzh*/ + kEmb /*dz*/;
 
 struct GcinEngine {
     float *theta = nullptr;

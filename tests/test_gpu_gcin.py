@@ -1,0 +1,189 @@
+"""GPU parity of the GCIN network (Sec. 3.2, App. A.1) and of the training
+path (Sec. 3.3, Algorithm 1) against the FP64 oracle, through the C ABI.
+
+Bars: coefficients within 1e-5 relative (FP32 network vs FP64 oracle, same
+FP32-rounded parameters); network gradients within 1e-4 relative; V-cycle
+loss and dL/dc within 1e-10 (FP64 V-cycle) and 1e-4 (FP32 V-cycle) of the
+oracle's autograd, and within 1e-4 of central finite differences.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_19251_gb300 as P
+import workloads as W
+from oracle import gcin as OG
+from oracle import setup as OS
+from oracle import solve as O
+from oracle import train as OT
+from tests.gpu_helpers import ctx_from_oracle, ctx_setup
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(theta):
+    return np.asarray(theta, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+MATS = {
+    "c1_64": lambda: W.poisson5(64),
+    "uniform_2k": lambda: W.fv_mesh("uniform", 2000, 3)[0],
+    "graded_6k": lambda: W.fv_mesh("graded", 6000, 4)[0],
+    "band_8k": lambda: W.fv_mesh("band", 8000, 5, max_aspect=100.0)[0],
+}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("seed", [0, 7])
+def test_predict_coeffs_parity(name, seed):
+    A = MATS[name]()
+    theta = W.gcin_init_params(seed, last_scale=1.0)
+    levels = OS.build_hierarchy(A)
+    ref = OG.predict(f32(theta), [l.A for l in levels])
+    ctx = ctx_setup(A, P.AMG_FP32_IN_FP64)
+    try:
+        P.gnn_load_params(ctx, theta)
+        c = P.gnn_predict_coeffs(ctx)
+        assert c.shape == ref.shape
+        assert rel(c, ref) < 1e-5, rel(c, ref)
+        # the predicted smoother is the one assembled on the device
+        q = P.amg_get_smoother(ctx, 0)
+        qref = O.pseudo_inverse_values(O.TMat.of(levels[0].A), c[0])
+        assert rel(q, qref.numpy()) < 1e-12
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_predict_coeffs_full_size_c2():
+    A = W.c2_matrix(0)
+    theta = W.gcin_init_params(3, last_scale=1.0)
+    levels = OS.build_hierarchy(A)
+    ref = OG.predict(f32(theta), [l.A for l in levels])
+    ctx = ctx_setup(A, P.AMG_FP32_IN_FP64)
+    try:
+        P.gnn_load_params(ctx, theta)
+        assert rel(P.gnn_predict_coeffs(ctx), ref) < 1e-5
+    finally:
+        P.amg_destroy(ctx)
+
+
+def _problems(names=("uniform_2k", "graded_6k", "band_8k")):
+    out = []
+    for k, nm in enumerate(names):
+        A = MATS[nm]()
+        out.append((A, OS.build_hierarchy(A), W.rhs_uniform(100 + k, A.n_rows)))
+    return out
+
+
+def test_network_backward_parity():
+    probs = _problems()
+    theta = W.gcin_init_params(11, last_scale=1.0)
+    ctxs = [ctx_setup(A, P.AMG_FP32_IN_FP64) for A, _, _ in probs]
+    tr = P.gcin_trainer_create(theta)
+    try:
+        c = P.gcin_trainer_forward(tr, ctxs)
+        rng = np.random.default_rng(0)
+        dc = rng.standard_normal(c.shape)
+        g = P.gcin_trainer_backward(tr, dc)
+        # oracle: d/dtheta of sum(dc * c) by autograd on the FP64 network
+        t = torch.tensor(f32(theta), requires_grad=True)
+        graphs = [OG.Graph(l.A) for _, lv, _ in probs for l in lv]
+        cref = OG.forward(t, graphs)
+        (cref * torch.from_numpy(dc)).sum().backward()
+        assert rel(c, cref.detach().numpy()) < 1e-5
+        gref = t.grad.numpy()
+        assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+        # every tensor individually; the conv biases are skipped because
+        # instance norm removes any per-feature constant, so their exact
+        # gradient is zero and both sides hold only rounding noise there
+        off = 0
+        for name, shape in OG.param_shapes():
+            k = int(np.prod(shape))
+            gs, rs = g[off:off + k], gref[off:off + k]
+            off += k
+            if name.startswith("conv") and name.endswith(".b"):
+                assert np.abs(rs).max() <= 1e-8 * np.abs(gref).max()
+                continue
+            assert np.linalg.norm(gs - rs) <= 1e-3 * max(np.linalg.norm(rs), 1e-6 * np.linalg.norm(gref)), name
+    finally:
+        P.gcin_trainer_destroy(tr)
+        for c_ in ctxs:
+            P.amg_destroy(c_)
+
+
+@pytest.mark.parametrize("prec,tol", [(P.AMG_FP64, 1e-10), (P.AMG_FP32_IN_FP64, 1e-4)])
+@pytest.mark.parametrize("name", ["c1_64", "band_8k"])
+def test_loss_and_adjoint_parity(name, prec, tol):
+    A = MATS[name]()
+    levels = OS.build_hierarchy(A)
+    c = np.array([[0.6 + 0.01 * l, 0.03, -0.01, -0.15, 0.02] for l in range(len(levels))])
+    f = W.rhs_uniform(9, A.n_rows)
+    Lref, dref = OT.loss_and_coeff_grad(O.OHierarchy.of(levels), c, f)
+    ctx = ctx_from_oracle(levels, prec)
+    try:
+        L, dc = P.amg_loss_grad(ctx, c, f)
+        assert abs(L - Lref) <= tol * abs(Lref)
+        assert np.abs(dc - dref).max() <= tol * np.abs(dref).max()
+        assert np.all(dc[-1] == 0)
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_adjoint_matches_finite_differences():
+    A = MATS["graded_6k"]()
+    c = np.array([[0.62, 0.02, -0.01, -0.12, 0.03]] * 8)
+    f = W.rhs_uniform(12, A.n_rows)
+    ctx = ctx_setup(A, P.AMG_FP64)
+    try:
+        nl = P.amg_num_levels(ctx)
+        c = c[:nl]
+        L, dc = P.amg_loss_grad(ctx, c, f)
+        eps = 1e-6
+        for l in range(nl - 1):
+            for k in range(5):
+                cp, cm = c.copy(), c.copy()
+                cp[l, k] += eps
+                cm[l, k] -= eps
+                fd = (P.amg_loss_grad(ctx, cp, f)[0] - P.amg_loss_grad(ctx, cm, f)[0]) / (2 * eps)
+                assert abs(fd - dc[l, k]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(dc).max()), (l, k, fd, dc[l, k])
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_training_step_matches_oracle():
+    probs = _problems()
+    theta = W.gcin_init_params(21)
+    ctxs = [ctx_setup(A, P.AMG_FP64) for A, _, _ in probs]
+    tr = P.gcin_trainer_create(theta)
+    try:
+        c = P.gcin_trainer_forward(tr, ctxs)
+        dc, losses, row = np.zeros_like(c), [], 0
+        for ctx, (A, lv, f) in zip(ctxs, probs):
+            nl = P.amg_num_levels(ctx)
+            L, g = P.amg_loss_grad(ctx, c[row:row + nl], f)
+            losses.append(L)
+            dc[row:row + nl] = g / len(probs)
+            row += nl
+        grad = P.gcin_trainer_backward(tr, dc)
+        # oracle: autograd through network and V-cycles (Algorithm 1)
+        hs = [O.OHierarchy.of(lv) for _, lv, _ in probs]
+        gs = [[OG.Graph(l.A) for l in lv] for _, lv, _ in probs]
+        Lref, gref = OT.batch_loss_and_grad(f32(theta), hs, gs, [f for _, _, f in probs])
+        assert abs(np.mean(losses) - Lref) <= 1e-5 * abs(Lref)
+        assert np.linalg.norm(grad - gref) <= 1e-4 * np.linalg.norm(gref)
+        # one clipped Adam step: first step moves each parameter by ~lr * sign(g)
+        P.gcin_trainer_adam_step(tr, 1e-3, 1.0)
+        new = P.gcin_trainer_get_params(tr).astype(np.float64)
+        ref, _, _ = OT.adam_step(f32(theta), OT.clip_grad(gref, 1.0), np.zeros_like(gref), np.zeros_like(gref), 1)
+        d = np.abs(new - ref)
+        assert d.max() <= 2.1e-3
+        assert np.mean(d < 1e-6) > 0.98
+    finally:
+        P.gcin_trainer_destroy(tr)
+        for c_ in ctxs:
+            P.amg_destroy(c_)
