@@ -1,0 +1,53 @@
+"""Train the GCIN on the synthetic training batch and write gcin_c3.npy.
+
+Training batch: 64 Delaunay finite-volume meshes of 2k-20k nodes cycling
+uniform / 10:1 graded / graded + anisotropic band (aspect <= 100) point
+sets (workloads.c3_batch, seed 0); validation: 8 more meshes of the same
+distribution (seed 1).  Algorithm 1 with N_vc = 1, mini-batch 5, Adam lr
+1e-3, clipping 1.0, ReduceLROnPlateau, best-validation parameters kept
+(Table train_hyper).  Every forward/backward runs on the GPU through
+libamggnn.so.
+
+    python -m paper_2606_19251_gb300.weights.make_weights [--epochs 150]
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--epochs", type=int, default=150)
+    ap.add_argument("--batch", type=int, default=5)
+    ap.add_argument("--meshes", type=int, default=64)
+    ap.add_argument("--out", default=os.path.join(HERE, "gcin_c3.npy"))
+    args = ap.parse_args()
+    import workloads as W
+    from paper_2606_19251_gb300 import _build
+    from paper_2606_19251_gb300.train import train
+    _build.build()
+    t0 = time.time()
+    mats = W.c3_batch(args.meshes, seed=0)
+    val = W.c3_batch(8, seed=1)
+    print(f"meshes ready in {time.time() - t0:.1f}s: n = {[m.n_rows for m in mats[:8]]}...", flush=True)
+    theta0 = W.gcin_init_params(0)
+    best, rows = train(mats, val, theta0, epochs=args.epochs, batch=args.batch,
+                       log=lambda r: print(json.dumps(r), flush=True))
+    np.save(args.out, np.asarray(best, dtype=np.float32))
+    with open(os.path.splitext(args.out)[0] + "_log.json", "w") as f:
+        json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "rows": rows,
+                   "seconds": time.time() - t0}, f, indent=1)
+    print("wrote", args.out, flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,92 @@
+"""Full-size generalisation case: 2.5M-node graded Delaunay mesh with an
+anisotropic band (aspect up to 1000), about 128x the training meshes.
+
+The oracle cannot run the whole solve at this size, so the checks are
+properties that hold at any size plus outputs it computes one by one:
+sampled rows of A_l x on every level, sampled entries of the Galerkin
+product P^T A P, the final residual of both solves recomputed in FP64 by
+the oracle's own product, and the trained network's V-cycle reduction.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_19251_gb300 as P
+import workloads as W
+from oracle import solve as O
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2606_19251_gb300",
+                       "weights", "gcin_c3.npy")
+
+
+@pytest.fixture(scope="module")
+def c4():
+    A = W.c4_matrix(0)
+    ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64)
+    P.amg_setup(ctx, A)
+    yield A, ctx
+    P.amg_destroy(ctx)
+
+
+def test_c4_sampled_spmv_and_galerkin(c4):
+    A, ctx = c4
+    rng = np.random.default_rng(0)
+    ctx64 = P.amg_create(precision=P.AMG_FP64)
+    try:
+        nl = P.amg_num_levels(ctx)
+        levels = [P.amg_get_level(ctx, l) for l in range(nl)]
+        A_l = [W.CSR(a["n"], a["n"], a["row_ptr"], a["col"], a["val"]) for a, _ in levels]
+        P_l = [W.CSR(p["n"], p["nc"], p["row_ptr"], p["col"], p["val"]) for _, p in levels[:-1]]
+        P.amg_load_hierarchy(ctx64, A_l, P_l)
+        for l in range(nl):
+            x = W.rhs_uniform(40 + l, A_l[l].n_rows)
+            dx = torch.tensor(x, device="cuda")
+            dy = torch.empty_like(dx)
+            P.amg_spmv_device(ctx64, l, dx, dy)
+            torch.cuda.synchronize()
+            y = dy.cpu().numpy()
+            M = A_l[l]
+            for i in rng.integers(0, M.n_rows, 200):
+                lo, hi = M.row_ptr[i], M.row_ptr[i + 1]
+                ref = sum(M.val[p] * x[M.col[p]] for p in range(lo, hi))
+                assert abs(y[i] - ref) <= 1e-13 * max(1.0, sum(abs(M.val[p] * x[M.col[p]]) for p in range(lo, hi)))
+        # Galerkin entries (A_{l+1})_{IJ} = sum_{i,j} P_iI a_ij P_jJ, one by one
+        for l in range(min(2, nl - 1)):
+            M, Pm, C = A_l[l], P_l[l], A_l[l + 1]
+            PT = {}
+            for i in range(Pm.n_rows):
+                for p in range(Pm.row_ptr[i], Pm.row_ptr[i + 1]):
+                    PT.setdefault(int(Pm.col[p]), []).append((i, Pm.val[p]))
+            Prow = [dict(zip(Pm.col[Pm.row_ptr[i]:Pm.row_ptr[i + 1]], Pm.val[Pm.row_ptr[i]:Pm.row_ptr[i + 1]]))
+                    for i in range(Pm.n_rows)]
+            for I in rng.integers(0, C.n_rows, 20):
+                for p in range(C.row_ptr[I], C.row_ptr[I + 1]):
+                    J = int(C.col[p])
+                    ref = 0.0
+                    for i, wi in PT[int(I)]:
+                        for q in range(M.row_ptr[i], M.row_ptr[i + 1]):
+                            j = int(M.col[q])
+                            ref += wi * M.val[q] * Prow[j].get(J, 0.0)
+                    assert abs(C.val[p] - ref) <= 1e-12 * max(1.0, abs(M.val).max())
+    finally:
+        P.amg_destroy(ctx64)
+
+
+def test_c4_trained_gcin_vs_jacobi_to_1e8(c4):
+    A, ctx = c4
+    b = W.rhs_zero_mean(3, A.n_rows)
+    st_j, x_j, h_j = P.amg_solve(ctx, b)
+    P.gnn_load_params(ctx, np.load(WEIGHTS))
+    P.gnn_predict_coeffs(ctx)
+    st_g, x_g, h_g = P.amg_solve(ctx, b)
+    P.amg_set_jacobi(ctx)
+    T = O.TMat.of(A)
+    for st, x in ((st_j, x_j), (st_g, x_g)):
+        assert st == P.AMG_OK
+        r = b - O.mv(T, torch.from_numpy(x)).numpy()
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-8
+    assert len(h_g) < len(h_j), (len(h_g) - 1, len(h_j) - 1)
