@@ -332,6 +332,18 @@ def run_kernel_only(args, wl):
     A = wl["matrix"]()
     ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64)
     P.amg_setup(ctx, A)
+    if args.kernel_only == "gcin":
+        theta, _ = load_theta()
+        P.gnn_load_params(ctx, theta)
+        times = []
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.gnn_predict_coeffs(ctx)
+            times.append((time.perf_counter() - t0) * 1e3)
+        print(json.dumps({"kernel": "gcin", "workload": wl["workload"], "ms": times}))
+        P.amg_destroy(ctx)
+        return
     P.amg_set_coeffs(ctx, [[0.62, 0.03, -0.01, -0.18, 0.02]] * P.amg_num_levels(ctx))
     kid = {"residual": P.AMG_K_RESIDUAL, "pinv": P.AMG_K_PINV, "jacobi": P.AMG_K_JACOBI,
            "restrict": P.AMG_K_RESTRICT, "prolong": P.AMG_K_PROLONG, "outer": P.AMG_K_OUTER,

@@ -239,7 +239,8 @@ __global__ void k_state_init(SolveState *st, double tol, int max_iter) {
 // history entry k and the stopping rule (Sec. 4 tolerance, divergence,
 // stagnation, iteration cap).
 __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ partial, int np, SolveState *st,
-                                                     double *__restrict__ hist, int mode) {
+                                                     double *__restrict__ hist, int mode, int use_cond,
+                                                     cudaGraphConditionalHandle cond) {
     __shared__ double red[32];
     double v = 0.0;
     for (int i = threadIdx.x; i < np; i += 1024) v += partial[i];
@@ -271,6 +272,12 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ 
     }
     st->status = status;
     st->k = k + 1;
+    if (use_cond) cudaGraphSetConditional(cond, status == kRunning ? 1u : 0u);
+}
+
+// Copies "still running" into the solve graph's WHILE condition.
+__global__ void k_set_cond(const SolveState *st, cudaGraphConditionalHandle cond) {
+    cudaGraphSetConditional(cond, st->status == kRunning ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -313,27 +320,34 @@ __global__ void k_max_final(const double *__restrict__ partial, int np, double *
     *out = m > 0.0 ? m : 1.0;
 }
 
-// Q^-1 values on A's pattern from c = (d0, d1, d2, o1, o2) (Sec. 3.1), in
-// FP64 with the polynomial evaluated as d0 + d1 x + (d2 x) x, uncontracted.
-__global__ void k_assemble_q(int n, const int *__restrict__ rp, const int *__restrict__ col,
+// Per-entry basis of the pseudo-inverse (Sec. 3.1), computed once per
+// hierarchy: bx = a_ij / s and bw = 1 / a_ii (diagonal) or 1 / (a_ii + a_jj).
+__global__ void k_pinv_basis(int n, const int *__restrict__ rp, const int *__restrict__ col,
                              const double *__restrict__ a, const double *__restrict__ d,
-                             const double *__restrict__ s_ptr, double c0, double c1, double c2, double c3,
-                             double c4, double *__restrict__ q64, float *__restrict__ q32) {
+                             const double *__restrict__ s_ptr, double *__restrict__ bx, double *__restrict__ bw) {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= n) return;
-    const double s = *s_ptr;
-    const double di = d[i];
+    const double s = *s_ptr, di = d[i];
     for (int p = rp[i]; p < rp[i + 1]; ++p) {
         const int j = col[p];
-        const double x = __ddiv_rn(a[p], s);
-        double q;
-        if (j == i) {
-            double f = __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x));
-            q = __ddiv_rn(f, di);
-        } else {
-            double f = __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
-            q = __ddiv_rn(f, __dadd_rn(di, d[j]));
-        }
+        bx[p] = a[p] / s;
+        bw[p] = 1.0 / (j == i ? di : di + d[j]);
+    }
+}
+
+// Q^-1 values on A's pattern from c = (d0, d1, d2, o1, o2) (Sec. 3.1):
+// q_ii = (d0 + d1 x + d2 x^2) bw, q_ij = (o1 x + o2 x^2) bw, in FP64 with the
+// polynomial evaluated as d0 + d1 x + (d2 x) x, uncontracted.
+__global__ void k_assemble_q(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ bx, const double *__restrict__ bw, double c0, double c1,
+                             double c2, double c3, double c4, double *__restrict__ q64, float *__restrict__ q32) {
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const double x = bx[p];
+        const double f = (col[p] == i) ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
+                                       : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
+        const double q = __dmul_rn(f, bw[p]);
         q64[p] = q;
         q32[p] = static_cast<float>(q);
     }
@@ -524,12 +538,13 @@ static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
 }
 
 template <class T>
-static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s) {
+static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s, int use_cond = 0,
+                                   cudaGraphConditionalHandle cond = 0) {
     const DevMat &A = c->lev[0].A;
     const int nb = outer_blocks(A);
     TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb),
                  c->partials, nb, s);
-    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 1); AMG_COUNT();
+    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 1, use_cond, cond); AMG_COUNT();
 }
 
 template <class T>
@@ -538,32 +553,79 @@ static void enqueue_init(amg_ctx *c, cudaStream_t s, double tol, int max_iter) {
     const int nb = std::min(grid_for(n0), kNumSMs * 8);
     k_state_init<<<1, 1, 0, s>>>(c->state, tol, max_iter); AMG_COUNT();
     k_sqnorm_partial<<<nb, kBlock, 0, s>>>(n0, c->db, c->partials); AMG_COUNT();
-    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 0); AMG_COUNT();
+    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 0, 0, 0); AMG_COUNT();
     enqueue_outer_residual<T>(c, s);
 }
 
 template <class T>
-static void enqueue_iteration(amg_ctx *c, cudaStream_t s) {
+static void enqueue_iteration(amg_ctx *c, cudaStream_t s, int use_cond = 0, cudaGraphConditionalHandle cond = 0) {
     T *e = vcycle_level<T>(c, 0, s);
     k_axpy<T><<<grid_for(c->lev[0].n), kBlock, 0, s>>>(c->lev[0].n, c->dx, e); AMG_COUNT();
-    enqueue_outer_residual<T>(c, s);
+    enqueue_outer_residual<T>(c, s, use_cond, cond);
+}
+
+static void free_graph(SolveGraph &G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = SolveGraph{};
+}
+
+// Build (once per hierarchy and smoother) the whole-solve graph.
+template <class T>
+static int ensure_graph(amg_ctx *c) {
+    SolveGraph &G = c->sgraph[c->smoother];
+    if (G.exec && G.version == c->hier_version) return AMG_OK;
+    free_graph(G);
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    G.graph = g;
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+    SolveState *st = c->state;
+    void *args[] = {&st, &cond};
+    cudaKernelNodeParams kp{};
+    kp.func = reinterpret_cast<void *>(k_set_cond);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    cudaGraphNode_t setnode;
+    CK(cudaGraphAddKernelNode(&setnode, g, nullptr, 0, &kp));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, g, &setnode, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const long long before = g_launches.load();
+    CK(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    enqueue_iteration<T>(c, c->stream, 1, cond);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &captured);
+    G.body_kernels = g_launches.load() - before;
+    g_launches.fetch_sub(G.body_kernels);
+    CK(e);
+    CK(cudaGraphInstantiate(&G.exec, g, 0));
+    G.version = c->hier_version;
+    return AMG_OK;
 }
 
 // Solve on the staging buffers c->db / c->dx.
 template <class T>
 static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, double *hist) {
     const int max_iter = c->opt.max_iter;
+    int rc = ensure_graph<T>(c);
+    if (rc) return rc;
     enqueue_init<T>(c, s, tol, max_iter);
     CKL("solve init launch");
+    const SolveGraph &G = c->sgraph[c->smoother];
+    CK(cudaGraphLaunch(G.exec, s));
     CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    while (c->h_state->status == kRunning) {
-        enqueue_iteration<T>(c, s);
-        CKL("V-cycle launch");
-        CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    }
     const int nh = c->h_state->k;
+    g_launches.fetch_add(1 + static_cast<long long>(nh - 1) * G.body_kernels);
     if (n_vc) *n_vc = nh - 1;
     if (hist) CK(cudaMemcpyAsync(hist, c->hist, sizeof(double) * nh, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -575,8 +637,11 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
 // ---------------------------------------------------------------------------
 static const int kMaxCoarseDense = 4096;
 
+static void free_graph(SolveGraph &G);
+
 static void free_device(amg_ctx *c) {
     train_bufs_free(c);
+    for (auto &G : c->sgraph) free_graph(G);
     if (c->arena) cudaFree(c->arena);
     c->arena = nullptr;
     c->arena_bytes = 0;
@@ -609,6 +674,8 @@ static void layout(amg_ctx *c, Planner &pl) {
             layout_mat(pl, L.R, H.R);
         }
         L.diag = pl.take<double>(L.n);
+        L.bx = pl.take<double>(std::max(1, L.A.nnz));
+        L.bw = pl.take<double>(std::max(1, L.A.nnz));
         L.q64 = pl.take<double>(std::max(1, L.A.nnz));
         L.q32 = pl.take<float>(std::max(1, L.A.nnz));
         L.j64 = pl.take<double>(L.n);
@@ -672,6 +739,8 @@ static int upload(amg_ctx *c) {
         k_offdiag_absmax<<<nb, kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, c->partials); AMG_COUNT();
         k_max_final<<<1, 32, 0, s>>>(c->partials, nb, c->scal + l); AMG_COUNT();
         k_jacobi_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, c->opt.omega, L.j64, L.j32); AMG_COUNT();
+        k_pinv_basis<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag, c->scal + l, L.bx,
+                                                      L.bw); AMG_COUNT();
     }
     c->jac_omega = c->opt.omega;
     // coarsest level: dense FP64 Cholesky and the inverse factor
@@ -898,8 +967,8 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
         const double *q = coef + 5 * l;
         for (int k = 0; k < 5; ++k)
             if (!std::isfinite(q[k])) return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
-        k_assemble_q<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag, c->scal + l, q[0],
-                                                      q[1], q[2], q[3], q[4], L.q64, L.q32); AMG_COUNT();
+        k_assemble_q<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.bx, L.bw, q[0], q[1], q[2], q[3],
+                                                      q[4], L.q64, L.q32); AMG_COUNT();
     }
     (void)n_rows;
     CKL("assemble pseudo-inverse");
@@ -1368,28 +1437,25 @@ namespace {
 
 template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_coef_grad(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                      const double *__restrict__ a, const double *__restrict__ d,
-                                                      const double *__restrict__ s_ptr, const T *__restrict__ ubar,
-                                                      const T *__restrict__ r, double *__restrict__ partial) {
+                                                      const double *__restrict__ bx, const double *__restrict__ bw,
+                                                      const T *__restrict__ ubar, const T *__restrict__ r,
+                                                      double *__restrict__ partial) {
     constexpr int RPB = kBlock / TPR;
     const int lane = threadIdx.x % TPR;
-    const double s = *s_ptr;
     double g[5] = {0, 0, 0, 0, 0};
     for (int base = blockIdx.x * RPB; base < n; base += gridDim.x * RPB) {
         const int row = base + threadIdx.x / TPR;
         double acc[5] = {0, 0, 0, 0, 0};
         if (row < n) {
-            const double ui = static_cast<double>(ubar[row]), di = d[row];
+            const double ui = static_cast<double>(ubar[row]);
             for (int p = rp[row] + lane; p < rp[row + 1]; p += TPR) {
                 const int j = col[p];
-                const double x = a[p] / s;
+                const double x = bx[p], w = ui * static_cast<double>(r[j]) * bw[p];
                 if (j == row) {
-                    const double w = ui * static_cast<double>(r[j]) / di;
                     acc[0] += w;
                     acc[1] += w * x;
                     acc[2] += w * x * x;
                 } else {
-                    const double w = ui * static_cast<double>(r[j]) / (di + d[j]);
                     acc[3] += w * x;
                     acc[4] += w * x * x;
                 }
@@ -1530,7 +1596,7 @@ void coef_grad(amg_ctx *c, TrainBufs &tb, int l, const T *ubar, const T *r, cuda
     const DevMat &A = L.A;
     const int nb = outer_blocks(A);
 #define CG_LAUNCH(TP)                                                                                          \
-    k_coef_grad<T, TP><<<nb, kBlock, 0, s>>>(A.nr, A.rp, A.col, A.v64, L.diag, c->scal + l, ubar, r, c->partials); \
+    k_coef_grad<T, TP><<<nb, kBlock, 0, s>>>(A.nr, A.rp, A.col, L.bx, L.bw, ubar, r, c->partials); \
     AMG_COUNT();
     switch (A.tpr) {
         case 2: CG_LAUNCH(2) break;

@@ -23,6 +23,7 @@ struct DevLevel {
     int n = 0;
     DevMat A, P, R;                            // P: n x n_{l+1}; R: n_{l+1} x n
     double *diag = nullptr;                    // a_ii (FP64)
+    double *bx = nullptr, *bw = nullptr;       // pseudo-inverse basis a_ij/s and 1/a_ii or 1/(a_ii+a_jj)
     double *q64 = nullptr; float *q32 = nullptr;   // pseudo-inverse values on A's pattern
     double *j64 = nullptr; float *j32 = nullptr;   // omega / a_ii
     // V-cycle vectors; storage sized for n doubles, used as float or double
@@ -39,6 +40,17 @@ struct SolveState {
     double tol;
     double bnorm;   // ||b|| (1 if b = 0)
     double r0;      // ||b - A x0||
+};
+
+// Whole-solve CUDA graph: a kernel node copies the device-side status into
+// a conditional handle, and a WHILE node repeats the captured iteration body
+// (V-cycle, x += e, outer residual, norm and stopping rule) until the rule
+// clears the handle.  One graph per smoother, rebuilt when the hierarchy changes.
+struct SolveGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long version = -1;
+    long long body_kernels = 0;
 };
 
 struct GcinEngine;
@@ -71,6 +83,7 @@ struct amg_ctx {
     amg::GcinEngine *gnn = nullptr;
     long long hier_version = 0;                // bumped by every hierarchy upload
     void *train = nullptr;                     // training (adjoint) buffers, created on demand
+    amg::SolveGraph sgraph[2];                 // per smoother (AMG_SMOOTHER_JACOBI / _GNN)
 };
 
 namespace amg {

@@ -97,6 +97,7 @@ static void batch_layout(GcinBatch &b, Planner &pl, bool backward) {
         b.gS1 = pl.take<double>(G * kHidden);
         b.gS2 = pl.take<double>(G * kHidden);
         b.dWt = pl.take<float>(NT * (kHidden * kHidden + kHidden));
+        b.dWc = pl.take<double>(static_cast<size_t>(kGradChunks) * (kHidden * kHidden + kHidden));
     }
 }
 
@@ -240,8 +241,9 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
             h1[2 * i + 1] = static_cast<float>(a1);
         }
         const int f = 2 * lane;
-        const float y0 = static_cast<float>(a0 * W[f] + a1 * W[kHidden + f] + bias[f]);
-        const float y1 = static_cast<float>(a0 * W[f + 1] + a1 * W[kHidden + f + 1] + bias[f + 1]);
+        const float h0 = static_cast<float>(a0), h1v = static_cast<float>(a1);
+        const float y0 = fmaf(h0, W[f], fmaf(h1v, W[kHidden + f], bias[f]));
+        const float y1 = fmaf(h0, W[f + 1], fmaf(h1v, W[kHidden + f + 1], bias[f + 1]));
         reinterpret_cast<float2 *>(y)[static_cast<size_t>(i) * 32 + lane] = make_float2(y0, y1);
         sY[k][f] = y0;
         sY[k][f + 1] = y1;
@@ -291,24 +293,49 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__
     tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
 }
 
-// Per-graph instance-norm statistics: Chan combination of the tile partials
-// in tile order (biased variance, FP64).
-__global__ void k_stats_combine(const int *__restrict__ gtile, const int *__restrict__ tstart,
-                                const float *__restrict__ tmean, const float *__restrict__ tm2,
-                                float *__restrict__ mu, float *__restrict__ rstd) {
-    const int g = blockIdx.x, f = threadIdx.x;
-    double n = 0.0, mean = 0.0, m2 = 0.0;
-    for (int t = gtile[g]; t < gtile[g + 1]; ++t) {
-        const double nb = tstart[t + 1] - tstart[t];
-        const double mb = tmean[static_cast<size_t>(t) * kHidden + f];
-        const double delta = mb - mean;
-        const double nn = n + nb;
-        mean += delta * nb / nn;
-        m2 += tm2[static_cast<size_t>(t) * kHidden + f] + delta * delta * n * nb / nn;
-        n = nn;
+// Fixed-order sum over the 16 tile lanes of one feature (1024-thread blocks:
+// f = tid % 64, lane = tid / 64); every thread receives the total.
+constexpr int kLanes = 16, kCombine = kLanes * kHidden;
+__device__ __forceinline__ double lanes_sum(double v, double (*red)[kHidden]) {
+    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+    red[q][f] = v;
+    __syncthreads();
+    for (int w = kLanes / 2; w > 0; w >>= 1) {
+        if (q < w) red[q][f] += red[q + w][f];
+        __syncthreads();
     }
-    mu[g * kHidden + f] = static_cast<float>(mean);
-    rstd[g * kHidden + f] = static_cast<float>(1.0 / sqrt(m2 / n + static_cast<double>(kEps)));
+    const double t = red[0][f];
+    __syncthreads();
+    return t;
+}
+
+// Per-graph instance-norm statistics from the tile partials (biased
+// variance): mean = sum_t n_t mean_t / n, M2 = sum_t [M2_t + n_t (mean_t - mean)^2].
+// 16 lanes of tiles per feature; one FP64 add per tile, the rest in FP32.
+__global__ void __launch_bounds__(kCombine) k_stats_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
+                                                            const int *__restrict__ tstart,
+                                                            const float *__restrict__ tmean,
+                                                            const float *__restrict__ tm2, float *__restrict__ mu,
+                                                            float *__restrict__ rstd) {
+    __shared__ double red[kLanes][kHidden];
+    const int g = blockIdx.x, f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+    const double n = gptr[g + 1] - gptr[g];
+    double s = 0.0;
+    for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes)
+        s += static_cast<double>(static_cast<float>(tstart[t + 1] - tstart[t]) * tmean[static_cast<size_t>(t) * kHidden + f]);
+    const double mean = lanes_sum(s, red) / n;
+    const float mf = static_cast<float>(mean);
+    double v = 0.0;
+    for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes) {
+        const float d = tmean[static_cast<size_t>(t) * kHidden + f] - mf;
+        v += static_cast<double>(fmaf(static_cast<float>(tstart[t + 1] - tstart[t]) * d, d,
+                                      tm2[static_cast<size_t>(t) * kHidden + f]));
+    }
+    const double m2 = lanes_sum(v, red);
+    if (q == 0) {
+        mu[g * kHidden + f] = mf;
+        rstd[g * kHidden + f] = static_cast<float>(1.0 / sqrt(m2 / n + static_cast<double>(kEps)));
+    }
 }
 
 // x = ReLU((y - mu) rstd gamma + beta); tile sum / max / argmax of x.
@@ -356,23 +383,34 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
 }
 
 // Per-graph mean and max (first index of the max kept) from the tile partials.
-__global__ void k_pool_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
-                               const double *__restrict__ tsum, const float *__restrict__ tmax,
-                               const int *__restrict__ targ, float *__restrict__ pooled, int *__restrict__ argmax,
-                               int layer) {
-    const int g = blockIdx.x, f = threadIdx.x;
+__global__ void __launch_bounds__(kCombine) k_pool_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
+                                                           const double *__restrict__ tsum,
+                                                           const float *__restrict__ tmax,
+                                                           const int *__restrict__ targ, float *__restrict__ pooled,
+                                                           int *__restrict__ argmax, int layer) {
+    __shared__ double red[kLanes][kHidden];
+    __shared__ float rm[kLanes][kHidden];
+    __shared__ int ri[kLanes][kHidden];
+    const int g = blockIdx.x, f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
     double s = 0.0;
     float bm = -INFINITY;
     int bi = gptr[g];
-    for (int t = gtile[g]; t < gtile[g + 1]; ++t) {
+    for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes) {
         const size_t o = static_cast<size_t>(t) * kHidden + f;
         s += tsum[o];
-        if (tmax[o] > bm) { bm = tmax[o]; bi = targ[o]; }
+        if (tmax[o] > bm) { bm = tmax[o]; bi = targ[o]; }   // tiles ascend, so the first max wins
     }
-    float *P = pooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
-    P[f] = static_cast<float>(s / (gptr[g + 1] - gptr[g]));
-    P[kHidden + f] = bm;
-    argmax[(static_cast<size_t>(g) * kLayers + layer) * kHidden + f] = bi;
+    rm[q][f] = bm;
+    ri[q][f] = bi;
+    const double total = lanes_sum(s, red);
+    if (q == 0) {
+        for (int k = 1; k < kLanes; ++k)
+            if (rm[k][f] > bm || (rm[k][f] == bm && ri[k][f] < bi)) { bm = rm[k][f]; bi = ri[k][f]; }
+        float *P = pooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
+        P[f] = static_cast<float>(total / (gptr[g + 1] - gptr[g]));
+        P[kHidden + f] = bm;
+        argmax[(static_cast<size_t>(g) * kLayers + layer) * kHidden + f] = bi;
+    }
 }
 
 __device__ __forceinline__ float block128_sum(float v, float *red) {
@@ -454,11 +492,11 @@ void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
                                                  th + kPL.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
                                                  b.tm2); AMG_COUNT();
         }
-        k_stats_combine<<<G, kHidden, 0, s>>>(b.gtile, b.tstart, b.tmean, b.tm2, b.mu[l], b.rstd[l]); AMG_COUNT();
+        k_stats_combine<<<G, kCombine, 0, s>>>(b.gtile, b.gptr, b.tstart, b.tmean, b.tm2, b.mu[l], b.rstd[l]); AMG_COUNT();
         k_norm_relu_pool_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
                                                     th + kPL.inG[l], th + kPL.inB[l], b.x[l], b.tsum, b.tmax,
                                                     b.targ); AMG_COUNT();
-        k_pool_combine<<<G, kHidden, 0, s>>>(b.gtile, b.gptr, b.tsum, b.tmax, b.targ, b.pooled, b.argmax, l); AMG_COUNT();
+        k_pool_combine<<<G, kCombine, 0, s>>>(b.gtile, b.gptr, b.tsum, b.tmax, b.targ, b.pooled, b.argmax, l); AMG_COUNT();
     }
     k_head<<<G, 128, 0, s>>>(b.pooled, th, b.head, b.c); AMG_COUNT();
 }
@@ -602,16 +640,23 @@ __global__ void __launch_bounds__(kBlock) k_bwd_relu_tile(const int *__restrict_
     }
 }
 
-__global__ void k_bwd_combine(const int *__restrict__ gtile, const double *__restrict__ tsum,
-                              const double *__restrict__ tsum2, double *__restrict__ gS1, double *__restrict__ gS2) {
-    const int g = blockIdx.x, f = threadIdx.x;
+__global__ void __launch_bounds__(kCombine) k_bwd_combine(const int *__restrict__ gtile,
+                                                          const double *__restrict__ tsum,
+                                                          const double *__restrict__ tsum2,
+                                                          double *__restrict__ gS1, double *__restrict__ gS2) {
+    __shared__ double red[kLanes][kHidden];
+    const int g = blockIdx.x, f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
     double s1 = 0.0, s2 = 0.0;
-    for (int t = gtile[g]; t < gtile[g + 1]; ++t) {
+    for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes) {
         s1 += tsum[static_cast<size_t>(t) * kHidden + f];
         s2 += tsum2[static_cast<size_t>(t) * kHidden + f];
     }
-    gS1[g * kHidden + f] = s1;
-    gS2[g * kHidden + f] = s2;
+    const double t1 = lanes_sum(s1, red);
+    const double t2 = lanes_sum(s2, red);
+    if (q == 0) {
+        gS1[g * kHidden + f] = t1;
+        gS2[g * kHidden + f] = t2;
+    }
 }
 
 // Layer backward, part 2 (per tile): instance-norm backward
@@ -709,18 +754,30 @@ __global__ void __launch_bounds__(kBlock) k_agg_plain(int N, const int *__restri
     reinterpret_cast<float2 *>(out)[static_cast<size_t>(i) * 32 + lane] = make_float2(ax, ay);
 }
 
-// Conv weight/bias gradient (sum of tile partials, tile order) and the
-// instance-norm affine gradients (sum over graphs).
-__global__ void k_layer_param_grad(int NT, int G, int fin, const float *__restrict__ dWt,
-                                   const double *__restrict__ gS1, const double *__restrict__ gS2,
-                                   float *__restrict__ gW, float *__restrict__ gB, float *__restrict__ gG,
-                                   float *__restrict__ gBeta) {
+// Conv weight/bias gradient: tile partials summed per chunk of tiles (FP64,
+// tile order), then the chunks in order; instance-norm affine gradients are
+// the per-graph sums added in graph order.
+constexpr int kGradStride = kHidden * kHidden + kHidden;
+__global__ void k_layer_param_partial(int NT, int fin, const float *__restrict__ dWt, double *__restrict__ chunk) {
+    const int e = blockIdx.x * kBlock + threadIdx.x, c = blockIdx.y;
+    const int nW = fin * kHidden;
+    if (e >= nW + kHidden) return;
+    const int src = (e < nW) ? e : kHidden * kHidden + (e - nW);
+    const int t0 = static_cast<int>(static_cast<long long>(NT) * c / kGradChunks);
+    const int t1 = static_cast<int>(static_cast<long long>(NT) * (c + 1) / kGradChunks);
+    double acc = 0.0;
+    for (int t = t0; t < t1; ++t) acc += dWt[static_cast<size_t>(t) * kGradStride + src];
+    chunk[static_cast<size_t>(c) * kGradStride + e] = acc;
+}
+
+__global__ void k_layer_param_final(int G, int fin, const double *__restrict__ chunk, const double *__restrict__ gS1,
+                                    const double *__restrict__ gS2, float *__restrict__ gW, float *__restrict__ gB,
+                                    float *__restrict__ gG, float *__restrict__ gBeta) {
     const int e = blockIdx.x * kBlock + threadIdx.x;
     const int nW = fin * kHidden;
     if (e < nW + kHidden) {
-        const int src = (e < nW) ? e : kHidden * kHidden + (e - nW);
         double acc = 0.0;
-        for (int t = 0; t < NT; ++t) acc += dWt[static_cast<size_t>(t) * (kHidden * kHidden + kHidden) + src];
+        for (int c = 0; c < kGradChunks; ++c) acc += chunk[static_cast<size_t>(c) * kGradStride + e];
         if (e < nW) gW[e] = static_cast<float>(acc);
         else gB[e - nW] = static_cast<float>(acc);
     } else if (e < nW + 2 * kHidden) {
@@ -745,7 +802,7 @@ void gcin_backward(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
         k_bwd_relu_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.x[l], b.y[l], b.mu[l], b.rstd[l],
                                               l == kLayers - 1 ? nullptr : b.dx, b.dpooled, b.argmax, l, b.dy,
                                               b.tsum, b.tsum2); AMG_COUNT();
-        k_bwd_combine<<<G, kHidden, 0, s>>>(b.gtile, b.tsum, b.tsum2, b.gS1, b.gS2); AMG_COUNT();
+        k_bwd_combine<<<G, kCombine, 0, s>>>(b.gtile, b.tsum, b.tsum2, b.gS1, b.gS2); AMG_COUNT();
         if (l > 0) {
             k_bwd_in_lin_tile<kHidden><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
                                                              th + kPL.inG[l], b.gS1, b.gS2, th + kPL.convW[l],
@@ -757,8 +814,10 @@ void gcin_backward(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
                                                        nullptr, b.dWt); AMG_COUNT();
         }
         const int fin = (l == 0) ? 2 : kHidden;
-        k_layer_param_grad<<<grid_for(fin * kHidden + 2 * kHidden), kBlock, 0, s>>>(
-            NT, G, fin, b.dWt, b.gS1, b.gS2, grad + kPL.convW[l], grad + kPL.convB[l], grad + kPL.inG[l],
+        k_layer_param_partial<<<dim3(grid_for(fin * kHidden + kHidden), kGradChunks), kBlock, 0, s>>>(
+            NT, fin, b.dWt, b.dWc); AMG_COUNT();
+        k_layer_param_final<<<grid_for(fin * kHidden + 2 * kHidden), kBlock, 0, s>>>(
+            G, fin, b.dWc, b.gS1, b.gS2, grad + kPL.convW[l], grad + kPL.convB[l], grad + kPL.inG[l],
             grad + kPL.inB[l]); AMG_COUNT();
     }
 }

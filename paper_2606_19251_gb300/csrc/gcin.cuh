@@ -61,6 +61,7 @@ static_assert(kPL.total == kNumParams, "GCIN layout must have 55,045 parameters 
 // cross a graph boundary; every reduction over a graph is a fixed-order
 // combination of per-tile partials (deterministic, no atomics).
 constexpr int kTile = 64;
+constexpr int kGradChunks = 64;      // tile chunks of the weight-gradient reduction
 
 struct GcinBatch {
     int G = 0, N = 0, NT = 0;            // graphs, nodes, tiles
@@ -92,6 +93,7 @@ struct GcinBatch {
     float *dx = nullptr, *dh = nullptr, *dy = nullptr;   // N x 64
     double *gS1 = nullptr, *gS2 = nullptr;               // G x 64 per-graph sums
     float *dWt = nullptr;                // NT x (64 x 64 + 64) per-tile weight/bias gradient partials
+    double *dWc = nullptr;               // kGradChunks x (64 x 64 + 64) chunk sums of dWt
     char *arena = nullptr;
     size_t bytes = 0;
 };
