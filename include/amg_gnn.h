@@ -196,10 +196,25 @@ int amg_smooth_device(amg_ctx *ctx, int level, const double *d_b, double *d_u, i
 int amg_spmv_device(amg_ctx *ctx, int level, const double *d_x, double *d_y, void *stream);
 
 /* Relative validation metric of Sec. 3.3 on right-hand side b (host, n_0):
- * log10(||r_1^GNN|| / ||r_1^omega-J||) after one V-cycle from x = 0 with the
- * current pseudo-inverse smoother and with omega-Jacobi.  A value >= 0 means
- * the learned smoother does not beat Jacobi on this matrix. */
-int amg_judge(amg_ctx *ctx, const double *b, double *metric);
+ * log10(||r_n^GNN|| / ||r_n^omega-J||) after n = n_cycles V-cycles from x = 0
+ * with the current pseudo-inverse smoother and with omega-Jacobi (the paper
+ * compares residuals after cycle n+1; more than one cycle exposes smoothers
+ * that reduce the first residual well but converge slowly).  *metric is
+ * +inf when the learned smoother diverges, -inf when only Jacobi does.
+ * A value >= 0 means the learned smoother does not beat Jacobi.
+ * Errors: AMG_ERR_ARG (n_cycles outside 1..10000), AMG_ERR_STATE, AMG_ERR_CUDA. */
+int amg_judge(amg_ctx *ctx, const double *b, int n_cycles, double *metric);
+
+/* Judge and reroute (the fallback of the learned smoother).  Runs n_cycles
+ * (>= 4) V-cycles from x = 0 on b with each smoother and compares
+ *   m1 = log10(||r_n^GNN|| / ||r_n^J||)                       (Sec. 3.3) and
+ *   m2 = the same log-ratio for the reduction over the last n/4 cycles,
+ * which exposes smoothers that start well but converge slowly.  *metric =
+ * max(m1, m2) (+inf when the learned smoother diverges or alone stagnates).
+ * If it is not negative the context falls back to omega-Jacobi and
+ * amg_last_error reports the rerouting; *smoother receives the smoother in
+ * use afterwards.  metric/smoother may be NULL. */
+int amg_reroute(amg_ctx *ctx, const double *b, int n_cycles, double *metric, int *smoother);
 
 /* ------------------------------------------------------------------------
  * Measurement aids (no counterpart in the paper; used for roofline timing)
@@ -282,12 +297,16 @@ int gcin_trainer_backward(gcin_trainer *tr, const double *dc, double *dtheta_out
  * (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr. */
 int gcin_trainer_adam_step(gcin_trainer *tr, double lr, double max_norm);
 
-/* Loss of one problem (Sec. 3.3, N_vc = 1, u_0 = 0):
- * L = log10(||f - A u_1|| / ||f||), u_1 = one V-cycle of the pseudo-inverse
- * smoother with coefficients c (n_levels rows of 5) on f (host, n_0), and its
- * gradient dL/dc (host, n_levels rows of 5) from the hand-written adjoint of
- * the V-cycle.  Runs in the context's precision. */
-int amg_loss_grad(amg_ctx *ctx, const double *c, const double *f, double *loss, double *dc);
+/* Loss of one problem (Sec. 3.3, u_0 = 0) and its gradient:
+ *   L = sum_{n=1}^{n_vc} log10(||r_n|| / ||r_{n-1}||) = log10(||f - A u_nvc|| / ||f||),
+ * u_n = one V-cycle of the pseudo-inverse smoother with coefficients c
+ * (n_levels rows of 5) applied to u_{n-1}, f host (n_0); dL/dc (host,
+ * n_levels rows of 5, zero on the coarsest level) from the hand-written
+ * adjoint of the n_vc chained V-cycles.  n_vc = 1 is the paper's primary
+ * loss, n_vc > 1 its multi-V-cycle loss.  Runs in the context's precision.
+ * Errors: AMG_ERR_ARG (n_vc outside 1..64), AMG_ERR_STATE, AMG_ERR_DIVERGED
+ * (zero or non-finite residual), AMG_ERR_CUDA. */
+int amg_loss_grad(amg_ctx *ctx, const double *c, const double *f, int n_vc, double *loss, double *dc);
 
 #ifdef __cplusplus
 }

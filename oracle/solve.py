@@ -238,13 +238,21 @@ def vcycle_operator_apply(h: OHierarchy, r, nu1: int = 2, nu2: int = 2) -> np.nd
         return vcycle(h, r, torch.zeros_like(r), nu1, nu2).numpy()
 
 
-def relative_metric(h_gnn: OHierarchy, h_jac: OHierarchy, f, u0=None, nu1=2, nu2=2) -> float:
-    """log10(||r_{n+1}|| / ||r^{omega-J}_{n+1}||) after one cycle from u0."""
+def relative_metric(h_gnn: OHierarchy, h_jac: OHierarchy, f, u0=None, nu1=2, nu2=2, n_cycles: int = 1) -> float:
+    """log10(||r_n|| / ||r^{omega-J}_n||) after n_cycles V-cycles from u0 (Sec. 3.3).
+
+    The paper's metric compares the residuals after cycle n+1; n_cycles
+    chooses that cycle.  A non-finite GNN residual gives +inf.
+    """
     f = torch.as_tensor(np.asarray(f, dtype=np.float64))
     u = torch.zeros_like(f) if u0 is None else torch.as_tensor(np.asarray(u0, dtype=np.float64))
     with torch.no_grad():
-        ug = vcycle(h_gnn, f, u.clone(), nu1, nu2)
-        uj = vcycle(h_jac, f, u.clone(), nu1, nu2)
+        ug, uj = u.clone(), u.clone()
+        for _ in range(n_cycles):
+            ug = vcycle(h_gnn, f, ug, nu1, nu2)
+            uj = vcycle(h_jac, f, uj, nu1, nu2)
         rg = torch.linalg.vector_norm(f - mv(h_gnn.levels[0].A, ug))
         rj = torch.linalg.vector_norm(f - mv(h_jac.levels[0].A, uj))
+    if not bool(torch.isfinite(rg)):
+        return math.inf
     return float(torch.log10(rg / rj))

@@ -3,8 +3,9 @@
 Test infrastructure only.  FP64; gradients by autograd through the plain
 V-cycle of ``oracle.solve`` and the network of ``oracle.gcin``.
 
-* loss of one problem with N_vc = 1 and u_0 = 0 (Sec. 3.3):
-  L_m = log10(||r_1||_2 / ||r_0||_2), r_0 = f, r_1 = f - A u_1, u_1 = V-cycle(0, f);
+* loss of one problem with u_0 = 0 (Sec. 3.3, multi-V-cycle form):
+  L_m = sum_{n=1}^{N_vc} log10(||r_n||_2 / ||r_{n-1}||_2), r_n = f - A u_n,
+  u_n = V-cycle(u_{n-1}, f); N_vc = 1 is the primary loss;
 * batch loss = mean over problems (Algorithm 1 steps 7-12);
 * global-norm clipping to 1.0 (Table train_hyper) as g * min(1, 1/(||g|| + 1e-6))
   (reading; the paper gives only the max norm);
@@ -24,31 +25,38 @@ from .solve import DT, OHierarchy, mv, pseudo_inverse_values, vcycle
 LOG10 = math.log(10.0)
 
 
-def problem_loss(h: OHierarchy, coeffs: torch.Tensor, f, nu1: int = 2, nu2: int = 2) -> torch.Tensor:
+def problem_loss(h: OHierarchy, coeffs: torch.Tensor, f, nu1: int = 2, nu2: int = 2, n_vc: int = 1) -> torch.Tensor:
     """L_m for one problem; coeffs (n_levels, 5) may require grad."""
     f = torch.as_tensor(np.asarray(f, dtype=np.float64))
     for l, lv in enumerate(h.levels[:-1]):
         lv.M = pseudo_inverse_values(lv.A, coeffs[l], lv.s)
-    u1 = vcycle(h, f, torch.zeros_like(f), nu1, nu2)
-    r1 = f - mv(h.levels[0].A, u1)
-    return torch.log10(torch.linalg.vector_norm(r1) / torch.linalg.vector_norm(f))
+    A = h.levels[0].A
+    u = torch.zeros_like(f)
+    r_prev = torch.linalg.vector_norm(f)
+    L = 0.0
+    for _ in range(n_vc):
+        u = vcycle(h, f, u, nu1, nu2)
+        r = torch.linalg.vector_norm(f - mv(A, u))
+        L = L + torch.log10(r / r_prev)
+        r_prev = r
+    return L
 
 
-def loss_and_coeff_grad(h: OHierarchy, coeffs, f):
+def loss_and_coeff_grad(h: OHierarchy, coeffs, f, n_vc: int = 1):
     """(L_m, dL_m/dc) for one problem, c of shape (n_levels, 5)."""
     c = torch.as_tensor(np.asarray(coeffs, dtype=np.float64)).clone().requires_grad_(True)
-    L = problem_loss(h, c, f)
+    L = problem_loss(h, c, f, n_vc=n_vc)
     L.backward()
     return float(L.detach()), c.grad.numpy().copy()
 
 
-def batch_loss(theta: torch.Tensor, hierarchies, graphs_per_problem, rhs) -> torch.Tensor:
+def batch_loss(theta: torch.Tensor, hierarchies, graphs_per_problem, rhs, n_vc: int = 1) -> torch.Tensor:
     """Algorithm 1: batched inference over all levels, then per-problem losses, mean."""
     all_graphs = [g for gs in graphs_per_problem for g in gs]
     c_all = gcin.forward(theta, all_graphs)
     total, off = 0.0, 0
     for h, gs, f in zip(hierarchies, graphs_per_problem, rhs):
-        total = total + problem_loss(h, c_all[off:off + len(gs)], f)
+        total = total + problem_loss(h, c_all[off:off + len(gs)], f, n_vc=n_vc)
         off += len(gs)
     return total / len(hierarchies)
 

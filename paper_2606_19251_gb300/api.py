@@ -92,7 +92,8 @@ def _declare(L):
         "amg_vcycle_device": (I, [P, P, P, P]),
         "amg_smooth_device": (I, [P, I, P, P, I, P]),
         "amg_spmv_device": (I, [P, I, P, P, P]),
-        "amg_judge": (I, [P, pd, pd]),
+        "amg_judge": (I, [P, pd, I, pd]),
+        "amg_reroute": (I, [P, pd, I, pd, pi]),
         "gcin_trainer_create": (I, [C.POINTER(P), I, pf]),
         "gcin_trainer_destroy": (V, [P]),
         "gcin_trainer_last_error": (C.c_char_p, [P]),
@@ -100,7 +101,7 @@ def _declare(L):
         "gcin_trainer_forward": (I, [P, I, C.POINTER(P), pd]),
         "gcin_trainer_backward": (I, [P, pd, pd]),
         "gcin_trainer_adam_step": (I, [P, D, D]),
-        "amg_loss_grad": (I, [P, pd, pd, pd, pd]),
+        "amg_loss_grad": (I, [P, pd, pd, I, pd, pd]),
         "amg_kernel_launch": (I, [P, I, I, I, P, pd]),
         "amg_vcycle_bytes": (I, [P, pd]),
         "amg_launch_count": (LL, []),
@@ -120,7 +121,7 @@ def exported_symbols():
             "amg_load_hierarchy", "amg_num_levels", "amg_level_info", "amg_get_level", "amg_get_scales",
             "amg_set_jacobi", "amg_set_coeffs", "amg_get_smoother", "gnn_load_params", "gnn_predict_coeffs",
             "amg_solve", "amg_solve_device", "amg_vcycle_device", "amg_smooth_device", "amg_spmv_device",
-            "amg_judge", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
+            "amg_judge", "amg_reroute", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
             "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
             "gcin_trainer_adam_step", "amg_loss_grad", "amg_kernel_launch", "amg_vcycle_bytes",
             "amg_launch_count", "amg_residual_norm_noalloc"]
@@ -302,20 +303,28 @@ def amg_spmv_device(ctx, level, d_x, d_y, stream=None):
     return _check(ctx, lib().amg_spmv_device(ctx, level, _dev(d_x), _dev(d_y), _stream(stream)))
 
 
-def amg_judge(ctx, b) -> float:
+def amg_judge(ctx, b, n_cycles=1) -> float:
     b = np.ascontiguousarray(b, dtype=np.float64)
     m = C.c_double()
-    _check(ctx, lib().amg_judge(ctx, _dptr(b), C.byref(m)))
+    _check(ctx, lib().amg_judge(ctx, _dptr(b), int(n_cycles), C.byref(m)))
     return m.value
 
 
-def amg_loss_grad(ctx, c, f):
-    """(loss, dL/dc) of one V-cycle from zero (Sec. 3.3)."""
+def amg_reroute(ctx, b, n_cycles=10):
+    """(metric, smoother in use afterwards)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m, sm = C.c_double(), C.c_int()
+    _check(ctx, lib().amg_reroute(ctx, _dptr(b), int(n_cycles), C.byref(m), C.byref(sm)))
+    return m.value, sm.value
+
+
+def amg_loss_grad(ctx, c, f, n_vc=1):
+    """(loss, dL/dc) of n_vc V-cycles from zero (Sec. 3.3)."""
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, 5))
     f = np.ascontiguousarray(f, dtype=np.float64)
     loss = C.c_double()
     dc = np.zeros_like(c)
-    _check(ctx, lib().amg_loss_grad(ctx, _dptr(c), _dptr(f), C.byref(loss), _dptr(dc)))
+    _check(ctx, lib().amg_loss_grad(ctx, _dptr(c), _dptr(f), int(n_vc), C.byref(loss), _dptr(dc)))
     return loss.value, dc
 
 

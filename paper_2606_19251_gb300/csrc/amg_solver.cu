@@ -1137,10 +1137,10 @@ int amg_spmv_device(amg_ctx *c, int level, const double *d_x, double *d_y, void 
     return AMG_OK;
 }
 
-int amg_judge(amg_ctx *c, const double *b, double *metric) {
+int amg_judge(amg_ctx *c, const double *b, int n_cycles, double *metric) {
     if (!c) return AMG_ERR_ARG;
     c->err.clear();
-    if (!b || !metric) return ctx_fail(c, "NULL argument"), AMG_ERR_ARG;
+    if (!b || !metric || n_cycles < 1 || n_cycles > 10000) return ctx_fail(c, "bad argument"), AMG_ERR_ARG;
     if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
     if (!c->have_q) return ctx_fail(c, "no pseudo-inverse coefficients set"), AMG_ERR_STATE;
     CK(cudaSetDevice(c->opt.device));
@@ -1148,19 +1148,75 @@ int amg_judge(amg_ctx *c, const double *b, double *metric) {
     cudaStream_t s = c->stream;
     const int saved_iter = c->opt.max_iter;
     const int saved_sm = c->smoother;
-    double h_gnn[2] = {0, 0}, h_jac[2] = {0, 0};
-    int rc = AMG_OK;
-    c->opt.max_iter = 1;
+    std::vector<double> hg(n_cycles + 1, 0.0), hj(n_cycles + 1, 0.0);
+    int kg = 0, kj = 0, stg = AMG_OK, stj = AMG_OK, rc = AMG_OK;
+    c->opt.max_iter = n_cycles;
     for (int pass = 0; pass < 2 && rc != AMG_ERR_CUDA; ++pass) {
         c->smoother = pass == 0 ? AMG_SMOOTHER_GNN : AMG_SMOOTHER_JACOBI;
-        CK(cudaMemcpyAsync(c->db, b, sizeof(double) * n0, cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(c->dx, 0, sizeof(double) * n0, s));
-        rc = solve_dispatch(c, s, 0.0, nullptr, pass == 0 ? h_gnn : h_jac);
+        rc = ctx_cuda_check(c, cudaMemcpyAsync(c->db, b, sizeof(double) * n0, cudaMemcpyHostToDevice, s), "copy b");
+        if (!rc) rc = ctx_cuda_check(c, cudaMemsetAsync(c->dx, 0, sizeof(double) * n0, s), "zero x");
+        if (!rc) rc = solve_dispatch(c, s, 0.0, pass == 0 ? &kg : &kj, pass == 0 ? hg.data() : hj.data());
+        if (pass == 0) stg = rc; else stj = rc;
     }
     c->opt.max_iter = saved_iter;
     c->smoother = saved_sm;
-    if (rc == AMG_ERR_CUDA) return rc;
-    *metric = std::log10(h_gnn[1] / h_jac[1]);
+    if (rc == AMG_ERR_CUDA || stg == AMG_ERR_CUDA) return AMG_ERR_CUDA;
+    if (stg == AMG_ERR_DIVERGED) *metric = INFINITY;
+    else if (stj == AMG_ERR_DIVERGED) *metric = -INFINITY;
+    else {
+        const int m = std::min(kg, kj);
+        *metric = std::log10(hg[m] / hj[m]);
+    }
+    return AMG_OK;
+}
+
+int amg_reroute(amg_ctx *c, const double *b, int n_cycles, double *metric, int *smoother) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (!b || n_cycles < 4 || n_cycles > 10000) return ctx_fail(c, "bad argument (n_cycles >= 4)"), AMG_ERR_ARG;
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (!c->have_q) return ctx_fail(c, "no pseudo-inverse coefficients set"), AMG_ERR_STATE;
+    CK(cudaSetDevice(c->opt.device));
+    const int n0 = c->lev[0].n;
+    cudaStream_t s = c->stream;
+    const int saved_iter = c->opt.max_iter;
+    std::vector<double> h[2];
+    int k[2] = {0, 0}, st[2] = {AMG_OK, AMG_OK}, rc = AMG_OK;
+    c->opt.max_iter = n_cycles;
+    for (int pass = 0; pass < 2 && rc != AMG_ERR_CUDA; ++pass) {
+        c->smoother = pass == 0 ? AMG_SMOOTHER_GNN : AMG_SMOOTHER_JACOBI;
+        h[pass].assign(n_cycles + 1, 0.0);
+        rc = ctx_cuda_check(c, cudaMemcpyAsync(c->db, b, sizeof(double) * n0, cudaMemcpyHostToDevice, s), "copy b");
+        if (!rc) rc = ctx_cuda_check(c, cudaMemsetAsync(c->dx, 0, sizeof(double) * n0, s), "zero x");
+        if (!rc) rc = solve_dispatch(c, s, 0.0, &k[pass], h[pass].data());
+        st[pass] = rc;
+    }
+    c->opt.max_iter = saved_iter;
+    c->smoother = AMG_SMOOTHER_GNN;
+    if (rc == AMG_ERR_CUDA || st[0] == AMG_ERR_CUDA) return AMG_ERR_CUDA;
+    // metric 1: log10(||r_n^GNN|| / ||r_n^J||) (Sec. 3.3); metric 2: the same
+    // ratio for the reduction over the last quarter of the cycles, which
+    // exposes smoothers that start well but converge slowly
+    double m;
+    if (st[0] == AMG_ERR_DIVERGED) {
+        m = INFINITY;
+    } else if (st[1] == AMG_ERR_DIVERGED) {
+        m = -INFINITY;
+    } else {
+        const int n = std::min(k[0], k[1]);
+        const int q = std::max(1, n / 4);
+        const double m1 = std::log10(h[0][n] / h[1][n]);
+        const double m2 = (n > q) ? std::log10((h[0][n] / h[0][n - q]) / (h[1][n] / h[1][n - q])) : m1;
+        const bool stalled = (st[0] == AMG_ERR_STAGNATED && st[1] != AMG_ERR_STAGNATED);
+        m = stalled ? INFINITY : std::max(m1, m2);
+    }
+    if (metric) *metric = m;
+    if (!(m < 0.0)) {
+        rc = amg_set_jacobi(c, c->jac_omega);
+        if (rc) return rc;
+        c->err = "pseudo-inverse smoother rerouted to Jacobi (metric " + std::to_string(m) + ")";
+    }
+    if (smoother) *smoother = c->smoother;
     return AMG_OK;
 }
 
@@ -1521,30 +1577,38 @@ __global__ void k_sum_final(int np, const double *__restrict__ partial, double *
 }
 
 struct TrainBufs {
-    std::vector<double *> ck;      // per level: (nu1 + nu2) checkpoint vectors
+    int ncyc = 0, nsw = 0, nlev = 0;
+    std::vector<double *> ck;      // [cycle][level][sweep]: slot 0 = that cycle's b_l, k >= 1 = r of sweep k
     std::vector<double *> ubar, tmp, bbar, zero;
+    double *xu = nullptr;          // level-0 iterate of the multi-cycle loss
     double *dcoef = nullptr;       // n_levels x 5
     double *scal = nullptr;        // 4 doubles
     char *arena = nullptr;
+    double *slot(int cyc, int l, int k) const { return ck[(static_cast<size_t>(cyc) * nlev + l) * nsw + k]; }
 };
 
-int train_bufs(amg_ctx *c, TrainBufs &tb) {
+int train_bufs(amg_ctx *c, TrainBufs &tb, int ncyc) {
     const int nlev = static_cast<int>(c->lev.size());
-    const int nsw = c->opt.nu1 + c->opt.nu2;
+    const int nsw = std::max(1, c->opt.nu1 + c->opt.nu2);
+    tb.ncyc = ncyc;
+    tb.nsw = nsw;
+    tb.nlev = nlev;
     auto lay = [&](Planner &pl) {
-        tb.ck.assign(static_cast<size_t>(nlev) * std::max(1, nsw), nullptr);
+        tb.ck.assign(static_cast<size_t>(ncyc) * nlev * nsw, nullptr);
         tb.ubar.assign(nlev, nullptr);
         tb.tmp.assign(nlev, nullptr);
         tb.bbar.assign(nlev, nullptr);
         tb.zero.assign(nlev, nullptr);
         for (int l = 0; l < nlev; ++l) {
             const int n = c->lev[l].n;
-            for (int k = 0; k < nsw; ++k) tb.ck[static_cast<size_t>(l) * nsw + k] = pl.take<double>(n);
+            for (int q = 0; q < ncyc; ++q)
+                for (int k = 0; k < nsw; ++k) tb.ck[(static_cast<size_t>(q) * nlev + l) * nsw + k] = pl.take<double>(n);
             tb.ubar[l] = pl.take<double>(n);
             tb.tmp[l] = pl.take<double>(n);
             tb.bbar[l] = pl.take<double>(n);
             tb.zero[l] = pl.take<double>(n);
         }
+        tb.xu = pl.take<double>(c->lev[0].n);
         tb.dcoef = pl.take<double>(static_cast<size_t>(nlev) * 5);
         tb.scal = pl.take<double>(4);
     };
@@ -1560,7 +1624,7 @@ int train_bufs(amg_ctx *c, TrainBufs &tb) {
 }
 
 template <class T>
-T *fwd_level_ckpt(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
+T *fwd_level_ckpt(amg_ctx *c, TrainBufs &tb, int cyc, int l, cudaStream_t s) {
     DevLevel &L = c->lev[l];
     T *b = reinterpret_cast<T *>(L.vb), *u = reinterpret_cast<T *>(L.vu), *r = reinterpret_cast<T *>(L.vr);
     const int nlev = static_cast<int>(c->lev.size());
@@ -1569,7 +1633,8 @@ T *fwd_level_ckpt(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
         k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
         return u;
     }
-    auto ck = [&](int k) { return reinterpret_cast<T *>(tb.ck[static_cast<size_t>(l) * nsw + k]); };
+    auto ck = [&](int k) { return reinterpret_cast<T *>(tb.slot(cyc, l, k)); };
+    cudaMemcpyAsync(ck(0), b, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s);
     if (nu1 == 0) cudaMemsetAsync(u, 0, sizeof(T) * L.n, s);
     for (int k = 0; k < nu1; ++k) {
         if (k == 0) {
@@ -1581,12 +1646,13 @@ T *fwd_level_ckpt(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
     }
     L_resid<T>(L.A, b, u, r, s);
     L_spmv<T>(L.R, r, reinterpret_cast<T *>(c->lev[l + 1].vb), s);
-    T *e = fwd_level_ckpt<T>(c, tb, l + 1, s);
+    T *e = fwd_level_ckpt<T>(c, tb, cyc, l + 1, s);
     L_apply<T>(L.P, mvals<T>(L.P), e, u, 1, s);
     for (int k = nu1; k < nsw; ++k) {
         L_resid<T>(L.A, b, u, ck(k), s);
         L_apply<T>(L.A, qvals<T>(L), ck(k), u, 1, s);
     }
+    (void)nsw;
     return u;
 }
 
@@ -1625,7 +1691,7 @@ T *sweep_adjoint(amg_ctx *c, TrainBufs &tb, int l, T *ubar, T *spare, const T *r
 // Backward of the V-cycle on level l: tb.ubar[l] = dL/d(level output) in,
 // tb.bbar[l] = dL/d(level right-hand side) out.
 template <class T>
-void bwd_level(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
+void bwd_level(amg_ctx *c, TrainBufs &tb, int cyc, int l, cudaStream_t s) {
     DevLevel &L = c->lev[l];
     const int nlev = static_cast<int>(c->lev.size());
     const int nu1 = c->opt.nu1, nu2 = c->opt.nu2, nsw = nu1 + nu2;
@@ -1635,7 +1701,7 @@ void bwd_level(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
         k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, ub, bb); AMG_COUNT();
         return;
     }
-    auto ck = [&](int k) { return reinterpret_cast<const T *>(tb.ck[static_cast<size_t>(l) * nsw + k]); };
+    auto ck = [&](int k) { return reinterpret_cast<const T *>(tb.slot(cyc, l, k)); };
     cudaMemsetAsync(bb, 0, sizeof(T) * L.n, s);
     for (int k = nsw - 1; k >= nu1; --k) {
         T *nu = sweep_adjoint<T>(c, tb, l, ub, sp, ck(k), bb, s);
@@ -1644,7 +1710,7 @@ void bwd_level(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
     }
     // prolongation u += P e: ebar = P^T ubar = R ubar
     L_spmv<T>(L.R, ub, reinterpret_cast<T *>(tb.ubar[l + 1]), s);
-    bwd_level<T>(c, tb, l + 1, s);
+    bwd_level<T>(c, tb, cyc, l + 1, s);
     // restriction b_{l+1} = R (b - A u): rhobar = R^T bbar_{l+1} = P bbar_{l+1}
     T *rhobar = reinterpret_cast<T *>(L.vt);
     L_spmv<T>(L.P, reinterpret_cast<const T *>(tb.bbar[l + 1]), rhobar, s);
@@ -1657,24 +1723,36 @@ void bwd_level(amg_ctx *c, TrainBufs &tb, int l, cudaStream_t s) {
         ub = nu;
     }
     if (nu1 >= 1) {        // first sweep from zero: u = M b
-        coef_grad<T>(c, tb, l, ub, reinterpret_cast<const T *>(L.vb), s);
+        coef_grad<T>(c, tb, l, ub, ck(0), s);
         L_apply<T>(L.A, qvals<T>(L), ub, reinterpret_cast<T *>(L.vt), 0, s);
         k_add<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, bb, reinterpret_cast<const T *>(L.vt)); AMG_COUNT();
     }
 }
 
+// Multi-V-cycle loss (Sec. 3.3): u_n = u_{n-1} + B(f - A u_{n-1}) (the
+// stationary V-cycle in refinement form), L = sum_n log10(||r_n|| / ||r_{n-1}||)
+// = log10(||r_N|| / ||f||).  Backward: ubar_N = -A r_N / (ln10 ||r_N||^2);
+// for n = N..1: rbar = B^T ubar (level adjoint, accumulating dL/dc), ubar -= A rbar.
 template <class T>
-int loss_grad(amg_ctx *c, TrainBufs &tb, const double *f, double *loss, double *dc) {
+int loss_grad(amg_ctx *c, TrainBufs &tb, const double *f, int nvc, double *loss, double *dc) {
     cudaStream_t s = c->stream;
     DevLevel &L0 = c->lev[0];
     const int n0 = L0.n, nlev = static_cast<int>(c->lev.size());
+    T *fT = reinterpret_cast<T *>(tb.tmp[0]);
+    T *xu = reinterpret_cast<T *>(tb.xu);
+    T *b0 = reinterpret_cast<T *>(L0.vb);
     CK(cudaMemcpyAsync(c->db, f, sizeof(double) * n0, cudaMemcpyHostToDevice, s));
-    k_convert<double, T><<<grid_for(n0), kBlock, 0, s>>>(n0, c->db, reinterpret_cast<T *>(L0.vb)); AMG_COUNT();
-    T *u = fwd_level_ckpt<T>(c, tb, 0, s);
-    T *fT = reinterpret_cast<T *>(L0.vb), *r1 = reinterpret_cast<T *>(tb.tmp[0]);
-    L_resid<T>(L0.A, fT, u, r1, s);
+    k_convert<double, T><<<grid_for(n0), kBlock, 0, s>>>(n0, c->db, fT); AMG_COUNT();
+    CK(cudaMemsetAsync(xu, 0, sizeof(T) * n0, s));
+    for (int q = 0; q < nvc; ++q) {
+        L_resid<T>(L0.A, fT, xu, b0, s);          // r_{q} = f - A u_q -> level-0 right-hand side
+        T *e = fwd_level_ckpt<T>(c, tb, q, 0, s);
+        k_add<T><<<grid_for(n0), kBlock, 0, s>>>(n0, xu, e); AMG_COUNT();
+    }
+    T *rN = reinterpret_cast<T *>(L0.vr);
+    L_resid<T>(L0.A, fT, xu, rN, s);
     const int nb = std::min(grid_for(n0), kNumSMs * 8);
-    k_dot_partial<T><<<nb, kBlock, 0, s>>>(n0, r1, r1, c->partials); AMG_COUNT();
+    k_dot_partial<T><<<nb, kBlock, 0, s>>>(n0, rN, rN, c->partials); AMG_COUNT();
     k_sum_final<<<1, 1024, 0, s>>>(nb, c->partials, tb.scal); AMG_COUNT();
     k_dot_partial<T><<<nb, kBlock, 0, s>>>(n0, fT, fT, c->partials); AMG_COUNT();
     k_sum_final<<<1, 1024, 0, s>>>(nb, c->partials, tb.scal + 1); AMG_COUNT();
@@ -1685,12 +1763,24 @@ int loss_grad(amg_ctx *c, TrainBufs &tb, const double *f, double *loss, double *
     if (!(rr > 0.0) || !(ff > 0.0) || !std::isfinite(rr))
         return ctx_fail(c, "loss undefined: zero or non-finite residual"), AMG_ERR_DIVERGED;
     *loss = 0.5 * std::log10(rr / ff);
-    // dL/du = -A^T r1 / (ln10 ||r1||^2)
-    T *seed = reinterpret_cast<T *>(L0.vt);
-    k_scale_copy<T><<<grid_for(n0), kBlock, 0, s>>>(n0, seed, r1, 1.0 / (std::log(10.0) * rr)); AMG_COUNT();
-    L_resid<T>(L0.A, reinterpret_cast<const T *>(tb.zero[0]), seed, reinterpret_cast<T *>(tb.ubar[0]), s);
+    // ubar_N = -A (r_N / (ln10 ||r_N||^2)) into ubar[0].  The carried adjoint
+    // and its scratch use xu and vr of level 0, which the level adjoint never
+    // touches (it works in ubar/tmp/bbar and vt).
+    T *seed = xu;                                   // the forward iterate is no longer needed
+    T *ub0 = reinterpret_cast<T *>(tb.ubar[0]);
+    k_scale_copy<T><<<grid_for(n0), kBlock, 0, s>>>(n0, seed, rN, 1.0 / (std::log(10.0) * rr)); AMG_COUNT();
+    L_resid<T>(L0.A, reinterpret_cast<const T *>(tb.zero[0]), seed, ub0, s);
     CK(cudaMemsetAsync(tb.dcoef, 0, sizeof(double) * 5 * nlev, s));
-    bwd_level<T>(c, tb, 0, s);
+    T *uacc = rN;                                   // dL/du_q carried across cycles (r_N no longer needed)
+    CK(cudaMemcpyAsync(uacc, ub0, sizeof(T) * n0, cudaMemcpyDeviceToDevice, s));
+    for (int q = nvc - 1; q >= 0; --q) {
+        CK(cudaMemcpyAsync(ub0, uacc, sizeof(T) * n0, cudaMemcpyDeviceToDevice, s));   // ebar = ubar_{q+1}
+        bwd_level<T>(c, tb, q, 0, s);                                                // bbar[0] = rbar_q
+        if (q > 0) {
+            L_resid<T>(L0.A, uacc, reinterpret_cast<const T *>(tb.bbar[0]), seed, s);   // ubar_q = ubar - A rbar
+            std::swap(uacc, seed);
+        }
+    }
     CKL("V-cycle adjoint");
     CK(cudaMemcpyAsync(dc, tb.dcoef, sizeof(double) * 5 * nlev, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1699,18 +1789,19 @@ int loss_grad(amg_ctx *c, TrainBufs &tb, const double *f, double *loss, double *
 
 }  // namespace
 
-extern "C" int amg_loss_grad(amg_ctx *c, const double *coef, const double *f, double *loss, double *dc) {
+extern "C" int amg_loss_grad(amg_ctx *c, const double *coef, const double *f, int n_vc, double *loss, double *dc) {
     if (!c) return AMG_ERR_ARG;
     c->err.clear();
     if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
-    if (!coef || !f || !loss || !dc) return ctx_fail(c, "NULL argument"), AMG_ERR_ARG;
+    if (!coef || !f || !loss || !dc || n_vc < 1 || n_vc > 64) return ctx_fail(c, "bad argument"), AMG_ERR_ARG;
     CK(cudaSetDevice(c->opt.device));
     const int nlev = static_cast<int>(c->lev.size());
     int rc = set_coeffs_device(c, coef, nlev, c->stream);
     if (rc) return rc;
+    if (c->train && static_cast<TrainBufs *>(c->train)->ncyc < n_vc) train_bufs_free(c);
     if (!c->train) {
         TrainBufs *tb = new TrainBufs();
-        rc = train_bufs(c, *tb);
+        rc = train_bufs(c, *tb, n_vc);
         if (rc) {
             if (tb->arena) cudaFree(tb->arena);
             delete tb;
@@ -1719,8 +1810,8 @@ extern "C" int amg_loss_grad(amg_ctx *c, const double *coef, const double *f, do
         c->train = tb;
     }
     TrainBufs &tb = *static_cast<TrainBufs *>(c->train);
-    if (c->opt.precision == AMG_FP64) return loss_grad<double>(c, tb, f, loss, dc);
-    return loss_grad<float>(c, tb, f, loss, dc);
+    if (c->opt.precision == AMG_FP64) return loss_grad<double>(c, tb, f, n_vc, loss, dc);
+    return loss_grad<float>(c, tb, f, n_vc, loss, dc);
 }
 
 namespace amg {

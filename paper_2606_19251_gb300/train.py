@@ -4,14 +4,15 @@ Host-side loop only; every forward, adjoint and optimiser step runs in the
 library's CUDA kernels:
   1. batched GCIN inference over every level of every problem of the
      mini-batch (gcin_trainer_forward; Algorithm 1 steps 1-6);
-  2. per problem, one V-cycle from u_0 = 0 with the predicted smoothers and
-     the loss log10(||r_1|| / ||r_0||) with its gradient dL/dc from the
-     hand-written V-cycle adjoint (amg_loss_grad; steps 7-12);
+  2. per problem, N_vc V-cycles from u_0 = 0 with the predicted smoothers
+     and the loss sum_n log10(||r_n|| / ||r_{n-1}||), averaged over the
+     N_vc cycles, with its gradient dL/dc from the hand-written V-cycle
+     adjoint (amg_loss_grad; steps 7-12; N_vc = 1 is the primary loss);
   3. backward through the network of the batch-mean loss, global-norm
      clipping to 1.0 and Adam with lr 1e-3 (gcin_trainer_backward /
      gcin_trainer_adam_step; step 13).
-Validation uses the relative metric log10(||r^GNN|| / ||r^Jacobi||) after one
-V-cycle (Sec. 3.3); the best-validation parameters are kept (early stopping,
+Validation uses the relative metric log10(||r^GNN|| / ||r^Jacobi||) after
+`val_cycles` V-cycles (Sec. 3.3); the best-validation parameters are kept (early stopping,
 App. B.1) and the learning rate follows ReduceLROnPlateau (factor 0.1,
 patience 10; the factor and patience are readings).
 """
@@ -41,8 +42,9 @@ class Problem:
 
 
 class Trainer:
-    def __init__(self, theta0, device=0, lr=1e-3, max_norm=1.0, factor=0.1, patience=10):
+    def __init__(self, theta0, device=0, lr=1e-3, max_norm=1.0, factor=0.1, patience=10, n_vc=1, val_cycles=10):
         self.tr = P.gcin_trainer_create(theta0, device)
+        self.n_vc, self.val_cycles = n_vc, val_cycles
         self.lr, self.max_norm = lr, max_norm
         self.factor, self.patience = factor, patience
         self.best_val, self.best_theta, self.bad_epochs = math.inf, None, 0
@@ -54,9 +56,9 @@ class Trainer:
         dc = np.zeros_like(c)
         losses, row = [], 0
         for p, f in zip(problems, rhs):
-            L, g = P.amg_loss_grad(p.ctx, c[row:row + p.n_levels], f)
-            losses.append(L)
-            dc[row:row + p.n_levels] = g / len(problems)
+            L, g = P.amg_loss_grad(p.ctx, c[row:row + p.n_levels], f, self.n_vc)
+            losses.append(L / self.n_vc)
+            dc[row:row + p.n_levels] = g / (len(problems) * self.n_vc)
             row += p.n_levels
         if not np.all(np.isfinite(dc)):
             return float("nan")
@@ -74,7 +76,7 @@ class Trainer:
         for p, f in zip(problems, rhs):
             P.gnn_load_params(p.ctx, theta)
             P.gnn_predict_coeffs(p.ctx)
-            out.append(P.amg_judge(p.ctx, f))
+            out.append(P.amg_judge(p.ctx, f, self.val_cycles))
         return float(np.mean(out))
 
     def end_epoch(self, val):
@@ -93,13 +95,13 @@ class Trainer:
             self.tr = None
 
 
-def train(train_mats, val_mats, theta0, epochs=30, batch=5, seed=0, log=print, device=0):
+def train(train_mats, val_mats, theta0, epochs=30, batch=5, seed=0, log=print, device=0, n_vc=1, val_cycles=10):
     """Train on `train_mats`, validate on `val_mats`; returns (best theta, log rows)."""
     import workloads as W
     probs = [Problem(A, device=device) for A in train_mats]
     vals = [Problem(A, device=device) for A in val_mats]
     val_rhs = [W.rhs_uniform(10_000 + k, p.A.n_rows) for k, p in enumerate(vals)]
-    tr = Trainer(theta0, device=device)
+    tr = Trainer(theta0, device=device, n_vc=n_vc, val_cycles=val_cycles)
     rows = []
     try:
         val0 = tr.validate(vals, val_rhs)

@@ -3,7 +3,7 @@
 Training batch: 64 Delaunay finite-volume meshes of 2k-20k nodes cycling
 uniform / 10:1 graded / graded + anisotropic band (aspect <= 100) point
 sets (workloads.c3_batch, seed 0); validation: 8 more meshes of the same
-distribution (seed 1).  Algorithm 1 with N_vc = 1, mini-batch 5, Adam lr
+distribution (seed 1).  Algorithm 1 with the multi-V-cycle loss (N_vc = 3 by default), mini-batch 5, Adam lr
 1e-3, clipping 1.0, ReduceLROnPlateau, best-validation parameters kept
 (Table train_hyper).  Every forward/backward runs on the GPU through
 libamggnn.so.
@@ -29,6 +29,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=150)
     ap.add_argument("--batch", type=int, default=5)
     ap.add_argument("--meshes", type=int, default=64)
+    ap.add_argument("--nvc", type=int, default=3, help="V-cycles per loss (Sec. 3.3 multi-V-cycle loss)")
+    ap.add_argument("--val-cycles", type=int, default=10)
     ap.add_argument("--out", default=os.path.join(HERE, "gcin_c3.npy"))
     args = ap.parse_args()
     import workloads as W
@@ -40,11 +42,12 @@ def main():
     val = W.c3_batch(8, seed=1)
     print(f"meshes ready in {time.time() - t0:.1f}s: n = {[m.n_rows for m in mats[:8]]}...", flush=True)
     theta0 = W.gcin_init_params(0)
-    best, rows = train(mats, val, theta0, epochs=args.epochs, batch=args.batch,
-                       log=lambda r: print(json.dumps(r), flush=True))
+    best, rows = train(mats, val, theta0, epochs=args.epochs, batch=args.batch, n_vc=args.nvc,
+                       val_cycles=args.val_cycles, log=lambda r: print(json.dumps(r), flush=True))
     np.save(args.out, np.asarray(best, dtype=np.float32))
     with open(os.path.splitext(args.out)[0] + "_log.json", "w") as f:
-        json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "rows": rows,
+        json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "n_vc": args.nvc,
+                   "val_cycles": args.val_cycles, "rows": rows,
                    "seconds": time.time() - t0}, f, indent=1)
     print("wrote", args.out, flush=True)
 

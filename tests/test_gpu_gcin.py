@@ -116,17 +116,18 @@ def test_network_backward_parity():
             P.amg_destroy(c_)
 
 
+@pytest.mark.parametrize("nvc", [1, 3])
 @pytest.mark.parametrize("prec,tol", [(P.AMG_FP64, 1e-10), (P.AMG_FP32_IN_FP64, 1e-4)])
 @pytest.mark.parametrize("name", ["c1_64", "band_8k"])
-def test_loss_and_adjoint_parity(name, prec, tol):
+def test_loss_and_adjoint_parity(name, prec, tol, nvc):
     A = MATS[name]()
     levels = OS.build_hierarchy(A)
     c = np.array([[0.6 + 0.01 * l, 0.03, -0.01, -0.15, 0.02] for l in range(len(levels))])
     f = W.rhs_uniform(9, A.n_rows)
-    Lref, dref = OT.loss_and_coeff_grad(O.OHierarchy.of(levels), c, f)
+    Lref, dref = OT.loss_and_coeff_grad(O.OHierarchy.of(levels), c, f, n_vc=nvc)
     ctx = ctx_from_oracle(levels, prec)
     try:
-        L, dc = P.amg_loss_grad(ctx, c, f)
+        L, dc = P.amg_loss_grad(ctx, c, f, nvc)
         assert abs(L - Lref) <= tol * abs(Lref)
         assert np.abs(dc - dref).max() <= tol * np.abs(dref).max()
         assert np.all(dc[-1] == 0)
@@ -142,14 +143,14 @@ def test_adjoint_matches_finite_differences():
     try:
         nl = P.amg_num_levels(ctx)
         c = c[:nl]
-        L, dc = P.amg_loss_grad(ctx, c, f)
+        L, dc = P.amg_loss_grad(ctx, c, f, 2)
         eps = 1e-6
         for l in range(nl - 1):
             for k in range(5):
                 cp, cm = c.copy(), c.copy()
                 cp[l, k] += eps
                 cm[l, k] -= eps
-                fd = (P.amg_loss_grad(ctx, cp, f)[0] - P.amg_loss_grad(ctx, cm, f)[0]) / (2 * eps)
+                fd = (P.amg_loss_grad(ctx, cp, f, 2)[0] - P.amg_loss_grad(ctx, cm, f, 2)[0]) / (2 * eps)
                 assert abs(fd - dc[l, k]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(dc).max()), (l, k, fd, dc[l, k])
     finally:
         P.amg_destroy(ctx)

@@ -251,15 +251,39 @@ def test_device_solve_matches_host_solve(cases):
         P.amg_destroy(ctx)
 
 
-def test_judge_matches_oracle(cases):
+@pytest.mark.parametrize("n_cycles", [1, 4])
+def test_judge_matches_oracle(cases, n_cycles):
     A, levels = cases["band_4k"]
     coeffs = [COEFFS] * len(levels)
     b = W.rhs_uniform(6, A.n_rows)
-    ref = O.relative_metric(oracle_hier(levels, "pinv", coeffs), oracle_hier(levels), b)
+    ref = O.relative_metric(oracle_hier(levels, "pinv", coeffs), oracle_hier(levels), b, n_cycles=n_cycles)
     ctx = ctx_from_oracle(levels)
     try:
         P.amg_set_coeffs(ctx, coeffs)
-        m = P.amg_judge(ctx, b)
+        m = P.amg_judge(ctx, b, n_cycles)
         assert abs(m - ref) < 1e-10
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_reroute_falls_back_to_jacobi(cases):
+    A, levels = cases["graded_5k"]
+    b = W.rhs_uniform(7, A.n_rows)
+    ctx = ctx_setup(A, P.AMG_FP32_IN_FP64)
+    try:
+        P.amg_set_coeffs(ctx, [[3.0, 0, 0, 0, 0]] * len(levels))      # unstable smoother
+        m, sm = P.amg_reroute(ctx, b, 6)
+        assert m > 0 and sm == P.AMG_SMOOTHER_JACOBI
+        assert "rerouted" in P.amg_last_error(ctx)
+        st, x, hist = P.amg_solve(ctx, b)
+        assert st == P.AMG_OK
+        coeffs = [[0.75, 0, 0, 0, 0]] * len(levels)                   # mildly better than 2/3
+        P.amg_set_coeffs(ctx, coeffs)
+        m2, sm2 = P.amg_reroute(ctx, b, 8)
+        hg = O.solve(oracle_hier(levels, "pinv", coeffs), b, tol=0.0, max_iter=8).history
+        hj = O.solve(oracle_hier(levels), b, tol=0.0, max_iter=8).history
+        m_ref = max(np.log10(hg[8] / hj[8]), np.log10((hg[8] / hg[6]) / (hj[8] / hj[6])))
+        assert abs(m2 - m_ref) < 1e-4
+        assert (sm2 == P.AMG_SMOOTHER_GNN) == (m_ref < 0)
     finally:
         P.amg_destroy(ctx)

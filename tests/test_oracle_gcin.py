@@ -144,3 +144,37 @@ def test_jacobi_loss_equals_first_cycle_reduction():
     hj.set_jacobi()
     res = O.solve(hj, f, tol=0.0, max_iter=1)
     assert abs(L - np.log10(res.history[1])) < 1e-12
+
+
+def test_multi_cycle_loss_telescopes_and_matches_finite_differences():
+    # Sec. 3.3: sum_n log10(||r_n|| / ||r_{n-1}||) = log10(||r_N|| / ||r_0||);
+    # pinned against the solve's residual history and against FD.
+    levels, h, f = _small_problem(4)
+    c = np.array([[0.6, 0.02, -0.01, -0.12, 0.02]] * len(levels))
+    L3, d3 = T.loss_and_coeff_grad(h, c, f, n_vc=3)
+    hp = O.OHierarchy.of(levels)
+    hp.set_pseudo_inverse(c)
+    res = O.solve(hp, f, tol=0.0, max_iter=3)
+    assert abs(L3 - np.log10(res.history[3])) < 1e-12
+    eps = 1e-6
+    for l, k in ((0, 0), (0, 3), (1, 1), (len(levels) - 2, 4)):
+        cp, cm = c.copy(), c.copy()
+        cp[l, k] += eps
+        cm[l, k] -= eps
+        with torch.no_grad():
+            fd = (float(T.problem_loss(h, torch.from_numpy(cp), f, n_vc=3)) -
+                  float(T.problem_loss(h, torch.from_numpy(cm), f, n_vc=3))) / (2 * eps)
+        assert abs(fd - d3[l, k]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_relative_metric_after_n_cycles():
+    levels, h, f = _small_problem(5)
+    hj = O.OHierarchy.of(levels)
+    hj.set_jacobi()
+    hg = O.OHierarchy.of(levels)
+    hg.set_pseudo_inverse([[2.0 / 3.0, 0, 0, 0, 0]] * len(levels))
+    for n in (1, 4):
+        assert abs(O.relative_metric(hg, hj, f, n_cycles=n)) < 1e-10
+    hb = O.OHierarchy.of(levels)
+    hb.set_pseudo_inverse([[3.0, 0, 0, 0, 0]] * len(levels))   # unstable smoother
+    assert O.relative_metric(hb, hj, f, n_cycles=6) > 0.5
