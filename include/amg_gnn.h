@@ -216,6 +216,13 @@ int amg_judge(amg_ctx *ctx, const double *b, int n_cycles, double *metric);
  * use afterwards.  metric/smoother may be NULL. */
 int amg_reroute(amg_ctx *ctx, const double *b, int n_cycles, double *metric, int *smoother);
 
+/* When amg_reroute keeps the learned smoother it also arms an in-solve check:
+ * if some 10 consecutive V-cycles of a later solve reduce the residual by
+ * less than half the decades Jacobi gained over 10 cycles in the probe, the
+ * solve switches to Jacobi and continues from the current iterate (history
+ * and V-cycle count continue).  Returns 1 if the last solve on ctx did so. */
+int amg_last_solve_rerouted(const amg_ctx *ctx);
+
 /* ------------------------------------------------------------------------
  * Measurement aids (no counterpart in the paper; used for roofline timing)
  * ------------------------------------------------------------------------ */

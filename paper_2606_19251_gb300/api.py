@@ -94,6 +94,7 @@ def _declare(L):
         "amg_spmv_device": (I, [P, I, P, P, P]),
         "amg_judge": (I, [P, pd, I, pd]),
         "amg_reroute": (I, [P, pd, I, pd, pi]),
+        "amg_last_solve_rerouted": (I, [P]),
         "gcin_trainer_create": (I, [C.POINTER(P), I, pf]),
         "gcin_trainer_destroy": (V, [P]),
         "gcin_trainer_last_error": (C.c_char_p, [P]),
@@ -121,7 +122,7 @@ def exported_symbols():
             "amg_load_hierarchy", "amg_num_levels", "amg_level_info", "amg_get_level", "amg_get_scales",
             "amg_set_jacobi", "amg_set_coeffs", "amg_get_smoother", "gnn_load_params", "gnn_predict_coeffs",
             "amg_solve", "amg_solve_device", "amg_vcycle_device", "amg_smooth_device", "amg_spmv_device",
-            "amg_judge", "amg_reroute", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
+            "amg_judge", "amg_reroute", "amg_last_solve_rerouted", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
             "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
             "gcin_trainer_adam_step", "amg_loss_grad", "amg_kernel_launch", "amg_vcycle_bytes",
             "amg_launch_count", "amg_residual_norm_noalloc"]
@@ -310,12 +311,16 @@ def amg_judge(ctx, b, n_cycles=1) -> float:
     return m.value
 
 
-def amg_reroute(ctx, b, n_cycles=10):
+def amg_reroute(ctx, b, n_cycles=30):
     """(metric, smoother in use afterwards)."""
     b = np.ascontiguousarray(b, dtype=np.float64)
     m, sm = C.c_double(), C.c_int()
     _check(ctx, lib().amg_reroute(ctx, _dptr(b), int(n_cycles), C.byref(m), C.byref(sm)))
     return m.value, sm.value
+
+
+def amg_last_solve_rerouted(ctx) -> bool:
+    return bool(lib().amg_last_solve_rerouted(ctx))
 
 
 def amg_loss_grad(ctx, c, f, n_vc=1):

@@ -131,6 +131,95 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
     if (row < n && lane == 0) uout[row] = uin[row] + jac[row] * (b[row] - acc);
 }
 
+// Single-pass pseudo-inverse sweep on latency-optimised levels:
+// u_out = u_in + w - (M A) u_in  (= u_in + M (b - A u_in), with w = M b)
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_ma_sweep(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                     const T *__restrict__ ma, const T *__restrict__ w,
+                                                     const T *__restrict__ uin, T *__restrict__ uout) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) {
+        const int e = rp[row + 1];
+        for (int p = rp[row] + lane; p < e; p += TPR) acc += ma[p] * uin[col[p]];
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) uout[row] = uin[row] + (w[row] - acc);
+}
+
+// First sweep from zero that also keeps w = M b: u = w = M b
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_apply_w(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                    const T *__restrict__ m, const T *__restrict__ b,
+                                                    T *__restrict__ u, T *__restrict__ w) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) {
+        const int e = rp[row + 1];
+        for (int p = rp[row] + lane; p < e; p += TPR) acc += m[p] * b[col[p]];
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) {
+        u[row] = acc;
+        w[row] = acc;
+    }
+}
+
+// Fused residual + restriction with the precomputed product R A:
+// b_c = R (b - A u) = R b - (R A) u, two flat gathers per coarse row.
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_resid_restrict(int nc, const int *__restrict__ rrp,
+                                                           const int *__restrict__ rcol, const T *__restrict__ rv,
+                                                           const int *__restrict__ sp, const int *__restrict__ scol,
+                                                           const T *__restrict__ sv, const T *__restrict__ b,
+                                                           const T *__restrict__ u, T *__restrict__ bc) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < nc) {
+        for (int p = rrp[row] + lane; p < rrp[row + 1]; p += TPR) acc += rv[p] * b[rcol[p]];
+        for (int p = sp[row] + lane; p < sp[row + 1]; p += TPR) acc -= sv[p] * u[scol[p]];
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < nc && lane == 0) bc[row] = acc;
+}
+
+// Two Jacobi sweeps from zero in one pass: u = j b + j (b - A (j b)), j = omega/a_ii
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                          const T *__restrict__ a, const T *__restrict__ jac,
+                                                          const T *__restrict__ b, T *__restrict__ u) {
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) {
+        const int e = rp[row + 1];
+        for (int p = rp[row] + lane; p < e; p += TPR) {
+            const int j = col[p];
+            acc += a[p] * (jac[j] * b[j]);
+        }
+    }
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) {
+        const T u1 = jac[row] * b[row];
+        u[row] = u1 + jac[row] * (b[row] - acc);
+    }
+}
+
+// (M A) values from the pair list (FP64), with the V-cycle-precision copy
+__global__ void k_assemble_ma(int nnz, const int *__restrict__ pp, const int *__restrict__ pq_p,
+                              const int *__restrict__ pq_q, const double *__restrict__ q64,
+                              const double *__restrict__ a64, double *__restrict__ ma64, float *__restrict__ ma32) {
+    const int e = blockIdx.x * kBlock + threadIdx.x;
+    if (e >= nnz) return;
+    double acc = 0.0;
+    for (int t = pp[e]; t < pp[e + 1]; ++t) acc = fma(q64[pq_p[t]], a64[pq_q[t]], acc);
+    ma64[e] = acc;
+    ma32[e] = static_cast<float>(acc);
+}
+
 // u = (omega/a_ii) b  (first Jacobi sweep from u = 0)
 template <class T>
 __global__ void k_scale(int n, const T *__restrict__ jac, const T *__restrict__ b, T *__restrict__ u) {
@@ -226,13 +315,20 @@ __global__ void __launch_bounds__(kBlock) k_sqnorm_partial(int n, const double *
     block_partial(sq, partial);
 }
 
-__global__ void k_state_init(SolveState *st, double tol, int max_iter) {
+__global__ void k_state_init(SolveState *st, double tol, int max_iter, double stall) {
     st->k = 0;
     st->status = kRunning;
     st->max_iter = max_iter;
     st->tol = tol;
     st->bnorm = 1.0;
     st->r0 = 0.0;
+    st->stall = stall;
+}
+
+// Continue a stalled solve with another smoother (history and count go on).
+__global__ void k_state_continue(SolveState *st) {
+    st->status = kRunning;
+    st->stall = 0.0;
 }
 
 // Sum the partials in a fixed order.  mode 0: ||b||.  mode 1: residual
@@ -267,6 +363,7 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ 
     } else {
         if (!isfinite(nrm) || nrm > 1e3 * st->r0) status = AMG_ERR_DIVERGED;
         else if (rel <= st->tol) status = AMG_OK;
+        else if (k >= 10 && st->stall > 0.0 && rel > st->stall * hist[k - 10]) status = kStalled;
         else if (k >= 10 && rel > 0.99 * hist[k - 10]) status = AMG_ERR_STAGNATED;
         else if (k >= st->max_iter) status = AMG_ERR_MAXITER;
     }
@@ -457,6 +554,26 @@ template <class T> struct Launch {
             A.nr, A.rp, A.col, mvals<T>(A), jac, b, uin, uout); AMG_COUNT();
     }
     template <int TPR>
+    static void ma_sweep(const DevMat &MA, const T *w, const T *uin, T *uout, cudaStream_t s) {
+        k_ma_sweep<T, TPR><<<grid_for(static_cast<long long>(MA.nr) * TPR), kBlock, 0, s>>>(
+            MA.nr, MA.rp, MA.col, mvals<T>(MA), w, uin, uout); AMG_COUNT();
+    }
+    template <int TPR>
+    static void apply_w(const DevMat &A, const T *m, const T *b, T *u, T *w, cudaStream_t s) {
+        k_apply_w<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(A.nr, A.rp, A.col, m, b,
+                                                                                           u, w); AMG_COUNT();
+    }
+    template <int TPR>
+    static void resid_restrict(const DevMat &R, const DevMat &RA, const T *b, const T *u, T *bc, cudaStream_t s) {
+        k_resid_restrict<T, TPR><<<grid_for(static_cast<long long>(R.nr) * TPR), kBlock, 0, s>>>(
+            R.nr, R.rp, R.col, mvals<T>(R), RA.rp, RA.col, mvals<T>(RA), b, u, bc); AMG_COUNT();
+    }
+    template <int TPR>
+    static void jacobi_first2(const DevMat &A, const T *jac, const T *b, T *u, cudaStream_t s) {
+        k_jacobi_first2<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(
+            A.nr, A.rp, A.col, mvals<T>(A), jac, b, u); AMG_COUNT();
+    }
+    template <int TPR>
     static void outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nblk,
                       cudaStream_t s) {
         k_outer_resid<T, TPR><<<nblk, kBlock, 0, s>>>(A.nr, A.rp, A.col, A.v64, b, x, rT, partial); AMG_COUNT();
@@ -515,6 +632,77 @@ static T *smooth(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *alt, 
     return cur;
 }
 
+// Coarsest solve: one warp with a lane per row when n <= 32, else k_coarse.
+template <class T>
+__global__ void __launch_bounds__(32) k_coarse_warp(int n, const double *__restrict__ Linv,
+                                                    const double *__restrict__ LinvT, const T *__restrict__ b,
+                                                    T *__restrict__ u) {
+    __shared__ double sb[32], sy[32];
+    const int i = threadIdx.x;
+    if (i < n) sb[i] = static_cast<double>(b[i]);
+    __syncwarp();
+    double y = 0.0;
+    if (i < n)
+        for (int k = 0; k <= i; ++k) y = fma(Linv[i * n + k], sb[k], y);
+    if (i < n) sy[i] = y;
+    __syncwarp();
+    double x = 0.0;
+    if (i < n)
+        for (int k = i; k < n; ++k) x = fma(LinvT[i * n + k], sy[k], x);
+    if (i < n) u[i] = static_cast<T>(x);
+}
+
+template <class T>
+static void launch_coarse(amg_ctx *c, const T *b, T *u, cudaStream_t s) {
+    if (c->nL <= 32) {
+        k_coarse_warp<T><<<1, 32, 0, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
+    } else {
+        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
+    }
+}
+
+// Smoothing on a latency-optimised level: every pseudo-inverse sweep is one
+// pass with M A (ping-pong between cur and alt); the first sweep from zero
+// also keeps w = M b.  Jacobi fuses its first two sweeps from zero.
+template <class T>
+static T *smooth_fast(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *alt, int nsweeps, bool zero_init,
+                      bool &have_w) {
+    const DevLevel &L = c->lev[l];
+    const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
+    T *w = reinterpret_cast<T *>(L.vw);
+    if (nsweeps == 0) {
+        if (zero_init) cudaMemsetAsync(cur, 0, sizeof(T) * L.n, s);
+        return cur;
+    }
+    int k = 0;
+    if (zero_init) {
+        if (gnn) {
+            TPR_DISPATCH(L.A.tpr, Launch<T>::template apply_w, L.A, qvals<T>(L), b, cur, w, s);
+            have_w = true;
+            k = 1;
+        } else if (nsweeps >= 2) {
+            TPR_DISPATCH(L.A.tpr, Launch<T>::template jacobi_first2, L.A, jvals<T>(L), b, cur, s);
+            k = 2;
+        } else {
+            k_scale<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, jvals<T>(L), b, cur); AMG_COUNT();
+            k = 1;
+        }
+    }
+    if (gnn && !have_w) {
+        L_apply<T>(L.A, qvals<T>(L), b, w, 0, s);
+        have_w = true;
+    }
+    for (; k < nsweeps; ++k) {
+        if (gnn) {
+            TPR_DISPATCH(L.MA.tpr, Launch<T>::template ma_sweep, L.MA, w, cur, alt, s);
+        } else {
+            L_jacobi<T>(L.A, jvals<T>(L), b, cur, alt, s);
+        }
+        std::swap(cur, alt);
+    }
+    return cur;
+}
+
 // One V-cycle on level l with right-hand side lev[l].vb; returns the result buffer.
 template <class T>
 static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
@@ -525,13 +713,23 @@ static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
     T *t = reinterpret_cast<T *>(L.vt);
     const int nlev = static_cast<int>(c->lev.size());
     if (l == nlev - 1) {
-        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
+        launch_coarse<T>(c, b, u, s);
         return u;
+    }
+    T *bc = reinterpret_cast<T *>(c->lev[l + 1].vb);
+    if (L.fast) {
+        bool have_w = false;
+        T *cur = smooth_fast<T>(c, l, s, b, u, t, c->opt.nu1, true, have_w);
+        T *alt = (cur == u) ? t : u;
+        TPR_DISPATCH(L.RA.tpr, Launch<T>::template resid_restrict, L.R, L.RA, b, cur, bc, s);
+        T *ec = vcycle_level<T>(c, l + 1, s);
+        L_apply<T>(L.P, mvals<T>(L.P), ec, cur, 1, s);
+        return smooth_fast<T>(c, l, s, b, cur, alt, c->opt.nu2, false, have_w);
     }
     T *cur = smooth<T>(c, l, s, b, u, t, r, c->opt.nu1, true);
     T *alt = (cur == u) ? t : u;
     L_resid<T>(L.A, b, cur, r, s);
-    L_spmv<T>(L.R, r, reinterpret_cast<T *>(c->lev[l + 1].vb), s);
+    L_spmv<T>(L.R, r, bc, s);
     T *ec = vcycle_level<T>(c, l + 1, s);
     L_apply<T>(L.P, mvals<T>(L.P), ec, cur, 1, s);
     return smooth<T>(c, l, s, b, cur, alt, r, c->opt.nu2, false);
@@ -551,7 +749,8 @@ template <class T>
 static void enqueue_init(amg_ctx *c, cudaStream_t s, double tol, int max_iter) {
     const int n0 = c->lev[0].n;
     const int nb = std::min(grid_for(n0), kNumSMs * 8);
-    k_state_init<<<1, 1, 0, s>>>(c->state, tol, max_iter); AMG_COUNT();
+    const double stall = (c->smoother == AMG_SMOOTHER_GNN) ? c->stall_ratio : 0.0;
+    k_state_init<<<1, 1, 0, s>>>(c->state, tol, max_iter, stall); AMG_COUNT();
     k_sqnorm_partial<<<nb, kBlock, 0, s>>>(n0, c->db, c->partials); AMG_COUNT();
     k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 0, 0, 0); AMG_COUNT();
     enqueue_outer_residual<T>(c, s);
@@ -624,8 +823,24 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
     CK(cudaGraphLaunch(G.exec, s));
     CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const int nh = c->h_state->k;
+    int nh = c->h_state->k;
     g_launches.fetch_add(1 + static_cast<long long>(nh - 1) * G.body_kernels);
+    c->last_rerouted = 0;
+    if (c->h_state->status == kStalled) {
+        // the learned smoother stopped converging: reroute to Jacobi and go on
+        // from the current iterate (Sec. 3.3 fallback)
+        c->smoother = AMG_SMOOTHER_JACOBI;
+        c->last_rerouted = 1;
+        rc = ensure_graph<T>(c);
+        if (rc) return rc;
+        k_state_continue<<<1, 1, 0, s>>>(c->state); AMG_COUNT();
+        const SolveGraph &GJ = c->sgraph[AMG_SMOOTHER_JACOBI];
+        CK(cudaGraphLaunch(GJ.exec, s));
+        CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        g_launches.fetch_add(1 + static_cast<long long>(c->h_state->k - nh) * GJ.body_kernels);
+        nh = c->h_state->k;
+    }
     if (n_vc) *n_vc = nh - 1;
     if (hist) CK(cudaMemcpyAsync(hist, c->hist, sizeof(double) * nh, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -680,6 +895,15 @@ static void layout(amg_ctx *c, Planner &pl) {
         L.q32 = pl.take<float>(std::max(1, L.A.nnz));
         L.j64 = pl.take<double>(L.n);
         L.j32 = pl.take<float>(L.n);
+        L.fast = H.fast;
+        if (H.fast) {
+            layout_mat(pl, L.MA, H.MA);
+            layout_mat(pl, L.RA, H.RA);
+            L.pp = pl.take<int>(H.pair_ptr.size());
+            L.pq_p = pl.take<int>(std::max<size_t>(1, H.pair_p.size()));
+            L.pq_q = pl.take<int>(std::max<size_t>(1, H.pair_q.size()));
+        }
+        L.vw = pl.take<double>(L.n);
         L.vb = pl.take<double>(L.n);
         L.vu = pl.take<double>(L.n);
         L.vr = pl.take<double>(L.n);
@@ -711,9 +935,38 @@ static int upload_mat(amg_ctx *c, const DevMat &m, const HostCSR &h, cudaStream_
     return AMG_OK;
 }
 
+// Levels whose M A pair list stays small are latency-bound at any size this
+// library meets (their working set sits in the 129 MB L2): they take the
+// single-pass sweeps and the fused residual + restriction.
+static const long long kFastPairs = 8LL << 20;
+
+static void plan_fast_levels(amg_ctx *c) {
+    const int nlev = static_cast<int>(c->host.size());
+    for (int l = 0; l < nlev; ++l) {
+        HostLevel &H = c->host[l];
+        H.fast = false;
+        H.MA = HostCSR{};
+        H.RA = HostCSR{};
+        H.pair_ptr.clear();
+        H.pair_p.clear();
+        H.pair_q.clear();
+        if (l == nlev - 1) continue;
+        long long pairs = 0;
+        for (int k = 0; k < H.A.n_rows; ++k) {
+            const long long d = H.A.rp[k + 1] - H.A.rp[k];
+            pairs += d * d;
+        }
+        if (pairs > kFastPairs) continue;
+        product_pattern(H.A, H.MA, H.pair_ptr, H.pair_p, H.pair_q);
+        H.RA = spgemm(H.R, H.A);
+        H.fast = true;
+    }
+}
+
 static int upload(amg_ctx *c) {
     free_device(c);
     ++c->hier_version;
+    plan_fast_levels(c);
     Planner pl;
     layout(c, pl);
     c->arena_bytes = pl.off;
@@ -733,6 +986,15 @@ static int upload(amg_ctx *c) {
         if (l < nlev - 1) {
             if ((rc = upload_mat(c, L.P, H.P, s))) return rc;
             if ((rc = upload_mat(c, L.R, H.R, s))) return rc;
+        }
+        if (L.fast) {
+            if ((rc = upload_mat(c, L.MA, H.MA, s))) return rc;
+            if ((rc = upload_mat(c, L.RA, H.RA, s))) return rc;
+            CK(cudaMemcpyAsync(L.pp, H.pair_ptr.data(), sizeof(int) * H.pair_ptr.size(), cudaMemcpyHostToDevice, s));
+            if (!H.pair_p.empty()) {
+                CK(cudaMemcpyAsync(L.pq_p, H.pair_p.data(), sizeof(int) * H.pair_p.size(), cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(L.pq_q, H.pair_q.data(), sizeof(int) * H.pair_q.size(), cudaMemcpyHostToDevice, s));
+            }
         }
         k_extract_diag<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag); AMG_COUNT();
         const int nb = std::min(grid_for(L.n), kNumSMs * 8);
@@ -969,10 +1231,15 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
             if (!std::isfinite(q[k])) return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
         k_assemble_q<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.bx, L.bw, q[0], q[1], q[2], q[3],
                                                       q[4], L.q64, L.q32); AMG_COUNT();
+        if (L.fast) {
+            k_assemble_ma<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q64, L.A.v64,
+                                                                L.MA.v64, L.MA.v32); AMG_COUNT();
+        }
     }
     (void)n_rows;
     CKL("assemble pseudo-inverse");
     c->have_q = true;
+    c->stall_ratio = 0.0;
     c->smoother = AMG_SMOOTHER_GNN;
     return AMG_OK;
 }
@@ -1040,6 +1307,7 @@ int amg_solve(amg_ctx *c, const double *b, double *x, double rtol, int *n_vc, do
     CK(cudaMemcpyAsync(x, c->dx, sizeof(double) * n0, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (rc != AMG_OK) c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
+    else if (c->last_rerouted) c->err = "learned smoother stalled; solve finished with Jacobi (rerouted)";
     return rc;
 }
 
@@ -1060,6 +1328,7 @@ int amg_solve_device(amg_ctx *c, const double *d_b, double *d_x, double rtol, vo
     CK(cudaMemcpyAsync(d_x, c->dx, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     if (rc != AMG_OK) c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
+    else if (c->last_rerouted) c->err = "learned smoother stalled; solve finished with Jacobi (rerouted)";
     return rc;
 }
 
@@ -1211,6 +1480,13 @@ int amg_reroute(amg_ctx *c, const double *b, int n_cycles, double *metric, int *
         m = stalled ? INFINITY : std::max(m1, m2);
     }
     if (metric) *metric = m;
+    if (m < 0.0 && st[1] != AMG_ERR_DIVERGED) {
+        // arm the in-solve check: over any 10 cycles the learned smoother must
+        // gain at least half the decades Jacobi gained in this probe
+        const int n = k[1], q = std::max(1, n / 4);
+        const double rate10 = std::pow(h[1][n] / h[1][n - q], 10.0 / q);
+        c->stall_ratio = (rate10 > 0.0 && rate10 < 1.0) ? std::sqrt(rate10) : 0.0;
+    }
     if (!(m < 0.0)) {
         rc = amg_set_jacobi(c, c->jac_omega);
         if (rc) return rc;
@@ -1248,11 +1524,37 @@ double smooth_bytes(const amg_ctx *c, const DevLevel &L, int tb, int nsweeps, bo
     return b;
 }
 
+double smooth_fast_bytes(const amg_ctx *c, const DevLevel &L, int tb, int nsweeps, bool zero_init) {
+    const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
+    double b = 0.0;
+    int k = 0;
+    if (nsweeps == 0) return zero_init ? tb * L.n : 0.0;
+    if (zero_init) {
+        if (gnn) { b += pass_bytes(L.A, tb, L.n, 2); k = 1; }              // u = w = M b
+        else if (nsweeps >= 2) { b += pass_bytes(L.A, tb, 2.0 * L.n, 1); k = 2; }   // two Jacobi sweeps
+        else { b += 3.0 * tb * L.n; k = 1; }
+    } else if (gnn && c->opt.nu1 == 0) {
+        b += pass_bytes(L.A, tb, L.n, 1);                                  // w = M b
+    }
+    for (; k < nsweeps; ++k)
+        b += gnn ? pass_bytes(L.MA, tb, L.n, 2) : pass_bytes(L.A, tb, L.n, 3);   // u' = u + w - (M A) u
+    return b;
+}
+
 double vcycle_bytes_level(const amg_ctx *c, int l, int tb) {
     const DevLevel &L = c->lev[l];
     const int nlev = static_cast<int>(c->lev.size());
     if (l == nlev - 1) return 8.0 * c->nL * c->nL + 2.0 * tb * c->nL;
-    double b = smooth_bytes(c, L, tb, c->opt.nu1, true);
+    double b;
+    if (L.fast) {
+        b = smooth_fast_bytes(c, L, tb, c->opt.nu1, true);
+        b += pass_bytes(L.R, tb, L.n, 1) + pass_bytes(L.RA, tb, L.n, 0);   // b_c = R b - (R A) u
+        b += vcycle_bytes_level(c, l + 1, tb);
+        b += pass_bytes(L.P, tb, L.P.nc, 2);
+        b += smooth_fast_bytes(c, L, tb, c->opt.nu2, false);
+        return b;
+    }
+    b = smooth_bytes(c, L, tb, c->opt.nu1, true);
     b += pass_bytes(L.A, tb, L.n, 2);                           // residual
     b += pass_bytes(L.R, tb, L.n, 1);                           // restriction
     b += vcycle_bytes_level(c, l + 1, tb);
@@ -1318,6 +1620,8 @@ int kernel_launch(amg_ctx *c, int which, int l, int reps, cudaStream_t s, double
 extern "C" {
 
 long long amg_launch_count(void) { return amg::g_launches.load(); }
+
+int amg_last_solve_rerouted(const amg_ctx *c) { return c ? c->last_rerouted : 0; }
 
 int amg_vcycle_bytes(const amg_ctx *c, double *bytes) {
     if (!c || !bytes) return AMG_ERR_ARG;

@@ -28,9 +28,16 @@ struct DevLevel {
     double *j64 = nullptr; float *j32 = nullptr;   // omega / a_ii
     // V-cycle vectors; storage sized for n doubles, used as float or double
     double *vb = nullptr, *vu = nullptr, *vr = nullptr, *vt = nullptr;
+    // latency-optimised levels (L2-resident): single-pass sweeps with M A and
+    // fused residual + restriction
+    bool fast = false;
+    DevMat MA;                                 // pattern of M A, values from the pair list
+    DevMat RA;                                 // R A for the fused residual + restriction
+    int *pp = nullptr, *pq_p = nullptr, *pq_q = nullptr;
+    double *vw = nullptr;                      // w = M b of the current V-cycle
 };
 
-enum : int { kRunning = 1 };
+enum : int { kRunning = 1, kStalled = 2 };
 
 struct SolveState {
     int k;          // index of the next residual-history entry
@@ -40,6 +47,7 @@ struct SolveState {
     double tol;
     double bnorm;   // ||b|| (1 if b = 0)
     double r0;      // ||b - A x0||
+    double stall;   // > 0: a 10-cycle reduction worse than this ends the learned smoother's run
 };
 
 // Whole-solve CUDA graph: a kernel node copies the device-side status into
@@ -84,6 +92,8 @@ struct amg_ctx {
     long long hier_version = 0;                // bumped by every hierarchy upload
     void *train = nullptr;                     // training (adjoint) buffers, created on demand
     amg::SolveGraph sgraph[2];                 // per smoother (AMG_SMOOTHER_JACOBI / _GNN)
+    double stall_ratio = 0.0;                  // armed by amg_reroute for the learned smoother
+    int last_rerouted = 0;                     // the last solve switched to Jacobi
 };
 
 namespace amg {

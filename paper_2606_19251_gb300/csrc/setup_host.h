@@ -18,6 +18,11 @@ struct HostLevel {
     HostCSR A;   // n_l x n_l
     HostCSR P;   // n_l x n_{l+1}   (empty on the coarsest level)
     HostCSR R;   // n_{l+1} x n_l, R = P^T
+    // latency-optimised levels only: pattern of M A (M = Q^-1) and its pair list
+    bool fast = false;
+    HostCSR MA;
+    HostCSR RA;        // R A (n_{l+1} x n_l): fused residual + restriction b_c = R b - (R A) u
+    std::vector<int> pair_ptr, pair_p, pair_q;
 };
 
 // Checks CSR structure; square/diag requirements only when asked.
@@ -34,6 +39,16 @@ HostCSR direct_interpolation(const HostCSR& A, const std::vector<int>& S_rp,
 
 // A_c = P^T A P on the structural pattern of the product.
 HostCSR galerkin(const HostCSR& A, const HostCSR& P, const HostCSR& R);
+
+// Pattern of the product M A for two matrices with A's pattern (M = Q^-1)
+// and the pair list that assembles its values: for output entry e,
+// (M A)[e] = sum over t in [pair_ptr[e], pair_ptr[e+1]) of M[pair_p[t]] * A[pair_q[t]],
+// pairs in ascending (p) order.  The values of MA are left empty.
+void product_pattern(const HostCSR &A, HostCSR &MA, std::vector<int> &pair_ptr, std::vector<int> &pair_p,
+                     std::vector<int> &pair_q);
+
+// Row-by-row sparse product X Y keeping the structural pattern.
+HostCSR spgemm(const HostCSR &X, const HostCSR &Y);
 
 // Setup-AMG-Hierarchy of Algorithm 1 (finest level first).
 void build_hierarchy(const HostCSR& A0, double theta, int max_levels, int max_coarse,
