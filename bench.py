@@ -241,14 +241,21 @@ def run_gpu(args, wl, rank, world):
     P.gnn_predict_coeffs(ctx)
     judge = P.amg_judge(ctx, rhs_host[0].numpy(), 10)
 
-    # dominant kernel: finest-level A pass (residual), timed back to back
+    # dominant kernel: the finest level's pseudo-inverse sweep (single pass
+    # with Q^-1 A on latency-optimised levels, else the residual pass),
+    # timed back to back on the stream it is launched on
     peak, peak_kind = read_peaks()
     reps = 200
-    P.amg_kernel_launch(ctx, P.AMG_K_RESIDUAL, 0, 10)
+    kid, kname = P.AMG_K_MASWEEP, "k_ma_sweep (finest level, u' = u + w - (Q^-1 A) u, FP32)"
+    try:
+        P.amg_kernel_launch(ctx, kid, 0, 10)
+    except P.AmgError:
+        kid, kname = P.AMG_K_RESIDUAL, "k_resid (finest level, r = b - A u, FP32)"
+        P.amg_kernel_launch(ctx, kid, 0, 10)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    kbytes = P.amg_kernel_launch(ctx, P.AMG_K_RESIDUAL, 0, reps)
+    kbytes = P.amg_kernel_launch(ctx, kid, 0, reps)
     e1.record(stream)
     torch.cuda.synchronize()
     k_us = e0.elapsed_time(e1) * 1e3 / reps
@@ -300,7 +307,7 @@ def run_gpu(args, wl, rank, world):
             "judge_log10_ratio_10cycles": judge, "final_rel_residual": final_res,
             "status": sorted(set(statuses)), "setup_host_ms": setup_ms,
             "vcycle": {"bytes": vbytes, "us": vc_us, "GBs": vbytes / (vc_us * 1e-6) / 1e9},
-            "roofline": {"bound": "hbm", "kernel": "k_resid (finest level, r = b - A u, FP32)",
+            "roofline": {"bound": "hbm", "kernel": kname,
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": kbytes,
                          "us_per_launch": k_us, "note": "L2-resident at this size (effective GB/s)"},
@@ -347,7 +354,7 @@ def run_kernel_only(args, wl):
     P.amg_set_coeffs(ctx, [[0.62, 0.03, -0.01, -0.18, 0.02]] * P.amg_num_levels(ctx))
     kid = {"residual": P.AMG_K_RESIDUAL, "pinv": P.AMG_K_PINV, "jacobi": P.AMG_K_JACOBI,
            "restrict": P.AMG_K_RESTRICT, "prolong": P.AMG_K_PROLONG, "outer": P.AMG_K_OUTER,
-           "vcycle": P.AMG_K_VCYCLE}[args.kernel_only]
+           "vcycle": P.AMG_K_VCYCLE, "masweep": P.AMG_K_MASWEEP}[args.kernel_only]
     b = P.amg_kernel_launch(ctx, kid, 0, args.steps)
     torch.cuda.synchronize()
     print(json.dumps({"kernel": args.kernel_only, "workload": wl["workload"], "bytes_per_launch": b,

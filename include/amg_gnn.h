@@ -235,6 +235,7 @@ int amg_last_solve_rerouted(const amg_ctx *ctx);
 #define AMG_K_PROLONG   4   /* u += P_l e_{l+1}                        (V-cycle precision) */
 #define AMG_K_OUTER     5   /* FP64 r = b - A_0 x with norm partials   (level 0 only)      */
 #define AMG_K_VCYCLE    6   /* one whole V-cycle from level 0          (level ignored)     */
+#define AMG_K_MASWEEP   7   /* u' = u + w - (Q^-1 A) u single pass   (latency-optimised levels) */
 
 /* Launch `reps` back-to-back instances of one solve-path kernel on level
  * `level`, using the context's own work vectors, asynchronously on

@@ -333,7 +333,7 @@ def amg_loss_grad(ctx, c, f, n_vc=1):
     return loss.value, dc
 
 
-AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE = range(7)
+AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE, AMG_K_MASWEEP = range(8)
 
 
 def amg_kernel_launch(ctx, kernel, level, reps, stream=None) -> float:

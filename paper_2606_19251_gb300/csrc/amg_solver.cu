@@ -70,6 +70,7 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_resid(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                   const T *__restrict__ a, const T *__restrict__ b,
                                                   const T *__restrict__ u, T *__restrict__ r) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -86,6 +87,7 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                  const T *__restrict__ m, const T *__restrict__ x,
                                                  T *__restrict__ y) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -103,6 +105,7 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_apply(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                   const T *__restrict__ m, const T *__restrict__ r,
                                                   T *__restrict__ u, int add) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -120,6 +123,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
                                                    const T *__restrict__ a, const T *__restrict__ jac,
                                                    const T *__restrict__ b, const T *__restrict__ uin,
                                                    T *__restrict__ uout) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -137,6 +141,7 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_ma_sweep(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                      const T *__restrict__ ma, const T *__restrict__ w,
                                                      const T *__restrict__ uin, T *__restrict__ uout) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -153,6 +158,7 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_apply_w(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                     const T *__restrict__ m, const T *__restrict__ b,
                                                     T *__restrict__ u, T *__restrict__ w) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -175,6 +181,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_restrict(int nc, const int *__
                                                            const int *__restrict__ sp, const int *__restrict__ scol,
                                                            const T *__restrict__ sv, const T *__restrict__ b,
                                                            const T *__restrict__ u, T *__restrict__ bc) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -191,6 +198,7 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                           const T *__restrict__ a, const T *__restrict__ jac,
                                                           const T *__restrict__ b, T *__restrict__ u) {
+    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
@@ -223,12 +231,14 @@ __global__ void k_assemble_ma(int nnz, const int *__restrict__ pp, const int *__
 // u = (omega/a_ii) b  (first Jacobi sweep from u = 0)
 template <class T>
 __global__ void k_scale(int n, const T *__restrict__ jac, const T *__restrict__ b, T *__restrict__ u) {
+    pdl_wait_and_release();
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i < n) u[i] = jac[i] * b[i];
 }
 
 template <class S, class D>
 __global__ void k_convert(int n, const S *__restrict__ s, D *__restrict__ d) {
+    pdl_wait_and_release();
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i < n) d[i] = static_cast<D>(s[i]);
 }
@@ -236,6 +246,7 @@ __global__ void k_convert(int n, const S *__restrict__ s, D *__restrict__ d) {
 // x += e  (outer FP64 update)
 template <class T>
 __global__ void k_axpy(int n, double *__restrict__ x, const T *__restrict__ e) {
+    pdl_wait_and_release();
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i < n) x[i] += static_cast<double>(e[i]);
 }
@@ -245,6 +256,7 @@ template <class T>
 __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double *__restrict__ Linv,
                                                    const double *__restrict__ LinvT, const T *__restrict__ b,
                                                    T *__restrict__ u) {
+    pdl_wait_and_release();
     extern __shared__ double sm[];
     double *sb = sm, *sy = sm + n;
     for (int i = threadIdx.x; i < n; i += kBlock) sb[i] = static_cast<double>(b[i]);
@@ -288,6 +300,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(int n, const int *__rest
                                                         const int *__restrict__ col, const double *__restrict__ a,
                                                         const double *__restrict__ b, const double *__restrict__ x,
                                                         T *__restrict__ rT, double *__restrict__ partial) {
+    pdl_wait_and_release();
     constexpr int RPB = kBlock / TPR;
     const int lane = threadIdx.x % TPR;
     double sq = 0.0;
@@ -310,12 +323,14 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(int n, const int *__rest
 
 __global__ void __launch_bounds__(kBlock) k_sqnorm_partial(int n, const double *__restrict__ v,
                                                            double *__restrict__ partial) {
+    pdl_wait_and_release();
     double sq = 0.0;
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) sq += v[i] * v[i];
     block_partial(sq, partial);
 }
 
 __global__ void k_state_init(SolveState *st, double tol, int max_iter, double stall) {
+    pdl_wait_and_release();
     st->k = 0;
     st->status = kRunning;
     st->max_iter = max_iter;
@@ -327,6 +342,7 @@ __global__ void k_state_init(SolveState *st, double tol, int max_iter, double st
 
 // Continue a stalled solve with another smoother (history and count go on).
 __global__ void k_state_continue(SolveState *st) {
+    pdl_wait_and_release();
     st->status = kRunning;
     st->stall = 0.0;
 }
@@ -337,6 +353,7 @@ __global__ void k_state_continue(SolveState *st) {
 __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ partial, int np, SolveState *st,
                                                      double *__restrict__ hist, int mode, int use_cond,
                                                      cudaGraphConditionalHandle cond) {
+    pdl_wait_and_release();
     __shared__ double red[32];
     double v = 0.0;
     for (int i = threadIdx.x; i < np; i += 1024) v += partial[i];
@@ -525,6 +542,7 @@ template <> const float *jvals<float>(const DevLevel &L) { return L.j32; }
 
 #define TPR_DISPATCH(tpr, KERNEL, ...)                    \
     switch (tpr) {                                        \
+        case 1: KERNEL<1>(__VA_ARGS__); break;            \
         case 2: KERNEL<2>(__VA_ARGS__); break;            \
         case 4: KERNEL<4>(__VA_ARGS__); break;            \
         case 8: KERNEL<8>(__VA_ARGS__); break;            \
@@ -535,48 +553,48 @@ template <> const float *jvals<float>(const DevLevel &L) { return L.j32; }
 template <class T> struct Launch {
     template <int TPR>
     static void resid(const DevMat &A, const T *b, const T *u, T *r, cudaStream_t s) {
-        k_resid<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(A.nr, A.rp, A.col,
-                                                                                         mvals<T>(A), b, u, r); AMG_COUNT();
+        launch_pdl(k_resid<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, A.nr, A.rp, A.col,
+                                                                                         mvals<T>(A), b, u, r);
     }
     template <int TPR>
     static void spmv(const DevMat &M, const T *x, T *y, cudaStream_t s) {
-        k_spmv<T, TPR><<<grid_for(static_cast<long long>(M.nr) * TPR), kBlock, 0, s>>>(M.nr, M.rp, M.col,
-                                                                                        mvals<T>(M), x, y); AMG_COUNT();
+        launch_pdl(k_spmv<T, TPR>, dim3(grid_for(static_cast<long long>(M.nr) * TPR)), dim3(kBlock), 0, s, M.nr, M.rp, M.col,
+                                                                                        mvals<T>(M), x, y);
     }
     template <int TPR>
     static void apply(const DevMat &M, const T *m, const T *r, T *u, int add, cudaStream_t s) {
-        k_apply<T, TPR><<<grid_for(static_cast<long long>(M.nr) * TPR), kBlock, 0, s>>>(M.nr, M.rp, M.col, m,
-                                                                                         r, u, add); AMG_COUNT();
+        launch_pdl(k_apply<T, TPR>, dim3(grid_for(static_cast<long long>(M.nr) * TPR)), dim3(kBlock), 0, s, M.nr, M.rp, M.col, m,
+                                                                                         r, u, add);
     }
     template <int TPR>
     static void jacobi(const DevMat &A, const T *jac, const T *b, const T *uin, T *uout, cudaStream_t s) {
-        k_jacobi<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(
-            A.nr, A.rp, A.col, mvals<T>(A), jac, b, uin, uout); AMG_COUNT();
+        launch_pdl(k_jacobi<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, 
+            A.nr, A.rp, A.col, mvals<T>(A), jac, b, uin, uout);
     }
     template <int TPR>
     static void ma_sweep(const DevMat &MA, const T *w, const T *uin, T *uout, cudaStream_t s) {
-        k_ma_sweep<T, TPR><<<grid_for(static_cast<long long>(MA.nr) * TPR), kBlock, 0, s>>>(
-            MA.nr, MA.rp, MA.col, mvals<T>(MA), w, uin, uout); AMG_COUNT();
+        launch_pdl(k_ma_sweep<T, TPR>, dim3(grid_for(static_cast<long long>(MA.nr) * TPR)), dim3(kBlock), 0, s, 
+            MA.nr, MA.rp, MA.col, mvals<T>(MA), w, uin, uout);
     }
     template <int TPR>
     static void apply_w(const DevMat &A, const T *m, const T *b, T *u, T *w, cudaStream_t s) {
-        k_apply_w<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(A.nr, A.rp, A.col, m, b,
-                                                                                           u, w); AMG_COUNT();
+        launch_pdl(k_apply_w<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, A.nr, A.rp, A.col, m, b,
+                                                                                           u, w);
     }
     template <int TPR>
     static void resid_restrict(const DevMat &R, const DevMat &RA, const T *b, const T *u, T *bc, cudaStream_t s) {
-        k_resid_restrict<T, TPR><<<grid_for(static_cast<long long>(R.nr) * TPR), kBlock, 0, s>>>(
-            R.nr, R.rp, R.col, mvals<T>(R), RA.rp, RA.col, mvals<T>(RA), b, u, bc); AMG_COUNT();
+        launch_pdl(k_resid_restrict<T, TPR>, dim3(grid_for(static_cast<long long>(R.nr) * TPR)), dim3(kBlock), 0, s, 
+            R.nr, R.rp, R.col, mvals<T>(R), RA.rp, RA.col, mvals<T>(RA), b, u, bc);
     }
     template <int TPR>
     static void jacobi_first2(const DevMat &A, const T *jac, const T *b, T *u, cudaStream_t s) {
-        k_jacobi_first2<T, TPR><<<grid_for(static_cast<long long>(A.nr) * TPR), kBlock, 0, s>>>(
-            A.nr, A.rp, A.col, mvals<T>(A), jac, b, u); AMG_COUNT();
+        launch_pdl(k_jacobi_first2<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, 
+            A.nr, A.rp, A.col, mvals<T>(A), jac, b, u);
     }
     template <int TPR>
     static void outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nblk,
                       cudaStream_t s) {
-        k_outer_resid<T, TPR><<<nblk, kBlock, 0, s>>>(A.nr, A.rp, A.col, A.v64, b, x, rT, partial); AMG_COUNT();
+        launch_pdl(k_outer_resid<T, TPR>, dim3(nblk), dim3(kBlock), 0, s, A.nr, A.rp, A.col, A.v64, b, x, rT, partial);
     }
 };
 
@@ -622,7 +640,7 @@ static T *smooth(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *alt, 
             }
         } else {
             if (first) {
-                k_scale<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, jvals<T>(L), b, cur); AMG_COUNT();
+                launch_pdl(k_scale<T>, dim3(grid_for(L.n)), dim3(kBlock), 0, s, L.n, jvals<T>(L), b, cur);
             } else {
                 L_jacobi<T>(L.A, jvals<T>(L), b, cur, alt, s);
                 std::swap(cur, alt);
@@ -637,6 +655,7 @@ template <class T>
 __global__ void __launch_bounds__(32) k_coarse_warp(int n, const double *__restrict__ Linv,
                                                     const double *__restrict__ LinvT, const T *__restrict__ b,
                                                     T *__restrict__ u) {
+    pdl_wait_and_release();
     __shared__ double sb[32], sy[32];
     const int i = threadIdx.x;
     if (i < n) sb[i] = static_cast<double>(b[i]);
@@ -655,9 +674,9 @@ __global__ void __launch_bounds__(32) k_coarse_warp(int n, const double *__restr
 template <class T>
 static void launch_coarse(amg_ctx *c, const T *b, T *u, cudaStream_t s) {
     if (c->nL <= 32) {
-        k_coarse_warp<T><<<1, 32, 0, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
+        launch_pdl(k_coarse_warp<T>, dim3(1), dim3(32), 0, s, c->nL, c->Linv, c->LinvT, b, u);
     } else {
-        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
+        launch_pdl(k_coarse<T>, dim3(1), dim3(kBlock), 2 * sizeof(double) * c->nL, s, c->nL, c->Linv, c->LinvT, b, u);
     }
 }
 
@@ -684,7 +703,7 @@ static T *smooth_fast(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *
             TPR_DISPATCH(L.A.tpr, Launch<T>::template jacobi_first2, L.A, jvals<T>(L), b, cur, s);
             k = 2;
         } else {
-            k_scale<T><<<grid_for(L.n), kBlock, 0, s>>>(L.n, jvals<T>(L), b, cur); AMG_COUNT();
+            launch_pdl(k_scale<T>, dim3(grid_for(L.n)), dim3(kBlock), 0, s, L.n, jvals<T>(L), b, cur);
             k = 1;
         }
     }
@@ -742,7 +761,7 @@ static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s, int use_cond = 0,
     const int nb = outer_blocks(A);
     TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb),
                  c->partials, nb, s);
-    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 1, use_cond, cond); AMG_COUNT();
+    launch_pdl(k_norm_final, dim3(1), dim3(1024), 0, s, c->partials, nb, c->state, c->hist, 1, use_cond, cond);
 }
 
 template <class T>
@@ -750,16 +769,16 @@ static void enqueue_init(amg_ctx *c, cudaStream_t s, double tol, int max_iter) {
     const int n0 = c->lev[0].n;
     const int nb = std::min(grid_for(n0), kNumSMs * 8);
     const double stall = (c->smoother == AMG_SMOOTHER_GNN) ? c->stall_ratio : 0.0;
-    k_state_init<<<1, 1, 0, s>>>(c->state, tol, max_iter, stall); AMG_COUNT();
-    k_sqnorm_partial<<<nb, kBlock, 0, s>>>(n0, c->db, c->partials); AMG_COUNT();
-    k_norm_final<<<1, 1024, 0, s>>>(c->partials, nb, c->state, c->hist, 0, 0, 0); AMG_COUNT();
+    launch_pdl(k_state_init, dim3(1), dim3(1), 0, s, c->state, tol, max_iter, stall);
+    launch_pdl(k_sqnorm_partial, dim3(nb), dim3(kBlock), 0, s, n0, c->db, c->partials);
+    launch_pdl(k_norm_final, dim3(1), dim3(1024), 0, s, c->partials, nb, c->state, c->hist, 0, 0, 0);
     enqueue_outer_residual<T>(c, s);
 }
 
 template <class T>
 static void enqueue_iteration(amg_ctx *c, cudaStream_t s, int use_cond = 0, cudaGraphConditionalHandle cond = 0) {
     T *e = vcycle_level<T>(c, 0, s);
-    k_axpy<T><<<grid_for(c->lev[0].n), kBlock, 0, s>>>(c->lev[0].n, c->dx, e); AMG_COUNT();
+    launch_pdl(k_axpy<T>, dim3(grid_for(c->lev[0].n)), dim3(kBlock), 0, s, c->lev[0].n, c->dx, e);
     enqueue_outer_residual<T>(c, s, use_cond, cond);
 }
 
@@ -833,7 +852,7 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
         c->last_rerouted = 1;
         rc = ensure_graph<T>(c);
         if (rc) return rc;
-        k_state_continue<<<1, 1, 0, s>>>(c->state); AMG_COUNT();
+        launch_pdl(k_state_continue, dim3(1), dim3(1), 0, s, c->state);
         const SolveGraph &GJ = c->sgraph[AMG_SMOOTHER_JACOBI];
         CK(cudaGraphLaunch(GJ.exec, s));
         CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -930,7 +949,7 @@ static int upload_mat(amg_ctx *c, const DevMat &m, const HostCSR &h, cudaStream_
     if (h.nnz() > 0) {
         CK(cudaMemcpyAsync(m.col, h.col.data(), sizeof(int) * h.nnz(), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(m.v64, h.val.data(), sizeof(double) * h.nnz(), cudaMemcpyHostToDevice, s));
-        k_convert<double, float><<<grid_for(h.nnz()), kBlock, 0, s>>>(m.nnz, m.v64, m.v32); AMG_COUNT();
+        launch_pdl(k_convert<double, float>, dim3(grid_for(h.nnz())), dim3(kBlock), 0, s, m.nnz, m.v64, m.v32);
     }
     return AMG_OK;
 }
@@ -1346,9 +1365,9 @@ int amg_vcycle_device(amg_ctx *c, const double *d_r, double *d_e, void *stream) 
         double *e = vcycle_level<double>(c, 0, s);
         CK(cudaMemcpyAsync(d_e, e, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
     } else {
-        k_convert<double, float><<<grid_for(n0), kBlock, 0, s>>>(n0, d_r, reinterpret_cast<float *>(c->lev[0].vb)); AMG_COUNT();
+        launch_pdl(k_convert<double, float>, dim3(grid_for(n0)), dim3(kBlock), 0, s, n0, d_r, reinterpret_cast<float *>(c->lev[0].vb));
         float *e = vcycle_level<float>(c, 0, s);
-        k_convert<float, double><<<grid_for(n0), kBlock, 0, s>>>(n0, e, d_e); AMG_COUNT();
+        launch_pdl(k_convert<float, double>, dim3(grid_for(n0)), dim3(kBlock), 0, s, n0, e, d_e);
     }
     CKL("vcycle");
     return AMG_OK;
@@ -1361,10 +1380,10 @@ static void smooth_level_device(amg_ctx *c, int l, const double *d_b, double *d_
     DevLevel &L = c->lev[l];
     const int n = L.n;
     T *b = reinterpret_cast<T *>(L.vb), *u = reinterpret_cast<T *>(L.vu);
-    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_b, b); AMG_COUNT();
-    k_convert<double, T><<<grid_for(n), kBlock, 0, s>>>(n, d_u, u); AMG_COUNT();
+    launch_pdl(k_convert<double, T>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, d_b, b);
+    launch_pdl(k_convert<double, T>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, d_u, u);
     T *res = smooth<T>(c, l, s, b, u, reinterpret_cast<T *>(L.vt), reinterpret_cast<T *>(L.vr), nsw, false);
-    k_convert<T, double><<<grid_for(n), kBlock, 0, s>>>(n, res, d_u); AMG_COUNT();
+    launch_pdl(k_convert<T, double>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, res, d_u);
 }
 
 extern "C" {
@@ -1398,9 +1417,9 @@ int amg_spmv_device(amg_ctx *c, int level, const double *d_x, double *d_y, void 
         L_spmv<double>(L.A, d_x, d_y, s);
     } else {
         float *x = reinterpret_cast<float *>(L.vu), *y = reinterpret_cast<float *>(L.vr);
-        k_convert<double, float><<<grid_for(n), kBlock, 0, s>>>(n, d_x, x); AMG_COUNT();
+        launch_pdl(k_convert<double, float>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, d_x, x);
         L_spmv<float>(L.A, x, y, s);
-        k_convert<float, double><<<grid_for(n), kBlock, 0, s>>>(n, y, d_y); AMG_COUNT();
+        launch_pdl(k_convert<float, double>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, y, d_y);
     }
     CKL("spmv");
     return AMG_OK;
@@ -1605,6 +1624,14 @@ int kernel_launch(amg_ctx *c, int which, int l, int reps, cudaStream_t s, double
             }
             break;
         }
+        case AMG_K_MASWEEP:
+            if (!L.fast || !c->have_q) return ctx_fail(c, "level has no M A product (not latency-optimised or no coefficients)"), AMG_ERR_STATE;
+            by = pass_bytes(L.MA, tb, L.n, 2);
+            for (int k = 0; k < reps; ++k) {
+                TPR_DISPATCH(L.MA.tpr, Launch<T>::template ma_sweep, L.MA, reinterpret_cast<const T *>(L.vw),
+                             (k & 1) ? t : u, (k & 1) ? u : t, s);
+            }
+            break;
         case AMG_K_VCYCLE:
             by = vcycle_bytes_level(c, 0, tb);
             for (int k = 0; k < reps; ++k) vcycle_level<T>(c, 0, s);
@@ -1765,6 +1792,7 @@ extern "C" int amg_residual_norm_noalloc(int n, long long nnz, const int *d_row_
         const long long need = (static_cast<long long>(n) * tpr + kBlock - 1) / kBlock;
         const int nb = static_cast<int>(std::max(1LL, std::min<long long>(need, kStaticSlots)));
         switch (tpr) {
+            case 1: k_resid_norm_static<1><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
             case 2: k_resid_norm_static<2><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
             case 4: k_resid_norm_static<4><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
             case 8: k_resid_norm_static<8><<<nb, kBlock, 0, s>>>(n, d_row_ptr, d_col, d_val, d_b, d_x, d_r, scratch); break;
@@ -1934,7 +1962,7 @@ T *fwd_level_ckpt(amg_ctx *c, TrainBufs &tb, int cyc, int l, cudaStream_t s) {
     const int nlev = static_cast<int>(c->lev.size());
     const int nu1 = c->opt.nu1, nu2 = c->opt.nu2, nsw = nu1 + nu2;
     if (l == nlev - 1) {
-        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, b, u); AMG_COUNT();
+        launch_pdl(k_coarse<T>, dim3(1), dim3(kBlock), 2 * sizeof(double) * c->nL, s, c->nL, c->Linv, c->LinvT, b, u);
         return u;
     }
     auto ck = [&](int k) { return reinterpret_cast<T *>(tb.slot(cyc, l, k)); };
@@ -1969,6 +1997,7 @@ void coef_grad(amg_ctx *c, TrainBufs &tb, int l, const T *ubar, const T *r, cuda
     k_coef_grad<T, TP><<<nb, kBlock, 0, s>>>(A.nr, A.rp, A.col, L.bx, L.bw, ubar, r, c->partials); \
     AMG_COUNT();
     switch (A.tpr) {
+        case 1: CG_LAUNCH(1) break;
         case 2: CG_LAUNCH(2) break;
         case 4: CG_LAUNCH(4) break;
         case 8: CG_LAUNCH(8) break;
@@ -2002,7 +2031,7 @@ void bwd_level(amg_ctx *c, TrainBufs &tb, int cyc, int l, cudaStream_t s) {
     T *ub = reinterpret_cast<T *>(tb.ubar[l]), *sp = reinterpret_cast<T *>(tb.tmp[l]);
     T *bb = reinterpret_cast<T *>(tb.bbar[l]);
     if (l == nlev - 1) {   // u = A_L^-1 b is self-adjoint
-        k_coarse<T><<<1, kBlock, 2 * sizeof(double) * c->nL, s>>>(c->nL, c->Linv, c->LinvT, ub, bb); AMG_COUNT();
+        launch_pdl(k_coarse<T>, dim3(1), dim3(kBlock), 2 * sizeof(double) * c->nL, s, c->nL, c->Linv, c->LinvT, ub, bb);
         return;
     }
     auto ck = [&](int k) { return reinterpret_cast<const T *>(tb.slot(cyc, l, k)); };
@@ -2046,7 +2075,7 @@ int loss_grad(amg_ctx *c, TrainBufs &tb, const double *f, int nvc, double *loss,
     T *xu = reinterpret_cast<T *>(tb.xu);
     T *b0 = reinterpret_cast<T *>(L0.vb);
     CK(cudaMemcpyAsync(c->db, f, sizeof(double) * n0, cudaMemcpyHostToDevice, s));
-    k_convert<double, T><<<grid_for(n0), kBlock, 0, s>>>(n0, c->db, fT); AMG_COUNT();
+    launch_pdl(k_convert<double, T>, dim3(grid_for(n0)), dim3(kBlock), 0, s, n0, c->db, fT);
     CK(cudaMemsetAsync(xu, 0, sizeof(T) * n0, s));
     for (int q = 0; q < nvc; ++q) {
         L_resid<T>(L0.A, fT, xu, b0, s);          // r_{q} = f - A u_q -> level-0 right-hand side

@@ -45,15 +45,41 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Threads per row for CSR kernels, from the average row length.
+// Programmatic dependent launch (PDL).  A solve-path kernel first waits for
+// its predecessor grid to finish and flush (griddepcontrol.wait), touching no
+// memory before that, then lets its own dependents start launching, so the
+// next kernel's launch and block scheduling overlap this kernel's tail.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    AMG_COUNT();
+}
+
+// Threads per row of the row-group CSR kernels: about three independent
+// entries per lane (a power of two, 1..32), so each thread keeps several
+// loads in flight and a finest-level pass fits in few waves.
 inline int pick_tpr(long long nnz, int n) {
-    if (n <= 0) return 2;
-    double avg = static_cast<double>(nnz) / n;
-    if (avg <= 2.5) return 2;
-    if (avg <= 6.0) return 4;
-    if (avg <= 12.0) return 8;
-    if (avg <= 24.0) return 16;
-    return 32;
+    if (n <= 0) return 1;
+    const double per_lane = static_cast<double>(nnz) / n / 3.0;
+    int t = 1;
+    while (t * 2 <= per_lane && t < 32) t *= 2;
+    return t;
 }
 
 inline int grid_for(long long threads) {
