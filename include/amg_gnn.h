@@ -44,6 +44,10 @@ extern "C" {
 #define AMG_SMOOTHER_JACOBI 0   /* relaxed Jacobi, Q^-1 = omega D^-1 (Sec. 2.3)          */
 #define AMG_SMOOTHER_GNN    1   /* sparse pseudo-inverse from coefficients (Sec. 3.1)    */
 
+/* arithmetic of the GCIN node linears (layers 2..4) */
+#define AMG_GNN_FP32 0   /* FP32 CUDA-core FMAs                                  */
+#define AMG_GNN_BF16 1   /* tcgen05 tensor cores: BF16 operands, FP32 accumulation */
+
 #define AMG_GCIN_NUM_PARAMS 55045   /* App. A.1 */
 
 typedef struct amg_ctx amg_ctx;
@@ -68,11 +72,13 @@ typedef struct {
     double omega;     /* Jacobi relaxation (Sec. 4: 2/3)                             */
     double theta;     /* Ruge-Stueben strength threshold (Sec. 4: 0.25)              */
     int device;       /* CUDA device ordinal                                         */
+    int gnn_precision;/* AMG_GNN_BF16 (default) or AMG_GNN_FP32                      */
 } amg_options;
 
 /* Fill *opt with the paper's settings: nu1 = nu2 = 2, max_levels = 10,
  * max_coarse = 64, max_iter = 500, FP32 V-cycle in FP64 refinement, Jacobi,
- * omega = 2/3, theta = 0.25, device 0 (Sec. 4, Table train_hyper). */
+ * omega = 2/3, theta = 0.25, device 0, BF16 tensor-core GCIN linears
+ * (Sec. 4, Table train_hyper). */
 void amg_default_options(amg_options *opt);
 
 /* Create a context bound to opt->device.  *ctx receives the handle (NULL on
@@ -286,8 +292,10 @@ int amg_residual_norm_noalloc(int n, long long nnz, const int *d_row_ptr, const 
 typedef struct gcin_trainer gcin_trainer;
 
 /* Trainer owning the parameters, their gradient and Adam moments on
- * `device`.  theta0: AMG_GCIN_NUM_PARAMS floats (copied). */
-int gcin_trainer_create(gcin_trainer **tr, int device, const float *theta0);
+ * `device`; precision AMG_GNN_FP32 or AMG_GNN_BF16 selects the arithmetic of
+ * the forward node linears (the backward runs in FP32 on the same rounded
+ * operands).  theta0: AMG_GCIN_NUM_PARAMS floats (copied). */
+int gcin_trainer_create(gcin_trainer **tr, int device, int precision, const float *theta0);
 void gcin_trainer_destroy(gcin_trainer *tr);
 const char *gcin_trainer_last_error(const gcin_trainer *tr);
 int gcin_trainer_get_params(const gcin_trainer *tr, float *theta_out);

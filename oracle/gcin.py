@@ -19,6 +19,13 @@ This layout has exactly 55,045 trainable parameters (App. A.1).
 Readings: no activation after the readout linears, linear output on the five
 coefficients, max-pooling after the ReLU, readout over layers 1..L only.
 
+BF16 mode (bf16_linears=True): the network evaluated with the operands of the
+layer 2..4 node linears, h and Theta^(l), rounded to bfloat16 (round to
+nearest, ties to even, from their FP32 values), everything else in FP64.  This
+is the arithmetic of a tensor-core evaluation with BF16 operands and exact (or
+FP32) accumulation; under autograd the rounding passes gradients straight
+through.
+
 Flat parameter order (weights stored [in][out], row-major; then bias):
 conv1 W(2x64) b(64); conv2..4 W(64x64) b(64); IN1..4 gamma(64) beta(64);
 readout1..4 W(128x32) b(32); LN gamma(128) beta(128);
@@ -97,13 +104,21 @@ def layer_norm(z: torch.Tensor, gamma, beta) -> torch.Tensor:
     return (z - mu) / torch.sqrt(var + EPS) * gamma + beta
 
 
-def forward_graph(p: dict, g: Graph, keep=None) -> torch.Tensor:
+def bf16_round(t: torch.Tensor) -> torch.Tensor:
+    """Round to the nearest bfloat16 (ties to even) via FP32; returned in FP64."""
+    return t.to(torch.float32).to(torch.bfloat16).to(DT)
+
+
+def forward_graph(p: dict, g: Graph, keep=None, bf16_linears=False) -> torch.Tensor:
     """Coefficients c (5,) for one graph."""
     x = g.features()
     pooled = []
     for l in range(1, N_LAYERS + 1):
         h = g.aggregate(x)
-        y = h @ p[f"conv{l}.W"] + p[f"conv{l}.b"]
+        Wl = p[f"conv{l}.W"]
+        if bf16_linears and l >= 2:
+            h, Wl = bf16_round(h), bf16_round(Wl)
+        y = h @ Wl + p[f"conv{l}.b"]
         x = torch.relu(instance_norm(y, p[f"in{l}.gamma"], p[f"in{l}.beta"]))
         if keep is not None:
             keep.append((h, y, x))
@@ -115,14 +130,15 @@ def forward_graph(p: dict, g: Graph, keep=None) -> torch.Tensor:
     return z @ p["h3.W"] + p["h3.b"]
 
 
-def forward(theta, graphs) -> torch.Tensor:
+def forward(theta, graphs, bf16_linears=False) -> torch.Tensor:
     """Batched inference (Algorithm 1 step 6): c[g] for every graph, shape (G, 5)."""
     theta = torch.as_tensor(theta, dtype=DT) if not isinstance(theta, torch.Tensor) else theta
     p = unpack(theta)
-    return torch.stack([forward_graph(p, g) for g in graphs])
+    return torch.stack([forward_graph(p, g, bf16_linears=bf16_linears) for g in graphs])
 
 
-def predict(theta, matrices) -> np.ndarray:
+def predict(theta, matrices, bf16_linears=False) -> np.ndarray:
     """Coefficients for a list of CSR matrices (no gradient)."""
     with torch.no_grad():
-        return forward(torch.as_tensor(np.asarray(theta, dtype=np.float64)), [Graph(A) for A in matrices]).numpy()
+        return forward(torch.as_tensor(np.asarray(theta, dtype=np.float64)), [Graph(A) for A in matrices],
+                       bf16_linears).numpy()

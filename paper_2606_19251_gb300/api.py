@@ -31,6 +31,8 @@ AMG_FP64 = 0
 AMG_FP32_IN_FP64 = 1
 AMG_SMOOTHER_JACOBI = 0
 AMG_SMOOTHER_GNN = 1
+AMG_GNN_FP32 = 0
+AMG_GNN_BF16 = 1
 AMG_GCIN_NUM_PARAMS = 55045
 
 SOLVE_STATUSES = (AMG_OK, AMG_ERR_DIVERGED, AMG_ERR_STAGNATED, AMG_ERR_MAXITER)
@@ -50,7 +52,7 @@ class amg_csr(C.Structure):
 class amg_options(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_levels", C.c_int), ("max_coarse", C.c_int),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
-                ("theta", C.c_double), ("device", C.c_int)]
+                ("theta", C.c_double), ("device", C.c_int), ("gnn_precision", C.c_int)]
 
 
 _LIB = None
@@ -95,7 +97,7 @@ def _declare(L):
         "amg_judge": (I, [P, pd, I, pd]),
         "amg_reroute": (I, [P, pd, I, pd, pi]),
         "amg_last_solve_rerouted": (I, [P]),
-        "gcin_trainer_create": (I, [C.POINTER(P), I, pf]),
+        "gcin_trainer_create": (I, [C.POINTER(P), I, I, pf]),
         "gcin_trainer_destroy": (V, [P]),
         "gcin_trainer_last_error": (C.c_char_p, [P]),
         "gcin_trainer_get_params": (I, [P, pf]),
@@ -377,12 +379,12 @@ def _tcheck(tr, rc):
     return rc
 
 
-def gcin_trainer_create(theta0, device=0):
+def gcin_trainer_create(theta0, device=0, precision=AMG_GNN_BF16):
     t = np.ascontiguousarray(np.asarray(theta0, dtype=np.float32))
     if t.size != AMG_GCIN_NUM_PARAMS:
         raise ValueError("theta0 must have 55045 entries")
     h = C.c_void_p()
-    rc = lib().gcin_trainer_create(C.byref(h), int(device), _fptr(t))
+    rc = lib().gcin_trainer_create(C.byref(h), int(device), int(precision), _fptr(t))
     if rc != AMG_OK:
         raise AmgError(rc, "gcin_trainer_create failed")
     return h

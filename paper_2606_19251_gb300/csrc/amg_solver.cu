@@ -1082,6 +1082,7 @@ void amg_default_options(amg_options *o) {
     o->omega = 2.0 / 3.0;
     o->theta = 0.25;
     o->device = 0;
+    o->gnn_precision = AMG_GNN_BF16;
 }
 
 int amg_create(amg_ctx **ctx, const amg_options *opt) {
@@ -1097,6 +1098,7 @@ int amg_create(amg_ctx **ctx, const amg_options *opt) {
         o.max_coarse < 1 || o.max_iter < 0 || o.max_iter > 100000 ||
         (o.precision != AMG_FP64 && o.precision != AMG_FP32_IN_FP64) ||
         (o.smoother != AMG_SMOOTHER_JACOBI && o.smoother != AMG_SMOOTHER_GNN) || !(o.theta >= 0.0) ||
+        (o.gnn_precision != AMG_GNN_FP32 && o.gnn_precision != AMG_GNN_BF16) ||
         !(o.theta <= 1.0) || !std::isfinite(o.omega)) {
         g_create_err = "invalid amg_options";
         return AMG_ERR_ARG;

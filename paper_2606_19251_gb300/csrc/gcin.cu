@@ -24,6 +24,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "gcin.cuh"
 
 namespace amg {
@@ -87,6 +89,7 @@ static void batch_layout(GcinBatch &b, Planner &pl, bool backward) {
     b.argmax = pl.take<int>(G * kLayers * kHidden);
     b.head = pl.take<float>(G * kHeadScratch);
     b.c = pl.take<float>(G * 5);
+    b.err = pl.take<int>(4);
     if (backward) {
         b.dc = pl.take<float>(G * 5);
         b.dhead = pl.take<float>(G * kHeadGrad);
@@ -162,6 +165,7 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
         }
     }
     k_set_int<<<1, 1, 0, s>>>(b.rp + b.N, static_cast<int>(E)); AMG_COUNT();
+    cudaMemsetAsync(b.err, 0, sizeof(int) * 4, s);
     e = cudaStreamSynchronize(s);   // host vectors above must outlive the async copies
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -480,6 +484,10 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     }
 }
 
+}  // namespace amg
+#include "gcin_tc.cuh"
+namespace amg {
+
 void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
     const int N = b.N, G = b.G, NT = b.NT;
     k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
@@ -487,6 +495,15 @@ void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
         if (l == 0) {
             k_layer1_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + kPL.convW[0], th + kPL.convB[0],
                                                 b.tstart, b.h1, b.y[0], b.tmean, b.tm2); AMG_COUNT();
+        } else if (b.bf16) {
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_agg_lin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+                attr_set = true;
+            }
+            k_agg_lin_tc<<<(NT + 1) / 2, kBlock, kTcSmem, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
+                                                               th + kPL.convB[l], b.tstart, NT, b.h[l], b.y[l],
+                                                               b.tmean, b.tm2, b.err); AMG_COUNT();
         } else {
             k_agg_lin_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
                                                  th + kPL.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
@@ -674,14 +691,19 @@ __global__ void __launch_bounds__(kBlock) k_bwd_in_lin_tile(const int *__restric
                                                             const double *__restrict__ gS2,
                                                             const float *__restrict__ W, const float *__restrict__ hin,
                                                             const float *__restrict__ dyn, float *__restrict__ dh,
-                                                            float *__restrict__ dWt) {
+                                                            float *__restrict__ dWt, int round_w) {
     __shared__ float2 sWT[FIN == kHidden ? kHidden * 32 : 1];   // (W[2 lane][k], W[2 lane + 1][k])
     __shared__ float sH[kTile][FIN + 1];
     __shared__ float sD[kTile][kHidden + 1];
     if (FIN == kHidden) {
         for (int e = threadIdx.x; e < kHidden * 32; e += kBlock) {
             const int k = e / 32, ln = e % 32;
-            sWT[e] = make_float2(W[(2 * ln) * kHidden + k], W[(2 * ln + 1) * kHidden + k]);
+            float w0 = W[(2 * ln) * kHidden + k], w1 = W[(2 * ln + 1) * kHidden + k];
+            if (round_w) {   // the forward multiplied by the BF16-rounded weights
+                w0 = __bfloat162float(__float2bfloat16_rn(w0));
+                w1 = __bfloat162float(__float2bfloat16_rn(w1));
+            }
+            sWT[e] = make_float2(w0, w1);
         }
     }
     const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a, g = tgraph[t];
@@ -806,12 +828,12 @@ void gcin_backward(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
         if (l > 0) {
             k_bwd_in_lin_tile<kHidden><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
                                                              th + kPL.inG[l], b.gS1, b.gS2, th + kPL.convW[l],
-                                                             b.h[l], b.dy, b.dh, b.dWt); AMG_COUNT();
+                                                             b.h[l], b.dy, b.dh, b.dWt, b.bf16); AMG_COUNT();
             k_agg_plain<<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w, b.dh, b.dx); AMG_COUNT();
         } else {
             k_bwd_in_lin_tile<2><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
                                                        th + kPL.inG[l], b.gS1, b.gS2, th + kPL.convW[l], b.h1, b.dy,
-                                                       nullptr, b.dWt); AMG_COUNT();
+                                                       nullptr, b.dWt, 0); AMG_COUNT();
         }
         const int fin = (l == 0) ? 2 : kHidden;
         k_layer_param_partial<<<dim3(grid_for(fin * kHidden + kHidden), kGradChunks), kBlock, 0, s>>>(
@@ -874,6 +896,7 @@ using namespace amg;
 
 struct gcin_trainer {
     int device = 0;
+    int bf16 = 0;
     std::string err;
     cudaStream_t stream = nullptr;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
@@ -937,13 +960,17 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
         if (rc) return ctx_fail(c, err), rc;
         g->batch_version = c->hier_version;
     }
+    g->batch.bf16 = (c->opt.gnn_precision == AMG_GNN_BF16) ? 1 : 0;
     gcin_forward(g->batch, g->theta, s);
+    int dflag = 0;
     const int G = g->batch.G;
     std::vector<float> cf(static_cast<size_t>(G) * 5);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(cf.data(), g->batch.c, sizeof(float) * cf.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&dflag, g->batch.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ctx_cuda_check(c, e, "GCIN forward");
+    if (dflag) return ctx_fail(c, "tensor-core GCIN kernel timed out waiting for its MMAs"), AMG_ERR_DEVICE_FLAG;
     std::vector<double> cd(cf.begin(), cf.end());
     if (c_out) std::copy(cd.begin(), cd.end(), c_out);
     int rc = set_coeffs_device(c, cd.data(), G, s);
@@ -953,12 +980,13 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
     return AMG_OK;
 }
 
-int gcin_trainer_create(gcin_trainer **out, int device, const float *theta0) {
-    if (!out || !theta0) return AMG_ERR_ARG;
+int gcin_trainer_create(gcin_trainer **out, int device, int precision, const float *theta0) {
+    if (!out || !theta0 || (precision != AMG_GNN_FP32 && precision != AMG_GNN_BF16)) return AMG_ERR_ARG;
     *out = nullptr;
     if (cudaSetDevice(device) != cudaSuccess) return AMG_ERR_CUDA;
     gcin_trainer *t = new gcin_trainer();
     t->device = device;
+    t->bf16 = (precision == AMG_GNN_BF16) ? 1 : 0;
     cudaError_t e = cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking);
     const size_t P = kNumParams;
     const size_t fbytes = ((sizeof(float) * 4 * P + 255) / 256) * 256;
@@ -1025,13 +1053,18 @@ int gcin_trainer_forward(gcin_trainer *t, int n_problems, amg_ctx *const *proble
         t->key = key;
         t->versions = versions;
     }
+    t->batch.bf16 = t->bf16;
     gcin_forward(t->batch, t->theta, t->stream);
     std::vector<float> cf(static_cast<size_t>(t->batch.G) * 5);
+    int dflag = 0;
     rc = tr_cuda(t, cudaGetLastError(), "GCIN forward");
     if (!rc) rc = tr_cuda(t, cudaMemcpyAsync(cf.data(), t->batch.c, sizeof(float) * cf.size(), cudaMemcpyDeviceToHost,
                                              t->stream), "coefficients download");
+    if (!rc) rc = tr_cuda(t, cudaMemcpyAsync(&dflag, t->batch.err, sizeof(int), cudaMemcpyDeviceToHost, t->stream),
+                          "flag download");
     if (!rc) rc = tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
     if (rc) return rc;
+    if (dflag) return tr_fail(t, AMG_ERR_DEVICE_FLAG, "tensor-core GCIN kernel timed out waiting for its MMAs");
     std::copy(cf.begin(), cf.end(), c_out);
     t->have_forward = true;
     return AMG_OK;

@@ -65,6 +65,8 @@ constexpr int kGradChunks = 64;      // tile chunks of the weight-gradient reduc
 
 struct GcinBatch {
     int G = 0, N = 0, NT = 0;            // graphs, nodes, tiles
+    int bf16 = 0;                        // layers 2..4 on tensor cores (BF16 operands, FP32 accumulation)
+    int *err = nullptr;                  // device error flag (tensor-core wait timeout)
     long long E = 0;
     int *rp = nullptr, *col = nullptr, *gptr = nullptr, *gid = nullptr;
     int *tstart = nullptr, *tgraph = nullptr, *gtile = nullptr;   // tile -> first node / graph; graph -> first tile

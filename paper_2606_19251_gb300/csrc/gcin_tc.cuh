@@ -1,0 +1,183 @@
+// Tensor-core (tcgen05, sm_103a) form of the GCIN aggregation + node linear
+// for layers 2..4 (Eq. GCN, App. A.1): BF16 operands, FP32 accumulation in
+// tensor memory.  One CTA owns two consecutive statistic tiles of at most 64
+// nodes each (a graph's last tile is ragged; up to 128 nodes = one M = 128
+// MMA tile):
+//   1. warps aggregate h_i = sum_j w_ij x_j (FP32) and store h in BF16 into the
+//      A tile (128 x 64, K-major, canonical no-swizzle core-matrix layout);
+//      W^T goes to the B tile (64 x 64, K-major) in BF16;
+//   2. one thread issues 4 x tcgen05.mma.kind::f16 (M 128, N 64, K 16) into a
+//      64-column TMEM accumulator and commits to an mbarrier;
+//   3. warps 0..3 read their 32 TMEM lanes (rows) with tcgen05.ld, add the
+//      bias, and the CTA writes y and the two tiles' mean / M2 statistics.
+// The mbarrier wait is bounded; on timeout the kernel raises an error flag,
+// waits (bounded) once more, frees its TMEM columns and returns.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace amg {
+
+constexpr int kTcRows = 128;                       // MMA M
+constexpr int kTcA = kTcRows * kHidden * 2;        // 16 KB BF16 A tile
+constexpr int kTcB = kHidden * kHidden * 2;        //  8 KB BF16 B tile
+constexpr int kTcY = kTcRows * (kHidden + 1) * 4;  // FP32 staging of y
+constexpr int kTcSmem = kTcA + kTcB + kTcY;
+
+// Byte offset of element (row, k) in a K-major, no-swizzle tile of 64-wide
+// BF16 rows: core matrices of 8 rows x 16 bytes, K-adjacent cores 128 B
+// apart (leading-dimension offset), 8-row groups 1024 B apart (stride offset).
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+    return static_cast<uint32_t>((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// tcgen05 shared-memory matrix descriptor for that layout.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);        // start address
+    d |= static_cast<uint64_t>(128u >> 4) << 16;                // leading-dimension byte offset (K)
+    d |= static_cast<uint64_t>(1024u >> 4) << 32;               // stride-dimension byte offset (rows)
+    d |= static_cast<uint64_t>(1u) << 46;                       // fixed 0b001
+    return d;                                                   // base offset 0, no swizzle
+}
+
+// Instruction descriptor: D F32, A BF16, B BF16, both K-major, N = 64, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kHidden >> 3) << 17) | ((kTcRows >> 4) << 24);
+
+__device__ __forceinline__ bool tc_try_wait(uint32_t mbar) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(mbar), "r"(0u)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool tc_wait_bounded(uint32_t mbar) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (tc_try_wait(mbar)) return true;
+        if (it > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kBlock) k_agg_lin_tc(const int *__restrict__ rp, const int *__restrict__ col,
+                                                       const float *__restrict__ w, const float *__restrict__ x,
+                                                       const float *__restrict__ W, const float *__restrict__ bias,
+                                                       const int *__restrict__ tstart, int NT,
+                                                       float *__restrict__ hout, float *__restrict__ y,
+                                                       float *__restrict__ tmean, float *__restrict__ tm2,
+                                                       int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char *sA = tc_smem, *sB = tc_smem + kTcA;
+    float(*sY)[kHidden + 1] = reinterpret_cast<float(*)[kHidden + 1]>(tc_smem + kTcA + kTcB);
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_ok;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t a_addr = static_cast<uint32_t>(__cvta_generic_to_shared(sA));
+    const uint32_t b_addr = static_cast<uint32_t>(__cvta_generic_to_shared(sB));
+    const uint32_t mbar = static_cast<uint32_t>(__cvta_generic_to_shared(&s_mbar));
+    if (warp == 0) {
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&s_taddr));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(64u) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // B = W^T (row n = output feature, k = input feature), BF16
+    for (int e = threadIdx.x; e < kHidden * kHidden; e += kBlock) {
+        const int k = e / kHidden, n = e % kHidden;
+        *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off(n, k)) = __float2bfloat16_rn(W[e]);
+    }
+    // A = h of the (up to) 128 nodes of tiles 2b, 2b + 1, BF16
+    const int t0 = 2 * blockIdx.x;
+    const int t1 = min(t0 + 2, NT);
+    const int a0 = tstart[t0], nn = tstart[t1] - a0;
+    const float2 *x2 = reinterpret_cast<const float2 *>(x);
+    for (int k = warp; k < kTcRows; k += kBlock / 32) {
+        __nv_bfloat162 hb = __floats2bfloat162_rn(0.f, 0.f);
+        if (k < nn) {
+            const int i = a0 + k;
+            float hx = 0.f, hy = 0.f;
+            for (int p = rp[i]; p < rp[i + 1]; ++p) {
+                const float wv = w[p];
+                const float2 v = x2[static_cast<size_t>(col[p]) * 32 + lane];
+                hx = fmaf(wv, v.x, hx);
+                hy = fmaf(wv, v.y, hy);
+            }
+            hb = __floats2bfloat162_rn(hx, hy);
+            const float2 hr = __bfloat1622float2(hb);     // the rounded h the MMA sees (kept for the backward)
+            reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = hr;
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off(k, 2 * lane)) = hb;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    if (threadIdx.x == 0) {
+        for (int ks = 0; ks < kHidden / 16; ++ks) {
+            const uint64_t ad = tc_desc(a_addr + ks * 256), bd = tc_desc(b_addr + ks * 256);
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                         ::"r"(taddr), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(static_cast<uint32_t>(ks))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+    }
+    const bool ok = tc_wait_bounded(mbar);
+    if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool all_ok = s_ok != 0;
+    if (all_ok && warp < 4) {
+        uint32_t r[kHidden];
+        const uint32_t ta = taddr + (static_cast<uint32_t>(32 * warp) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+            "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+              "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+              "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+              "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+              "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+            : "r"(ta)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = 32 * warp + lane;
+#pragma unroll
+        for (int f = 0; f < kHidden; ++f) sY[row][f] = __uint_as_float(r[f]) + bias[f];
+    }
+    if (!all_ok) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        tc_wait_bounded(mbar);          // let an in-flight MMA drain before the columns are freed
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(64u) : "memory");
+    if (!all_ok) return;
+    // y (coalesced) and the statistics of the two 64-node tiles
+    for (int e = threadIdx.x; e < nn * kHidden; e += kBlock) {
+        const int k = e / kHidden, f = e % kHidden;
+        y[static_cast<size_t>(a0 + k) * kHidden + f] = sY[k][f];
+    }
+    // the first tile may be a graph's ragged last tile: split at tstart[t0 + 1]
+    const int n0 = tstart[t0 + 1] - a0;
+    tile_stats(sY, n0, tmean + static_cast<size_t>(t0) * kHidden, tm2 + static_cast<size_t>(t0) * kHidden);
+    if (t0 + 1 < t1) {
+        __syncthreads();
+        tile_stats(sY + n0, nn - n0, tmean + static_cast<size_t>(t0 + 1) * kHidden,
+                   tm2 + static_cast<size_t>(t0 + 1) * kHidden);
+    }
+}
+
+}  // namespace amg

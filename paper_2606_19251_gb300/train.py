@@ -42,8 +42,9 @@ class Problem:
 
 
 class Trainer:
-    def __init__(self, theta0, device=0, lr=1e-3, max_norm=1.0, factor=0.1, patience=10, n_vc=1, val_cycles=10):
-        self.tr = P.gcin_trainer_create(theta0, device)
+    def __init__(self, theta0, device=0, lr=1e-3, max_norm=1.0, factor=0.1, patience=10, n_vc=1, val_cycles=10,
+                 precision=P.AMG_GNN_FP32):
+        self.tr = P.gcin_trainer_create(theta0, device, precision)
         self.n_vc, self.val_cycles = n_vc, val_cycles
         self.lr, self.max_norm = lr, max_norm
         self.factor, self.patience = factor, patience

@@ -20,7 +20,15 @@ def test_parameter_count_matches_paper():
     assert sum(s for s, _ in W.GCIN_PARAM_SIZES) == 55045
 
 
-def _library_forward(theta, A):
+def _rne_bf16_bits(t):
+    """bfloat16 rounding done on the FP32 bit pattern (round to nearest, ties to
+    even): keep the top 16 bits after adding 0x7FFF plus the lowest kept bit."""
+    u = t.detach().numpy().astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return torch.from_numpy(u.astype(np.uint32).view(np.float32).astype(np.float64))
+
+
+def _library_forward(theta, A, bf16=False):
     """Same network from library layers: dense A_hat, F.linear, F.instance_norm, F.layer_norm."""
     p = G.unpack(torch.from_numpy(theta))
     Ad = torch.from_numpy(A.to_dense())
@@ -29,7 +37,10 @@ def _library_forward(theta, A):
     x = torch.stack([torch.diagonal(Ad), deg], 1)
     pooled = []
     for l in range(1, 5):
-        y = Fn.linear(Ad @ x, p[f"conv{l}.W"].T, p[f"conv{l}.b"])
+        h, Wt = Ad @ x, p[f"conv{l}.W"].T
+        if bf16 and l > 1:
+            h, Wt = _rne_bf16_bits(h), _rne_bf16_bits(Wt)
+        y = Fn.linear(h, Wt, p[f"conv{l}.b"])
         y = Fn.instance_norm(y.T.unsqueeze(0), weight=p[f"in{l}.gamma"], bias=p[f"in{l}.beta"], eps=1e-5)[0].T
         x = Fn.relu(y)
         g = torch.cat([x.mean(0), x.amax(0)])
@@ -49,6 +60,34 @@ def test_forward_equals_library_layers(kind):
     for k, lv in enumerate(levels):
         ref = _library_forward(theta, lv.A).numpy()
         np.testing.assert_allclose(c[k], ref, rtol=1e-10, atol=1e-12)
+
+
+def test_bf16_rounding_ties_to_even():
+    v = torch.tensor([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 1.0 + 2.0 ** -8 + 2.0 ** -20,
+                      3.0e38, 1.0e-40, 0.0])
+    r = G.bf16_round(v).numpy()
+    assert r[0] == 1.0                       # tie, even neighbour below
+    assert r[1] == 1.0 + 2.0 ** -6           # tie, even neighbour above
+    assert r[2] == -1.0
+    assert r[3] == 1.0 + 2.0 ** -7           # just above the tie
+    x = torch.from_numpy(W.uniform_pm1(5, 4096) * 1e3)
+    assert torch.equal(G.bf16_round(x), _rne_bf16_bits(x))
+
+
+@pytest.mark.parametrize("kind", ["uniform", "band"])
+def test_bf16_mode_equals_library_layers(kind):
+    """BF16 mode rounds exactly the layer 2..4 linear operands."""
+    A = W.fv_mesh(kind, 600, 3, max_aspect=100.0)[0]
+    levels = S.build_hierarchy(A, max_coarse=20)
+    theta = W.gcin_init_params(1, last_scale=1.0)
+    c = G.predict(theta, [l.A for l in levels], bf16_linears=True)
+    c64 = G.predict(theta, [l.A for l in levels])
+    for k, lv in enumerate(levels):
+        ref = _library_forward(theta, lv.A, bf16=True).numpy()
+        np.testing.assert_allclose(c[k], ref, rtol=1e-10, atol=1e-12)
+    # rounding 8-bit mantissas moves the coefficients, but within the BF16 bar
+    d = np.abs(c - c64).max() / np.abs(c64).max()
+    assert 1e-7 < d < 2e-2
 
 
 def test_permutation_invariance():
