@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kBlock) k_resid(int n, const int *__restrict__
     T acc = T(0);
     if (row < n) {
         const int e = rp[row + 1];
-        for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * u[col[p]];
+        acc = row_dot<TPR>(lane, rp[row], e, col, a, Gather<T>{u});
     }
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) r[row] = b[row] - acc;
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int *__restrict__ 
     T acc = T(0);
     if (row < n) {
         const int e = rp[row + 1];
-        for (int p = rp[row] + lane; p < e; p += TPR) acc += m[p] * x[col[p]];
+        acc = row_dot<TPR>(lane, rp[row], e, col, m, Gather<T>{x});
     }
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) y[row] = acc;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(int n, const int *__restrict__
     T acc = T(0);
     if (row < n) {
         const int e = rp[row + 1];
-        for (int p = rp[row] + lane; p < e; p += TPR) acc += m[p] * r[col[p]];
+        acc = row_dot<TPR>(lane, rp[row], e, col, m, Gather<T>{r});
     }
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) u[row] = (add ? u[row] : T(0)) + acc;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
     T acc = T(0);
     if (row < n) {
         const int e = rp[row + 1];
-        for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * uin[col[p]];
+        acc = row_dot<TPR>(lane, rp[row], e, col, a, Gather<T>{uin});
     }
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) uout[row] = uin[row] + jac[row] * (b[row] - acc);
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBlock) k_ma_sweep(int n, const int *__restric
     T acc = T(0);
     if (row < n) {
         const int e = rp[row + 1];
-        for (int p = rp[row] + lane; p < e; p += TPR) acc += ma[p] * uin[col[p]];
+        acc = row_dot<TPR>(lane, rp[row], e, col, ma, Gather<T>{uin});
     }
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) uout[row] = uin[row] + (w[row] - acc);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_w(int n, const int *__restrict
     T acc = T(0);
     if (row < n) {
         const int e = rp[row + 1];
-        for (int p = rp[row] + lane; p < e; p += TPR) acc += m[p] * b[col[p]];
+        acc = row_dot<TPR>(lane, rp[row], e, col, m, Gather<T>{b});
     }
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) {
@@ -186,12 +186,17 @@ __global__ void __launch_bounds__(kBlock) k_resid_restrict(int nc, const int *__
     const int row = g / TPR, lane = g % TPR;
     T acc = T(0);
     if (row < nc) {
-        for (int p = rrp[row] + lane; p < rrp[row + 1]; p += TPR) acc += rv[p] * b[rcol[p]];
-        for (int p = sp[row] + lane; p < sp[row + 1]; p += TPR) acc -= sv[p] * u[scol[p]];
+        acc = row_dot<TPR>(lane, rrp[row], rrp[row + 1], rcol, rv, Gather<T>{b});
+        acc -= row_dot<TPR>(lane, sp[row], sp[row + 1], scol, sv, Gather<T>{u});
     }
     acc = group_sum<TPR>(acc);
     if (row < nc && lane == 0) bc[row] = acc;
 }
+
+template <class T> struct JacB {   // gathered j_j b_j
+    const T *__restrict__ jac, *__restrict__ b;
+    __device__ __forceinline__ T operator()(int j) const { return jac[j] * b[j]; }
+};
 
 // Two Jacobi sweeps from zero in one pass: u = j b + j (b - A (j b)), j = omega/a_ii
 template <class T, int TPR>
@@ -204,10 +209,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__re
     T acc = T(0);
     if (row < n) {
         const int e = rp[row + 1];
-        for (int p = rp[row] + lane; p < e; p += TPR) {
-            const int j = col[p];
-            acc += a[p] * (jac[j] * b[j]);
-        }
+        acc = row_dot<TPR>(lane, rp[row], e, col, a, JacB<T>{jac, b});
     }
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) {
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(int n, const int *__rest
         double acc = 0.0;
         if (row < n) {
             const int e = rp[row + 1];
-            for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * x[col[p]];
+            acc = row_dot<TPR>(lane, rp[row], e, col, a, Gather<double>{x});
         }
         acc = group_sum<TPR>(acc);
         if (row < n && lane == 0) {
@@ -618,6 +620,13 @@ static int outer_blocks(const DevMat &A) {
     return static_cast<int>(std::max(1LL, std::min(need, cap)));
 }
 
+// FP64 outer residual with nb = outer_blocks(A) partial sums.
+template <class T>
+static void L_outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nb,
+                    cudaStream_t s) {
+    TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, b, x, rT, partial, nb, s);
+}
+
 // ---------------------------------------------------------------------------
 // V-cycle driver
 // ---------------------------------------------------------------------------
@@ -759,8 +768,7 @@ static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s, int use_cond = 0,
                                    cudaGraphConditionalHandle cond = 0) {
     const DevMat &A = c->lev[0].A;
     const int nb = outer_blocks(A);
-    TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb),
-                 c->partials, nb, s);
+    L_outer<T>(A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb), c->partials, nb, s);
     launch_pdl(k_norm_final, dim3(1), dim3(1024), 0, s, c->partials, nb, c->state, c->hist, 1, use_cond, cond);
 }
 
@@ -1621,8 +1629,7 @@ int kernel_launch(amg_ctx *c, int which, int l, int reps, cudaStream_t s, double
             by = 4.0 * (A.nr + 1) + 12.0 * A.nnz + 16.0 * A.nr + tb * A.nr;
             const int nb = outer_blocks(A);
             for (int k = 0; k < reps; ++k) {
-                TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, c->db, c->dx,
-                             reinterpret_cast<T *>(c->lev[0].vr), c->partials, nb, s);
+                L_outer<T>(A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vr), c->partials, nb, s);
             }
             break;
         }
@@ -1700,7 +1707,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_norm_static(int n, const int *
         double acc = 0.0;
         if (row < n) {
             const int e = rp[row + 1];
-            for (int p = rp[row] + lane; p < e; p += TPR) acc += a[p] * x[col[p]];
+            acc = row_dot<TPR>(lane, rp[row], e, col, a, Gather<double>{x});
         }
         acc = group_sum<TPR>(acc);
         if (row < n && lane == 0) {

@@ -45,6 +45,39 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Dot product of one CSR row with a gathered operand, split over the TPR
+// lanes of a row group: lane `lane` takes entries p0 + lane, p0 + lane + TPR,
+// ... and adds them in that order.  Each step issues the col / value loads of
+// four entries before their four gathers, so a lane has up to eight loads in
+// flight instead of one dependent pair per entry.
+template <int TPR, class T, class X>
+__device__ __forceinline__ T row_dot(int lane, int p0, int e, const int *__restrict__ col,
+                                     const T *__restrict__ val, const X &xg) {
+    T acc = T(0);
+    for (int base = p0 + lane; base < e; base += 4 * TPR) {
+        int c[4];
+        T v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int p = base + j * TPR;
+            c[j] = p < e ? __ldg(col + p) : 0;
+            v[j] = p < e ? __ldg(val + p) : T(0);
+        }
+        T x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = (base + j * TPR < e) ? xg(c[j]) : T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (base + j * TPR < e) acc += v[j] * x[j];
+    }
+    return acc;
+}
+
+template <class T> struct Gather {
+    const T *__restrict__ x;
+    __device__ __forceinline__ T operator()(int j) const { return x[j]; }
+};
+
 // Programmatic dependent launch (PDL).  A solve-path kernel first waits for
 // its predecessor grid to finish and flush (griddepcontrol.wait), touching no
 // memory before that, then lets its own dependents start launching, so the

@@ -70,6 +70,15 @@ static void batch_layout(GcinBatch &b, Planner &pl, bool backward) {
     b.tstart = pl.take<int>(NT + 1);
     b.tgraph = pl.take<int>(NT);
     b.gtile = pl.take<int>(G + 1);
+    const size_t NC = b.NC;
+    b.ctile = pl.take<int>(NC + 1);
+    b.cnode = pl.take<int>(NC + 1);
+    b.gchunk = pl.take<int>(G + 1);
+    b.cmean = pl.take<float>(NC * kHidden);
+    b.cm2 = pl.take<float>(NC * kHidden);
+    b.cmax = pl.take<float>(NC * kHidden);
+    b.csum = pl.take<double>(NC * kHidden);
+    b.carg = pl.take<int>(NC * kHidden);
     b.x0 = pl.take<double>(N * 2);
     b.h1 = pl.take<float>(N * 2);
     for (int l = 0; l < kLayers; ++l) {
@@ -136,6 +145,18 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
     b.E = E;
     tstart.push_back(b.N);
     gtile.push_back(b.NT);
+    std::vector<int> ctile, cnode, gchunk;
+    for (int g = 0; g < b.G; ++g) {
+        gchunk.push_back(static_cast<int>(ctile.size()));
+        for (int t = gtile[g]; t < gtile[g + 1]; t += kChunkTiles) {
+            ctile.push_back(t);
+            cnode.push_back(tstart[t]);
+        }
+    }
+    b.NC = static_cast<int>(ctile.size());
+    ctile.push_back(b.NT);
+    cnode.push_back(b.N);
+    gchunk.push_back(b.NC);
     Planner pl;
     batch_layout(b, pl, backward);
     cudaError_t e = cudaMalloc(&b.arena, pl.off);
@@ -152,6 +173,9 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
     cudaMemcpyAsync(b.tstart, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b.tgraph, tgraph.data(), sizeof(int) * tgraph.size(), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b.gtile, gtile.data(), sizeof(int) * gtile.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b.ctile, ctile.data(), sizeof(int) * ctile.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b.cnode, cnode.data(), sizeof(int) * cnode.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b.gchunk, gchunk.data(), sizeof(int) * gchunk.size(), cudaMemcpyHostToDevice, s);
     int g = 0;
     long long eoff = 0;
     for (int m = 0; m < n_problems; ++m) {
@@ -256,6 +280,50 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
     tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
 }
 
+// h_i = sum_p w_p x_{col p} for the warp's row (lane owns features 2 lane,
+// 2 lane + 1), entries added in row order.  Up to 32 (col, w) pairs come in
+// with one coalesced load and are broadcast by shuffles; four 256-byte row
+// gathers are in flight at a time.  Called by a whole warp.
+__device__ __forceinline__ float2 agg_row64(int p0, int p1, const int *__restrict__ col, const float *__restrict__ w,
+                                            const float2 *__restrict__ x2, int lane) {
+    float hx = 0.f, hy = 0.f;
+    for (int pb = p0; pb < p1; pb += 32) {
+        const int cnt = min(32, p1 - pb);
+        int cj = 0;
+        float wj = 0.f;
+        if (lane < cnt) {
+            cj = col[pb + lane];
+            wj = w[pb + lane];
+        }
+        int k = 0;
+        for (; k + 4 <= cnt; k += 4) {
+            int c[4];
+            float wk[4];
+            float2 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                c[j] = __shfl_sync(0xffffffffu, cj, k + j);
+                wk[j] = __shfl_sync(0xffffffffu, wj, k + j);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = x2[static_cast<size_t>(c[j]) * 32 + lane];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                hx = fmaf(wk[j], v[j].x, hx);
+                hy = fmaf(wk[j], v[j].y, hy);
+            }
+        }
+        for (; k < cnt; ++k) {
+            const int c = __shfl_sync(0xffffffffu, cj, k);
+            const float wk = __shfl_sync(0xffffffffu, wj, k);
+            const float2 v = x2[static_cast<size_t>(c) * 32 + lane];
+            hx = fmaf(wk, v.x, hx);
+            hy = fmaf(wk, v.y, hy);
+        }
+    }
+    return make_float2(hx, hy);
+}
+
 // Layers 2..4: h = A_hat x (64 features), y = h W + b; tile stats.
 __global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__ rp, const int *__restrict__ col,
                                                          const float *__restrict__ w, const float *__restrict__ x,
@@ -273,14 +341,9 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__
     const float2 b2 = reinterpret_cast<const float2 *>(bias)[lane];
     for (int k = warp; k < nn; k += kBlock / 32) {
         const int i = a + k;
-        float hx = 0.f, hy = 0.f;
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            const float wv = w[p];
-            const float2 v = x2[static_cast<size_t>(col[p]) * 32 + lane];
-            hx = fmaf(wv, v.x, hx);
-            hy = fmaf(wv, v.y, hy);
-        }
-        reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = make_float2(hx, hy);
+        const float2 hv = agg_row64(rp[i], rp[i + 1], col, w, x2, lane);
+        const float hx = hv.x, hy = hv.y;
+        reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = hv;
         float y0 = b2.x, y1 = b2.y;
 #pragma unroll 8
         for (int m = 0; m < kHidden; ++m) {
@@ -313,14 +376,18 @@ __device__ __forceinline__ double lanes_sum(double v, double (*red)[kHidden]) {
     return t;
 }
 
-// Per-graph instance-norm statistics from the tile partials (biased
-// variance): mean = sum_t n_t mean_t / n, M2 = sum_t [M2_t + n_t (mean_t - mean)^2].
-// 16 lanes of tiles per feature; one FP64 add per tile, the rest in FP32.
+// Group statistics from part statistics (biased variance):
+// mean = sum_t n_t mean_t / n, M2 = sum_t [M2_t + n_t (mean_t - mean)^2].
+// Parts t of group g are gtile[g] .. gtile[g+1] with node ranges
+// tstart[t] .. tstart[t+1].  Run twice: tiles -> chunks (final = 0: writes
+// the chunk mean and M2 into mu / rstd) and chunks -> graphs (final = 1:
+// writes the instance-norm mean and 1/sqrt(var + eps)).  16 lanes of parts
+// per feature; one FP64 add per part, the rest in FP32.
 __global__ void __launch_bounds__(kCombine) k_stats_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
                                                             const int *__restrict__ tstart,
                                                             const float *__restrict__ tmean,
                                                             const float *__restrict__ tm2, float *__restrict__ mu,
-                                                            float *__restrict__ rstd) {
+                                                            float *__restrict__ rstd, int final) {
     __shared__ double red[kLanes][kHidden];
     const int g = blockIdx.x, f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
     const double n = gptr[g + 1] - gptr[g];
@@ -337,8 +404,9 @@ __global__ void __launch_bounds__(kCombine) k_stats_combine(const int *__restric
     }
     const double m2 = lanes_sum(v, red);
     if (q == 0) {
-        mu[g * kHidden + f] = mf;
-        rstd[g * kHidden + f] = static_cast<float>(1.0 / sqrt(m2 / n + static_cast<double>(kEps)));
+        mu[static_cast<size_t>(g) * kHidden + f] = mf;
+        rstd[static_cast<size_t>(g) * kHidden + f] =
+            final ? static_cast<float>(1.0 / sqrt(m2 / n + static_cast<double>(kEps))) : static_cast<float>(m2);
     }
 }
 
@@ -386,12 +454,16 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
     }
 }
 
-// Per-graph mean and max (first index of the max kept) from the tile partials.
+// Group sum and max (first index of the max kept) from part partials; as
+// for the statistics, tiles -> chunks (csum != nullptr: writes the chunk sum,
+// max and argmax) and chunks -> graphs (writes the pooled mean and max).
 __global__ void __launch_bounds__(kCombine) k_pool_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
                                                            const double *__restrict__ tsum,
                                                            const float *__restrict__ tmax,
                                                            const int *__restrict__ targ, float *__restrict__ pooled,
-                                                           int *__restrict__ argmax, int layer) {
+                                                           int *__restrict__ argmax, int layer,
+                                                           double *__restrict__ csum, float *__restrict__ cmax,
+                                                           int *__restrict__ carg) {
     __shared__ double red[kLanes][kHidden];
     __shared__ float rm[kLanes][kHidden];
     __shared__ int ri[kLanes][kHidden];
@@ -410,6 +482,13 @@ __global__ void __launch_bounds__(kCombine) k_pool_combine(const int *__restrict
     if (q == 0) {
         for (int k = 1; k < kLanes; ++k)
             if (rm[k][f] > bm || (rm[k][f] == bm && ri[k][f] < bi)) { bm = rm[k][f]; bi = ri[k][f]; }
+        if (csum) {
+            const size_t o = static_cast<size_t>(g) * kHidden + f;
+            csum[o] = total;
+            cmax[o] = bm;
+            carg[o] = bi;
+            return;
+        }
         float *P = pooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
         P[f] = static_cast<float>(total / (gptr[g + 1] - gptr[g]));
         P[kHidden + f] = bm;
@@ -509,11 +588,15 @@ void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
                                                  th + kPL.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
                                                  b.tm2); AMG_COUNT();
         }
-        k_stats_combine<<<G, kCombine, 0, s>>>(b.gtile, b.gptr, b.tstart, b.tmean, b.tm2, b.mu[l], b.rstd[l]); AMG_COUNT();
+        k_stats_combine<<<b.NC, kCombine, 0, s>>>(b.ctile, b.cnode, b.tstart, b.tmean, b.tm2, b.cmean, b.cm2, 0); AMG_COUNT();
+        k_stats_combine<<<G, kCombine, 0, s>>>(b.gchunk, b.gptr, b.cnode, b.cmean, b.cm2, b.mu[l], b.rstd[l], 1); AMG_COUNT();
         k_norm_relu_pool_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
                                                     th + kPL.inG[l], th + kPL.inB[l], b.x[l], b.tsum, b.tmax,
                                                     b.targ); AMG_COUNT();
-        k_pool_combine<<<G, kCombine, 0, s>>>(b.gtile, b.gptr, b.tsum, b.tmax, b.targ, b.pooled, b.argmax, l); AMG_COUNT();
+        k_pool_combine<<<b.NC, kCombine, 0, s>>>(b.ctile, b.cnode, b.tsum, b.tmax, b.targ, nullptr, nullptr, l,
+                                                 b.csum, b.cmax, b.carg); AMG_COUNT();
+        k_pool_combine<<<G, kCombine, 0, s>>>(b.gchunk, b.gptr, b.csum, b.cmax, b.carg, b.pooled, b.argmax, l,
+                                              nullptr, nullptr, nullptr); AMG_COUNT();
     }
     k_head<<<G, 128, 0, s>>>(b.pooled, th, b.head, b.c); AMG_COUNT();
 }
@@ -765,15 +848,8 @@ __global__ void __launch_bounds__(kBlock) k_agg_plain(int N, const int *__restri
                                                       float *__restrict__ out) {
     const int i = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32;
     if (i >= N) return;
-    const float2 *v2 = reinterpret_cast<const float2 *>(v);
-    float ax = 0.f, ay = 0.f;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const float wv = w[p];
-        const float2 u = v2[static_cast<size_t>(col[p]) * 32 + lane];
-        ax = fmaf(wv, u.x, ax);
-        ay = fmaf(wv, u.y, ay);
-    }
-    reinterpret_cast<float2 *>(out)[static_cast<size_t>(i) * 32 + lane] = make_float2(ax, ay);
+    reinterpret_cast<float2 *>(out)[static_cast<size_t>(i) * 32 + lane] =
+        agg_row64(rp[i], rp[i + 1], col, w, reinterpret_cast<const float2 *>(v), lane);
 }
 
 // Conv weight/bias gradient: tile partials summed per chunk of tiles (FP64,

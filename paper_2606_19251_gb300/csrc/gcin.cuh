@@ -61,6 +61,7 @@ static_assert(kPL.total == kNumParams, "GCIN layout must have 55,045 parameters 
 // cross a graph boundary; every reduction over a graph is a fixed-order
 // combination of per-tile partials (deterministic, no atomics).
 constexpr int kTile = 64;
+constexpr int kChunkTiles = 64;
 constexpr int kGradChunks = 64;      // tile chunks of the weight-gradient reduction
 
 struct GcinBatch {
@@ -70,6 +71,13 @@ struct GcinBatch {
     long long E = 0;
     int *rp = nullptr, *col = nullptr, *gptr = nullptr, *gid = nullptr;
     int *tstart = nullptr, *tgraph = nullptr, *gtile = nullptr;   // tile -> first node / graph; graph -> first tile
+    // chunks of up to kChunkTiles tiles of one graph: the per-graph
+    // reductions run tiles -> chunks -> graph, every stage in parallel
+    int NC = 0;
+    int *ctile = nullptr, *cnode = nullptr, *gchunk = nullptr;      // chunk -> first tile / node; graph -> first chunk
+    float *cmean = nullptr, *cm2 = nullptr, *cmax = nullptr;        // NC x 64 chunk statistics
+    double *csum = nullptr;                                         // NC x 64
+    int *carg = nullptr;                                            // NC x 64
     float *w = nullptr;
     double *w64 = nullptr;
     // activations (kept for the backward pass)

@@ -103,14 +103,8 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tc(const int *__restrict__ r
         __nv_bfloat162 hb = __floats2bfloat162_rn(0.f, 0.f);
         if (k < nn) {
             const int i = a0 + k;
-            float hx = 0.f, hy = 0.f;
-            for (int p = rp[i]; p < rp[i + 1]; ++p) {
-                const float wv = w[p];
-                const float2 v = x2[static_cast<size_t>(col[p]) * 32 + lane];
-                hx = fmaf(wv, v.x, hx);
-                hy = fmaf(wv, v.y, hy);
-            }
-            hb = __floats2bfloat162_rn(hx, hy);
+            const float2 hv = agg_row64(rp[i], rp[i + 1], col, w, x2, lane);
+            hb = __floats2bfloat162_rn(hv.x, hv.y);
             const float2 hr = __bfloat1622float2(hb);     // the rounded h the MMA sees (kept for the backward)
             reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = hr;
         }
