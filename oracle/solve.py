@@ -21,6 +21,13 @@ autograd can differentiate through the smoother's values (Sec. 3.3).
 * Sec. 3.3: the relative validation metric
   log10(||r_{n+1}|| / ||r^{omega-J}_{n+1}||) after one cycle from the same
   state.
+* Krylov outer loop (the Krylov form of the Sec. 2.1 correction): conjugate
+  gradients on A u = f preconditioned by one V-cycle from a zero guess
+  (symmetric for a symmetric smoother), with the flexible coefficient
+  beta = z_k . (r_k - r_{k-1}) / (z_{k-1} . r_{k-1}), which equals the
+  classical z_k . r_k / (z_{k-1} . r_{k-1}) for a fixed symmetric
+  preconditioner and keeps a slightly non-symmetric one (an FP32 V-cycle)
+  convergent.
 """
 from __future__ import annotations
 
@@ -218,6 +225,66 @@ def solve(h: OHierarchy, f, tol: float = 1e-8, max_iter: int = 500, u0=None,
             u = vcycle(h, f, u, nu1, nu2)
             k += 1
             rn = float(torch.linalg.vector_norm(f - mv(A, u)))
+            hist.append(rn / fnorm)
+            if not math.isfinite(rn) or rn > 1e3 * r0:
+                status = DIVERGED
+                break
+            if hist[-1] <= tol:
+                status = OK
+                break
+            if k >= 10 and hist[-1] > 0.99 * hist[-11]:
+                status = STAGNATED
+                break
+    return SolveResult(u.numpy(), hist, k, status)
+
+
+def solve_pcg(h: OHierarchy, f, tol: float = 1e-8, max_iter: int = 500, u0=None, nu1: int = 2, nu2: int = 2,
+              precond=None) -> SolveResult:
+    """Preconditioned conjugate gradients to ||r|| / ||f|| <= tol (FP64).
+
+    precond(r) -> z defaults to one V-cycle from a zero initial guess.  The
+    history holds the recurrence residual r_{k+1} = r_k - alpha q_k relative
+    to ||f||; statuses as in solve(), and DIVERGED also on a breakdown
+    (z . r <= 0 or p . A p <= 0: the preconditioned operator is not SPD),
+    which leaves the iterate and the history as they were.
+    """
+    f = torch.as_tensor(np.asarray(f, dtype=np.float64))
+    A = h.levels[0].A
+    if precond is None:
+        def precond(r):
+            with torch.no_grad():
+                return vcycle(h, r, torch.zeros_like(r), nu1, nu2)
+    u = torch.zeros(A.n_rows, dtype=DT) if u0 is None else torch.as_tensor(np.asarray(u0, dtype=np.float64)).clone()
+    fnorm = float(torch.linalg.vector_norm(f))
+    if fnorm == 0.0:
+        fnorm = 1.0
+    r = f - mv(A, u)
+    r0 = float(torch.linalg.vector_norm(r))
+    hist = [r0 / fnorm]
+    if hist[0] <= tol:
+        return SolveResult(u.numpy(), hist, 0, OK)
+    status, k = MAXITER, 0
+    p = r_prev = rho_prev = None
+    with torch.no_grad():
+        while k < max_iter:
+            z = precond(r)
+            rho = float(torch.dot(z, r))
+            if p is None:
+                p = z.clone()
+            else:
+                beta = float(torch.dot(z, r - r_prev)) / rho_prev
+                p = z + beta * p
+            q = mv(A, p)
+            pq = float(torch.dot(p, q))
+            if not (math.isfinite(rho) and math.isfinite(pq) and rho > 0.0 and pq > 0.0):
+                status = DIVERGED          # breakdown: the iterate and history stay as they were
+                break
+            k += 1
+            alpha = rho / pq
+            u = u + alpha * p
+            r_prev, rho_prev = r, rho
+            r = r - alpha * q
+            rn = float(torch.linalg.vector_norm(r))
             hist.append(rn / fnorm)
             if not math.isfinite(rn) or rn > 1e3 * r0:
                 status = DIVERGED

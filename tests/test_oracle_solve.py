@@ -158,3 +158,79 @@ def test_relative_metric_zero_for_identical_smoothers():
     hg = _hier(A, "pinv", [2.0 / 3.0, 0, 0, 0, 0], max_coarse=8)
     hj = _hier(A, max_coarse=8)
     assert abs(O.relative_metric(hg, hj, W.rhs_uniform(1, A.n_rows))) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Krylov outer loop (conjugate gradients preconditioned by one V-cycle)
+# ---------------------------------------------------------------------------
+def _iterates_scipy_cg(A, b, precond, k):
+    """x_1 .. x_k of scipy's (classical) preconditioned CG."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    As = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n_rows, A.n_rows))
+    M = sla.LinearOperator(As.shape, matvec=lambda r: precond(torch.from_numpy(np.asarray(r).ravel())).numpy())
+    xs = []
+    sla.cg(As, b, M=M, rtol=1e-300, atol=0.0, maxiter=k, callback=lambda x: xs.append(np.array(x)))
+    return xs
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "pinv"])
+def test_pcg_iterates_equal_scipy_cg(smoother):
+    """With a fixed symmetric preconditioner (FP64 V-cycle) the flexible
+    coefficient reduces to the classical one: every iterate equals scipy's."""
+    A = W.fv_mesh("graded", 1500, 3)[0]
+    levels = S.build_hierarchy(A)
+    h = O.OHierarchy.of(levels)
+    if smoother == "jacobi":
+        h.set_jacobi()
+    else:
+        h.set_pseudo_inverse([[0.62, 0.03, -0.01, -0.18, 0.02]] * len(levels))
+    b = W.rhs_uniform(4, A.n_rows)
+    pre = lambda r: O.vcycle(h, r, torch.zeros_like(r))
+    ref = _iterates_scipy_cg(A, b, pre, 6)
+    for k in range(1, 7):
+        res = O.solve_pcg(h, b, tol=0.0, max_iter=k)
+        assert res.n_vcycles == k
+        assert np.abs(res.x - ref[k - 1]).max() <= 1e-10 * np.abs(ref[k - 1]).max()
+        # the recurrence residual is the true residual in FP64
+        rt = b - O.mv(h.levels[0].A, torch.from_numpy(res.x)).numpy()
+        assert abs(np.linalg.norm(rt) / np.linalg.norm(b) - res.history[-1]) <= 1e-10
+
+
+def test_pcg_exact_preconditioner_converges_in_one_step():
+    A = W.poisson5(9)
+    h = O.OHierarchy.of(S.build_hierarchy(A, max_coarse=4))
+    Ad = A.to_dense()
+    b = W.rhs_uniform(1, A.n_rows)
+    res = O.solve_pcg(h, b, tol=1e-12, precond=lambda r: torch.from_numpy(np.linalg.solve(Ad, r.numpy())))
+    assert res.status == O.OK and res.n_vcycles == 1
+    assert np.abs(res.x - np.linalg.solve(Ad, b)).max() <= 1e-12 * np.abs(res.x).max()
+
+
+def test_pcg_unpreconditioned_finishes_in_n_steps():
+    """Plain CG on an n x n SPD matrix reaches the solution in at most n steps."""
+    A = W.poisson5(4)              # n = 16, four distinct eigenvalue clusters by symmetry
+    h = O.OHierarchy.of(S.build_hierarchy(A, max_coarse=4))
+    b = W.rhs_uniform(2, A.n_rows)
+    res = O.solve_pcg(h, b, tol=1e-13, precond=lambda r: r.clone())
+    assert res.status == O.OK and res.n_vcycles <= A.n_rows
+    assert np.abs(res.x - np.linalg.solve(A.to_dense(), b)).max() <= 1e-10
+
+
+def test_pcg_beats_stationary_iteration():
+    A = W.fv_mesh("band", 3000, 7, max_aspect=100.0)[0]
+    h = O.OHierarchy.of(S.build_hierarchy(A))
+    h.set_jacobi()
+    b = W.rhs_zero_mean(3, A.n_rows)
+    st = O.solve(h, b, tol=1e-8)
+    kr = O.solve_pcg(h, b, tol=1e-8)
+    assert st.status == kr.status == O.OK
+    assert kr.n_vcycles < st.n_vcycles
+
+
+def test_pcg_breakdown_on_indefinite_preconditioner():
+    A = W.poisson5(8)
+    h = O.OHierarchy.of(S.build_hierarchy(A, max_coarse=4))
+    b = W.rhs_uniform(3, A.n_rows)
+    res = O.solve_pcg(h, b, tol=1e-8, precond=lambda r: -r)
+    assert res.status == O.DIVERGED and res.n_vcycles == 0 and len(res.history) == 1
