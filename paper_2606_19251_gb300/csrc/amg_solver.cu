@@ -440,7 +440,8 @@ __global__ void k_max_final(const double *__restrict__ partial, int np, double *
 // hierarchy: bx = a_ij / s and bw = 1 / a_ii (diagonal) or 1 / (a_ii + a_jj).
 __global__ void k_pinv_basis(int n, const int *__restrict__ rp, const int *__restrict__ col,
                              const double *__restrict__ a, const double *__restrict__ d,
-                             const double *__restrict__ s_ptr, double *__restrict__ bx, double *__restrict__ bw) {
+                             const double *__restrict__ s_ptr, double *__restrict__ bx, double *__restrict__ bw,
+                             unsigned char *__restrict__ isd) {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= n) return;
     const double s = *s_ptr, di = d[i];
@@ -448,25 +449,24 @@ __global__ void k_pinv_basis(int n, const int *__restrict__ rp, const int *__res
         const int j = col[p];
         bx[p] = a[p] / s;
         bw[p] = 1.0 / (j == i ? di : di + d[j]);
+        isd[p] = (j == i) ? 1 : 0;
     }
 }
 
 // Q^-1 values on A's pattern from c = (d0, d1, d2, o1, o2) (Sec. 3.1):
 // q_ii = (d0 + d1 x + d2 x^2) bw, q_ij = (o1 x + o2 x^2) bw, in FP64 with the
 // polynomial evaluated as d0 + d1 x + (d2 x) x, uncontracted.
-__global__ void k_assemble_q(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                             const double *__restrict__ bx, const double *__restrict__ bw, double c0, double c1,
-                             double c2, double c3, double c4, double *__restrict__ q64, float *__restrict__ q32) {
-    int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= n) return;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const double x = bx[p];
-        const double f = (col[p] == i) ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
-                                       : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
-        const double q = __dmul_rn(f, bw[p]);
-        q64[p] = q;
-        q32[p] = static_cast<float>(q);
-    }
+__global__ void k_assemble_q(int nnz, const unsigned char *__restrict__ isd, const double *__restrict__ bx,
+                             const double *__restrict__ bw, double c0, double c1, double c2, double c3, double c4,
+                             double *__restrict__ q64, float *__restrict__ q32) {
+    const int p = blockIdx.x * kBlock + threadIdx.x;
+    if (p >= nnz) return;
+    const double x = bx[p];
+    const double f = isd[p] ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
+                            : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
+    const double q = __dmul_rn(f, bw[p]);
+    q64[p] = q;
+    q32[p] = static_cast<float>(q);
 }
 
 __global__ void k_jacobi_vals(int n, const double *__restrict__ d, double omega, double *__restrict__ j64,
@@ -917,6 +917,7 @@ static void layout(amg_ctx *c, Planner &pl) {
         }
         L.diag = pl.take<double>(L.n);
         L.bx = pl.take<double>(std::max(1, L.A.nnz));
+        L.isd = pl.take<unsigned char>(std::max(1, L.A.nnz));
         L.bw = pl.take<double>(std::max(1, L.A.nnz));
         L.q64 = pl.take<double>(std::max(1, L.A.nnz));
         L.q32 = pl.take<float>(std::max(1, L.A.nnz));
@@ -1029,7 +1030,7 @@ static int upload(amg_ctx *c) {
         k_max_final<<<1, 32, 0, s>>>(c->partials, nb, c->scal + l); AMG_COUNT();
         k_jacobi_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, c->opt.omega, L.j64, L.j32); AMG_COUNT();
         k_pinv_basis<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag, c->scal + l, L.bx,
-                                                      L.bw); AMG_COUNT();
+                                                      L.bw, L.isd); AMG_COUNT();
     }
     c->jac_omega = c->opt.omega;
     // coarsest level: dense FP64 Cholesky and the inverse factor
@@ -1258,8 +1259,8 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
         const double *q = coef + 5 * l;
         for (int k = 0; k < 5; ++k)
             if (!std::isfinite(q[k])) return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
-        k_assemble_q<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.bx, L.bw, q[0], q[1], q[2], q[3],
-                                                      q[4], L.q64, L.q32); AMG_COUNT();
+        k_assemble_q<<<grid_for(L.A.nnz), kBlock, 0, s>>>(L.A.nnz, L.isd, L.bx, L.bw, q[0], q[1], q[2], q[3],
+                                                          q[4], L.q64, L.q32); AMG_COUNT();
         if (L.fast) {
             k_assemble_ma<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q64, L.A.v64,
                                                                 L.MA.v64, L.MA.v32); AMG_COUNT();

@@ -24,6 +24,7 @@ struct DevLevel {
     DevMat A, P, R;                            // P: n x n_{l+1}; R: n_{l+1} x n
     double *diag = nullptr;                    // a_ii (FP64)
     double *bx = nullptr, *bw = nullptr;       // pseudo-inverse basis a_ij/s and 1/a_ii or 1/(a_ii+a_jj)
+    unsigned char *isd = nullptr;              // 1 on the diagonal entries of A's pattern
     double *q64 = nullptr; float *q32 = nullptr;   // pseudo-inverse values on A's pattern
     double *j64 = nullptr; float *j32 = nullptr;   // omega / a_ii
     // V-cycle vectors; storage sized for n doubles, used as float or double

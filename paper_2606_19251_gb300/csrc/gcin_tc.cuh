@@ -23,8 +23,8 @@ namespace amg {
 constexpr int kTcRows = 128;                       // MMA M
 constexpr int kTcA = kTcRows * kHidden * 2;        // 16 KB BF16 A tile
 constexpr int kTcB = kHidden * kHidden * 2;        //  8 KB BF16 B tile
-constexpr int kTcY = kTcRows * (kHidden + 1) * 4;  // FP32 staging of y
-constexpr int kTcSmem = kTcA + kTcB + kTcY;
+constexpr int kTcY = kTcRows * (kHidden + 1) * 4;  // FP32 staging of y, reusing the operand tiles
+constexpr int kTcSmem = (kTcA + kTcB > kTcY) ? kTcA + kTcB : kTcY;
 
 // Byte offset of element (row, k) in a K-major, no-swizzle tile of 64-wide
 // BF16 rows: core matrices of 8 rows x 16 bytes, K-adjacent cores 128 B
@@ -63,7 +63,7 @@ __device__ __forceinline__ bool tc_wait_bounded(uint32_t mbar) {
     return false;
 }
 
-__global__ void __launch_bounds__(kBlock) k_agg_lin_tc(const int *__restrict__ rp, const int *__restrict__ col,
+__global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict__ rp, const int *__restrict__ col,
                                                        const float *__restrict__ w, const float *__restrict__ x,
                                                        const float *__restrict__ W, const float *__restrict__ bias,
                                                        const int *__restrict__ tstart, int NT,
@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tc(const int *__restrict__ r
                                                        int *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char tc_smem[];
     unsigned char *sA = tc_smem, *sB = tc_smem + kTcA;
-    float(*sY)[kHidden + 1] = reinterpret_cast<float(*)[kHidden + 1]>(tc_smem + kTcA + kTcB);
+    // y is staged over the A / B tiles once the MMAs that read them have completed
+    float(*sY)[kHidden + 1] = reinterpret_cast<float(*)[kHidden + 1]>(tc_smem);
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ int s_ok;
@@ -130,26 +131,25 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tc(const int *__restrict__ r
     __syncthreads();
     const bool all_ok = s_ok != 0;
     if (all_ok && warp < 4) {
-        uint32_t r[kHidden];
-        const uint32_t ta = taddr + (static_cast<uint32_t>(32 * warp) << 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-            "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-              "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-              "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-              "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-              "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-            : "r"(ta)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // warp w reads TMEM lanes 32 w .. 32 w + 31 (its rows), 32 columns at a time
         const int row = 32 * warp + lane;
 #pragma unroll
-        for (int f = 0; f < kHidden; ++f) sY[row][f] = __uint_as_float(r[f]) + bias[f];
+        for (int half = 0; half < 2; ++half) {
+            uint32_t r[32];
+            const uint32_t ta = taddr + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(32 * half);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                  "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(ta)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int f = 0; f < 32; ++f) sY[row][32 * half + f] = __uint_as_float(r[f]) + bias[32 * half + f];
+        }
     }
     if (!all_ok) {
         if (threadIdx.x == 0) atomicExch(err, 1);
