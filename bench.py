@@ -179,6 +179,15 @@ def run_gpu(args, wl, rank, world):
     nlev = P.amg_num_levels(ctx)
     K, Wm = args.steps, args.warmup
     rhs_host = [torch.from_numpy(wl["rhs"](1000 + 7919 * rank + k, n)).pin_memory() for k in range(Wm + K)]
+    # per-mesh setup of the learned smoother (not part of a step): predict the
+    # coefficients and let the Jacobi judge decide whether this mesh keeps them
+    # (Sec. 3.3 fallback); a kept smoother also arms the in-solve stall check
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.gnn_predict_coeffs(ctx)
+    reroute_metric, kept = P.amg_reroute(ctx, rhs_host[0].numpy(), 30)
+    reroute_ms = (time.perf_counter() - t0) * 1e3
+    use_gnn = kept == P.AMG_SMOOTHER_GNN
     rhs_dev = [r.to(f"cuda:{dev}") for r in rhs_host]
     x = torch.zeros(n, dtype=torch.float64, device=f"cuda:{dev}")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
@@ -196,7 +205,9 @@ def run_gpu(args, wl, rank, world):
         return e0.elapsed_time(e1), out
 
     def gnn_step(k):
-        P.gnn_predict_coeffs(ctx)
+        # a mesh the judge rerouted solves with Jacobi and skips the inference
+        if use_gnn:
+            P.gnn_predict_coeffs(ctx)
         return P.amg_solve_device(ctx, rhs_dev[k], x, TOL)
 
     def solve_only(k):
@@ -232,6 +243,8 @@ def run_gpu(args, wl, rank, world):
 
     # solve-only and inference-only splits, and the Jacobi baseline
     P.gnn_predict_coeffs(ctx)
+    if not use_gnn:
+        P.amg_set_jacobi(ctx)
     solve_ms = statistics.mean(timed(solve_only, Wm + k)[0] for k in range(K))
     infer_ms = statistics.mean(timed(lambda k: P.gnn_predict_coeffs(ctx), k)[0] for k in range(K))
     P.amg_set_jacobi(ctx)
@@ -240,6 +253,33 @@ def run_gpu(args, wl, rank, world):
     cyc_jac = statistics.mean(len(j[1][1]) - 1 for j in jac)
     P.gnn_predict_coeffs(ctx)
     judge = P.amg_judge(ctx, rhs_host[0].numpy(), 10)
+
+    # the same step with the Krylov outer loop (FP64 conjugate gradients, one
+    # FP32 V-cycle as the preconditioner)
+    ctx_k = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev, outer=P.AMG_OUTER_PCG)
+    P.amg_setup(ctx_k, A)
+    P.gnn_load_params(ctx_k, theta)
+    P.gnn_predict_coeffs(ctx_k)
+    _, kept_k = P.amg_reroute(ctx_k, rhs_host[0].numpy(), 30)
+    use_gnn_k = kept_k == P.AMG_SMOOTHER_GNN
+
+    def pcg_step(k):
+        if use_gnn_k:
+            P.gnn_predict_coeffs(ctx_k)
+        return P.amg_solve_device(ctx_k, rhs_dev[k], x, TOL)
+
+    for k in range(Wm):
+        timed(pcg_step, k)
+    pk = [timed(pcg_step, Wm + k) for k in range(K)]
+    P.amg_set_jacobi(ctx_k)
+    pj = [timed(lambda k: P.amg_solve_device(ctx_k, rhs_dev[k], x, TOL), Wm + k) for k in range(K)]
+    pcg = {"gnn_step_ms": statistics.mean(v[0] for v in pk),
+           "iterations_gnn": statistics.mean(len(v[1][1]) - 1 for v in pk),
+           "jacobi_solve_ms": statistics.mean(v[0] for v in pj),
+           "iterations_jacobi": statistics.mean(len(v[1][1]) - 1 for v in pj),
+           "status": sorted(set(v[1][0] for v in pk)),
+           "smoother": "gcin-pseudo-inverse" if use_gnn_k else "jacobi (rerouted)"}
+    P.amg_destroy(ctx_k)
 
     # dominant kernel: the finest level's pseudo-inverse sweep (single pass
     # with Q^-1 A on latency-optimised levels, else the residual pass),
@@ -270,19 +310,23 @@ def run_gpu(args, wl, rank, world):
     torch.cuda.synchronize()
     vc_us = e0.elapsed_time(e1) * 1e3 / 20
 
-    # end to end through the host-buffer API (copies inside the timed region)
+    # end to end through the host-buffer API (copies inside the timed region),
+    # the same step as above: inference + solve, or the rerouted Jacobi solve
+    if not use_gnn:
+        P.amg_set_jacobi(ctx)
     e2e = []
     for k in range(Wm, Wm + K):
         b = rhs_host[k].numpy()
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        P.gnn_predict_coeffs(ctx)
+        if use_gnn:
+            P.gnn_predict_coeffs(ctx)
         st, xh, hist_h = P.amg_solve(ctx, b, rtol=TOL)
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = statistics.mean(e2e)
     h2d = 2 * n * 8
-    d2h = n * 8 + len(hist_h) * 8 + nlev * 5 * 4
+    d2h = n * 8 + len(hist_h) * 8 + (nlev * 5 * 4 if use_gnn else 0)
 
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
@@ -299,8 +343,12 @@ def run_gpu(args, wl, rank, world):
             "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-vcycle/f64-outer", "data": "synthetic",
             "config": {"workload": wl["workload"], "n": n, "nnz": A.nnz, "levels": nlev,
-                       "smoother": f"gcin-pseudo-inverse ({tag})", "tol": TOL, "l2": "flushed (512 MB) per step",
+                       "smoother": f"gcin-pseudo-inverse ({tag})" if use_gnn else
+                       "jacobi (the judge rerouted this mesh: the learned smoother loses)",
+                       "outer": "fp64 iterative refinement", "tol": TOL, "l2": "flushed (512 MB) per step",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "reroute": {"metric": reroute_metric, "kept_gnn": use_gnn, "setup_ms": reroute_ms, "probe_cycles": 30},
+            "pcg": pcg,
             "gnn_step_ms": ms_per_step, "gnn_solve_ms": solve_ms, "gnn_infer_ms": infer_ms,
             "jacobi_solve_ms": jac_ms, "vcycles_gnn": statistics.mean(cyc_gnn), "vcycles_jacobi": cyc_jac,
             "speedup_solve_vs_jacobi": jac_ms / solve_ms, "speedup_step_vs_jacobi": jac_ms / ms_per_step,

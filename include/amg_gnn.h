@@ -44,6 +44,10 @@ extern "C" {
 #define AMG_SMOOTHER_JACOBI 0   /* relaxed Jacobi, Q^-1 = omega D^-1 (Sec. 2.3)          */
 #define AMG_SMOOTHER_GNN    1   /* sparse pseudo-inverse from coefficients (Sec. 3.1)    */
 
+/* outer iteration around the V-cycle */
+#define AMG_OUTER_REFINE 0      /* stationary correction x += V(b - A x) (Sec. 2.1)       */
+#define AMG_OUTER_PCG    1      /* conjugate gradients preconditioned by one V-cycle      */
+
 /* arithmetic of the GCIN node linears (layers 2..4) */
 #define AMG_GNN_FP32 0   /* FP32 CUDA-core FMAs                                  */
 #define AMG_GNN_BF16 1   /* tcgen05 tensor cores: BF16 operands, FP32 accumulation */
@@ -73,6 +77,13 @@ typedef struct {
     double theta;     /* Ruge-Stueben strength threshold (Sec. 4: 0.25)              */
     int device;       /* CUDA device ordinal                                         */
     int gnn_precision;/* AMG_GNN_BF16 (default) or AMG_GNN_FP32                      */
+    int outer;        /* AMG_OUTER_REFINE (default) or AMG_OUTER_PCG: FP64 conjugate
+                         gradients with the V-cycle (zero initial guess) as the
+                         preconditioner and the flexible coefficient
+                         beta = z_k.(r_k - r_{k-1}) / (z_{k-1}.r_{k-1}); the history
+                         then holds the recurrence residual, and a breakdown
+                         (z.r <= 0 or p.Ap <= 0) ends the solve with
+                         AMG_ERR_DIVERGED leaving x at the last iterate           */
 } amg_options;
 
 /* Fill *opt with the paper's settings: nu1 = nu2 = 2, max_levels = 10,
@@ -222,11 +233,13 @@ int amg_judge(amg_ctx *ctx, const double *b, int n_cycles, double *metric);
  * use afterwards.  metric/smoother may be NULL. */
 int amg_reroute(amg_ctx *ctx, const double *b, int n_cycles, double *metric, int *smoother);
 
-/* When amg_reroute keeps the learned smoother it also arms an in-solve check:
- * if some 10 consecutive V-cycles of a later solve reduce the residual by
- * less than half the decades Jacobi gained over 10 cycles in the probe, the
- * solve switches to Jacobi and continues from the current iterate (history
- * and V-cycle count continue).  Returns 1 if the last solve on ctx did so. */
+/* When amg_reroute keeps the learned smoother it also arms an in-solve check
+ * for the mesh (kept across coefficient updates, cleared by a new
+ * hierarchy): if some 10 consecutive V-cycles of a later solve with the
+ * learned smoother reduce the residual by less than half the decades Jacobi
+ * gained over 10 cycles in the probe, the solve switches to Jacobi and
+ * continues from the current iterate (history and V-cycle count continue).
+ * Returns 1 if the last solve on ctx did so. */
 int amg_last_solve_rerouted(const amg_ctx *ctx);
 
 /* ------------------------------------------------------------------------

@@ -31,6 +31,8 @@ AMG_FP64 = 0
 AMG_FP32_IN_FP64 = 1
 AMG_SMOOTHER_JACOBI = 0
 AMG_SMOOTHER_GNN = 1
+AMG_OUTER_REFINE = 0
+AMG_OUTER_PCG = 1
 AMG_GNN_FP32 = 0
 AMG_GNN_BF16 = 1
 AMG_GCIN_NUM_PARAMS = 55045
@@ -52,7 +54,8 @@ class amg_csr(C.Structure):
 class amg_options(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_levels", C.c_int), ("max_coarse", C.c_int),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
-                ("theta", C.c_double), ("device", C.c_int), ("gnn_precision", C.c_int)]
+                ("theta", C.c_double), ("device", C.c_int), ("gnn_precision", C.c_int),
+                ("outer", C.c_int)]
 
 
 _LIB = None

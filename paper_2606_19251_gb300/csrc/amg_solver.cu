@@ -296,12 +296,14 @@ __device__ __forceinline__ void block_partial(double v, double *out) {
     }
 }
 
-// r = b - A x (FP64), rT = (T) r, partial[block] = sum r^2 over the block's rows
+// r = b - A x (FP64), rT = (T) r, r64 = r (when given), partial[block] = sum
+// r^2 over the block's rows
 template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_outer_resid(int n, const int *__restrict__ rp,
                                                         const int *__restrict__ col, const double *__restrict__ a,
                                                         const double *__restrict__ b, const double *__restrict__ x,
-                                                        T *__restrict__ rT, double *__restrict__ partial) {
+                                                        T *__restrict__ rT, double *__restrict__ partial,
+                                                        double *__restrict__ r64) {
     pdl_wait_and_release();
     constexpr int RPB = kBlock / TPR;
     const int lane = threadIdx.x % TPR;
@@ -317,6 +319,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(int n, const int *__rest
         if (row < n && lane == 0) {
             const double r = b[row] - acc;
             rT[row] = static_cast<T>(r);
+            if (r64) r64[row] = r;
             sq += r * r;
         }
     }
@@ -331,6 +334,137 @@ __global__ void __launch_bounds__(kBlock) k_sqnorm_partial(int n, const double *
     block_partial(sq, partial);
 }
 
+// ---------------------------------------------------------------------------
+// kernels: conjugate gradients preconditioned by one V-cycle (FP64)
+// ---------------------------------------------------------------------------
+// Fixed-order sum of np partials, computed identically by every block (so
+// each block derives the same alpha / beta without a separate launch).
+__device__ __forceinline__ double sum_partials(const double *__restrict__ part, int np, double *red) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < np; i += kBlock) v += part[i];
+    v = warp_sum(v);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ void block_partial2(double a, double b, double *outa, double *outb) {
+    __shared__ double ra[kBlock / 32], rb[kBlock / 32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x % 32 == 0) {
+        ra[threadIdx.x / 32] = a;
+        rb[threadIdx.x / 32] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            ta += ra[w];
+            tb += rb[w];
+        }
+        outa[blockIdx.x] = ta;
+        outb[blockIdx.x] = tb;
+    }
+}
+
+// z = (double) e (the V-cycle's output); partials of z.r and z.r_prev
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_pcg_dots(int n, const T *__restrict__ e, const double *__restrict__ r,
+                                                     const double *__restrict__ rprev, double *__restrict__ z,
+                                                     double *__restrict__ pzr, double *__restrict__ pzrp) {
+    pdl_wait_and_release();
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+        const double zi = static_cast<double>(e[i]);
+        z[i] = zi;
+        a += zi * r[i];
+        b += zi * rprev[i];
+    }
+    block_partial2(a, b, pzr, pzrp);
+}
+
+// p = z (restart) or p = z + beta p with beta = (z.r - z.r_prev) / rho_old;
+// z.r <= 0 (or not finite) is a breakdown.
+__global__ void __launch_bounds__(kBlock) k_pcg_dir(int n, const double *__restrict__ z, double *__restrict__ p,
+                                                    const double *__restrict__ pzr, const double *__restrict__ pzrp,
+                                                    int np, SolveState *st) {
+    pdl_wait_and_release();
+    __shared__ double red[kBlock / 32];
+    const double rho = sum_partials(pzr, np, red);
+    const double zrp = sum_partials(pzrp, np, red);
+    if (!(rho > 0.0) || !isfinite(rho) || st->breakdown) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->breakdown = 1;
+        return;
+    }
+    const bool restart = st->restart != 0;
+    const double beta = restart ? 0.0 : (rho - zrp) / st->rho_old;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+        p[i] = restart ? z[i] : z[i] + beta * p[i];
+}
+
+// q = A p (FP64), partial p.q
+template <int TPR>
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                     const double *__restrict__ a, const double *__restrict__ p,
+                                                     double *__restrict__ q, double *__restrict__ partial) {
+    pdl_wait_and_release();
+    constexpr int RPB = kBlock / TPR;
+    const int lane = threadIdx.x % TPR;
+    double pq = 0.0;
+    for (int base = blockIdx.x * RPB; base < n; base += gridDim.x * RPB) {
+        const int row = base + threadIdx.x / TPR;
+        double acc = 0.0;
+        if (row < n) acc = row_dot<TPR>(lane, rp[row], rp[row + 1], col, a, Gather<double>{p});
+        acc = group_sum<TPR>(acc);
+        if (row < n && lane == 0) {
+            q[row] = acc;
+            pq += p[row] * acc;
+        }
+    }
+    block_partial(pq, partial);
+}
+
+// alpha = (z.r) / (p.Ap); x += alpha p; r_prev = r; r -= alpha q; rT = (T) r;
+// partial ||r||^2.  p.Ap <= 0 (or not finite) is a breakdown.
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(int n, double *__restrict__ x, double *__restrict__ r,
+                                                       double *__restrict__ rprev, const double *__restrict__ p,
+                                                       const double *__restrict__ q, T *__restrict__ rT,
+                                                       const double *__restrict__ pzr, const double *__restrict__ ppq,
+                                                       int np, SolveState *st, double *__restrict__ prr) {
+    pdl_wait_and_release();
+    __shared__ double red[kBlock / 32];
+    const double rho = sum_partials(pzr, np, red);
+    const double pq = sum_partials(ppq, np, red);
+    const bool bad = st->breakdown || !(pq > 0.0) || !isfinite(pq);
+    double rr = 0.0;
+    if (!bad) {
+        const double alpha = rho / pq;
+        for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+            x[i] += alpha * p[i];
+            const double ri = r[i];
+            const double rn = ri - alpha * q[i];
+            rprev[i] = ri;
+            r[i] = rn;
+            rT[i] = static_cast<T>(rn);
+            rr += rn * rn;
+        }
+    }
+    block_partial(rr, prr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bad) {
+            st->breakdown = 1;
+        } else {
+            st->rho_old = rho;
+            st->restart = 0;
+        }
+    }
+}
+
 __global__ void k_state_init(SolveState *st, double tol, int max_iter, double stall) {
     pdl_wait_and_release();
     st->k = 0;
@@ -340,6 +474,9 @@ __global__ void k_state_init(SolveState *st, double tol, int max_iter, double st
     st->bnorm = 1.0;
     st->r0 = 0.0;
     st->stall = stall;
+    st->rho_old = 0.0;
+    st->restart = 1;
+    st->breakdown = 0;
 }
 
 // Continue a stalled solve with another smoother (history and count go on).
@@ -347,6 +484,7 @@ __global__ void k_state_continue(SolveState *st) {
     pdl_wait_and_release();
     st->status = kRunning;
     st->stall = 0.0;
+    st->restart = 1;
 }
 
 // Sum the partials in a fixed order.  mode 0: ||b||.  mode 1: residual
@@ -368,6 +506,11 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ 
     const double nrm = sqrt(v);
     if (mode == 0) {
         st->bnorm = nrm > 0.0 ? nrm : 1.0;
+        return;
+    }
+    if (st->breakdown) {   // conjugate gradients broke down: the iterate and history stay
+        st->status = AMG_ERR_DIVERGED;
+        if (use_cond) cudaGraphSetConditional(cond, 0u);
         return;
     }
     const int k = st->k;
@@ -595,8 +738,13 @@ template <class T> struct Launch {
     }
     template <int TPR>
     static void outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nblk,
-                      cudaStream_t s) {
-        launch_pdl(k_outer_resid<T, TPR>, dim3(nblk), dim3(kBlock), 0, s, A.nr, A.rp, A.col, A.v64, b, x, rT, partial);
+                      double *r64, cudaStream_t s) {
+        launch_pdl(k_outer_resid<T, TPR>, dim3(nblk), dim3(kBlock), 0, s, A.nr, A.rp, A.col, A.v64, b, x, rT, partial,
+                   r64);
+    }
+    template <int TPR>
+    static void pcg_spmv(const DevMat &A, const double *p, double *q, double *partial, int nblk, cudaStream_t s) {
+        launch_pdl(k_pcg_spmv<TPR>, dim3(nblk), dim3(kBlock), 0, s, A.nr, A.rp, A.col, A.v64, p, q, partial);
     }
 };
 
@@ -623,8 +771,8 @@ static int outer_blocks(const DevMat &A) {
 // FP64 outer residual with nb = outer_blocks(A) partial sums.
 template <class T>
 static void L_outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nb,
-                    cudaStream_t s) {
-    TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, b, x, rT, partial, nb, s);
+                    cudaStream_t s, double *r64 = nullptr) {
+    TPR_DISPATCH(A.tpr, Launch<T>::template outer, A, b, x, rT, partial, nb, r64, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -768,8 +916,31 @@ static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s, int use_cond = 0,
                                    cudaGraphConditionalHandle cond = 0) {
     const DevMat &A = c->lev[0].A;
     const int nb = outer_blocks(A);
-    L_outer<T>(A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb), c->partials, nb, s);
+    double *r64 = (c->opt.outer == AMG_OUTER_PCG) ? c->pcg : nullptr;   // CG keeps r in FP64
+    L_outer<T>(A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb), c->partials, nb, s, r64);
     launch_pdl(k_norm_final, dim3(1), dim3(1024), 0, s, c->partials, nb, c->state, c->hist, 1, use_cond, cond);
+}
+
+// One conjugate-gradient iteration preconditioned by a V-cycle on r (held in
+// FP64 in pcg[0..n) and in the V-cycle precision in lev[0].vb).
+template <class T>
+static void enqueue_pcg_iteration(amg_ctx *c, cudaStream_t s, int use_cond, cudaGraphConditionalHandle cond) {
+    const DevMat &A = c->lev[0].A;
+    const int n = c->lev[0].n;
+    const int nb = outer_blocks(A);
+    double *r = c->pcg, *rprev = r + n, *z = rprev + n, *p = z + n, *q = p + n;
+    double *P0 = c->partials, *P1 = P0 + c->n_partials, *P2 = P1 + c->n_partials, *P3 = P2 + c->n_partials;
+    T *e = vcycle_level<T>(c, 0, s);
+    launch_pdl(k_pcg_dots<T>, dim3(nb), dim3(kBlock), 0, s, n, static_cast<const T *>(e),
+               static_cast<const double *>(r), static_cast<const double *>(rprev), z, P0, P1);
+    launch_pdl(k_pcg_dir, dim3(nb), dim3(kBlock), 0, s, n, static_cast<const double *>(z), p,
+               static_cast<const double *>(P0), static_cast<const double *>(P1), nb, c->state);
+    TPR_DISPATCH(A.tpr, Launch<T>::template pcg_spmv, A, p, q, P2, nb, s);
+    launch_pdl(k_pcg_update<T>, dim3(nb), dim3(kBlock), 0, s, n, c->dx, r, rprev, static_cast<const double *>(p),
+               static_cast<const double *>(q), reinterpret_cast<T *>(c->lev[0].vb), static_cast<const double *>(P0),
+               static_cast<const double *>(P2), nb, c->state, P3);
+    launch_pdl(k_norm_final, dim3(1), dim3(1024), 0, s, static_cast<const double *>(P3), nb, c->state, c->hist, 1,
+               use_cond, cond);
 }
 
 template <class T>
@@ -785,6 +956,10 @@ static void enqueue_init(amg_ctx *c, cudaStream_t s, double tol, int max_iter) {
 
 template <class T>
 static void enqueue_iteration(amg_ctx *c, cudaStream_t s, int use_cond = 0, cudaGraphConditionalHandle cond = 0) {
+    if (c->opt.outer == AMG_OUTER_PCG) {
+        enqueue_pcg_iteration<T>(c, s, use_cond, cond);
+        return;
+    }
     T *e = vcycle_level<T>(c, 0, s);
     launch_pdl(k_axpy<T>, dim3(grid_for(c->lev[0].n)), dim3(kBlock), 0, s, c->lev[0].n, c->dx, e);
     enqueue_outer_residual<T>(c, s, use_cond, cond);
@@ -799,7 +974,7 @@ static void free_graph(SolveGraph &G) {
 // Build (once per hierarchy and smoother) the whole-solve graph.
 template <class T>
 static int ensure_graph(amg_ctx *c) {
-    SolveGraph &G = c->sgraph[c->smoother];
+    SolveGraph &G = c->sgraph[c->smoother + 2 * c->opt.outer];
     if (G.exec && G.version == c->hier_version) return AMG_OK;
     free_graph(G);
     cudaGraph_t g = nullptr;
@@ -846,7 +1021,7 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
     if (rc) return rc;
     enqueue_init<T>(c, s, tol, max_iter);
     CKL("solve init launch");
-    const SolveGraph &G = c->sgraph[c->smoother];
+    const SolveGraph &G = c->sgraph[c->smoother + 2 * c->opt.outer];
     CK(cudaGraphLaunch(G.exec, s));
     CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -861,7 +1036,7 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
         rc = ensure_graph<T>(c);
         if (rc) return rc;
         launch_pdl(k_state_continue, dim3(1), dim3(1), 0, s, c->state);
-        const SolveGraph &GJ = c->sgraph[AMG_SMOOTHER_JACOBI];
+        const SolveGraph &GJ = c->sgraph[AMG_SMOOTHER_JACOBI + 2 * c->opt.outer];
         CK(cudaGraphLaunch(GJ.exec, s));
         CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -945,6 +1120,7 @@ static void layout(amg_ctx *c, Planner &pl) {
     const int n0 = c->host[0].A.n_rows;
     c->db = pl.take<double>(n0);
     c->dx = pl.take<double>(n0);
+    c->pcg = pl.take<double>(5 * static_cast<size_t>(n0));
     c->n_partials = kNumSMs * 8;                       // blocks of a capped grid
     c->partials = pl.take<double>(5 * c->n_partials);  // up to 5 partial sums per block
     c->scal = pl.take<double>(nlev);
@@ -994,6 +1170,7 @@ static void plan_fast_levels(amg_ctx *c) {
 static int upload(amg_ctx *c) {
     free_device(c);
     ++c->hier_version;
+    c->stall_ratio = 0.0;   // the in-solve check belongs to a mesh
     plan_fast_levels(c);
     Planner pl;
     layout(c, pl);
@@ -1092,6 +1269,7 @@ void amg_default_options(amg_options *o) {
     o->theta = 0.25;
     o->device = 0;
     o->gnn_precision = AMG_GNN_BF16;
+    o->outer = AMG_OUTER_REFINE;
 }
 
 int amg_create(amg_ctx **ctx, const amg_options *opt) {
@@ -1108,6 +1286,7 @@ int amg_create(amg_ctx **ctx, const amg_options *opt) {
         (o.precision != AMG_FP64 && o.precision != AMG_FP32_IN_FP64) ||
         (o.smoother != AMG_SMOOTHER_JACOBI && o.smoother != AMG_SMOOTHER_GNN) || !(o.theta >= 0.0) ||
         (o.gnn_precision != AMG_GNN_FP32 && o.gnn_precision != AMG_GNN_BF16) ||
+        (o.outer != AMG_OUTER_REFINE && o.outer != AMG_OUTER_PCG) ||
         !(o.theta <= 1.0) || !std::isfinite(o.omega)) {
         g_create_err = "invalid amg_options";
         return AMG_ERR_ARG;
@@ -1269,7 +1448,6 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
     (void)n_rows;
     CKL("assemble pseudo-inverse");
     c->have_q = true;
-    c->stall_ratio = 0.0;
     c->smoother = AMG_SMOOTHER_GNN;
     return AMG_OK;
 }
@@ -1447,9 +1625,11 @@ int amg_judge(amg_ctx *c, const double *b, int n_cycles, double *metric) {
     cudaStream_t s = c->stream;
     const int saved_iter = c->opt.max_iter;
     const int saved_sm = c->smoother;
+    const int saved_outer = c->opt.outer;
     std::vector<double> hg(n_cycles + 1, 0.0), hj(n_cycles + 1, 0.0);
     int kg = 0, kj = 0, stg = AMG_OK, stj = AMG_OK, rc = AMG_OK;
     c->opt.max_iter = n_cycles;
+    c->opt.outer = AMG_OUTER_REFINE;   // the metric compares the stationary V-cycle iteration (Sec. 3.3)
     for (int pass = 0; pass < 2 && rc != AMG_ERR_CUDA; ++pass) {
         c->smoother = pass == 0 ? AMG_SMOOTHER_GNN : AMG_SMOOTHER_JACOBI;
         rc = ctx_cuda_check(c, cudaMemcpyAsync(c->db, b, sizeof(double) * n0, cudaMemcpyHostToDevice, s), "copy b");
@@ -1459,6 +1639,7 @@ int amg_judge(amg_ctx *c, const double *b, int n_cycles, double *metric) {
     }
     c->opt.max_iter = saved_iter;
     c->smoother = saved_sm;
+    c->opt.outer = saved_outer;
     if (rc == AMG_ERR_CUDA || stg == AMG_ERR_CUDA) return AMG_ERR_CUDA;
     if (stg == AMG_ERR_DIVERGED) *metric = INFINITY;
     else if (stj == AMG_ERR_DIVERGED) *metric = -INFINITY;
@@ -1479,9 +1660,11 @@ int amg_reroute(amg_ctx *c, const double *b, int n_cycles, double *metric, int *
     const int n0 = c->lev[0].n;
     cudaStream_t s = c->stream;
     const int saved_iter = c->opt.max_iter;
+    const int saved_outer = c->opt.outer;
     std::vector<double> h[2];
     int k[2] = {0, 0}, st[2] = {AMG_OK, AMG_OK}, rc = AMG_OK;
     c->opt.max_iter = n_cycles;
+    c->opt.outer = AMG_OUTER_REFINE;   // probe with the stationary V-cycle iteration (Sec. 3.3)
     for (int pass = 0; pass < 2 && rc != AMG_ERR_CUDA; ++pass) {
         c->smoother = pass == 0 ? AMG_SMOOTHER_GNN : AMG_SMOOTHER_JACOBI;
         h[pass].assign(n_cycles + 1, 0.0);
@@ -1491,6 +1674,7 @@ int amg_reroute(amg_ctx *c, const double *b, int n_cycles, double *metric, int *
         st[pass] = rc;
     }
     c->opt.max_iter = saved_iter;
+    c->opt.outer = saved_outer;
     c->smoother = AMG_SMOOTHER_GNN;
     if (rc == AMG_ERR_CUDA || st[0] == AMG_ERR_CUDA) return AMG_ERR_CUDA;
     // metric 1: log10(||r_n^GNN|| / ||r_n^J||) (Sec. 3.3); metric 2: the same

@@ -49,6 +49,9 @@ struct SolveState {
     double bnorm;   // ||b|| (1 if b = 0)
     double r0;      // ||b - A x0||
     double stall;   // > 0: a 10-cycle reduction worse than this ends the learned smoother's run
+    double rho_old; // conjugate gradients: z.r of the previous iteration
+    int restart;    // conjugate gradients: next direction is p = z
+    int breakdown;  // conjugate gradients: z.r or p.Ap not positive
 };
 
 // Whole-solve CUDA graph: a kernel node copies the device-side status into
@@ -92,7 +95,8 @@ struct amg_ctx {
     amg::GcinEngine *gnn = nullptr;
     long long hier_version = 0;                // bumped by every hierarchy upload
     void *train = nullptr;                     // training (adjoint) buffers, created on demand
-    amg::SolveGraph sgraph[2];                 // per smoother (AMG_SMOOTHER_JACOBI / _GNN)
+    amg::SolveGraph sgraph[4];                 // per smoother + 2 x outer iteration
+    double *pcg = nullptr;                     // conjugate gradients: r, r_prev, z, p, q (n_0 each)
     double stall_ratio = 0.0;                  // armed by amg_reroute for the learned smoother
     int last_rerouted = 0;                     // the last solve switched to Jacobi
 };
