@@ -218,6 +218,18 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__re
     }
 }
 
+// (M A) values from the pair list in FP32, for the FP32 V-cycle (GB300's FP64
+// pipe is narrow; the FP32 V-cycle needs only the FP32 product)
+__global__ void k_assemble_ma32(int nnz, const int *__restrict__ pp, const int *__restrict__ pq_p,
+                                const int *__restrict__ pq_q, const float *__restrict__ q32,
+                                const float *__restrict__ a32, float *__restrict__ ma32) {
+    const int e = blockIdx.x * kBlock + threadIdx.x;
+    if (e >= nnz) return;
+    float acc = 0.f;
+    for (int t = pp[e]; t < pp[e + 1]; ++t) acc = fmaf(q32[pq_p[t]], a32[pq_q[t]], acc);
+    ma32[e] = acc;
+}
+
 // (M A) values from the pair list (FP64), with the V-cycle-precision copy
 __global__ void k_assemble_ma(int nnz, const int *__restrict__ pp, const int *__restrict__ pq_p,
                               const int *__restrict__ pq_q, const double *__restrict__ q64,
@@ -604,6 +616,22 @@ __global__ void k_assemble_q(int nnz, const unsigned char *__restrict__ isd, con
                              double *__restrict__ q64, float *__restrict__ q32) {
     const int p = blockIdx.x * kBlock + threadIdx.x;
     if (p >= nnz) return;
+    const double x = bx[p];
+    const double f = isd[p] ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
+                            : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
+    const double q = __dmul_rn(f, bw[p]);
+    q64[p] = q;
+    q32[p] = static_cast<float>(q);
+}
+
+// The same with the coefficients read from device memory (FP32 network
+// output, widened to FP64 exactly as the host path does).
+__global__ void k_assemble_q_dev(int nnz, const unsigned char *__restrict__ isd, const double *__restrict__ bx,
+                                 const double *__restrict__ bw, const float *__restrict__ dc,
+                                 double *__restrict__ q64, float *__restrict__ q32) {
+    const int p = blockIdx.x * kBlock + threadIdx.x;
+    if (p >= nnz) return;
+    const double c0 = dc[0], c1 = dc[1], c2 = dc[2], c3 = dc[3], c4 = dc[4];
     const double x = bx[p];
     const double f = isd[p] ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
                             : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
@@ -1431,6 +1459,29 @@ int amg_set_jacobi(amg_ctx *c, double omega) {
 }  // extern "C"
 
 namespace amg {
+// Assemble Q^-1 (and M A on latency-optimised levels) from coefficients in
+// device memory (G x 5 FP32, level order) without a host round trip; the
+// caller validates the coefficients after its own synchronisation.
+int set_coeffs_from_device(amg_ctx *c, const float *d_coef, cudaStream_t s) {
+    const int nlev = static_cast<int>(c->lev.size());
+    for (int l = 0; l < nlev - 1; ++l) {
+        const DevLevel &L = c->lev[l];
+        k_assemble_q_dev<<<grid_for(L.A.nnz), kBlock, 0, s>>>(L.A.nnz, L.isd, L.bx, L.bw, d_coef + 5 * l, L.q64,
+                                                              L.q32); AMG_COUNT();
+        if (L.fast && c->opt.precision == AMG_FP64) {
+            k_assemble_ma<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q64, L.A.v64,
+                                                                L.MA.v64, L.MA.v32); AMG_COUNT();
+        } else if (L.fast) {
+            k_assemble_ma32<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q32, L.A.v32,
+                                                                  L.MA.v32); AMG_COUNT();
+        }
+    }
+    CKL("assemble pseudo-inverse");
+    c->have_q = true;
+    c->smoother = AMG_SMOOTHER_GNN;
+    return AMG_OK;
+}
+
 int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s) {
     const int nlev = static_cast<int>(c->lev.size());
     for (int l = 0; l < nlev - 1; ++l) {
@@ -1440,9 +1491,12 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
             if (!std::isfinite(q[k])) return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
         k_assemble_q<<<grid_for(L.A.nnz), kBlock, 0, s>>>(L.A.nnz, L.isd, L.bx, L.bw, q[0], q[1], q[2], q[3],
                                                           q[4], L.q64, L.q32); AMG_COUNT();
-        if (L.fast) {
+        if (L.fast && c->opt.precision == AMG_FP64) {
             k_assemble_ma<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q64, L.A.v64,
                                                                 L.MA.v64, L.MA.v32); AMG_COUNT();
+        } else if (L.fast) {
+            k_assemble_ma32<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q32, L.A.v32,
+                                                                  L.MA.v32); AMG_COUNT();
         }
     }
     (void)n_rows;

@@ -243,7 +243,8 @@ __device__ __forceinline__ void tile_stats(const float (*sY)[kHidden + 1], int n
     }
 }
 
-// Layer 1: h = A_hat x0 (FP64 sums of the raw features), y = h W + b; tile stats.
+// Layer 1: h = A_hat x0 (FP64 sums of the raw features, one thread per node,
+// entries in row order), y = h W + b (K = 2: FMA units); tile stats.
 __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ rp, const int *__restrict__ col,
                                                         const double *__restrict__ w64, const double *__restrict__ x0,
                                                         const float *__restrict__ W, const float *__restrict__ bias,
@@ -251,77 +252,99 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
                                                         float *__restrict__ y, float *__restrict__ tmean,
                                                         float *__restrict__ tm2) {
     __shared__ float sY[kTile][kHidden + 1];
+    __shared__ float sH[kTile][2];
     const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int k = warp; k < nn; k += kBlock / 32) {
-        const int i = a + k;
+    if (threadIdx.x < nn) {
+        const int i = a + threadIdx.x;
         double a0 = 0.0, a1 = 0.0;
-        for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
             const double wv = w64[p];
             const int j = col[p];
             a0 += wv * x0[2 * j];
             a1 += wv * x0[2 * j + 1];
         }
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        if (lane == 0) {
-            h1[2 * i] = static_cast<float>(a0);
-            h1[2 * i + 1] = static_cast<float>(a1);
+        const float h0 = static_cast<float>(a0), hv1 = static_cast<float>(a1);
+        reinterpret_cast<float2 *>(h1)[i] = make_float2(h0, hv1);
+        sH[threadIdx.x][0] = h0;
+        sH[threadIdx.x][1] = hv1;
+    }
+    __syncthreads();
+    // 64 nodes x 64 features: thread -> node k = tid / 4, features 16 (tid % 4) .. + 15
+    const int k = threadIdx.x / 4, f0 = 16 * (threadIdx.x % 4);
+    if (k < nn) {
+        const float h0 = sH[k][0], hv1 = sH[k][1];
+        float out[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int f = f0 + q;
+            out[q] = fmaf(h0, W[f], fmaf(hv1, W[kHidden + f], bias[f]));
+            sY[k][f] = out[q];
         }
-        const int f = 2 * lane;
-        const float h0 = static_cast<float>(a0), h1v = static_cast<float>(a1);
-        const float y0 = fmaf(h0, W[f], fmaf(h1v, W[kHidden + f], bias[f]));
-        const float y1 = fmaf(h0, W[f + 1], fmaf(h1v, W[kHidden + f + 1], bias[f + 1]));
-        reinterpret_cast<float2 *>(y)[static_cast<size_t>(i) * 32 + lane] = make_float2(y0, y1);
-        sY[k][f] = y0;
-        sY[k][f + 1] = y1;
+        float4 *yo = reinterpret_cast<float4 *>(y + static_cast<size_t>(a + k) * kHidden + f0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) yo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
     }
     __syncthreads();
     tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
 }
 
-// h_i = sum_p w_p x_{col p} for the warp's row (lane owns features 2 lane,
-// 2 lane + 1), entries added in row order.  Up to 32 (col, w) pairs come in
-// with one coalesced load and are broadcast by shuffles; four 256-byte row
-// gathers are in flight at a time.  Called by a whole warp.
-__device__ __forceinline__ float2 agg_row64(int p0, int p1, const int *__restrict__ col, const float *__restrict__ w,
-                                            const float2 *__restrict__ x2, int lane) {
-    float hx = 0.f, hy = 0.f;
-    for (int pb = p0; pb < p1; pb += 32) {
-        const int cnt = min(32, p1 - pb);
+// h_i = sum_p w_p x_{col p} for two rows per warp: half-warp h (lanes
+// 16 h .. 16 h + 15) aggregates its own row [p0, p1), lane j of the half owns
+// features 4 j .. 4 j + 3, and entries are added in row order.  Up to 16
+// (col, w) pairs per half come in with one coalesced load and are broadcast
+// by shuffles; each lane keeps four 16-byte gathers in flight, so a warp has
+// eight 256-byte feature rows in flight.  Called by a whole warp (the loop
+// runs to the longer of the two rows, the shorter half predicated off).
+__device__ __forceinline__ float4 agg_row64_pair(int p0, int p1, const int *__restrict__ col,
+                                                 const float *__restrict__ w, const float4 *__restrict__ x4, int hl) {
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int deg = p1 - p0;
+    const int maxdeg = max(deg, __shfl_xor_sync(0xffffffffu, deg, 16));
+    for (int base = 0; base < maxdeg; base += 16) {
         int cj = 0;
         float wj = 0.f;
-        if (lane < cnt) {
-            cj = col[pb + lane];
-            wj = w[pb + lane];
+        if (base + hl < deg) {
+            cj = col[p0 + base + hl];
+            wj = w[p0 + base + hl];
         }
+        const int cnt = deg - base;                  // entries of this half in the chunk (may be <= 0)
+        const int cmax = min(16, maxdeg - base);
         int k = 0;
-        for (; k + 4 <= cnt; k += 4) {
+        for (; k + 4 <= cmax; k += 4) {
             int c[4];
             float wk[4];
-            float2 v[4];
+            float4 v[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                c[j] = __shfl_sync(0xffffffffu, cj, k + j);
-                wk[j] = __shfl_sync(0xffffffffu, wj, k + j);
+                c[j] = __shfl_sync(0xffffffffu, cj, k + j, 16);
+                wk[j] = __shfl_sync(0xffffffffu, wj, k + j, 16);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = x2[static_cast<size_t>(c[j]) * 32 + lane];
+            for (int j = 0; j < 4; ++j)
+                v[j] = (k + j < cnt) ? x4[static_cast<size_t>(c[j]) * 16 + hl] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                hx = fmaf(wk[j], v[j].x, hx);
-                hy = fmaf(wk[j], v[j].y, hy);
+                if (k + j < cnt) {
+                    h.x = fmaf(wk[j], v[j].x, h.x);
+                    h.y = fmaf(wk[j], v[j].y, h.y);
+                    h.z = fmaf(wk[j], v[j].z, h.z);
+                    h.w = fmaf(wk[j], v[j].w, h.w);
+                }
             }
         }
-        for (; k < cnt; ++k) {
-            const int c = __shfl_sync(0xffffffffu, cj, k);
-            const float wk = __shfl_sync(0xffffffffu, wj, k);
-            const float2 v = x2[static_cast<size_t>(c) * 32 + lane];
-            hx = fmaf(wk, v.x, hx);
-            hy = fmaf(wk, v.y, hy);
+        for (; k < cmax; ++k) {
+            const int c = __shfl_sync(0xffffffffu, cj, k, 16);
+            const float wk = __shfl_sync(0xffffffffu, wj, k, 16);
+            if (k < cnt) {
+                const float4 v = x4[static_cast<size_t>(c) * 16 + hl];
+                h.x = fmaf(wk, v.x, h.x);
+                h.y = fmaf(wk, v.y, h.y);
+                h.z = fmaf(wk, v.z, h.z);
+                h.w = fmaf(wk, v.w, h.w);
+            }
         }
     }
-    return make_float2(hx, hy);
+    return h;
 }
 
 // Layers 2..4: h = A_hat x (64 features), y = h W + b; tile stats.
@@ -331,30 +354,39 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__
                                                          const int *__restrict__ tstart, float *__restrict__ hout,
                                                          float *__restrict__ y, float *__restrict__ tmean,
                                                          float *__restrict__ tm2) {
-    __shared__ float2 sW[kHidden * 32];   // W[m][2 lane .. 2 lane + 1]
+    __shared__ float4 sW[kHidden * 16];   // W[m][4 j .. 4 j + 3]
     __shared__ float sY[kTile][kHidden + 1];
-    for (int t2 = threadIdx.x; t2 < kHidden * 32; t2 += kBlock) sW[t2] = reinterpret_cast<const float2 *>(W)[t2];
+    for (int t2 = threadIdx.x; t2 < kHidden * 16; t2 += kBlock) sW[t2] = reinterpret_cast<const float4 *>(W)[t2];
     __syncthreads();
     const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const float2 *x2 = reinterpret_cast<const float2 *>(x);
-    const float2 b2 = reinterpret_cast<const float2 *>(bias)[lane];
-    for (int k = warp; k < nn; k += kBlock / 32) {
-        const int i = a + k;
-        const float2 hv = agg_row64(rp[i], rp[i + 1], col, w, x2, lane);
-        const float hx = hv.x, hy = hv.y;
-        reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = hv;
-        float y0 = b2.x, y1 = b2.y;
-#pragma unroll 8
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, half = lane / 16, hl = lane % 16;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const float4 b4 = reinterpret_cast<const float4 *>(bias)[hl];
+    for (int k0 = 2 * warp; k0 < nn; k0 += 2 * (kBlock / 32)) {
+        const int k = k0 + half;
+        const bool live = k < nn;                    // the second row of the last pair may be absent
+        const int i = a + (live ? k : k0);
+        const int p0 = rp[i], p1 = live ? rp[i + 1] : p0;
+        const float4 hv = agg_row64_pair(p0, p1, col, w, x4, hl);
+        if (live) reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * 16 + hl] = hv;
+        float4 yv = b4;
+#pragma unroll 4
         for (int m = 0; m < kHidden; ++m) {
-            const float hm = __shfl_sync(0xffffffffu, (m & 1) ? hy : hx, m >> 1);
-            const float2 wm = sW[m * 32 + lane];
-            y0 = fmaf(hm, wm.x, y0);
-            y1 = fmaf(hm, wm.y, y1);
+            const float hsrc = (m & 3) == 0 ? hv.x : (m & 3) == 1 ? hv.y : (m & 3) == 2 ? hv.z : hv.w;
+            const float hm = __shfl_sync(0xffffffffu, hsrc, m >> 2, 16);
+            const float4 wm = sW[m * 16 + hl];
+            yv.x = fmaf(hm, wm.x, yv.x);
+            yv.y = fmaf(hm, wm.y, yv.y);
+            yv.z = fmaf(hm, wm.z, yv.z);
+            yv.w = fmaf(hm, wm.w, yv.w);
         }
-        reinterpret_cast<float2 *>(y)[static_cast<size_t>(i) * 32 + lane] = make_float2(y0, y1);
-        sY[k][2 * lane] = y0;
-        sY[k][2 * lane + 1] = y1;
+        if (live) {
+            reinterpret_cast<float4 *>(y)[static_cast<size_t>(i) * 16 + hl] = yv;
+            sY[k][4 * hl] = yv.x;
+            sY[k][4 * hl + 1] = yv.y;
+            sY[k][4 * hl + 2] = yv.z;
+            sY[k][4 * hl + 3] = yv.w;
+        }
     }
     __syncthreads();
     tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
@@ -842,14 +874,18 @@ __global__ void __launch_bounds__(kBlock) k_bwd_in_lin_tile(const int *__restric
     }
 }
 
-// dx = A_hat dh (A_hat symmetric), 64 features, warp per node.
+// dx = A_hat dh (A_hat symmetric), 64 features, two nodes per warp.
 __global__ void __launch_bounds__(kBlock) k_agg_plain(int N, const int *__restrict__ rp, const int *__restrict__ col,
                                                       const float *__restrict__ w, const float *__restrict__ v,
                                                       float *__restrict__ out) {
-    const int i = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32;
-    if (i >= N) return;
-    reinterpret_cast<float2 *>(out)[static_cast<size_t>(i) * 32 + lane] =
-        agg_row64(rp[i], rp[i + 1], col, w, reinterpret_cast<const float2 *>(v), lane);
+    const int pair = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32, hl = lane % 16;
+    const int i0 = 2 * pair;
+    if (i0 >= N) return;                         // warp-uniform
+    const int i = i0 + lane / 16;
+    const bool live = i < N;
+    const int p0 = rp[live ? i : i0], p1 = live ? rp[i + 1] : p0;
+    const float4 h = agg_row64_pair(p0, p1, col, w, reinterpret_cast<const float4 *>(v), hl);
+    if (live) reinterpret_cast<float4 *>(out)[static_cast<size_t>(i) * 16 + hl] = h;
 }
 
 // Conv weight/bias gradient: tile partials summed per chunk of tiles (FP64,
@@ -895,7 +931,7 @@ void gcin_backward(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
     k_head_bwd<<<G, 128, 0, s>>>(b.head, th, b.dc, b.dhead, b.dpooled); AMG_COUNT();
     const int nhead = kNumParams - kPL.roW[0];
     k_head_param_grad<<<grid_for(nhead), kBlock, 0, s>>>(G, b.pooled, b.head, b.dhead, b.dc, grad); AMG_COUNT();
-    const int warp_grid = grid_for(static_cast<long long>(N) * 32);
+    const int warp_grid = grid_for((static_cast<long long>(N) + 1) / 2 * 32);   // two nodes per warp
     for (int l = kLayers - 1; l >= 0; --l) {
         k_bwd_relu_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.x[l], b.y[l], b.mu[l], b.rstd[l],
                                               l == kLayers - 1 ? nullptr : b.dx, b.dpooled, b.argmax, l, b.dy,
@@ -1038,21 +1074,26 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
     }
     g->batch.bf16 = (c->opt.gnn_precision == AMG_GNN_BF16) ? 1 : 0;
     gcin_forward(g->batch, g->theta, s);
+    // the smoother is assembled straight from the device coefficients; the
+    // host copy (returned and validated) comes back with one synchronisation
+    int rc = set_coeffs_from_device(c, g->batch.c, s);
+    if (rc) return rc;
     int dflag = 0;
     const int G = g->batch.G;
     std::vector<float> cf(static_cast<size_t>(G) * 5);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cf.data(), g->batch.c, sizeof(float) * cf.size(), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(cf.data(), g->batch.c, sizeof(float) * cf.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&dflag, g->batch.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return ctx_cuda_check(c, e, "GCIN forward");
-    if (dflag) return ctx_fail(c, "tensor-core GCIN kernel timed out waiting for its MMAs"), AMG_ERR_DEVICE_FLAG;
-    std::vector<double> cd(cf.begin(), cf.end());
-    if (c_out) std::copy(cd.begin(), cd.end(), c_out);
-    int rc = set_coeffs_device(c, cd.data(), G, s);
-    if (rc) return rc;
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return ctx_cuda_check(c, e, "assemble smoother");
+    if (e != cudaSuccess) return ctx_cuda_check(c, e, "GCIN forward and smoother assembly");
+    bool finite = true;
+    for (size_t k = 0; k < static_cast<size_t>(G - 1) * 5; ++k) finite = finite && std::isfinite(cf[k]);   // smoothed levels
+    if (dflag || !finite) {
+        c->have_q = false;
+        c->smoother = AMG_SMOOTHER_JACOBI;
+        if (dflag) return ctx_fail(c, "tensor-core GCIN kernel timed out waiting for its MMAs"), AMG_ERR_DEVICE_FLAG;
+        return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
+    }
+    if (c_out) std::copy(cf.begin(), cf.end(), c_out);
     return AMG_OK;
 }
 

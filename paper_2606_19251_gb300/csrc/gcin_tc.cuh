@@ -3,8 +3,9 @@
 // tensor memory.  One CTA owns two consecutive statistic tiles of at most 64
 // nodes each (a graph's last tile is ragged; up to 128 nodes = one M = 128
 // MMA tile):
-//   1. warps aggregate h_i = sum_j w_ij x_j (FP32) and store h in BF16 into the
-//      A tile (128 x 64, K-major, canonical no-swizzle core-matrix layout);
+//   1. warps aggregate h_i = sum_j w_ij x_j (FP32, two rows per warp) and
+//      store h in BF16 into the A tile (128 x 64, K-major, canonical
+//      no-swizzle core-matrix layout);
 //      W^T goes to the B tile (64 x 64, K-major) in BF16;
 //   2. one thread issues 4 x tcgen05.mma.kind::f16 (M 128, N 64, K 16) into a
 //      64-column TMEM accumulator and commits to an mbarrier;
@@ -99,17 +100,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     const int t0 = 2 * blockIdx.x;
     const int t1 = min(t0 + 2, NT);
     const int a0 = tstart[t0], nn = tstart[t1] - a0;
-    const float2 *x2 = reinterpret_cast<const float2 *>(x);
-    for (int k = warp; k < kTcRows; k += kBlock / 32) {
-        __nv_bfloat162 hb = __floats2bfloat162_rn(0.f, 0.f);
-        if (k < nn) {
-            const int i = a0 + k;
-            const float2 hv = agg_row64(rp[i], rp[i + 1], col, w, x2, lane);
-            hb = __floats2bfloat162_rn(hv.x, hv.y);
-            const float2 hr = __bfloat1622float2(hb);     // the rounded h the MMA sees (kept for the backward)
-            reinterpret_cast<float2 *>(hout)[static_cast<size_t>(i) * 32 + lane] = hr;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const int half = lane / 16, hl = lane % 16;
+    for (int k0 = 2 * warp; k0 < kTcRows; k0 += 2 * (kBlock / 32)) {
+        const int k = k0 + half;
+        const bool live = k < nn;
+        const int i = a0 + (live ? k : 0);
+        const int p0 = live ? rp[i] : 0, p1 = live ? rp[i + 1] : 0;
+        const float4 hv = agg_row64_pair(p0, p1, col, w, x4, hl);   // zero for rows past the tiles
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(hv.x, hv.y), hi = __floats2bfloat162_rn(hv.z, hv.w);
+        if (live) {   // the rounded h the MMA sees (kept for the backward)
+            const float2 rl = __bfloat1622float2(lo), rh = __bfloat1622float2(hi);
+            reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * 16 + hl] = make_float4(rl.x, rl.y, rh.x, rh.y);
         }
-        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off(k, 2 * lane)) = hb;
+        // features 4 hl .. 4 hl + 3 are contiguous within one core matrix row
+        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off(k, 4 * hl)) = lo;
+        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off(k, 4 * hl + 2)) = hi;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
