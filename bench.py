@@ -310,6 +310,29 @@ def run_gpu(args, wl, rank, world):
     torch.cuda.synchronize()
     vc_us = e0.elapsed_time(e1) * 1e3 / 20
 
+    # the same sweep kernels in the HBM regime: the finest level of a
+    # 2048 x 2048 5-point grid (4.2M rows, 21M entries, 235 MB per FP32 pass,
+    # well beyond the 129 MB L2), launched back to back
+    hbm = None
+    if wl["workload"] != "band-delaunay-fv-2.5M":
+        Ag = W.poisson5(2048)
+        ctx_g = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev)
+        P.amg_setup(ctx_g, Ag)
+        P.amg_set_coeffs(ctx_g, [[0.62, 0.03, -0.01, -0.18, 0.02]] * P.amg_num_levels(ctx_g))
+        hbm = {"workload": "5point-grid-2048 (finest level)", "peak": peak, "unit": "GB/s", "kernels": {}}
+        for name_k, kid_g in (("k_resid", P.AMG_K_RESIDUAL), ("k_apply (Q^-1 r)", P.AMG_K_PINV),
+                              ("k_jacobi", P.AMG_K_JACOBI), ("k_outer_resid (FP64)", P.AMG_K_OUTER)):
+            P.amg_kernel_launch(ctx_g, kid_g, 0, 3)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            bg = P.amg_kernel_launch(ctx_g, kid_g, 0, 50)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            us_g = e0.elapsed_time(e1) * 1e3 / 50
+            gbs = bg / (us_g * 1e-6) / 1e9
+            hbm["kernels"][name_k] = {"bytes": bg, "us": us_g, "achieved": gbs, "frac": gbs / peak}
+        P.amg_destroy(ctx_g)
+
     # end to end through the host-buffer API (copies inside the timed region),
     # the same step as above: inference + solve, or the rerouted Jacobi solve
     if not use_gnn:
@@ -359,6 +382,7 @@ def run_gpu(args, wl, rank, world):
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": kbytes,
                          "us_per_launch": k_us, "note": "L2-resident at this size (effective GB/s)"},
+            "roofline_hbm_regime": hbm,
             "gpu_launches": launches,
             "clocks": {k2: v for k2, v in clocks.items()},
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
