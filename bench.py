@@ -354,8 +354,9 @@ def run_gpu(args, wl, rank, world):
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
+        key = "masweep" if kid == P.AMG_K_MASWEEP else "residual"
         with open(tfile) as f:
-            tr = json.load(f).get(f"{wl['workload']}:residual")
+            tr = json.load(f).get(f"{wl['workload']}:{key}")
         if tr and tr.get("kernel_source_sha") == _kernel_sha():
             traffic = tr["dram_bytes_per_launch"]
 
@@ -399,9 +400,14 @@ def run_gpu(args, wl, rank, world):
 
 
 def _kernel_sha():
+    """Hash of the sources of the solve-path kernels (traffic counters are
+    only reported while they still describe the code that runs)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2606_19251_gb300", "csrc", "amg_solver.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("amg_solver.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_19251_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def run_kernel_only(args, wl):
@@ -411,6 +417,27 @@ def run_kernel_only(args, wl):
     A = wl["matrix"]()
     ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64)
     P.amg_setup(ctx, A)
+    if args.kernel_only == "step":
+        # one bench step (GCIN inference + solve to 1e-8) after one untimed
+        # step, for an ncu launch list of exactly one step
+        theta, _ = load_theta()
+        P.gnn_load_params(ctx, theta)
+        b = torch.from_numpy(wl["rhs"](1000, A.n_rows)).cuda()
+        for k in range(2):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            if k == 1:
+                torch.cuda.nvtx.range_push("step")
+                c0 = P.amg_launch_count()
+            P.gnn_predict_coeffs(ctx)
+            st, hist = P.amg_solve_device(ctx, b, x, TOL)
+            torch.cuda.synchronize()
+            if k == 1:
+                torch.cuda.nvtx.range_pop()
+        print(json.dumps({"kernel": "step", "workload": wl["workload"], "status": st, "vcycles": len(hist) - 1,
+                          "launches_per_step": P.amg_launch_count() - c0}))
+        P.amg_destroy(ctx)
+        return
     if args.kernel_only == "gcin":
         theta, _ = load_theta()
         P.gnn_load_params(ctx, theta)
