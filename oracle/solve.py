@@ -21,6 +21,14 @@ autograd can differentiate through the smoother's values (Sec. 3.3).
 * Sec. 3.3: the relative validation metric
   log10(||r_{n+1}|| / ||r^{omega-J}_{n+1}||) after one cycle from the same
   state.
+* Chebyshev baseline smoother (not in the paper; the fixed-coefficient
+  polynomial the learned smoother is compared with): one application of the
+  degree-k Chebyshev polynomial in D^-1 A per smoothing phase, on the interval
+  [rho/30, 1.1 rho] with rho from 20 power iterations on D^-1 A started from
+  v_i = frac(i * 2654435761 / 2^32) + 0.5; the classical three-term
+  recurrence theta = (hi + lo)/2, delta = (hi - lo)/2, sigma = theta/delta:
+  d = D^-1 r / theta, then d <- rho_k rho_{k-1} d + (2 rho_k / delta) D^-1 r
+  with rho_0 = 1/sigma, rho_k = 1/(2 sigma - rho_{k-1}), u <- u + d.
 * Krylov outer loop (the Krylov form of the Sec. 2.1 correction): conjugate
   gradients on A u = f preconditioned by one V-cycle from a zero guess
   (symmetric for a symmetric smoother), with the flexible coefficient
@@ -146,6 +154,7 @@ class OLevel:
     M: torch.Tensor | None = None      # smoother values on A's pattern
     L: torch.Tensor | None = None      # Cholesky factor on the coarsest level
     s: float = 1.0
+    cheb: tuple | None = None          # Chebyshev smoother: (theta, delta, degree, D^-1)
 
 
 @dataclass
@@ -168,11 +177,63 @@ class OHierarchy:
     def set_jacobi(self, omega: float = 2.0 / 3.0):
         for lv in self.levels[:-1]:
             lv.M = jacobi_values(lv.A, omega)
+            lv.cheb = None
 
     def set_pseudo_inverse(self, coeffs):
         """coeffs[l] = (d0, d1, d2, o1, o2) for level l (rows past the last smoothed level unused)."""
         for l, lv in enumerate(self.levels[:-1]):
             lv.M = pseudo_inverse_values(lv.A, coeffs[l], lv.s)
+            lv.cheb = None
+
+    def set_chebyshev(self, degree: int = 3, lo: float = 1.0 / 30.0, hi: float = 1.1, n_power: int = 20):
+        for lv in self.levels[:-1]:
+            rho = power_estimate(lv.A, n_power)
+            dinv = 1.0 / diagonal(lv.A)
+            a, b = lo * rho, hi * rho
+            lv.cheb = ((b + a) / 2.0, (b - a) / 2.0, degree, dinv)
+            lv.M = None
+
+
+def diagonal(A: TMat) -> torch.Tensor:
+    on = A.row == A.col
+    return torch.zeros(A.n_rows, dtype=DT).index_add(0, A.row[on], A.val[on])
+
+
+def power_start(n: int) -> torch.Tensor:
+    """v_i = frac(i * 2654435761 / 2^32) + 0.5 (a fixed, RNG-free start vector)."""
+    i = np.arange(n, dtype=np.uint64)
+    return torch.from_numpy(((i * np.uint64(2654435761)) & np.uint64(0xFFFFFFFF)).astype(np.float64) / 2.0 ** 32 + 0.5)
+
+
+def power_estimate(A: TMat, n_power: int = 20) -> float:
+    """Largest eigenvalue of D^-1 A by n_power power iterations: v <- w / ||w||,
+    w = D^-1 A v; the estimate is ||w|| of the last iteration."""
+    dinv = 1.0 / diagonal(A)
+    v = power_start(A.n_rows)
+    v = v / torch.linalg.vector_norm(v)
+    lam = 0.0
+    for _ in range(n_power):
+        w = dinv * mv(A, v)
+        lam = float(torch.linalg.vector_norm(w))
+        v = w / lam
+    return lam
+
+
+def cheb_smooth(lv: OLevel, b: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+    """One application of the degree-k Chebyshev polynomial smoother."""
+    theta, delta, degree, dinv = lv.cheb
+    sigma = theta / delta
+    rho_prev = 1.0 / sigma
+    r = b - mv(lv.A, u)
+    d = dinv * r / theta
+    u = u + d
+    for _ in range(degree - 1):
+        r = b - mv(lv.A, u)
+        rho = 1.0 / (2.0 * sigma - rho_prev)
+        d = (rho * rho_prev) * d + (2.0 * rho / delta) * (dinv * r)
+        u = u + d
+        rho_prev = rho
+    return u
 
 
 def sweep(lv: OLevel, b: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
@@ -186,14 +247,20 @@ def vcycle(h: OHierarchy, b: torch.Tensor, u: torch.Tensor, nu1: int = 2, nu2: i
     lv = h.levels[l]
     if l == len(h.levels) - 1:
         return cholesky_solve(lv.L, b)
-    for _ in range(nu1):
-        u = sweep(lv, b, u)
+    if lv.cheb is not None:
+        u = cheb_smooth(lv, b, u)          # one polynomial application per phase
+    else:
+        for _ in range(nu1):
+            u = sweep(lv, b, u)
     r = b - mv(lv.A, u)
     bc = mv(lv.R, r)
     ec = vcycle(h, bc, torch.zeros(lv.R.n_rows, dtype=DT), nu1, nu2, l + 1)
     u = u + mv(lv.P, ec)
-    for _ in range(nu2):
-        u = sweep(lv, b, u)
+    if lv.cheb is not None:
+        u = cheb_smooth(lv, b, u)
+    else:
+        for _ in range(nu2):
+            u = sweep(lv, b, u)
     return u
 
 

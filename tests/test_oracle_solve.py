@@ -234,3 +234,53 @@ def test_pcg_breakdown_on_indefinite_preconditioner():
     b = W.rhs_uniform(3, A.n_rows)
     res = O.solve_pcg(h, b, tol=1e-8, precond=lambda r: -r)
     assert res.status == O.DIVERGED and res.n_vcycles == 0 and len(res.history) == 1
+
+
+# ---------------------------------------------------------------------------
+# Chebyshev baseline smoother
+# ---------------------------------------------------------------------------
+def _lap1d(n):
+    r = np.concatenate([np.arange(n), np.arange(n - 1), np.arange(1, n)])
+    c = np.concatenate([np.arange(n), np.arange(1, n), np.arange(n - 1)])
+    v = np.concatenate([np.full(n, 2.0), np.full(2 * (n - 1), -1.0)])
+    return W._coo_to_csr(n, n, r, c, v)
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 5])
+def test_chebyshev_error_propagation_closed_form(degree):
+    """On the 1D Laplacian (D^-1 A eigenpairs 1 - cos(k pi/(n+1)), sin) the
+    smoother maps an eigenvector e_k to T_d((theta - lam)/delta) / T_d(theta/delta) e_k."""
+    n = 31
+    A = _lap1d(n)
+    lv = O.OLevel(O.TMat.of(A), None, None)
+    theta, delta = 1.05, 0.95
+    lv.cheb = (theta, delta, degree, torch.full((n,), 0.5, dtype=torch.float64))
+    T = lambda x: np.cosh(degree * np.arccosh(x)) if abs(x) >= 1 else np.cos(degree * np.arccos(x))
+    i = np.arange(1, n + 1)
+    for k in (1, 5, 16, 30):
+        lam = 1.0 - np.cos(k * np.pi / (n + 1))
+        e = torch.from_numpy(np.sin(i * k * np.pi / (n + 1)))
+        out = O.cheb_smooth(lv, torch.zeros(n, dtype=torch.float64), e).numpy()
+        gain = T((theta - lam) / delta) / T(theta / delta)
+        np.testing.assert_allclose(out, gain * e.numpy(), rtol=1e-12, atol=1e-13)
+
+
+def test_power_estimate_brackets_the_spectrum():
+    A = W.fv_mesh("graded", 800, 2)[0]
+    Ad = A.to_dense()
+    lam_max = np.linalg.eigvals(Ad / np.diag(Ad)[:, None]).real.max()
+    rho = O.power_estimate(O.TMat.of(A), 20)
+    assert 0.9 * lam_max <= rho <= lam_max * (1 + 1e-12)
+    assert np.array_equal(O.power_start(5).numpy()[:2], [0.5, (2654435761 % 2 ** 32) / 2 ** 32 + 0.5])
+
+
+def test_chebyshev_vcycle_converges_and_is_symmetric():
+    A = W.fv_mesh("band", 2000, 4, max_aspect=100.0)[0]
+    h = O.OHierarchy.of(S.build_hierarchy(A))
+    h.set_chebyshev(3)
+    b = W.rhs_zero_mean(2, A.n_rows)
+    res = O.solve(h, b, tol=1e-8)
+    assert res.status == O.OK
+    n = A.n_rows
+    x, y = W.rhs_uniform(7, n), W.rhs_uniform(8, n)
+    assert abs(x @ O.vcycle_operator_apply(h, y) - y @ O.vcycle_operator_apply(h, x)) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
