@@ -251,6 +251,13 @@ def run_gpu(args, wl, rank, world):
     jac = [timed(solve_only, Wm + k) for k in range(K)]
     jac_ms = statistics.mean(j[0] for j in jac)
     cyc_jac = statistics.mean(len(j[1][1]) - 1 for j in jac)
+    # the fixed-coefficient polynomial baseline: Chebyshev of degree 3 in D^-1 A
+    P.amg_set_chebyshev(ctx, 3)
+    for k in range(Wm):
+        timed(solve_only, k)
+    chb = [timed(solve_only, Wm + k) for k in range(K)]
+    cheb = {"solve_ms": statistics.mean(v[0] for v in chb), "vcycles": statistics.mean(len(v[1][1]) - 1 for v in chb),
+            "status": sorted(set(v[1][0] for v in chb))}
     P.gnn_predict_coeffs(ctx)
     judge = P.amg_judge(ctx, rhs_host[0].numpy(), 10)
 
@@ -273,10 +280,14 @@ def run_gpu(args, wl, rank, world):
     pk = [timed(pcg_step, Wm + k) for k in range(K)]
     P.amg_set_jacobi(ctx_k)
     pj = [timed(lambda k: P.amg_solve_device(ctx_k, rhs_dev[k], x, TOL), Wm + k) for k in range(K)]
+    P.amg_set_chebyshev(ctx_k, 3)
+    pc = [timed(lambda k: P.amg_solve_device(ctx_k, rhs_dev[k], x, TOL), Wm + k) for k in range(K)]
     pcg = {"gnn_step_ms": statistics.mean(v[0] for v in pk),
            "iterations_gnn": statistics.mean(len(v[1][1]) - 1 for v in pk),
            "jacobi_solve_ms": statistics.mean(v[0] for v in pj),
            "iterations_jacobi": statistics.mean(len(v[1][1]) - 1 for v in pj),
+           "chebyshev3_solve_ms": statistics.mean(v[0] for v in pc),
+           "iterations_chebyshev3": statistics.mean(len(v[1][1]) - 1 for v in pc),
            "status": sorted(set(v[1][0] for v in pk)),
            "smoother": "gcin-pseudo-inverse" if use_gnn_k else "jacobi (rerouted)"}
     P.amg_destroy(ctx_k)
@@ -375,6 +386,7 @@ def run_gpu(args, wl, rank, world):
             "pcg": pcg,
             "gnn_step_ms": ms_per_step, "gnn_solve_ms": solve_ms, "gnn_infer_ms": infer_ms,
             "jacobi_solve_ms": jac_ms, "vcycles_gnn": statistics.mean(cyc_gnn), "vcycles_jacobi": cyc_jac,
+            "chebyshev3": cheb,
             "speedup_solve_vs_jacobi": jac_ms / solve_ms, "speedup_step_vs_jacobi": jac_ms / ms_per_step,
             "judge_log10_ratio_10cycles": judge, "final_rel_residual": final_res,
             "status": sorted(set(statuses)), "setup_host_ms": setup_ms,

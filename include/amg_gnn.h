@@ -43,6 +43,7 @@ extern "C" {
 /* smoother of the V-cycle */
 #define AMG_SMOOTHER_JACOBI 0   /* relaxed Jacobi, Q^-1 = omega D^-1 (Sec. 2.3)          */
 #define AMG_SMOOTHER_GNN    1   /* sparse pseudo-inverse from coefficients (Sec. 3.1)    */
+#define AMG_SMOOTHER_CHEB   2   /* Chebyshev polynomial in D^-1 A (fixed-coefficient baseline) */
 
 /* outer iteration around the V-cycle */
 #define AMG_OUTER_REFINE 0      /* stationary correction x += V(b - A x) (Sec. 2.1)       */
@@ -241,6 +242,22 @@ int amg_reroute(amg_ctx *ctx, const double *b, int n_cycles, double *metric, int
  * continues from the current iterate (history and V-cycle count continue).
  * Returns 1 if the last solve on ctx did so. */
 int amg_last_solve_rerouted(const amg_ctx *ctx);
+
+/* Chebyshev baseline smoother (not in the paper: the fixed-coefficient
+ * polynomial the learned smoother is compared with).  Each pre- and
+ * post-smoothing phase of the V-cycle applies the degree-`degree`
+ * Chebyshev polynomial in D^-1 A once (degree residual evaluations),
+ * on the interval [rho/30, 1.1 rho] with rho the largest eigenvalue of
+ * D^-1 A estimated by 20 power iterations from v_i = frac(i 2654435761 / 2^32)
+ * + 0.5 (FP64, on the host, once per hierarchy), by the three-term recurrence
+ *   d = D^-1 r / theta;  d <- rho_k rho_{k-1} d + (2 rho_k / delta) D^-1 r,
+ *   rho_0 = delta / theta, rho_k = 1 / (2 theta / delta - rho_{k-1}), u <- u + d,
+ * theta = (hi + lo)/2, delta = (hi - lo)/2.  amg_smooth_device applies the
+ * polynomial n_sweeps times.  degree: 1..16.  Errors: AMG_ERR_ARG, AMG_ERR_STATE. */
+int amg_set_chebyshev(amg_ctx *ctx, int degree);
+
+/* The Chebyshev interval of level `level`: rho (power estimate), theta, delta. */
+int amg_get_chebyshev(const amg_ctx *ctx, int level, double *rho, double *theta, double *delta);
 
 /* ------------------------------------------------------------------------
  * Measurement aids (no counterpart in the paper; used for roofline timing)

@@ -31,6 +31,7 @@ AMG_FP64 = 0
 AMG_FP32_IN_FP64 = 1
 AMG_SMOOTHER_JACOBI = 0
 AMG_SMOOTHER_GNN = 1
+AMG_SMOOTHER_CHEB = 2
 AMG_OUTER_REFINE = 0
 AMG_OUTER_PCG = 1
 AMG_GNN_FP32 = 0
@@ -109,6 +110,8 @@ def _declare(L):
         "gcin_trainer_adam_step": (I, [P, D, D]),
         "amg_loss_grad": (I, [P, pd, pd, I, pd, pd]),
         "amg_kernel_launch": (I, [P, I, I, I, P, pd]),
+        "amg_set_chebyshev": (I, [P, I]),
+        "amg_get_chebyshev": (I, [P, I, pd, pd, pd]),
         "amg_vcycle_bytes": (I, [P, pd]),
         "amg_launch_count": (LL, []),
         "amg_residual_norm_noalloc": (I, [I, LL, P, P, P, P, P, P, P, P]),
@@ -130,7 +133,7 @@ def exported_symbols():
             "amg_judge", "amg_reroute", "amg_last_solve_rerouted", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
             "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
             "gcin_trainer_adam_step", "amg_loss_grad", "amg_kernel_launch", "amg_vcycle_bytes",
-            "amg_launch_count", "amg_residual_norm_noalloc"]
+            "amg_launch_count", "amg_residual_norm_noalloc", "amg_set_chebyshev", "amg_get_chebyshev"]
 
 
 # ---------------------------------------------------------------------------
@@ -339,6 +342,17 @@ def amg_loss_grad(ctx, c, f, n_vc=1):
 
 
 AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE, AMG_K_MASWEEP = range(8)
+
+
+def amg_set_chebyshev(ctx, degree=3):
+    return _check(ctx, lib().amg_set_chebyshev(ctx, int(degree)))
+
+
+def amg_get_chebyshev(ctx, level):
+    """(rho, theta, delta) of the Chebyshev interval on `level`."""
+    r, t, d = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, lib().amg_get_chebyshev(ctx, int(level), C.byref(r), C.byref(t), C.byref(d)))
+    return r.value, t.value, d.value
 
 
 def amg_kernel_launch(ctx, kernel, level, reps, stream=None) -> float:

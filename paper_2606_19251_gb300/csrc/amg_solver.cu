@@ -218,6 +218,49 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__re
     }
 }
 
+// Chebyshev smoother steps (fixed-coefficient baseline): first step from a
+// zero guess d = cr D^-1 b, u = d; later steps r = b - A u_in,
+// d = (first ? 0 : cd d) + cr D^-1 r, u_out = u_in + d.
+template <class T>
+__global__ void k_cheb_zero(int n, const T *__restrict__ dinv, const T *__restrict__ b, T *__restrict__ u,
+                            T *__restrict__ d, T cr) {
+    pdl_wait_and_release();
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const T di = cr * (dinv[i] * b[i]);
+    d[i] = di;
+    u[i] = di;
+}
+
+template <class T, int TPR>
+__global__ void __launch_bounds__(kBlock) k_cheb_step(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                      const T *__restrict__ a, const T *__restrict__ dinv,
+                                                      const T *__restrict__ b, const T *__restrict__ uin,
+                                                      T *__restrict__ uout, T *__restrict__ d, T cd, T cr,
+                                                      int first) {
+    pdl_wait_and_release();
+    const int g = blockIdx.x * kBlock + threadIdx.x;
+    const int row = g / TPR, lane = g % TPR;
+    T acc = T(0);
+    if (row < n) acc = row_dot<TPR>(lane, rp[row], rp[row + 1], col, a, Gather<T>{uin});
+    acc = group_sum<TPR>(acc);
+    if (row < n && lane == 0) {
+        const T dr = cr * (dinv[row] * (b[row] - acc));
+        const T di = first ? dr : cd * d[row] + dr;
+        d[row] = di;
+        uout[row] = uin[row] + di;
+    }
+}
+
+__global__ void k_dinv_vals(int n, const double *__restrict__ diag, double *__restrict__ d64,
+                            float *__restrict__ d32) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const double v = 1.0 / diag[i];
+    d64[i] = v;
+    d32[i] = static_cast<float>(v);
+}
+
 // (M A) values from the pair list in FP32, for the FP32 V-cycle (GB300's FP64
 // pipe is narrow; the FP32 V-cycle needs only the FP32 product)
 __global__ void k_assemble_ma32(int nnz, const int *__restrict__ pp, const int *__restrict__ pq_p,
@@ -776,6 +819,49 @@ template <class T> struct Launch {
     }
 };
 
+template <class T> static const T *dinvvals(const DevLevel &L);
+template <> const double *dinvvals<double>(const DevLevel &L) { return L.dinv64; }
+template <> const float *dinvvals<float>(const DevLevel &L) { return L.dinv32; }
+
+template <class T> struct ChebLaunch {
+    template <int TPR>
+    static void step(const DevLevel &L, const T *b, const T *uin, T *uout, T *d, T cd, T cr, int first,
+                     cudaStream_t s) {
+        launch_pdl(k_cheb_step<T, TPR>, dim3(grid_for(static_cast<long long>(L.n) * TPR)), dim3(kBlock), 0, s, L.n,
+                   L.A.rp, L.A.col, mvals<T>(L.A), dinvvals<T>(L), b, uin, uout, d, cd, cr, first);
+    }
+};
+
+// `apps` applications of the degree-k Chebyshev polynomial on level L from
+// cur (zero when zero_init); returns the buffer holding the result.
+template <class T>
+static T *cheb_smooth(amg_ctx *c, const DevLevel &L, cudaStream_t s, const T *b, T *cur, T *alt, int apps,
+                      bool zero_init) {
+    T *d = reinterpret_cast<T *>(L.vw);
+    const double theta = L.cheb_theta, delta = L.cheb_delta, sigma = theta / delta;
+    for (int a = 0; a < apps; ++a) {
+        double rho_prev = 1.0 / sigma;
+        for (int k = 0; k < c->cheb_degree; ++k) {
+            double cd = 0.0, cr = 1.0 / theta;
+            if (k > 0) {
+                const double rho = 1.0 / (2.0 * sigma - rho_prev);
+                cd = rho * rho_prev;
+                cr = 2.0 * rho / delta;
+                rho_prev = rho;
+            }
+            if (k == 0 && a == 0 && zero_init) {
+                launch_pdl(k_cheb_zero<T>, dim3(grid_for(L.n)), dim3(kBlock), 0, s, L.n, dinvvals<T>(L), b, cur, d,
+                           static_cast<T>(cr));
+                continue;
+            }
+            TPR_DISPATCH(L.A.tpr, ChebLaunch<T>::template step, L, b, static_cast<const T *>(cur), alt, d,
+                         static_cast<T>(cd), static_cast<T>(cr), k == 0 ? 1 : 0, s);
+            std::swap(cur, alt);
+        }
+    }
+    return cur;
+}
+
 template <class T> static void L_resid(const DevMat &A, const T *b, const T *u, T *r, cudaStream_t s) {
     TPR_DISPATCH(A.tpr, Launch<T>::template resid, A, b, u, r, s);
 }
@@ -814,6 +900,7 @@ static T *smooth(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *alt, 
     const DevLevel &L = c->lev[l];
     const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
     if (nsweeps == 0 && zero_init) cudaMemsetAsync(cur, 0, sizeof(T) * L.n, s);
+    if (c->smoother == AMG_SMOOTHER_CHEB) return cheb_smooth<T>(c, L, s, b, cur, alt, nsweeps, zero_init);
     for (int k = 0; k < nsweeps; ++k) {
         const bool first = (k == 0 && zero_init);
         if (gnn) {
@@ -878,6 +965,7 @@ static T *smooth_fast(amg_ctx *c, int l, cudaStream_t s, const T *b, T *cur, T *
         if (zero_init) cudaMemsetAsync(cur, 0, sizeof(T) * L.n, s);
         return cur;
     }
+    if (c->smoother == AMG_SMOOTHER_CHEB) return cheb_smooth<T>(c, L, s, b, cur, alt, nsweeps, zero_init);
     int k = 0;
     if (zero_init) {
         if (gnn) {
@@ -921,22 +1009,26 @@ static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
         return u;
     }
     T *bc = reinterpret_cast<T *>(c->lev[l + 1].vb);
+    // the Chebyshev baseline applies its polynomial once per smoothing phase
+    const bool cheb = (c->smoother == AMG_SMOOTHER_CHEB);
+    const int nu1 = cheb ? (c->opt.nu1 > 0 ? 1 : 0) : c->opt.nu1;
+    const int nu2 = cheb ? (c->opt.nu2 > 0 ? 1 : 0) : c->opt.nu2;
     if (L.fast) {
         bool have_w = false;
-        T *cur = smooth_fast<T>(c, l, s, b, u, t, c->opt.nu1, true, have_w);
+        T *cur = smooth_fast<T>(c, l, s, b, u, t, nu1, true, have_w);
         T *alt = (cur == u) ? t : u;
         TPR_DISPATCH(L.RA.tpr, Launch<T>::template resid_restrict, L.R, L.RA, b, cur, bc, s);
         T *ec = vcycle_level<T>(c, l + 1, s);
         L_apply<T>(L.P, mvals<T>(L.P), ec, cur, 1, s);
-        return smooth_fast<T>(c, l, s, b, cur, alt, c->opt.nu2, false, have_w);
+        return smooth_fast<T>(c, l, s, b, cur, alt, nu2, false, have_w);
     }
-    T *cur = smooth<T>(c, l, s, b, u, t, r, c->opt.nu1, true);
+    T *cur = smooth<T>(c, l, s, b, u, t, r, nu1, true);
     T *alt = (cur == u) ? t : u;
     L_resid<T>(L.A, b, cur, r, s);
     L_spmv<T>(L.R, r, bc, s);
     T *ec = vcycle_level<T>(c, l + 1, s);
     L_apply<T>(L.P, mvals<T>(L.P), ec, cur, 1, s);
-    return smooth<T>(c, l, s, b, cur, alt, r, c->opt.nu2, false);
+    return smooth<T>(c, l, s, b, cur, alt, r, nu2, false);
 }
 
 template <class T>
@@ -1002,7 +1094,7 @@ static void free_graph(SolveGraph &G) {
 // Build (once per hierarchy and smoother) the whole-solve graph.
 template <class T>
 static int ensure_graph(amg_ctx *c) {
-    SolveGraph &G = c->sgraph[c->smoother + 2 * c->opt.outer];
+    SolveGraph &G = c->sgraph[c->smoother + 3 * c->opt.outer];
     if (G.exec && G.version == c->hier_version) return AMG_OK;
     free_graph(G);
     cudaGraph_t g = nullptr;
@@ -1049,7 +1141,7 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
     if (rc) return rc;
     enqueue_init<T>(c, s, tol, max_iter);
     CKL("solve init launch");
-    const SolveGraph &G = c->sgraph[c->smoother + 2 * c->opt.outer];
+    const SolveGraph &G = c->sgraph[c->smoother + 3 * c->opt.outer];
     CK(cudaGraphLaunch(G.exec, s));
     CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1064,7 +1156,7 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
         rc = ensure_graph<T>(c);
         if (rc) return rc;
         launch_pdl(k_state_continue, dim3(1), dim3(1), 0, s, c->state);
-        const SolveGraph &GJ = c->sgraph[AMG_SMOOTHER_JACOBI + 2 * c->opt.outer];
+        const SolveGraph &GJ = c->sgraph[AMG_SMOOTHER_JACOBI + 3 * c->opt.outer];
         CK(cudaGraphLaunch(GJ.exec, s));
         CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1126,6 +1218,8 @@ static void layout(amg_ctx *c, Planner &pl) {
         L.q32 = pl.take<float>(std::max(1, L.A.nnz));
         L.j64 = pl.take<double>(L.n);
         L.j32 = pl.take<float>(L.n);
+        L.dinv64 = pl.take<double>(L.n);
+        L.dinv32 = pl.take<float>(L.n);
         L.fast = H.fast;
         if (H.fast) {
             layout_mat(pl, L.MA, H.MA);
@@ -1234,6 +1328,7 @@ static int upload(amg_ctx *c) {
         k_offdiag_absmax<<<nb, kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, c->partials); AMG_COUNT();
         k_max_final<<<1, 32, 0, s>>>(c->partials, nb, c->scal + l); AMG_COUNT();
         k_jacobi_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, c->opt.omega, L.j64, L.j32); AMG_COUNT();
+        k_dinv_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, L.dinv64, L.dinv32); AMG_COUNT();
         k_pinv_basis<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag, c->scal + l, L.bx,
                                                       L.bw, L.isd); AMG_COUNT();
     }
@@ -1456,6 +1551,42 @@ int amg_set_jacobi(amg_ctx *c, double omega) {
     c->smoother = AMG_SMOOTHER_JACOBI;
     return AMG_OK;
 }
+
+int amg_set_chebyshev(amg_ctx *c, int degree) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    if (degree < 1 || degree > 16) return ctx_fail(c, "Chebyshev degree outside 1..16"), AMG_ERR_ARG;
+    if (c->cheb_version != c->hier_version) {
+        const int nlev = static_cast<int>(c->lev.size());
+        for (int l = 0; l < nlev - 1; ++l) {
+            DevLevel &L = c->lev[l];
+            const double rho = power_estimate(c->host[l].A, 20);
+            if (!(rho > 0.0) || !std::isfinite(rho)) return ctx_fail(c, "power estimate failed"), AMG_ERR_ARG;
+            const double lo = rho / 30.0, hi = 1.1 * rho;
+            L.cheb_rho = rho;
+            L.cheb_theta = 0.5 * (hi + lo);
+            L.cheb_delta = 0.5 * (hi - lo);
+        }
+        c->cheb_version = c->hier_version;
+    }
+    if (degree != c->cheb_degree) {   // the captured graphs hold the polynomial's steps
+        for (int o = 0; o < 2; ++o) free_graph(c->sgraph[AMG_SMOOTHER_CHEB + 3 * o]);
+        c->cheb_degree = degree;
+    }
+    c->smoother = AMG_SMOOTHER_CHEB;
+    return AMG_OK;
+}
+
+int amg_get_chebyshev(const amg_ctx *c, int level, double *rho, double *theta, double *delta) {
+    if (!c || level < 0 || level >= static_cast<int>(c->lev.size()) - 1) return AMG_ERR_ARG;
+    if (c->cheb_version != c->hier_version) return AMG_ERR_STATE;
+    const DevLevel &L = c->lev[level];
+    if (rho) *rho = L.cheb_rho;
+    if (theta) *theta = L.cheb_theta;
+    if (delta) *delta = L.cheb_delta;
+    return AMG_OK;
+}
 }  // extern "C"
 
 namespace amg {
@@ -1527,6 +1658,7 @@ int amg_get_smoother(const amg_ctx *cc, int level, double *q_out) {
     if (!c || !q_out || level < 0 || level >= static_cast<int>(c->lev.size()) - 1) return AMG_ERR_ARG;
     const DevLevel &L = c->lev[level];
     CK(cudaSetDevice(c->opt.device));
+    if (c->smoother == AMG_SMOOTHER_CHEB) return ctx_fail(c, "the Chebyshev smoother has no explicit Q^-1"), AMG_ERR_STATE;
     if (c->smoother == AMG_SMOOTHER_GNN) {
         CK(cudaMemcpyAsync(q_out, L.q64, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -1776,7 +1908,19 @@ double pass_bytes(const DevMat &M, int tb, double gathered, double vec_rw) {
     return 4.0 * (M.nr + 1) + (4.0 + tb) * M.nnz + tb * gathered + tb * vec_rw * M.nr;
 }
 
+// Chebyshev: `apps` polynomial applications of cheb_degree steps; a step
+// reads dinv, b, u_in, d and writes d, u_out; the zero-guess first step
+// reads dinv, b and writes d, u
+double cheb_bytes(const amg_ctx *c, const DevLevel &L, int tb, int apps, bool zero_init) {
+    double b = 0.0;
+    for (int a = 0; a < apps; ++a)
+        for (int k = 0; k < c->cheb_degree; ++k)
+            b += (k == 0 && a == 0 && zero_init) ? 4.0 * tb * L.n : pass_bytes(L.A, tb, L.n, 6);
+    return b;
+}
+
 double smooth_bytes(const amg_ctx *c, const DevLevel &L, int tb, int nsweeps, bool zero_init) {
+    if (c->smoother == AMG_SMOOTHER_CHEB) return cheb_bytes(c, L, tb, nsweeps, zero_init);
     const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
     double b = 0.0;
     for (int k = 0; k < nsweeps; ++k) {
@@ -1793,6 +1937,7 @@ double smooth_bytes(const amg_ctx *c, const DevLevel &L, int tb, int nsweeps, bo
 }
 
 double smooth_fast_bytes(const amg_ctx *c, const DevLevel &L, int tb, int nsweeps, bool zero_init) {
+    if (c->smoother == AMG_SMOOTHER_CHEB) return cheb_bytes(c, L, tb, nsweeps, zero_init);
     const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
     double b = 0.0;
     int k = 0;
@@ -1813,21 +1958,24 @@ double vcycle_bytes_level(const amg_ctx *c, int l, int tb) {
     const DevLevel &L = c->lev[l];
     const int nlev = static_cast<int>(c->lev.size());
     if (l == nlev - 1) return 8.0 * c->nL * c->nL + 2.0 * tb * c->nL;
+    const bool cheb = (c->smoother == AMG_SMOOTHER_CHEB);
+    const int nu1 = cheb ? (c->opt.nu1 > 0 ? 1 : 0) : c->opt.nu1;
+    const int nu2 = cheb ? (c->opt.nu2 > 0 ? 1 : 0) : c->opt.nu2;
     double b;
     if (L.fast) {
-        b = smooth_fast_bytes(c, L, tb, c->opt.nu1, true);
+        b = smooth_fast_bytes(c, L, tb, nu1, true);
         b += pass_bytes(L.R, tb, L.n, 1) + pass_bytes(L.RA, tb, L.n, 0);   // b_c = R b - (R A) u
         b += vcycle_bytes_level(c, l + 1, tb);
         b += pass_bytes(L.P, tb, L.P.nc, 2);
-        b += smooth_fast_bytes(c, L, tb, c->opt.nu2, false);
+        b += smooth_fast_bytes(c, L, tb, nu2, false);
         return b;
     }
-    b = smooth_bytes(c, L, tb, c->opt.nu1, true);
+    b = smooth_bytes(c, L, tb, nu1, true);
     b += pass_bytes(L.A, tb, L.n, 2);                           // residual
     b += pass_bytes(L.R, tb, L.n, 1);                           // restriction
     b += vcycle_bytes_level(c, l + 1, tb);
     b += pass_bytes(L.P, tb, L.P.nc, 2);                        // prolongation-correction
-    b += smooth_bytes(c, L, tb, c->opt.nu2, false);
+    b += smooth_bytes(c, L, tb, nu2, false);
     return b;
 }
 

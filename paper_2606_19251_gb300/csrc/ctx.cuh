@@ -27,6 +27,8 @@ struct DevLevel {
     unsigned char *isd = nullptr;              // 1 on the diagonal entries of A's pattern
     double *q64 = nullptr; float *q32 = nullptr;   // pseudo-inverse values on A's pattern
     double *j64 = nullptr; float *j32 = nullptr;   // omega / a_ii
+    double *dinv64 = nullptr; float *dinv32 = nullptr;   // 1 / a_ii (Chebyshev smoother)
+    double cheb_theta = 0.0, cheb_delta = 0.0, cheb_rho = 0.0;   // Chebyshev interval (host)
     // V-cycle vectors; storage sized for n doubles, used as float or double
     double *vb = nullptr, *vu = nullptr, *vr = nullptr, *vt = nullptr;
     // latency-optimised levels (L2-resident): single-pass sweeps with M A and
@@ -95,7 +97,9 @@ struct amg_ctx {
     amg::GcinEngine *gnn = nullptr;
     long long hier_version = 0;                // bumped by every hierarchy upload
     void *train = nullptr;                     // training (adjoint) buffers, created on demand
-    amg::SolveGraph sgraph[4];                 // per smoother + 2 x outer iteration
+    amg::SolveGraph sgraph[6];                 // per smoother + 3 x outer iteration
+    int cheb_degree = 3;
+    long long cheb_version = -1;               // hierarchy version the Chebyshev intervals belong to
     double *pcg = nullptr;                     // conjugate gradients: r, r_prev, z, p, q (n_0 each)
     double stall_ratio = 0.0;                  // armed by amg_reroute for the learned smoother
     int last_rerouted = 0;                     // the last solve switched to Jacobi

@@ -13,6 +13,7 @@
 #include "setup_host.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <queue>
 #include <utility>
@@ -295,6 +296,37 @@ void build_hierarchy(const HostCSR& A0, double theta, int max_levels, int max_co
         levels.emplace_back();
         levels.back().A = std::move(Ac);
     }
+}
+
+double power_estimate(const HostCSR &A, int n_power) {
+    const int n = A.n_rows;
+    if (n <= 0) return 0.0;
+    std::vector<double> dinv(n, 0.0), v(n), w(n);
+    for (int i = 0; i < n; ++i)
+        for (int p = A.rp[i]; p < A.rp[i + 1]; ++p)
+            if (A.col[p] == i) dinv[i] += A.val[p];
+    for (int i = 0; i < n; ++i) dinv[i] = 1.0 / dinv[i];
+    double nv = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t h = static_cast<uint32_t>(static_cast<uint64_t>(i) * 2654435761ull);
+        v[i] = static_cast<double>(h) / 4294967296.0 + 0.5;
+        nv += v[i] * v[i];
+    }
+    nv = std::sqrt(nv);
+    for (int i = 0; i < n; ++i) v[i] /= nv;
+    double lam = 0.0;
+    for (int it = 0; it < n_power; ++it) {
+        double nw = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) acc += A.val[p] * v[A.col[p]];
+            w[i] = dinv[i] * acc;
+            nw += w[i] * w[i];
+        }
+        lam = std::sqrt(nw);
+        for (int i = 0; i < n; ++i) v[i] = w[i] / lam;
+    }
+    return lam;
 }
 
 }  // namespace amg

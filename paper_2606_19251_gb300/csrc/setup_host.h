@@ -50,6 +50,11 @@ void product_pattern(const HostCSR &A, HostCSR &MA, std::vector<int> &pair_ptr, 
 // Row-by-row sparse product X Y keeping the structural pattern.
 HostCSR spgemm(const HostCSR &X, const HostCSR &Y);
 
+// Largest eigenvalue of D^-1 A by n_power power iterations (FP64):
+// v0_i = frac(i 2654435761 / 2^32) + 0.5 normalised, w = D^-1 A v,
+// estimate = ||w|| of the last iteration, v = w / ||w||.
+double power_estimate(const HostCSR &A, int n_power);
+
 // Setup-AMG-Hierarchy of Algorithm 1 (finest level first).
 void build_hierarchy(const HostCSR& A0, double theta, int max_levels, int max_coarse,
                      std::vector<HostLevel>& levels);
