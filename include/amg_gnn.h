@@ -31,7 +31,8 @@ extern "C" {
 #define AMG_ERR_CUDA        -2  /* a CUDA runtime call failed                       */
 #define AMG_ERR_NOT_SPD     -3  /* coarsest matrix not positive definite            */
 #define AMG_ERR_DIVERGED    -4  /* residual not finite or > 1e3 x initial residual  */
-#define AMG_ERR_STAGNATED   -5  /* < 1% residual reduction over 10 V-cycles         */
+#define AMG_ERR_STAGNATED   -5  /* best residual of the last 10 V-cycles not 1% below
+                                   the best of the 10 before them               */
 #define AMG_ERR_MAXITER     -6  /* max_iter V-cycles without reaching the tolerance */
 #define AMG_ERR_DEVICE_FLAG -7  /* a kernel reported an invalid index or value      */
 #define AMG_ERR_STATE       -8  /* call made in the wrong order (e.g. no hierarchy) */

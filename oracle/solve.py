@@ -16,8 +16,10 @@ autograd can differentiate through the smoother's values (Sec. 3.3).
   the coarsest level is solved by a dense Cholesky factorisation.
 * Sec. 4: stop when ||f - A u||_2 / ||f||_2 <= tol (relative to ||f||: a
   reading) or after max_iter cycles; diverged when a norm is not finite or
-  exceeds 1e3 times the initial one; stagnated when 10 cycles reduce the
-  norm by less than 1%.
+  exceeds 1e3 times the initial one; stagnated when the smallest norm of
+  the last 10 cycles is not 1% below the smallest of the 10 before them
+  (a window of minima: a stationary V-cycle need not reduce the 2-norm
+  monotonically, and from a warm start the first cycles can raise it).
 * Sec. 3.3: the relative validation metric
   log10(||r_{n+1}|| / ||r^{omega-J}_{n+1}||) after one cycle from the same
   state.
@@ -299,7 +301,7 @@ def solve(h: OHierarchy, f, tol: float = 1e-8, max_iter: int = 500, u0=None,
             if hist[-1] <= tol:
                 status = OK
                 break
-            if k >= 10 and hist[-1] > 0.99 * hist[-11]:
+            if k >= 20 and min(hist[-10:]) > 0.99 * min(hist[-20:-10]):
                 status = STAGNATED
                 break
     return SolveResult(u.numpy(), hist, k, status)
@@ -359,7 +361,7 @@ def solve_pcg(h: OHierarchy, f, tol: float = 1e-8, max_iter: int = 500, u0=None,
             if hist[-1] <= tol:
                 status = OK
                 break
-            if k >= 10 and hist[-1] > 0.99 * hist[-11]:
+            if k >= 20 and min(hist[-10:]) > 0.99 * min(hist[-20:-10]):
                 status = STAGNATED
                 break
     return SolveResult(u.numpy(), hist, k, status)

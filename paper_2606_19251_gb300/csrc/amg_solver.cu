@@ -542,6 +542,13 @@ __global__ void k_state_continue(SolveState *st) {
     st->restart = 1;
 }
 
+// Smallest of hist[k - off - 9 .. k - off].
+__device__ __forceinline__ double window_min(const double *hist, int k, int off) {
+    double m = hist[k - off];
+    for (int j = 1; j < 10; ++j) m = fmin(m, hist[k - off - j]);
+    return m;
+}
+
 // Sum the partials in a fixed order.  mode 0: ||b||.  mode 1: residual
 // history entry k and the stopping rule (Sec. 4 tolerance, divergence,
 // stagnation, iteration cap).
@@ -581,7 +588,7 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ 
         if (!isfinite(nrm) || nrm > 1e3 * st->r0) status = AMG_ERR_DIVERGED;
         else if (rel <= st->tol) status = AMG_OK;
         else if (k >= 10 && st->stall > 0.0 && rel > st->stall * hist[k - 10]) status = kStalled;
-        else if (k >= 10 && rel > 0.99 * hist[k - 10]) status = AMG_ERR_STAGNATED;
+        else if (k >= 20 && window_min(hist, k, 0) > 0.99 * window_min(hist, k, 10)) status = AMG_ERR_STAGNATED;
         else if (k >= st->max_iter) status = AMG_ERR_MAXITER;
     }
     st->status = status;

@@ -203,11 +203,16 @@ def fv_points(kind: str, n_points: int, seed: int, max_aspect: float = 1000.0):
 # ----------------------------------------------------------------------------
 # vertex-centred finite-volume assembly on a Delaunay triangulation
 # ----------------------------------------------------------------------------
-def delaunay_fv(points: np.ndarray, dirichlet: np.ndarray):
-    """Assemble the SPD FV Laplacian; returns (CSR, stats dict)."""
+def delaunay_fv(points: np.ndarray, dirichlet: np.ndarray, drop=None):
+    """Assemble the SPD FV Laplacian; returns (CSR, stats dict).
+
+    drop(centroids) -> bool mask removes triangles outside the domain (e.g.
+    inside an airfoil, whose surface is then a Neumann boundary)."""
     from scipy.spatial import Delaunay
 
     tri = Delaunay(points).simplices.astype(np.int64)
+    if drop is not None:
+        tri = tri[~drop(points[tri].mean(axis=1))]
     n_all = points.shape[0]
     ea, eb, ew = [], [], []
     for k in range(3):
@@ -238,6 +243,8 @@ def delaunay_fv(points: np.ndarray, dirichlet: np.ndarray):
     np.add.at(diag, ia, w)
     np.add.at(diag, ib, w)
     live = ~dirichlet
+    if drop is not None:   # points left without a kept triangle or coupling are not unknowns
+        live &= diag > 0.0
     newid = -np.ones(n_all, dtype=np.int64)
     newid[live] = np.arange(int(live.sum()))
     both = live[ia] & live[ib]
@@ -248,7 +255,7 @@ def delaunay_fv(points: np.ndarray, dirichlet: np.ndarray):
     vals = np.concatenate([-rw, -rw, diag[live]])
     A = _coo_to_csr(n, n, rows, cols, vals)
     stats = {"n_points": n_all, "n_triangles": int(tri.shape[0]), "n_clipped": n_clipped,
-             "n_dirichlet": int(dirichlet.sum()), "n": n, "nnz": A.nnz}
+             "n_dirichlet": int(dirichlet.sum()), "n": n, "nnz": A.nnz, "live": live}
     return A, stats
 
 
@@ -279,6 +286,105 @@ def c3_batch(n_meshes: int = 64, seed: int = 0, n_min: int = 2000, n_max: int = 
 def c4_matrix(seed: int = 0, n_points: int = 2_500_000) -> CSR:
     """2.5M-point graded mesh with an anisotropic band (aspect up to 1000)."""
     return fv_mesh("band", n_points, seed, max_aspect=1000.0)[0]
+
+
+# ----------------------------------------------------------------------------
+# airfoil sequence: NACA m4 12 in a circular farfield
+# ----------------------------------------------------------------------------
+def _naca(x, m, p=0.4, t=0.12):
+    """Camber line, its slope and the half thickness of a NACA 4-digit section
+    with a closed trailing edge (last thickness coefficient -0.1036)."""
+    yt = 5 * t * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3 - 0.1036 * x ** 4)
+    if m == 0.0:
+        return np.zeros_like(x), np.zeros_like(x), yt
+    front = x < p
+    yc = np.where(front, m / p ** 2 * (2 * p * x - x ** 2), m / (1 - p) ** 2 * ((1 - 2 * p) + 2 * p * x - x ** 2))
+    dyc = np.where(front, 2 * m / p ** 2 * (p - x), 2 * m / (1 - p) ** 2 * (p - x))
+    return yc, dyc, yt
+
+
+def naca_points(seed: int, n_surface: int = 1000, n_far: int = 200_000, r_far: float = 20.0,
+                h1: float = 1e-5, growth: float = 1.1):
+    """Points of an airfoil mesh: cosine-spaced surface points, wall-normal
+    layers (first height h1 chords, growth 1.1, until a layer is as tall as
+    the local surface spacing), then points uniform in angle and in log r out
+    to a farfield circle of radius r_far (Dirichlet).  Camber m ~ U[0, 0.04]
+    by seed, p = 0.4, thickness 12 %.  Returns (points, dirichlet mask, m)."""
+    m = 0.04 * float(uniform01(_sub_seed(seed, 51), 1)[0])
+    half = n_surface // 2
+    beta = np.linspace(0.0, np.pi, half + 1)
+    xs = 0.5 * (1.0 - np.cos(beta))
+    yc, dyc, yt = _naca(xs, m)
+    th = np.arctan(dyc)
+    up = np.stack([xs - yt * np.sin(th), yc + yt * np.cos(th)], 1)
+    lo = np.stack([xs + yt * np.sin(th), yc - yt * np.cos(th)], 1)
+    surf = np.concatenate([up, lo[1:-1][::-1]])              # closed loop, leading edge at index 0
+    nxt, prv = np.roll(surf, -1, 0), np.roll(surf, 1, 0)
+    tang = nxt - prv
+    normal = np.stack([tang[:, 1], -tang[:, 0]], 1)
+    normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+    # orient outward: away from the section's centroid line
+    cx = surf - np.array([0.5, 0.0])
+    sign = np.sign(np.sum(normal * cx, axis=1))
+    sign[sign == 0] = 1.0
+    normal *= sign[:, None]
+    ds = 0.5 * np.linalg.norm(tang, axis=1)                  # local surface spacing
+    layers, h, dist = [surf], h1, 0.0
+    while True:
+        dist += h
+        live = h < ds
+        if not live.any() or dist > 0.5:
+            break
+        layers.append((surf + dist * normal)[live])
+        h *= growth
+    inner = np.concatenate(layers)
+    r0 = 0.5 + dist + 0.1
+    u = uniform01(_sub_seed(seed, 52), n_far)
+    v = uniform01(_sub_seed(seed, 53), n_far)
+    r = r0 * np.exp(u * np.log(r_far / r0))
+    ang = 2 * np.pi * v
+    far = np.stack([0.5 + r * np.cos(ang), r * np.sin(ang)], 1)
+    n_ring = 2000
+    a = 2 * np.pi * np.arange(n_ring) / n_ring
+    ring = np.stack([0.5 + r_far * np.cos(a), r_far * np.sin(a)], 1)
+    pts = np.concatenate([inner, far[r < r_far * 0.999], ring])
+    dmask = np.zeros(len(pts), dtype=bool)
+    dmask[-n_ring:] = True
+    return pts, dmask, m
+
+
+def c5_problem(seed: int = 0, n_rhs: int = 50, **kw):
+    """Airfoil pressure sequence (C5): the FV Laplacian of naca_points, with
+    the wall (inside of the section) removed, and n_rhs right-hand sides
+    f_t = f_{t-1} + 0.05 g_t, f_0 = g_0, each g a zero-mean sum of 16 Fourier
+    modes with wave numbers 1..3 over the farfield diameter.
+    Returns (A, list of f_t, camber m)."""
+    pts, dmask, m = naca_points(seed, **kw)
+
+    def inside(c):
+        x = c[:, 0]
+        ok = (x > 0.0) & (x < 1.0)
+        xc = np.clip(x, 0.0, 1.0)
+        yc, _, yt = _naca(xc, m)
+        return ok & (np.abs(c[:, 1] - yc) < yt)
+
+    A, st = delaunay_fv(pts, dmask, drop=inside)
+    xy = pts[st["live"]]
+    L = 40.0
+    seqs, f = [], None
+    for t in range(n_rhs):
+        s = _sub_seed(seed, 1000 + t)
+        kx = np.floor(1 + 3 * uniform01(_sub_seed(s, 1), 16))
+        ky = np.floor(1 + 3 * uniform01(_sub_seed(s, 2), 16))
+        ph = 2 * np.pi * uniform01(_sub_seed(s, 3), 16)
+        amp = uniform_pm1(_sub_seed(s, 4), 16)
+        g = np.zeros(len(xy))
+        for k in range(16):
+            g += amp[k] * np.sin(2 * np.pi * (kx[k] * xy[:, 0] + ky[k] * xy[:, 1]) / L + ph[k])
+        g -= g.mean()
+        f = g if f is None else f + 0.05 * g
+        seqs.append(f.copy())
+    return A, seqs, m
 
 
 def rhs_uniform(seed: int, n: int) -> np.ndarray:
