@@ -1597,10 +1597,11 @@ int amg_get_chebyshev(const amg_ctx *c, int level, double *rho, double *theta, d
 }  // extern "C"
 
 namespace amg {
-// Assemble Q^-1 (and M A on latency-optimised levels) from coefficients in
-// device memory (G x 5 FP32, level order) without a host round trip; the
-// caller validates the coefficients after its own synchronisation.
-int set_coeffs_from_device(amg_ctx *c, const float *d_coef, cudaStream_t s) {
+// Enqueue the assembly of Q^-1 (and M A on latency-optimised levels) from
+// coefficients in device memory (G x 5 FP32, level order) without a host
+// round trip; the caller validates the coefficients after its own
+// synchronisation and selects the smoother.
+int enqueue_coeff_assembly(amg_ctx *c, const float *d_coef, cudaStream_t s) {
     const int nlev = static_cast<int>(c->lev.size());
     for (int l = 0; l < nlev - 1; ++l) {
         const DevLevel &L = c->lev[l];
@@ -1615,8 +1616,6 @@ int set_coeffs_from_device(amg_ctx *c, const float *d_coef, cudaStream_t s) {
         }
     }
     CKL("assemble pseudo-inverse");
-    c->have_q = true;
-    c->smoother = AMG_SMOOTHER_GNN;
     return AMG_OK;
 }
 

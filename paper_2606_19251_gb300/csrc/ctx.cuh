@@ -110,6 +110,6 @@ namespace amg {
 bool ctx_fail(amg_ctx *c, const std::string &msg);
 int ctx_cuda_check(amg_ctx *c, cudaError_t e, const char *what);
 int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s);
-int set_coeffs_from_device(amg_ctx *c, const float *d_coef, cudaStream_t s);
+int enqueue_coeff_assembly(amg_ctx *c, const float *d_coef, cudaStream_t s);
 void train_bufs_free(amg_ctx *c);
 }  // namespace amg

@@ -599,7 +599,16 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
 #include "gcin_tc.cuh"
 namespace amg {
 
+void gcin_prepare_device() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(k_agg_lin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    done[dev] = true;
+}
+
 void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
+    gcin_prepare_device();
     const int N = b.N, G = b.G, NT = b.NT;
     k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
     for (int l = 0; l < kLayers; ++l) {
@@ -607,11 +616,6 @@ void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
             k_layer1_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + kPL.convW[0], th + kPL.convB[0],
                                                 b.tstart, b.h1, b.y[0], b.tmean, b.tm2); AMG_COUNT();
         } else if (b.bf16) {
-            static bool attr_set = false;
-            if (!attr_set) {
-                cudaFuncSetAttribute(k_agg_lin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-                attr_set = true;
-            }
             k_agg_lin_tc<<<(NT + 1) / 2, kBlock, kTcSmem, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
                                                                th + kPL.convB[l], b.tstart, NT, b.h[l], b.y[l],
                                                                b.tmean, b.tm2, b.err); AMG_COUNT();
@@ -997,6 +1001,7 @@ __global__ void k_adam(int n, float *__restrict__ theta, const float *__restrict
 
 void gcin_engine_free(GcinEngine *e) {
     if (!e) return;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
     gcin_batch_free(e->batch);
     if (e->theta) cudaFree(e->theta);
     delete e;
@@ -1073,11 +1078,41 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
         g->batch_version = c->hier_version;
     }
     g->batch.bf16 = (c->opt.gnn_precision == AMG_GNN_BF16) ? 1 : 0;
-    gcin_forward(g->batch, g->theta, s);
-    // the smoother is assembled straight from the device coefficients; the
-    // host copy (returned and validated) comes back with one synchronisation
-    int rc = set_coeffs_from_device(c, g->batch.c, s);
-    if (rc) return rc;
+    // forward + smoother assembly (straight from the device coefficients) run
+    // as one CUDA graph, captured once per batch and arithmetic: ~40 small
+    // kernels whose host launch cost would otherwise exceed their run time
+    const int key = g->batch.bf16 + 2 * c->opt.precision;
+    if (!g->exec || g->exec_version != g->batch_version || g->exec_key != key) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+        gcin_prepare_device();
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return ctx_cuda_check(c, e, "GCIN capture begin");
+        const long long before = g_launches.load();
+        gcin_forward(g->batch, g->theta, s);
+        const int rc0 = enqueue_coeff_assembly(c, g->batch.c, s);
+        g->exec_kernels = g_launches.load() - before;
+        g_launches.fetch_sub(g->exec_kernels);
+        e = cudaStreamEndCapture(s, &graph);
+        if (rc0) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc0;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g->exec = nullptr;
+            return ctx_cuda_check(c, e, "GCIN graph");
+        }
+        g->exec_version = g->batch_version;
+        g->exec_key = key;
+    }
+    e = cudaGraphLaunch(g->exec, s);
+    if (e != cudaSuccess) return ctx_cuda_check(c, e, "GCIN graph launch");
+    g_launches.fetch_add(g->exec_kernels);
+    c->have_q = true;
+    c->smoother = AMG_SMOOTHER_GNN;
     int dflag = 0;
     const int G = g->batch.G;
     std::vector<float> cf(static_cast<size_t>(G) * 5);

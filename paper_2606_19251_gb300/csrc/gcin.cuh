@@ -127,6 +127,15 @@ struct GcinEngine {
     bool have_params = false;
     GcinBatch batch;
     long long batch_version = -1;   // hierarchy version the batch was built from
+    // inference + smoother assembly captured once per batch and arithmetic
+    // (the parameters are read from `theta` at replay)
+    cudaGraphExec_t exec = nullptr;
+    long long exec_version = -1;
+    int exec_key = -1;
+    long long exec_kernels = 0;
 };
+
+// Per-device kernel attributes of the GCIN forward (set before any capture).
+void gcin_prepare_device();
 
 }  // namespace amg
