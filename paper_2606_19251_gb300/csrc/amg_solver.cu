@@ -883,9 +883,13 @@ static void L_jacobi(const DevMat &A, const T *jac, const T *b, const T *uin, T 
     TPR_DISPATCH(A.tpr, Launch<T>::template jacobi, A, jac, b, uin, uout, s);
 }
 
+// Grid of the FP64 outer-loop passes: one thread group per row up to 32
+// blocks per SM (the partial sums have one slot per block; a wider grid
+// keeps more rows' loads in flight than a grid-stride loop over few blocks).
+constexpr int kOuterBlocksPerSM = 32;
 static int outer_blocks(const DevMat &A) {
     long long need = (static_cast<long long>(A.nr) * A.tpr + kBlock - 1) / kBlock;
-    long long cap = static_cast<long long>(kNumSMs) * 8;
+    long long cap = static_cast<long long>(kNumSMs) * kOuterBlocksPerSM;
     return static_cast<int>(std::max(1LL, std::min(need, cap)));
 }
 
@@ -1250,7 +1254,7 @@ static void layout(amg_ctx *c, Planner &pl) {
     c->db = pl.take<double>(n0);
     c->dx = pl.take<double>(n0);
     c->pcg = pl.take<double>(5 * static_cast<size_t>(n0));
-    c->n_partials = kNumSMs * 8;                       // blocks of a capped grid
+    c->n_partials = kNumSMs * kOuterBlocksPerSM;        // blocks of a capped grid
     c->partials = pl.take<double>(5 * c->n_partials);  // up to 5 partial sums per block
     c->scal = pl.take<double>(nlev);
     c->state = pl.take<SolveState>(1);

@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
     double s = 0.0;
     float mx = -INFINITY;
     int mi = a;
+#pragma unroll 4
     for (int i = a + q; i < e; i += 4) {
         const size_t o = static_cast<size_t>(i) * kHidden + f;
         const float v = fmaxf((y[o] - m) * r * ga + be, 0.f);
@@ -557,6 +558,7 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     const int l = t / kRo, k = t % kRo;
     const float *W = th + kPLd.roW[l];
     float z = th[kPLd.roB[l] + k];
+#pragma unroll 8
     for (int m = 0; m < 2 * kHidden; ++m) z = fmaf(sp[l * 2 * kHidden + m], W[m * kRo + k], z);
     // layer norm over the 128-vector
     const float mean = block128_sum(z, red) / kEmb;
@@ -575,6 +577,7 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     ss[t] = sg;
     __syncthreads();
     float a1 = th[kPLd.h1B + t];
+#pragma unroll 8
     for (int m = 0; m < kEmb; ++m) a1 = fmaf(ss[m], th[kPLd.h1W + m * 128 + t], a1);
     a1 = fmaxf(a1, 0.f);
     sa1[t] = a1;
@@ -582,6 +585,7 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     __syncthreads();
     if (t < 64) {
         float a2 = th[kPLd.h2B + t];
+#pragma unroll 8
         for (int m = 0; m < 128; ++m) a2 = fmaf(sa1[m], th[kPLd.h2W + m * 64 + t], a2);
         a2 = fmaxf(a2, 0.f);
         sa2[t] = a2;
@@ -590,6 +594,7 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     __syncthreads();
     if (t < 5) {
         float o = th[kPLd.h3B + t];
+#pragma unroll 8
         for (int m = 0; m < 64; ++m) o = fmaf(sa2[m], th[kPLd.h3W + m * 5 + t], o);
         c[g * 5 + t] = o;
     }
