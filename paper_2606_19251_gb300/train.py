@@ -96,13 +96,14 @@ class Trainer:
             self.tr = None
 
 
-def train(train_mats, val_mats, theta0, epochs=30, batch=5, seed=0, log=print, device=0, n_vc=1, val_cycles=10):
+def train(train_mats, val_mats, theta0, epochs=30, batch=5, seed=0, log=print, device=0, n_vc=1, val_cycles=10,
+          precision=P.AMG_GNN_FP32):
     """Train on `train_mats`, validate on `val_mats`; returns (best theta, log rows)."""
     import workloads as W
     probs = [Problem(A, device=device) for A in train_mats]
     vals = [Problem(A, device=device) for A in val_mats]
     val_rhs = [W.rhs_uniform(10_000 + k, p.A.n_rows) for k, p in enumerate(vals)]
-    tr = Trainer(theta0, device=device, n_vc=n_vc, val_cycles=val_cycles)
+    tr = Trainer(theta0, device=device, n_vc=n_vc, val_cycles=val_cycles, precision=precision)
     rows = []
     try:
         val0 = tr.validate(vals, val_rhs)

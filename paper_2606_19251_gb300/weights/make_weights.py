@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--meshes", type=int, default=64)
     ap.add_argument("--nvc", type=int, default=3, help="V-cycles per loss (Sec. 3.3 multi-V-cycle loss)")
     ap.add_argument("--val-cycles", type=int, default=10)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="arithmetic of the forward node linears during training")
     ap.add_argument("--out", default=os.path.join(HERE, "gcin_c3.npy"))
     args = ap.parse_args()
     import workloads as W
@@ -42,11 +44,14 @@ def main():
     val = W.c3_batch(8, seed=1)
     print(f"meshes ready in {time.time() - t0:.1f}s: n = {[m.n_rows for m in mats[:8]]}...", flush=True)
     theta0 = W.gcin_init_params(0)
+    from paper_2606_19251_gb300 import api as P
+    prec = P.AMG_GNN_BF16 if args.precision == "bf16" else P.AMG_GNN_FP32
     best, rows = train(mats, val, theta0, epochs=args.epochs, batch=args.batch, n_vc=args.nvc,
-                       val_cycles=args.val_cycles, log=lambda r: print(json.dumps(r), flush=True))
+                       val_cycles=args.val_cycles, log=lambda r: print(json.dumps(r), flush=True), precision=prec)
     np.save(args.out, np.asarray(best, dtype=np.float32))
     with open(os.path.splitext(args.out)[0] + "_log.json", "w") as f:
         json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "n_vc": args.nvc,
+                   "precision": args.precision,
                    "val_cycles": args.val_cycles, "rows": rows,
                    "seconds": time.time() - t0}, f, indent=1)
     print("wrote", args.out, flush=True)
