@@ -165,6 +165,23 @@ def run_reference(args, wl):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms_per_step: float, world: int) -> float:
+    """Whole-job time per solve: `world` replicas each finish one solve per
+    ms_per_step (the max over ranks), so the job solves one every
+    ms_per_step / world."""
+    return ms_per_step / world
+
+
 def run_sequence(args, wl, rank, world):
     """The airfoil sequence: coefficients predicted and judged once, then 50
     right-hand sides solved one after another from the previous solution
@@ -300,11 +317,7 @@ def run_gpu(args, wl, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    total = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(sum(step_ms), world, f"cuda:{dev}")
     ms_per_step = total / K
     final_res = float(hist[-1])
 
@@ -439,7 +452,7 @@ def run_gpu(args, wl, rank, world):
             traffic = tr["dram_bytes_per_launch"]
 
     if rank == 0:
-        value = ms_per_step / world
+        value = replica_value(ms_per_step, world)
         line = {
             "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
