@@ -70,14 +70,13 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_resid(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                   const T *__restrict__ a, const T *__restrict__ b,
                                                   const T *__restrict__ u, T *__restrict__ r) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, a);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) {
-        const int e = rp[row + 1];
-        acc = row_dot<TPR>(lane, rp[row], e, col, a, Gather<T>{u});
-    }
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, a, Gather<T>{u});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) r[row] = b[row] - acc;
 }
@@ -87,14 +86,13 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                  const T *__restrict__ m, const T *__restrict__ x,
                                                  T *__restrict__ y) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, m);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) {
-        const int e = rp[row + 1];
-        acc = row_dot<TPR>(lane, rp[row], e, col, m, Gather<T>{x});
-    }
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, m, Gather<T>{x});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) y[row] = acc;
 }
@@ -105,14 +103,13 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_apply(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                   const T *__restrict__ m, const T *__restrict__ r,
                                                   T *__restrict__ u, int add) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, m);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) {
-        const int e = rp[row + 1];
-        acc = row_dot<TPR>(lane, rp[row], e, col, m, Gather<T>{r});
-    }
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, m, Gather<T>{r});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) u[row] = (add ? u[row] : T(0)) + acc;
 }
@@ -123,14 +120,13 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
                                                    const T *__restrict__ a, const T *__restrict__ jac,
                                                    const T *__restrict__ b, const T *__restrict__ uin,
                                                    T *__restrict__ uout) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, a);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) {
-        const int e = rp[row + 1];
-        acc = row_dot<TPR>(lane, rp[row], e, col, a, Gather<T>{uin});
-    }
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, a, Gather<T>{uin});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) uout[row] = uin[row] + jac[row] * (b[row] - acc);
 }
@@ -141,14 +137,13 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_ma_sweep(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                      const T *__restrict__ ma, const T *__restrict__ w,
                                                      const T *__restrict__ uin, T *__restrict__ uout) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, ma);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) {
-        const int e = rp[row + 1];
-        acc = row_dot<TPR>(lane, rp[row], e, col, ma, Gather<T>{uin});
-    }
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, ma, Gather<T>{uin});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) uout[row] = uin[row] + (w[row] - acc);
 }
@@ -158,14 +153,13 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_apply_w(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                     const T *__restrict__ m, const T *__restrict__ b,
                                                     T *__restrict__ u, T *__restrict__ w) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, m);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) {
-        const int e = rp[row + 1];
-        acc = row_dot<TPR>(lane, rp[row], e, col, m, Gather<T>{b});
-    }
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, m, Gather<T>{b});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) {
         u[row] = acc;
@@ -181,13 +175,16 @@ __global__ void __launch_bounds__(kBlock) k_resid_restrict(int nc, const int *__
                                                            const int *__restrict__ sp, const int *__restrict__ scol,
                                                            const T *__restrict__ sv, const T *__restrict__ b,
                                                            const T *__restrict__ u, T *__restrict__ bc) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rr, rs;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rr, row < nc, lane, rrp, row, rcol, rv);
+    row_prefetch<TPR>(rs, row < nc, lane, sp, row, scol, sv);
+    pdl_wait_and_release();
     T acc = T(0);
     if (row < nc) {
-        acc = row_dot<TPR>(lane, rrp[row], rrp[row + 1], rcol, rv, Gather<T>{b});
-        acc -= row_dot<TPR>(lane, sp[row], sp[row + 1], scol, sv, Gather<T>{u});
+        acc = row_dot_pref<TPR>(rr, rcol, rv, Gather<T>{b});
+        acc -= row_dot_pref<TPR>(rs, scol, sv, Gather<T>{u});
     }
     acc = group_sum<TPR>(acc);
     if (row < nc && lane == 0) bc[row] = acc;
@@ -203,14 +200,13 @@ template <class T, int TPR>
 __global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                           const T *__restrict__ a, const T *__restrict__ jac,
                                                           const T *__restrict__ b, T *__restrict__ u) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, a);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) {
-        const int e = rp[row + 1];
-        acc = row_dot<TPR>(lane, rp[row], e, col, a, JacB<T>{jac, b});
-    }
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, a, JacB<T>{jac, b});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) {
         const T u1 = jac[row] * b[row];
@@ -238,11 +234,13 @@ __global__ void __launch_bounds__(kBlock) k_cheb_step(int n, const int *__restri
                                                       const T *__restrict__ b, const T *__restrict__ uin,
                                                       T *__restrict__ uout, T *__restrict__ d, T cd, T cr,
                                                       int first) {
-    pdl_wait_and_release();
     const int g = blockIdx.x * kBlock + threadIdx.x;
     const int row = g / TPR, lane = g % TPR;
+    RowBatch<T> rb;   // matrix loads ahead of the wait (constant during a solve)
+    row_prefetch<TPR>(rb, row < n, lane, rp, row, col, a);
+    pdl_wait_and_release();
     T acc = T(0);
-    if (row < n) acc = row_dot<TPR>(lane, rp[row], rp[row + 1], col, a, Gather<T>{uin});
+    if (row < n) acc = row_dot_pref<TPR>(rb, col, a, Gather<T>{uin});
     acc = group_sum<TPR>(acc);
     if (row < n && lane == 0) {
         const T dr = cr * (dinv[row] * (b[row] - acc));
@@ -1642,6 +1640,9 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
     }
     (void)n_rows;
     CKL("assemble pseudo-inverse");
+    // the solve kernels fetch matrix values ahead of their grid-dependency
+    // wait: finish writing them before any of those kernels is launched
+    CK(cudaStreamSynchronize(s));
     c->have_q = true;
     c->smoother = AMG_SMOOTHER_GNN;
     return AMG_OK;

@@ -73,6 +73,62 @@ __device__ __forceinline__ T row_dot(int lane, int p0, int e, const int *__restr
     return acc;
 }
 
+// The first batch of a row-group lane's entries (row bounds, columns and
+// values), fetched before griddepcontrol.wait: matrices do not change while
+// a V-cycle runs, so these loads overlap the previous kernel and only the
+// gathers of the vector it produced remain after the wait.
+template <class T> struct RowBatch {
+    int base = 0, e = 0;
+    int c[4] = {0, 0, 0, 0};
+    T v[4] = {T(0), T(0), T(0), T(0)};
+};
+
+template <int TPR, class T>
+__device__ __forceinline__ void row_prefetch(RowBatch<T> &rb, bool live, int lane, const int *__restrict__ rp,
+                                             int row, const int *__restrict__ col, const T *__restrict__ val) {
+    if (!live) return;
+    const int p0 = __ldg(rp + row);
+    rb.e = __ldg(rp + row + 1);
+    rb.base = p0 + lane;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int p = rb.base + j * TPR;
+        rb.c[j] = p < rb.e ? __ldg(col + p) : 0;
+        rb.v[j] = p < rb.e ? __ldg(val + p) : T(0);
+    }
+}
+
+// row_dot with the first batch taken from a RowBatch (same entries, same order).
+template <int TPR, class T, class X>
+__device__ __forceinline__ T row_dot_pref(const RowBatch<T> &rb, const int *__restrict__ col,
+                                          const T *__restrict__ val, const X &xg) {
+    T acc = T(0);
+    if (rb.base >= rb.e) return acc;
+    T x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = (rb.base + j * TPR < rb.e) ? xg(rb.c[j]) : T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (rb.base + j * TPR < rb.e) acc += rb.v[j] * x[j];
+    for (int base = rb.base + 4 * TPR; base < rb.e; base += 4 * TPR) {
+        int c[4];
+        T v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int p = base + j * TPR;
+            c[j] = p < rb.e ? __ldg(col + p) : 0;
+            v[j] = p < rb.e ? __ldg(val + p) : T(0);
+        }
+        T y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = (base + j * TPR < rb.e) ? xg(c[j]) : T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (base + j * TPR < rb.e) acc += v[j] * y[j];
+    }
+    return acc;
+}
+
 template <class T> struct Gather {
     const T *__restrict__ x;
     __device__ __forceinline__ T operator()(int j) const { return x[j]; }
