@@ -936,19 +936,24 @@ template <class T>
 __global__ void __launch_bounds__(32) k_coarse_warp(int n, const double *__restrict__ Linv,
                                                     const double *__restrict__ LinvT, const T *__restrict__ b,
                                                     T *__restrict__ u) {
-    pdl_wait_and_release();
-    __shared__ double sb[32], sy[32];
+    __shared__ double sb[32], sy[32], sL[32 * 33], sLT[32 * 33];
     const int i = threadIdx.x;
+    // the factors are constant: stage them before the grid-dependency wait
+    for (int e = i; e < n * n; e += 32) {
+        sL[(e / n) * 33 + e % n] = Linv[e];
+        sLT[(e / n) * 33 + e % n] = LinvT[e];
+    }
+    pdl_wait_and_release();
     if (i < n) sb[i] = static_cast<double>(b[i]);
     __syncwarp();
     double y = 0.0;
     if (i < n)
-        for (int k = 0; k <= i; ++k) y = fma(Linv[i * n + k], sb[k], y);
+        for (int k = 0; k <= i; ++k) y = fma(sL[i * 33 + k], sb[k], y);
     if (i < n) sy[i] = y;
     __syncwarp();
     double x = 0.0;
     if (i < n)
-        for (int k = i; k < n; ++k) x = fma(LinvT[i * n + k], sy[k], x);
+        for (int k = i; k < n; ++k) x = fma(sLT[i * 33 + k], sy[k], x);
     if (i < n) u[i] = static_cast<T>(x);
 }
 
