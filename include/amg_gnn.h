@@ -316,6 +316,18 @@ int amg_residual_norm_noalloc(int n, long long nnz, const int *d_row_ptr, const 
                               const double *d_val, const double *d_b, const double *d_x, double *d_r,
                               double *d_out, void *stream);
 
+/* Self-test of the tensor-core node linear (no counterpart in the paper):
+ * runs the GCIN layer kernel once on 128 nodes of an identity graph, so that
+ * y = round_bf16(x) round_bf16(W) + bias with FP32 accumulation (x: 128 x 64,
+ * W: 64 x 64 [in][out], bias: 64, y and h: 128 x 64, host, row-major; h
+ * receives the BF16-rounded x).  no_commit != 0 issues no MMA, so the
+ * kernel's bounded mbarrier wait runs out: *flag becomes 1, the kernel frees
+ * its tensor memory and returns, and the context stays usable (about 0.2 s).
+ * Allocates and frees its own device buffers; synchronises the device.
+ * Errors: AMG_ERR_ARG, AMG_ERR_CUDA. */
+int gcin_tc_selftest(int device, int no_commit, const float *x, const float *W, const float *bias, float *y,
+                     float *h, int *flag);
+
 /* ------------------------------------------------------------------------
  * Training (Sec. 3.3, Algorithm 1, Table train_hyper)
  * ------------------------------------------------------------------------ */

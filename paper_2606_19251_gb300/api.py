@@ -110,6 +110,7 @@ def _declare(L):
         "gcin_trainer_adam_step": (I, [P, D, D]),
         "amg_loss_grad": (I, [P, pd, pd, I, pd, pd]),
         "amg_kernel_launch": (I, [P, I, I, I, P, pd]),
+        "gcin_tc_selftest": (I, [I, I, pf, pf, pf, pf, pf, C.POINTER(C.c_int)]),
         "amg_set_chebyshev": (I, [P, I]),
         "amg_get_chebyshev": (I, [P, I, pd, pd, pd]),
         "amg_vcycle_bytes": (I, [P, pd]),
@@ -133,7 +134,7 @@ def exported_symbols():
             "amg_judge", "amg_reroute", "amg_last_solve_rerouted", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
             "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
             "gcin_trainer_adam_step", "amg_loss_grad", "amg_kernel_launch", "amg_vcycle_bytes",
-            "amg_launch_count", "amg_residual_norm_noalloc", "amg_set_chebyshev", "amg_get_chebyshev"]
+            "amg_launch_count", "amg_residual_norm_noalloc", "amg_set_chebyshev", "amg_get_chebyshev", "gcin_tc_selftest"]
 
 
 # ---------------------------------------------------------------------------
@@ -342,6 +343,22 @@ def amg_loss_grad(ctx, c, f, n_vc=1):
 
 
 AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE, AMG_K_MASWEEP = range(8)
+
+
+def gcin_tc_selftest(x, W, bias, no_commit=False, device=0):
+    """(y, h, flag) of one tensor-core GCIN layer on an identity graph."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    W = np.ascontiguousarray(W, dtype=np.float32)
+    bias = np.ascontiguousarray(bias, dtype=np.float32)
+    assert x.shape == (128, 64) and W.shape == (64, 64) and bias.shape == (64,)
+    y = np.zeros((128, 64), dtype=np.float32)
+    h = np.zeros((128, 64), dtype=np.float32)
+    flag = C.c_int(-1)
+    rc = lib().gcin_tc_selftest(int(device), 1 if no_commit else 0, _fptr(x), _fptr(W), _fptr(bias), _fptr(y),
+                                _fptr(h), C.byref(flag))
+    if rc != AMG_OK:
+        raise AmgError(rc, "gcin_tc_selftest failed")
+    return y, h, flag.value
 
 
 def amg_set_chebyshev(ctx, degree=3):

@@ -623,7 +623,7 @@ void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
         } else if (b.bf16) {
             k_agg_lin_tc<<<(NT + 1) / 2, kBlock, kTcSmem, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
                                                                th + kPL.convB[l], b.tstart, NT, b.h[l], b.y[l],
-                                                               b.tmean, b.tm2, b.err); AMG_COUNT();
+                                                               b.tmean, b.tm2, b.err, 0); AMG_COUNT();
         } else {
             k_agg_lin_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
                                                  th + kPL.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
@@ -1135,6 +1135,53 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
     }
     if (c_out) std::copy(cf.begin(), cf.end(), c_out);
     return AMG_OK;
+}
+
+int gcin_tc_selftest(int device, int no_commit, const float *x, const float *W, const float *bias, float *y,
+                     float *h, int *flag) {
+    if (!x || !W || !bias || !y || !h || !flag) return AMG_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return AMG_ERR_CUDA;
+    gcin_prepare_device();
+    constexpr int n = kTcRows;
+    // identity graph (h = x), two 64-node tiles
+    std::vector<int> rp(n + 1), col(n), tstart = {0, kTile, 2 * kTile};
+    std::vector<float> w(n, 1.0f);
+    for (int i = 0; i <= n; ++i) rp[i] = i;
+    for (int i = 0; i < n; ++i) col[i] = i;
+    char *mem = nullptr;
+    Planner pl;
+    auto lay = [&](Planner &P) {
+        struct L { int *rp, *col, *ts, *err; float *w, *x, *W, *b, *h, *y, *tm, *t2; } l{};
+        l.rp = P.take<int>(n + 1); l.col = P.take<int>(n); l.ts = P.take<int>(3); l.err = P.take<int>(4);
+        l.w = P.take<float>(n); l.x = P.take<float>(n * kHidden); l.W = P.take<float>(kHidden * kHidden);
+        l.b = P.take<float>(kHidden); l.h = P.take<float>(n * kHidden); l.y = P.take<float>(n * kHidden);
+        l.tm = P.take<float>(2 * kHidden); l.t2 = P.take<float>(2 * kHidden);
+        return l;
+    };
+    lay(pl);
+    if (cudaMalloc(&mem, pl.off) != cudaSuccess) return AMG_ERR_CUDA;
+    Planner p2;
+    p2.base = mem;
+    auto L = lay(p2);
+    cudaError_t e = cudaMemset(mem, 0, p2.off);
+    if (e == cudaSuccess) e = cudaMemcpy(L.rp, rp.data(), sizeof(int) * rp.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.ts, tstart.data(), sizeof(int) * 3, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.w, w.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.x, x, sizeof(float) * n * kHidden, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.W, W, sizeof(float) * kHidden * kHidden, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.b, bias, sizeof(float) * kHidden, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_agg_lin_tc<<<1, kBlock, kTcSmem>>>(L.rp, L.col, L.w, L.x, L.W, L.b, L.ts, 2, L.h, L.y, L.tm, L.t2, L.err,
+                                             no_commit ? 1 : 0); AMG_COUNT();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(y, L.y, sizeof(float) * n * kHidden, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h, L.h, sizeof(float) * n * kHidden, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(flag, L.err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    return e == cudaSuccess ? AMG_OK : AMG_ERR_CUDA;
 }
 
 int gcin_trainer_create(gcin_trainer **out, int device, int precision, const float *theta0) {

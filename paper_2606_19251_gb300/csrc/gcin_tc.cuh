@@ -12,7 +12,8 @@
 //   3. warps 0..3 read their 32 TMEM lanes (rows) with tcgen05.ld, add the
 //      bias, and the CTA writes y and the two tiles' mean / M2 statistics.
 // The mbarrier wait is bounded; on timeout the kernel raises an error flag,
-// waits (bounded) once more, frees its TMEM columns and returns.
+// waits (bounded) once more, frees its TMEM columns and returns
+// (gcin_tc_selftest exercises that path with no_commit).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
                                                        const int *__restrict__ tstart, int NT,
                                                        float *__restrict__ hout, float *__restrict__ y,
                                                        float *__restrict__ tmean, float *__restrict__ tm2,
-                                                       int *__restrict__ err) {
+                                                       int *__restrict__ err, int no_commit) {
     extern __shared__ __align__(128) unsigned char tc_smem[];
     unsigned char *sA = tc_smem, *sB = tc_smem + kTcA;
     // y is staged over the A / B tiles once the MMAs that read them have completed
@@ -122,7 +123,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = s_taddr;
-    if (threadIdx.x == 0) {
+    // no_commit (self-test only) issues nothing, so the bounded wait below runs out
+    if (threadIdx.x == 0 && !no_commit) {
         for (int ks = 0; ks < kHidden / 16; ++ks) {
             const uint64_t ad = tc_desc(a_addr + ks * 256), bd = tc_desc(b_addr + ks * 256);
             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"

@@ -284,3 +284,15 @@ def test_chebyshev_vcycle_converges_and_is_symmetric():
     n = A.n_rows
     x, y = W.rhs_uniform(7, n), W.rhs_uniform(8, n)
     assert abs(x @ O.vcycle_operator_apply(h, y) - y @ O.vcycle_operator_apply(h, x)) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
+
+
+def test_poisson7_closed_form_spectrum():
+    """The 3D 7-point Laplacian: eigenvalues sum_d (2 - 2 cos(k_d pi/(m+1)))."""
+    m = 6
+    ev = np.sort(np.linalg.eigvalsh(W.poisson7(m).to_dense()))
+    k = np.arange(1, m + 1)
+    lam1 = 2 - 2 * np.cos(k * np.pi / (m + 1))
+    ref = np.sort((lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :]).ravel())
+    np.testing.assert_allclose(ev, ref, rtol=1e-12, atol=1e-12)
+    B = W.poisson7(8, body_ratio=1e-2).to_dense()
+    assert np.allclose(B, B.T) and np.linalg.eigvalsh(B).min() > 0

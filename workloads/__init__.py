@@ -114,6 +114,42 @@ def poisson5(m: int) -> CSR:
     return _coo_to_csr(n, n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
+def poisson7(m: int, body_ratio: float = 1.0, radius: float = 0.2) -> CSR:
+    """7-point finite-volume Laplacian on an m x m x m interior grid of the unit
+    cube, Dirichlet eliminated (a Cartesian 3D stand-in).  Cells inside a
+    centred sphere of the given radius carry conductivity body_ratio (1 = the
+    plain Laplacian; small values mimic an immersed solid); face coefficients
+    are harmonic means of the two cells, boundary faces use the cell's own."""
+    n = m ** 3
+    h = 1.0 / (m + 1)
+    g = (np.arange(m) + 1) * h
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    cond = np.where((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2 < radius ** 2, body_ratio, 1.0)
+    idx = np.arange(n).reshape(m, m, m)
+    rows, cols, vals = [], [], []
+    diag = np.zeros((m, m, m))
+    for axis in range(3):
+        for side in (-1, 1):
+            nb = np.roll(cond, -side, axis=axis)
+            face = 2.0 * cond * nb / (cond + nb)
+            edge = [slice(None)] * 3
+            edge[axis] = slice(m - 1, m) if side == 1 else slice(0, 1)
+            face[tuple(edge)] = cond[tuple(edge)]          # Dirichlet face
+            diag += face
+            inner = [slice(None)] * 3
+            inner[axis] = slice(0, m - 1) if side == 1 else slice(1, m)
+            inner = tuple(inner)
+            src = idx[inner].ravel()
+            dst = np.roll(idx, -side, axis=axis)[inner].ravel()
+            rows.append(src)
+            cols.append(dst)
+            vals.append(-face[inner].ravel())
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    return _coo_to_csr(n, n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
 def _coo_to_csr(nr, nc, r, c, v) -> CSR:
     order = np.lexsort((c, r))
     r, c, v = r[order], c[order], v[order]
