@@ -36,6 +36,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "time-to-1e-8 residual, GNN-poly vs Jacobi AMG on GB300; V-cycle HBM GB/s"
 WEIGHTS = os.path.join(ROOT, "paper_2606_19251_gb300", "weights", "gcin_c3.npy")
+# trained on the C3 batch plus 16 band meshes with aspect ratios up to 1000 and 16
+# small airfoil meshes: the parameters for the anisotropic and airfoil workloads
+WEIGHTS_WIDE = os.path.join(ROOT, "paper_2606_19251_gb300", "weights", "gcin_wide.npy")
 TOL = 1e-8
 
 
@@ -45,19 +48,20 @@ def workload(name):
                     points=50_000)
     if name == "c4":
         return dict(workload="band-delaunay-fv-2.5M", matrix=lambda: W.c4_matrix(0), rhs=W.rhs_zero_mean,
-                    points=2_500_000)
+                    points=2_500_000, wide=True)
     if name == "c5":
         return dict(workload="naca-airfoil-sequence-254k", matrix=lambda: W.c5_problem(0, n_rhs=1)[0],
-                    rhs=W.rhs_zero_mean, points=254_227, sequence=True)
+                    rhs=W.rhs_zero_mean, points=254_227, sequence=True, wide=True)
     if name.startswith("grid"):
         m = int(name[4:])
         return dict(workload=f"5point-grid-{m}x{m}", matrix=lambda: W.poisson5(m), rhs=W.rhs_uniform, points=m * m)
     raise SystemExit(f"unknown workload {name}")
 
 
-def load_theta():
-    if os.path.exists(WEIGHTS):
-        return np.load(WEIGHTS).astype(np.float64), "trained"
+def load_theta(wide=False):
+    path = WEIGHTS_WIDE if wide else WEIGHTS
+    if os.path.exists(path):
+        return np.load(path).astype(np.float64), ("trained on C3 + widened meshes" if wide else "trained on C3")
     return W.gcin_init_params(0), "untrained-init"
 
 
@@ -139,7 +143,7 @@ def oracle_setup(wl):
 def run_reference(args, wl):
     import torch
     A, levels = oracle_setup(wl)
-    theta, tag = load_theta()
+    theta, tag = load_theta(wl.get("wide", False))
     times, cycles = [], []
     for k in range(args.warmup + args.steps):
         ms, res = oracle_step(levels, theta, A, wl["rhs"](1000 + k, A.n_rows))
@@ -193,7 +197,7 @@ def run_sequence(args, wl, rank, world):
     torch.cuda.set_device(dev)
     A, fs, m = W.c5_problem(0)
     n = A.n_rows
-    theta, tag = load_theta()
+    theta, tag = load_theta(wl.get("wide", False))
     stream = torch.cuda.current_stream()
     f_dev = [torch.tensor(f, device=f"cuda:{dev}") for f in fs]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
@@ -258,7 +262,7 @@ def run_gpu(args, wl, rank, world):
     ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev)
     P.amg_setup(ctx, A)
     setup_ms = (time.perf_counter() - t0) * 1e3
-    theta, tag = load_theta()
+    theta, tag = load_theta(wl.get("wide", False))
     P.gnn_load_params(ctx, theta)
     nlev = P.amg_num_levels(ctx)
     K, Wm = args.steps, args.warmup

@@ -9,6 +9,13 @@ distribution (seed 1).  Algorithm 1 with the multi-V-cycle loss (N_vc = 3 by def
 libamggnn.so.
 
     python -m paper_2606_19251_gb300.weights.make_weights [--epochs 150]
+
+gcin_wide.npy (the parameters used for the anisotropic band and airfoil
+workloads) comes from the same run with the distribution widened by 16 band
+meshes of aspect ratio up to 1000 and 16 small airfoil meshes:
+
+    python -m paper_2606_19251_gb300.weights.make_weights --extra-band1000 16 --extra-airfoil 16 \
+        --out paper_2606_19251_gb300/weights/gcin_wide.npy
 """
 import argparse
 import json
@@ -31,6 +38,10 @@ def main():
     ap.add_argument("--meshes", type=int, default=64)
     ap.add_argument("--nvc", type=int, default=3, help="V-cycles per loss (Sec. 3.3 multi-V-cycle loss)")
     ap.add_argument("--val-cycles", type=int, default=10)
+    ap.add_argument("--extra-band1000", type=int, default=0,
+                    help="add this many graded + band meshes with aspect ratios up to 1000")
+    ap.add_argument("--extra-airfoil", type=int, default=0,
+                    help="add this many small airfoil meshes (wall layers from 1e-5 chords)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="arithmetic of the forward node linears during training")
     ap.add_argument("--out", default=os.path.join(HERE, "gcin_c3.npy"))
@@ -42,6 +53,12 @@ def main():
     t0 = time.time()
     mats = W.c3_batch(args.meshes, seed=0)
     val = W.c3_batch(8, seed=1)
+    # optional widening of the training distribution (not part of the C3 batch)
+    for k in range(args.extra_band1000):
+        n = int(2000 + 18000 * W.uniform01(7000 + k, 1)[0])
+        mats.append(W.fv_mesh("band", n, 7000 + k, max_aspect=1000.0)[0])
+    for k in range(args.extra_airfoil):
+        mats.append(W.c5_problem(8000 + k, n_rhs=1, n_surface=160, n_far=4000 + 500 * k)[0])
     print(f"meshes ready in {time.time() - t0:.1f}s: n = {[m.n_rows for m in mats[:8]]}...", flush=True)
     theta0 = W.gcin_init_params(0)
     from paper_2606_19251_gb300 import api as P
@@ -51,6 +68,7 @@ def main():
     np.save(args.out, np.asarray(best, dtype=np.float32))
     with open(os.path.splitext(args.out)[0] + "_log.json", "w") as f:
         json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "n_vc": args.nvc,
+                   "extra_band1000": args.extra_band1000, "extra_airfoil": args.extra_airfoil,
                    "precision": args.precision,
                    "val_cycles": args.val_cycles, "rows": rows,
                    "seconds": time.time() - t0}, f, indent=1)

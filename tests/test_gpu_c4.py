@@ -19,6 +19,8 @@ from oracle import solve as O
 
 pytestmark = pytest.mark.gpu
 
+WEIGHTS_WIDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2606_19251_gb300",
+                            "weights", "gcin_wide.npy")
 WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2606_19251_gb300",
                        "weights", "gcin_c3.npy")
 
@@ -104,3 +106,26 @@ def test_c4_trained_gcin_vs_jacobi_to_1e8(c4):
     elif sm != P.AMG_SMOOTHER_GNN:
         assert metric >= 0 and len(h_g) == len(h_j), diag
     print(diag)
+
+
+def test_c4_widened_gcin_beats_jacobi_to_1e8(c4):
+    """The network trained on the C3 batch plus band meshes of aspect ratio up
+    to 1000 and small airfoils generalises to the 2.5M-node mesh: the judge
+    keeps it and it needs clearly fewer V-cycles than Jacobi."""
+    A, ctx = c4
+    b = W.rhs_zero_mean(3, A.n_rows)
+    P.amg_set_jacobi(ctx)
+    st_j, x_j, h_j = P.amg_solve(ctx, b)
+    P.gnn_load_params(ctx, np.load(WEIGHTS_WIDE))
+    P.gnn_predict_coeffs(ctx)
+    metric, sm = P.amg_reroute(ctx, W.rhs_uniform(8, A.n_rows), 30)
+    st_g, x_g, h_g = P.amg_solve(ctx, b)
+    P.amg_set_jacobi(ctx)
+    diag = f"jacobi {len(h_j) - 1} cycles; judged {metric:.3f} -> {sm}; learned {len(h_g) - 1} cycles"
+    assert st_j == st_g == P.AMG_OK, diag
+    assert sm == P.AMG_SMOOTHER_GNN and metric < 0, diag
+    assert len(h_g) < 0.9 * len(h_j), diag
+    r = b - O.mv(O.TMat.of(A), torch.from_numpy(x_g)).numpy()
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-8, diag
+    print(diag)
+

@@ -7,7 +7,8 @@ from the previous solution, with the smoother's coefficients predicted once
 Small mesh: every solve of the sequence equals the FP64 oracle's solve from
 the same warm start (same V-cycle count, x within 1e-10).  Full mesh
 (254k unknowns): every solve reaches 1e-8 (checked in FP64 by the oracle's
-matrix-vector product), and the judged smoother needs no more cycles than
+matrix-vector product), and the judged smoother (the network trained with
+the widened distribution, airfoils included) needs no more cycles than
 Jacobi over the sequence.
 """
 import os
@@ -25,7 +26,7 @@ from tests.gpu_helpers import ctx_setup, oracle_hier, rel_err
 pytestmark = pytest.mark.gpu
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2606_19251_gb300",
-                       "weights", "gcin_c3.npy")
+                       "weights", "gcin_wide.npy")
 COEFFS = [0.62, 0.03, -0.01, -0.18, 0.02]
 
 
