@@ -16,6 +16,12 @@ Readout (JK-like, Sec. 3.2 readout equations; App. A.1):
     z = sigmoid(LayerNorm_128(concat_l g^(l)))                  (eps 1e-5)
     c = Linear_{64->5}(ReLU(Linear_{128->64}(ReLU(Linear_{128->128}(z)))))
 This layout has exactly 55,045 trainable parameters (App. A.1).
+
+Hidden width H (App. B.3 halves it to 32 for structured meshes): every 64 above
+that is the GCIN width becomes H (conv and instance-norm widths, readout
+input 2H); the readout output (32 per layer), the 128-vector and the head
+are unchanged (reading).  H = 32 has 37,189 parameters.  The width is
+inferred from the length of the parameter vector.
 Readings: no activation after the readout linears, linear output on the five
 coefficients, max-pooling after the ReLU, readout over layers 1..L only.
 
@@ -40,31 +46,41 @@ from workloads import CSR
 
 DT = torch.float64
 HIDDEN = 64
+WIDTHS = (64, 32)
 N_LAYERS = 4
 EPS = 1e-5
 
 
-def param_shapes():
-    shapes = [("conv1.W", (2, HIDDEN)), ("conv1.b", (HIDDEN,))]
+def param_shapes(hidden: int = HIDDEN):
+    H = hidden
+    shapes = [("conv1.W", (2, H)), ("conv1.b", (H,))]
     for l in range(2, N_LAYERS + 1):
-        shapes += [(f"conv{l}.W", (HIDDEN, HIDDEN)), (f"conv{l}.b", (HIDDEN,))]
+        shapes += [(f"conv{l}.W", (H, H)), (f"conv{l}.b", (H,))]
     for l in range(1, N_LAYERS + 1):
-        shapes += [(f"in{l}.gamma", (HIDDEN,)), (f"in{l}.beta", (HIDDEN,))]
+        shapes += [(f"in{l}.gamma", (H,)), (f"in{l}.beta", (H,))]
     for l in range(1, N_LAYERS + 1):
-        shapes += [(f"ro{l}.W", (2 * HIDDEN, 32)), (f"ro{l}.b", (32,))]
+        shapes += [(f"ro{l}.W", (2 * H, 32)), (f"ro{l}.b", (32,))]
     shapes += [("ln.gamma", (128,)), ("ln.beta", (128,))]
     shapes += [("h1.W", (128, 128)), ("h1.b", (128,)), ("h2.W", (128, 64)), ("h2.b", (64,)),
                ("h3.W", (64, 5)), ("h3.b", (5,))]
     return shapes
 
 
-def n_params() -> int:
-    return sum(int(np.prod(s)) for _, s in param_shapes())
+def n_params(hidden: int = HIDDEN) -> int:
+    return sum(int(np.prod(s)) for _, s in param_shapes(hidden))
+
+
+def hidden_of(n: int) -> int:
+    """GCIN width of a parameter vector of length n."""
+    for H in WIDTHS:
+        if n == n_params(H):
+            return H
+    raise ValueError(f"no GCIN width has {n} parameters")
 
 
 def unpack(theta: torch.Tensor) -> dict:
     out, off = {}, 0
-    for name, shape in param_shapes():
+    for name, shape in param_shapes(hidden_of(theta.numel())):
         k = int(np.prod(shape))
         out[name] = theta[off:off + k].reshape(shape)
         off += k

@@ -18,6 +18,63 @@ from oracle import train as T
 def test_parameter_count_matches_paper():
     assert G.n_params() == 55045          # App. A.1
     assert sum(s for s, _ in W.GCIN_PARAM_SIZES) == 55045
+    # hidden 32 (App. B.3): conv 2*32+32 + 3*(32*32+32), IN 4*64, readout 4*(64*32+32),
+    # LN 256 and the unchanged head 16512 + 8256 + 325
+    assert G.n_params(32) == 96 + 3168 + 256 + 8320 + 256 + 16512 + 8256 + 325 == 37189
+    assert sum(s for s, _ in W.gcin_param_sizes(32)) == 37189
+    assert G.hidden_of(55045) == 64 and G.hidden_of(37189) == 32
+    with pytest.raises(ValueError):
+        G.hidden_of(55044)
+
+
+def _pad_to_64(theta32):
+    """Embed a hidden-32 parameter vector into the hidden-64 layout: the extra
+    channels get zero weights in and out, zero bias and zero beta (their gamma
+    is random), and the readout rows of their pooled features are random."""
+    p32 = G.unpack(torch.from_numpy(theta32))
+    rng = np.random.default_rng(7)
+    out = []
+    for name, shape in G.param_shapes(64):
+        t = np.zeros(shape)
+        src = p32[name].numpy()
+        if name.startswith("conv"):
+            t[tuple(slice(0, k) for k in src.shape)] = src
+        elif name.endswith("gamma") and name.startswith("in"):
+            t[:] = rng.uniform(0.5, 2.0, shape)
+            t[:32] = src
+        elif name.endswith("beta") and name.startswith("in"):
+            t[:32] = src
+        elif name.startswith("ro") and name.endswith(".W"):
+            t[:] = rng.standard_normal(shape)       # multiplied by exact zeros
+            t[0:32] = src[0:32]                     # mean of the 32 live channels
+            t[64:96] = src[32:64]                   # max of the 32 live channels
+        else:
+            t[:] = src
+        out.append(t.ravel())
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "band"])
+def test_hidden32_equals_zero_padded_hidden64(kind):
+    """A hidden-32 network is the hidden-64 network whose extra channels carry
+    nothing: zero weights keep them at y = 0, the instance norm maps a constant
+    channel to beta = 0 and the ReLU keeps 0, so every pooled feature of those
+    channels is 0 and their readout rows add exact zeros."""
+    A = W.fv_mesh(kind, 600, 3, max_aspect=100.0)[0]
+    levels = S.build_hierarchy(A, max_coarse=20)
+    theta32 = W.gcin_init_params(5, last_scale=1.0, hidden=32)
+    mats = [l.A for l in levels]
+    c32 = G.predict(theta32, mats)
+    c64 = G.predict(_pad_to_64(theta32), mats)
+    np.testing.assert_allclose(c32, c64, rtol=1e-12, atol=1e-13)
+    # and the BF16 evaluation agrees the same way (zeros round to zeros)
+    np.testing.assert_allclose(G.predict(theta32, mats, True), G.predict(_pad_to_64(theta32), mats, True),
+                               rtol=1e-12, atol=1e-13)
+    # the padding is not vacuous: a non-zero bias on an extra channel moves c
+    bad = _pad_to_64(theta32)
+    off = sum(int(np.prod(s)) for n, s in G.param_shapes(64)[:G.param_shapes(64).index(("in1.beta", (64,)))])
+    bad[off + 40] = 0.5
+    assert np.abs(G.predict(bad, mats) - c32).max() > 1e-6
 
 
 def _rne_bf16_bits(t):
@@ -51,11 +108,12 @@ def _library_forward(theta, A, bf16=False):
     return Fn.linear(z, p["h3.W"].T, p["h3.b"])
 
 
+@pytest.mark.parametrize("hidden", [64, 32])
 @pytest.mark.parametrize("kind", ["uniform", "band"])
-def test_forward_equals_library_layers(kind):
+def test_forward_equals_library_layers(kind, hidden):
     A = W.fv_mesh(kind, 600, 3, max_aspect=100.0)[0]
     levels = S.build_hierarchy(A, max_coarse=20)
-    theta = W.gcin_init_params(1, last_scale=1.0)
+    theta = W.gcin_init_params(1, last_scale=1.0, hidden=hidden)
     c = G.predict(theta, [l.A for l in levels])
     for k, lv in enumerate(levels):
         ref = _library_forward(theta, lv.A).numpy()
@@ -136,12 +194,13 @@ def test_coefficient_gradient_matches_finite_differences():
     assert np.all(dc[-1] == 0)   # the coarsest level has no smoother
 
 
-def test_network_gradient_matches_finite_differences():
+@pytest.mark.parametrize("hidden", [64, 32])
+def test_network_gradient_matches_finite_differences(hidden):
     probs = [_small_problem(s) for s in (0, 2)]
     hs = [p[1] for p in probs]
     gs = [[G.Graph(l.A) for l in p[0]] for p in probs]
     fs = [p[2] for p in probs]
-    theta = W.gcin_init_params(4)
+    theta = W.gcin_init_params(4, hidden=hidden)
     L, g = T.batch_loss_and_grad(theta, hs, gs, fs)
     rng = np.random.default_rng(0)
     for _ in range(4):

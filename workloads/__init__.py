@@ -39,7 +39,7 @@ import numpy as np
 __all__ = [
     "CSR", "splitmix64", "uniform01", "uniform_pm1", "poisson5", "fv_mesh",
     "rhs_uniform", "rhs_zero_mean", "gcin_init_params", "c2_matrix",
-    "c3_batch", "c4_matrix", "GCIN_PARAM_SIZES",
+    "c3_batch", "c4_matrix", "GCIN_PARAM_SIZES", "gcin_param_sizes",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -438,29 +438,34 @@ def rhs_zero_mean(seed: int, n: int) -> np.ndarray:
 # random initial network parameters
 # ----------------------------------------------------------------------------
 # (size, fan_in) of each parameter tensor in flat order.  The order is the
-# parameter-vector interface of the coefficient network: conv linears
-# (weight [in][out] then bias) for 4 layers, instance-norm affine (gamma, beta)
-# for 4 layers, per-layer readout linears 128->32, layer norm (gamma, beta),
-# head linears 128->128, 128->64, 64->5.  fan_in = 0 marks gamma (init 1) and
-# -1 marks beta (init 0).
-GCIN_PARAM_SIZES = (
-    [(2 * 64, 2), (64, 2)]
-    + [(64 * 64, 64), (64, 64)] * 3
-    + [(64, 0), (64, -1)] * 4
-    + [(128 * 32, 128), (32, 128)] * 4
-    + [(128, 0), (128, -1)]
-    + [(128 * 128, 128), (128, 128), (128 * 64, 128), (64, 128), (64 * 5, 64), (5, 64)]
-)
+# parameter-vector interface of the coefficient network of GCIN width H
+# (64, or 32 for the cheaper network): conv linears (weight [in][out] then
+# bias) for 4 layers, instance-norm affine (gamma, beta) for 4 layers,
+# per-layer readout linears 2H->32, layer norm (gamma, beta), head linears
+# 128->128, 128->64, 64->5.  fan_in = 0 marks gamma (init 1) and -1 marks
+# beta (init 0).
+def gcin_param_sizes(hidden: int = 64):
+    H = hidden
+    return ([(2 * H, 2), (H, 2)]
+            + [(H * H, H), (H, H)] * 3
+            + [(H, 0), (H, -1)] * 4
+            + [(2 * H * 32, 2 * H), (32, 2 * H)] * 4
+            + [(128, 0), (128, -1)]
+            + [(128 * 128, 128), (128, 128), (128 * 64, 128), (64, 128), (64 * 5, 64), (5, 64)])
 
 
-def gcin_init_params(seed: int, last_bias=(2.0 / 3.0, 0.0, 0.0, 0.0, 0.0), last_scale: float = 0.1) -> np.ndarray:
+GCIN_PARAM_SIZES = gcin_param_sizes(64)
+
+
+def gcin_init_params(seed: int, last_bias=(2.0 / 3.0, 0.0, 0.0, 0.0, 0.0), last_scale: float = 0.1,
+                     hidden: int = 64) -> np.ndarray:
     """Flat float64 parameter vector: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights.
 
     The last layer's weights are scaled by ``last_scale`` and its bias set to
     ``last_bias`` so that an untrained network starts near weighted Jacobi.
     """
     parts = []
-    for t, (size, fan_in) in enumerate(GCIN_PARAM_SIZES):
+    for t, (size, fan_in) in enumerate(gcin_param_sizes(hidden)):
         if fan_in == 0:
             parts.append(np.ones(size))
         elif fan_in == -1:
