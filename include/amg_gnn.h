@@ -54,7 +54,8 @@ extern "C" {
 #define AMG_GNN_FP32 0   /* FP32 CUDA-core FMAs                                  */
 #define AMG_GNN_BF16 1   /* tcgen05 tensor cores: BF16 operands, FP32 accumulation */
 
-#define AMG_GCIN_NUM_PARAMS 55045   /* App. A.1 */
+#define AMG_GCIN_NUM_PARAMS 55045       /* App. A.1: GCIN width 64 */
+#define AMG_GCIN_NUM_PARAMS_H32 37189   /* App. B.3: the halved GCIN width 32 */
 
 typedef struct amg_ctx amg_ctx;
 
@@ -167,11 +168,13 @@ int amg_get_smoother(const amg_ctx *ctx, int level, double *q_out);
  * Coefficient network (Sec. 3.2, App. A.1; Algorithm 1 steps 3-6)
  * ------------------------------------------------------------------------ */
 
-/* Load the GCIN parameters: n == AMG_GCIN_NUM_PARAMS floats in the flat
- * order conv1 W(2x64) b(64); conv2..4 W(64x64) b(64); IN1..4 gamma(64)
- * beta(64); readout1..4 W(128x32) b(32); LN gamma(128) beta(128); head
- * W(128x128) b(128), W(128x64) b(64), W(64x5) b(5); weights [in][out]
- * row-major.  Errors: AMG_ERR_ARG (wrong n), AMG_ERR_CUDA. */
+/* Load the GCIN parameters (copied to the device): n floats in the flat
+ * order conv1 W(2xH) b(H); conv2..4 W(HxH) b(H); IN1..4 gamma(H) beta(H);
+ * readout1..4 W(2Hx32) b(32); LN gamma(128) beta(128); head W(128x128)
+ * b(128), W(128x64) b(64), W(64x5) b(5); weights [in][out] row-major.  The
+ * GCIN width H follows from n: AMG_GCIN_NUM_PARAMS -> H = 64 (App. A.1),
+ * AMG_GCIN_NUM_PARAMS_H32 -> H = 32 (App. B.3).  Errors: AMG_ERR_ARG (any
+ * other n, or theta NULL), AMG_ERR_CUDA. */
 int gnn_load_params(amg_ctx *ctx, const float *theta, long long n);
 
 /* Batched GCIN inference over every level graph of the loaded hierarchy
@@ -337,8 +340,11 @@ typedef struct gcin_trainer gcin_trainer;
 /* Trainer owning the parameters, their gradient and Adam moments on
  * `device`; precision AMG_GNN_FP32 or AMG_GNN_BF16 selects the arithmetic of
  * the forward node linears (the backward runs in FP32 on the same rounded
- * operands).  theta0: AMG_GCIN_NUM_PARAMS floats (copied). */
-int gcin_trainer_create(gcin_trainer **tr, int device, int precision, const float *theta0);
+ * operands).  theta0: n_params floats (copied); n_params is
+ * AMG_GCIN_NUM_PARAMS (width 64) or AMG_GCIN_NUM_PARAMS_H32 (width 32), and
+ * gcin_trainer_get_params / gcin_trainer_backward return that many values.
+ * Errors: AMG_ERR_ARG (NULL pointer, precision or n_params), AMG_ERR_CUDA. */
+int gcin_trainer_create(gcin_trainer **tr, int device, int precision, const float *theta0, long long n_params);
 void gcin_trainer_destroy(gcin_trainer *tr);
 const char *gcin_trainer_last_error(const gcin_trainer *tr);
 int gcin_trainer_get_params(const gcin_trainer *tr, float *theta_out);

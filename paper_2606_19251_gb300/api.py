@@ -36,7 +36,8 @@ AMG_OUTER_REFINE = 0
 AMG_OUTER_PCG = 1
 AMG_GNN_FP32 = 0
 AMG_GNN_BF16 = 1
-AMG_GCIN_NUM_PARAMS = 55045
+AMG_GCIN_NUM_PARAMS = 55045        # GCIN width 64 (App. A.1)
+AMG_GCIN_NUM_PARAMS_H32 = 37189    # GCIN width 32 (App. B.3)
 
 SOLVE_STATUSES = (AMG_OK, AMG_ERR_DIVERGED, AMG_ERR_STAGNATED, AMG_ERR_MAXITER)
 
@@ -101,7 +102,7 @@ def _declare(L):
         "amg_judge": (I, [P, pd, I, pd]),
         "amg_reroute": (I, [P, pd, I, pd, pi]),
         "amg_last_solve_rerouted": (I, [P]),
-        "gcin_trainer_create": (I, [C.POINTER(P), I, I, pf]),
+        "gcin_trainer_create": (I, [C.POINTER(P), I, I, pf, C.c_longlong]),
         "gcin_trainer_destroy": (V, [P]),
         "gcin_trainer_last_error": (C.c_char_p, [P]),
         "gcin_trainer_get_params": (I, [P, pf]),
@@ -415,12 +416,13 @@ def _tcheck(tr, rc):
 
 def gcin_trainer_create(theta0, device=0, precision=AMG_GNN_BF16):
     t = np.ascontiguousarray(np.asarray(theta0, dtype=np.float32))
-    if t.size != AMG_GCIN_NUM_PARAMS:
-        raise ValueError("theta0 must have 55045 entries")
+    if t.size not in (AMG_GCIN_NUM_PARAMS, AMG_GCIN_NUM_PARAMS_H32):
+        raise ValueError("theta0 must have 55045 (width 64) or 37189 (width 32) entries")
     h = C.c_void_p()
-    rc = lib().gcin_trainer_create(C.byref(h), int(device), int(precision), _fptr(t))
+    rc = lib().gcin_trainer_create(C.byref(h), int(device), int(precision), _fptr(t), t.size)
     if rc != AMG_OK:
         raise AmgError(rc, "gcin_trainer_create failed")
+    h.n_params = t.size
     return h
 
 
@@ -433,7 +435,7 @@ def gcin_trainer_last_error(tr) -> str:
 
 
 def gcin_trainer_get_params(tr) -> np.ndarray:
-    t = np.zeros(AMG_GCIN_NUM_PARAMS, np.float32)
+    t = np.zeros(tr.n_params, np.float32)
     _tcheck(tr, lib().gcin_trainer_get_params(tr, _fptr(t)))
     return t
 
@@ -448,7 +450,7 @@ def gcin_trainer_forward(tr, ctxs) -> np.ndarray:
 
 def gcin_trainer_backward(tr, dc) -> np.ndarray:
     dc = np.ascontiguousarray(np.asarray(dc, dtype=np.float64))
-    g = np.zeros(AMG_GCIN_NUM_PARAMS)
+    g = np.zeros(tr.n_params)
     _tcheck(tr, lib().gcin_trainer_backward(tr, _dptr(dc), _dptr(g)))
     return g
 

@@ -31,7 +31,11 @@
 namespace amg {
 
 constexpr float kEps = 1e-5f;
-__constant__ ParamLayout kPLd = make_layout();   // device copy of the parameter offsets
+__constant__ ParamLayout kPLd[2] = {make_layout(kHidden), make_layout(kHidden32)};   // device copies of the offsets
+template <int H>
+__device__ __forceinline__ const ParamLayout &PL() { return kPLd[H == kHidden ? 0 : 1]; }
+template <int H>
+__host__ __device__ constexpr int num_params() { return make_layout(H).total; }
 
 // ---------------------------------------------------------------------------
 // batch construction
@@ -217,20 +221,28 @@ __global__ void k_feat0(int N, const int *__restrict__ rp, const int *__restrict
     x0[2 * i + 1] = static_cast<double>(deg);
 }
 
-// mean and M2 (sum of squared deviations) per feature of the tile's y rows
-__device__ __forceinline__ void tile_stats(const float (*sY)[kHidden + 1], int nn, float *tmean, float *tm2) {
-    __shared__ float red[4][kHidden];
-    __shared__ float smean[kHidden];
-    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+// mean and M2 (sum of squared deviations) per feature of the tile's y rows;
+// the block's threads form kBlock / H groups of H (one thread per feature)
+template <int H>
+__device__ __forceinline__ void tile_stats(const float (*sY)[H + 1], int nn, float *tmean, float *tm2) {
+    constexpr int Q = kBlock / H;
+    __shared__ float red[Q][H];
+    __shared__ float smean[H];
+    const int f = threadIdx.x % H, q = threadIdx.x / H;
     float s = 0.f;
-    for (int k = q; k < nn; k += 4) s += sY[k][f];
+    for (int k = q; k < nn; k += Q) s += sY[k][f];
     red[q][f] = s;
     __syncthreads();
-    if (q == 0) smean[f] = (red[0][f] + red[1][f] + red[2][f] + red[3][f]) / nn;
+    if (q == 0) {
+        float t = red[0][f];
+#pragma unroll
+        for (int j = 1; j < Q; ++j) t += red[j][f];
+        smean[f] = t / nn;
+    }
     __syncthreads();
     const float m = smean[f];
     float v = 0.f;
-    for (int k = q; k < nn; k += 4) {
+    for (int k = q; k < nn; k += Q) {
         const float d = sY[k][f] - m;
         v = fmaf(d, d, v);
     }
@@ -238,20 +250,24 @@ __device__ __forceinline__ void tile_stats(const float (*sY)[kHidden + 1], int n
     red[q][f] = v;
     __syncthreads();
     if (q == 0) {
+        float t = red[0][f];
+#pragma unroll
+        for (int j = 1; j < Q; ++j) t += red[j][f];
         tmean[f] = m;
-        tm2[f] = red[0][f] + red[1][f] + red[2][f] + red[3][f];
+        tm2[f] = t;
     }
 }
 
 // Layer 1: h = A_hat x0 (FP64 sums of the raw features, one thread per node,
 // entries in row order), y = h W + b (K = 2: FMA units); tile stats.
+template <int H>
 __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ rp, const int *__restrict__ col,
                                                         const double *__restrict__ w64, const double *__restrict__ x0,
                                                         const float *__restrict__ W, const float *__restrict__ bias,
                                                         const int *__restrict__ tstart, float *__restrict__ h1,
                                                         float *__restrict__ y, float *__restrict__ tmean,
                                                         float *__restrict__ tm2) {
-    __shared__ float sY[kTile][kHidden + 1];
+    __shared__ float sY[kTile][H + 1];
     __shared__ float sH[kTile][2];
     const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a;
     if (threadIdx.x < nn) {
@@ -269,46 +285,52 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
         sH[threadIdx.x][1] = hv1;
     }
     __syncthreads();
-    // 64 nodes x 64 features: thread -> node k = tid / 4, features 16 (tid % 4) .. + 15
-    const int k = threadIdx.x / 4, f0 = 16 * (threadIdx.x % 4);
+    // 64 nodes x H features: thread -> node k = tid / 4, features FT (tid % 4) .. + FT - 1
+    constexpr int FT = H / 4;
+    const int k = threadIdx.x / 4, f0 = FT * (threadIdx.x % 4);
     if (k < nn) {
         const float h0 = sH[k][0], hv1 = sH[k][1];
-        float out[16];
+        float out[FT];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < FT; ++q) {
             const int f = f0 + q;
-            out[q] = fmaf(h0, W[f], fmaf(hv1, W[kHidden + f], bias[f]));
+            out[q] = fmaf(h0, W[f], fmaf(hv1, W[H + f], bias[f]));
             sY[k][f] = out[q];
         }
-        float4 *yo = reinterpret_cast<float4 *>(y + static_cast<size_t>(a + k) * kHidden + f0);
+        float4 *yo = reinterpret_cast<float4 *>(y + static_cast<size_t>(a + k) * H + f0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) yo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+        for (int q = 0; q < FT / 4; ++q) yo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
     }
     __syncthreads();
-    tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
+    tile_stats<H>(sY, nn, tmean + static_cast<size_t>(t) * H, tm2 + static_cast<size_t>(t) * H);
 }
 
-// h_i = sum_p w_p x_{col p} for two rows per warp: half-warp h (lanes
-// 16 h .. 16 h + 15) aggregates its own row [p0, p1), lane j of the half owns
-// features 4 j .. 4 j + 3, and entries are added in row order.  Up to 16
-// (col, w) pairs per half come in with one coalesced load and are broadcast
-// by shuffles; each lane keeps four 16-byte gathers in flight, so a warp has
-// eight 256-byte feature rows in flight.  Called by a whole warp (the loop
-// runs to the longer of the two rows, the shorter half predicated off).
-__device__ __forceinline__ float4 agg_row64_pair(int p0, int p1, const int *__restrict__ col,
-                                                 const float *__restrict__ w, const float4 *__restrict__ x4, int hl) {
+// h_i = sum_p w_p x_{col p} with L = H / 4 lanes per row and 32 / L rows per
+// warp (two rows for H = 64, four for H = 32): lane j of a row's group owns
+// features 4 j .. 4 j + 3, and entries are added in row order.  Up to L
+// (col, w) pairs per row come in with one coalesced load and are broadcast by
+// shuffles; each lane keeps four 16-byte gathers in flight, so a warp has
+// eight H = 64 (or sixteen H = 32) feature rows in flight.  Called by a whole
+// warp (the loop runs to the longest row of the warp, shorter rows predicated
+// off).
+template <int H>
+__device__ __forceinline__ float4 agg_rows(int p0, int p1, const int *__restrict__ col, const float *__restrict__ w,
+                                           const float4 *__restrict__ x4, int hl) {
+    constexpr int L = H / 4;
     float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
     const int deg = p1 - p0;
-    const int maxdeg = max(deg, __shfl_xor_sync(0xffffffffu, deg, 16));
-    for (int base = 0; base < maxdeg; base += 16) {
+    int maxdeg = deg;
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
+    for (int base = 0; base < maxdeg; base += L) {
         int cj = 0;
         float wj = 0.f;
         if (base + hl < deg) {
             cj = col[p0 + base + hl];
             wj = w[p0 + base + hl];
         }
-        const int cnt = deg - base;                  // entries of this half in the chunk (may be <= 0)
-        const int cmax = min(16, maxdeg - base);
+        const int cnt = deg - base;                  // entries of this row in the chunk (may be <= 0)
+        const int cmax = min(L, maxdeg - base);
         int k = 0;
         for (; k + 4 <= cmax; k += 4) {
             int c[4];
@@ -316,12 +338,12 @@ __device__ __forceinline__ float4 agg_row64_pair(int p0, int p1, const int *__re
             float4 v[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                c[j] = __shfl_sync(0xffffffffu, cj, k + j, 16);
-                wk[j] = __shfl_sync(0xffffffffu, wj, k + j, 16);
+                c[j] = __shfl_sync(0xffffffffu, cj, k + j, L);
+                wk[j] = __shfl_sync(0xffffffffu, wj, k + j, L);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                v[j] = (k + j < cnt) ? x4[static_cast<size_t>(c[j]) * 16 + hl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[j] = (k + j < cnt) ? x4[static_cast<size_t>(c[j]) * L + hl] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (k + j < cnt) {
@@ -333,10 +355,10 @@ __device__ __forceinline__ float4 agg_row64_pair(int p0, int p1, const int *__re
             }
         }
         for (; k < cmax; ++k) {
-            const int c = __shfl_sync(0xffffffffu, cj, k, 16);
-            const float wk = __shfl_sync(0xffffffffu, wj, k, 16);
+            const int c = __shfl_sync(0xffffffffu, cj, k, L);
+            const float wk = __shfl_sync(0xffffffffu, wj, k, L);
             if (k < cnt) {
-                const float4 v = x4[static_cast<size_t>(c) * 16 + hl];
+                const float4 v = x4[static_cast<size_t>(c) * L + hl];
                 h.x = fmaf(wk, v.x, h.x);
                 h.y = fmaf(wk, v.y, h.y);
                 h.z = fmaf(wk, v.z, h.z);
@@ -347,41 +369,43 @@ __device__ __forceinline__ float4 agg_row64_pair(int p0, int p1, const int *__re
     return h;
 }
 
-// Layers 2..4: h = A_hat x (64 features), y = h W + b; tile stats.
+// Layers 2..4: h = A_hat x (H features), y = h W + b; tile stats.
+template <int H>
 __global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__ rp, const int *__restrict__ col,
                                                          const float *__restrict__ w, const float *__restrict__ x,
                                                          const float *__restrict__ W, const float *__restrict__ bias,
                                                          const int *__restrict__ tstart, float *__restrict__ hout,
                                                          float *__restrict__ y, float *__restrict__ tmean,
                                                          float *__restrict__ tm2) {
-    __shared__ float4 sW[kHidden * 16];   // W[m][4 j .. 4 j + 3]
-    __shared__ float sY[kTile][kHidden + 1];
-    for (int t2 = threadIdx.x; t2 < kHidden * 16; t2 += kBlock) sW[t2] = reinterpret_cast<const float4 *>(W)[t2];
+    constexpr int L = H / 4, R = 32 / L;   // lanes per row, rows per warp
+    __shared__ float4 sW[H * L];   // W[m][4 j .. 4 j + 3]
+    __shared__ float sY[kTile][H + 1];
+    for (int t2 = threadIdx.x; t2 < H * L; t2 += kBlock) sW[t2] = reinterpret_cast<const float4 *>(W)[t2];
     __syncthreads();
     const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, half = lane / 16, hl = lane % 16;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, grp = lane / L, hl = lane % L;
     const float4 *x4 = reinterpret_cast<const float4 *>(x);
     const float4 b4 = reinterpret_cast<const float4 *>(bias)[hl];
-    for (int k0 = 2 * warp; k0 < nn; k0 += 2 * (kBlock / 32)) {
-        const int k = k0 + half;
-        const bool live = k < nn;                    // the second row of the last pair may be absent
+    for (int k0 = R * warp; k0 < nn; k0 += R * (kBlock / 32)) {
+        const int k = k0 + grp;
+        const bool live = k < nn;                    // the last rows of the last group may be absent
         const int i = a + (live ? k : k0);
         const int p0 = rp[i], p1 = live ? rp[i + 1] : p0;
-        const float4 hv = agg_row64_pair(p0, p1, col, w, x4, hl);
-        if (live) reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * 16 + hl] = hv;
+        const float4 hv = agg_rows<H>(p0, p1, col, w, x4, hl);
+        if (live) reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * L + hl] = hv;
         float4 yv = b4;
 #pragma unroll 4
-        for (int m = 0; m < kHidden; ++m) {
+        for (int m = 0; m < H; ++m) {
             const float hsrc = (m & 3) == 0 ? hv.x : (m & 3) == 1 ? hv.y : (m & 3) == 2 ? hv.z : hv.w;
-            const float hm = __shfl_sync(0xffffffffu, hsrc, m >> 2, 16);
-            const float4 wm = sW[m * 16 + hl];
+            const float hm = __shfl_sync(0xffffffffu, hsrc, m >> 2, L);
+            const float4 wm = sW[m * L + hl];
             yv.x = fmaf(hm, wm.x, yv.x);
             yv.y = fmaf(hm, wm.y, yv.y);
             yv.z = fmaf(hm, wm.z, yv.z);
             yv.w = fmaf(hm, wm.w, yv.w);
         }
         if (live) {
-            reinterpret_cast<float4 *>(y)[static_cast<size_t>(i) * 16 + hl] = yv;
+            reinterpret_cast<float4 *>(y)[static_cast<size_t>(i) * L + hl] = yv;
             sY[k][4 * hl] = yv.x;
             sY[k][4 * hl + 1] = yv.y;
             sY[k][4 * hl + 2] = yv.z;
@@ -389,14 +413,17 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__
         }
     }
     __syncthreads();
-    tile_stats(sY, nn, tmean + static_cast<size_t>(t) * kHidden, tm2 + static_cast<size_t>(t) * kHidden);
+    tile_stats<H>(sY, nn, tmean + static_cast<size_t>(t) * H, tm2 + static_cast<size_t>(t) * H);
 }
 
-// Fixed-order sum over the 16 tile lanes of one feature (1024-thread blocks:
-// f = tid % 64, lane = tid / 64); every thread receives the total.
-constexpr int kLanes = 16, kCombine = kLanes * kHidden;
-__device__ __forceinline__ double lanes_sum(double v, double (*red)[kHidden]) {
-    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+// Fixed-order sum over the 16 tile lanes of one feature (16 H-thread blocks:
+// f = tid % H, lane = tid / H); every thread receives the total.
+constexpr int kLanes = 16;
+template <int H>
+constexpr int combine_threads() { return kLanes * H; }
+template <int H>
+__device__ __forceinline__ double lanes_sum(double v, double (*red)[H]) {
+    const int f = threadIdx.x % H, q = threadIdx.x / H;
     red[q][f] = v;
     __syncthreads();
     for (int w = kLanes / 2; w > 0; w >>= 1) {
@@ -415,34 +442,37 @@ __device__ __forceinline__ double lanes_sum(double v, double (*red)[kHidden]) {
 // the chunk mean and M2 into mu / rstd) and chunks -> graphs (final = 1:
 // writes the instance-norm mean and 1/sqrt(var + eps)).  16 lanes of parts
 // per feature; one FP64 add per part, the rest in FP32.
-__global__ void __launch_bounds__(kCombine) k_stats_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
+template <int H>
+__global__ void __launch_bounds__(kLanes * H) k_stats_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
                                                             const int *__restrict__ tstart,
                                                             const float *__restrict__ tmean,
                                                             const float *__restrict__ tm2, float *__restrict__ mu,
                                                             float *__restrict__ rstd, int final) {
-    __shared__ double red[kLanes][kHidden];
-    const int g = blockIdx.x, f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+    __shared__ double red[kLanes][H];
+    const int g = blockIdx.x, f = threadIdx.x % H, q = threadIdx.x / H;
     const double n = gptr[g + 1] - gptr[g];
     double s = 0.0;
     for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes)
-        s += static_cast<double>(static_cast<float>(tstart[t + 1] - tstart[t]) * tmean[static_cast<size_t>(t) * kHidden + f]);
-    const double mean = lanes_sum(s, red) / n;
+        s += static_cast<double>(static_cast<float>(tstart[t + 1] - tstart[t]) * tmean[static_cast<size_t>(t) * H + f]);
+    const double mean = lanes_sum<H>(s, red) / n;
     const float mf = static_cast<float>(mean);
     double v = 0.0;
     for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes) {
-        const float d = tmean[static_cast<size_t>(t) * kHidden + f] - mf;
+        const float d = tmean[static_cast<size_t>(t) * H + f] - mf;
         v += static_cast<double>(fmaf(static_cast<float>(tstart[t + 1] - tstart[t]) * d, d,
-                                      tm2[static_cast<size_t>(t) * kHidden + f]));
+                                      tm2[static_cast<size_t>(t) * H + f]));
     }
-    const double m2 = lanes_sum(v, red);
+    const double m2 = lanes_sum<H>(v, red);
     if (q == 0) {
-        mu[static_cast<size_t>(g) * kHidden + f] = mf;
-        rstd[static_cast<size_t>(g) * kHidden + f] =
+        mu[static_cast<size_t>(g) * H + f] = mf;
+        rstd[static_cast<size_t>(g) * H + f] =
             final ? static_cast<float>(1.0 / sqrt(m2 / n + static_cast<double>(kEps))) : static_cast<float>(m2);
     }
 }
 
-// x = ReLU((y - mu) rstd gamma + beta); tile sum / max / argmax of x.
+// x = ReLU((y - mu) rstd gamma + beta); tile sum / max / argmax of x
+// (kBlock / H groups of H threads, one thread per feature).
+template <int H>
 __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__restrict__ tstart,
                                                                 const int *__restrict__ tgraph,
                                                                 const float *__restrict__ y,
@@ -452,18 +482,19 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
                                                                 const float *__restrict__ beta, float *__restrict__ x,
                                                                 double *__restrict__ tsum, float *__restrict__ tmax,
                                                                 int *__restrict__ targ) {
-    __shared__ double rs[4][kHidden];
-    __shared__ float rm[4][kHidden];
-    __shared__ int ri[4][kHidden];
+    constexpr int Q = kBlock / H;
+    __shared__ double rs[Q][H];
+    __shared__ float rm[Q][H];
+    __shared__ int ri[Q][H];
     const int t = blockIdx.x, a = tstart[t], e = tstart[t + 1], g = tgraph[t];
-    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
-    const float m = mu[g * kHidden + f], r = rstd[g * kHidden + f], ga = gamma[f], be = beta[f];
+    const int f = threadIdx.x % H, q = threadIdx.x / H;
+    const float m = mu[g * H + f], r = rstd[g * H + f], ga = gamma[f], be = beta[f];
     double s = 0.0;
     float mx = -INFINITY;
     int mi = a;
 #pragma unroll 4
-    for (int i = a + q; i < e; i += 4) {
-        const size_t o = static_cast<size_t>(i) * kHidden + f;
+    for (int i = a + q; i < e; i += Q) {
+        const size_t o = static_cast<size_t>(i) * H + f;
         const float v = fmaxf((y[o] - m) * r * ga + be, 0.f);
         x[o] = v;
         s += v;
@@ -477,55 +508,56 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
         double ts = 0.0;
         float bm = -INFINITY;
         int bi = a;
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < Q; ++k) {
             ts += rs[k][f];
             if (rm[k][f] > bm || (rm[k][f] == bm && ri[k][f] < bi)) { bm = rm[k][f]; bi = ri[k][f]; }
         }
-        tsum[static_cast<size_t>(t) * kHidden + f] = ts;
-        tmax[static_cast<size_t>(t) * kHidden + f] = bm;
-        targ[static_cast<size_t>(t) * kHidden + f] = bi;
+        tsum[static_cast<size_t>(t) * H + f] = ts;
+        tmax[static_cast<size_t>(t) * H + f] = bm;
+        targ[static_cast<size_t>(t) * H + f] = bi;
     }
 }
 
 // Group sum and max (first index of the max kept) from part partials; as
 // for the statistics, tiles -> chunks (csum != nullptr: writes the chunk sum,
 // max and argmax) and chunks -> graphs (writes the pooled mean and max).
-__global__ void __launch_bounds__(kCombine) k_pool_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
+template <int H>
+__global__ void __launch_bounds__(kLanes * H) k_pool_combine(const int *__restrict__ gtile, const int *__restrict__ gptr,
                                                            const double *__restrict__ tsum,
                                                            const float *__restrict__ tmax,
                                                            const int *__restrict__ targ, float *__restrict__ pooled,
                                                            int *__restrict__ argmax, int layer,
                                                            double *__restrict__ csum, float *__restrict__ cmax,
                                                            int *__restrict__ carg) {
-    __shared__ double red[kLanes][kHidden];
-    __shared__ float rm[kLanes][kHidden];
-    __shared__ int ri[kLanes][kHidden];
-    const int g = blockIdx.x, f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+    __shared__ double red[kLanes][H];
+    __shared__ float rm[kLanes][H];
+    __shared__ int ri[kLanes][H];
+    const int g = blockIdx.x, f = threadIdx.x % H, q = threadIdx.x / H;
     double s = 0.0;
     float bm = -INFINITY;
     int bi = gptr[g];
     for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes) {
-        const size_t o = static_cast<size_t>(t) * kHidden + f;
+        const size_t o = static_cast<size_t>(t) * H + f;
         s += tsum[o];
         if (tmax[o] > bm) { bm = tmax[o]; bi = targ[o]; }   // tiles ascend, so the first max wins
     }
     rm[q][f] = bm;
     ri[q][f] = bi;
-    const double total = lanes_sum(s, red);
+    const double total = lanes_sum<H>(s, red);
     if (q == 0) {
         for (int k = 1; k < kLanes; ++k)
             if (rm[k][f] > bm || (rm[k][f] == bm && ri[k][f] < bi)) { bm = rm[k][f]; bi = ri[k][f]; }
         if (csum) {
-            const size_t o = static_cast<size_t>(g) * kHidden + f;
+            const size_t o = static_cast<size_t>(g) * H + f;
             csum[o] = total;
             cmax[o] = bm;
             carg[o] = bi;
             return;
         }
-        float *P = pooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
+        float *P = pooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * H;
         P[f] = static_cast<float>(total / (gptr[g + 1] - gptr[g]));
-        P[kHidden + f] = bm;
-        argmax[(static_cast<size_t>(g) * kLayers + layer) * kHidden + f] = bi;
+        P[H + f] = bm;
+        argmax[(static_cast<size_t>(g) * kLayers + layer) * H + f] = bi;
     }
 }
 
@@ -545,27 +577,28 @@ constexpr int kSz = 0, kSzh = kEmb, kSsg = 2 * kEmb, kSa1 = 3 * kEmb, kSa2 = 3 *
 constexpr int kGdz1 = 0, kGdz2 = 128, kGdzh = 192, kGdz = 192 + kEmb;
 
 // Readout + head for one graph (128 threads).
+template <int H>
 __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, const float *__restrict__ th,
                                               float *__restrict__ scratch, float *__restrict__ c) {
-    __shared__ float sp[kLayers * 2 * kHidden];
+    __shared__ float sp[kLayers * 2 * H];
     __shared__ float ss[kEmb], sa1[128], sa2[64];
     __shared__ float red[4];
     const int g = blockIdx.x, t = threadIdx.x;
-    for (int k = t; k < kLayers * 2 * kHidden; k += 128) sp[k] = pooled[static_cast<size_t>(g) * kLayers * 2 * kHidden + k];
+    for (int k = t; k < kLayers * 2 * H; k += 128) sp[k] = pooled[static_cast<size_t>(g) * kLayers * 2 * H + k];
     __syncthreads();
     float *S = scratch + static_cast<size_t>(g) * kHeadScratch;
     // readout linears: z[32 l + k] = [mean_l, max_l] . W_l[:, k] + b_l[k]
     const int l = t / kRo, k = t % kRo;
-    const float *W = th + kPLd.roW[l];
-    float z = th[kPLd.roB[l] + k];
+    const float *W = th + PL<H>().roW[l];
+    float z = th[PL<H>().roB[l] + k];
 #pragma unroll 8
-    for (int m = 0; m < 2 * kHidden; ++m) z = fmaf(sp[l * 2 * kHidden + m], W[m * kRo + k], z);
+    for (int m = 0; m < 2 * H; ++m) z = fmaf(sp[l * 2 * H + m], W[m * kRo + k], z);
     // layer norm over the 128-vector
     const float mean = block128_sum(z, red) / kEmb;
     const float d = z - mean;
     const float var = block128_sum(d * d, red) / kEmb;
     const float rs = rsqrtf(var + kEps);
-    const float zh = d * rs * th[kPLd.lnG + t] + th[kPLd.lnB + t];
+    const float zh = d * rs * th[PL<H>().lnG + t] + th[PL<H>().lnB + t];
     const float sg = 1.f / (1.f + expf(-zh));
     S[kSz + t] = z;
     S[kSzh + t] = zh;
@@ -576,26 +609,26 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
     }
     ss[t] = sg;
     __syncthreads();
-    float a1 = th[kPLd.h1B + t];
+    float a1 = th[PL<H>().h1B + t];
 #pragma unroll 8
-    for (int m = 0; m < kEmb; ++m) a1 = fmaf(ss[m], th[kPLd.h1W + m * 128 + t], a1);
+    for (int m = 0; m < kEmb; ++m) a1 = fmaf(ss[m], th[PL<H>().h1W + m * 128 + t], a1);
     a1 = fmaxf(a1, 0.f);
     sa1[t] = a1;
     S[kSa1 + t] = a1;
     __syncthreads();
     if (t < 64) {
-        float a2 = th[kPLd.h2B + t];
+        float a2 = th[PL<H>().h2B + t];
 #pragma unroll 8
-        for (int m = 0; m < 128; ++m) a2 = fmaf(sa1[m], th[kPLd.h2W + m * 64 + t], a2);
+        for (int m = 0; m < 128; ++m) a2 = fmaf(sa1[m], th[PL<H>().h2W + m * 64 + t], a2);
         a2 = fmaxf(a2, 0.f);
         sa2[t] = a2;
         S[kSa2 + t] = a2;
     }
     __syncthreads();
     if (t < 5) {
-        float o = th[kPLd.h3B + t];
+        float o = th[PL<H>().h3B + t];
 #pragma unroll 8
-        for (int m = 0; m < 64; ++m) o = fmaf(sa2[m], th[kPLd.h3W + m * 5 + t], o);
+        for (int m = 0; m < 64; ++m) o = fmaf(sa2[m], th[PL<H>().h3W + m * 5 + t], o);
         c[g * 5 + t] = o;
     }
 }
@@ -608,38 +641,48 @@ void gcin_prepare_device() {
     static bool done[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_agg_lin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(k_agg_lin_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden>());
+    cudaFuncSetAttribute(k_agg_lin_tc<kHidden32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden32>());
     done[dev] = true;
+}
+
+template <int H>
+static void forward_impl(GcinBatch &b, const float *th, cudaStream_t s) {
+    const ParamLayout &pl = host_layout(H);
+    const int N = b.N, G = b.G, NT = b.NT;
+    constexpr int CT = combine_threads<H>();
+    k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
+    for (int l = 0; l < kLayers; ++l) {
+        if (l == 0) {
+            k_layer1_tile<H><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + pl.convW[0], th + pl.convB[0],
+                                                   b.tstart, b.h1, b.y[0], b.tmean, b.tm2); AMG_COUNT();
+        } else if (b.bf16) {
+            k_agg_lin_tc<H><<<(NT + 1) / 2, kBlock, tc_smem<H>(), s>>>(b.rp, b.col, b.w, b.x[l - 1],
+                                                                     th + pl.convW[l], th + pl.convB[l], b.tstart,
+                                                                     NT, b.h[l], b.y[l], b.tmean, b.tm2, b.err,
+                                                                     0); AMG_COUNT();
+        } else {
+            k_agg_lin_tile<H><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + pl.convW[l],
+                                                    th + pl.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
+                                                    b.tm2); AMG_COUNT();
+        }
+        k_stats_combine<H><<<b.NC, CT, 0, s>>>(b.ctile, b.cnode, b.tstart, b.tmean, b.tm2, b.cmean, b.cm2, 0); AMG_COUNT();
+        k_stats_combine<H><<<G, CT, 0, s>>>(b.gchunk, b.gptr, b.cnode, b.cmean, b.cm2, b.mu[l], b.rstd[l], 1); AMG_COUNT();
+        k_norm_relu_pool_tile<H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
+                                                       th + pl.inG[l], th + pl.inB[l], b.x[l], b.tsum, b.tmax,
+                                                       b.targ); AMG_COUNT();
+        k_pool_combine<H><<<b.NC, CT, 0, s>>>(b.ctile, b.cnode, b.tsum, b.tmax, b.targ, nullptr, nullptr, l,
+                                              b.csum, b.cmax, b.carg); AMG_COUNT();
+        k_pool_combine<H><<<G, CT, 0, s>>>(b.gchunk, b.gptr, b.csum, b.cmax, b.carg, b.pooled, b.argmax, l,
+                                           nullptr, nullptr, nullptr); AMG_COUNT();
+    }
+    k_head<H><<<G, 128, 0, s>>>(b.pooled, th, b.head, b.c); AMG_COUNT();
 }
 
 void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
     gcin_prepare_device();
-    const int N = b.N, G = b.G, NT = b.NT;
-    k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
-    for (int l = 0; l < kLayers; ++l) {
-        if (l == 0) {
-            k_layer1_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + kPL.convW[0], th + kPL.convB[0],
-                                                b.tstart, b.h1, b.y[0], b.tmean, b.tm2); AMG_COUNT();
-        } else if (b.bf16) {
-            k_agg_lin_tc<<<(NT + 1) / 2, kBlock, kTcSmem, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
-                                                               th + kPL.convB[l], b.tstart, NT, b.h[l], b.y[l],
-                                                               b.tmean, b.tm2, b.err, 0); AMG_COUNT();
-        } else {
-            k_agg_lin_tile<<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + kPL.convW[l],
-                                                 th + kPL.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
-                                                 b.tm2); AMG_COUNT();
-        }
-        k_stats_combine<<<b.NC, kCombine, 0, s>>>(b.ctile, b.cnode, b.tstart, b.tmean, b.tm2, b.cmean, b.cm2, 0); AMG_COUNT();
-        k_stats_combine<<<G, kCombine, 0, s>>>(b.gchunk, b.gptr, b.cnode, b.cmean, b.cm2, b.mu[l], b.rstd[l], 1); AMG_COUNT();
-        k_norm_relu_pool_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
-                                                    th + kPL.inG[l], th + kPL.inB[l], b.x[l], b.tsum, b.tmax,
-                                                    b.targ); AMG_COUNT();
-        k_pool_combine<<<b.NC, kCombine, 0, s>>>(b.ctile, b.cnode, b.tsum, b.tmax, b.targ, nullptr, nullptr, l,
-                                                 b.csum, b.cmax, b.carg); AMG_COUNT();
-        k_pool_combine<<<G, kCombine, 0, s>>>(b.gchunk, b.gptr, b.csum, b.cmax, b.carg, b.pooled, b.argmax, l,
-                                              nullptr, nullptr, nullptr); AMG_COUNT();
-    }
-    k_head<<<G, 128, 0, s>>>(b.pooled, th, b.head, b.c); AMG_COUNT();
+    if (b.hidden == kHidden32) forward_impl<kHidden32>(b, th, s);
+    else forward_impl<kHidden>(b, th, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -647,6 +690,7 @@ void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Head backward for one graph: dc -> dz2, dz1, dzh, dz (readout outputs) and
 // the pooled-feature gradient dpooled.
+template <int H>
 __global__ void __launch_bounds__(128) k_head_bwd(const float *__restrict__ scratch, const float *__restrict__ th,
                                                   const float *__restrict__ dc, float *__restrict__ dhead,
                                                   float *__restrict__ dpooled) {
@@ -659,27 +703,27 @@ __global__ void __launch_bounds__(128) k_head_bwd(const float *__restrict__ scra
     __syncthreads();
     if (t < 64) {
         float da2 = 0.f;
-        for (int k = 0; k < 5; ++k) da2 = fmaf(sdc[k], th[kPLd.h3W + t * 5 + k], da2);
+        for (int k = 0; k < 5; ++k) da2 = fmaf(sdc[k], th[PL<H>().h3W + t * 5 + k], da2);
         const float dz2 = S[kSa2 + t] > 0.f ? da2 : 0.f;
         sdz2[t] = dz2;
         D[kGdz2 + t] = dz2;
     }
     __syncthreads();
     float da1 = 0.f;
-    for (int k = 0; k < 64; ++k) da1 = fmaf(sdz2[k], th[kPLd.h2W + t * 64 + k], da1);
+    for (int k = 0; k < 64; ++k) da1 = fmaf(sdz2[k], th[PL<H>().h2W + t * 64 + k], da1);
     const float dz1 = S[kSa1 + t] > 0.f ? da1 : 0.f;
     sdz1[t] = dz1;
     D[kGdz1 + t] = dz1;
     __syncthreads();
     float ds = 0.f;
-    for (int k = 0; k < 128; ++k) ds = fmaf(sdz1[k], th[kPLd.h1W + t * 128 + k], ds);
+    for (int k = 0; k < 128; ++k) ds = fmaf(sdz1[k], th[PL<H>().h1W + t * 128 + k], ds);
     const float sg = S[kSsg + t];
     const float dzh = ds * sg * (1.f - sg);
     D[kGdzh + t] = dzh;
     // layer norm backward
     const float rs = S[kSrs], mean = S[kSmean];
     const float zn = (S[kSz + t] - mean) * rs;
-    const float dzn = dzh * th[kPLd.lnG + t];
+    const float dzn = dzh * th[PL<H>().lnG + t];
     const float m1 = block128_sum(dzn, red) / kEmb;
     const float m2 = block128_sum(dzn * zn, red) / kEmb;
     const float dz = rs * (dzn - m1 - zn * m2);
@@ -687,58 +731,59 @@ __global__ void __launch_bounds__(128) k_head_bwd(const float *__restrict__ scra
     D[kGdz + t] = dz;
     __syncthreads();
     // readout linears: dpooled_l[m] = sum_k dz[32 l + k] W_l[m][k]
-    for (int j = t; j < kLayers * 2 * kHidden; j += 128) {
-        const int l = j / (2 * kHidden), m = j % (2 * kHidden);
-        const float *W = th + kPLd.roW[l] + m * kRo;
+    for (int j = t; j < kLayers * 2 * H; j += 128) {
+        const int l = j / (2 * H), m = j % (2 * H);
+        const float *W = th + PL<H>().roW[l] + m * kRo;
         float acc = 0.f;
         for (int k = 0; k < kRo; ++k) acc = fmaf(sdz[l * kRo + k], W[k], acc);
-        dpooled[static_cast<size_t>(g) * kLayers * 2 * kHidden + j] = acc;
+        dpooled[static_cast<size_t>(g) * kLayers * 2 * H + j] = acc;
     }
 }
 
 // Gradients of the readout / layer-norm / head parameters: one thread per
 // parameter, sum over graphs in graph order.
+template <int H>
 __global__ void k_head_param_grad(int G, const float *__restrict__ pooled, const float *__restrict__ scratch,
                                   const float *__restrict__ dhead, const float *__restrict__ dc,
                                   float *__restrict__ grad) {
-    const int p = kPLd.roW[0] + blockIdx.x * kBlock + threadIdx.x;
-    if (p >= kNumParams) return;
+    const int p = PL<H>().roW[0] + blockIdx.x * kBlock + threadIdx.x;
+    if (p >= num_params<H>()) return;
     double acc = 0.0;
     int l = -1;
     for (int k = 0; k < kLayers; ++k)
-        if (p >= kPLd.roW[k] && p < kPLd.roB[k] + kRo) l = k;
+        if (p >= PL<H>().roW[k] && p < PL<H>().roB[k] + kRo) l = k;
     for (int g = 0; g < G; ++g) {
         const float *S = scratch + static_cast<size_t>(g) * kHeadScratch;
         const float *D = dhead + static_cast<size_t>(g) * kHeadGrad;
         double v;
         if (l >= 0) {
-            if (p < kPLd.roB[l]) {
-                const int o = p - kPLd.roW[l], m = o / kRo, k = o % kRo;
-                v = static_cast<double>(pooled[(static_cast<size_t>(g) * kLayers + l) * 2 * kHidden + m]) *
+            if (p < PL<H>().roB[l]) {
+                const int o = p - PL<H>().roW[l], m = o / kRo, k = o % kRo;
+                v = static_cast<double>(pooled[(static_cast<size_t>(g) * kLayers + l) * 2 * H + m]) *
                     D[kGdz + l * kRo + k];
             } else {
-                v = D[kGdz + l * kRo + (p - kPLd.roB[l])];
+                v = D[kGdz + l * kRo + (p - PL<H>().roB[l])];
             }
-        } else if (p < kPLd.lnB) {
-            const int k = p - kPLd.lnG;
+        } else if (p < PL<H>().lnB) {
+            const int k = p - PL<H>().lnG;
             v = static_cast<double>(D[kGdzh + k]) * ((S[kSz + k] - S[kSmean]) * S[kSrs]);
-        } else if (p < kPLd.h1W) {
-            v = D[kGdzh + (p - kPLd.lnB)];
-        } else if (p < kPLd.h1B) {
-            const int o = p - kPLd.h1W, m = o / 128, k = o % 128;
+        } else if (p < PL<H>().h1W) {
+            v = D[kGdzh + (p - PL<H>().lnB)];
+        } else if (p < PL<H>().h1B) {
+            const int o = p - PL<H>().h1W, m = o / 128, k = o % 128;
             v = static_cast<double>(S[kSsg + m]) * D[kGdz1 + k];
-        } else if (p < kPLd.h2W) {
-            v = D[kGdz1 + (p - kPLd.h1B)];
-        } else if (p < kPLd.h2B) {
-            const int o = p - kPLd.h2W, m = o / 64, k = o % 64;
+        } else if (p < PL<H>().h2W) {
+            v = D[kGdz1 + (p - PL<H>().h1B)];
+        } else if (p < PL<H>().h2B) {
+            const int o = p - PL<H>().h2W, m = o / 64, k = o % 64;
             v = static_cast<double>(S[kSa1 + m]) * D[kGdz2 + k];
-        } else if (p < kPLd.h3W) {
-            v = D[kGdz2 + (p - kPLd.h2B)];
-        } else if (p < kPLd.h3B) {
-            const int o = p - kPLd.h3W, m = o / 5, k = o % 5;
+        } else if (p < PL<H>().h3W) {
+            v = D[kGdz2 + (p - PL<H>().h2B)];
+        } else if (p < PL<H>().h3B) {
+            const int o = p - PL<H>().h3W, m = o / 5, k = o % 5;
             v = static_cast<double>(S[kSa2 + m]) * dc[g * 5 + k];
         } else {
-            v = dc[g * 5 + (p - kPLd.h3B)];
+            v = dc[g * 5 + (p - PL<H>().h3B)];
         }
         acc += v;
     }
@@ -747,6 +792,7 @@ __global__ void k_head_param_grad(int G, const float *__restrict__ pooled, const
 
 // Layer backward, part 1 (per tile): dX = dx_next + pooling routes; the
 // ReLU mask gives d(yn); tile sums S1 = sum d(yn), S2 = sum d(yn) * yhat.
+template <int H>
 __global__ void __launch_bounds__(kBlock) k_bwd_relu_tile(const int *__restrict__ tstart,
                                                           const int *__restrict__ tgraph, const int *__restrict__ gptr,
                                                           const float *__restrict__ x, const float *__restrict__ y,
@@ -755,16 +801,17 @@ __global__ void __launch_bounds__(kBlock) k_bwd_relu_tile(const int *__restrict_
                                                           const int *__restrict__ argmax, int layer,
                                                           float *__restrict__ dyn, double *__restrict__ tsum,
                                                           double *__restrict__ tsum2) {
-    __shared__ double r1[4][kHidden], r2[4][kHidden];
+    constexpr int Q = kBlock / H;
+    __shared__ double r1[Q][H], r2[Q][H];
     const int t = blockIdx.x, a = tstart[t], e = tstart[t + 1], g = tgraph[t];
-    const int f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
-    const float *dp = dpooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * kHidden;
-    const float dmean = dp[f] / (gptr[g + 1] - gptr[g]), dmax = dp[kHidden + f];
-    const int am = argmax[(static_cast<size_t>(g) * kLayers + layer) * kHidden + f];
-    const float m = mu[g * kHidden + f], r = rstd[g * kHidden + f];
+    const int f = threadIdx.x % H, q = threadIdx.x / H;
+    const float *dp = dpooled + (static_cast<size_t>(g) * kLayers + layer) * 2 * H;
+    const float dmean = dp[f] / (gptr[g + 1] - gptr[g]), dmax = dp[H + f];
+    const int am = argmax[(static_cast<size_t>(g) * kLayers + layer) * H + f];
+    const float m = mu[g * H + f], r = rstd[g * H + f];
     double s1 = 0.0, s2 = 0.0;
-    for (int i = a + q; i < e; i += 4) {
-        const size_t o = static_cast<size_t>(i) * kHidden + f;
+    for (int i = a + q; i < e; i += Q) {
+        const size_t o = static_cast<size_t>(i) * H + f;
         float dX = dmean + (i == am ? dmax : 0.f);
         if (dx) dX += dx[o];
         const float d = x[o] > 0.f ? dX : 0.f;
@@ -776,35 +823,60 @@ __global__ void __launch_bounds__(kBlock) k_bwd_relu_tile(const int *__restrict_
     r2[q][f] = s2;
     __syncthreads();
     if (q == 0) {
-        tsum[static_cast<size_t>(t) * kHidden + f] = r1[0][f] + r1[1][f] + r1[2][f] + r1[3][f];
-        tsum2[static_cast<size_t>(t) * kHidden + f] = r2[0][f] + r2[1][f] + r2[2][f] + r2[3][f];
+        double t1 = r1[0][f], t2 = r2[0][f];
+        for (int k = 1; k < Q; ++k) {
+            t1 += r1[k][f];
+            t2 += r2[k][f];
+        }
+        tsum[static_cast<size_t>(t) * H + f] = t1;
+        tsum2[static_cast<size_t>(t) * H + f] = t2;
     }
 }
 
-__global__ void __launch_bounds__(kCombine) k_bwd_combine(const int *__restrict__ gtile,
-                                                          const double *__restrict__ tsum,
-                                                          const double *__restrict__ tsum2,
-                                                          double *__restrict__ gS1, double *__restrict__ gS2) {
-    __shared__ double red[kLanes][kHidden];
-    const int g = blockIdx.x, f = threadIdx.x % kHidden, q = threadIdx.x / kHidden;
+template <int H>
+__global__ void __launch_bounds__(kLanes * H) k_bwd_combine(const int *__restrict__ gtile,
+                                                            const double *__restrict__ tsum,
+                                                            const double *__restrict__ tsum2,
+                                                            double *__restrict__ gS1, double *__restrict__ gS2) {
+    __shared__ double red[kLanes][H];
+    const int g = blockIdx.x, f = threadIdx.x % H, q = threadIdx.x / H;
     double s1 = 0.0, s2 = 0.0;
     for (int t = gtile[g] + q; t < gtile[g + 1]; t += kLanes) {
-        s1 += tsum[static_cast<size_t>(t) * kHidden + f];
-        s2 += tsum2[static_cast<size_t>(t) * kHidden + f];
+        s1 += tsum[static_cast<size_t>(t) * H + f];
+        s2 += tsum2[static_cast<size_t>(t) * H + f];
     }
-    const double t1 = lanes_sum(s1, red);
-    const double t2 = lanes_sum(s2, red);
+    const double t1 = lanes_sum<H>(s1, red);
+    const double t2 = lanes_sum<H>(s2, red);
     if (q == 0) {
-        gS1[g * kHidden + f] = t1;
-        gS2[g * kHidden + f] = t2;
+        gS1[g * H + f] = t1;
+        gS2[g * H + f] = t2;
     }
+}
+
+// FPL = H / 32 consecutive floats of row i owned by lane `lane` (float2 for H = 64)
+template <int FPL>
+__device__ __forceinline__ void lane_load(const float *__restrict__ p, size_t i, int lane, float (&v)[FPL]) {
+    if constexpr (FPL == 2) {
+        const float2 t = reinterpret_cast<const float2 *>(p)[i * 32 + lane];
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+        v[0] = p[i * 32 + lane];
+    }
+}
+
+template <int FPL>
+__device__ __forceinline__ void lane_store(float *__restrict__ p, size_t i, int lane, const float (&v)[FPL]) {
+    if constexpr (FPL == 2) reinterpret_cast<float2 *>(p)[i * 32 + lane] = make_float2(v[0], v[1]);
+    else p[i * 32 + lane] = v[0];
 }
 
 // Layer backward, part 2 (per tile): instance-norm backward
 //   dy = rstd (gamma d(yn) - gamma S1/n - yhat gamma S2/n),
 // then dh = dy W^T (layers 2..4) and the tile's partial weight and bias
-// gradients sum_i h_i^T dy_i, sum_i dy_i.
-template <int FIN>
+// gradients sum_i h_i^T dy_i, sum_i dy_i.  A warp takes one node; lane j owns
+// features FPL j .. FPL j + FPL - 1 (FPL = H / 32).
+template <int FIN, int H>
 __global__ void __launch_bounds__(kBlock) k_bwd_in_lin_tile(const int *__restrict__ tstart,
                                                             const int *__restrict__ tgraph,
                                                             const int *__restrict__ gptr, const float *__restrict__ y,
@@ -816,153 +888,174 @@ __global__ void __launch_bounds__(kBlock) k_bwd_in_lin_tile(const int *__restric
                                                             const float *__restrict__ W, const float *__restrict__ hin,
                                                             const float *__restrict__ dyn, float *__restrict__ dh,
                                                             float *__restrict__ dWt, int round_w) {
-    __shared__ float2 sWT[FIN == kHidden ? kHidden * 32 : 1];   // (W[2 lane][k], W[2 lane + 1][k])
+    constexpr int FPL = H / 32;
+    // sWT[k][FPL lane + j] = W[FPL lane + j][k]
+    __shared__ __align__(8) float sWT[FIN == H ? H * H : 1];
     __shared__ float sH[kTile][FIN + 1];
-    __shared__ float sD[kTile][kHidden + 1];
-    if (FIN == kHidden) {
-        for (int e = threadIdx.x; e < kHidden * 32; e += kBlock) {
-            const int k = e / 32, ln = e % 32;
-            float w0 = W[(2 * ln) * kHidden + k], w1 = W[(2 * ln + 1) * kHidden + k];
-            if (round_w) {   // the forward multiplied by the BF16-rounded weights
-                w0 = __bfloat162float(__float2bfloat16_rn(w0));
-                w1 = __bfloat162float(__float2bfloat16_rn(w1));
-            }
-            sWT[e] = make_float2(w0, w1);
+    __shared__ float sD[kTile][H + 1];
+    if (FIN == H) {
+        for (int e = threadIdx.x; e < H * H; e += kBlock) {
+            const int k = e / H, n = e % H;
+            float wv = W[n * H + k];
+            if (round_w) wv = __bfloat162float(__float2bfloat16_rn(wv));   // the forward multiplied by the BF16-rounded weights
+            sWT[e] = wv;
         }
     }
     const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a, g = tgraph[t];
     const float inv_n = 1.f / (gptr[g + 1] - gptr[g]);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int f0 = 2 * lane, f1 = 2 * lane + 1;
-    const float ga0 = gamma[f0], ga1 = gamma[f1];
-    const float m0 = mu[g * kHidden + f0], m1 = mu[g * kHidden + f1];
-    const float r0 = rstd[g * kHidden + f0], r1 = rstd[g * kHidden + f1];
-    const float c10 = ga0 * static_cast<float>(gS1[g * kHidden + f0]) * inv_n;
-    const float c11 = ga1 * static_cast<float>(gS1[g * kHidden + f1]) * inv_n;
-    const float c20 = ga0 * static_cast<float>(gS2[g * kHidden + f0]) * inv_n;
-    const float c21 = ga1 * static_cast<float>(gS2[g * kHidden + f1]) * inv_n;
+    float ga[FPL], m[FPL], r[FPL], c1[FPL], c2[FPL];
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) {
+        const int f = FPL * lane + j;
+        ga[j] = gamma[f];
+        m[j] = mu[g * H + f];
+        r[j] = rstd[g * H + f];
+        c1[j] = ga[j] * static_cast<float>(gS1[g * H + f]) * inv_n;
+        c2[j] = ga[j] * static_cast<float>(gS2[g * H + f]) * inv_n;
+    }
     __syncthreads();
     for (int k = warp; k < nn; k += kBlock / 32) {
         const int i = a + k;
-        const float2 d2 = reinterpret_cast<const float2 *>(dyn)[static_cast<size_t>(i) * 32 + lane];
-        const float2 y2 = reinterpret_cast<const float2 *>(y)[static_cast<size_t>(i) * 32 + lane];
-        const float yh0 = (y2.x - m0) * r0, yh1 = (y2.y - m1) * r1;
-        const float dy0 = r0 * (ga0 * d2.x - c10 - yh0 * c20);
-        const float dy1 = r1 * (ga1 * d2.y - c11 - yh1 * c21);
-        sD[k][f0] = dy0;
-        sD[k][f1] = dy1;
-        if (FIN == kHidden) {
-            const float2 h2 = reinterpret_cast<const float2 *>(hin)[static_cast<size_t>(i) * 32 + lane];
-            sH[k][f0] = h2.x;
-            sH[k][f1] = h2.y;
-            float a0 = 0.f, a1 = 0.f;
+        float d[FPL], yv[FPL], dy[FPL];
+        lane_load<FPL>(dyn, i, lane, d);
+        lane_load<FPL>(y, i, lane, yv);
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+            const float yh = (yv[j] - m[j]) * r[j];
+            dy[j] = r[j] * (ga[j] * d[j] - c1[j] - yh * c2[j]);
+            sD[k][FPL * lane + j] = dy[j];
+        }
+        if (FIN == H) {
+            float hv[FPL];
+            lane_load<FPL>(hin, i, lane, hv);
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) sH[k][FPL * lane + j] = hv[j];
+            float acc[FPL] = {};
 #pragma unroll 8
-            for (int kk = 0; kk < kHidden; ++kk) {
-                const float dk = __shfl_sync(0xffffffffu, (kk & 1) ? dy1 : dy0, kk >> 1);
-                const float2 wk = sWT[kk * 32 + lane];
-                a0 = fmaf(dk, wk.x, a0);
-                a1 = fmaf(dk, wk.y, a1);
+            for (int kk = 0; kk < H; ++kk) {
+                const float dk = __shfl_sync(0xffffffffu, dy[kk % FPL], kk / FPL);
+                if constexpr (FPL == 2) {
+                    const float2 wk = reinterpret_cast<const float2 *>(sWT)[kk * 32 + lane];
+                    acc[0] = fmaf(dk, wk.x, acc[0]);
+                    acc[1] = fmaf(dk, wk.y, acc[1]);
+                } else {
+                    acc[0] = fmaf(dk, sWT[kk * H + lane], acc[0]);
+                }
             }
-            reinterpret_cast<float2 *>(dh)[static_cast<size_t>(i) * 32 + lane] = make_float2(a0, a1);
+            lane_store<FPL>(dh, i, lane, acc);
         } else {
             if (lane < FIN) sH[k][lane] = hin[static_cast<size_t>(i) * FIN + lane];
         }
     }
     __syncthreads();
-    float *out = dWt + static_cast<size_t>(t) * (kHidden * kHidden + kHidden);
-    for (int e = threadIdx.x; e < FIN * kHidden; e += kBlock) {
-        const int m = e / kHidden, k = e % kHidden;
+    float *out = dWt + static_cast<size_t>(t) * (H * H + H);
+    for (int e = threadIdx.x; e < FIN * H; e += kBlock) {
+        const int mm = e / H, kk = e % H;
         float acc = 0.f;
-        for (int j = 0; j < nn; ++j) acc = fmaf(sH[j][m], sD[j][k], acc);
+        for (int j = 0; j < nn; ++j) acc = fmaf(sH[j][mm], sD[j][kk], acc);
         out[e] = acc;
     }
-    if (threadIdx.x < kHidden) {
+    if (threadIdx.x < H) {
         float acc = 0.f;
         for (int j = 0; j < nn; ++j) acc += sD[j][threadIdx.x];
-        out[kHidden * kHidden + threadIdx.x] = acc;
+        out[H * H + threadIdx.x] = acc;
     }
 }
 
-// dx = A_hat dh (A_hat symmetric), 64 features, two nodes per warp.
+// dx = A_hat dh (A_hat symmetric), H features, 32 / (H / 4) nodes per warp.
+template <int H>
 __global__ void __launch_bounds__(kBlock) k_agg_plain(int N, const int *__restrict__ rp, const int *__restrict__ col,
                                                       const float *__restrict__ w, const float *__restrict__ v,
                                                       float *__restrict__ out) {
-    const int pair = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32, hl = lane % 16;
-    const int i0 = 2 * pair;
+    constexpr int L = H / 4, R = 32 / L;
+    const int wid = (blockIdx.x * kBlock + threadIdx.x) / 32, lane = threadIdx.x % 32, hl = lane % L;
+    const int i0 = R * wid;
     if (i0 >= N) return;                         // warp-uniform
-    const int i = i0 + lane / 16;
+    const int i = i0 + lane / L;
     const bool live = i < N;
     const int p0 = rp[live ? i : i0], p1 = live ? rp[i + 1] : p0;
-    const float4 h = agg_row64_pair(p0, p1, col, w, reinterpret_cast<const float4 *>(v), hl);
-    if (live) reinterpret_cast<float4 *>(out)[static_cast<size_t>(i) * 16 + hl] = h;
+    const float4 h = agg_rows<H>(p0, p1, col, w, reinterpret_cast<const float4 *>(v), hl);
+    if (live) reinterpret_cast<float4 *>(out)[static_cast<size_t>(i) * L + hl] = h;
 }
 
 // Conv weight/bias gradient: tile partials summed per chunk of tiles (FP64,
 // tile order), then the chunks in order; instance-norm affine gradients are
 // the per-graph sums added in graph order.
-constexpr int kGradStride = kHidden * kHidden + kHidden;
+template <int H>
+constexpr int grad_stride() { return H * H + H; }
+template <int H>
 __global__ void k_layer_param_partial(int NT, int fin, const float *__restrict__ dWt, double *__restrict__ chunk) {
     const int e = blockIdx.x * kBlock + threadIdx.x, c = blockIdx.y;
-    const int nW = fin * kHidden;
-    if (e >= nW + kHidden) return;
-    const int src = (e < nW) ? e : kHidden * kHidden + (e - nW);
+    const int nW = fin * H;
+    if (e >= nW + H) return;
+    const int src = (e < nW) ? e : H * H + (e - nW);
     const int t0 = static_cast<int>(static_cast<long long>(NT) * c / kGradChunks);
     const int t1 = static_cast<int>(static_cast<long long>(NT) * (c + 1) / kGradChunks);
     double acc = 0.0;
-    for (int t = t0; t < t1; ++t) acc += dWt[static_cast<size_t>(t) * kGradStride + src];
-    chunk[static_cast<size_t>(c) * kGradStride + e] = acc;
+    for (int t = t0; t < t1; ++t) acc += dWt[static_cast<size_t>(t) * grad_stride<H>() + src];
+    chunk[static_cast<size_t>(c) * grad_stride<H>() + e] = acc;
 }
 
+template <int H>
 __global__ void k_layer_param_final(int G, int fin, const double *__restrict__ chunk, const double *__restrict__ gS1,
                                     const double *__restrict__ gS2, float *__restrict__ gW, float *__restrict__ gB,
                                     float *__restrict__ gG, float *__restrict__ gBeta) {
     const int e = blockIdx.x * kBlock + threadIdx.x;
-    const int nW = fin * kHidden;
-    if (e < nW + kHidden) {
+    const int nW = fin * H;
+    if (e < nW + H) {
         double acc = 0.0;
-        for (int c = 0; c < kGradChunks; ++c) acc += chunk[static_cast<size_t>(c) * kGradStride + e];
+        for (int c = 0; c < kGradChunks; ++c) acc += chunk[static_cast<size_t>(c) * grad_stride<H>() + e];
         if (e < nW) gW[e] = static_cast<float>(acc);
         else gB[e - nW] = static_cast<float>(acc);
-    } else if (e < nW + 2 * kHidden) {
-        const int f = e - nW - kHidden;
+    } else if (e < nW + 2 * H) {
+        const int f = e - nW - H;
         double s1 = 0.0, s2 = 0.0;
         for (int g = 0; g < G; ++g) {
-            s1 += gS1[g * kHidden + f];
-            s2 += gS2[g * kHidden + f];
+            s1 += gS1[g * H + f];
+            s2 += gS2[g * H + f];
         }
         gG[f] = static_cast<float>(s2);
         gBeta[f] = static_cast<float>(s1);
     }
 }
 
-void gcin_backward(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
+template <int H>
+static void backward_impl(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
+    const ParamLayout &pl = host_layout(H);
     const int N = b.N, G = b.G, NT = b.NT;
-    k_head_bwd<<<G, 128, 0, s>>>(b.head, th, b.dc, b.dhead, b.dpooled); AMG_COUNT();
-    const int nhead = kNumParams - kPL.roW[0];
-    k_head_param_grad<<<grid_for(nhead), kBlock, 0, s>>>(G, b.pooled, b.head, b.dhead, b.dc, grad); AMG_COUNT();
-    const int warp_grid = grid_for((static_cast<long long>(N) + 1) / 2 * 32);   // two nodes per warp
+    k_head_bwd<H><<<G, 128, 0, s>>>(b.head, th, b.dc, b.dhead, b.dpooled); AMG_COUNT();
+    const int nhead = pl.total - pl.roW[0];
+    k_head_param_grad<H><<<grid_for(nhead), kBlock, 0, s>>>(G, b.pooled, b.head, b.dhead, b.dc, grad); AMG_COUNT();
+    constexpr int R = 32 / (H / 4);                                          // nodes per warp
+    const int warp_grid = grid_for((static_cast<long long>(N) + R - 1) / R * 32);
     for (int l = kLayers - 1; l >= 0; --l) {
-        k_bwd_relu_tile<<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.x[l], b.y[l], b.mu[l], b.rstd[l],
-                                              l == kLayers - 1 ? nullptr : b.dx, b.dpooled, b.argmax, l, b.dy,
-                                              b.tsum, b.tsum2); AMG_COUNT();
-        k_bwd_combine<<<G, kCombine, 0, s>>>(b.gtile, b.tsum, b.tsum2, b.gS1, b.gS2); AMG_COUNT();
+        k_bwd_relu_tile<H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.x[l], b.y[l], b.mu[l], b.rstd[l],
+                                                 l == kLayers - 1 ? nullptr : b.dx, b.dpooled, b.argmax, l, b.dy,
+                                                 b.tsum, b.tsum2); AMG_COUNT();
+        k_bwd_combine<H><<<G, combine_threads<H>(), 0, s>>>(b.gtile, b.tsum, b.tsum2, b.gS1, b.gS2); AMG_COUNT();
         if (l > 0) {
-            k_bwd_in_lin_tile<kHidden><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
-                                                             th + kPL.inG[l], b.gS1, b.gS2, th + kPL.convW[l],
-                                                             b.h[l], b.dy, b.dh, b.dWt, b.bf16); AMG_COUNT();
-            k_agg_plain<<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w, b.dh, b.dx); AMG_COUNT();
+            k_bwd_in_lin_tile<H, H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
+                                                          th + pl.inG[l], b.gS1, b.gS2, th + pl.convW[l], b.h[l],
+                                                          b.dy, b.dh, b.dWt, b.bf16); AMG_COUNT();
+            k_agg_plain<H><<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w, b.dh, b.dx); AMG_COUNT();
         } else {
-            k_bwd_in_lin_tile<2><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
-                                                       th + kPL.inG[l], b.gS1, b.gS2, th + kPL.convW[l], b.h1, b.dy,
-                                                       nullptr, b.dWt, 0); AMG_COUNT();
+            k_bwd_in_lin_tile<2, H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
+                                                          th + pl.inG[l], b.gS1, b.gS2, th + pl.convW[l], b.h1,
+                                                          b.dy, nullptr, b.dWt, 0); AMG_COUNT();
         }
-        const int fin = (l == 0) ? 2 : kHidden;
-        k_layer_param_partial<<<dim3(grid_for(fin * kHidden + kHidden), kGradChunks), kBlock, 0, s>>>(
-            NT, fin, b.dWt, b.dWc); AMG_COUNT();
-        k_layer_param_final<<<grid_for(fin * kHidden + 2 * kHidden), kBlock, 0, s>>>(
-            G, fin, b.dWc, b.gS1, b.gS2, grad + kPL.convW[l], grad + kPL.convB[l], grad + kPL.inG[l],
-            grad + kPL.inB[l]); AMG_COUNT();
+        const int fin = (l == 0) ? 2 : H;
+        k_layer_param_partial<H><<<dim3(grid_for(fin * H + H), kGradChunks), kBlock, 0, s>>>(NT, fin, b.dWt,
+                                                                                          b.dWc); AMG_COUNT();
+        k_layer_param_final<H><<<grid_for(fin * H + 2 * H), kBlock, 0, s>>>(
+            G, fin, b.dWc, b.gS1, b.gS2, grad + pl.convW[l], grad + pl.convB[l], grad + pl.inG[l],
+            grad + pl.inB[l]); AMG_COUNT();
     }
+}
+
+void gcin_backward(GcinBatch &b, const float *th, float *grad, cudaStream_t s) {
+    if (b.hidden == kHidden32) backward_impl<kHidden32>(b, th, grad, s);
+    else backward_impl<kHidden>(b, th, grad, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1019,6 +1112,8 @@ using namespace amg;
 struct gcin_trainer {
     int device = 0;
     int bf16 = 0;
+    int hidden = kHidden;            // GCIN width of the parameters
+    int n = kNumParams;              // parameter count
     std::string err;
     cudaStream_t stream = nullptr;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
@@ -1047,7 +1142,8 @@ extern "C" {
 int gnn_load_params(amg_ctx *c, const float *theta, long long n) {
     if (!c) return AMG_ERR_ARG;
     c->err.clear();
-    if (!theta || n != kNumParams) return ctx_fail(c, "expected 55045 parameters"), AMG_ERR_ARG;
+    const int H = hidden_of(n);
+    if (!theta || !H) return ctx_fail(c, "expected 55045 (hidden 64) or 37189 (hidden 32) parameters"), AMG_ERR_ARG;
     cudaError_t e = cudaSetDevice(c->opt.device);
     if (e != cudaSuccess) return ctx_cuda_check(c, e, "cudaSetDevice");
     if (!c->gnn) {
@@ -1059,10 +1155,11 @@ int gnn_load_params(amg_ctx *c, const float *theta, long long n) {
             return ctx_cuda_check(c, e, "cudaMalloc params");
         }
     }
-    e = cudaMemcpyAsync(c->gnn->theta, theta, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, c->stream);
+    e = cudaMemcpyAsync(c->gnn->theta, theta, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return ctx_cuda_check(c, e, "upload params");
     c->gnn->have_params = true;
+    c->gnn->hidden = H;
     return AMG_OK;
 }
 
@@ -1083,10 +1180,11 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
         g->batch_version = c->hier_version;
     }
     g->batch.bf16 = (c->opt.gnn_precision == AMG_GNN_BF16) ? 1 : 0;
+    g->batch.hidden = g->hidden;
     // forward + smoother assembly (straight from the device coefficients) run
     // as one CUDA graph, captured once per batch and arithmetic: ~40 small
     // kernels whose host launch cost would otherwise exceed their run time
-    const int key = g->batch.bf16 + 2 * c->opt.precision;
+    const int key = g->batch.bf16 + 2 * c->opt.precision + 4 * (g->hidden == kHidden32 ? 1 : 0);
     if (!g->exec || g->exec_version != g->batch_version || g->exec_key != key) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;
@@ -1172,7 +1270,7 @@ int gcin_tc_selftest(int device, int no_commit, const float *x, const float *W, 
     if (e == cudaSuccess) e = cudaMemcpy(L.W, W, sizeof(float) * kHidden * kHidden, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L.b, bias, sizeof(float) * kHidden, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_agg_lin_tc<<<1, kBlock, kTcSmem>>>(L.rp, L.col, L.w, L.x, L.W, L.b, L.ts, 2, L.h, L.y, L.tm, L.t2, L.err,
+        k_agg_lin_tc<kHidden><<<1, kBlock, tc_smem<kHidden>()>>>(L.rp, L.col, L.w, L.x, L.W, L.b, L.ts, 2, L.h, L.y, L.tm, L.t2, L.err,
                                              no_commit ? 1 : 0); AMG_COUNT();
         e = cudaGetLastError();
     }
@@ -1184,15 +1282,18 @@ int gcin_tc_selftest(int device, int no_commit, const float *x, const float *W, 
     return e == cudaSuccess ? AMG_OK : AMG_ERR_CUDA;
 }
 
-int gcin_trainer_create(gcin_trainer **out, int device, int precision, const float *theta0) {
-    if (!out || !theta0 || (precision != AMG_GNN_FP32 && precision != AMG_GNN_BF16)) return AMG_ERR_ARG;
+int gcin_trainer_create(gcin_trainer **out, int device, int precision, const float *theta0, long long n_params) {
+    if (!out || !theta0 || (precision != AMG_GNN_FP32 && precision != AMG_GNN_BF16) || !hidden_of(n_params))
+        return AMG_ERR_ARG;
     *out = nullptr;
     if (cudaSetDevice(device) != cudaSuccess) return AMG_ERR_CUDA;
     gcin_trainer *t = new gcin_trainer();
     t->device = device;
     t->bf16 = (precision == AMG_GNN_BF16) ? 1 : 0;
+    t->hidden = hidden_of(n_params);
+    t->n = static_cast<int>(n_params);
     cudaError_t e = cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking);
-    const size_t P = kNumParams;
+    const size_t P = t->n;
     const size_t fbytes = ((sizeof(float) * 4 * P + 255) / 256) * 256;
     if (e == cudaSuccess) e = cudaMalloc(&t->theta, fbytes + sizeof(double) * (kNormBlocks + 1));
     if (e != cudaSuccess) {
@@ -1232,7 +1333,7 @@ int gcin_trainer_get_params(const gcin_trainer *tc, float *theta_out) {
     if (!t || !theta_out) return AMG_ERR_ARG;
     int rc = tr_cuda(t, cudaSetDevice(t->device), "cudaSetDevice");
     if (rc) return rc;
-    rc = tr_cuda(t, cudaMemcpyAsync(theta_out, t->theta, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, t->stream),
+    rc = tr_cuda(t, cudaMemcpyAsync(theta_out, t->theta, sizeof(float) * t->n, cudaMemcpyDeviceToHost, t->stream),
                  "params download");
     if (rc) return rc;
     return tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
@@ -1258,6 +1359,7 @@ int gcin_trainer_forward(gcin_trainer *t, int n_problems, amg_ctx *const *proble
         t->versions = versions;
     }
     t->batch.bf16 = t->bf16;
+    t->batch.hidden = t->hidden;
     gcin_forward(t->batch, t->theta, t->stream);
     std::vector<float> cf(static_cast<size_t>(t->batch.G) * 5);
     int dflag = 0;
@@ -1288,9 +1390,9 @@ int gcin_trainer_backward(gcin_trainer *t, const double *dc, double *dtheta_out)
     gcin_backward(t->batch, t->theta, t->grad, t->stream);
     rc = tr_cuda(t, cudaGetLastError(), "GCIN backward");
     if (rc) return rc;
-    std::vector<float> g(kNumParams);
+    std::vector<float> g(t->n);
     if (dtheta_out) {
-        rc = tr_cuda(t, cudaMemcpyAsync(g.data(), t->grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost,
+        rc = tr_cuda(t, cudaMemcpyAsync(g.data(), t->grad, sizeof(float) * t->n, cudaMemcpyDeviceToHost,
                                         t->stream), "gradient download");
         if (rc) return rc;
     }
@@ -1310,9 +1412,9 @@ int gcin_trainer_adam_step(gcin_trainer *t, double lr, double max_norm) {
     const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
     const double bc1 = 1.0 - std::pow(b1, static_cast<double>(t->step));
     const double bc2 = 1.0 - std::pow(b2, static_cast<double>(t->step));
-    k_sq_partial_f<<<kNormBlocks, kBlock, 0, t->stream>>>(kNumParams, t->grad, t->part); AMG_COUNT();
+    k_sq_partial_f<<<kNormBlocks, kBlock, 0, t->stream>>>(t->n, t->grad, t->part); AMG_COUNT();
     k_norm_from_partials<<<1, 32, 0, t->stream>>>(kNormBlocks, t->part, t->part + kNormBlocks); AMG_COUNT();
-    k_adam<<<grid_for(kNumParams), kBlock, 0, t->stream>>>(kNumParams, t->theta, t->grad, t->m, t->v,
+    k_adam<<<grid_for(t->n), kBlock, 0, t->stream>>>(t->n, t->theta, t->grad, t->m, t->v,
                                                            t->part + kNormBlocks, max_norm, lr, b1, b2, eps, bc1,
                                                            bc2); AMG_COUNT();
     rc = tr_cuda(t, cudaGetLastError(), "adam");

@@ -9,13 +9,16 @@
 
 namespace amg {
 
-constexpr int kHidden = 64;
+constexpr int kHidden = 64;      // GCIN width of the App. A.1 network (the widest one built)
+constexpr int kHidden32 = 32;    // the halved width of App. B.3 (structured meshes)
 constexpr int kLayers = 4;
 constexpr int kRo = 32;          // readout width per layer
 constexpr int kEmb = kRo * kLayers;   // 128
-constexpr int kNumParams = 55045;
+constexpr int kNumParams = 55045;     // hidden 64
+constexpr int kNumParams32 = 37189;   // hidden 32
 
-// Offsets of each tensor in the flat parameter vector (App. A.1 layout).
+// Offsets of each tensor in the flat parameter vector (App. A.1 layout; a
+// width H replaces every GCIN width 64, the readout input being 2H).
 struct ParamLayout {
     int convW[kLayers], convB[kLayers];
     int inG[kLayers], inB[kLayers];
@@ -25,20 +28,20 @@ struct ParamLayout {
     int total;
 };
 
-constexpr ParamLayout make_layout() {
+constexpr ParamLayout make_layout(int H) {
     ParamLayout p{};
     int o = 0;
     for (int l = 0; l < kLayers; ++l) {
-        const int fin = (l == 0) ? 2 : kHidden;
-        p.convW[l] = o; o += fin * kHidden;
-        p.convB[l] = o; o += kHidden;
+        const int fin = (l == 0) ? 2 : H;
+        p.convW[l] = o; o += fin * H;
+        p.convB[l] = o; o += H;
     }
     for (int l = 0; l < kLayers; ++l) {
-        p.inG[l] = o; o += kHidden;
-        p.inB[l] = o; o += kHidden;
+        p.inG[l] = o; o += H;
+        p.inB[l] = o; o += H;
     }
     for (int l = 0; l < kLayers; ++l) {
-        p.roW[l] = o; o += 2 * kHidden * kRo;
+        p.roW[l] = o; o += 2 * H * kRo;
         p.roB[l] = o; o += kRo;
     }
     p.lnG = o; o += kEmb;
@@ -52,8 +55,13 @@ constexpr ParamLayout make_layout() {
     p.total = o;
     return p;
 }
-constexpr ParamLayout kPL = make_layout();
+constexpr ParamLayout kPL = make_layout(kHidden);
+constexpr ParamLayout kPL32 = make_layout(kHidden32);
 static_assert(kPL.total == kNumParams, "GCIN layout must have 55,045 parameters (App. A.1)");
+static_assert(kPL32.total == kNumParams32, "hidden-32 GCIN layout has 37,189 parameters");
+inline const ParamLayout &host_layout(int H) { return H == kHidden32 ? kPL32 : kPL; }
+// GCIN width of a parameter vector of n entries (0 if none matches)
+inline int hidden_of(long long n) { return n == kNumParams ? kHidden : n == kNumParams32 ? kHidden32 : 0; }
 
 // Batch graph (Algorithm 1 steps 1-5): disjoint union of level graphs with
 // node ranges gptr[g] .. gptr[g+1] and edges = the concatenated CSR patterns.
@@ -64,8 +72,11 @@ constexpr int kTile = 64;
 constexpr int kChunkTiles = 64;
 constexpr int kGradChunks = 64;      // tile chunks of the weight-gradient reduction
 
+// Per-node and per-tile buffers are sized for the widest network (64) and
+// indexed with the width of the parameters in use (`hidden`).
 struct GcinBatch {
     int G = 0, N = 0, NT = 0;            // graphs, nodes, tiles
+    int hidden = kHidden;                // GCIN width H of the parameters (64 or 32)
     int bf16 = 0;                        // layers 2..4 on tensor cores (BF16 operands, FP32 accumulation)
     int *err = nullptr;                  // device error flag (tensor-core wait timeout)
     long long E = 0;
@@ -75,35 +86,35 @@ struct GcinBatch {
     // reductions run tiles -> chunks -> graph, every stage in parallel
     int NC = 0;
     int *ctile = nullptr, *cnode = nullptr, *gchunk = nullptr;      // chunk -> first tile / node; graph -> first chunk
-    float *cmean = nullptr, *cm2 = nullptr, *cmax = nullptr;        // NC x 64 chunk statistics
-    double *csum = nullptr;                                         // NC x 64
-    int *carg = nullptr;                                            // NC x 64
+    float *cmean = nullptr, *cm2 = nullptr, *cmax = nullptr;        // NC x H chunk statistics
+    double *csum = nullptr;                                         // NC x H
+    int *carg = nullptr;                                            // NC x H
     float *w = nullptr;
     double *w64 = nullptr;
     // activations (kept for the backward pass)
     double *x0 = nullptr;                // N x 2 raw features [a_ii, deg] (FP64)
     float *h1 = nullptr;                 // N x 2      layer-1 aggregation
-    float *h[kLayers] = {};              // N x 64     layers 2..4 aggregation (h[0] unused)
-    float *y[kLayers] = {};              // N x 64     linear outputs
-    float *x[kLayers] = {};              // N x 64     ReLU(IN(y))
-    float *mu[kLayers] = {}, *rstd[kLayers] = {};   // G x 64
-    float *tmean = nullptr, *tm2 = nullptr;          // NT x 64 tile statistics of y
-    double *tsum = nullptr;                          // NT x 64 tile sums (pooling / backward)
-    double *tsum2 = nullptr;                         // NT x 64 second tile sums (backward)
-    float *tmax = nullptr;                           // NT x 64
-    int *targ = nullptr;                             // NT x 64
-    float *pooled = nullptr;             // G x 4 x 128 (mean | max per layer)
-    int *argmax = nullptr;               // G x 4 x 64  node index of each max
+    float *h[kLayers] = {};              // N x H      layers 2..4 aggregation (h[0] unused)
+    float *y[kLayers] = {};              // N x H      linear outputs
+    float *x[kLayers] = {};              // N x H      ReLU(IN(y))
+    float *mu[kLayers] = {}, *rstd[kLayers] = {};   // G x H
+    float *tmean = nullptr, *tm2 = nullptr;          // NT x H tile statistics of y
+    double *tsum = nullptr;                          // NT x H tile sums (pooling / backward)
+    double *tsum2 = nullptr;                         // NT x H second tile sums (backward)
+    float *tmax = nullptr;                           // NT x H
+    int *targ = nullptr;                             // NT x H
+    float *pooled = nullptr;             // G x 4 x 2H (mean | max per layer)
+    int *argmax = nullptr;               // G x 4 x H   node index of each max
     float *head = nullptr;               // G x head scratch
     float *c = nullptr;                  // G x 5
     // backward work
     float *dc = nullptr;                 // G x 5
     float *dhead = nullptr;              // G x (dz1 128 | dz2 64 | dzh 128 | dz 128)
-    float *dpooled = nullptr;            // G x 4 x 128
-    float *dx = nullptr, *dh = nullptr, *dy = nullptr;   // N x 64
-    double *gS1 = nullptr, *gS2 = nullptr;               // G x 64 per-graph sums
-    float *dWt = nullptr;                // NT x (64 x 64 + 64) per-tile weight/bias gradient partials
-    double *dWc = nullptr;               // kGradChunks x (64 x 64 + 64) chunk sums of dWt
+    float *dpooled = nullptr;            // G x 4 x 2H
+    float *dx = nullptr, *dh = nullptr, *dy = nullptr;   // N x H
+    double *gS1 = nullptr, *gS2 = nullptr;               // G x H per-graph sums
+    float *dWt = nullptr;                // NT x (H x H + H) per-tile weight/bias gradient partials
+    double *dWc = nullptr;               // kGradChunks x (H x H + H) chunk sums of dWt
     char *arena = nullptr;
     size_t bytes = 0;
 };
@@ -113,9 +124,11 @@ void gcin_batch_free(GcinBatch &b);
 // (with the backward buffers when `backward` is set).
 int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cudaStream_t s, std::string &err,
                      bool backward);
-// Forward pass on the batch with parameters theta (device, 55,045 floats).
+// Forward pass on the batch with parameters theta (device; 55,045 floats for
+// b.hidden = 64, 37,189 for 32).
 void gcin_forward(GcinBatch &b, const float *theta, cudaStream_t s);
-// Backward from b.dc (device, G x 5) into grad (device, 55,045 floats, overwritten).
+// Backward from b.dc (device, G x 5) into grad (device, one float per
+// parameter of width b.hidden, overwritten).
 void gcin_backward(GcinBatch &b, const float *theta, float *grad, cudaStream_t s);
 
 // Per-graph head scratch floats (activations kept for backward).
@@ -123,8 +136,9 @@ constexpr int kHeadScratch = kEmb /*z*/ + kEmb /*zhat*/ + kEmb /*sig*/ + 128 /*a
 constexpr int kHeadGrad = 128 /*dz1*/ + 64 /*dz2*/ + kEmb /*dzh*/ + kEmb /*dz*/;
 
 struct GcinEngine {
-    float *theta = nullptr;
+    float *theta = nullptr;              // room for the widest network
     bool have_params = false;
+    int hidden = kHidden;                // width of the loaded parameters
     GcinBatch batch;
     long long batch_version = -1;   // hierarchy version the batch was built from
     // inference + smoother assembly captured once per batch and arithmetic

@@ -1,14 +1,14 @@
 // Tensor-core (tcgen05, sm_103a) form of the GCIN aggregation + node linear
-// for layers 2..4 (Eq. GCN, App. A.1): BF16 operands, FP32 accumulation in
-// tensor memory.  One CTA owns two consecutive statistic tiles of at most 64
-// nodes each (a graph's last tile is ragged; up to 128 nodes = one M = 128
-// MMA tile):
-//   1. warps aggregate h_i = sum_j w_ij x_j (FP32, two rows per warp) and
-//      store h in BF16 into the A tile (128 x 64, K-major, canonical
-//      no-swizzle core-matrix layout);
-//      W^T goes to the B tile (64 x 64, K-major) in BF16;
-//   2. one thread issues 4 x tcgen05.mma.kind::f16 (M 128, N 64, K 16) into a
-//      64-column TMEM accumulator and commits to an mbarrier;
+// for layers 2..4 (Eq. GCN, App. A.1), for a GCIN width H of 64 or 32
+// (App. B.3): BF16 operands, FP32 accumulation in tensor memory.  One CTA
+// owns two consecutive statistic tiles of at most 64 nodes each (a graph's
+// last tile is ragged; up to 128 nodes = one M = 128 MMA tile):
+//   1. warps aggregate h_i = sum_j w_ij x_j (FP32, 32 / (H / 4) rows per
+//      warp) and store h in BF16 into the A tile (128 x H, K-major,
+//      canonical no-swizzle core-matrix layout);
+//      W^T goes to the B tile (H x H, K-major) in BF16;
+//   2. one thread issues H / 16 x tcgen05.mma.kind::f16 (M 128, N H, K 16)
+//      into an H-column TMEM accumulator and commits to an mbarrier;
 //   3. warps 0..3 read their 32 TMEM lanes (rows) with tcgen05.ld, add the
 //      bias, and the CTA writes y and the two tiles' mean / M2 statistics.
 // The mbarrier wait is bounded; on timeout the kernel raises an error flag,
@@ -23,30 +23,40 @@
 namespace amg {
 
 constexpr int kTcRows = 128;                       // MMA M
-constexpr int kTcA = kTcRows * kHidden * 2;        // 16 KB BF16 A tile
-constexpr int kTcB = kHidden * kHidden * 2;        //  8 KB BF16 B tile
-constexpr int kTcY = kTcRows * (kHidden + 1) * 4;  // FP32 staging of y, reusing the operand tiles
-constexpr int kTcSmem = (kTcA + kTcB > kTcY) ? kTcA + kTcB : kTcY;
+template <int H> constexpr int tc_a_bytes() { return kTcRows * H * 2; }        // BF16 A tile (16 / 8 KB)
+template <int H> constexpr int tc_b_bytes() { return H * H * 2; }              // BF16 B tile (8 / 2 KB)
+template <int H> constexpr int tc_y_bytes() { return kTcRows * (H + 1) * 4; }  // FP32 staging of y over the operands
+template <int H> constexpr int tc_smem() {
+    return (tc_a_bytes<H>() + tc_b_bytes<H>() > tc_y_bytes<H>()) ? tc_a_bytes<H>() + tc_b_bytes<H>() : tc_y_bytes<H>();
+}
+// 8-row groups of a K-major tile of H-wide BF16 rows are H / 8 core matrices of 128 B apart
+template <int H> constexpr uint32_t tc_sbo() { return static_cast<uint32_t>(H / 8) * 128u; }
 
-// Byte offset of element (row, k) in a K-major, no-swizzle tile of 64-wide
+// Byte offset of element (row, k) in a K-major, no-swizzle tile of H-wide
 // BF16 rows: core matrices of 8 rows x 16 bytes, K-adjacent cores 128 B
-// apart (leading-dimension offset), 8-row groups 1024 B apart (stride offset).
+// apart (leading-dimension offset), 8-row groups tc_sbo<H>() apart (stride
+// offset: 1024 B for H = 64, 512 B for H = 32).
+template <int H>
 __device__ __forceinline__ uint32_t tc_off(int row, int k) {
-    return static_cast<uint32_t>((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+    return static_cast<uint32_t>((row >> 3) * tc_sbo<H>() + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
 // tcgen05 shared-memory matrix descriptor for that layout.
+template <int H>
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);        // start address
     d |= static_cast<uint64_t>(128u >> 4) << 16;                // leading-dimension byte offset (K)
-    d |= static_cast<uint64_t>(1024u >> 4) << 32;               // stride-dimension byte offset (rows)
+    d |= static_cast<uint64_t>(tc_sbo<H>() >> 4) << 32;         // stride-dimension byte offset (rows)
     d |= static_cast<uint64_t>(1u) << 46;                       // fixed 0b001
     return d;                                                   // base offset 0, no swizzle
 }
 
-// Instruction descriptor: D F32, A BF16, B BF16, both K-major, N = 64, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kHidden >> 3) << 17) | ((kTcRows >> 4) << 24);
+// Instruction descriptor: D F32, A BF16, B BF16, both K-major, N = H, M = 128.
+template <int H>
+constexpr uint32_t tc_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(H >> 3) << 17) | ((kTcRows >> 4) << 24);
+}
 
 __device__ __forceinline__ bool tc_try_wait(uint32_t mbar) {
     uint32_t ok;
@@ -65,6 +75,7 @@ __device__ __forceinline__ bool tc_wait_bounded(uint32_t mbar) {
     return false;
 }
 
+template <int H>
 __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict__ rp, const int *__restrict__ col,
                                                        const float *__restrict__ w, const float *__restrict__ x,
                                                        const float *__restrict__ W, const float *__restrict__ bias,
@@ -73,9 +84,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
                                                        float *__restrict__ tmean, float *__restrict__ tm2,
                                                        int *__restrict__ err, int no_commit) {
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    unsigned char *sA = tc_smem, *sB = tc_smem + kTcA;
+    static_assert(H == 64 || H == 32, "GCIN widths with a tensor-core form: 64, 32");
+    constexpr int L = H / 4, R = 32 / L;       // lanes per aggregated row, rows per warp
+    constexpr uint32_t kCols = H;              // TMEM accumulator columns (a power of two >= 32)
+    unsigned char *sA = tc_smem, *sB = tc_smem + tc_a_bytes<H>();
     // y is staged over the A / B tiles once the MMAs that read them have completed
-    float(*sY)[kHidden + 1] = reinterpret_cast<float(*)[kHidden + 1]>(tc_smem);
+    float(*sY)[H + 1] = reinterpret_cast<float(*)[H + 1]>(tc_smem);
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ int s_ok;
@@ -85,7 +99,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     const uint32_t mbar = static_cast<uint32_t>(__cvta_generic_to_shared(&s_mbar));
     if (warp == 0) {
         const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&s_taddr));
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(64u) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(kCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
@@ -93,30 +107,30 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // B = W^T (row n = output feature, k = input feature), BF16
-    for (int e = threadIdx.x; e < kHidden * kHidden; e += kBlock) {
-        const int k = e / kHidden, n = e % kHidden;
-        *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off(n, k)) = __float2bfloat16_rn(W[e]);
+    for (int e = threadIdx.x; e < H * H; e += kBlock) {
+        const int k = e / H, n = e % H;
+        *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off<H>(n, k)) = __float2bfloat16_rn(W[e]);
     }
     // A = h of the (up to) 128 nodes of tiles 2b, 2b + 1, BF16
     const int t0 = 2 * blockIdx.x;
     const int t1 = min(t0 + 2, NT);
     const int a0 = tstart[t0], nn = tstart[t1] - a0;
     const float4 *x4 = reinterpret_cast<const float4 *>(x);
-    const int half = lane / 16, hl = lane % 16;
-    for (int k0 = 2 * warp; k0 < kTcRows; k0 += 2 * (kBlock / 32)) {
-        const int k = k0 + half;
+    const int grp = lane / L, hl = lane % L;
+    for (int k0 = R * warp; k0 < kTcRows; k0 += R * (kBlock / 32)) {
+        const int k = k0 + grp;
         const bool live = k < nn;
         const int i = a0 + (live ? k : 0);
         const int p0 = live ? rp[i] : 0, p1 = live ? rp[i + 1] : 0;
-        const float4 hv = agg_row64_pair(p0, p1, col, w, x4, hl);   // zero for rows past the tiles
+        const float4 hv = agg_rows<H>(p0, p1, col, w, x4, hl);     // zero for rows past the tiles
         const __nv_bfloat162 lo = __floats2bfloat162_rn(hv.x, hv.y), hi = __floats2bfloat162_rn(hv.z, hv.w);
         if (live) {   // the rounded h the MMA sees (kept for the backward)
             const float2 rl = __bfloat1622float2(lo), rh = __bfloat1622float2(hi);
-            reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * 16 + hl] = make_float4(rl.x, rl.y, rh.x, rh.y);
+            reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * L + hl] = make_float4(rl.x, rl.y, rh.x, rh.y);
         }
         // features 4 hl .. 4 hl + 3 are contiguous within one core matrix row
-        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off(k, 4 * hl)) = lo;
-        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off(k, 4 * hl + 2)) = hi;
+        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off<H>(k, 4 * hl)) = lo;
+        *reinterpret_cast<__nv_bfloat162 *>(sA + tc_off<H>(k, 4 * hl + 2)) = hi;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -125,10 +139,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     const uint32_t taddr = s_taddr;
     // no_commit (self-test only) issues nothing, so the bounded wait below runs out
     if (threadIdx.x == 0 && !no_commit) {
-        for (int ks = 0; ks < kHidden / 16; ++ks) {
-            const uint64_t ad = tc_desc(a_addr + ks * 256), bd = tc_desc(b_addr + ks * 256);
+        for (int ks = 0; ks < H / 16; ++ks) {
+            const uint64_t ad = tc_desc<H>(a_addr + ks * 256), bd = tc_desc<H>(b_addr + ks * 256);
             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                         ::"r"(taddr), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(static_cast<uint32_t>(ks))
+                         ::"r"(taddr), "l"(ad), "l"(bd), "r"(tc_idesc<H>()), "r"(static_cast<uint32_t>(ks))
                          : "memory");
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
@@ -142,7 +156,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
         // warp w reads TMEM lanes 32 w .. 32 w + 31 (its rows), 32 columns at a time
         const int row = 32 * warp + lane;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int half = 0; half < H / 32; ++half) {
             uint32_t r[32];
             const uint32_t ta = taddr + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(32 * half);
             asm volatile(
@@ -165,20 +179,20 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(64u) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols) : "memory");
     if (!all_ok) return;
     // y (coalesced) and the statistics of the two 64-node tiles
-    for (int e = threadIdx.x; e < nn * kHidden; e += kBlock) {
-        const int k = e / kHidden, f = e % kHidden;
-        y[static_cast<size_t>(a0 + k) * kHidden + f] = sY[k][f];
+    for (int e = threadIdx.x; e < nn * H; e += kBlock) {
+        const int k = e / H, f = e % H;
+        y[static_cast<size_t>(a0 + k) * H + f] = sY[k][f];
     }
     // the first tile may be a graph's ragged last tile: split at tstart[t0 + 1]
     const int n0 = tstart[t0 + 1] - a0;
-    tile_stats(sY, n0, tmean + static_cast<size_t>(t0) * kHidden, tm2 + static_cast<size_t>(t0) * kHidden);
+    tile_stats<H>(sY, n0, tmean + static_cast<size_t>(t0) * H, tm2 + static_cast<size_t>(t0) * H);
     if (t0 + 1 < t1) {
         __syncthreads();
-        tile_stats(sY + n0, nn - n0, tmean + static_cast<size_t>(t0 + 1) * kHidden,
-                   tm2 + static_cast<size_t>(t0 + 1) * kHidden);
+        tile_stats<H>(sY + n0, nn - n0, tmean + static_cast<size_t>(t0 + 1) * H,
+                      tm2 + static_cast<size_t>(t0 + 1) * H);
     }
 }
 

@@ -16,6 +16,12 @@ meshes of aspect ratio up to 1000 and 16 small airfoil meshes:
 
     python -m paper_2606_19251_gb300.weights.make_weights --extra-band1000 16 --extra-airfoil 16 \
         --out paper_2606_19251_gb300/weights/gcin_wide.npy
+
+gcin_c3_h32.npy is the halved GCIN width of App. B.3 (37,189 parameters)
+trained on the same C3 batch:
+
+    python -m paper_2606_19251_gb300.weights.make_weights --hidden 32 \
+        --out paper_2606_19251_gb300/weights/gcin_c3_h32.npy
 """
 import argparse
 import json
@@ -44,6 +50,7 @@ def main():
                     help="add this many small airfoil meshes (wall layers from 1e-5 chords)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="arithmetic of the forward node linears during training")
+    ap.add_argument("--hidden", type=int, default=64, choices=[64, 32], help="GCIN width (App. A.1: 64; App. B.3: 32)")
     ap.add_argument("--out", default=os.path.join(HERE, "gcin_c3.npy"))
     args = ap.parse_args()
     import workloads as W
@@ -60,7 +67,7 @@ def main():
     for k in range(args.extra_airfoil):
         mats.append(W.c5_problem(8000 + k, n_rhs=1, n_surface=160, n_far=4000 + 500 * k)[0])
     print(f"meshes ready in {time.time() - t0:.1f}s: n = {[m.n_rows for m in mats[:8]]}...", flush=True)
-    theta0 = W.gcin_init_params(0)
+    theta0 = W.gcin_init_params(0, hidden=args.hidden)
     from paper_2606_19251_gb300 import api as P
     prec = P.AMG_GNN_BF16 if args.precision == "bf16" else P.AMG_GNN_FP32
     best, rows = train(mats, val, theta0, epochs=args.epochs, batch=args.batch, n_vc=args.nvc,
@@ -69,7 +76,7 @@ def main():
     with open(os.path.splitext(args.out)[0] + "_log.json", "w") as f:
         json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "n_vc": args.nvc,
                    "extra_band1000": args.extra_band1000, "extra_airfoil": args.extra_airfoil,
-                   "precision": args.precision,
+                   "precision": args.precision, "hidden": args.hidden,
                    "val_cycles": args.val_cycles, "rows": rows,
                    "seconds": time.time() - t0}, f, indent=1)
     print("wrote", args.out, flush=True)
