@@ -24,16 +24,28 @@ theta = 0.25", Sec. 4, and "at most 10 levels", Table train_hyper):
 * stop coarsening when n <= max_coarse, when the hierarchy has max_levels
   levels, or when a coarse level would keep more than 90% of the points (or
   none).
+
+Parallel split (device setup; not the paper's coarsening, which is RS): PMIS
+of De Sterck, Yang and Heys (2006), on the same strength graph.  Measure
+lambda_i = |S_i^T| + r_i with r_i in [0, 1) the level's random numbers
+(an input: splitmix64 doubles, workloads.uniform01(seed + level, n_l)), summed
+in FP64.  Points that strongly influence no point (|S_i^T| = 0) start as F.
+Each round, over the undecided points U and using the states at the start of
+the round: i joins C when it beats every undecided j in S_i u S_i^T
+(lambda_i > lambda_j, ties to the lower index); then every undecided point
+with a strong dependency among the new C points becomes F.  Rounds repeat
+until no point is undecided.  Interpolation and Galerkin product as for RS.
 """
 from __future__ import annotations
 
 import heapq
 from dataclasses import dataclass
+from itertools import chain
 
 import numpy as np
 import scipy.sparse as sp
 
-from workloads import CSR
+from workloads import CSR, uniform01
 
 F_PT, C_PT, U_PT = 0, 1, -1
 
@@ -92,6 +104,28 @@ def rs_split(n: int, S, ST) -> np.ndarray:
             if state[k] == U_PT:
                 lam[k] -= 1
                 heapq.heappush(heap, (-int(lam[k]), int(k)))
+    return (state == C_PT).astype(np.int64)
+
+
+def pmis_split(n: int, S, ST, r) -> np.ndarray:
+    """PMIS C/F split with random numbers r (n doubles in [0, 1)); 1 for C, 0 for F."""
+    state = np.full(n, U_PT, dtype=np.int64)
+    lam = [float(len(ST[i])) + float(r[i]) for i in range(n)]
+    for i in range(n):
+        if len(ST[i]) == 0:
+            state[i] = F_PT
+
+    def beats(i, j):
+        return lam[i] > lam[j] or (lam[i] == lam[j] and i < j)
+
+    while (state == U_PT).any():
+        new_c = {i for i in range(n) if state[i] == U_PT and
+                 all(beats(i, int(j)) for j in chain(S[i], ST[i]) if state[j] == U_PT)}
+        for j in range(n):
+            if state[j] == U_PT and j not in new_c and any(int(k) in new_c for k in S[j]):
+                state[j] = F_PT
+        for i in new_c:
+            state[i] = C_PT
     return (state == C_PT).astype(np.int64)
 
 
@@ -177,13 +211,19 @@ class Level:
     split: np.ndarray | None = None
 
 
-def build_hierarchy(A: CSR, theta: float = 0.25, max_levels: int = 10, max_coarse: int = 64):
-    """Setup-AMG-Hierarchy of Algorithm 1: list of Level, finest first."""
+def build_hierarchy(A: CSR, theta: float = 0.25, max_levels: int = 10, max_coarse: int = 64,
+                    coarsening: str = "rs", seed: int = 0):
+    """Setup-AMG-Hierarchy of Algorithm 1: list of Level, finest first.
+    coarsening "rs" (the paper's) or "pmis" (level l draws its random numbers
+    from uniform01(seed + l, n_l))."""
     levels = [Level(A)]
     while len(levels) < max_levels and levels[-1].A.n_rows > max_coarse:
         Al = levels[-1].A
         S, ST = strength(Al, theta)
-        split = rs_split(Al.n_rows, S, ST)
+        if coarsening == "pmis":
+            split = pmis_split(Al.n_rows, S, ST, uniform01(seed + len(levels) - 1, Al.n_rows))
+        else:
+            split = rs_split(Al.n_rows, S, ST)
         nc = int(split.sum())
         if nc == 0 or nc > 0.9 * Al.n_rows:
             break

@@ -116,3 +116,88 @@ def test_hierarchy_stopping_rules():
     assert len(lv2) == 3
     small = W.poisson5(8)
     assert len(S.build_hierarchy(small, max_coarse=64)) == 1
+
+
+# ---------------------------------------------------------------------------
+# PMIS split (device setup)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("increasing", [True, False])
+def test_pmis_1d_wavefront_closed_form(increasing):
+    # 1-D Laplacian, n = 16: interior measures 2 + r_i, end points 1 + r_i.
+    # With r increasing only the last interior point is a local maximum, and
+    # each round moves the C front two points down: C = {14, 12, ..., 2}, then
+    # point 0 is left with no undecided neighbour and joins C.  With r
+    # decreasing the front runs upward: C = {1, 3, ..., 13}, then 15.
+    n = 16
+    A = lap1d(n)
+    Sg, ST = S.strength(A, 0.25)
+    r = np.arange(n) / (2.0 * n)
+    split = S.pmis_split(n, Sg, ST, r if increasing else r[::-1].copy())
+    expect = np.arange(0, n, 2) if increasing else np.arange(1, n, 2)
+    assert np.array_equal(np.nonzero(split)[0], expect)
+
+
+def _greedy_mis(n, Sg, ST, lam):
+    """Sequential greedy maximal independent set in decreasing (lambda, -index)
+    order, points with no strong dependent excluded from the start."""
+    state = np.full(n, -1)
+    for i in range(n):
+        if len(ST[i]) == 0:
+            state[i] = 0
+    for i in sorted(range(n), key=lambda k: (-lam[k], k)):
+        if state[i] != -1:
+            continue
+        state[i] = 1
+        for j in list(Sg[i]) + list(ST[i]):
+            if state[j] == -1:
+                state[j] = 0
+    return (state == 1).astype(np.int64)
+
+
+@pytest.mark.parametrize("make", [lambda: W.poisson5(40), lambda: W.poisson7(12)])
+def test_pmis_equals_sequential_greedy_mis_on_symmetric_strength(make):
+    # With a symmetric strength graph and fixed priorities, the round-parallel
+    # selection reaches exactly the greedy MIS taken in priority order.
+    A = make()
+    Sg, ST = S.strength(A, 0.25)
+    assert all(set(Sg[i]) == set(ST[i]) for i in range(A.n_rows))
+    r = W.uniform01(3, A.n_rows)
+    lam = [len(ST[i]) + r[i] for i in range(A.n_rows)]
+    assert np.array_equal(S.pmis_split(A.n_rows, Sg, ST, r), _greedy_mis(A.n_rows, Sg, ST, lam))
+
+
+@pytest.mark.parametrize("kind", ["uniform", "graded", "band"])
+def test_pmis_split_properties(kind):
+    # every F point either influences no point or strongly depends on a C
+    # point; no point depends strongly on a C point chosen before it became C
+    # (in particular no C point depends strongly on a C point it is
+    # symmetric-strongly tied to); the split changes with the random numbers
+    A, _ = W.fv_mesh(kind, 1500, 5, max_aspect=100.0)
+    n = A.n_rows
+    Sg, ST = S.strength(A, 0.25)
+    split = S.pmis_split(n, Sg, ST, W.uniform01(1, n))
+    for i in range(n):
+        if split[i] == 0:
+            assert len(ST[i]) == 0 or any(split[j] == 1 for j in Sg[i])
+        else:
+            both = set(int(j) for j in Sg[i]) & set(int(j) for j in ST[i])
+            assert not any(split[j] == 1 for j in both)
+    assert 0.1 * n < split.sum() < 0.6 * n
+    assert not np.array_equal(split, S.pmis_split(n, Sg, ST, W.uniform01(2, n)))
+
+
+def test_pmis_hierarchy_galerkin_and_convergence():
+    A, _ = W.fv_mesh("graded", 1500, 4)
+    lv = S.build_hierarchy(A, max_coarse=20, coarsening="pmis", seed=5)
+    assert len(lv) >= 3
+    for l in range(len(lv) - 1):
+        Ad, Pd = lv[l].A.to_dense(), lv[l].P.to_dense()
+        np.testing.assert_allclose(lv[l + 1].A.to_dense(), Pd.T @ Ad @ Pd, rtol=0, atol=1e-12 * np.abs(Ad).max())
+        # level l drew its random numbers from seed + l
+        Sg, ST = S.strength(lv[l].A, 0.25)
+        assert np.array_equal(lv[l].split, S.pmis_split(lv[l].A.n_rows, Sg, ST, W.uniform01(5 + l, lv[l].A.n_rows)))
+    from oracle import solve as O
+    h = O.OHierarchy.of(lv)
+    h.set_jacobi()
+    res = O.solve(h, W.rhs_uniform(0, A.n_rows), tol=1e-8)
+    assert res.status == O.OK and res.n_vcycles < 200
