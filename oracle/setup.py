@@ -35,6 +35,16 @@ the round: i joins C when it beats every undecided j in S_i u S_i^T
 (lambda_i > lambda_j, ties to the lower index); then every undecided point
 with a strong dependency among the new C points becomes F.  Rounds repeat
 until no point is undecided.  Interpolation and Galerkin product as for RS.
+
+Optional second pass after PMIS (coarsening "pmis-h1"), a round-parallel form
+of the RS second pass: a pair (i, j) of F points with j in S_i violates when
+no C point is a strong dependency of both (S_i n S_j n C empty).  Each
+round counts v_j, the violating pairs whose second point is j, and every j
+with v_j > 0 that beats each such candidate in S_j u S_j^T (measure v + r
+with the level's random numbers, ties to the lower index) becomes C; rounds
+repeat until no pair violates.  Afterwards every strong F-F connection has a
+common strong C point, the property classical interpolation formulas rely
+on (denser coarse levels, faster convergence with direct interpolation).
 """
 from __future__ import annotations
 
@@ -129,6 +139,28 @@ def pmis_split(n: int, S, ST, r) -> np.ndarray:
     return (state == C_PT).astype(np.int64)
 
 
+def second_pass(n: int, S, ST, split, r) -> np.ndarray:
+    """Round-parallel second pass (see the module notes); returns the new split."""
+    split = np.array(split, dtype=np.int64, copy=True)
+    while True:
+        C = split == C_PT
+        cs = [set(int(k) for k in S[i] if C[k]) for i in range(n)]
+        v = np.zeros(n, dtype=np.int64)
+        for i in range(n):
+            if C[i]:
+                continue
+            for j in S[i]:
+                j = int(j)
+                if not C[j] and not (cs[i] & cs[j]):
+                    v[j] += 1
+        if not v.any():
+            return split
+        w = [float(v[j]) + float(r[j]) for j in range(n)]
+        promote = [j for j in range(n) if v[j] > 0 and
+                   all(v[k] == 0 or w[j] > w[k] or (w[j] == w[k] and j < k) for k in chain(S[j], ST[j]))]
+        split[promote] = C_PT
+
+
 def direct_interpolation(A: CSR, S, split: np.ndarray) -> CSR:
     """Direct interpolation P (n x n_c); C points map to themselves."""
     n = A.n_rows
@@ -214,14 +246,18 @@ class Level:
 def build_hierarchy(A: CSR, theta: float = 0.25, max_levels: int = 10, max_coarse: int = 64,
                     coarsening: str = "rs", seed: int = 0):
     """Setup-AMG-Hierarchy of Algorithm 1: list of Level, finest first.
-    coarsening "rs" (the paper's) or "pmis" (level l draws its random numbers
-    from uniform01(seed + l, n_l))."""
+    coarsening "rs" (the paper's), "pmis" or "pmis-h1" (PMIS then the
+    second pass; level l draws its random numbers from
+    uniform01(seed + l, n_l) for both)."""
     levels = [Level(A)]
     while len(levels) < max_levels and levels[-1].A.n_rows > max_coarse:
         Al = levels[-1].A
         S, ST = strength(Al, theta)
-        if coarsening == "pmis":
-            split = pmis_split(Al.n_rows, S, ST, uniform01(seed + len(levels) - 1, Al.n_rows))
+        if coarsening in ("pmis", "pmis-h1"):
+            r = uniform01(seed + len(levels) - 1, Al.n_rows)
+            split = pmis_split(Al.n_rows, S, ST, r)
+            if coarsening == "pmis-h1":
+                split = second_pass(Al.n_rows, S, ST, split, r)
         else:
             split = rs_split(Al.n_rows, S, ST)
         nc = int(split.sum())

@@ -201,3 +201,50 @@ def test_pmis_hierarchy_galerkin_and_convergence():
     h.set_jacobi()
     res = O.solve(h, W.rhs_uniform(0, A.n_rows), tol=1e-8)
     assert res.status == O.OK and res.n_vcycles < 200
+
+
+def test_second_pass_hand_case():
+    # 1-D Laplacian on 4 points with C = {0}: pairs (1,2) and (2,1) share no
+    # strong C point, nor do (2,3) and (3,2), so v = (0, 1, 2, 1); point 2
+    # has the largest measure and becomes C, after which every F point's
+    # strong neighbours are C: the result is C = {0, 2} for any r in [0, 1).
+    A = lap1d(4)
+    Sg, ST = S.strength(A, 0.25)
+    for r in (np.zeros(4), np.array([0.9, 0.8, 0.1, 0.95])):
+        out = S.second_pass(4, Sg, ST, np.array([1, 0, 0, 0]), r)
+        assert np.array_equal(out, [1, 0, 1, 0])
+
+
+@pytest.mark.parametrize("make", [lambda: W.poisson5(48), lambda: W.fv_mesh("graded", 2000, 4)[0],
+                                  lambda: W.fv_mesh("band", 2000, 5, max_aspect=100.0)[0]])
+def test_second_pass_establishes_common_c_points(make):
+    # brute force: after the pass every strong F-F connection has a common
+    # strong C point; the PMIS C points stay C; a second application changes
+    # nothing; the pass acted on these meshes
+    A = make()
+    n = A.n_rows
+    Sg, ST = S.strength(A, 0.25)
+    r = W.uniform01(9, n)
+    s0 = S.pmis_split(n, Sg, ST, r)
+    s1 = S.second_pass(n, Sg, ST, s0, r)
+    assert np.all(s1[s0 == 1] == 1) and s1.sum() > s0.sum()
+    Cs = [set(int(k) for k in Sg[i] if s1[k]) for i in range(n)]
+    for i in range(n):
+        if s1[i] == 0:
+            for j in Sg[i]:
+                if s1[j] == 0:
+                    assert Cs[i] & Cs[int(j)], (i, j)
+    assert np.array_equal(S.second_pass(n, Sg, ST, s1, r), s1)
+
+
+def test_second_pass_hierarchy_converges_faster_than_pmis():
+    A, _ = W.fv_mesh("graded", 3000, 4)
+    from oracle import solve as O
+    cyc = {}
+    for mode in ("pmis", "pmis-h1"):
+        h = O.OHierarchy.of(S.build_hierarchy(A, coarsening=mode, seed=2))
+        h.set_jacobi()
+        res = O.solve(h, W.rhs_uniform(1, A.n_rows), tol=1e-8)
+        assert res.status == O.OK
+        cyc[mode] = res.n_vcycles
+    assert cyc["pmis-h1"] < 0.5 * cyc["pmis"], cyc
