@@ -84,6 +84,7 @@ def _declare(L):
         "amg_destroy": (V, [P]),
         "amg_last_error": (C.c_char_p, [P]),
         "amg_setup": (I, [P, C.POINTER(amg_csr)]),
+        "amg_setup_device": (I, [P, C.POINTER(amg_csr), C.c_ulonglong, I]),
         "amg_load_hierarchy": (I, [P, I, C.POINTER(amg_csr), C.POINTER(amg_csr), C.POINTER(amg_csr)]),
         "amg_num_levels": (I, [P]),
         "amg_level_info": (I, [P, I, pi, C.POINTER(LL), C.POINTER(LL)]),
@@ -128,7 +129,7 @@ def _declare(L):
 
 def exported_symbols():
     """Names of the C entry points this binding knows about."""
-    return ["amg_default_options", "amg_create", "amg_destroy", "amg_last_error", "amg_setup",
+    return ["amg_default_options", "amg_create", "amg_destroy", "amg_last_error", "amg_setup", "amg_setup_device",
             "amg_load_hierarchy", "amg_num_levels", "amg_level_info", "amg_get_level", "amg_get_scales",
             "amg_set_jacobi", "amg_set_coeffs", "amg_get_smoother", "gnn_load_params", "gnn_predict_coeffs",
             "amg_solve", "amg_solve_device", "amg_vcycle_device", "amg_smooth_device", "amg_spmv_device",
@@ -213,6 +214,12 @@ def amg_setup(ctx, A):
     keep = []
     m = _csr(A, keep)
     return _check(ctx, lib().amg_setup(ctx, C.byref(m)))
+
+
+def amg_setup_device(ctx, A, seed=0, second_pass=True):
+    keep = []
+    m = _csr(A, keep)
+    return _check(ctx, lib().amg_setup_device(ctx, C.byref(m), int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(second_pass))))
 
 
 def amg_load_hierarchy(ctx, A_list, P_list, R_list=None):

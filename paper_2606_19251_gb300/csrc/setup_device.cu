@@ -1,0 +1,685 @@
+// AMG setup on the GB300 (Sec. 2.2; Algorithm 1 step 2) with a parallel
+// C/F split.  Per level, all in CUDA kernels:
+//   strength     j in S_i iff j != i and -a_ij >= theta max_{k != i}(-a_ik)
+//                (that maximum > 0); S as CSR, S^T by counting + scatter
+//   PMIS split   (De Sterck, Yang & Heys 2006) lambda_i = |S_i^T| + r_i in
+//                FP64, r_i from splitmix64 (seed + level); points with
+//                |S_i^T| = 0 start as F; rounds of "undecided i beats every
+//                undecided j in S_i u S_i^T (ties: lower index) -> C, then
+//                undecided points with a strong dependency on a new C -> F"
+//                until nothing is undecided; the host reads the count of
+//                undecided points after each round (at least the global
+//                maximum is decided per round, so rounds <= n)
+//   second pass  (optional) rounds in which the F points j with strong F
+//                partners i (j in S_i, S_i n S_j n C empty) count their
+//                violating pairs v_j, and candidates beating every candidate
+//                of S_j u S_j^T (v + r, ties to the lower index) become C,
+//                until no pair violates (the top candidate is promoted each
+//                round, so rounds <= n)
+//   direct interpolation, one thread per row in the row's entry order
+//   R = P^T      counting transpose, rows sorted by column
+//   Galerkin     A_c = R (A P): two row-wise products, each row hashed into
+//                its own open-addressing table (load <= 2/3), products
+//                summed in the row-by-row (Gustavson) order, the row's
+//                entries sorted by column
+// Offsets come from a three-phase exclusive scan.  The same stopping rules as
+// the host setup; the finished hierarchy is copied to host CSR.
+#include "setup_device.h"
+
+#include <algorithm>
+#include <cstdint>
+
+#include "amg_gnn.h"
+#include "common.cuh"
+
+namespace amg {
+namespace {
+
+constexpr int8_t kF = 0, kC = 1, kU = -1;
+
+struct DevCSR {
+    int n_rows = 0, n_cols = 0;
+    long long nnz = 0;
+    int *rp = nullptr, *col = nullptr;
+    double *val = nullptr;
+};
+
+// device allocations of one setup call, freed together
+struct Pool {
+    std::vector<void *> ptrs;
+    cudaError_t err = cudaSuccess;
+    template <class T>
+    T *get(long long n) {
+        if (err != cudaSuccess) return nullptr;
+        void *p = nullptr;
+        err = cudaMalloc(&p, static_cast<size_t>(std::max<long long>(1, n)) * sizeof(T));
+        if (err != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    ~Pool() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// exclusive scan (out may alias in)
+// ---------------------------------------------------------------------------
+constexpr int kScanBlock = 256, kScanItems = 4, kScanTile = kScanBlock * kScanItems;
+
+template <class T>
+__global__ void __launch_bounds__(kScanBlock) k_scan_tile(const T *in, T *out, T *__restrict__ tile_sum, long long n) {
+    __shared__ T warp_tot[kScanBlock / 32];
+    const long long base = static_cast<long long>(blockIdx.x) * kScanTile + static_cast<long long>(threadIdx.x) * kScanItems;
+    T v[kScanItems];
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = (base + j < n) ? in[base + j] : T(0);
+        s += v[j];
+    }
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    T inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    T woff = 0;
+    for (int k = 0; k < w; ++k) woff += warp_tot[k];
+    T run = woff + inc - s;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == kScanBlock - 1) tile_sum[blockIdx.x] = woff + inc;
+}
+
+template <class T>
+__global__ void k_scan_add(T *out, const T *__restrict__ tile_off, long long n) {
+    const long long i = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
+    if (i < n) out[i] += tile_off[i / kScanTile];
+}
+
+template <class T>
+cudaError_t exclusive_scan(const T *in, T *out, long long n, Pool &pool, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long nt = (n + kScanTile - 1) / kScanTile;
+    T *sums = pool.get<T>(nt);
+    if (!sums) return pool.err;
+    k_scan_tile<T><<<static_cast<unsigned>(nt), kScanBlock, 0, s>>>(in, out, sums, n); AMG_COUNT();
+    if (nt > 1) {
+        const cudaError_t e = exclusive_scan<T>(sums, sums, nt, pool, s);
+        if (e != cudaSuccess) return e;
+        k_scan_add<T><<<grid_for(n), kBlock, 0, s>>>(out, sums, n); AMG_COUNT();
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// strength graph
+// ---------------------------------------------------------------------------
+__global__ void k_strength(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                           const double *__restrict__ val, double theta, uint8_t *__restrict__ strong,
+                           int *__restrict__ scnt) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    bool has_off = false;
+    double m = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        if (col[p] == i) continue;
+        const double neg = -val[p];
+        if (!has_off || neg > m) m = neg;
+        has_off = true;
+    }
+    int cnt = 0;
+    if (has_off && m > 0.0) {
+        const double thr = theta * m;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            const uint8_t st = (col[p] != i && -val[p] >= thr) ? 1 : 0;
+            strong[p] = st;
+            cnt += st;
+        }
+    } else {
+        for (int p = rp[i]; p < rp[i + 1]; ++p) strong[p] = 0;
+    }
+    scnt[i] = cnt;
+}
+
+__global__ void k_fill_strong(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                              const uint8_t *__restrict__ strong, const int *__restrict__ S_rp,
+                              int *__restrict__ S_col) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    int o = S_rp[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (strong[p]) S_col[o++] = col[p];
+}
+
+__global__ void k_count_cols(int n, const int *__restrict__ rp, const int *__restrict__ col, int *__restrict__ cnt) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) atomicAdd(cnt + col[p], 1);
+}
+
+// scatter of a transpose (entries of a row land in arbitrary order)
+__global__ void k_scatter_transpose(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                    const double *__restrict__ val, int *__restrict__ cursor, int *__restrict__ T_col,
+                                    double *__restrict__ T_val) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int at = atomicAdd(cursor + col[p], 1);
+        T_col[at] = i;
+        if (T_val) T_val[at] = val[p];
+    }
+}
+
+// sort each row by column (insertion sort; values carried along)
+__global__ void k_sort_rows(int n, const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const int p0 = rp[i], p1 = rp[i + 1];
+    for (int a = p0 + 1; a < p1; ++a) {
+        const int c = col[a];
+        const double v = val[a];
+        int b = a - 1;
+        while (b >= p0 && col[b] > c) {
+            col[b + 1] = col[b];
+            val[b + 1] = val[b];
+            --b;
+        }
+        col[b + 1] = c;
+        val[b + 1] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PMIS
+// ---------------------------------------------------------------------------
+// splitmix64 (Steele, Lea & Flood 2014): output k of the sequence started at
+// `seed`, mapped to [0, 1) by its top 53 bits
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long k) {
+    unsigned long long z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return static_cast<double>(z >> 11) * 0x1.0p-53;
+}
+
+__global__ void k_pmis_init(int n, const int *__restrict__ T_rp, unsigned long long seed, double *__restrict__ lam,
+                            int8_t *__restrict__ state) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const int d = T_rp[i + 1] - T_rp[i];
+    lam[i] = static_cast<double>(d) + splitmix_uniform(seed, static_cast<unsigned long long>(i) + 1ull);
+    state[i] = d == 0 ? kF : kU;
+}
+
+__device__ __forceinline__ bool beats(double li, int i, double lj, int j) { return li > lj || (li == lj && i < j); }
+
+__global__ void k_pmis_select(int n, const int *__restrict__ S_rp, const int *__restrict__ S_col,
+                              const int *__restrict__ T_rp, const int *__restrict__ T_col,
+                              const double *__restrict__ lam, const int8_t *__restrict__ state,
+                              int8_t *__restrict__ newc) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    int8_t win = 0;
+    if (state[i] == kU) {
+        win = 1;
+        const double li = lam[i];
+        for (int p = S_rp[i]; p < S_rp[i + 1] && win; ++p) {
+            const int j = S_col[p];
+            if (state[j] == kU && !beats(li, i, lam[j], j)) win = 0;
+        }
+        for (int p = T_rp[i]; p < T_rp[i + 1] && win; ++p) {
+            const int j = T_col[p];
+            if (state[j] == kU && !beats(li, i, lam[j], j)) win = 0;
+        }
+    }
+    newc[i] = win;
+}
+
+__global__ void k_pmis_update(int n, const int *__restrict__ S_rp, const int *__restrict__ S_col,
+                              const int8_t *__restrict__ newc, int8_t *__restrict__ state, int *__restrict__ remaining) {
+    __shared__ int red[kBlock / 32];
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    int still = 0;
+    if (i < n && state[i] == kU) {
+        if (newc[i]) {
+            state[i] = kC;
+        } else {
+            bool f = false;
+            for (int p = S_rp[i]; p < S_rp[i + 1] && !f; ++p) f = newc[S_col[p]] != 0;
+            if (f) state[i] = kF;
+            else still = 1;
+        }
+    }
+    still = warp_sum(still);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = still;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < kBlock / 32; ++k) t += red[k];
+        if (t) atomicAdd(remaining, t);
+    }
+}
+
+// v_j += 1 for every F point i with j in S_i an F point and no common strong
+// C point (S rows are sorted: a merge of the two rows)
+__global__ void k_h1_violations(int n, const int *__restrict__ S_rp, const int *__restrict__ S_col,
+                                const int8_t *__restrict__ state, int *__restrict__ v, int *__restrict__ total) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n || state[i] != kF) return;
+    int mine = 0;
+    const int pe = S_rp[i + 1];
+    for (int p0 = S_rp[i]; p0 < pe; ++p0) {
+        const int j = S_col[p0];
+        if (state[j] != kF) continue;
+        bool share = false;
+        int p = S_rp[i], q = S_rp[j];
+        const int qe = S_rp[j + 1];
+        while (p < pe && q < qe && !share) {
+            const int a = S_col[p], b = S_col[q];
+            if (a == b) {
+                share = state[a] == kC;
+                ++p;
+                ++q;
+            } else if (a < b) {
+                ++p;
+            } else {
+                ++q;
+            }
+        }
+        if (!share) {
+            atomicAdd(v + j, 1);
+            ++mine;
+        }
+    }
+    if (mine) atomicAdd(total, mine);
+}
+
+// candidates (v_j > 0) that beat every candidate of S_j u S_j^T become C
+__global__ void k_h1_promote(int n, const int *__restrict__ S_rp, const int *__restrict__ S_col,
+                             const int *__restrict__ T_rp, const int *__restrict__ T_col, const int *__restrict__ v,
+                             unsigned long long seed, int8_t *__restrict__ state) {
+    const int j = blockIdx.x * kBlock + threadIdx.x;
+    if (j >= n || v[j] == 0) return;
+    const double wj = static_cast<double>(v[j]) + splitmix_uniform(seed, static_cast<unsigned long long>(j) + 1ull);
+    bool win = true;
+    for (int p = S_rp[j]; p < S_rp[j + 1] && win; ++p) {
+        const int k = S_col[p];
+        if (v[k] && !beats(wj, j, static_cast<double>(v[k]) + splitmix_uniform(seed, static_cast<unsigned long long>(k) + 1ull), k))
+            win = false;
+    }
+    for (int p = T_rp[j]; p < T_rp[j + 1] && win; ++p) {
+        const int k = T_col[p];
+        if (v[k] && !beats(wj, j, static_cast<double>(v[k]) + splitmix_uniform(seed, static_cast<unsigned long long>(k) + 1ull), k))
+            win = false;
+    }
+    if (win) state[j] = kC;
+}
+
+__global__ void k_cflag(int n, const int8_t *__restrict__ state, int *__restrict__ cflag) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n) cflag[i] = state[i] == kC ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// direct interpolation (one thread per row, the row's entry order)
+// ---------------------------------------------------------------------------
+__global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                               const uint8_t *__restrict__ strong, const int8_t *__restrict__ state,
+                               int *__restrict__ pcnt) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    if (state[i] == kC) {
+        pcnt[i] = 1;
+        return;
+    }
+    int c = 0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) c += (strong[p] && state[col[p]] == kC) ? 1 : 0;
+    pcnt[i] = c;
+}
+
+// C rows: identity onto the coarse numbering.  F row i with strong C
+// neighbours C_i: w_ij = -alpha_i a_ij / d_i, alpha_i = (sum of the negative
+// off-diagonal a_ik) / (sum over C_i of a_ik), d_i = a_ii + (sum of the
+// positive off-diagonal a_ik); sums taken in the row's entry order.
+__global__ void k_interp_fill(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                              const double *__restrict__ val, const uint8_t *__restrict__ strong,
+                              const int8_t *__restrict__ state, const int *__restrict__ cidx,
+                              const int *__restrict__ P_rp, int *__restrict__ P_col, double *__restrict__ P_val) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    int o = P_rp[i];
+    if (state[i] == kC) {
+        P_col[o] = cidx[i];
+        P_val[o] = 1.0;
+        return;
+    }
+    if (P_rp[i + 1] == o) return;    // no strong C neighbour: empty row
+    double a_ii = 0.0, neg_all = 0.0, pos_all = 0.0, neg_c = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = col[p];
+        const double a = val[p];
+        if (j == i) {
+            a_ii += a;
+        } else if (a < 0.0) {
+            neg_all += a;
+            if (strong[p] && state[j] == kC) neg_c += a;
+        } else if (a > 0.0) {
+            pos_all += a;
+        }
+    }
+    const double d = a_ii + pos_all;
+    const double alpha = neg_all / neg_c;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = col[p];
+        if (j != i && strong[p] && state[j] == kC) {
+            P_col[o] = cidx[j];
+            P_val[o] = (-alpha * val[p]) / d;
+            ++o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// row-wise sparse product Z = X Y
+// ---------------------------------------------------------------------------
+__global__ void k_spgemm_size(int nX, const int *__restrict__ X_rp, const int *__restrict__ X_col,
+                              const int *__restrict__ Y_rp, long long *__restrict__ hsz) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= nX) return;
+    long long ub = 0;
+    for (int p = X_rp[i]; p < X_rp[i + 1]; ++p) {
+        const int k = X_col[p];
+        ub += Y_rp[k + 1] - Y_rp[k];
+    }
+    long long h = 0;
+    if (ub > 0) {
+        h = 1;
+        while (h < ub + ub / 2 + 1) h <<= 1;
+    }
+    hsz[i] = h;
+}
+
+// Row i: every product x_ik y_kj accumulated into the row's table slot of j
+// in (k, then j) row order; the distinct columns are then compacted to the
+// front of the table and sorted.  cnt[i] = number of distinct columns.
+__global__ void k_spgemm_hash(int nX, const int *__restrict__ X_rp, const int *__restrict__ X_col,
+                              const double *__restrict__ X_val, const int *__restrict__ Y_rp,
+                              const int *__restrict__ Y_col, const double *__restrict__ Y_val,
+                              const long long *__restrict__ hoff, int *__restrict__ keys, double *__restrict__ vals,
+                              int *__restrict__ cnt) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= nX) return;
+    const long long o = hoff[i], size = hoff[i + 1] - o;
+    if (size == 0) {
+        cnt[i] = 0;
+        return;
+    }
+    int *K = keys + o;
+    double *V = vals + o;
+    const unsigned long long mask = static_cast<unsigned long long>(size) - 1ull;
+    for (long long t = 0; t < size; ++t) K[t] = -1;
+    for (int p = X_rp[i]; p < X_rp[i + 1]; ++p) {
+        const int k = X_col[p];
+        const double x = X_val[p];
+        for (int q = Y_rp[k]; q < Y_rp[k + 1]; ++q) {
+            const int j = Y_col[q];
+            const double prod = x * Y_val[q];
+            unsigned long long h = (static_cast<unsigned long long>(static_cast<unsigned>(j)) * 0x9E3779B1ull) & mask;
+            while (true) {
+                const int kk = K[h];
+                if (kk == j) {
+                    V[h] += prod;
+                    break;
+                }
+                if (kk == -1) {
+                    K[h] = j;
+                    V[h] = prod;
+                    break;
+                }
+                h = (h + 1ull) & mask;
+            }
+        }
+    }
+    int u = 0;
+    for (long long t = 0; t < size; ++t) {
+        const int kk = K[t];
+        if (kk != -1) {
+            const double v = V[t];
+            K[u] = kk;
+            V[u] = v;
+            ++u;
+        }
+    }
+    for (int a = 1; a < u; ++a) {
+        const int c = K[a];
+        const double v = V[a];
+        int b = a - 1;
+        while (b >= 0 && K[b] > c) {
+            K[b + 1] = K[b];
+            V[b + 1] = V[b];
+            --b;
+        }
+        K[b + 1] = c;
+        V[b + 1] = v;
+    }
+    cnt[i] = u;
+}
+
+__global__ void k_spgemm_copy(int nX, const long long *__restrict__ hoff, const int *__restrict__ keys,
+                              const double *__restrict__ vals, const int *__restrict__ Z_rp, int *__restrict__ Z_col,
+                              double *__restrict__ Z_val) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= nX) return;
+    const long long o = hoff[i];
+    const int w = Z_rp[i], u = Z_rp[i + 1] - w;
+    for (int t = 0; t < u; ++t) {
+        Z_col[w + t] = keys[o + t];
+        Z_val[w + t] = vals[o + t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+struct Fail {
+    std::string msg;
+};
+
+void check(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw Fail{std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+template <class T>
+T read_one(const T *d, cudaStream_t s) {
+    T v{};
+    check(cudaMemcpyAsync(&v, d, sizeof(T), cudaMemcpyDeviceToHost, s), "read back");
+    check(cudaStreamSynchronize(s), "synchronise");
+    return v;
+}
+
+template <class T>
+T *need(Pool &pool, long long n) {
+    T *p = pool.get<T>(n);
+    if (!p) check(pool.err, "cudaMalloc");
+    return p;
+}
+
+// counts[0..n) filled by the caller's kernel; counts[n] = 0; scanned in place
+template <class T>
+T scan_counts(T *counts, long long n, Pool &pool, cudaStream_t s) {
+    check(exclusive_scan<T>(counts, counts, n + 1, pool, s), "scan");
+    return read_one(counts + n, s);
+}
+
+DevCSR transpose_sorted(const DevCSR &M, Pool &pool, cudaStream_t s) {
+    DevCSR T;
+    T.n_rows = M.n_cols;
+    T.n_cols = M.n_rows;
+    T.nnz = M.nnz;
+    T.rp = need<int>(pool, T.n_rows + 1);
+    check(cudaMemsetAsync(T.rp, 0, sizeof(int) * (T.n_rows + 1), s), "memset");
+    k_count_cols<<<grid_for(M.n_rows), kBlock, 0, s>>>(M.n_rows, M.rp, M.col, T.rp); AMG_COUNT();
+    scan_counts<int>(T.rp, T.n_rows, pool, s);
+    int *cursor = need<int>(pool, T.n_rows);
+    check(cudaMemcpyAsync(cursor, T.rp, sizeof(int) * T.n_rows, cudaMemcpyDeviceToDevice, s), "copy");
+    T.col = need<int>(pool, T.nnz);
+    T.val = need<double>(pool, T.nnz);
+    k_scatter_transpose<<<grid_for(M.n_rows), kBlock, 0, s>>>(M.n_rows, M.rp, M.col, M.val, cursor, T.col, T.val); AMG_COUNT();
+    k_sort_rows<<<grid_for(T.n_rows), kBlock, 0, s>>>(T.n_rows, T.rp, T.col, T.val); AMG_COUNT();
+    return T;
+}
+
+DevCSR spgemm(const DevCSR &X, const DevCSR &Y, Pool &pool, cudaStream_t s) {
+    const int n = X.n_rows;
+    long long *hoff = need<long long>(pool, n + 1);
+    check(cudaMemsetAsync(hoff + n, 0, sizeof(long long), s), "memset");
+    k_spgemm_size<<<grid_for(n), kBlock, 0, s>>>(n, X.rp, X.col, Y.rp, hoff); AMG_COUNT();
+    const long long total = scan_counts<long long>(hoff, n, pool, s);
+    if (total > 2000000000LL) throw Fail{"sparse product too large for 32-bit offsets"};
+    int *keys = need<int>(pool, total);
+    double *vals = need<double>(pool, total);
+    DevCSR Z;
+    Z.n_rows = n;
+    Z.n_cols = Y.n_cols;
+    Z.rp = need<int>(pool, n + 1);
+    check(cudaMemsetAsync(Z.rp + n, 0, sizeof(int), s), "memset");
+    k_spgemm_hash<<<grid_for(n), kBlock, 0, s>>>(n, X.rp, X.col, X.val, Y.rp, Y.col, Y.val, hoff, keys, vals, Z.rp); AMG_COUNT();
+    Z.nnz = scan_counts<int>(Z.rp, n, pool, s);
+    Z.col = need<int>(pool, Z.nnz);
+    Z.val = need<double>(pool, Z.nnz);
+    k_spgemm_copy<<<grid_for(n), kBlock, 0, s>>>(n, hoff, keys, vals, Z.rp, Z.col, Z.val); AMG_COUNT();
+    check(cudaGetLastError(), "sparse product");
+    return Z;
+}
+
+void download(const DevCSR &M, HostCSR &h, cudaStream_t s) {
+    h.n_rows = M.n_rows;
+    h.n_cols = M.n_cols;
+    h.rp.resize(M.n_rows + 1);
+    h.col.resize(M.nnz);
+    h.val.resize(M.nnz);
+    check(cudaMemcpyAsync(h.rp.data(), M.rp, sizeof(int) * (M.n_rows + 1), cudaMemcpyDeviceToHost, s), "download");
+    if (M.nnz) {
+        check(cudaMemcpyAsync(h.col.data(), M.col, sizeof(int) * M.nnz, cudaMemcpyDeviceToHost, s), "download");
+        check(cudaMemcpyAsync(h.val.data(), M.val, sizeof(double) * M.nnz, cudaMemcpyDeviceToHost, s), "download");
+    }
+}
+
+void build(const HostCSR &A0, double theta, int max_levels, int max_coarse, unsigned long long seed,
+           bool second, cudaStream_t s, std::vector<HostLevel> &levels, Pool &pool) {
+    DevCSR A;
+    A.n_rows = A.n_cols = A0.n_rows;
+    A.nnz = A0.nnz();
+    A.rp = need<int>(pool, A.n_rows + 1);
+    A.col = need<int>(pool, A.nnz);
+    A.val = need<double>(pool, A.nnz);
+    check(cudaMemcpyAsync(A.rp, A0.rp.data(), sizeof(int) * (A.n_rows + 1), cudaMemcpyHostToDevice, s), "upload");
+    check(cudaMemcpyAsync(A.col, A0.col.data(), sizeof(int) * A.nnz, cudaMemcpyHostToDevice, s), "upload");
+    check(cudaMemcpyAsync(A.val, A0.val.data(), sizeof(double) * A.nnz, cudaMemcpyHostToDevice, s), "upload");
+    std::vector<DevCSR> dA{A}, dP, dR;
+    while (static_cast<int>(dA.size()) < max_levels && dA.back().n_rows > max_coarse) {
+        const DevCSR L = dA.back();
+        const int n = L.n_rows;
+        const unsigned long long seed_l = seed + static_cast<unsigned long long>(dA.size() - 1);
+        const int g = grid_for(n);
+        // strength graph and its transpose
+        uint8_t *strong = need<uint8_t>(pool, L.nnz);
+        int *S_rp = need<int>(pool, n + 1);
+        check(cudaMemsetAsync(S_rp + n, 0, sizeof(int), s), "memset");
+        k_strength<<<g, kBlock, 0, s>>>(n, L.rp, L.col, L.val, theta, strong, S_rp); AMG_COUNT();
+        const int nS = scan_counts<int>(S_rp, n, pool, s);
+        int *S_col = need<int>(pool, nS);
+        k_fill_strong<<<g, kBlock, 0, s>>>(n, L.rp, L.col, strong, S_rp, S_col); AMG_COUNT();
+        int *T_rp = need<int>(pool, n + 1);
+        check(cudaMemsetAsync(T_rp, 0, sizeof(int) * (n + 1), s), "memset");
+        k_count_cols<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp); AMG_COUNT();
+        scan_counts<int>(T_rp, n, pool, s);
+        int *cursor = need<int>(pool, n);
+        check(cudaMemcpyAsync(cursor, T_rp, sizeof(int) * n, cudaMemcpyDeviceToDevice, s), "copy");
+        int *T_col = need<int>(pool, nS);
+        k_scatter_transpose<<<g, kBlock, 0, s>>>(n, S_rp, S_col, nullptr, cursor, T_col, nullptr); AMG_COUNT();
+        // PMIS rounds
+        double *lam = need<double>(pool, n);
+        int8_t *state = need<int8_t>(pool, n);
+        int8_t *newc = need<int8_t>(pool, n);
+        int *remaining = need<int>(pool, 1);
+        k_pmis_init<<<g, kBlock, 0, s>>>(n, T_rp, seed_l, lam, state); AMG_COUNT();
+        for (int round = 0;; ++round) {
+            if (round > n) throw Fail{"PMIS split did not finish"};
+            check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
+            k_pmis_select<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, lam, state, newc); AMG_COUNT();
+            k_pmis_update<<<g, kBlock, 0, s>>>(n, S_rp, S_col, newc, state, remaining); AMG_COUNT();
+            if (read_one(remaining, s) == 0) break;
+        }
+        if (second) {
+            int *v = need<int>(pool, n);
+            for (int round = 0;; ++round) {
+                if (round > n) throw Fail{"second pass did not finish"};
+                check(cudaMemsetAsync(v, 0, sizeof(int) * n, s), "memset");
+                check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
+                k_h1_violations<<<g, kBlock, 0, s>>>(n, S_rp, S_col, state, v, remaining); AMG_COUNT();
+                if (read_one(remaining, s) == 0) break;
+                k_h1_promote<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, v, seed_l, state); AMG_COUNT();
+            }
+        }
+        int *cidx = need<int>(pool, n + 1);
+        check(cudaMemsetAsync(cidx + n, 0, sizeof(int), s), "memset");
+        k_cflag<<<g, kBlock, 0, s>>>(n, state, cidx); AMG_COUNT();
+        const int nc = scan_counts<int>(cidx, n, pool, s);
+        if (nc == 0 || static_cast<double>(nc) > 0.9 * n) break;
+        // P, R = P^T, A_c = R (A P)
+        DevCSR P;
+        P.n_rows = n;
+        P.n_cols = nc;
+        P.rp = need<int>(pool, n + 1);
+        check(cudaMemsetAsync(P.rp + n, 0, sizeof(int), s), "memset");
+        k_interp_count<<<g, kBlock, 0, s>>>(n, L.rp, L.col, strong, state, P.rp); AMG_COUNT();
+        P.nnz = scan_counts<int>(P.rp, n, pool, s);
+        P.col = need<int>(pool, P.nnz);
+        P.val = need<double>(pool, P.nnz);
+        k_interp_fill<<<g, kBlock, 0, s>>>(n, L.rp, L.col, L.val, strong, state, cidx, P.rp, P.col, P.val); AMG_COUNT();
+        const DevCSR R = transpose_sorted(P, pool, s);
+        const DevCSR AP = spgemm(L, P, pool, s);
+        const DevCSR Ac = spgemm(R, AP, pool, s);
+        dP.push_back(P);
+        dR.push_back(R);
+        dA.push_back(Ac);
+    }
+    levels.assign(dA.size(), HostLevel{});
+    for (size_t l = 0; l < dA.size(); ++l) {
+        download(dA[l], levels[l].A, s);
+        if (l + 1 < dA.size()) {
+            download(dP[l], levels[l].P, s);
+            download(dR[l], levels[l].R, s);
+        }
+    }
+    check(cudaStreamSynchronize(s), "setup");
+    check(cudaGetLastError(), "setup kernels");
+}
+
+}  // namespace
+
+int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int max_coarse,
+                           unsigned long long seed, bool second_pass, cudaStream_t s,
+                           std::vector<HostLevel> &levels, std::string &err) {
+    Pool pool;
+    try {
+        build(A0, theta, max_levels, max_coarse, seed, second_pass, s, levels, pool);
+    } catch (const Fail &f) {
+        cudaStreamSynchronize(s);
+        err = "device setup: " + f.msg;
+        levels.clear();
+        return AMG_ERR_CUDA;
+    }
+    return AMG_OK;
+}
+
+}  // namespace amg

@@ -1,0 +1,24 @@
+// AMG setup on the device (Sec. 2.2 with a parallel C/F split): strength
+// graph, PMIS splitting, direct interpolation, R = P^T and the Galerkin
+// product A_c = R (A P), every level built by CUDA kernels.  The hierarchy is
+// returned as host CSR (the context keeps a host copy of every level).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "setup_host.h"
+
+namespace amg {
+
+// Setup-AMG-Hierarchy of Algorithm 1 on the device.  Level l draws its PMIS
+// random numbers r_i = top 53 bits of splitmix64(seed + l) output i + 1,
+// times 2^-53; second_pass adds the round-parallel second pass (every strong
+// F-F pair gets a common strong C point).  Same stopping rules as the host
+// RS setup.  Returns AMG_OK or AMG_ERR_CUDA (message in err).
+int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int max_coarse,
+                           unsigned long long seed, bool second_pass, cudaStream_t s,
+                           std::vector<HostLevel> &levels, std::string &err);
+
+}  // namespace amg
