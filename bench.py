@@ -39,6 +39,8 @@ WEIGHTS = os.path.join(ROOT, "paper_2606_19251_gb300", "weights", "gcin_c3.npy")
 # trained on the C3 batch plus 16 band meshes with aspect ratios up to 1000 and 16
 # small airfoil meshes: the parameters for the anisotropic and airfoil workloads
 WEIGHTS_WIDE = os.path.join(ROOT, "paper_2606_19251_gb300", "weights", "gcin_wide.npy")
+# the halved GCIN width of App. B.3 (37,189 parameters), trained on the C3 batch
+WEIGHTS_H32 = os.path.join(ROOT, "paper_2606_19251_gb300", "weights", "gcin_c3_h32.npy")
 TOL = 1e-8
 
 
@@ -376,6 +378,69 @@ def run_gpu(args, wl, rank, world):
            "smoother": "gcin-pseudo-inverse" if use_gnn_k else "jacobi (rerouted)"}
     P.amg_destroy(ctx_k)
 
+    # the same step with the halved GCIN width (App. B.3): its own parameters,
+    # judged on this mesh like the width-64 network
+    h32 = None
+    if not wl.get("wide", False) and os.path.exists(WEIGHTS_H32):
+        ctx_h = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev)
+        P.amg_setup(ctx_h, A)
+        P.gnn_load_params(ctx_h, np.load(WEIGHTS_H32))
+        P.gnn_predict_coeffs(ctx_h)
+        _, kept_h = P.amg_reroute(ctx_h, rhs_host[0].numpy(), 30)
+        use_h = kept_h == P.AMG_SMOOTHER_GNN
+
+        def h32_step(k):
+            if use_h:
+                P.gnn_predict_coeffs(ctx_h)
+            return P.amg_solve_device(ctx_h, rhs_dev[k], x, TOL)
+
+        for k in range(Wm):
+            timed(h32_step, k)
+        hs = [timed(h32_step, Wm + k) for k in range(K)]
+        hi = [timed(lambda k: P.gnn_predict_coeffs(ctx_h), k)[0] for k in range(K)]
+        h32 = {"params": P.AMG_GCIN_NUM_PARAMS_H32, "weights": os.path.basename(WEIGHTS_H32),
+               "step_ms": statistics.mean(v[0] for v in hs), "vcycles": statistics.mean(len(v[1][1]) - 1 for v in hs),
+               "infer_ms": statistics.mean(hi), "kept_gnn": use_h, "status": sorted(set(v[1][0] for v in hs))}
+        P.amg_destroy(ctx_h)
+
+    # the hierarchy built on the device (PMIS split and the round-parallel
+    # second pass, Galerkin products on the GB300; not the paper's RS
+    # coarsening): its setup time, then the same step on it with either smoother
+    ctx_d = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev)
+    dsetup = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.amg_setup_device(ctx_d, A, 0, True)
+        torch.cuda.synchronize()
+        dsetup.append((time.perf_counter() - t0) * 1e3)
+    dinfo = [P.amg_level_info(ctx_d, l) for l in range(P.amg_num_levels(ctx_d))]
+    P.gnn_load_params(ctx_d, theta)
+    P.gnn_predict_coeffs(ctx_d)
+    _, kept_d = P.amg_reroute(ctx_d, rhs_host[0].numpy(), 30)
+    use_d = kept_d == P.AMG_SMOOTHER_GNN
+
+    def dev_step(k):
+        if use_d:
+            P.gnn_predict_coeffs(ctx_d)
+        return P.amg_solve_device(ctx_d, rhs_dev[k], x, TOL)
+
+    for k in range(Wm):
+        timed(dev_step, k)
+    ds = [timed(dev_step, Wm + k) for k in range(K)]
+    P.amg_set_jacobi(ctx_d)
+    dj = [timed(lambda k: P.amg_solve_device(ctx_d, rhs_dev[k], x, TOL), Wm + k) for k in range(K)]
+    device_setup = {"coarsening": "PMIS + round-parallel second pass (device)", "setup_ms": dsetup[-1],
+                    "setup_ms_first_call": dsetup[0], "levels": len(dinfo),
+                    "operator_complexity": sum(i[1] for i in dinfo) / dinfo[0][1],
+                    "gnn_step_ms": statistics.mean(v[0] for v in ds),
+                    "vcycles_gnn": statistics.mean(len(v[1][1]) - 1 for v in ds), "kept_gnn": use_d,
+                    "jacobi_solve_ms": statistics.mean(v[0] for v in dj),
+                    "vcycles_jacobi": statistics.mean(len(v[1][1]) - 1 for v in dj),
+                    "status": sorted(set(v[1][0] for v in ds) | set(v[1][0] for v in dj))}
+    P.amg_destroy(ctx_d)
+    hinfo = [P.amg_level_info(ctx, l) for l in range(nlev)]
+
     # dominant kernel: the finest level's pseudo-inverse sweep (single pass
     # with Q^-1 A on latency-optimised levels, else the residual pass),
     # timed back to back on the stream it is launched on
@@ -452,7 +517,7 @@ def run_gpu(args, wl, rank, world):
         key = "masweep" if kid == P.AMG_K_MASWEEP else "residual"
         with open(tfile) as f:
             tr = json.load(f).get(f"{wl['workload']}:{key}")
-        if tr and tr.get("kernel_source_sha") == _kernel_sha():
+        if tr and tr.get("kernel_source_sha") == _kernel_sha(key):
             traffic = tr["dram_bytes_per_launch"]
 
     if rank == 0:
@@ -467,7 +532,8 @@ def run_gpu(args, wl, rank, world):
                        "outer": "fp64 iterative refinement", "tol": TOL, "l2": "flushed (512 MB) per step",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "reroute": {"metric": reroute_metric, "kept_gnn": use_gnn, "setup_ms": reroute_ms, "probe_cycles": 30},
-            "pcg": pcg,
+            "pcg": pcg, "gcin_hidden32": h32, "device_setup": device_setup,
+            "operator_complexity": sum(i[1] for i in hinfo) / hinfo[0][1],
             "gnn_step_ms": ms_per_step, "gnn_solve_ms": solve_ms, "gnn_infer_ms": infer_ms,
             "jacobi_solve_ms": jac_ms, "vcycles_gnn": statistics.mean(cyc_gnn), "vcycles_jacobi": cyc_jac,
             "chebyshev3": cheb,
@@ -495,15 +561,36 @@ def run_gpu(args, wl, rank, world):
     P.amg_destroy(ctx)
 
 
-def _kernel_sha():
-    """Hash of the sources of the solve-path kernels (traffic counters are
-    only reported while they still describe the code that runs)."""
+TRAFFIC_KERNELS = {"masweep": "k_ma_sweep", "residual": "k_resid"}
+
+
+def _kernel_source(text, name):
+    """The definition of __global__ function `name` (template header, signature
+    and body) as it appears in the source text."""
+    import re
+    m = re.search(r"(template\s*<[^>]*>\s*)?__global__[^;{]*?\b" + re.escape(name) + r"\s*\(", text)
+    if not m:
+        raise KeyError(name)
+    i = text.index("{", m.end())
+    depth = 0
+    for j in range(i, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[j], 0)
+        if depth == 0:
+            return text[m.start():j + 1]
+    raise ValueError(name)
+
+
+def _kernel_sha(key):
+    """Hash of one measured kernel's source and the shared device helpers
+    (traffic counters are only reported while they still describe the code
+    that runs)."""
     import hashlib
-    h = hashlib.sha256()
-    for name in ("amg_solver.cu", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2606_19251_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2606_19251_gb300", "csrc")
+    with open(os.path.join(csrc, "amg_solver.cu")) as f:
+        body = _kernel_source(f.read(), TRAFFIC_KERNELS[key])
+    with open(os.path.join(csrc, "common.cuh")) as f:
+        common = f.read()
+    return hashlib.sha256((body + common).encode()).hexdigest()[:16]
 
 
 def run_kernel_only(args, wl):
