@@ -1281,8 +1281,9 @@ static int upload_mat(amg_ctx *c, const DevMat &m, const HostCSR &h, cudaStream_
 // single-pass sweeps and the fused residual + restriction.
 static const long long kFastPairs = 8LL << 20;
 
-static void plan_fast_levels(amg_ctx *c) {
+static int plan_fast_levels(amg_ctx *c) {
     const int nlev = static_cast<int>(c->host.size());
+    std::vector<char> which(nlev, 0);
     for (int l = 0; l < nlev; ++l) {
         HostLevel &H = c->host[l];
         H.fast = false;
@@ -1298,17 +1299,23 @@ static void plan_fast_levels(amg_ctx *c) {
             pairs += d * d;
         }
         if (pairs > kFastPairs) continue;
-        product_pattern(H.A, H.MA, H.pair_ptr, H.pair_p, H.pair_q);
-        H.RA = spgemm(H.R, H.A);
+        which[l] = 1;
         H.fast = true;
     }
+    // M A pattern + pair list and R A on the device (the same lists as the
+    // host planner product_pattern builds)
+    std::string why;
+    const int rc = device_plan_products(c->host, which, c->stream, why);
+    if (rc) ctx_fail(c, why);
+    return rc;
 }
 
 static int upload(amg_ctx *c) {
     free_device(c);
     ++c->hier_version;
     c->stall_ratio = 0.0;   // the in-solve check belongs to a mesh
-    plan_fast_levels(c);
+    const int prc = plan_fast_levels(c);
+    if (prc) return prc;
     Planner pl;
     layout(c, pl);
     c->arena_bytes = pl.off;

@@ -24,6 +24,10 @@
 //                entries sorted by column
 // Offsets come from a three-phase exclusive scan.  The same stopping rules as
 // the host setup; the finished hierarchy is copied to host CSR.
+//
+// Also here: the products the latency-optimised (small) levels use, for
+// hierarchies from either setup: the pattern of A A (that of M A, M = Q^-1 on
+// A's pattern) with the pair list assembling M A, and R A.
 #include "setup_device.h"
 
 #include <algorithm>
@@ -178,23 +182,15 @@ __global__ void k_scatter_transpose(int n, const int *__restrict__ rp, const int
     }
 }
 
-// sort each row by column (insertion sort; values carried along)
+template <class V>
+__device__ void heap_sort(int *K, V *W, int u);
+
+// sort each row by column (values carried along)
 __global__ void k_sort_rows(int n, const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val) {
     const int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= n) return;
-    const int p0 = rp[i], p1 = rp[i + 1];
-    for (int a = p0 + 1; a < p1; ++a) {
-        const int c = col[a];
-        const double v = val[a];
-        int b = a - 1;
-        while (b >= p0 && col[b] > c) {
-            col[b + 1] = col[b];
-            val[b + 1] = val[b];
-            --b;
-        }
-        col[b + 1] = c;
-        val[b + 1] = v;
-    }
+    const int p0 = rp[i];
+    heap_sort(col + p0, val + p0, rp[i + 1] - p0);
 }
 
 // ---------------------------------------------------------------------------
@@ -390,6 +386,40 @@ __global__ void k_interp_fill(int n, const int *__restrict__ rp, const int *__re
 // ---------------------------------------------------------------------------
 // row-wise sparse product Z = X Y
 // ---------------------------------------------------------------------------
+// In-place heapsort of u (key, value) pairs by key (keys distinct): a
+// thread's own row, O(u log u) where the rows of dense coarse levels hold
+// hundreds of entries.
+template <class V>
+__device__ void heap_sift(int *K, V *W, int root, int end) {
+    while (true) {
+        int child = 2 * root + 1;
+        if (child >= end) return;
+        if (child + 1 < end && K[child + 1] > K[child]) ++child;
+        if (K[root] >= K[child]) return;
+        const int tk = K[root];
+        K[root] = K[child];
+        K[child] = tk;
+        const V tv = W[root];
+        W[root] = W[child];
+        W[child] = tv;
+        root = child;
+    }
+}
+
+template <class V>
+__device__ void heap_sort(int *K, V *W, int u) {
+    for (int r = u / 2 - 1; r >= 0; --r) heap_sift(K, W, r, u);
+    for (int end = u - 1; end > 0; --end) {
+        const int tk = K[0];
+        K[0] = K[end];
+        K[end] = tk;
+        const V tv = W[0];
+        W[0] = W[end];
+        W[end] = tv;
+        heap_sift(K, W, 0, end);
+    }
+}
+
 __global__ void k_spgemm_size(int nX, const int *__restrict__ X_rp, const int *__restrict__ X_col,
                               const int *__restrict__ Y_rp, long long *__restrict__ hsz) {
     const int i = blockIdx.x * kBlock + threadIdx.x;
@@ -458,19 +488,96 @@ __global__ void k_spgemm_hash(int nX, const int *__restrict__ X_rp, const int *_
             ++u;
         }
     }
-    for (int a = 1; a < u; ++a) {
-        const int c = K[a];
-        const double v = V[a];
-        int b = a - 1;
-        while (b >= 0 && K[b] > c) {
-            K[b + 1] = K[b];
-            V[b + 1] = V[b];
-            --b;
-        }
-        K[b + 1] = c;
-        V[b + 1] = v;
-    }
+    heap_sort(K, V, u);
     cnt[i] = u;
+}
+
+// Pattern of row i of A A: the distinct columns j of A_k over k in A_i,
+// sorted, each with its number of contributing pairs (p, q).
+__global__ void k_pattern_hash(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                               const long long *__restrict__ hoff, int *__restrict__ keys, int *__restrict__ counts,
+                               int *__restrict__ cnt) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const long long o = hoff[i], size = hoff[i + 1] - o;
+    if (size == 0) {
+        cnt[i] = 0;
+        return;
+    }
+    int *K = keys + o, *V = counts + o;
+    const unsigned long long mask = static_cast<unsigned long long>(size) - 1ull;
+    for (long long t = 0; t < size; ++t) K[t] = -1;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int k = col[p];
+        for (int q = rp[k]; q < rp[k + 1]; ++q) {
+            const int j = col[q];
+            unsigned long long h = (static_cast<unsigned long long>(static_cast<unsigned>(j)) * 0x9E3779B1ull) & mask;
+            while (true) {
+                const int kk = K[h];
+                if (kk == j) {
+                    ++V[h];
+                    break;
+                }
+                if (kk == -1) {
+                    K[h] = j;
+                    V[h] = 1;
+                    break;
+                }
+                h = (h + 1ull) & mask;
+            }
+        }
+    }
+    int u = 0;
+    for (long long t = 0; t < size; ++t) {
+        const int kk = K[t];
+        if (kk != -1) {
+            const int v = V[t];
+            K[u] = kk;
+            V[u] = v;
+            ++u;
+        }
+    }
+    heap_sort(K, V, u);
+    cnt[i] = u;
+}
+
+__global__ void k_pattern_copy(int n, const long long *__restrict__ hoff, const int *__restrict__ keys,
+                               const int *__restrict__ counts, const int *__restrict__ Z_rp, int *__restrict__ Z_col,
+                               int *__restrict__ entry_cnt) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const long long o = hoff[i];
+    const int w = Z_rp[i], u = Z_rp[i + 1] - w;
+    for (int t = 0; t < u; ++t) {
+        Z_col[w + t] = keys[o + t];
+        entry_cnt[w + t] = counts[o + t];
+    }
+}
+
+// Pairs (p, q) of row i grouped by output entry (binary search in the row's
+// sorted pattern), each group in ascending p: one thread per row writes its
+// own groups in order, so the list is the host planner's.
+__global__ void k_pairs_fill(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                             const int *__restrict__ Z_rp, const int *__restrict__ Z_col, int *__restrict__ cursor,
+                             int *__restrict__ pair_p, int *__restrict__ pair_q) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const int z0 = Z_rp[i], z1 = Z_rp[i + 1];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int k = col[p];
+        for (int q = rp[k]; q < rp[k + 1]; ++q) {
+            const int j = col[q];
+            int lo = z0, hi = z1 - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) / 2;
+                if (Z_col[mid] < j) lo = mid + 1;
+                else hi = mid;
+            }
+            const int at = cursor[lo]++;
+            pair_p[at] = p;
+            pair_q[at] = q;
+        }
+    }
 }
 
 __global__ void k_spgemm_copy(int nX, const long long *__restrict__ hoff, const int *__restrict__ keys,
@@ -573,6 +680,70 @@ void download(const DevCSR &M, HostCSR &h, cudaStream_t s) {
     }
 }
 
+DevCSR upload_csr(const HostCSR &h, Pool &pool, cudaStream_t s) {
+    DevCSR M;
+    M.n_rows = h.n_rows;
+    M.n_cols = h.n_cols;
+    M.nnz = h.nnz();
+    M.rp = need<int>(pool, M.n_rows + 1);
+    M.col = need<int>(pool, M.nnz);
+    M.val = need<double>(pool, M.nnz);
+    check(cudaMemcpyAsync(M.rp, h.rp.data(), sizeof(int) * (M.n_rows + 1), cudaMemcpyHostToDevice, s), "upload");
+    if (M.nnz) {
+        check(cudaMemcpyAsync(M.col, h.col.data(), sizeof(int) * M.nnz, cudaMemcpyHostToDevice, s), "upload");
+        check(cudaMemcpyAsync(M.val, h.val.data(), sizeof(double) * M.nnz, cudaMemcpyHostToDevice, s), "upload");
+    }
+    return M;
+}
+
+void plan_products(HostLevel &H, Pool &pool, cudaStream_t s) {
+    const DevCSR A = upload_csr(H.A, pool, s);
+    const DevCSR R = upload_csr(H.R, pool, s);
+    const int n = A.n_rows;
+    // pattern of A A with per-entry pair counts
+    long long *hoff = need<long long>(pool, n + 1);
+    check(cudaMemsetAsync(hoff + n, 0, sizeof(long long), s), "memset");
+    k_spgemm_size<<<grid_for(n), kBlock, 0, s>>>(n, A.rp, A.col, A.rp, hoff); AMG_COUNT();
+    const long long total = scan_counts<long long>(hoff, n, pool, s);
+    if (total > 2000000000LL) throw Fail{"product pattern too large for 32-bit offsets"};
+    int *keys = need<int>(pool, total), *counts = need<int>(pool, total);
+    int *Z_rp = need<int>(pool, n + 1);
+    check(cudaMemsetAsync(Z_rp + n, 0, sizeof(int), s), "memset");
+    k_pattern_hash<<<grid_for(n), kBlock, 0, s>>>(n, A.rp, A.col, hoff, keys, counts, Z_rp); AMG_COUNT();
+    const int nz = scan_counts<int>(Z_rp, n, pool, s);
+    int *Z_col = need<int>(pool, nz);
+    int *pp = need<int>(pool, static_cast<long long>(nz) + 1);
+    check(cudaMemsetAsync(pp + nz, 0, sizeof(int), s), "memset");
+    k_pattern_copy<<<grid_for(n), kBlock, 0, s>>>(n, hoff, keys, counts, Z_rp, Z_col, pp); AMG_COUNT();
+    const int npairs = scan_counts<int>(pp, nz, pool, s);
+    int *cursor = need<int>(pool, nz);
+    check(cudaMemcpyAsync(cursor, pp, sizeof(int) * nz, cudaMemcpyDeviceToDevice, s), "copy");
+    int *pair_p = need<int>(pool, npairs), *pair_q = need<int>(pool, npairs);
+    k_pairs_fill<<<grid_for(n), kBlock, 0, s>>>(n, A.rp, A.col, Z_rp, Z_col, cursor, pair_p, pair_q); AMG_COUNT();
+    const DevCSR RA = spgemm(R, A, pool, s);
+    // back to the host level
+    H.MA = HostCSR{};
+    H.MA.n_rows = n;
+    H.MA.n_cols = A.n_cols;
+    H.MA.rp.resize(n + 1);
+    H.MA.col.resize(nz);
+    H.MA.val.assign(nz, 0.0);
+    H.pair_ptr.resize(static_cast<size_t>(nz) + 1);
+    H.pair_p.resize(npairs);
+    H.pair_q.resize(npairs);
+    check(cudaMemcpyAsync(H.MA.rp.data(), Z_rp, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s), "download");
+    check(cudaMemcpyAsync(H.MA.col.data(), Z_col, sizeof(int) * nz, cudaMemcpyDeviceToHost, s), "download");
+    check(cudaMemcpyAsync(H.pair_ptr.data(), pp, sizeof(int) * (static_cast<size_t>(nz) + 1), cudaMemcpyDeviceToHost, s),
+          "download");
+    if (npairs) {
+        check(cudaMemcpyAsync(H.pair_p.data(), pair_p, sizeof(int) * npairs, cudaMemcpyDeviceToHost, s), "download");
+        check(cudaMemcpyAsync(H.pair_q.data(), pair_q, sizeof(int) * npairs, cudaMemcpyDeviceToHost, s), "download");
+    }
+    download(RA, H.RA, s);
+    check(cudaStreamSynchronize(s), "products");
+    check(cudaGetLastError(), "product kernels");
+}
+
 void build(const HostCSR &A0, double theta, int max_levels, int max_coarse, unsigned long long seed,
            bool second, cudaStream_t s, std::vector<HostLevel> &levels, Pool &pool) {
     DevCSR A;
@@ -666,6 +837,20 @@ void build(const HostCSR &A0, double theta, int max_levels, int max_coarse, unsi
 }
 
 }  // namespace
+
+int device_plan_products(std::vector<HostLevel> &levels, const std::vector<char> &which, cudaStream_t s,
+                         std::string &err) {
+    Pool pool;
+    try {
+        for (size_t l = 0; l < levels.size() && l < which.size(); ++l)
+            if (which[l]) plan_products(levels[l], pool, s);
+    } catch (const Fail &f) {
+        cudaStreamSynchronize(s);
+        err = "device planning: " + f.msg;
+        return AMG_ERR_CUDA;
+    }
+    return AMG_OK;
+}
 
 int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int max_coarse,
                            unsigned long long seed, bool second_pass, cudaStream_t s,
