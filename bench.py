@@ -623,8 +623,20 @@ def run_kernel_only(args, wl):
                           "launches_per_step": P.amg_launch_count() - c0}))
         P.amg_destroy(ctx)
         return
+    if args.kernel_only == "setup":
+        # the device setup (PMIS + second pass), args.steps times
+        times = []
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.amg_setup_device(ctx, A, 0, True)
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t0) * 1e3)
+        print(json.dumps({"kernel": "setup_device", "workload": wl["workload"], "ms": times}))
+        P.amg_destroy(ctx)
+        return
     if args.kernel_only == "gcin":
-        theta, _ = load_theta()
+        theta = np.load(WEIGHTS_H32) if args.hidden == 32 else load_theta()[0]
         P.gnn_load_params(ctx, theta)
         times = []
         for k in range(args.steps):
@@ -655,6 +667,8 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", default=None)
+    ap.add_argument("--hidden", type=int, default=64, choices=[64, 32],
+                    help="GCIN width of the network --kernel-only gcin runs")
     args = ap.parse_args()
     if args.warmup < 3 and args.kernel_only is None:
         raise SystemExit("--warmup must be >= 3")

@@ -136,7 +136,9 @@ int amg_setup(amg_ctx *ctx, const amg_csr *A);
  * A_c = R (A P) as amg_setup, on the device; the hierarchy is then kept on
  * the host too (amg_get_level) and uploaded as by amg_setup.  A (host CSR) is
  * copied.  Same stopping rules and errors as amg_setup; AMG_ERR_CUDA also
- * covers device allocation failures. */
+ * covers device allocation failures.  With the second pass each level keeps
+ * about half the points, so meshes of millions of rows need max_levels of
+ * about 16 to keep the coarsest level within the dense solve's 4096 rows. */
 int amg_setup_device(amg_ctx *ctx, const amg_csr *A, unsigned long long seed, int second_pass);
 
 /* Load a caller-built hierarchy: A[0..n_levels-1] (finest first),
