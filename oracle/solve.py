@@ -107,6 +107,25 @@ def pseudo_inverse_values(A: TMat, c, s: float | None = None) -> torch.Tensor:
     return torch.where(on, q_diag, q_off)
 
 
+def pseudo_inverse_values_nodes(A: TMat, C, s: float | None = None) -> torch.Tensor:
+    """Q^-1 with one coefficient row per node, C (n x 5): the diagonal entry of
+    row i uses node i's (d0, d1, d2); an off-diagonal entry (i, j) uses the
+    mean of nodes i's and j's (o1, o2), so Q^-1 stays symmetric (reading: the
+    paper's coefficients are per level; equal rows reduce to that form)."""
+    if s is None:
+        s = smoother_scale(A)
+    C = torch.as_tensor(np.asarray(C, dtype=np.float64))
+    d = A.diag()
+    x = A.val / s
+    on = A.row == A.col
+    ci, cj = C[A.row], C[A.col]
+    f_d = ci[:, 0] + ci[:, 1] * x + ci[:, 2] * x * x
+    o1 = (ci[:, 3] + cj[:, 3]) / 2.0
+    o2 = (ci[:, 4] + cj[:, 4]) / 2.0
+    f_o = o1 * x + o2 * x * x
+    return torch.where(on, f_d / d[A.row], f_o / (d[A.row] + d[A.col]))
+
+
 def jacobi_values(A: TMat, omega: float) -> torch.Tensor:
     """Values of omega D^-1 on A's pattern (zero off the diagonal)."""
     d = A.diag()
@@ -185,6 +204,12 @@ class OHierarchy:
         """coeffs[l] = (d0, d1, d2, o1, o2) for level l (rows past the last smoothed level unused)."""
         for l, lv in enumerate(self.levels[:-1]):
             lv.M = pseudo_inverse_values(lv.A, coeffs[l], lv.s)
+            lv.cheb = None
+
+    def set_pseudo_inverse_nodes(self, node_coeffs):
+        """node_coeffs[l] = (n_l x 5) per-node coefficients of level l."""
+        for l, lv in enumerate(self.levels[:-1]):
+            lv.M = pseudo_inverse_values_nodes(lv.A, node_coeffs[l], lv.s)
             lv.cheb = None
 
     def set_chebyshev(self, degree: int = 3, lo: float = 1.0 / 30.0, hi: float = 1.1, n_power: int = 20):

@@ -71,6 +71,34 @@ def test_pseudo_inverse_symmetric_and_pattern():
     assert np.all(Q[Ad == 0] == 0)
 
 
+def test_node_coefficients_hand_worked():
+    # tridiag(-1, 2, -1) on 3 points, s = 1: x_ii = 2, x_ij = -1.  Nodes carry
+    # (d0, d1, d2, o1, o2) = (1,0,0,1,0), (0,1,0,3,0), (0,0,1,0,2):
+    # q_00 = 1/2, q_11 = 2/2, q_22 = 4/2; q_01 = ((1+3)/2 * -1) / 4 = -1/2;
+    # q_12 = ((3+0)/2 * -1 + (0+2)/2 * 1) / 4 = -1/8 (the same by symmetry)
+    A = W._coo_to_csr(3, 3, np.array([0, 0, 1, 1, 1, 2, 2]), np.array([0, 1, 0, 1, 2, 1, 2]),
+                      np.array([2.0, -1, -1, 2, -1, -1, 2]))
+    T = O.TMat.of(A)
+    C = [[1, 0, 0, 1, 0], [0, 1, 0, 3, 0], [0, 0, 1, 0, 2]]
+    q = O.pseudo_inverse_values_nodes(T, C).numpy()
+    expect = {(0, 0): 0.5, (0, 1): -0.5, (1, 0): -0.5, (1, 1): 1.0, (1, 2): -0.125, (2, 1): -0.125, (2, 2): 2.0}
+    for r, c, v in zip(T.row.numpy(), T.col.numpy(), q):
+        assert v == expect[(int(r), int(c))]
+
+
+def test_node_coefficients_reduce_to_level_form_and_stay_symmetric():
+    Acsr = W.fv_mesh("band", 2000, 4, max_aspect=100.0)[0]
+    A = O.TMat.of(Acsr)
+    c = [0.7, -0.1, 0.02, 0.3, -0.05]
+    same = np.tile(c, (Acsr.n_rows, 1))
+    assert torch.equal(O.pseudo_inverse_values_nodes(A, same), O.pseudo_inverse_values(A, c))
+    C = same + 0.1 * W.uniform_pm1(5, 5 * Acsr.n_rows).reshape(-1, 5)
+    q = O.pseudo_inverse_values_nodes(A, C)
+    Q = W.CSR(Acsr.n_rows, Acsr.n_cols, Acsr.row_ptr, Acsr.col, q.numpy()).to_dense()
+    np.testing.assert_allclose(Q, Q.T, rtol=0, atol=1e-15)
+    assert not torch.equal(q, O.pseudo_inverse_values(A, c))
+
+
 def test_cholesky_against_library_solve():
     A = W.fv_mesh("uniform", 200, 9)[0]
     Ad = A.to_dense()
