@@ -182,6 +182,16 @@ int amg_set_jacobi(amg_ctx *ctx, double omega);
  * V-cycle precision.  c = (omega, 0, 0, 0, 0) reproduces weighted Jacobi. */
 int amg_set_coeffs(amg_ctx *ctx, const double *c, int n_rows);
 
+/* The same smoother with one coefficient row per node instead of per level
+ * (a generalisation; the paper's coefficients are per level): c holds, level
+ * by level for l = 0 .. amg_num_levels() - 2, n_l rows of
+ * (d0, d1, d2, o1, o2) (host, n_values = 5 sum_l n_l doubles, copied).
+ * q_ii^-1 uses node i's (d0, d1, d2); q_ij^-1 uses the mean of nodes i's and
+ * j's (o1, o2), so Q^-1 stays symmetric.  Rows all equal to c_l give exactly
+ * amg_set_coeffs' values.  Errors: AMG_ERR_ARG (wrong n_values, NULL or
+ * non-finite values), AMG_ERR_STATE (no hierarchy), AMG_ERR_CUDA. */
+int amg_set_node_coeffs(amg_ctx *ctx, const double *c, long long n_values);
+
 /* Read back the smoother values of level `level` on A_l's pattern (nnz_A
  * entries, FP64 copy).  Jacobi leaves zeros off the diagonal. */
 int amg_get_smoother(const amg_ctx *ctx, int level, double *q_out);

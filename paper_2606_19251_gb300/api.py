@@ -92,6 +92,7 @@ def _declare(L):
         "amg_get_scales": (I, [P, pd]),
         "amg_set_jacobi": (I, [P, D]),
         "amg_set_coeffs": (I, [P, pd, I]),
+        "amg_set_node_coeffs": (I, [P, pd, C.c_longlong]),
         "amg_get_smoother": (I, [P, I, pd]),
         "gnn_load_params": (I, [P, pf, LL]),
         "gnn_predict_coeffs": (I, [P, pd]),
@@ -131,7 +132,7 @@ def exported_symbols():
     """Names of the C entry points this binding knows about."""
     return ["amg_default_options", "amg_create", "amg_destroy", "amg_last_error", "amg_setup", "amg_setup_device",
             "amg_load_hierarchy", "amg_num_levels", "amg_level_info", "amg_get_level", "amg_get_scales",
-            "amg_set_jacobi", "amg_set_coeffs", "amg_get_smoother", "gnn_load_params", "gnn_predict_coeffs",
+            "amg_set_jacobi", "amg_set_coeffs", "amg_set_node_coeffs", "amg_get_smoother", "gnn_load_params", "gnn_predict_coeffs",
             "amg_solve", "amg_solve_device", "amg_vcycle_device", "amg_smooth_device", "amg_spmv_device",
             "amg_judge", "amg_reroute", "amg_last_solve_rerouted", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
             "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
@@ -269,6 +270,12 @@ def amg_set_jacobi(ctx, omega=2.0 / 3.0):
 def amg_set_coeffs(ctx, c):
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, 5))
     return _check(ctx, lib().amg_set_coeffs(ctx, _dptr(c), c.shape[0]))
+
+
+def amg_set_node_coeffs(ctx, c_levels):
+    """c_levels[l]: (n_l x 5) per-node coefficients of smoothed level l."""
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).reshape(-1) for c in c_levels]))
+    return _check(ctx, lib().amg_set_node_coeffs(ctx, _dptr(flat), flat.size))
 
 
 def amg_get_smoother(ctx, level) -> np.ndarray:

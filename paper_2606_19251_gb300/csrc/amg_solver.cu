@@ -689,6 +689,32 @@ __global__ void k_assemble_q_dev(int nnz, const unsigned char *__restrict__ isd,
     q32[p] = static_cast<float>(q);
 }
 
+// Q^-1 values with one coefficient row per node (cn: n x 5): the diagonal of
+// row i from node i's (d0, d1, d2), an off-diagonal entry (i, j) from the mean
+// of nodes i's and j's (o1, o2) (a symmetric Q^-1); arithmetic as k_assemble_q.
+__global__ void k_assemble_q_nodes(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                   const unsigned char *__restrict__ isd, const double *__restrict__ bx,
+                                   const double *__restrict__ bw, const double *__restrict__ cn,
+                                   double *__restrict__ q64, float *__restrict__ q32) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const double *ci = cn + 5 * static_cast<size_t>(i);
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const double x = bx[p];
+        double f;
+        if (isd[p]) {
+            f = __dadd_rn(__dadd_rn(ci[0], __dmul_rn(ci[1], x)), __dmul_rn(__dmul_rn(ci[2], x), x));
+        } else {
+            const double *cj = cn + 5 * static_cast<size_t>(col[p]);
+            const double o1 = __dmul_rn(__dadd_rn(ci[3], cj[3]), 0.5), o2 = __dmul_rn(__dadd_rn(ci[4], cj[4]), 0.5);
+            f = __dadd_rn(__dmul_rn(o1, x), __dmul_rn(__dmul_rn(o2, x), x));
+        }
+        const double q = __dmul_rn(f, bw[p]);
+        q64[p] = q;
+        q32[p] = static_cast<float>(q);
+    }
+}
+
 __global__ void k_jacobi_vals(int n, const double *__restrict__ d, double omega, double *__restrict__ j64,
                               float *__restrict__ j32) {
     int i = blockIdx.x * kBlock + threadIdx.x;
@@ -1692,6 +1718,50 @@ int amg_set_coeffs(amg_ctx *c, const double *coef, int n_rows) {
     int rc = set_coeffs_device(c, coef, n_rows, c->stream);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
+    return AMG_OK;
+}
+
+int amg_set_node_coeffs(amg_ctx *c, const double *coef, long long n_values) {
+    if (!c) return AMG_ERR_ARG;
+    c->err.clear();
+    if (c->lev.empty()) return ctx_fail(c, "no hierarchy loaded"), AMG_ERR_STATE;
+    const int nlev = static_cast<int>(c->lev.size());
+    long long need = 0;
+    for (int l = 0; l < nlev - 1; ++l) need += 5LL * c->lev[l].n;
+    if (!coef || n_values != need)
+        return ctx_fail(c, "need 5 coefficients per node of every smoothed level"), AMG_ERR_ARG;
+    for (long long k = 0; k < need; ++k)
+        if (!std::isfinite(coef[k])) return ctx_fail(c, "non-finite coefficient"), AMG_ERR_ARG;
+    CK(cudaSetDevice(c->opt.device));
+    cudaStream_t s = c->stream;
+    if (need == 0) {
+        c->have_q = true;
+        c->smoother = AMG_SMOOTHER_GNN;
+        return AMG_OK;
+    }
+    double *d_c = nullptr;
+    CK(cudaMalloc(&d_c, sizeof(double) * need));
+    cudaError_t e = cudaMemcpyAsync(d_c, coef, sizeof(double) * need, cudaMemcpyHostToDevice, s);
+    long long off = 0;
+    for (int l = 0; l < nlev - 1 && e == cudaSuccess; ++l) {
+        const DevLevel &L = c->lev[l];
+        k_assemble_q_nodes<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.isd, L.bx, L.bw, d_c + off,
+                                                             L.q64, L.q32); AMG_COUNT();
+        if (L.fast && c->opt.precision == AMG_FP64) {
+            k_assemble_ma<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q64, L.A.v64,
+                                                                L.MA.v64, L.MA.v32); AMG_COUNT();
+        } else if (L.fast) {
+            k_assemble_ma32<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q32, L.A.v32,
+                                                                  L.MA.v32); AMG_COUNT();
+        }
+        off += 5LL * L.n;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_c);
+    if (e != cudaSuccess) return ctx_cuda_check(c, e, "assemble per-node pseudo-inverse");
+    c->have_q = true;
+    c->smoother = AMG_SMOOTHER_GNN;
     return AMG_OK;
 }
 
