@@ -381,6 +381,11 @@ void gcin_trainer_destroy(gcin_trainer *tr);
 const char *gcin_trainer_last_error(const gcin_trainer *tr);
 int gcin_trainer_get_params(const gcin_trainer *tr, float *theta_out);
 
+/* Replace the trainer's parameters with theta (host, n floats, n = the
+ * count it was created with; copied); Adam moments are kept.  The next
+ * backward needs a new forward.  Errors: AMG_ERR_ARG, AMG_ERR_CUDA. */
+int gcin_trainer_set_params(gcin_trainer *tr, const float *theta, long long n);
+
 /* Batched inference over every level of every problem (Algorithm 1 step 6),
  * keeping the activations for gcin_trainer_backward.  c_out (host) receives
  * sum_m amg_num_levels(problems[m]) rows of 5, problem by problem. */

@@ -108,6 +108,7 @@ def _declare(L):
         "gcin_trainer_destroy": (V, [P]),
         "gcin_trainer_last_error": (C.c_char_p, [P]),
         "gcin_trainer_get_params": (I, [P, pf]),
+        "gcin_trainer_set_params": (I, [P, pf, C.c_longlong]),
         "gcin_trainer_forward": (I, [P, I, C.POINTER(P), pd]),
         "gcin_trainer_backward": (I, [P, pd, pd]),
         "gcin_trainer_adam_step": (I, [P, D, D]),
@@ -135,7 +136,7 @@ def exported_symbols():
             "amg_set_jacobi", "amg_set_coeffs", "amg_set_node_coeffs", "amg_get_smoother", "gnn_load_params", "gnn_predict_coeffs",
             "amg_solve", "amg_solve_device", "amg_vcycle_device", "amg_smooth_device", "amg_spmv_device",
             "amg_judge", "amg_reroute", "amg_last_solve_rerouted", "gcin_trainer_create", "gcin_trainer_destroy", "gcin_trainer_last_error",
-            "gcin_trainer_get_params", "gcin_trainer_forward", "gcin_trainer_backward",
+            "gcin_trainer_get_params", "gcin_trainer_set_params", "gcin_trainer_forward", "gcin_trainer_backward",
             "gcin_trainer_adam_step", "amg_loss_grad", "amg_kernel_launch", "amg_vcycle_bytes",
             "amg_launch_count", "amg_residual_norm_noalloc", "amg_set_chebyshev", "amg_get_chebyshev", "gcin_tc_selftest"]
 
@@ -452,6 +453,11 @@ def gcin_trainer_get_params(tr) -> np.ndarray:
     t = np.zeros(tr.n_params, np.float32)
     _tcheck(tr, lib().gcin_trainer_get_params(tr, _fptr(t)))
     return t
+
+
+def gcin_trainer_set_params(tr, theta):
+    t = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+    return _tcheck(tr, lib().gcin_trainer_set_params(tr, _fptr(t), t.size))
 
 
 def gcin_trainer_forward(tr, ctxs) -> np.ndarray:

@@ -1339,6 +1339,19 @@ int gcin_trainer_get_params(const gcin_trainer *tc, float *theta_out) {
     return tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
 }
 
+int gcin_trainer_set_params(gcin_trainer *t, const float *theta, long long n) {
+    if (!t) return AMG_ERR_ARG;
+    t->err.clear();
+    if (!theta || n != t->n) return tr_fail(t, AMG_ERR_ARG, "parameter count differs from the trainer's");
+    int rc = tr_cuda(t, cudaSetDevice(t->device), "cudaSetDevice");
+    if (rc) return rc;
+    rc = tr_cuda(t, cudaMemcpyAsync(t->theta, theta, sizeof(float) * n, cudaMemcpyHostToDevice, t->stream),
+                 "params upload");
+    if (rc) return rc;
+    t->have_forward = false;
+    return tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
+}
+
 int gcin_trainer_forward(gcin_trainer *t, int n_problems, amg_ctx *const *problems, double *c_out) {
     if (!t) return AMG_ERR_ARG;
     t->err.clear();
