@@ -18,10 +18,10 @@
 //                round, so rounds <= n)
 //   direct interpolation, one thread per row in the row's entry order
 //   R = P^T      counting transpose, rows sorted by column
-//   Galerkin     A_c = R (A P): two row-wise products, each row hashed into
-//                its own open-addressing table (load <= 2/3), products
-//                summed in the row-by-row (Gustavson) order, the row's
-//                entries sorted by column
+//   Galerkin     A_c = R (A P): two row-wise products, a warp per row: the
+//                row's columns hashed into its own open-addressing table
+//                (load <= 2/3), compacted and rank-sorted; each entry then
+//                summed over the row in ascending order (the Gustavson order)
 // Offsets come from a three-phase exclusive scan.  The same stopping rules as
 // the host setup; the finished hierarchy is copied to host CSR.
 //
@@ -437,159 +437,143 @@ __global__ void k_spgemm_size(int nX, const int *__restrict__ X_rp, const int *_
     hsz[i] = h;
 }
 
-// Row i: every product x_ik y_kj accumulated into the row's table slot of j
-// in (k, then j) row order; the distinct columns are then compacted to the
-// front of the table and sorted.  cnt[i] = number of distinct columns.
-__global__ void k_spgemm_hash(int nX, const int *__restrict__ X_rp, const int *__restrict__ X_col,
-                              const double *__restrict__ X_val, const int *__restrict__ Y_rp,
-                              const int *__restrict__ Y_col, const double *__restrict__ Y_val,
-                              const long long *__restrict__ hoff, int *__restrict__ keys, double *__restrict__ vals,
-                              int *__restrict__ cnt) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= nX) return;
+// The products below take one warp per output row i.  Symbolic pass: the
+// lanes insert every column j of Y_k, k in X_i, into the row's own
+// open-addressing table (atomicCAS on the key), compact the distinct columns
+// to the front of the table in slot order (ballot prefix), rank each column
+// by the number of smaller ones and write them sorted to skeys; cnt[i] = the
+// number of columns.  Numeric pass: lane t owns output entries t, t + 32, ...
+// and sums x_ik y_kj over k in X_i in ascending order, finding j in the
+// sorted row Y_k by binary search: the row-by-row (Gustavson) summation order
+// of each entry, deterministic and without atomics on values.
+__device__ __forceinline__ int find_sorted(const int *__restrict__ col, int lo, int hi, int j) {
+    // index of j in col[lo, hi) (ascending), or -1
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int c = col[mid];
+        if (c == j) return mid;
+        if (c < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return -1;
+}
+
+__global__ void k_sym_warp(int nX, const int *__restrict__ X_rp, const int *__restrict__ X_col,
+                           const int *__restrict__ Y_rp, const int *__restrict__ Y_col,
+                           const long long *__restrict__ hoff, int *__restrict__ table, int *__restrict__ skeys,
+                           int *__restrict__ cnt) {
+    const long long wid = (static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (wid >= nX) return;                       // warp-uniform
+    const int i = static_cast<int>(wid);
     const long long o = hoff[i], size = hoff[i + 1] - o;
     if (size == 0) {
-        cnt[i] = 0;
+        if (lane == 0) cnt[i] = 0;
         return;
     }
-    int *K = keys + o;
-    double *V = vals + o;
+    int *T = table + o;
     const unsigned long long mask = static_cast<unsigned long long>(size) - 1ull;
-    for (long long t = 0; t < size; ++t) K[t] = -1;
+    for (long long t = lane; t < size; t += 32) T[t] = -1;
+    __syncwarp();
     for (int p = X_rp[i]; p < X_rp[i + 1]; ++p) {
         const int k = X_col[p];
-        const double x = X_val[p];
-        for (int q = Y_rp[k]; q < Y_rp[k + 1]; ++q) {
+        for (int q = Y_rp[k] + lane; q < Y_rp[k + 1]; q += 32) {
             const int j = Y_col[q];
-            const double prod = x * Y_val[q];
             unsigned long long h = (static_cast<unsigned long long>(static_cast<unsigned>(j)) * 0x9E3779B1ull) & mask;
             while (true) {
-                const int kk = K[h];
-                if (kk == j) {
-                    V[h] += prod;
-                    break;
-                }
-                if (kk == -1) {
-                    K[h] = j;
-                    V[h] = prod;
-                    break;
-                }
+                const int prev = atomicCAS(T + h, -1, j);
+                if (prev == -1 || prev == j) break;
                 h = (h + 1ull) & mask;
             }
         }
     }
-    int u = 0;
-    for (long long t = 0; t < size; ++t) {
-        const int kk = K[t];
-        if (kk != -1) {
-            const double v = V[t];
-            K[u] = kk;
-            V[u] = v;
-            ++u;
-        }
+    __syncwarp();
+    int u = 0;                                   // distinct columns so far (warp-uniform)
+    for (long long base = 0; base < size; base += 32) {
+        const long long t = base + lane;
+        const int key = t < size ? T[t] : -1;
+        const unsigned occ = __ballot_sync(0xffffffffu, key != -1);
+        __syncwarp();                            // every lane has read its slot before any write
+        if (key != -1) T[u + __popc(occ & ((1u << lane) - 1u))] = key;
+        u += __popc(occ);
+        __syncwarp();
     }
-    heap_sort(K, V, u);
-    cnt[i] = u;
+    for (int a = lane; a < u; a += 32) {
+        const int key = T[a];
+        int rank = 0;
+        for (int b2 = 0; b2 < u; ++b2) rank += T[b2] < key ? 1 : 0;
+        skeys[o + rank] = key;
+    }
+    if (lane == 0) cnt[i] = u;
 }
 
-// Pattern of row i of A A: the distinct columns j of A_k over k in A_i,
-// sorted, each with its number of contributing pairs (p, q).
-__global__ void k_pattern_hash(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                               const long long *__restrict__ hoff, int *__restrict__ keys, int *__restrict__ counts,
-                               int *__restrict__ cnt) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= n) return;
-    const long long o = hoff[i], size = hoff[i + 1] - o;
-    if (size == 0) {
-        cnt[i] = 0;
-        return;
-    }
-    int *K = keys + o, *V = counts + o;
-    const unsigned long long mask = static_cast<unsigned long long>(size) - 1ull;
-    for (long long t = 0; t < size; ++t) K[t] = -1;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const int k = col[p];
-        for (int q = rp[k]; q < rp[k + 1]; ++q) {
-            const int j = col[q];
-            unsigned long long h = (static_cast<unsigned long long>(static_cast<unsigned>(j)) * 0x9E3779B1ull) & mask;
-            while (true) {
-                const int kk = K[h];
-                if (kk == j) {
-                    ++V[h];
-                    break;
-                }
-                if (kk == -1) {
-                    K[h] = j;
-                    V[h] = 1;
-                    break;
-                }
-                h = (h + 1ull) & mask;
-            }
-        }
-    }
-    int u = 0;
-    for (long long t = 0; t < size; ++t) {
-        const int kk = K[t];
-        if (kk != -1) {
-            const int v = V[t];
-            K[u] = kk;
-            V[u] = v;
-            ++u;
-        }
-    }
-    heap_sort(K, V, u);
-    cnt[i] = u;
-}
-
-__global__ void k_pattern_copy(int n, const long long *__restrict__ hoff, const int *__restrict__ keys,
-                               const int *__restrict__ counts, const int *__restrict__ Z_rp, int *__restrict__ Z_col,
-                               int *__restrict__ entry_cnt) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= n) return;
+__global__ void k_num_warp(int nX, const int *__restrict__ X_rp, const int *__restrict__ X_col,
+                           const double *__restrict__ X_val, const int *__restrict__ Y_rp,
+                           const int *__restrict__ Y_col, const double *__restrict__ Y_val,
+                           const long long *__restrict__ hoff, const int *__restrict__ skeys,
+                           const int *__restrict__ Z_rp, int *__restrict__ Z_col, double *__restrict__ Z_val) {
+    const long long wid = (static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (wid >= nX) return;
+    const int i = static_cast<int>(wid);
     const long long o = hoff[i];
     const int w = Z_rp[i], u = Z_rp[i + 1] - w;
-    for (int t = 0; t < u; ++t) {
-        Z_col[w + t] = keys[o + t];
-        entry_cnt[w + t] = counts[o + t];
-    }
-}
-
-// Pairs (p, q) of row i grouped by output entry (binary search in the row's
-// sorted pattern), each group in ascending p: one thread per row writes its
-// own groups in order, so the list is the host planner's.
-__global__ void k_pairs_fill(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                             const int *__restrict__ Z_rp, const int *__restrict__ Z_col, int *__restrict__ cursor,
-                             int *__restrict__ pair_p, int *__restrict__ pair_q) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= n) return;
-    const int z0 = Z_rp[i], z1 = Z_rp[i + 1];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const int k = col[p];
-        for (int q = rp[k]; q < rp[k + 1]; ++q) {
-            const int j = col[q];
-            int lo = z0, hi = z1 - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi) / 2;
-                if (Z_col[mid] < j) lo = mid + 1;
-                else hi = mid;
-            }
-            const int at = cursor[lo]++;
-            pair_p[at] = p;
-            pair_q[at] = q;
+    for (int t = lane; t < u; t += 32) {
+        const int j = skeys[o + t];
+        double acc = 0.0;
+        for (int p = X_rp[i]; p < X_rp[i + 1]; ++p) {
+            const int k = X_col[p];
+            const int q = find_sorted(Y_col, Y_rp[k], Y_rp[k + 1], j);
+            if (q >= 0) acc += X_val[p] * Y_val[q];
         }
+        Z_col[w + t] = j;
+        Z_val[w + t] = acc;
     }
 }
 
-__global__ void k_spgemm_copy(int nX, const long long *__restrict__ hoff, const int *__restrict__ keys,
-                              const double *__restrict__ vals, const int *__restrict__ Z_rp, int *__restrict__ Z_col,
-                              double *__restrict__ Z_val) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= nX) return;
+// Pattern of A A (sorted columns) with the number of pairs (p, q) of each entry.
+__global__ void k_pat_count_warp(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                 const long long *__restrict__ hoff, const int *__restrict__ skeys,
+                                 const int *__restrict__ Z_rp, int *__restrict__ Z_col, int *__restrict__ entry_cnt) {
+    const long long wid = (static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (wid >= n) return;
+    const int i = static_cast<int>(wid);
     const long long o = hoff[i];
     const int w = Z_rp[i], u = Z_rp[i + 1] - w;
-    for (int t = 0; t < u; ++t) {
-        Z_col[w + t] = keys[o + t];
-        Z_val[w + t] = vals[o + t];
+    for (int t = lane; t < u; t += 32) {
+        const int j = skeys[o + t];
+        int c = 0;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            const int k = col[p];
+            c += find_sorted(col, rp[k], rp[k + 1], j) >= 0 ? 1 : 0;
+        }
+        Z_col[w + t] = j;
+        entry_cnt[w + t] = c;
+    }
+}
+
+// Pair list of M A: entry e's pairs (p, q) from pair_ptr[e], in ascending p
+// (the host planner's order).
+__global__ void k_pairs_warp(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                             const int *__restrict__ Z_rp, const int *__restrict__ Z_col,
+                             const int *__restrict__ pair_ptr, int *__restrict__ pair_p, int *__restrict__ pair_q) {
+    const long long wid = (static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (wid >= n) return;
+    const int i = static_cast<int>(wid);
+    for (int e = Z_rp[i] + lane; e < Z_rp[i + 1]; e += 32) {
+        const int j = Z_col[e];
+        int at = pair_ptr[e];
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            const int k = col[p];
+            const int q = find_sorted(col, rp[k], rp[k + 1], j);
+            if (q >= 0) {
+                pair_p[at] = p;
+                pair_q[at] = q;
+                ++at;
+            }
+        }
     }
 }
 
@@ -651,18 +635,18 @@ DevCSR spgemm(const DevCSR &X, const DevCSR &Y, Pool &pool, cudaStream_t s) {
     k_spgemm_size<<<grid_for(n), kBlock, 0, s>>>(n, X.rp, X.col, Y.rp, hoff); AMG_COUNT();
     const long long total = scan_counts<long long>(hoff, n, pool, s);
     if (total > 2000000000LL) throw Fail{"sparse product too large for 32-bit offsets"};
-    int *keys = need<int>(pool, total);
-    double *vals = need<double>(pool, total);
+    int *table = need<int>(pool, total), *skeys = need<int>(pool, total);
     DevCSR Z;
     Z.n_rows = n;
     Z.n_cols = Y.n_cols;
     Z.rp = need<int>(pool, n + 1);
     check(cudaMemsetAsync(Z.rp + n, 0, sizeof(int), s), "memset");
-    k_spgemm_hash<<<grid_for(n), kBlock, 0, s>>>(n, X.rp, X.col, X.val, Y.rp, Y.col, Y.val, hoff, keys, vals, Z.rp); AMG_COUNT();
+    const int wg = grid_for(static_cast<long long>(n) * 32);
+    k_sym_warp<<<wg, kBlock, 0, s>>>(n, X.rp, X.col, Y.rp, Y.col, hoff, table, skeys, Z.rp); AMG_COUNT();
     Z.nnz = scan_counts<int>(Z.rp, n, pool, s);
     Z.col = need<int>(pool, Z.nnz);
     Z.val = need<double>(pool, Z.nnz);
-    k_spgemm_copy<<<grid_for(n), kBlock, 0, s>>>(n, hoff, keys, vals, Z.rp, Z.col, Z.val); AMG_COUNT();
+    k_num_warp<<<wg, kBlock, 0, s>>>(n, X.rp, X.col, X.val, Y.rp, Y.col, Y.val, hoff, skeys, Z.rp, Z.col, Z.val); AMG_COUNT();
     check(cudaGetLastError(), "sparse product");
     return Z;
 }
@@ -706,20 +690,19 @@ void plan_products(HostLevel &H, Pool &pool, cudaStream_t s) {
     k_spgemm_size<<<grid_for(n), kBlock, 0, s>>>(n, A.rp, A.col, A.rp, hoff); AMG_COUNT();
     const long long total = scan_counts<long long>(hoff, n, pool, s);
     if (total > 2000000000LL) throw Fail{"product pattern too large for 32-bit offsets"};
-    int *keys = need<int>(pool, total), *counts = need<int>(pool, total);
+    int *table = need<int>(pool, total), *skeys = need<int>(pool, total);
     int *Z_rp = need<int>(pool, n + 1);
     check(cudaMemsetAsync(Z_rp + n, 0, sizeof(int), s), "memset");
-    k_pattern_hash<<<grid_for(n), kBlock, 0, s>>>(n, A.rp, A.col, hoff, keys, counts, Z_rp); AMG_COUNT();
+    const int wg = grid_for(static_cast<long long>(n) * 32);
+    k_sym_warp<<<wg, kBlock, 0, s>>>(n, A.rp, A.col, A.rp, A.col, hoff, table, skeys, Z_rp); AMG_COUNT();
     const int nz = scan_counts<int>(Z_rp, n, pool, s);
     int *Z_col = need<int>(pool, nz);
     int *pp = need<int>(pool, static_cast<long long>(nz) + 1);
     check(cudaMemsetAsync(pp + nz, 0, sizeof(int), s), "memset");
-    k_pattern_copy<<<grid_for(n), kBlock, 0, s>>>(n, hoff, keys, counts, Z_rp, Z_col, pp); AMG_COUNT();
+    k_pat_count_warp<<<wg, kBlock, 0, s>>>(n, A.rp, A.col, hoff, skeys, Z_rp, Z_col, pp); AMG_COUNT();
     const int npairs = scan_counts<int>(pp, nz, pool, s);
-    int *cursor = need<int>(pool, nz);
-    check(cudaMemcpyAsync(cursor, pp, sizeof(int) * nz, cudaMemcpyDeviceToDevice, s), "copy");
     int *pair_p = need<int>(pool, npairs), *pair_q = need<int>(pool, npairs);
-    k_pairs_fill<<<grid_for(n), kBlock, 0, s>>>(n, A.rp, A.col, Z_rp, Z_col, cursor, pair_p, pair_q); AMG_COUNT();
+    k_pairs_warp<<<wg, kBlock, 0, s>>>(n, A.rp, A.col, Z_rp, Z_col, pp, pair_p, pair_q); AMG_COUNT();
     const DevCSR RA = spgemm(R, A, pool, s);
     // back to the host level
     H.MA = HostCSR{};
