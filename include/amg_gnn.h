@@ -263,8 +263,10 @@ int amg_judge(amg_ctx *ctx, const double *b, int n_cycles, double *metric);
  * (>= 4) V-cycles from x = 0 on b with each smoother and compares
  *   m1 = log10(||r_n^GNN|| / ||r_n^J||)                       (Sec. 3.3) and
  *   m2 = the same log-ratio for the reduction over the last n/4 cycles,
- * which exposes smoothers that start well but converge slowly.  *metric =
- * max(m1, m2) (+inf when the learned smoother diverges or alone stagnates).
+ * which exposes smoothers that start well but converge slowly; n is the
+ * last cycle, or the first at which either relative residual is <= 1e-12 if
+ * earlier (past it both runs sit at rounding level).  *metric = max(m1, m2)
+ * (+inf when the learned smoother diverges, or alone stagnates above 1e-12).
  * If it is not negative the context falls back to omega-Jacobi and
  * amg_last_error reports the rerouting; *smoother receives the smoother in
  * use afterwards.  metric/smoother may be NULL. */

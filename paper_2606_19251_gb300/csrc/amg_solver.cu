@@ -1977,25 +1977,35 @@ int amg_reroute(amg_ctx *c, const double *b, int n_cycles, double *metric, int *
     if (rc == AMG_ERR_CUDA || st[0] == AMG_ERR_CUDA) return AMG_ERR_CUDA;
     // metric 1: log10(||r_n^GNN|| / ||r_n^J||) (Sec. 3.3); metric 2: the same
     // ratio for the reduction over the last quarter of the cycles, which
-    // exposes smoothers that start well but converge slowly
+    // exposes smoothers that start well but converge slowly.  Both stop at the
+    // first cycle at which either relative residual is down to kProbeFloor:
+    // past it both iterations sit at rounding level and their ratios are noise.
+    constexpr double kProbeFloor = 1e-12;
+    auto floor_cycle = [&](int pass) {
+        for (int t = 1; t <= k[pass]; ++t)
+            if (h[pass][t] <= kProbeFloor) return t;
+        return k[pass];
+    };
     double m;
     if (st[0] == AMG_ERR_DIVERGED) {
         m = INFINITY;
     } else if (st[1] == AMG_ERR_DIVERGED) {
         m = -INFINITY;
     } else {
-        const int n = std::min(k[0], k[1]);
+        const int n = std::min(floor_cycle(0), floor_cycle(1));
         const int q = std::max(1, n / 4);
         const double m1 = std::log10(h[0][n] / h[1][n]);
         const double m2 = (n > q) ? std::log10((h[0][n] / h[0][n - q]) / (h[1][n] / h[1][n - q])) : m1;
-        const bool stalled = (st[0] == AMG_ERR_STAGNATED && st[1] != AMG_ERR_STAGNATED);
+        // a stagnating learned smoother counts only if it stalled above the floor
+        const bool stalled = st[0] == AMG_ERR_STAGNATED && st[1] != AMG_ERR_STAGNATED && floor_cycle(0) == k[0] &&
+                             h[0][k[0]] > kProbeFloor;
         m = stalled ? INFINITY : std::max(m1, m2);
     }
     if (metric) *metric = m;
     if (m < 0.0 && st[1] != AMG_ERR_DIVERGED) {
         // arm the in-solve check: over any 10 cycles the learned smoother must
         // gain at least half the decades Jacobi gained in this probe
-        const int n = k[1], q = std::max(1, n / 4);
+        const int n = floor_cycle(1), q = std::max(1, n / 4);
         const double rate10 = std::pow(h[1][n] / h[1][n - q], 10.0 / q);
         c->stall_ratio = (rate10 > 0.0 && rate10 < 1.0) ? std::sqrt(rate10) : 0.0;
     }

@@ -22,6 +22,13 @@ trained on the same C3 batch:
 
     python -m paper_2606_19251_gb300.weights.make_weights --hidden 32 \
         --out paper_2606_19251_gb300/weights/gcin_c3_h32.npy
+
+gcin_struct.npy / gcin_struct_h32.npy are trained on Cartesian grids with
+immersed bodies (workloads.structured_batch: 64 training and 8 validation
+grids, 2D and 3D), the setting App. B.3 halves the width for:
+
+    python -m paper_2606_19251_gb300.weights.make_weights --dataset structured [--hidden 32] \
+        --out paper_2606_19251_gb300/weights/gcin_struct[_h32].npy
 """
 import argparse
 import json
@@ -51,6 +58,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="arithmetic of the forward node linears during training")
     ap.add_argument("--hidden", type=int, default=64, choices=[64, 32], help="GCIN width (App. A.1: 64; App. B.3: 32)")
+    ap.add_argument("--dataset", default="c3", choices=["c3", "structured"],
+                    help="C3 unstructured meshes or Cartesian grids with immersed bodies")
     ap.add_argument("--out", default=os.path.join(HERE, "gcin_c3.npy"))
     args = ap.parse_args()
     import workloads as W
@@ -58,8 +67,12 @@ def main():
     from paper_2606_19251_gb300.train import train
     _build.build()
     t0 = time.time()
-    mats = W.c3_batch(args.meshes, seed=0)
-    val = W.c3_batch(8, seed=1)
+    if args.dataset == "structured":
+        mats = W.structured_batch(args.meshes, seed=0)
+        val = W.structured_batch(8, seed=1)
+    else:
+        mats = W.c3_batch(args.meshes, seed=0)
+        val = W.c3_batch(8, seed=1)
     # optional widening of the training distribution (not part of the C3 batch)
     for k in range(args.extra_band1000):
         n = int(2000 + 18000 * W.uniform01(7000 + k, 1)[0])
@@ -76,7 +89,7 @@ def main():
     with open(os.path.splitext(args.out)[0] + "_log.json", "w") as f:
         json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "n_vc": args.nvc,
                    "extra_band1000": args.extra_band1000, "extra_airfoil": args.extra_airfoil,
-                   "precision": args.precision, "hidden": args.hidden,
+                   "precision": args.precision, "hidden": args.hidden, "dataset": args.dataset,
                    "val_cycles": args.val_cycles, "rows": rows,
                    "seconds": time.time() - t0}, f, indent=1)
     print("wrote", args.out, flush=True)

@@ -251,6 +251,32 @@ def test_device_solve_matches_host_solve(cases):
         P.amg_destroy(ctx)
 
 
+def test_reroute_probe_stops_at_rounding_floor(cases):
+    """On a fast-converging mesh both 30-cycle probe runs reach rounding level
+    early; the metric compares them at the first cycle either is <= 1e-12."""
+    A, levels = cases["c1_64"]
+    b = W.rhs_uniform(7, A.n_rows)
+    coeffs = [[0.75, 0, 0, 0, 0]] * len(levels)
+    hg = O.solve(oracle_hier(levels, "pinv", coeffs), b, tol=0.0, max_iter=30).history
+    hj = O.solve(oracle_hier(levels), b, tol=0.0, max_iter=30).history
+
+    def first_floor(h):
+        return next((t for t in range(1, len(h)) if h[t] <= 1e-12), len(h) - 1)
+
+    n = min(first_floor(hg), first_floor(hj))
+    assert n < 30
+    q = max(1, n // 4)
+    m_ref = max(np.log10(hg[n] / hj[n]), np.log10((hg[n] / hg[n - q]) / (hj[n] / hj[n - q])))
+    ctx = ctx_setup(A)
+    try:
+        P.amg_set_coeffs(ctx, coeffs)
+        m, sm = P.amg_reroute(ctx, b, 30)
+        assert abs(m - m_ref) < 1e-3, (m, m_ref, n)
+        assert (sm == P.AMG_SMOOTHER_GNN) == (m_ref < 0)
+    finally:
+        P.amg_destroy(ctx)
+
+
 @pytest.mark.parametrize("n_cycles", [1, 4])
 def test_judge_matches_oracle(cases, n_cycles):
     A, levels = cases["band_4k"]

@@ -324,3 +324,20 @@ def test_poisson7_closed_form_spectrum():
     np.testing.assert_allclose(ev, ref, rtol=1e-12, atol=1e-12)
     B = W.poisson7(8, body_ratio=1e-2).to_dense()
     assert np.allclose(B, B.T) and np.linalg.eigvalsh(B).min() > 0
+
+
+def test_poisson5_body_workload():
+    # conductivity 1 everywhere is the plain 5-point Laplacian; with a body the
+    # operator stays symmetric positive definite, interior rows sum to zero,
+    # and couplings across the body boundary are harmonic means
+    A = W.poisson5(24)
+    B = W.poisson5_body(24, 1.0)
+    assert np.array_equal(A.row_ptr, B.row_ptr) and np.array_equal(A.col, B.col) and np.array_equal(A.val, B.val)
+    m, ratio = 40, 1e-2
+    D = W.poisson5_body(m, ratio, 0.25).to_dense()
+    np.testing.assert_array_equal(D, D.T)
+    assert np.linalg.eigvalsh(D).min() > 0
+    i, j = np.divmod(np.arange(m * m), m)
+    interior = (i > 0) & (i < m - 1) & (j > 0) & (j < m - 1)
+    np.testing.assert_allclose(D.sum(1)[interior], 0.0, atol=1e-13)
+    assert np.isclose(-D.min(), 1.0) and np.isclose(np.sort(np.unique(-D[D < 0]))[1], 2 * ratio / (1 + ratio))

@@ -39,7 +39,7 @@ import numpy as np
 __all__ = [
     "CSR", "splitmix64", "uniform01", "uniform_pm1", "poisson5", "fv_mesh",
     "rhs_uniform", "rhs_zero_mean", "gcin_init_params", "c2_matrix",
-    "c3_batch", "c4_matrix", "GCIN_PARAM_SIZES", "gcin_param_sizes",
+    "c3_batch", "c4_matrix", "GCIN_PARAM_SIZES", "gcin_param_sizes", "poisson5_body", "structured_batch",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -148,6 +148,58 @@ def poisson7(m: int, body_ratio: float = 1.0, radius: float = 0.2) -> CSR:
     cols.append(idx.ravel())
     vals.append(diag.ravel())
     return _coo_to_csr(n, n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def poisson5_body(m: int, body_ratio: float = 1.0, radius: float = 0.2, center=(0.5, 0.5)) -> CSR:
+    """5-point finite-volume Laplacian on an m x m interior grid of the unit
+    square, Dirichlet eliminated, with cells inside a disk (radius, center)
+    of conductivity body_ratio; face coefficients are harmonic means of the two
+    cells, boundary faces use the cell's own (the 2D analogue of poisson7)."""
+    n = m * m
+    h = 1.0 / (m + 1)
+    g = (np.arange(m) + 1) * h
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    cond = np.where((X - center[0]) ** 2 + (Y - center[1]) ** 2 < radius ** 2, body_ratio, 1.0)
+    idx = np.arange(n).reshape(m, m)
+    rows, cols, vals = [], [], []
+    diag = np.zeros((m, m))
+    for axis in range(2):
+        for side in (-1, 1):
+            nb = np.roll(cond, -side, axis=axis)
+            face = 2.0 * cond * nb / (cond + nb)
+            edge = [slice(None)] * 2
+            edge[axis] = slice(m - 1, m) if side == 1 else slice(0, 1)
+            face[tuple(edge)] = cond[tuple(edge)]          # Dirichlet face
+            diag += face
+            inner = [slice(None)] * 2
+            inner[axis] = slice(0, m - 1) if side == 1 else slice(1, m)
+            inner = tuple(inner)
+            rows.append(idx[inner].ravel())
+            cols.append(np.roll(idx, -side, axis=axis)[inner].ravel())
+            vals.append(-face[inner].ravel())
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    return _coo_to_csr(n, n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def structured_batch(n_meshes: int, seed: int = 0) -> list:
+    """Cartesian training set for the structured-mesh networks: alternating 2D
+    grids (m in 16..64, poisson5_body) and 3D grids (m in 8..16, poisson7),
+    each with an immersed body of conductivity 10^-U[0, 3] and radius
+    U[0.1, 0.3] (2D disks off-centre by up to 0.15)."""
+    out = []
+    for k in range(n_meshes):
+        u = uniform01(_sub_seed(seed, 9000 + k), 5)
+        ratio = 10.0 ** (-3.0 * u[1])
+        radius = 0.1 + 0.2 * u[2]
+        if k % 2 == 0:
+            m = 16 + int(48 * u[0])
+            out.append(poisson5_body(m, ratio, radius, (0.35 + 0.3 * u[3], 0.35 + 0.3 * u[4])))
+        else:
+            m = 8 + int(8 * u[0])
+            out.append(poisson7(m, ratio, radius))
+    return out
 
 
 def _coo_to_csr(nr, nc, r, c, v) -> CSR:
