@@ -48,21 +48,35 @@ struct DevCSR {
     double *val = nullptr;
 };
 
-// device allocations of one setup call, freed together
+// device allocations of one setup call: 256-byte aligned pieces cut from
+// chunks of at least 64 MB (a few cudaMalloc calls instead of hundreds),
+// freed together
 struct Pool {
-    std::vector<void *> ptrs;
+    static constexpr size_t kChunk = size_t(64) << 20;
+    std::vector<void *> chunks;
+    char *cur = nullptr;
+    size_t left = 0;
     cudaError_t err = cudaSuccess;
     template <class T>
     T *get(long long n) {
         if (err != cudaSuccess) return nullptr;
-        void *p = nullptr;
-        err = cudaMalloc(&p, static_cast<size_t>(std::max<long long>(1, n)) * sizeof(T));
-        if (err != cudaSuccess) return nullptr;
-        ptrs.push_back(p);
-        return static_cast<T *>(p);
+        const size_t bytes = (static_cast<size_t>(std::max<long long>(1, n)) * sizeof(T) + 255) & ~size_t(255);
+        if (bytes > left) {
+            const size_t cb = std::max(bytes, kChunk);
+            void *p = nullptr;
+            err = cudaMalloc(&p, cb);
+            if (err != cudaSuccess) return nullptr;
+            chunks.push_back(p);
+            cur = static_cast<char *>(p);
+            left = cb;
+        }
+        T *r = reinterpret_cast<T *>(cur);
+        cur += bytes;
+        left -= bytes;
+        return r;
     }
     ~Pool() {
-        for (void *p : ptrs) cudaFree(p);
+        for (void *p : chunks) cudaFree(p);
     }
 };
 
@@ -766,22 +780,31 @@ void build(const HostCSR &A0, double theta, int max_levels, int max_coarse, unsi
         int8_t *newc = need<int8_t>(pool, n);
         int *remaining = need<int>(pool, 1);
         k_pmis_init<<<g, kBlock, 0, s>>>(n, T_rp, seed_l, lam, state); AMG_COUNT();
-        for (int round = 0;; ++round) {
+        // rounds in batches of kBatch between read-backs: a round after the
+        // split is complete decides nothing and changes nothing
+        constexpr int kBatch = 4;
+        for (int round = 0;; round += kBatch) {
             if (round > n) throw Fail{"PMIS split did not finish"};
-            check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
-            k_pmis_select<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, lam, state, newc); AMG_COUNT();
-            k_pmis_update<<<g, kBlock, 0, s>>>(n, S_rp, S_col, newc, state, remaining); AMG_COUNT();
+            for (int b = 0; b < kBatch; ++b) {
+                check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
+                k_pmis_select<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, lam, state, newc); AMG_COUNT();
+                k_pmis_update<<<g, kBlock, 0, s>>>(n, S_rp, S_col, newc, state, remaining); AMG_COUNT();
+            }
             if (read_one(remaining, s) == 0) break;
         }
         if (second) {
             int *v = need<int>(pool, n);
-            for (int round = 0;; ++round) {
+            // batched like the PMIS rounds: once a round finds no violating
+            // pair, later rounds find none and promote nothing
+            for (int round = 0;; round += kBatch) {
                 if (round > n) throw Fail{"second pass did not finish"};
-                check(cudaMemsetAsync(v, 0, sizeof(int) * n, s), "memset");
-                check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
-                k_h1_violations<<<g, kBlock, 0, s>>>(n, S_rp, S_col, state, v, remaining); AMG_COUNT();
+                for (int b = 0; b < kBatch; ++b) {
+                    check(cudaMemsetAsync(v, 0, sizeof(int) * n, s), "memset");
+                    check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
+                    k_h1_violations<<<g, kBlock, 0, s>>>(n, S_rp, S_col, state, v, remaining); AMG_COUNT();
+                    k_h1_promote<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, v, seed_l, state); AMG_COUNT();
+                }
                 if (read_one(remaining, s) == 0) break;
-                k_h1_promote<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, v, seed_l, state); AMG_COUNT();
             }
         }
         int *cidx = need<int>(pool, n + 1);
