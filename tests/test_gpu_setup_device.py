@@ -63,6 +63,20 @@ def test_device_setup_matches_oracle(name, seed, mode):
         P.amg_destroy(ctx)
 
 
+@pytest.mark.parametrize("make", [lambda: W.poisson7(14, 1e-2), lambda: W.c5_problem(3, n_rhs=1, n_surface=120, n_far=3000)[0]],
+                         ids=["sphere_14", "airfoil_small"])
+def test_device_setup_3d_and_airfoil(make):
+    """The 3D stencil and the airfoil's wall layers (couplings over nine
+    decades) through the same kernels, second pass on."""
+    A = make()
+    levels = OS.build_hierarchy(A, coarsening="pmis-h1", seed=4)
+    ctx = device_ctx(A, 4)
+    try:
+        assert_same_hierarchy(ctx, levels)
+    finally:
+        P.amg_destroy(ctx)
+
+
 @pytest.mark.parametrize("mode", list(MODES))
 def test_device_setup_full_size_c2(mode):
     A = W.c2_matrix(0)
