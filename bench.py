@@ -501,6 +501,9 @@ def run_gpu(args, wl, rank, world):
             us_g = e0.elapsed_time(e1) * 1e3 / 50
             gbs = bg / (us_g * 1e-6) / 1e9
             hbm["kernels"][name_k] = {"bytes": bg, "us": us_g, "achieved": gbs, "frac": gbs / peak}
+            if kid_g == P.AMG_K_OUTER:
+                hbm["kernels"][name_k]["bound"] = ("alu: FP64 pipe (ncu sm__pipe_fp64_cycles_active 86 %, "
+                                                   "profiles/k_outer_resid_5point-grid-2048.md)")
         P.amg_destroy(ctx_g)
 
     # end to end through the host-buffer API (copies inside the timed region),
