@@ -1328,8 +1328,7 @@ static int plan_fast_levels(amg_ctx *c) {
         which[l] = 1;
         H.fast = true;
     }
-    // M A pattern + pair list and R A on the device (the same lists as the
-    // host planner product_pattern builds)
+    // M A pattern + pair list and R A, built on the device
     std::string why;
     const int rc = device_plan_products(c->host, which, c->stream, why);
     if (rc) ctx_fail(c, why);

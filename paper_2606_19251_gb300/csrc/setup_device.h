@@ -21,11 +21,13 @@ int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int 
                            unsigned long long seed, bool second_pass, cudaStream_t s,
                            std::vector<HostLevel> &levels, std::string &err);
 
-// For every level l with which[l] set (R and A present): the pattern of A A
-// (values zero) and the pair list of product_pattern (setup_host.h), and R A,
-// computed on the device and stored into levels[l].MA, .pair_*, .RA.  The
-// pattern and pairs are identical to product_pattern's.  Returns AMG_OK or
-// AMG_ERR_CUDA (message in err).
+// For every level l with which[l] set (R and A present), computed on the
+// device and stored into levels[l]: MA = the pattern of A A (columns sorted,
+// values zero; the pattern of M A for M = Q^-1 on A's pattern), the pair list
+// that assembles its values, (M A)[e] = sum over t in
+// [pair_ptr[e], pair_ptr[e+1]) of M[pair_p[t]] * A[pair_q[t]] with each
+// entry's pairs in ascending p, and RA = R A.  Returns AMG_OK or AMG_ERR_CUDA
+// (message in err).
 int device_plan_products(std::vector<HostLevel> &levels, const std::vector<char> &which, cudaStream_t s,
                          std::string &err);
 

@@ -219,64 +219,6 @@ HostCSR galerkin(const HostCSR& A, const HostCSR& P, const HostCSR& R) {
     return spgemm(R, spgemm(A, P));
 }
 
-void product_pattern(const HostCSR &A, HostCSR &MA, std::vector<int> &pair_ptr, std::vector<int> &pair_p,
-                     std::vector<int> &pair_q) {
-    const int n = A.n_rows;
-    MA = HostCSR{};
-    MA.n_rows = n;
-    MA.n_cols = A.n_cols;
-    MA.rp.assign(n + 1, 0);
-    std::vector<int> pos(A.n_cols, -1), cols;
-    std::vector<long long> cnt;
-    // pass 1: pattern of each row and its pair counts
-    std::vector<int> row_pairs;          // (entry, p, q) triples of the current row
-    pair_ptr.assign(1, 0);
-    pair_p.clear();
-    pair_q.clear();
-    for (int i = 0; i < n; ++i) {
-        cols.clear();
-        for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-            const int k = A.col[p];
-            for (int q = A.rp[k]; q < A.rp[k + 1]; ++q) {
-                const int j = A.col[q];
-                if (pos[j] < 0) {
-                    pos[j] = 0;
-                    cols.push_back(j);
-                }
-            }
-        }
-        std::sort(cols.begin(), cols.end());
-        const int base = static_cast<int>(MA.col.size());
-        for (size_t t = 0; t < cols.size(); ++t) {
-            pos[cols[t]] = base + static_cast<int>(t);
-            MA.col.push_back(cols[t]);
-        }
-        MA.rp[i + 1] = static_cast<int>(MA.col.size());
-        // pairs grouped by output entry, each group in ascending p
-        cnt.assign(cols.size() + 1, 0);
-        for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-            const int k = A.col[p];
-            for (int q = A.rp[k]; q < A.rp[k + 1]; ++q) cnt[pos[A.col[q]] - base + 1]++;
-        }
-        for (size_t t = 0; t < cols.size(); ++t) cnt[t + 1] += cnt[t];
-        const size_t off = pair_p.size();
-        pair_p.resize(off + cnt.back());
-        pair_q.resize(off + cnt.back());
-        std::vector<long long> next(cnt.begin(), cnt.end() - 1);
-        for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-            const int k = A.col[p];
-            for (int q = A.rp[k]; q < A.rp[k + 1]; ++q) {
-                const long long at = off + next[pos[A.col[q]] - base]++;
-                pair_p[at] = p;
-                pair_q[at] = q;
-            }
-        }
-        for (size_t t = 0; t < cols.size(); ++t) pair_ptr.push_back(static_cast<int>(off + cnt[t + 1]));
-        for (int j : cols) pos[j] = -1;
-    }
-    MA.val.assign(MA.col.size(), 0.0);
-}
-
 void build_hierarchy(const HostCSR& A0, double theta, int max_levels, int max_coarse,
                      std::vector<HostLevel>& levels) {
     levels.clear();

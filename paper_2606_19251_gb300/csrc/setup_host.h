@@ -40,13 +40,6 @@ HostCSR direct_interpolation(const HostCSR& A, const std::vector<int>& S_rp,
 // A_c = P^T A P on the structural pattern of the product.
 HostCSR galerkin(const HostCSR& A, const HostCSR& P, const HostCSR& R);
 
-// Pattern of the product M A for two matrices with A's pattern (M = Q^-1)
-// and the pair list that assembles its values: for output entry e,
-// (M A)[e] = sum over t in [pair_ptr[e], pair_ptr[e+1]) of M[pair_p[t]] * A[pair_q[t]],
-// pairs in ascending (p) order.  The values of MA are left empty.
-void product_pattern(const HostCSR &A, HostCSR &MA, std::vector<int> &pair_ptr, std::vector<int> &pair_p,
-                     std::vector<int> &pair_q);
-
 // Row-by-row sparse product X Y keeping the structural pattern.
 HostCSR spgemm(const HostCSR &X, const HostCSR &Y);
 
