@@ -18,6 +18,7 @@ the same workload (the deliberately slow restatement used for parity).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -321,11 +322,15 @@ def run_gpu(args, wl, rank, world):
     launches0 = P.amg_launch_count()
     torch.cuda.nvtx.range_push("timed")
     step_ms, cyc_gnn, statuses = [], [], []
-    for k in range(Wm, Wm + K):
-        ms, (st, hist) = timed(gnn_step, k)
-        step_ms.append(ms)
-        cyc_gnn.append(len(hist) - 1)
-        statuses.append(st)
+    gc.disable()     # no collector pause inside a timed step (each step makes host calls)
+    try:
+        for k in range(Wm, Wm + K):
+            ms, (st, hist) = timed(gnn_step, k)
+            step_ms.append(ms)
+            cyc_gnn.append(len(hist) - 1)
+            statuses.append(st)
+    finally:
+        gc.enable()
     torch.cuda.nvtx.range_pop()
     launches = P.amg_launch_count() - launches0
     if world > 1:
@@ -548,6 +553,7 @@ def run_gpu(args, wl, rank, world):
             "pcg": pcg, "gcin_hidden32": h32, "device_setup": device_setup,
             "operator_complexity": sum(i[1] for i in hinfo) / hinfo[0][1],
             "gnn_step_ms": ms_per_step, "gnn_solve_ms": solve_ms, "gnn_infer_ms": infer_ms,
+            "step_ms_stats": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "jacobi_solve_ms": jac_ms, "vcycles_gnn": statistics.mean(cyc_gnn), "vcycles_jacobi": cyc_jac,
             "chebyshev3": cheb,
             "speedup_solve_vs_jacobi": jac_ms / solve_ms, "speedup_step_vs_jacobi": jac_ms / ms_per_step,

@@ -489,7 +489,9 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
     const int t = blockIdx.x, a = tstart[t], e = tstart[t + 1], g = tgraph[t];
     const int f = threadIdx.x % H, q = threadIdx.x / H;
     const float m = mu[g * H + f], r = rstd[g * H + f], ga = gamma[f], be = beta[f];
-    double s = 0.0;
+    // FP32 partial sum of at most kTile / Q values per thread (GB300's FP64
+    // pipe is narrow); the tile and graph sums are taken in FP64
+    float s = 0.f;
     float mx = -INFINITY;
     int mi = a;
 #pragma unroll 4
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
         s += v;
         if (v > mx) { mx = v; mi = i; }
     }
-    rs[q][f] = s;
+    rs[q][f] = static_cast<double>(s);
     rm[q][f] = mx;
     ri[q][f] = mi;
     __syncthreads();
@@ -809,7 +811,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_relu_tile(const int *__restrict_
     const float dmean = dp[f] / (gptr[g + 1] - gptr[g]), dmax = dp[H + f];
     const int am = argmax[(static_cast<size_t>(g) * kLayers + layer) * H + f];
     const float m = mu[g * H + f], r = rstd[g * H + f];
-    double s1 = 0.0, s2 = 0.0;
+    float s1 = 0.f, s2 = 0.f;                 // FP32 per thread, FP64 from the tile sum on
     for (int i = a + q; i < e; i += Q) {
         const size_t o = static_cast<size_t>(i) * H + f;
         float dX = dmean + (i == am ? dmax : 0.f);
@@ -817,10 +819,10 @@ __global__ void __launch_bounds__(kBlock) k_bwd_relu_tile(const int *__restrict_
         const float d = x[o] > 0.f ? dX : 0.f;
         dyn[o] = d;
         s1 += d;
-        s2 += static_cast<double>(d) * ((y[o] - m) * r);
+        s2 = fmaf(d, (y[o] - m) * r, s2);
     }
-    r1[q][f] = s1;
-    r2[q][f] = s2;
+    r1[q][f] = static_cast<double>(s1);
+    r2[q][f] = static_cast<double>(s2);
     __syncthreads();
     if (q == 0) {
         double t1 = r1[0][f], t2 = r2[0][f];
