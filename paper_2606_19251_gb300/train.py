@@ -5,9 +5,10 @@ library's CUDA kernels:
   1. batched GCIN inference over every level of every problem of the
      mini-batch (gcin_trainer_forward; Algorithm 1 steps 1-6);
   2. per problem, N_vc V-cycles from u_0 = 0 with the predicted smoothers
-     and the loss sum_n log10(||r_n|| / ||r_{n-1}||), averaged over the
-     N_vc cycles, with its gradient dL/dc from the hand-written V-cycle
-     adjoint (amg_loss_grad; steps 7-12; N_vc = 1 is the primary loss);
+     and the loss sum_{n=1}^{N_vc} log10(||r_n|| / ||r_{n-1}||) (it telescopes
+     to log10(||r_{N_vc}|| / ||f||)), with its gradient dL/dc from the
+     hand-written V-cycle adjoint (amg_loss_grad; steps 7-12; N_vc = 1 is the
+     primary loss); the batch loss is the mean over the problems;
   3. backward through the network of the batch-mean loss, global-norm
      clipping to 1.0 and Adam with lr 1e-3 (gcin_trainer_backward /
      gcin_trainer_adam_step; step 13).
