@@ -248,3 +248,13 @@ def test_second_pass_hierarchy_converges_faster_than_pmis():
         assert res.status == O.OK
         cyc[mode] = res.n_vcycles
     assert cyc["pmis-h1"] < 0.5 * cyc["pmis"], cyc
+
+
+def test_pmis_random_numbers_follow_splitmix64():
+    # the level's PMIS weights come from SplitMix64 (Steele, Lea & Flood 2014):
+    # its published first outputs for seed 0, and the 53-bit mapping to [0, 1)
+    z = W.splitmix64(0, 3)
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = W.uniform01(0, 3)
+    assert np.array_equal(u, np.array([(int(v) >> 11) * 2.0 ** -53 for v in z]))
+    assert np.all((0.0 <= u) & (u < 1.0))
