@@ -673,22 +673,6 @@ __global__ void k_assemble_q(int nnz, const unsigned char *__restrict__ isd, con
     q32[p] = static_cast<float>(q);
 }
 
-// The same with the coefficients read from device memory (FP32 network
-// output, widened to FP64 exactly as the host path does).
-__global__ void k_assemble_q_dev(int nnz, const unsigned char *__restrict__ isd, const double *__restrict__ bx,
-                                 const double *__restrict__ bw, const float *__restrict__ dc,
-                                 double *__restrict__ q64, float *__restrict__ q32) {
-    const int p = blockIdx.x * kBlock + threadIdx.x;
-    if (p >= nnz) return;
-    const double c0 = dc[0], c1 = dc[1], c2 = dc[2], c3 = dc[3], c4 = dc[4];
-    const double x = bx[p];
-    const double f = isd[p] ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
-                            : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
-    const double q = __dmul_rn(f, bw[p]);
-    q64[p] = q;
-    q32[p] = static_cast<float>(q);
-}
-
 // Q^-1 values with one coefficient row per node (cn: n x 5): the diagonal of
 // row i from node i's (d0, d1, d2), an off-diagonal entry (i, j) from the mean
 // of nodes i's and j's (o1, o2) (a symmetric Q^-1); arithmetic as k_assemble_q.
@@ -712,6 +696,68 @@ __global__ void k_assemble_q_nodes(int n, const int *__restrict__ rp, const int 
         const double q = __dmul_rn(f, bw[p]);
         q64[p] = q;
         q32[p] = static_cast<float>(q);
+    }
+}
+
+// Every smoothed level's Q^-1 (and then M A) in one launch each, with the
+// coefficients read from device memory (the FP32 network output, widened to
+// FP64 exactly as the host path does): a thread finds its level from the
+// cumulative entry offsets; the arithmetic per entry is k_assemble_q's (and
+// k_assemble_ma / k_assemble_ma32's).
+constexpr int kAsmMaxLevels = 32;
+struct AsmQ {
+    int nlev;
+    long long start[kAsmMaxLevels + 1];       // cumulative entries; start[nlev] = total
+    const unsigned char *isd[kAsmMaxLevels];
+    const double *bx[kAsmMaxLevels], *bw[kAsmMaxLevels];
+    double *q64[kAsmMaxLevels];
+    float *q32[kAsmMaxLevels];
+    int row[kAsmMaxLevels];                   // coefficient row of the level
+};
+
+__global__ void k_assemble_q_all(AsmQ L, const float *__restrict__ dc) {
+    const long long p = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
+    if (p >= L.start[L.nlev]) return;
+    int l = 0;
+    while (p >= L.start[l + 1]) ++l;
+    const long long e = p - L.start[l];
+    const float *cf = dc + 5 * L.row[l];
+    const double c0 = cf[0], c1 = cf[1], c2 = cf[2], c3 = cf[3], c4 = cf[4];
+    const double x = L.bx[l][e];
+    const double f = L.isd[l][e] ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
+                                 : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
+    const double q = __dmul_rn(f, L.bw[l][e]);
+    L.q64[l][e] = q;
+    L.q32[l][e] = static_cast<float>(q);
+}
+
+struct AsmMA {
+    int nlev;
+    long long start[kAsmMaxLevels + 1];
+    const int *pp[kAsmMaxLevels], *pq_p[kAsmMaxLevels], *pq_q[kAsmMaxLevels];
+    const float *q32[kAsmMaxLevels], *a32[kAsmMaxLevels];
+    float *ma32[kAsmMaxLevels];
+    const double *q64[kAsmMaxLevels], *a64[kAsmMaxLevels];
+    double *ma64[kAsmMaxLevels];
+};
+
+// fp64 != 0: FP64 products with the FP32 copy (FP64 V-cycle); else FP32 only
+__global__ void k_assemble_ma_all(AsmMA M, int fp64) {
+    const long long p = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
+    if (p >= M.start[M.nlev]) return;
+    int l = 0;
+    while (p >= M.start[l + 1]) ++l;
+    const long long e = p - M.start[l];
+    const int *pp = M.pp[l], *pq_p = M.pq_p[l], *pq_q = M.pq_q[l];
+    if (fp64) {
+        double acc = 0.0;
+        for (int t = pp[e]; t < pp[e + 1]; ++t) acc = fma(M.q64[l][pq_p[t]], M.a64[l][pq_q[t]], acc);
+        M.ma64[l][e] = acc;
+        M.ma32[l][e] = static_cast<float>(acc);
+    } else {
+        float acc = 0.f;
+        for (int t = pp[e]; t < pp[e + 1]; ++t) acc = fmaf(M.q32[l][pq_p[t]], M.a32[l][pq_q[t]], acc);
+        M.ma32[l][e] = acc;
     }
 }
 
@@ -1661,17 +1707,39 @@ namespace amg {
 // synchronisation and selects the smoother.
 int enqueue_coeff_assembly(amg_ctx *c, const float *d_coef, cudaStream_t s) {
     const int nlev = static_cast<int>(c->lev.size());
+    if (nlev - 1 > kAsmMaxLevels) return ctx_fail(c, "too many levels for the batched assembly"), AMG_ERR_ARG;
+    // all levels' Q^-1 in one launch, then all latency-optimised levels' M A
+    AsmQ Q{};
+    AsmMA M{};
     for (int l = 0; l < nlev - 1; ++l) {
         const DevLevel &L = c->lev[l];
-        k_assemble_q_dev<<<grid_for(L.A.nnz), kBlock, 0, s>>>(L.A.nnz, L.isd, L.bx, L.bw, d_coef + 5 * l, L.q64,
-                                                              L.q32); AMG_COUNT();
-        if (L.fast && c->opt.precision == AMG_FP64) {
-            k_assemble_ma<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q64, L.A.v64,
-                                                                L.MA.v64, L.MA.v32); AMG_COUNT();
-        } else if (L.fast) {
-            k_assemble_ma32<<<grid_for(L.MA.nnz), kBlock, 0, s>>>(L.MA.nnz, L.pp, L.pq_p, L.pq_q, L.q32, L.A.v32,
-                                                                  L.MA.v32); AMG_COUNT();
+        const int k = Q.nlev++;
+        Q.start[k + 1] = Q.start[k] + L.A.nnz;
+        Q.isd[k] = L.isd;
+        Q.bx[k] = L.bx;
+        Q.bw[k] = L.bw;
+        Q.q64[k] = L.q64;
+        Q.q32[k] = L.q32;
+        Q.row[k] = l;
+        if (L.fast) {
+            const int j = M.nlev++;
+            M.start[j + 1] = M.start[j] + L.MA.nnz;
+            M.pp[j] = L.pp;
+            M.pq_p[j] = L.pq_p;
+            M.pq_q[j] = L.pq_q;
+            M.q32[j] = L.q32;
+            M.a32[j] = L.A.v32;
+            M.ma32[j] = L.MA.v32;
+            M.q64[j] = L.q64;
+            M.a64[j] = L.A.v64;
+            M.ma64[j] = L.MA.v64;
         }
+    }
+    if (Q.nlev > 0 && Q.start[Q.nlev] > 0) {
+        k_assemble_q_all<<<grid_for(Q.start[Q.nlev]), kBlock, 0, s>>>(Q, d_coef); AMG_COUNT();
+    }
+    if (M.nlev > 0 && M.start[M.nlev] > 0) {
+        k_assemble_ma_all<<<grid_for(M.start[M.nlev]), kBlock, 0, s>>>(M, c->opt.precision == AMG_FP64 ? 1 : 0); AMG_COUNT();
     }
     CKL("assemble pseudo-inverse");
     return AMG_OK;
