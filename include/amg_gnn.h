@@ -343,7 +343,9 @@ long long amg_launch_count(void);
  * 32-bit int) and 0 <= nnz <= 2^31 - 1; anything larger is rejected with
  * AMG_ERR_ARG.  The first call on a device looks up the scratch array's
  * device address (once per device, with that device current); make that
- * first call before any stream capture.  All calls on a device share the
+ * first call before any stream capture.  The address is cached for the life
+ * of the process: do not call this entry point on a device after
+ * cudaDeviceReset of that device.  All calls on a device share the
  * scratch array, so calls whose work overlaps on the GPU (e.g. on two
  * concurrent streams) race and give wrong norms; serialise them.  The array
  * keeps the last call's contents, and every call overwrites the slots it

@@ -6,7 +6,10 @@ V-cycle of ``oracle.solve`` and the network of ``oracle.gcin``.
 * loss of one problem with u_0 = 0 (Sec. 3.3, multi-V-cycle form):
   L_m = sum_{n=1}^{N_vc} log10(||r_n||_2 / ||r_{n-1}||_2), r_n = f - A u_n,
   u_n = V-cycle(u_{n-1}, f); N_vc = 1 is the primary loss;
-* batch loss = mean over problems (Algorithm 1 steps 7-12);
+* batch loss = mean over problems (Algorithm 1 steps 7-12); with
+  average_cycles, each L_m is divided by N_vc first (Sec. 3.3 describes the
+  multi-V-cycle loss as averaging the reductions over the cycles; the
+  training loop uses that form, amg_loss_grad returns the sum);
 * global-norm clipping to 1.0 (Table train_hyper) as g * min(1, 1/(||g|| + 1e-6))
   (reading; the paper gives only the max norm);
 * Adam with lr 1e-3 (Table train_hyper); beta1 = 0.9, beta2 = 0.999,
@@ -50,20 +53,24 @@ def loss_and_coeff_grad(h: OHierarchy, coeffs, f, n_vc: int = 1):
     return float(L.detach()), c.grad.numpy().copy()
 
 
-def batch_loss(theta: torch.Tensor, hierarchies, graphs_per_problem, rhs, n_vc: int = 1) -> torch.Tensor:
+def batch_loss(theta: torch.Tensor, hierarchies, graphs_per_problem, rhs, n_vc: int = 1,
+               average_cycles: bool = False, bf16_linears: bool = False) -> torch.Tensor:
     """Algorithm 1: batched inference over all levels, then per-problem losses, mean."""
     all_graphs = [g for gs in graphs_per_problem for g in gs]
-    c_all = gcin.forward(theta, all_graphs)
+    c_all = gcin.forward(theta, all_graphs, bf16_linears=bf16_linears)
     total, off = 0.0, 0
     for h, gs, f in zip(hierarchies, graphs_per_problem, rhs):
-        total = total + problem_loss(h, c_all[off:off + len(gs)], f, n_vc=n_vc)
+        L_m = problem_loss(h, c_all[off:off + len(gs)], f, n_vc=n_vc)
+        total = total + (L_m / n_vc if average_cycles else L_m)
         off += len(gs)
     return total / len(hierarchies)
 
 
-def batch_loss_and_grad(theta, hierarchies, graphs_per_problem, rhs):
+def batch_loss_and_grad(theta, hierarchies, graphs_per_problem, rhs, n_vc: int = 1, average_cycles: bool = False,
+                        bf16_linears: bool = False):
     t = torch.as_tensor(np.asarray(theta, dtype=np.float64)).clone().requires_grad_(True)
-    L = batch_loss(t, hierarchies, graphs_per_problem, rhs)
+    L = batch_loss(t, hierarchies, graphs_per_problem, rhs, n_vc=n_vc, average_cycles=average_cycles,
+                   bf16_linears=bf16_linears)
     L.backward()
     return float(L.detach()), t.grad.numpy().copy()
 

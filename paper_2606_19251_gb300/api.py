@@ -406,12 +406,24 @@ def amg_launch_count() -> int:
 
 
 def amg_residual_norm_noalloc(d_row_ptr, d_col, d_val, d_b, d_x, d_out, d_r=None, stream=None):
-    """||b - A x|| and ||b|| into d_out[0:2] with no allocation; all arguments are device tensors."""
+    """||b - A x|| and ||b|| into d_out[0:2] with no allocation; all arguments are device tensors.
+
+    Every tensor must live on the current CUDA device (the library launches
+    there and looks up its scratch array there); lengths are checked against
+    n = d_b.numel() and nnz = d_col.numel() before the call, because a short
+    buffer would become an out-of-bounds device access."""
     import torch
     n = d_b.numel()
     nnz = d_col.numel()
     for t, dt in ((d_row_ptr, torch.int32), (d_col, torch.int32)):
         assert t.is_cuda and t.dtype == dt and t.is_contiguous()
+    dev = torch.cuda.current_device()
+    tensors = [d_row_ptr, d_col, d_val, d_b, d_x, d_out] + ([d_r] if d_r is not None else [])
+    if any(t.device.index != dev for t in tensors):
+        raise ValueError("amg_residual_norm_noalloc: every tensor must be on the current CUDA device")
+    if d_row_ptr.numel() != n + 1 or d_val.numel() != nnz or d_x.numel() != n or d_out.numel() < 2 or \
+            (d_r is not None and d_r.numel() != n):
+        raise ValueError("amg_residual_norm_noalloc: row_ptr needs n + 1 entries, val nnz, x and r n, out 2")
     rp = C.c_void_p(d_row_ptr.data_ptr())
     col = C.c_void_p(d_col.data_ptr())
     r = _dev(d_r) if d_r is not None else None

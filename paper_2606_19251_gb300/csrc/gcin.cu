@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -640,9 +641,12 @@ __global__ void __launch_bounds__(128) k_head(const float *__restrict__ pooled, 
 namespace amg {
 
 void gcin_prepare_device() {
+    static std::mutex mu;
     static bool done[64] = {};
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return;
     cudaFuncSetAttribute(k_agg_lin_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden>());
     cudaFuncSetAttribute(k_agg_lin_tc<kHidden32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden32>());
     done[dev] = true;
@@ -683,6 +687,10 @@ static void forward_impl(GcinBatch &b, const float *th, cudaStream_t s) {
 
 void gcin_forward(GcinBatch &b, const float *th, cudaStream_t s) {
     gcin_prepare_device();
+    // the tensor-core kernel's wait-timeout flag belongs to this forward pass
+    // only: clear it first (a captured inference graph replays this too), so
+    // one timed-out pass does not fail every later one
+    cudaMemsetAsync(b.err, 0, sizeof(int) * 4, s);
     if (b.hidden == kHidden32) forward_impl<kHidden32>(b, th, s);
     else forward_impl<kHidden>(b, th, s);
 }

@@ -8,7 +8,11 @@ library's CUDA kernels:
      and the loss sum_{n=1}^{N_vc} log10(||r_n|| / ||r_{n-1}||) (it telescopes
      to log10(||r_{N_vc}|| / ||f||)), with its gradient dL/dc from the
      hand-written V-cycle adjoint (amg_loss_grad; steps 7-12; N_vc = 1 is the
-     primary loss); the batch loss is the mean over the problems;
+     primary loss).  The training loss of a problem is that sum divided by
+     N_vc: Sec. 3.3 describes the multi-V-cycle loss as averaging the
+     reductions over the cycles (a reading of the equation's sum; it keeps
+     the gradient scale of the N_vc = 1 loss, to which the clipping norm of
+     1.0 applies).  The batch loss is the mean over the problems;
   3. backward through the network of the batch-mean loss, global-norm
      clipping to 1.0 and Adam with lr 1e-3 (gcin_trainer_backward /
      gcin_trainer_adam_step; step 13).
@@ -98,13 +102,14 @@ class Trainer:
 
 
 def train(train_mats, val_mats, theta0, epochs=30, batch=5, seed=0, log=print, device=0, n_vc=1, val_cycles=10,
-          precision=P.AMG_GNN_FP32):
+          precision=P.AMG_GNN_FP32, factor=0.1, patience=10):
     """Train on `train_mats`, validate on `val_mats`; returns (best theta, log rows)."""
     import workloads as W
     probs = [Problem(A, device=device) for A in train_mats]
     vals = [Problem(A, device=device) for A in val_mats]
     val_rhs = [W.rhs_uniform(10_000 + k, p.A.n_rows) for k, p in enumerate(vals)]
-    tr = Trainer(theta0, device=device, n_vc=n_vc, val_cycles=val_cycles, precision=precision)
+    tr = Trainer(theta0, device=device, n_vc=n_vc, val_cycles=val_cycles, precision=precision, factor=factor,
+                 patience=patience)
     rows = []
     try:
         val0 = tr.validate(vals, val_rhs)

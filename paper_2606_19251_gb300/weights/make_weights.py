@@ -86,7 +86,10 @@ def main():
     best, rows = train(mats, val, theta0, epochs=args.epochs, batch=args.batch, n_vc=args.nvc,
                        val_cycles=args.val_cycles, log=lambda r: print(json.dumps(r), flush=True), precision=prec)
     np.save(args.out, np.asarray(best, dtype=np.float32))
-    with open(os.path.splitext(args.out)[0] + "_log.json", "w") as f:
+    # the training log is run output, not a product file: it goes beside the
+    # run's other output (LOG_DIR, default the working directory)
+    log_dir = os.environ.get("LOG_DIR", os.getcwd())
+    with open(os.path.join(log_dir, os.path.basename(os.path.splitext(args.out)[0]) + "_log.json"), "w") as f:
         json.dump({"epochs": args.epochs, "batch": args.batch, "meshes": args.meshes, "n_vc": args.nvc,
                    "extra_band1000": args.extra_band1000, "extra_airfoil": args.extra_airfoil,
                    "precision": args.precision, "hidden": args.hidden, "dataset": args.dataset,

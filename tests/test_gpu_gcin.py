@@ -32,6 +32,15 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
+def rel_cols(a, b):
+    """Largest relative error of the coefficient columns (d0, d1, d2, o1, o2),
+    each against its own scale: a small column (d2 and o2 are often ~1e-2)
+    is held to the same relative bar as the largest one."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1, 5)
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 5)
+    return max(float(np.abs(a[:, k] - b[:, k]).max() / max(np.abs(b[:, k]).max(), 1e-30)) for k in range(5))
+
+
 MATS = {
     "c1_64": lambda: W.poisson5(64),
     "uniform_2k": lambda: W.fv_mesh("uniform", 2000, 3)[0],
@@ -52,7 +61,7 @@ def test_predict_coeffs_parity(name, seed):
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
         assert c.shape == ref.shape
-        assert rel(c, ref) < 1e-5, rel(c, ref)
+        assert rel_cols(c, ref) < 1e-5, rel_cols(c, ref)
         # the predicted smoother is the one assembled on the device
         q = P.amg_get_smoother(ctx, 0)
         qref = O.pseudo_inverse_values(O.TMat.of(levels[0].A), c[0])
@@ -69,7 +78,7 @@ def test_predict_coeffs_full_size_c2():
     ctx = ctx_setup(A, P.AMG_FP32_IN_FP64, gnn_precision=P.AMG_GNN_FP32)
     try:
         P.gnn_load_params(ctx, theta)
-        assert rel(P.gnn_predict_coeffs(ctx), ref) < 1e-5
+        assert rel_cols(P.gnn_predict_coeffs(ctx), ref) < 1e-5
     finally:
         P.amg_destroy(ctx)
 
@@ -88,10 +97,10 @@ def test_predict_coeffs_parity_bf16(name, seed):
     try:
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
-        assert rel(c, ref) < 2e-2, rel(c, ref)
+        assert rel_cols(c, ref) < 2e-2, rel_cols(c, ref)
         # the tensor-core result is the BF16-operand network up to FP32
         # accumulation and rare one-ulp rounding flips of h
-        assert rel(c, emu) < 1e-3, rel(c, emu)
+        assert rel_cols(c, emu) < 1e-3, rel_cols(c, emu)
     finally:
         P.amg_destroy(ctx)
 
@@ -106,9 +115,9 @@ def test_predict_coeffs_full_size_c2_bf16(seed):
     try:
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
-        assert rel(c, ref) < 2e-2, rel(c, ref)
+        assert rel_cols(c, ref) < 2e-2, rel_cols(c, ref)
         emu = OG.predict(f32(theta), [l.A for l in levels], bf16_linears=True)
-        assert rel(c, emu) < 1e-3, rel(c, emu)
+        assert rel_cols(c, emu) < 1e-3, rel_cols(c, emu)
         # repeated inference is deterministic (fixed-order reductions)
         assert np.array_equal(c, P.gnn_predict_coeffs(ctx))
     finally:
@@ -130,7 +139,7 @@ def test_trained_weights_bf16_vs_fp32():
             out.append(P.gnn_predict_coeffs(ctx))
         finally:
             P.amg_destroy(ctx)
-    assert rel(out[1], out[0]) < 2e-2
+    assert rel_cols(out[1], out[0]) < 2e-2
 
 
 def _problems(names=("uniform_2k", "graded_6k", "band_8k")):
@@ -156,7 +165,7 @@ def test_network_backward_parity():
         graphs = [OG.Graph(l.A) for _, lv, _ in probs for l in lv]
         cref = OG.forward(t, graphs)
         (cref * torch.from_numpy(dc)).sum().backward()
-        assert rel(c, cref.detach().numpy()) < 1e-5
+        assert rel_cols(c, cref.detach().numpy()) < 1e-5
         gref = t.grad.numpy()
         assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
         # every tensor individually; the conv biases are skipped because
@@ -269,11 +278,11 @@ def test_network_backward_bf16():
         dc = np.random.default_rng(0).standard_normal(c.shape)
         g = P.gcin_trainer_backward(tr, dc)
         graphs = [OG.Graph(l.A) for _, lv, _ in probs for l in lv]
-        assert rel(c, OG.forward(f32(theta), graphs).numpy()) < 2e-2
+        assert rel_cols(c, OG.forward(f32(theta), graphs).numpy()) < 2e-2
         t = torch.tensor(f32(theta), requires_grad=True)
         cref = OG.forward(t, graphs, bf16_linears=True)
         (cref * torch.from_numpy(dc)).sum().backward()
-        assert rel(c, cref.detach().numpy()) < 1e-3
+        assert rel_cols(c, cref.detach().numpy()) < 1e-3
         gref = t.grad.numpy()
         assert np.linalg.norm(g - gref) <= 1e-2 * np.linalg.norm(gref), np.linalg.norm(g - gref) / np.linalg.norm(gref)
     finally:

@@ -33,6 +33,15 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
+def rel_cols(a, b):
+    """Largest relative error of the coefficient columns (d0, d1, d2, o1, o2),
+    each against its own scale: a small column (d2 and o2 are often ~1e-2)
+    is held to the same relative bar as the largest one."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1, 5)
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 5)
+    return max(float(np.abs(a[:, k] - b[:, k]).max() / max(np.abs(b[:, k]).max(), 1e-30)) for k in range(5))
+
+
 MATS = {
     "c1_64": lambda: W.poisson5(64),
     "poisson7_16": lambda: W.poisson7(16),
@@ -58,7 +67,7 @@ def test_predict_coeffs_parity_fp32(name, seed):
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
         assert c.shape == ref.shape
-        assert rel(c, ref) < 1e-5, rel(c, ref)
+        assert rel_cols(c, ref) < 1e-5, rel_cols(c, ref)
         q = P.amg_get_smoother(ctx, 0)
         qref = O.pseudo_inverse_values(O.TMat.of(levels[0].A), c[0])
         assert rel(q, qref.numpy()) < 1e-12
@@ -78,8 +87,8 @@ def test_predict_coeffs_parity_bf16(name, seed):
     try:
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
-        assert rel(c, ref) < 2e-2, rel(c, ref)
-        assert rel(c, emu) < 1e-3, rel(c, emu)
+        assert rel_cols(c, ref) < 2e-2, rel_cols(c, ref)
+        assert rel_cols(c, emu) < 1e-3, rel_cols(c, emu)
     finally:
         P.amg_destroy(ctx)
 
@@ -97,8 +106,8 @@ def test_predict_full_size_c2_bf16_and_width_switch():
         for theta in (t32, t64, t32):
             P.gnn_load_params(ctx, theta)
             c = P.gnn_predict_coeffs(ctx)
-            assert rel(c, OG.predict(f32(theta), mats)) < 2e-2
-            assert rel(c, OG.predict(f32(theta), mats, bf16_linears=True)) < 1e-3
+            assert rel_cols(c, OG.predict(f32(theta), mats)) < 2e-2
+            assert rel_cols(c, OG.predict(f32(theta), mats, bf16_linears=True)) < 1e-3
             assert np.array_equal(c, P.gnn_predict_coeffs(ctx))   # deterministic replay
     finally:
         P.amg_destroy(ctx)
@@ -142,7 +151,7 @@ def test_network_backward_parity(prec):
         (cref * torch.from_numpy(dc)).sum().backward()
         gref = t.grad.numpy()
         if not bf16:
-            assert rel(c, cref.detach().numpy()) < 1e-5
+            assert rel_cols(c, cref.detach().numpy()) < 1e-5
             assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
             off = 0
             for name, shape in OG.param_shapes(H):
@@ -154,7 +163,7 @@ def test_network_backward_parity(prec):
                     continue
                 assert np.linalg.norm(gs - rs) <= 1e-3 * max(np.linalg.norm(rs), 1e-6 * np.linalg.norm(gref)), name
         else:
-            assert rel(c, cref.detach().numpy()) < 1e-3
+            assert rel_cols(c, cref.detach().numpy()) < 1e-3
             assert np.linalg.norm(g - gref) <= 1e-2 * np.linalg.norm(gref)
     finally:
         P.gcin_trainer_destroy(tr)

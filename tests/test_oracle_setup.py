@@ -258,3 +258,84 @@ def test_pmis_random_numbers_follow_splitmix64():
     u = W.uniform01(0, 3)
     assert np.array_equal(u, np.array([(int(v) >> 11) * 2.0 ** -53 for v in z]))
     assert np.all((0.0 <= u) & (u < 1.0))
+
+
+# ---------------------------------------------------------------------------
+# direct interpolation with positive couplings
+# ---------------------------------------------------------------------------
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)), "golden")
+
+
+def _read_sections(path):
+    sec, out = None, {}
+    with open(path) as f:
+        for ln in f:
+            ln = ln.split("#")[0].strip()
+            if not ln:
+                continue
+            if ln in ("A", "C", "P"):
+                sec = ln
+                out[sec] = []
+                continue
+            out[sec].append(ln.split())
+    return out
+
+
+def test_direct_interpolation_hand_worked_positive_coupling():
+    g = _read_sections(f"{GOLDEN}/direct_interp_5x5.txt")
+    r = np.array([int(t[0]) for t in g["A"]])
+    c = np.array([int(t[1]) for t in g["A"]])
+    v = np.array([float(t[2]) for t in g["A"]])
+    A = W._coo_to_csr(5, 5, r, c, v)
+    Sg, _ = S.strength(A, 0.25)
+    assert [sorted(map(int, s)) for s in Sg] == [[1], [0, 2], [1, 3], [2], [1]]
+    split = np.zeros(5, dtype=np.int64)
+    split[[int(t[0]) for t in g["C"]]] = 1
+    Pd = S.direct_interpolation(A, Sg, split).to_dense()
+    expect = np.zeros((5, 2))
+    for row, col, num, den in g["P"]:
+        expect[int(row), int(col)] = int(num) / int(den)
+    np.testing.assert_allclose(Pd, expect, rtol=1e-15, atol=0)
+    assert np.count_nonzero(Pd[4]) == 0
+
+
+def _hierarchy_case(kind):
+    if kind == "airfoil":
+        A = W.c5_problem(3, n_rhs=1, n_surface=120, n_far=2500)[0]
+    elif kind == "band":
+        A = W.fv_mesh("band", 6000, 8, max_aspect=1000.0)[0]
+    else:
+        A = W.fv_mesh(kind, 3000, 7, max_aspect=1000.0)[0]
+    return A, S.build_hierarchy(A, max_coarse=20)
+
+
+def _row_sums(M):
+    """(sum_j m_ij, sum_j |m_ij|, has a positive off-diagonal) per row."""
+    rows = np.repeat(np.arange(M.n_rows), np.diff(M.row_ptr))
+    s = np.bincount(rows, weights=M.val, minlength=M.n_rows)
+    a = np.bincount(rows, weights=np.abs(M.val), minlength=M.n_rows)
+    pos = np.bincount(rows, weights=((M.val > 0) & (M.col != rows)).astype(np.float64), minlength=M.n_rows) > 0
+    return s, a, pos
+
+
+@pytest.mark.parametrize("kind", ["graded", "band", "airfoil"])
+def test_direct_interpolation_preserves_constants_on_every_level(kind):
+    # On every level, an F row of A_l with a zero row sum gets direct weights
+    # that sum to one: sum_j w_ij = -alpha_i (sum of its strong-C couplings) / d_i
+    # = -(sum of its negative couplings) / (a_ii + sum of its positive couplings)
+    # = 1.  Galerkin levels keep zero row sums away from the Dirichlet rows and
+    # carry positive couplings, so this fails if those couplings are not lumped
+    # onto the diagonal (the row would sum to (a_ii + pos) / a_ii).
+    A, levels = _hierarchy_case(kind)
+    n_pos_rows = 0
+    for l in range(len(levels) - 1):
+        Al, Pl, split = levels[l].A, levels[l].P, levels[l].split
+        rowsum, scale, pos = _row_sums(Al)
+        zero = np.abs(rowsum) <= 1e-13 * scale
+        has_row = np.diff(Pl.row_ptr) > 0
+        sel = zero & has_row & (split == 0)
+        n_pos_rows += int((sel & pos).sum())
+        psum, _, _ = _row_sums(Pl)
+        np.testing.assert_allclose(psum[sel], 1.0, atol=1e-12, err_msg=f"level {l}")
+    # the check must reach rows with positive couplings to pin the lumping
+    assert n_pos_rows >= 3, n_pos_rows
