@@ -87,6 +87,12 @@ typedef struct {
                          then holds the recurrence residual, and a breakdown
                          (z.r <= 0 or p.Ap <= 0) ends the solve with
                          AMG_ERR_DIVERGED leaving x at the last iterate           */
+    int fused_sweeps; /* 1 (default): on levels too large for the L2 cache, each
+                         smoothing phase of the V-cycle (with the residual for
+                         restriction, or with the prolongation-correction) runs
+                         as one wavefront kernel that re-reads A from L2 instead
+                         of HBM, with the pseudo-inverse values evaluated on the
+                         fly in FP32; 0: one kernel per pass (same operators)    */
 } amg_options;
 
 /* Fill *opt with the paper's settings: nu1 = nu2 = 2, max_levels = 10,
@@ -310,6 +316,8 @@ int amg_get_chebyshev(const amg_ctx *ctx, int level, double *rho, double *theta,
 #define AMG_K_OUTER     5   /* FP64 r = b - A_0 x with norm partials   (level 0 only)      */
 #define AMG_K_VCYCLE    6   /* one whole V-cycle from level 0          (level ignored)     */
 #define AMG_K_MASWEEP   7   /* u' = u + w - (Q^-1 A) u single pass   (latency-optimised levels) */
+#define AMG_K_WF_PRE    8   /* wavefront chain: pre-smoothing from zero + residual (HBM-sized levels) */
+#define AMG_K_WF_POST   9   /* wavefront chain: prolongation-correction + post-smoothing            */
 
 /* Launch `reps` back-to-back instances of one solve-path kernel on level
  * `level`, using the context's own work vectors, asynchronously on

@@ -57,7 +57,7 @@ class amg_options(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_levels", C.c_int), ("max_coarse", C.c_int),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
                 ("theta", C.c_double), ("device", C.c_int), ("gnn_precision", C.c_int),
-                ("outer", C.c_int)]
+                ("outer", C.c_int), ("fused_sweeps", C.c_int)]
 
 
 _LIB = None
@@ -358,7 +358,8 @@ def amg_loss_grad(ctx, c, f, n_vc=1):
     return loss.value, dc
 
 
-AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE, AMG_K_MASWEEP = range(8)
+(AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE, AMG_K_MASWEEP,
+ AMG_K_WF_PRE, AMG_K_WF_POST) = range(10)
 
 
 def gcin_tc_selftest(x, W, bias, no_commit=False, device=0):

@@ -27,9 +27,11 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.cuh"
+#include "wavefront.cuh"
 #include "setup_device.h"
 
 using namespace amg;
@@ -741,6 +743,16 @@ struct AsmMA {
     double *ma64[kAsmMaxLevels];
 };
 
+// The wavefront chains' coefficient rows (d0 d1 d2 o1 o2 1/s per level, FP32)
+// from the network's FP32 output and the level scales.
+__global__ void k_wf_coef(int nlev, const float *__restrict__ dc, const double *__restrict__ scal,
+                          float *__restrict__ wcoef) {
+    const int l = threadIdx.x;
+    if (l >= nlev) return;
+    for (int k = 0; k < 5; ++k) wcoef[8 * l + k] = dc[5 * l + k];
+    wcoef[8 * l + 5] = static_cast<float>(1.0 / scal[l]);
+}
+
 // fp64 != 0: FP64 products with the FP32 copy (FP64 V-cycle); else FP32 only
 __global__ void k_assemble_ma_all(AsmMA M, int fp64) {
     const long long p = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
@@ -972,6 +984,258 @@ static void L_outer(const DevMat &A, const double *b, const double *x, T *rT, do
 }
 
 // ---------------------------------------------------------------------------
+// wavefront smoothing chains (wavefront.cuh) on levels too large for L2
+// ---------------------------------------------------------------------------
+constexpr int kWfMinBlocks = 64;   // smaller levels stay in L2 anyway: one kernel per pass
+constexpr int kWfMaxReach = 64;    // a block's columns reach at most this many blocks ahead
+
+template <class T, int TPR, bool FLY>
+static int wf_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wavefront<T, TPR, FLY>, kWfThreads, 0) != cudaSuccess)
+        return 1;
+    return std::max(1, nb);
+}
+
+template <class T>
+static int wf_blocks_per_sm(int tpr, bool fly) {
+    if (fly) {
+        if constexpr (std::is_same<T, float>::value) {
+            switch (tpr) {
+                case 1: return wf_occupancy<float, 1, true>();
+                case 2: return wf_occupancy<float, 2, true>();
+                default: return wf_occupancy<float, 4, true>();
+            }
+        }
+    }
+    switch (tpr) {
+        case 1: return wf_occupancy<T, 1, false>();
+        case 2: return wf_occupancy<T, 2, false>();
+        default: return wf_occupancy<T, 4, false>();
+    }
+}
+
+// Which levels run their smoothing as wavefront chains, with the block
+// ranges of their columns and the task orders of every chain length.
+static int plan_wavefront(amg_ctx *c) {
+    const int nlev = static_cast<int>(c->host.size());
+    c->wfplan.assign(nlev, WfPlan{});
+    if (!c->opt.fused_sweeps) return AMG_OK;
+    const bool f32 = (c->opt.precision != AMG_FP64);
+    for (int l = 0; l < nlev - 1; ++l) {
+        const HostLevel &H = c->host[l];
+        if (H.fast) continue;
+        const int n = H.A.n_rows;
+        const int tpr = pick_tpr(H.A.nnz(), n);
+        if (tpr > 4) continue;
+        const int brows = kWfIter * kWfThreads / tpr;
+        const int nblk = (n + brows - 1) / brows;
+        if (nblk < kWfMinBlocks) continue;
+        WfPlan &W = c->wfplan[l];
+        W.lohi.assign(2 * static_cast<size_t>(nblk), 0);
+        int front = 0, reach = 0;
+        for (int k = 0; k < nblk; ++k) {
+            int lo = k, hi = k;
+            const int r1 = std::min(n, (k + 1) * brows);
+            for (int p = H.A.rp[k * brows]; p < H.A.rp[r1]; ++p) {
+                const int cb = H.A.col[p] / brows;
+                lo = std::min(lo, cb);
+                hi = std::max(hi, cb);
+            }
+            W.lohi[2 * k] = lo;
+            W.lohi[2 * k + 1] = hi;
+            front = std::max(front, hi);
+            reach = std::max(reach, front - k);
+        }
+        if (reach > kWfMaxReach) {
+            W = WfPlan{};
+            continue;
+        }
+        W.grid = std::min(kWfCtasPerSM, f32 ? wf_blocks_per_sm<float>(tpr, true) : wf_blocks_per_sm<double>(tpr, false)) *
+                 kNumSMs;
+        W.brows = brows;
+        W.nblk = nblk;
+        std::vector<int> ord;
+        bool ok = true;
+        W.off[1] = 0;
+        for (int np = 1; np <= kWfMaxPhases && ok; ++np) {
+            const int lag = static_cast<int>((static_cast<long long>(kWfLagPct) * W.grid + 100LL * np - 1) /
+                                             (100LL * np)) + 1;
+            ok = wf_build_order(nblk, W.lohi, np, lag, ord);
+            W.order.insert(W.order.end(), ord.begin(), ord.end());
+            W.off[np + 1] = static_cast<int>(W.order.size());
+        }
+        if (!ok) return ctx_fail(c, "wavefront task order failed its dependency check"), AMG_ERR_ARG;
+        W.on = true;
+    }
+    return AMG_OK;
+}
+
+template <class T> static const T *diagvals(const DevLevel &L);
+template <> const double *diagvals<double>(const DevLevel &L) { return L.diag; }
+template <> const float *diagvals<float>(const DevLevel &L) { return L.diag32; }
+
+template <class T> struct WfLaunch {
+    template <int TPR>
+    static void go(const WfArgs<T> &a, int grid, bool fly, cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (fly) {
+                launch_pdl(k_wavefront<float, TPR, true>, dim3(grid), dim3(kWfThreads), 0, s, a);
+                return;
+            }
+        }
+        launch_pdl(k_wavefront<T, TPR, false>, dim3(grid), dim3(kWfThreads), 0, s, a);
+    }
+};
+
+// A chain being assembled: passes appended in order, outputs in fresh level
+// buffers (never one the chain reads as its own input `keep`).
+template <class T> struct WfChain {
+    WfArgs<T> a;
+    unsigned taken = 0;
+    bool ok = true;
+    int add(int op, int in = 0, int aux = 0) {
+        if (a.nphase >= kWfMaxPhases) {
+            ok = false;
+            return 0;
+        }
+        int out = 0;
+        while (out < kWfBufs && (taken >> out) & 1u) ++out;
+        if (out >= kWfBufs) {
+            ok = false;
+            return 0;
+        }
+        taken |= 1u << out;
+        const int p = a.nphase++;
+        a.op[p] = op;
+        a.in[p] = in;
+        a.aux[p] = aux;
+        a.out[p] = out;
+        return out;
+    }
+};
+
+template <class T>
+static WfChain<T> wf_chain_for(amg_ctx *c, int l, const T *b) {
+    DevLevel &L = c->lev[l];
+    WfChain<T> ch;
+    WfArgs<T> &a = ch.a;
+    a.n = L.n;
+    a.nblk = L.wf_nblk;
+    a.brows = L.wf_brows;
+    a.rp = L.A.rp;
+    a.col = L.A.col;
+    a.a = mvals<T>(L.A);
+    a.diag = diagvals<T>(L);
+    a.q = qvals<T>(L);
+    a.coef = c->wcoef + 8 * l;
+    a.jac = jvals<T>(L);
+    a.prp = L.P.rp;
+    a.pcol = L.P.col;
+    a.pv = mvals<T>(L.P);
+    a.b = b;
+    for (int k = 0; k < kWfBufs; ++k) a.v[k] = reinterpret_cast<T *>(L.wf_buf + static_cast<size_t>(k) * L.n);
+    a.lohi = L.wf_lohi;
+    a.flags = L.wf_flags;
+    a.ctrl = L.wf_ctrl;
+    a.err = c->dflag + 1;
+    return ch;
+}
+
+// Launch an assembled chain; returns false (nothing launched) if it does
+// not fit the kernel's pass or buffer limits.
+template <class T>
+static bool wf_launch(amg_ctx *c, int l, WfChain<T> &ch, cudaStream_t s) {
+    DevLevel &L = c->lev[l];
+    if (!ch.ok || ch.a.nphase < 1) return false;
+    const WfPlan &W = c->wfplan[l];
+    ch.a.ntask = W.off[ch.a.nphase + 1] - W.off[ch.a.nphase];
+    ch.a.order = L.wf_order + W.off[ch.a.nphase];
+    const bool fly = std::is_same<T, float>::value && !c->q_nodes;
+    const int grid = std::max(1, std::min(L.wf_grid, ch.a.ntask));
+    switch (L.A.tpr) {
+        case 1: WfLaunch<T>::template go<1>(ch.a, grid, fly, s); break;
+        case 2: WfLaunch<T>::template go<2>(ch.a, grid, fly, s); break;
+        default: WfLaunch<T>::template go<4>(ch.a, grid, fly, s); break;
+    }
+    return true;
+}
+
+// Chains exist for the pseudo-inverse and Jacobi smoothers with at least one
+// sweep per phase and passes that fit the kernel.
+static bool wf_usable(const amg_ctx *c, const DevLevel &L) {
+    if (!L.wf || c->smoother == AMG_SMOOTHER_CHEB || c->opt.nu1 < 1 || c->opt.nu2 < 1) return false;
+    const bool gnn = (c->smoother == AMG_SMOOTHER_GNN);
+    const int pre = gnn ? 2 * c->opt.nu1 : c->opt.nu1;          // sweeps + residual
+    const int post = gnn ? 1 + 2 * c->opt.nu2 : 1 + c->opt.nu2;  // prolongation + sweeps
+    return std::max(pre, post) <= kWfMaxPhases;
+}
+
+// Pre-smoothing from zero and the residual for restriction as one chain;
+// returns the buffer indices of the smoothed u and of r = b - A u.
+template <class T>
+static bool wf_pre(amg_ctx *c, int l, cudaStream_t s, const T *b, int &u_idx, int &r_idx) {
+    WfChain<T> ch = wf_chain_for<T>(c, l, b);
+    const int nu1 = c->opt.nu1;
+    int u;
+    if (c->smoother == AMG_SMOOTHER_GNN) {
+        u = ch.add(kWfQB);
+        for (int k = 1; k < nu1; ++k) {
+            const int r = ch.add(kWfResid, u);
+            u = ch.add(kWfQApply, r, u);
+        }
+    } else if (nu1 >= 2) {
+        u = ch.add(kWfJac12);
+        for (int k = 2; k < nu1; ++k) u = ch.add(kWfJac, u);
+    } else {
+        u = ch.add(kWfJacZ);
+    }
+    const int r = ch.add(kWfResid, u);
+    u_idx = u;
+    r_idx = r;
+    return wf_launch<T>(c, l, ch, s);
+}
+
+// Prolongation-correction u += P e and the post-smoothing as one chain;
+// returns the smoothed u.
+template <class T>
+static T *wf_post(amg_ctx *c, int l, cudaStream_t s, const T *b, int u_idx, const T *e) {
+    WfChain<T> ch = wf_chain_for<T>(c, l, b);
+    ch.a.e = e;
+    ch.taken |= 1u << u_idx;
+    int u = ch.add(kWfProlong, u_idx);
+    for (int k = 0; k < c->opt.nu2; ++k) {
+        if (c->smoother == AMG_SMOOTHER_GNN) {
+            const int r = ch.add(kWfResid, u);
+            u = ch.add(kWfQApply, r, u);
+        } else {
+            u = ch.add(kWfJac, u);
+        }
+    }
+    if (!wf_launch<T>(c, l, ch, s)) return nullptr;
+    return ch.a.v[u];
+}
+
+// nsweeps sweeps from the caller's u (amg_smooth_device); nullptr if the
+// chain does not fit.
+template <class T>
+static T *wf_smooth(amg_ctx *c, int l, cudaStream_t s, const T *b, T *u_in, int nsweeps) {
+    WfChain<T> ch = wf_chain_for<T>(c, l, b);
+    ch.a.v[kWfBufs] = u_in;
+    int u = kWfBufs;
+    for (int k = 0; k < nsweeps; ++k) {
+        if (c->smoother == AMG_SMOOTHER_GNN) {
+            const int r = ch.add(kWfResid, u);
+            u = ch.add(kWfQApply, r, u);
+        } else {
+            u = ch.add(kWfJac, u);
+        }
+    }
+    if (!ch.ok || !wf_launch<T>(c, l, ch, s)) return nullptr;
+    return ch.a.v[u];
+}
+
+// ---------------------------------------------------------------------------
 // V-cycle driver
 // ---------------------------------------------------------------------------
 // Smoothing sweeps on level l; returns the buffer holding the result (Jacobi
@@ -1109,6 +1373,16 @@ static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
         L_apply<T>(L.P, mvals<T>(L.P), ec, cur, 1, s);
         return smooth_fast<T>(c, l, s, b, cur, alt, nu2, false, have_w);
     }
+    if (wf_usable(c, L)) {
+        int ui = 0, ri = 0;
+        if (wf_pre<T>(c, l, s, b, ui, ri)) {
+            WfChain<T> view = wf_chain_for<T>(c, l, b);
+            L_spmv<T>(L.R, view.a.v[ri], bc, s);
+            T *ec = vcycle_level<T>(c, l + 1, s);
+            T *res = wf_post<T>(c, l, s, b, ui, ec);
+            if (res) return res;
+        }
+    }
     T *cur = smooth<T>(c, l, s, b, u, t, r, nu1, true);
     T *alt = (cur == u) ? t : u;
     L_resid<T>(L.A, b, cur, r, s);
@@ -1155,6 +1429,7 @@ static void enqueue_init(amg_ctx *c, cudaStream_t s, double tol, int max_iter) {
     const int n0 = c->lev[0].n;
     const int nb = std::min(grid_for(n0), kNumSMs * 8);
     const double stall = (c->smoother == AMG_SMOOTHER_GNN) ? c->stall_ratio : 0.0;
+    cudaMemsetAsync(c->dflag + 1, 0, sizeof(int), s);   // wavefront wait flag of this solve
     launch_pdl(k_state_init, dim3(1), dim3(1), 0, s, c->state, tol, max_iter, stall);
     launch_pdl(k_sqnorm_partial, dim3(nb), dim3(kBlock), 0, s, n0, c->db, c->partials);
     launch_pdl(k_norm_final, dim3(1), dim3(1024), 0, s, c->partials, nb, c->state, c->hist, 0, 0, 0);
@@ -1182,7 +1457,7 @@ static void free_graph(SolveGraph &G) {
 template <class T>
 static int ensure_graph(amg_ctx *c) {
     SolveGraph &G = c->sgraph[c->smoother + 3 * c->opt.outer];
-    if (G.exec && G.version == c->hier_version) return AMG_OK;
+    if (G.exec && G.version == c->hier_version && G.q_nodes == static_cast<int>(c->q_nodes)) return AMG_OK;
     free_graph(G);
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
@@ -1217,6 +1492,7 @@ static int ensure_graph(amg_ctx *c) {
     CK(e);
     CK(cudaGraphInstantiate(&G.exec, g, 0));
     G.version = c->hier_version;
+    G.q_nodes = static_cast<int>(c->q_nodes);
     return AMG_OK;
 }
 
@@ -1252,7 +1528,13 @@ static int solve_staged(amg_ctx *c, cudaStream_t s, double tol, int *n_vc, doubl
     }
     if (n_vc) *n_vc = nh - 1;
     if (hist) CK(cudaMemcpyAsync(hist, c->hist, sizeof(double) * nh, cudaMemcpyDeviceToHost, s));
+    int wferr = 0;
+    CK(cudaMemcpyAsync(&wferr, c->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (wferr) {
+        ctx_fail(c, "a wavefront smoothing kernel gave up waiting for a dependency (bounded wait ran out)");
+        return AMG_ERR_DEVICE_FLAG;
+    }
     return c->h_state->status;
 }
 
@@ -1315,6 +1597,19 @@ static void layout(amg_ctx *c, Planner &pl) {
             L.pq_p = pl.take<int>(std::max<size_t>(1, H.pair_p.size()));
             L.pq_q = pl.take<int>(std::max<size_t>(1, H.pair_q.size()));
         }
+        const WfPlan &W = c->wfplan[l];
+        L.wf = W.on;
+        if (W.on) {
+            L.wf_brows = W.brows;
+            L.wf_nblk = W.nblk;
+            L.wf_grid = W.grid;
+            L.wf_lohi = pl.take<int>(W.lohi.size());
+            L.wf_order = pl.take<int>(W.order.size());
+            L.wf_flags = pl.take<unsigned>(static_cast<size_t>(kWfMaxPhases) * W.nblk);
+            L.wf_ctrl = pl.take<unsigned>(4);
+            L.wf_buf = pl.take<double>(static_cast<size_t>(kWfBufs) * L.n);
+            L.diag32 = pl.take<float>(L.n);
+        }
         L.vw = pl.take<double>(L.n);
         L.vb = pl.take<double>(L.n);
         L.vu = pl.take<double>(L.n);
@@ -1333,6 +1628,7 @@ static void layout(amg_ctx *c, Planner &pl) {
     c->n_partials = kNumSMs * kOuterBlocksPerSM;        // blocks of a capped grid
     c->partials = pl.take<double>(5 * c->n_partials);  // up to 5 partial sums per block
     c->scal = pl.take<double>(nlev);
+    c->wcoef = pl.take<float>(8 * static_cast<size_t>(nlev));
     c->state = pl.take<SolveState>(1);
     c->hist = pl.take<double>(c->opt.max_iter + 1);
     c->dflag = pl.take<int>(4);
@@ -1385,8 +1681,11 @@ static int upload(amg_ctx *c) {
     free_device(c);
     ++c->hier_version;
     c->stall_ratio = 0.0;   // the in-solve check belongs to a mesh
-    const int prc = plan_fast_levels(c);
+    int prc = plan_fast_levels(c);
     if (prc) return prc;
+    prc = plan_wavefront(c);
+    if (prc) return prc;
+    c->q_nodes = false;
     Planner pl;
     layout(c, pl);
     c->arena_bytes = pl.off;
@@ -1417,6 +1716,13 @@ static int upload(amg_ctx *c) {
             }
         }
         k_extract_diag<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag); AMG_COUNT();
+        if (L.wf) {
+            const WfPlan &W = c->wfplan[l];
+            CK(cudaMemcpyAsync(L.wf_lohi, W.lohi.data(), sizeof(int) * W.lohi.size(), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(L.wf_order, W.order.data(), sizeof(int) * W.order.size(), cudaMemcpyHostToDevice, s));
+            launch_pdl(k_convert<double, float>, dim3(grid_for(L.n)), dim3(kBlock), 0, s, L.n,
+                       static_cast<const double *>(L.diag), L.diag32);
+        }
         const int nb = std::min(grid_for(L.n), kNumSMs * 8);
         k_offdiag_absmax<<<nb, kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, c->partials); AMG_COUNT();
         k_max_final<<<1, 32, 0, s>>>(c->partials, nb, c->scal + l); AMG_COUNT();
@@ -1486,6 +1792,7 @@ void amg_default_options(amg_options *o) {
     o->device = 0;
     o->gnn_precision = AMG_GNN_BF16;
     o->outer = AMG_OUTER_REFINE;
+    o->fused_sweeps = 1;
 }
 
 int amg_create(amg_ctx **ctx, const amg_options *opt) {
@@ -1502,7 +1809,7 @@ int amg_create(amg_ctx **ctx, const amg_options *opt) {
         (o.precision != AMG_FP64 && o.precision != AMG_FP32_IN_FP64) ||
         (o.smoother != AMG_SMOOTHER_JACOBI && o.smoother != AMG_SMOOTHER_GNN) || !(o.theta >= 0.0) ||
         (o.gnn_precision != AMG_GNN_FP32 && o.gnn_precision != AMG_GNN_BF16) ||
-        (o.outer != AMG_OUTER_REFINE && o.outer != AMG_OUTER_PCG) ||
+        (o.outer != AMG_OUTER_REFINE && o.outer != AMG_OUTER_PCG) || (o.fused_sweeps != 0 && o.fused_sweeps != 1) ||
         !(o.theta <= 1.0) || !std::isfinite(o.omega)) {
         g_create_err = "invalid amg_options";
         return AMG_ERR_ARG;
@@ -1741,6 +2048,9 @@ int enqueue_coeff_assembly(amg_ctx *c, const float *d_coef, cudaStream_t s) {
     if (M.nlev > 0 && M.start[M.nlev] > 0) {
         k_assemble_ma_all<<<grid_for(M.start[M.nlev]), kBlock, 0, s>>>(M, c->opt.precision == AMG_FP64 ? 1 : 0); AMG_COUNT();
     }
+    if (nlev > 1) {
+        k_wf_coef<<<1, 32, 0, s>>>(nlev - 1, d_coef, c->scal, c->wcoef); AMG_COUNT();
+    }
     CKL("assemble pseudo-inverse");
     return AMG_OK;
 }
@@ -1763,6 +2073,15 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
         }
     }
     (void)n_rows;
+    {
+        std::vector<float> wc(8 * static_cast<size_t>(nlev), 0.0f);
+        for (int l = 0; l < nlev - 1; ++l) {
+            for (int k = 0; k < 5; ++k) wc[8 * l + k] = static_cast<float>(coef[5 * l + k]);
+            wc[8 * l + 5] = static_cast<float>(1.0 / c->scales[l]);
+        }
+        CK(cudaMemcpyAsync(c->wcoef, wc.data(), sizeof(float) * wc.size(), cudaMemcpyHostToDevice, s));
+        c->q_nodes = false;
+    }
     CKL("assemble pseudo-inverse");
     // the solve kernels fetch matrix values ahead of their grid-dependency
     // wait: finish writing them before any of those kernels is launched
@@ -1803,6 +2122,7 @@ int amg_set_node_coeffs(amg_ctx *c, const double *coef, long long n_values) {
     cudaStream_t s = c->stream;
     if (need == 0) {
         c->have_q = true;
+        c->q_nodes = true;
         c->smoother = AMG_SMOOTHER_GNN;
         return AMG_OK;
     }
@@ -1828,6 +2148,7 @@ int amg_set_node_coeffs(amg_ctx *c, const double *coef, long long n_values) {
     cudaFree(d_c);
     if (e != cudaSuccess) return ctx_cuda_check(c, e, "assemble per-node pseudo-inverse");
     c->have_q = true;
+    c->q_nodes = true;   // the wavefront chains read the stored values
     c->smoother = AMG_SMOOTHER_GNN;
     return AMG_OK;
 }
@@ -1879,7 +2200,8 @@ int amg_solve(amg_ctx *c, const double *b, double *x, double rtol, int *n_vc, do
     if (rc == AMG_ERR_CUDA) return rc;
     CK(cudaMemcpyAsync(x, c->dx, sizeof(double) * n0, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (rc != AMG_OK) c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
+    if (rc != AMG_OK && rc != AMG_ERR_DEVICE_FLAG)
+        c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
     else if (c->last_rerouted) c->err = "learned smoother stalled; solve finished with Jacobi (rerouted)";
     return rc;
 }
@@ -1900,7 +2222,8 @@ int amg_solve_device(amg_ctx *c, const double *d_b, double *d_x, double rtol, vo
     if (rc == AMG_ERR_CUDA) return rc;
     CK(cudaMemcpyAsync(d_x, c->dx, sizeof(double) * n0, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
-    if (rc != AMG_OK) c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
+    if (rc != AMG_OK && rc != AMG_ERR_DEVICE_FLAG)
+        c->err = "solve ended without reaching the tolerance (status " + std::to_string(rc) + ")";
     else if (c->last_rerouted) c->err = "learned smoother stalled; solve finished with Jacobi (rerouted)";
     return rc;
 }
@@ -1936,7 +2259,12 @@ static void smooth_level_device(amg_ctx *c, int l, const double *d_b, double *d_
     T *b = reinterpret_cast<T *>(L.vb), *u = reinterpret_cast<T *>(L.vu);
     launch_pdl(k_convert<double, T>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, d_b, b);
     launch_pdl(k_convert<double, T>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, d_u, u);
-    T *res = smooth<T>(c, l, s, b, u, reinterpret_cast<T *>(L.vt), reinterpret_cast<T *>(L.vr), nsw, false);
+    T *res = nullptr;
+    if (nsw > 0 && L.wf && c->smoother != AMG_SMOOTHER_CHEB) {
+        cudaMemsetAsync(c->dflag + 1, 0, sizeof(int), s);
+        res = wf_smooth<T>(c, l, s, b, u, nsw);
+    }
+    if (!res) res = smooth<T>(c, l, s, b, u, reinterpret_cast<T *>(L.vt), reinterpret_cast<T *>(L.vr), nsw, false);
     launch_pdl(k_convert<T, double>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, res, d_u);
 }
 
@@ -2221,6 +2549,26 @@ int kernel_launch(amg_ctx *c, int which, int l, int reps, cudaStream_t s, double
             by = vcycle_bytes_level(c, 0, tb);
             for (int k = 0; k < reps; ++k) vcycle_level<T>(c, 0, s);
             break;
+        case AMG_K_WF_PRE:
+        case AMG_K_WF_POST: {
+            if (!wf_usable(c, L) || l >= last)
+                return ctx_fail(c, "level runs no wavefront chain (L2-sized level, Chebyshev, or fused_sweeps = 0)"),
+                       AMG_ERR_STATE;
+            if (c->smoother == AMG_SMOOTHER_GNN && !c->have_q)
+                return ctx_fail(c, "no pseudo-inverse coefficients set"), AMG_ERR_STATE;
+            const bool pre = (which == AMG_K_WF_PRE);
+            // the method's bytes of the passes the chain runs (as if unfused)
+            by = pre ? smooth_bytes(c, L, tb, c->opt.nu1, true) + pass_bytes(L.A, tb, L.n, 2)
+                     : pass_bytes(L.P, tb, L.P.nc, 2) + smooth_bytes(c, L, tb, c->opt.nu2, false);
+            const T *e = reinterpret_cast<const T *>(c->lev[l + 1].vu);
+            cudaMemsetAsync(c->dflag + 1, 0, sizeof(int), s);
+            for (int k = 0; k < reps; ++k) {
+                int ui = 0, ri = 0;
+                if (pre) wf_pre<T>(c, l, s, b, ui, ri);
+                else wf_post<T>(c, l, s, b, 2, e);
+            }
+            break;
+        }
         default:
             return ctx_fail(c, "unknown kernel id"), AMG_ERR_ARG;
     }

@@ -38,6 +38,24 @@ struct DevLevel {
     DevMat RA;                                 // R A for the fused residual + restriction
     int *pp = nullptr, *pq_p = nullptr, *pq_q = nullptr;
     double *vw = nullptr;                      // w = M b of the current V-cycle
+    // wavefront smoothing chains (levels too large for L2; wavefront.cuh)
+    bool wf = false;
+    int wf_brows = 0, wf_nblk = 0, wf_grid = 0;
+    int *wf_lohi = nullptr;                    // first / last block of each block's columns
+    int *wf_order = nullptr;                   // task orders of 1..kWfMaxPhases-pass chains
+    unsigned *wf_flags = nullptr;              // kWfMaxPhases x nblk completion epochs
+    unsigned *wf_ctrl = nullptr;               // task counter, finished CTAs, epoch
+    double *wf_buf = nullptr;                  // kWfBufs chain vectors (n doubles of storage each)
+    float *diag32 = nullptr;                   // a_ii in FP32 (pseudo-inverse values on the fly)
+};
+
+// Host-side plan of a level's wavefront chains (built at upload).
+struct WfPlan {
+    bool on = false;
+    int brows = 0, nblk = 0, grid = 0;
+    std::vector<int> lohi;                     // 2 x nblk
+    std::vector<int> order;                    // every chain length, back to back
+    int off[10] = {};                          // off[p]..off[p+1]: order of a p-pass chain (p = 1..8)
 };
 
 enum : int { kRunning = 1, kStalled = 2 };
@@ -65,6 +83,7 @@ struct SolveGraph {
     cudaGraphExec_t exec = nullptr;
     long long version = -1;
     long long body_kernels = 0;
+    int q_nodes = -1;    // the pseudo-inverse source the captured chains use
 };
 
 struct GcinEngine;
@@ -103,6 +122,9 @@ struct amg_ctx {
     double *pcg = nullptr;                     // conjugate gradients: r, r_prev, z, p, q (n_0 each)
     double stall_ratio = 0.0;                  // armed by amg_reroute for the learned smoother
     int last_rerouted = 0;                     // the last solve switched to Jacobi
+    float *wcoef = nullptr;                    // per level: d0 d1 d2 o1 o2 1/s (FP32, wavefront chains)
+    bool q_nodes = false;                      // Q^-1 from per-node coefficients (stored values only)
+    std::vector<amg::WfPlan> wfplan;           // per level
 };
 
 namespace amg {

@@ -1225,6 +1225,7 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
     if (e != cudaSuccess) return ctx_cuda_check(c, e, "GCIN graph launch");
     g_launches.fetch_add(g->exec_kernels);
     c->have_q = true;
+    c->q_nodes = false;
     c->smoother = AMG_SMOOTHER_GNN;
     int dflag = 0;
     const int G = g->batch.G;

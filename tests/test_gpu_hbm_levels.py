@@ -1,0 +1,100 @@
+"""Element-wise FP64 parity of the sweep and V-cycle kernels on levels past
+the L2 cache (the HBM-bound path of Sec. 2.2 / Sec. 2.3 / Sec. 3.1):
+
+* a 700 x 700 5-point grid (490,000 rows, 2,447,200 entries: one lane per
+  row, and an M A pair list too large for the single-pass sweep);
+* the finest levels of the 2.5M-node generalisation mesh (graded Delaunay
+  with an anisotropic band).
+
+The hierarchy is the library's own host setup (read back with
+amg_get_level and loaded into an FP64 context), so the oracle's V-cycle and
+the GPU's run on identical matrices; the oracle applies its sweep and
+V-cycle (oracle.solve.sweep / vcycle_operator_apply) to the same seeded
+vectors.  Bars: 1e-13 (sweeps) and 1e-12 (V-cycle) relative, the FP64 bars
+used everywhere else.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_19251_gb300 as P
+import workloads as W
+from oracle import setup as OS
+from oracle import solve as O
+from tests.gpu_helpers import library_levels, rel_err
+
+pytestmark = pytest.mark.gpu
+
+COEFFS = [0.62, 0.03, -0.01, -0.18, 0.02]
+
+
+class _Lv:
+    def __init__(self, A, Pm):
+        self.A, self.P = A, Pm
+        self.R = OS.transpose(Pm) if Pm is not None else None
+
+
+@pytest.fixture(scope="module", params=["grid700", "c4"])
+def hbm(request):
+    A = W.poisson5(700) if request.param == "grid700" else W.c4_matrix(0)
+    ctx0 = P.amg_create(precision=P.AMG_FP64)
+    try:
+        P.amg_setup(ctx0, A)
+        levels = [_Lv(a, p) for a, p in library_levels(ctx0)]
+    finally:
+        P.amg_destroy(ctx0)
+    ctx = P.amg_create(precision=P.AMG_FP64)
+    P.amg_load_hierarchy(ctx, [l.A for l in levels], [l.P for l in levels[:-1]], [l.R for l in levels[:-1]])
+    h = O.OHierarchy.of(levels)
+    yield request.param, levels, ctx, h
+    P.amg_destroy(ctx)
+
+
+def test_finest_level_is_hbm_sized(hbm):
+    name, levels, ctx, h = hbm
+    A0 = levels[0].A
+    assert A0.nnz >= 1 << 21                     # one lane per row group or two
+    assert A0.nnz * 8 > 16 * 2 ** 20             # an FP32 pass is far past what the single-pass rule accepts
+    with pytest.raises(P.AmgError):              # no single-pass M A sweep on this level
+        P.amg_kernel_launch(ctx, P.AMG_K_MASWEEP, 0, 1)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "pinv"])
+def test_sweeps_fp64(hbm, smoother):
+    name, levels, ctx, h = hbm
+    if smoother == "pinv":
+        P.amg_set_coeffs(ctx, [COEFFS] * len(levels))
+        h.set_pseudo_inverse([COEFFS] * len(levels))
+    else:
+        P.amg_set_jacobi(ctx)
+        h.set_jacobi()
+    for l in range(min(2, len(levels) - 1)):
+        n = levels[l].A.n_rows
+        b = W.rhs_uniform(20 + l, n)
+        u0 = W.rhs_uniform(30 + l, n)
+        db, du = torch.tensor(b, device="cuda"), torch.tensor(u0, device="cuda")
+        P.amg_smooth_device(ctx, l, db, du, 3)
+        torch.cuda.synchronize()
+        u = torch.from_numpy(u0)
+        for _ in range(3):
+            u = O.sweep(h.levels[l], torch.from_numpy(b), u)
+        err = rel_err(du.cpu().numpy(), u.numpy())
+        assert err < 1e-13, (name, l, err)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "pinv"])
+def test_vcycle_fp64(hbm, smoother):
+    name, levels, ctx, h = hbm
+    if smoother == "pinv":
+        P.amg_set_coeffs(ctx, [COEFFS] * len(levels))
+        h.set_pseudo_inverse([COEFFS] * len(levels))
+    else:
+        P.amg_set_jacobi(ctx)
+        h.set_jacobi()
+    r = W.rhs_uniform(5, levels[0].A.n_rows)
+    dr = torch.tensor(r, device="cuda")
+    de = torch.empty_like(dr)
+    P.amg_vcycle_device(ctx, dr, de)
+    torch.cuda.synchronize()
+    err = rel_err(de.cpu().numpy(), O.vcycle_operator_apply(h, r))
+    assert err < 1e-12, (name, err)
