@@ -87,12 +87,14 @@ typedef struct {
                          then holds the recurrence residual, and a breakdown
                          (z.r <= 0 or p.Ap <= 0) ends the solve with
                          AMG_ERR_DIVERGED leaving x at the last iterate           */
-    int fused_sweeps; /* 1 (default): on levels too large for the L2 cache, each
-                         smoothing phase of the V-cycle (with the residual for
-                         restriction, or with the prolongation-correction) runs
-                         as one wavefront kernel that re-reads A from L2 instead
-                         of HBM, with the pseudo-inverse values evaluated on the
-                         fly in FP32; 0: one kernel per pass (same operators)    */
+    int fused_sweeps; /* 0 (default): one kernel per pass.  1: on levels too
+                         large for the L2 cache, each smoothing phase of the
+                         V-cycle (with the residual for restriction, or with the
+                         prolongation-correction) runs as one wavefront kernel
+                         that re-reads A from L2 instead of HBM, with the
+                         pseudo-inverse values evaluated on the fly in FP32
+                         (same operators; slower on GB300 so far: the passes are
+                         bound by load latency, not by HBM bandwidth)            */
 } amg_options;
 
 /* Fill *opt with the paper's settings: nu1 = nu2 = 2, max_levels = 10,
@@ -318,6 +320,8 @@ int amg_get_chebyshev(const amg_ctx *ctx, int level, double *rho, double *theta,
 #define AMG_K_MASWEEP   7   /* u' = u + w - (Q^-1 A) u single pass   (latency-optimised levels) */
 #define AMG_K_WF_PRE    8   /* wavefront chain: pre-smoothing from zero + residual (HBM-sized levels) */
 #define AMG_K_WF_POST   9   /* wavefront chain: prolongation-correction + post-smoothing            */
+#define AMG_K_EMPTY    10   /* an empty one-CTA kernel with the solve's dependent-launch attribute
+                               (the floor of a chain of launches; level ignored)                 */
 
 /* Launch `reps` back-to-back instances of one solve-path kernel on level
  * `level`, using the context's own work vectors, asynchronously on

@@ -359,7 +359,7 @@ def amg_loss_grad(ctx, c, f, n_vc=1):
 
 
 (AMG_K_RESIDUAL, AMG_K_PINV, AMG_K_JACOBI, AMG_K_RESTRICT, AMG_K_PROLONG, AMG_K_OUTER, AMG_K_VCYCLE, AMG_K_MASWEEP,
- AMG_K_WF_PRE, AMG_K_WF_POST) = range(10)
+ AMG_K_WF_PRE, AMG_K_WF_POST, AMG_K_EMPTY) = range(11)
 
 
 def gcin_tc_selftest(x, W, bias, no_commit=False, device=0):

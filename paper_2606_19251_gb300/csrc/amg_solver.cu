@@ -382,6 +382,86 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(int n, const int *__rest
     block_partial(sq, partial);
 }
 
+// The finest level's FP64 operator for the outer-loop passes, in warp
+// slices: rows sorted by length (longest first) within windows of
+// kEllWindow rows, 32 rows per slice, a slice's entries column-major (entry
+// k of lane l at ptr[s] + 32 k + l) and padded with zeros to its longest
+// row.  One warp per slice issues the same number of DFMAs on every lane,
+// so GB300's narrow FP64 pipe spends its cycles on the entries (and the
+// little padding the sort leaves), not on lanes idle past a short row.
+// row[32 s + l] is the matrix row of lane l (-1 past the last row).
+struct Ell64 {
+    int nslice = 0;
+    const int *ptr = nullptr, *row = nullptr, *col = nullptr;
+    const double *val = nullptr;
+};
+constexpr int kEllWindow = 1024;
+
+// Dot product of a slice row with x: acc0 + sum_k v_k x_{c_k} (acc0 - ... when
+// NEG), four entries' loads in flight per step (the trip count is
+// warp-uniform).
+template <bool NEG>
+__device__ __forceinline__ double ell_dot(const Ell64 &E, int s, int lane, double acc, const double *__restrict__ x) {
+    const int p0 = __ldg(E.ptr + s);
+    const int w = (__ldg(E.ptr + s + 1) - p0) >> 5;
+    for (int k = 0; k < w; k += 4) {
+        int c[4];
+        double v[4], xv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int p = p0 + ((k + j) << 5) + lane;
+            c[j] = (k + j < w) ? __ldg(E.col + p) : 0;
+            v[j] = (k + j < w) ? __ldg(E.val + p) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xv[j] = (k + j < w) ? x[c[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (k + j < w) acc = NEG ? fma(-v[j], xv[j], acc) : fma(v[j], xv[j], acc);
+    }
+    return acc;
+}
+
+// r = b - A x (FP64) over warp slices, rT = (T) r, r64 = r (when given),
+// partial[block] = sum r^2 over the block's rows
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_outer_ell(Ell64 E, const double *__restrict__ b,
+                                                      const double *__restrict__ x, T *__restrict__ rT,
+                                                      double *__restrict__ partial, double *__restrict__ r64) {
+    pdl_wait_and_release();
+    const int lane = threadIdx.x & 31;
+    double sq = 0.0;
+    for (int s = blockIdx.x * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5); s < E.nslice;
+         s += gridDim.x * (kBlock / 32)) {
+        const int row = __ldg(E.row + 32 * s + lane);
+        const double r = ell_dot<true>(E, s, lane, row >= 0 ? b[row] : 0.0, x);
+        if (row >= 0) {
+            rT[row] = static_cast<T>(r);
+            if (r64) r64[row] = r;
+            sq = fma(r, r, sq);
+        }
+    }
+    block_partial(sq, partial);
+}
+
+// q = A p (FP64) over warp slices, partial p.q
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv_ell(Ell64 E, const double *__restrict__ p,
+                                                         double *__restrict__ q, double *__restrict__ partial) {
+    pdl_wait_and_release();
+    const int lane = threadIdx.x & 31;
+    double pq = 0.0;
+    for (int s = blockIdx.x * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5); s < E.nslice;
+         s += gridDim.x * (kBlock / 32)) {
+        const int row = __ldg(E.row + 32 * s + lane);
+        const double a = ell_dot<false>(E, s, lane, 0.0, p);
+        if (row >= 0) {
+            q[row] = a;
+            pq = fma(p[row], a, pq);
+        }
+    }
+    block_partial(pq, partial);
+}
+
 __global__ void __launch_bounds__(kBlock) k_sqnorm_partial(int n, const double *__restrict__ v,
                                                            double *__restrict__ partial) {
     pdl_wait_and_release();
@@ -596,6 +676,10 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ 
     st->k = k + 1;
     if (use_cond) cudaGraphSetConditional(cond, status == kRunning ? 1u : 0u);
 }
+
+// An empty dependent launch: the floor of one step of a chain of
+// programmatic-dependent launches (amg_kernel_launch, AMG_K_EMPTY).
+__global__ void k_empty() { pdl_wait_and_release(); }
 
 // Copies "still running" into the solve graph's WHILE condition.
 __global__ void k_set_cond(const SolveState *st, cudaGraphConditionalHandle cond) {
@@ -1055,15 +1139,15 @@ static int plan_wavefront(amg_ctx *c) {
                  kNumSMs;
         W.brows = brows;
         W.nblk = nblk;
-        std::vector<int> ord;
+        std::vector<int> desc;
         bool ok = true;
         W.off[1] = 0;
         for (int np = 1; np <= kWfMaxPhases && ok; ++np) {
             const int lag = static_cast<int>((static_cast<long long>(kWfLagPct) * W.grid + 100LL * np - 1) /
                                              (100LL * np)) + 1;
-            ok = wf_build_order(nblk, W.lohi, np, lag, ord);
-            W.order.insert(W.order.end(), ord.begin(), ord.end());
-            W.off[np + 1] = static_cast<int>(W.order.size());
+            ok = wf_build_order(nblk, W.lohi, np, lag, desc);
+            W.task.insert(W.task.end(), desc.begin(), desc.end());
+            W.off[np + 1] = static_cast<int>(W.task.size() / 4);
         }
         if (!ok) return ctx_fail(c, "wavefront task order failed its dependency check"), AMG_ERR_ARG;
         W.on = true;
@@ -1135,7 +1219,6 @@ static WfChain<T> wf_chain_for(amg_ctx *c, int l, const T *b) {
     a.pv = mvals<T>(L.P);
     a.b = b;
     for (int k = 0; k < kWfBufs; ++k) a.v[k] = reinterpret_cast<T *>(L.wf_buf + static_cast<size_t>(k) * L.n);
-    a.lohi = L.wf_lohi;
     a.flags = L.wf_flags;
     a.ctrl = L.wf_ctrl;
     a.err = c->dflag + 1;
@@ -1150,7 +1233,7 @@ static bool wf_launch(amg_ctx *c, int l, WfChain<T> &ch, cudaStream_t s) {
     if (!ch.ok || ch.a.nphase < 1) return false;
     const WfPlan &W = c->wfplan[l];
     ch.a.ntask = W.off[ch.a.nphase + 1] - W.off[ch.a.nphase];
-    ch.a.order = L.wf_order + W.off[ch.a.nphase];
+    ch.a.task = reinterpret_cast<const int4 *>(L.wf_task) + W.off[ch.a.nphase];
     const bool fly = std::is_same<T, float>::value && !c->q_nodes;
     const int grid = std::max(1, std::min(L.wf_grid, ch.a.ntask));
     switch (L.A.tpr) {
@@ -1392,13 +1475,44 @@ static T *vcycle_level(amg_ctx *c, int l, cudaStream_t s) {
     return smooth<T>(c, l, s, b, cur, alt, r, nu2, false);
 }
 
+static Ell64 ell_of(const amg_ctx *c) {
+    Ell64 E;
+    E.nslice = c->ell_nslice;
+    E.ptr = c->ell_ptr;
+    E.row = c->ell_row;
+    E.col = c->ell_col;
+    E.val = c->ell_val;
+    return E;
+}
+
+// Blocks of the warp-slice passes: one warp per slice, grid capped like the
+// CSR outer passes (one partial-sum slot per block).
+static int ell_blocks(const amg_ctx *c) {
+    const long long need = (static_cast<long long>(c->ell_nslice) + kBlock / 32 - 1) / (kBlock / 32);
+    return static_cast<int>(std::max(1LL, std::min<long long>(need, static_cast<long long>(kNumSMs) * kOuterBlocksPerSM)));
+}
+
+// FP64 outer residual r = b - A x with its FP32 copy and norm partials;
+// returns the number of partial sums.
+template <class T>
+static int launch_outer(amg_ctx *c, cudaStream_t s, T *rT, double *r64) {
+    if (c->ell_nslice > 0) {
+        const int nb = ell_blocks(c);
+        launch_pdl(k_outer_ell<T>, dim3(nb), dim3(kBlock), 0, s, ell_of(c), static_cast<const double *>(c->db),
+                   static_cast<const double *>(c->dx), rT, c->partials, r64);
+        return nb;
+    }
+    const DevMat &A = c->lev[0].A;
+    const int nb = outer_blocks(A);
+    L_outer<T>(A, c->db, c->dx, rT, c->partials, nb, s, r64);
+    return nb;
+}
+
 template <class T>
 static void enqueue_outer_residual(amg_ctx *c, cudaStream_t s, int use_cond = 0,
                                    cudaGraphConditionalHandle cond = 0) {
-    const DevMat &A = c->lev[0].A;
-    const int nb = outer_blocks(A);
     double *r64 = (c->opt.outer == AMG_OUTER_PCG) ? c->pcg : nullptr;   // CG keeps r in FP64
-    L_outer<T>(A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vb), c->partials, nb, s, r64);
+    const int nb = launch_outer<T>(c, s, reinterpret_cast<T *>(c->lev[0].vb), r64);
     launch_pdl(k_norm_final, dim3(1), dim3(1024), 0, s, c->partials, nb, c->state, c->hist, 1, use_cond, cond);
 }
 
@@ -1408,7 +1522,7 @@ template <class T>
 static void enqueue_pcg_iteration(amg_ctx *c, cudaStream_t s, int use_cond, cudaGraphConditionalHandle cond) {
     const DevMat &A = c->lev[0].A;
     const int n = c->lev[0].n;
-    const int nb = outer_blocks(A);
+    const int nb = c->ell_nslice > 0 ? ell_blocks(c) : outer_blocks(A);
     double *r = c->pcg, *rprev = r + n, *z = rprev + n, *p = z + n, *q = p + n;
     double *P0 = c->partials, *P1 = P0 + c->n_partials, *P2 = P1 + c->n_partials, *P3 = P2 + c->n_partials;
     T *e = vcycle_level<T>(c, 0, s);
@@ -1416,7 +1530,10 @@ static void enqueue_pcg_iteration(amg_ctx *c, cudaStream_t s, int use_cond, cuda
                static_cast<const double *>(r), static_cast<const double *>(rprev), z, P0, P1);
     launch_pdl(k_pcg_dir, dim3(nb), dim3(kBlock), 0, s, n, static_cast<const double *>(z), p,
                static_cast<const double *>(P0), static_cast<const double *>(P1), nb, c->state);
-    TPR_DISPATCH(A.tpr, Launch<T>::template pcg_spmv, A, p, q, P2, nb, s);
+    if (c->ell_nslice > 0)
+        launch_pdl(k_pcg_spmv_ell, dim3(nb), dim3(kBlock), 0, s, ell_of(c), static_cast<const double *>(p), q, P2);
+    else
+        TPR_DISPATCH(A.tpr, Launch<T>::template pcg_spmv, A, p, q, P2, nb, s);
     launch_pdl(k_pcg_update<T>, dim3(nb), dim3(kBlock), 0, s, n, c->dx, r, rprev, static_cast<const double *>(p),
                static_cast<const double *>(q), reinterpret_cast<T *>(c->lev[0].vb), static_cast<const double *>(P0),
                static_cast<const double *>(P2), nb, c->state, P3);
@@ -1546,6 +1663,9 @@ static const int kMaxCoarseDense = 4096;
 static void free_graph(SolveGraph &G);
 
 static void free_device(amg_ctx *c) {
+    c->ell_nslice = 0;   // the slices live in the arena
+    c->ell_ptr = c->ell_row = c->ell_col = nullptr;
+    c->ell_val = nullptr;
     train_bufs_free(c);
     for (auto &G : c->sgraph) free_graph(G);
     if (c->arena) cudaFree(c->arena);
@@ -1565,6 +1685,55 @@ static void layout_mat(Planner &pl, DevMat &m, const HostCSR &h) {
     m.col = pl.take<int>(std::max<long long>(1, h.nnz()));
     m.v64 = pl.take<double>(std::max<long long>(1, h.nnz()));
     m.v32 = pl.take<float>(std::max<long long>(1, h.nnz()));
+}
+
+// Warp slices of the finest level's FP64 operator (see Ell64): rows sorted
+// by length, longest first, within windows of kEllWindow rows (stable, so
+// equal lengths keep their order); padding entries have value 0 and point at
+// the lane's own row.
+static void build_ell(amg_ctx *c) {
+    const HostCSR &A = c->host[0].A;
+    const int n = A.n_rows;
+    const int nslice = (n + 31) / 32;
+    std::vector<int> rows(static_cast<size_t>(nslice) * 32, -1);
+    for (int w0 = 0; w0 < n; w0 += kEllWindow) {
+        const int w1 = std::min(n, w0 + kEllWindow);
+        std::vector<int> idx(w1 - w0);
+        for (int i = w0; i < w1; ++i) idx[i - w0] = i;
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int a, int b) { return A.rp[a + 1] - A.rp[a] > A.rp[b + 1] - A.rp[b]; });
+        std::copy(idx.begin(), idx.end(), rows.begin() + w0);
+    }
+    c->h_ell_ptr.assign(nslice + 1, 0);
+    for (int sl = 0; sl < nslice; ++sl) {
+        int w = 0;
+        for (int l = 0; l < 32; ++l) {
+            const int r = rows[32 * sl + l];
+            if (r >= 0) w = std::max(w, A.rp[r + 1] - A.rp[r]);
+        }
+        c->h_ell_ptr[sl + 1] = c->h_ell_ptr[sl] + 32 * w;
+    }
+    const size_t ne = static_cast<size_t>(c->h_ell_ptr[nslice]);
+    c->h_ell_col.assign(std::max<size_t>(1, ne), 0);
+    c->h_ell_val.assign(std::max<size_t>(1, ne), 0.0);
+    for (int sl = 0; sl < nslice; ++sl) {
+        const int p0 = c->h_ell_ptr[sl], w = (c->h_ell_ptr[sl + 1] - p0) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const int r = rows[32 * sl + l];
+            const int len = r >= 0 ? A.rp[r + 1] - A.rp[r] : 0;
+            for (int k = 0; k < w; ++k) {
+                const size_t p = static_cast<size_t>(p0) + 32 * k + l;
+                if (k < len) {
+                    c->h_ell_col[p] = A.col[A.rp[r] + k];
+                    c->h_ell_val[p] = A.val[A.rp[r] + k];
+                } else {
+                    c->h_ell_col[p] = r >= 0 ? r : 0;
+                }
+            }
+        }
+    }
+    c->h_ell_row.swap(rows);
+    c->ell_nslice = nslice;
 }
 
 static void layout(amg_ctx *c, Planner &pl) {
@@ -1603,8 +1772,7 @@ static void layout(amg_ctx *c, Planner &pl) {
             L.wf_brows = W.brows;
             L.wf_nblk = W.nblk;
             L.wf_grid = W.grid;
-            L.wf_lohi = pl.take<int>(W.lohi.size());
-            L.wf_order = pl.take<int>(W.order.size());
+            L.wf_task = pl.take<int>(W.task.size());
             L.wf_flags = pl.take<unsigned>(static_cast<size_t>(kWfMaxPhases) * W.nblk);
             L.wf_ctrl = pl.take<unsigned>(4);
             L.wf_buf = pl.take<double>(static_cast<size_t>(kWfBufs) * L.n);
@@ -1622,6 +1790,10 @@ static void layout(amg_ctx *c, Planner &pl) {
     c->Linv = pl.take<double>(static_cast<size_t>(nL) * nL);
     c->LinvT = pl.take<double>(static_cast<size_t>(nL) * nL);
     const int n0 = c->host[0].A.n_rows;
+    c->ell_ptr = pl.take<int>(c->h_ell_ptr.size());
+    c->ell_row = pl.take<int>(c->h_ell_row.size());
+    c->ell_col = pl.take<int>(c->h_ell_col.size());
+    c->ell_val = pl.take<double>(c->h_ell_val.size());
     c->db = pl.take<double>(n0);
     c->dx = pl.take<double>(n0);
     c->pcg = pl.take<double>(5 * static_cast<size_t>(n0));
@@ -1685,6 +1857,7 @@ static int upload(amg_ctx *c) {
     if (prc) return prc;
     prc = plan_wavefront(c);
     if (prc) return prc;
+    build_ell(c);
     c->q_nodes = false;
     Planner pl;
     layout(c, pl);
@@ -1718,8 +1891,7 @@ static int upload(amg_ctx *c) {
         k_extract_diag<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag); AMG_COUNT();
         if (L.wf) {
             const WfPlan &W = c->wfplan[l];
-            CK(cudaMemcpyAsync(L.wf_lohi, W.lohi.data(), sizeof(int) * W.lohi.size(), cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(L.wf_order, W.order.data(), sizeof(int) * W.order.size(), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(L.wf_task, W.task.data(), sizeof(int) * W.task.size(), cudaMemcpyHostToDevice, s));
             launch_pdl(k_convert<double, float>, dim3(grid_for(L.n)), dim3(kBlock), 0, s, L.n,
                        static_cast<const double *>(L.diag), L.diag32);
         }
@@ -1732,6 +1904,11 @@ static int upload(amg_ctx *c) {
                                                       L.bw, L.isd); AMG_COUNT();
     }
     c->jac_omega = c->opt.omega;
+    CK(cudaMemcpyAsync(c->ell_ptr, c->h_ell_ptr.data(), sizeof(int) * c->h_ell_ptr.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->ell_row, c->h_ell_row.data(), sizeof(int) * c->h_ell_row.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->ell_col, c->h_ell_col.data(), sizeof(int) * c->h_ell_col.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->ell_val, c->h_ell_val.data(), sizeof(double) * c->h_ell_val.size(), cudaMemcpyHostToDevice,
+                       s));
     // coarsest level: dense FP64 Cholesky and the inverse factor
     const DevLevel &Lc = c->lev.back();
     const int nL = c->nL;
@@ -1745,6 +1922,9 @@ static int upload(amg_ctx *c) {
     CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->scales.data(), c->scal, sizeof(double) * nlev, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    c->h_ell_col = std::vector<int>();    // copied: the host slices are not kept
+    c->h_ell_val = std::vector<double>();
+    c->h_ell_row = std::vector<int>();
     if (flag) {
         c->err = "coarsest-level matrix is not positive definite";
         free_device(c);
@@ -1792,7 +1972,7 @@ void amg_default_options(amg_options *o) {
     o->device = 0;
     o->gnn_precision = AMG_GNN_BF16;
     o->outer = AMG_OUTER_REFINE;
-    o->fused_sweeps = 1;
+    o->fused_sweeps = 0;
 }
 
 int amg_create(amg_ctx **ctx, const amg_options *opt) {
@@ -2531,10 +2711,7 @@ int kernel_launch(amg_ctx *c, int which, int l, int reps, cudaStream_t s, double
         case AMG_K_OUTER: {
             const DevMat &A = c->lev[0].A;
             by = 4.0 * (A.nr + 1) + 12.0 * A.nnz + 16.0 * A.nr + tb * A.nr;
-            const int nb = outer_blocks(A);
-            for (int k = 0; k < reps; ++k) {
-                L_outer<T>(A, c->db, c->dx, reinterpret_cast<T *>(c->lev[0].vr), c->partials, nb, s);
-            }
+            for (int k = 0; k < reps; ++k) launch_outer<T>(c, s, reinterpret_cast<T *>(c->lev[0].vr), nullptr);
             break;
         }
         case AMG_K_MASWEEP:
@@ -2548,6 +2725,10 @@ int kernel_launch(amg_ctx *c, int which, int l, int reps, cudaStream_t s, double
         case AMG_K_VCYCLE:
             by = vcycle_bytes_level(c, 0, tb);
             for (int k = 0; k < reps; ++k) vcycle_level<T>(c, 0, s);
+            break;
+        case AMG_K_EMPTY:
+            by = 0.0;
+            for (int k = 0; k < reps; ++k) launch_pdl(k_empty, dim3(1), dim3(kBlock), 0, s);
             break;
         case AMG_K_WF_PRE:
         case AMG_K_WF_POST: {

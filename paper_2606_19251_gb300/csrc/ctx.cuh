@@ -41,10 +41,9 @@ struct DevLevel {
     // wavefront smoothing chains (levels too large for L2; wavefront.cuh)
     bool wf = false;
     int wf_brows = 0, wf_nblk = 0, wf_grid = 0;
-    int *wf_lohi = nullptr;                    // first / last block of each block's columns
-    int *wf_order = nullptr;                   // task orders of 1..kWfMaxPhases-pass chains
+    int *wf_task = nullptr;                    // task descriptors of 1..8-pass chains (4 ints each)
     unsigned *wf_flags = nullptr;              // kWfMaxPhases x nblk completion epochs
-    unsigned *wf_ctrl = nullptr;               // task counter, finished CTAs, epoch
+    unsigned *wf_ctrl = nullptr;               // finished CTAs, epoch
     double *wf_buf = nullptr;                  // kWfBufs chain vectors (n doubles of storage each)
     float *diag32 = nullptr;                   // a_ii in FP32 (pseudo-inverse values on the fly)
 };
@@ -54,8 +53,8 @@ struct WfPlan {
     bool on = false;
     int brows = 0, nblk = 0, grid = 0;
     std::vector<int> lohi;                     // 2 x nblk
-    std::vector<int> order;                    // every chain length, back to back
-    int off[10] = {};                          // off[p]..off[p+1]: order of a p-pass chain (p = 1..8)
+    std::vector<int> task;                     // descriptors of every chain length, back to back
+    int off[10] = {};                          // tasks off[p]..off[p+1]: a p-pass chain (p = 1..8)
 };
 
 enum : int { kRunning = 1, kStalled = 2 };
@@ -123,6 +122,12 @@ struct amg_ctx {
     double stall_ratio = 0.0;                  // armed by amg_reroute for the learned smoother
     int last_rerouted = 0;                     // the last solve switched to Jacobi
     float *wcoef = nullptr;                    // per level: d0 d1 d2 o1 o2 1/s (FP32, wavefront chains)
+    // finest level's FP64 operator in warp slices (outer-loop passes)
+    int ell_nslice = 0;
+    int *ell_ptr = nullptr, *ell_row = nullptr, *ell_col = nullptr;
+    double *ell_val = nullptr;
+    std::vector<int> h_ell_ptr, h_ell_row, h_ell_col;
+    std::vector<double> h_ell_val;
     bool q_nodes = false;                      // Q^-1 from per-node coefficients (stored values only)
     std::vector<amg::WfPlan> wfplan;           // per level
 };

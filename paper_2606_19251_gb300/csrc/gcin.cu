@@ -649,6 +649,8 @@ void gcin_prepare_device() {
     if (done[dev]) return;
     cudaFuncSetAttribute(k_agg_lin_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden>());
     cudaFuncSetAttribute(k_agg_lin_tc<kHidden32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden32>());
+    cudaFuncSetAttribute(k_bwd_lin_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcb_smem<kHidden>());
+    cudaFuncSetAttribute(k_bwd_lin_tc<kHidden32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcb_smem<kHidden32>());
     done[dev] = true;
 }
 
@@ -1044,7 +1046,14 @@ static void backward_impl(GcinBatch &b, const float *th, float *grad, cudaStream
                                                  l == kLayers - 1 ? nullptr : b.dx, b.dpooled, b.argmax, l, b.dy,
                                                  b.tsum, b.tsum2); AMG_COUNT();
         k_bwd_combine<H><<<G, combine_threads<H>(), 0, s>>>(b.gtile, b.tsum, b.tsum2, b.gS1, b.gS2); AMG_COUNT();
-        if (l > 0) {
+        if (l > 0 && b.bf16) {
+            // the forward's node linear ran on the tensor cores: so does its backward
+            k_bwd_lin_tc<H><<<(NT + 1) / 2, kBlock, tcb_smem<H>(), s>>>(b.tstart, b.tgraph, b.gptr, NT, b.y[l], b.mu[l],
+                                                                      b.rstd[l], th + pl.inG[l], b.gS1, b.gS2,
+                                                                      th + pl.convW[l], b.h[l], b.dy, b.dh, b.dWt,
+                                                                      b.err); AMG_COUNT();
+            k_agg_plain<H><<<warp_grid, kBlock, 0, s>>>(N, b.rp, b.col, b.w, b.dh, b.dx); AMG_COUNT();
+        } else if (l > 0) {
             k_bwd_in_lin_tile<H, H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.gptr, b.y[l], b.mu[l], b.rstd[l],
                                                           th + pl.inG[l], b.gS1, b.gS2, th + pl.convW[l], b.h[l],
                                                           b.dy, b.dh, b.dWt, b.bf16); AMG_COUNT();
@@ -1420,8 +1429,13 @@ int gcin_trainer_backward(gcin_trainer *t, const double *dc, double *dtheta_out)
                                         t->stream), "gradient download");
         if (rc) return rc;
     }
+    int dflag = 0;   // the tensor-core backward's bounded MMA wait
+    rc = tr_cuda(t, cudaMemcpyAsync(&dflag, t->batch.err, sizeof(int), cudaMemcpyDeviceToHost, t->stream),
+                 "flag download");
+    if (rc) return rc;
     rc = tr_cuda(t, cudaStreamSynchronize(t->stream), "sync");
     if (rc) return rc;
+    if (dflag) return tr_fail(t, AMG_ERR_DEVICE_FLAG, "tensor-core GCIN kernel timed out waiting for its MMAs");
     if (dtheta_out) std::copy(g.begin(), g.end(), dtheta_out);
     return AMG_OK;
 }

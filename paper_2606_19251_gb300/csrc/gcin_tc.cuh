@@ -197,3 +197,182 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
 }
 
 }  // namespace amg
+
+namespace amg {
+
+// Tensor-core form of the node-linear backward of layers 2..4 when the
+// forward ran on tcgen05 with BF16 operands (App. A.1; the backward of
+// Sec. 3.3 differentiates that rounded forward): per CTA two statistic tiles
+// (at most 128 nodes),
+//   1. dy of every node from the instance-norm backward (FP32, staged in
+//      shared memory; the bias gradient is its fixed-order column sum), then
+//      BF16 copies of dy into A1 (nodes x H, K = output feature) and into B2
+//      (H x 128, K = node: dy transposed), the forward's BF16 h into A2
+//      (rows = input feature, K = node) and round(W) into B1 (rows = input
+//      feature, K = output feature), all K-major, no swizzle;
+//   2. one thread issues D1 = A1 B1^T (dh = dy W^T, 128 x H) and
+//      D2 = A2 B2^T (sum_i h_i^T dy_i, rows < H used) into 2H TMEM columns;
+//   3. warps 0..3 read both back; dh is written per node, the weight gradient
+//      as the first tile's partial (the second tile's partial is zero).
+// Nodes past the tiles are zero in A2 / B2, so they add nothing to D2.  The
+// mbarrier wait is bounded as in the forward: on timeout the error flag is
+// raised, the MMAs are drained (bounded) and the TMEM columns freed.
+template <int H> constexpr int tcb_a1_bytes() { return kTcRows * H * 2; }
+template <int H> constexpr int tcb_b1_bytes() { return H * H * 2; }
+constexpr int tcb_a2_bytes() { return kTcRows * kTcRows * 2; }
+template <int H> constexpr int tcb_b2_bytes() { return H * kTcRows * 2; }
+template <int H> constexpr int tcb_d_bytes() { return kTcRows * (H + 1) * 4; }
+template <int H> constexpr int tcb_smem() {
+    return tcb_a1_bytes<H>() + tcb_b1_bytes<H>() + tcb_a2_bytes() + tcb_b2_bytes<H>() + tcb_d_bytes<H>();
+}
+
+template <int H>
+__global__ void __launch_bounds__(kBlock, 2) k_bwd_lin_tc(const int *__restrict__ tstart, const int *__restrict__ tgraph,
+                                                          const int *__restrict__ gptr, int NT,
+                                                          const float *__restrict__ y, const float *__restrict__ mu,
+                                                          const float *__restrict__ rstd,
+                                                          const float *__restrict__ gamma,
+                                                          const double *__restrict__ gS1,
+                                                          const double *__restrict__ gS2,
+                                                          const float *__restrict__ W, const float *__restrict__ hin,
+                                                          const float *__restrict__ dyn, float *__restrict__ dh,
+                                                          float *__restrict__ dWt, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char tcb_smem_buf[];
+    static_assert(H == 64 || H == 32, "GCIN widths with a tensor-core form: 64, 32");
+    constexpr uint32_t kCols = (2 * H < 32) ? 32 : 2 * H;   // D1 at column 0, D2 at column H
+    unsigned char *sA1 = tcb_smem_buf, *sB1 = sA1 + tcb_a1_bytes<H>();
+    unsigned char *sA2 = sB1 + tcb_b1_bytes<H>(), *sB2 = sA2 + tcb_a2_bytes();
+    float(*sD)[H + 1] = reinterpret_cast<float(*)[H + 1]>(sB2 + tcb_b2_bytes<H>());
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_ok;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t a1 = static_cast<uint32_t>(__cvta_generic_to_shared(sA1));
+    const uint32_t b1 = static_cast<uint32_t>(__cvta_generic_to_shared(sB1));
+    const uint32_t a2 = static_cast<uint32_t>(__cvta_generic_to_shared(sA2));
+    const uint32_t b2 = static_cast<uint32_t>(__cvta_generic_to_shared(sB2));
+    const uint32_t mbar = static_cast<uint32_t>(__cvta_generic_to_shared(&s_mbar));
+    if (warp == 0) {
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&s_taddr));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(kCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const int t0 = 2 * blockIdx.x;
+    const int t1 = min(t0 + 2, NT);
+    const int a0 = tstart[t0], nn = tstart[t1] - a0;
+    const int n0 = tstart[t0 + 1] - a0;   // nodes of the first tile
+    // B1 = round(W): row = input feature k, K = output feature n (W is [in][out])
+    for (int e = threadIdx.x; e < H * H; e += kBlock) {
+        const int k = e / H, n = e % H;
+        *reinterpret_cast<__nv_bfloat16 *>(sB1 + tc_off<H>(k, n)) = __float2bfloat16_rn(W[e]);
+    }
+    // 1. dy (instance-norm backward) of every node, FP32 in shared memory
+    for (int e = threadIdx.x; e < kTcRows * H; e += kBlock) {
+        const int k = e / H, f = e % H;
+        float dy = 0.f;
+        if (k < nn) {
+            const int g = tgraph[k < n0 ? t0 : t0 + 1];
+            const float inv_n = 1.f / static_cast<float>(gptr[g + 1] - gptr[g]);
+            const float ga = gamma[f], r = rstd[g * H + f];
+            const float c1 = ga * static_cast<float>(gS1[g * H + f]) * inv_n;
+            const float c2 = ga * static_cast<float>(gS2[g * H + f]) * inv_n;
+            const size_t i = static_cast<size_t>(a0 + k) * H + f;
+            const float yh = (y[i] - mu[g * H + f]) * r;
+            dy = r * (ga * dyn[i] - c1 - yh * c2);
+        }
+        sD[k][f] = dy;
+    }
+    __syncthreads();
+    // BF16 operands: A1 (dy, node rows), B2 (dy transposed), A2 (h transposed)
+    for (int e = threadIdx.x; e < kTcRows * H; e += kBlock) {
+        const int k = e / H, f = e % H;
+        const __nv_bfloat16 d = __float2bfloat16_rn(sD[k][f]);
+        *reinterpret_cast<__nv_bfloat16 *>(sA1 + tc_off<H>(k, f)) = d;
+        *reinterpret_cast<__nv_bfloat16 *>(sB2 + tc_off<kTcRows>(f, k)) = d;
+        const float hv = k < nn ? hin[static_cast<size_t>(a0 + k) * H + f] : 0.f;   // already BF16 values
+        *reinterpret_cast<__nv_bfloat16 *>(sA2 + tc_off<kTcRows>(f, k)) = __float2bfloat16_rn(hv);
+    }
+    // rows H..127 of A2 only produce rows of D2 that are never read
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    if (threadIdx.x == 0) {
+        for (int ks = 0; ks < H / 16; ++ks) {
+            const uint64_t ad = tc_desc<H>(a1 + ks * 256), bd = tc_desc<H>(b1 + ks * 256);
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                         ::"r"(taddr), "l"(ad), "l"(bd), "r"(tc_idesc<H>()), "r"(static_cast<uint32_t>(ks))
+                         : "memory");
+        }
+        for (int ks = 0; ks < kTcRows / 16; ++ks) {
+            const uint64_t ad = tc_desc<kTcRows>(a2 + ks * 256), bd = tc_desc<kTcRows>(b2 + ks * 256);
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                         ::"r"(taddr + static_cast<uint32_t>(H)), "l"(ad), "l"(bd), "r"(tc_idesc<H>()),
+                         "r"(static_cast<uint32_t>(ks))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+    }
+    // the bias gradient (FP32, fixed node order) while the MMAs run
+    float *out0 = dWt + static_cast<size_t>(t0) * (H * H + H);
+    if (threadIdx.x < H) {
+        float acc = 0.f;
+        for (int k = 0; k < nn; ++k) acc += sD[k][threadIdx.x];
+        out0[H * H + threadIdx.x] = acc;
+        if (t0 + 1 < t1) dWt[static_cast<size_t>(t0 + 1) * (H * H + H) + H * H + threadIdx.x] = 0.f;
+    }
+    const bool ok = tc_wait_bounded(mbar);
+    if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool all_ok = s_ok != 0;
+    if (all_ok && warp < 4) {
+        const int row = 32 * warp + lane;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {          // part 0: D1 (dh), part 1: D2 (weight gradient)
+#pragma unroll
+            for (int half = 0; half < H / 32; ++half) {
+                uint32_t r[32];
+                const uint32_t ta = taddr + (static_cast<uint32_t>(32 * warp) << 16) +
+                                    static_cast<uint32_t>(part * H + 32 * half);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                      "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                      "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(ta)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (part == 0) {
+                    if (row < nn) {
+#pragma unroll
+                        for (int f = 0; f < 32; ++f)
+                            dh[static_cast<size_t>(a0 + row) * H + 32 * half + f] = __uint_as_float(r[f]);
+                    }
+                } else if (row < H) {
+#pragma unroll
+                    for (int f = 0; f < 32; ++f) out0[row * H + 32 * half + f] = __uint_as_float(r[f]);
+                }
+            }
+        }
+    }
+    if (!all_ok) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        tc_wait_bounded(mbar);
+    }
+    // the second tile's weight partial is zero (its nodes are in the first's sum)
+    if (t0 + 1 < t1)
+        for (int e = threadIdx.x; e < H * H; e += kBlock) dWt[static_cast<size_t>(t0 + 1) * (H * H + H) + e] = 0.f;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols) : "memory");
+}
+
+}  // namespace amg

@@ -19,16 +19,20 @@
 // Scheduling: the (pass, block) tasks of a chain are numbered on the host in
 // an order where every task comes after the tasks it depends on, each pass
 // trailing the previous one by `lag` blocks beyond its dependency front.
-// CTAs take task numbers from a global counter, so a task only ever waits
-// for tasks numbered before it, which CTAs that are already running hold:
-// the chain cannot deadlock whatever the number of resident CTAs.  A task
+// CTA c of the grid (no larger than the CTAs that fit on the GPU at once)
+// runs tasks c, c + grid, c + 2 grid, ... in that order, so a task only ever
+// waits for lower-numbered tasks, each of which its CTA reaches first: the
+// smallest unfinished task always has its inputs, and the chain cannot
+// deadlock.  Each task first issues the loads that depend on no other task
+// (row bounds, columns and values of its rows, and a_jj for the on-the-fly
+// values), then waits for the blocks it gathers from, then gathers.  A task
 // publishes its completion with a release store of the launch's epoch in a
 // per-(pass, block) flag; a dependent task polls the flags with acquire
 // loads.  Every wait is bounded: after kWfMaxPolls polls (or once another
 // wait has given up) the CTA records the failure in `err` and carries on,
 // so the kernel always ends and the host reports AMG_ERR_DEVICE_FLAG.
-// The last CTA to finish resets the task counter and advances the epoch,
-// so flags need no clearing between launches.
+// The last CTA to finish advances the epoch, so flags need no clearing
+// between launches.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -55,7 +59,7 @@ constexpr int kWfThreads = 256;
 #define AMG_WF_ITER 2
 #endif
 #ifndef AMG_WF_LAG_PCT
-#define AMG_WF_LAG_PCT 100
+#define AMG_WF_LAG_PCT 200
 #endif
 #ifndef AMG_WF_CTAS_PER_SM
 #define AMG_WF_CTAS_PER_SM 8
@@ -66,14 +70,14 @@ constexpr int kWfIter = AMG_WF_ITER;       // row-group passes of a CTA per task
 // earlier and have usually finished
 constexpr int kWfLagPct = AMG_WF_LAG_PCT;
 constexpr int kWfCtasPerSM = AMG_WF_CTAS_PER_SM;
-#ifndef AMG_WF_STATIC
-#define AMG_WF_STATIC 0
-#endif
 #ifndef AMG_WF_SLEEP_NS
 #define AMG_WF_SLEEP_NS 32
 #endif
 #ifndef AMG_WF_FENCE
 #define AMG_WF_FENCE 1
+#endif
+#ifndef AMG_WF_MINB
+#define AMG_WF_MINB 1
 #endif
 constexpr unsigned kWfMaxPolls = 1u << 20; // bounded dependency wait (with back-off: >= ~0.1 s)
 
@@ -90,10 +94,9 @@ template <class T> struct WfArgs {
     const T *pv = nullptr, *e = nullptr;   // prolongation P (n x n_c) and the coarse correction
     const T *b = nullptr;
     T *v[kWfBufs + 2] = {};         // chain buffers (n each), then two caller vectors
-    const int *lohi = nullptr;      // first and last block holding a column of block k's rows
-    const int *order = nullptr;     // ntask codes: pass << 24 | block
+    const int4 *task = nullptr;     // ntask descriptors: pass, block, first and last block it reads
     unsigned *flags = nullptr;      // kWfMaxPhases x nblk completion epochs
-    unsigned *ctrl = nullptr;       // [0] next task number, [1] CTAs finished, [2] epoch
+    unsigned *ctrl = nullptr;       // [1] CTAs finished, [2] epoch
     int *err = nullptr;             // set when a dependency wait gave up
 };
 
@@ -155,108 +158,142 @@ template <class T> struct WfCoef {
 // Row i of Q^-1 x with the values evaluated from A (Sec. 3.1):
 // q_ii = (d0 + d1 x + d2 x^2) / a_ii with x = a_ii / s,
 // q_ij = (o1 x + o2 x^2) / (a_ii + a_jj) with x = a_ij / s.
+// The first batch of the row's entries and their a_jj come prefetched.
+template <class T> __device__ __forceinline__ T qval(const WfCoef<T> &k, int row, int c, T a, T dii, T djj) {
+    const T s = a * k.inv_s;
+    return (c == row) ? wf_div(k.d0 + (k.d1 + k.d2 * s) * s, dii) : wf_div((k.o1 + k.o2 * s) * s, dii + djj);
+}
+
 template <int TPR, class T, class X>
-__device__ __forceinline__ T row_qfly(int lane, int row, int p0, int e, const int *__restrict__ col,
-                                      const T *__restrict__ a, const T *__restrict__ diag, const WfCoef<T> &k,
-                                      T dii, const X &xg) {
+__device__ __forceinline__ T row_qfly_pref(const RowBatch<T> &rb, const T (&dj)[4], int row, const int *__restrict__ col,
+                                           const T *__restrict__ a, const T *__restrict__ diag, const WfCoef<T> &k,
+                                           T dii, const X &xg) {
     T acc = T(0);
-    for (int base = p0 + lane; base < e; base += 4 * TPR) {
+    if (rb.base >= rb.e) return acc;
+    T x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = (rb.base + j * TPR < rb.e) ? xg(rb.c[j]) : T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (rb.base + j * TPR < rb.e) acc += qval(k, row, rb.c[j], rb.v[j], dii, dj[j]) * x[j];
+    for (int base = rb.base + 4 * TPR; base < rb.e; base += 4 * TPR) {
         int c[4];
-        T v[4];
+        T v[4], d[4], y[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int p = base + j * TPR;
-            c[j] = p < e ? __ldg(col + p) : row;
-            v[j] = p < e ? __ldg(a + p) : T(0);
-        }
-        T x[4], dj[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const bool live = base + j * TPR < e;
-            x[j] = live ? xg(c[j]) : T(0);
-            dj[j] = (live && c[j] != row) ? __ldg(diag + c[j]) : T(0);
+            c[j] = p < rb.e ? __ldg(col + p) : row;
+            v[j] = p < rb.e ? __ldg(a + p) : T(0);
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (base + j * TPR < e) {
-                const T s = v[j] * k.inv_s;
-                const T q = (c[j] == row) ? wf_div(k.d0 + (k.d1 + k.d2 * s) * s, dii)
-                                          : wf_div((k.o1 + k.o2 * s) * s, dii + dj[j]);
-                acc += q * x[j];
-            }
+            const bool live = base + j * TPR < rb.e;
+            y[j] = live ? xg(c[j]) : T(0);
+            d[j] = (live && c[j] != row) ? __ldg(diag + c[j]) : T(0);
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (base + j * TPR < rb.e) acc += qval(k, row, c[j], v[j], dii, d[j]) * y[j];
     }
     return acc;
 }
 
+// One task: pass `ph` of the chain on the rows of block `blk`, after the
+// previous pass has finished on blocks lo..hi.  Each thread takes kWfIter
+// rows (row groups of TPR lanes): their matrix loads are issued before the
+// wait, their gathers after it, and the stores once every row is summed.
 template <class T, int TPR, bool FLY>
-__device__ __forceinline__ void wf_run(const WfArgs<T> &A, int ph, int blk) {
+__device__ __forceinline__ void wf_task(const WfArgs<T> &A, const int4 d, unsigned target) {
     constexpr int RPB = kWfThreads / TPR;
+    const int ph = d.x, blk = d.y;
     const int lane = threadIdx.x % TPR;
     const int op = A.op[ph];
-    const T *in = A.v[A.in[ph]];
-    const T *aux = A.v[A.aux[ph]];
-    T *out = A.v[A.out[ph]];
+    const bool qpass = (op == kWfQApply || op == kWfQB);
+    const bool qfly = FLY && qpass;
+    const int *rp = A.rp, *col = A.col;
+    const T *val = (qpass && !FLY) ? A.q : A.a;
+    if (op == kWfProlong) {
+        rp = A.prp;
+        col = A.pcol;
+        val = A.pv;
+    }
     const int r0 = blk * A.brows;
     const int r1 = min(A.n, r0 + A.brows);
     WfCoef<T> k{};
-    if constexpr (FLY) {
-        if (op == kWfQApply || op == kWfQB)
-            k = WfCoef<T>{T(__ldg(A.coef)), T(__ldg(A.coef + 1)), T(__ldg(A.coef + 2)), T(__ldg(A.coef + 3)),
-                          T(__ldg(A.coef + 4)), T(__ldg(A.coef + 5))};
-    }
-    for (int base = r0; base < r1; base += RPB) {
-        const int row = base + threadIdx.x / TPR;
+    if (qfly)
+        k = WfCoef<T>{T(__ldg(A.coef)), T(__ldg(A.coef + 1)), T(__ldg(A.coef + 2)), T(__ldg(A.coef + 3)),
+                      T(__ldg(A.coef + 4)), T(__ldg(A.coef + 5))};
+    // 1. loads that depend on no other task
+    RowBatch<T> rb[kWfIter];
+    T dj[kWfIter][4], dii[kWfIter];
+#pragma unroll
+    for (int it = 0; it < kWfIter; ++it) {
+        const int row = r0 + it * RPB + static_cast<int>(threadIdx.x) / TPR;
         const bool live = row < r1;
-        T acc = T(0);
-        if (live) {
-            if (op == kWfProlong) {
-                acc = row_dot<TPR>(lane, __ldg(A.prp + row), __ldg(A.prp + row + 1), A.pcol, A.pv, Gather<T>{A.e});
-            } else {
-                const int p0 = __ldg(A.rp + row), pe = __ldg(A.rp + row + 1);
-                switch (op) {
-                    case kWfResid:
-                    case kWfJac:
-                        acc = row_dot<TPR>(lane, p0, pe, A.col, A.a, GatherCG<T>{in});
-                        break;
-                    case kWfJac12:
-                        acc = row_dot<TPR>(lane, p0, pe, A.col, A.a, JacBProd<T>{A.jac, A.b});
-                        break;
-                    case kWfQApply:
-                        if constexpr (FLY) acc = row_qfly<TPR>(lane, row, p0, pe, A.col, A.a, A.diag, k,
-                                                               __ldg(A.diag + row), GatherCG<T>{in});
-                        else acc = row_dot<TPR>(lane, p0, pe, A.col, A.q, GatherCG<T>{in});
-                        break;
-                    case kWfQB:
-                        if constexpr (FLY) acc = row_qfly<TPR>(lane, row, p0, pe, A.col, A.a, A.diag, k,
-                                                               __ldg(A.diag + row), Gather<T>{A.b});
-                        else acc = row_dot<TPR>(lane, p0, pe, A.col, A.q, Gather<T>{A.b});
-                        break;
-                    default:
-                        break;
-                }
+        row_prefetch<TPR>(rb[it], live, lane, rp, row, col, val);
+        dii[it] = T(1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dj[it][j] = T(0);
+        if (qfly && live) {
+            dii[it] = __ldg(A.diag + row);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (rb[it].base + j * TPR < rb[it].e && rb[it].c[j] != row) dj[it][j] = __ldg(A.diag + rb[it].c[j]);
+        }
+    }
+    // 2. the previous pass on the blocks this one gathers from
+    if (ph > 0 && threadIdx.x < 32) wf_wait(A.flags + static_cast<size_t>(ph - 1) * A.nblk, d.z, d.w, target, A.err);
+    __syncthreads();
+    // 3. gathers and sums of every row, then the stores
+    const T *in = A.v[A.in[ph]];
+    const T *aux = A.v[A.aux[ph]];
+    T *out = A.v[A.out[ph]];
+    T acc[kWfIter];
+#pragma unroll
+    for (int it = 0; it < kWfIter; ++it) {
+        const int row = r0 + it * RPB + static_cast<int>(threadIdx.x) / TPR;
+        T a = T(0);
+        if (row < r1) {
+            switch (op) {
+                case kWfResid:
+                case kWfJac: a = row_dot_pref<TPR>(rb[it], col, val, GatherCG<T>{in}); break;
+                case kWfJac12: a = row_dot_pref<TPR>(rb[it], col, val, JacBProd<T>{A.jac, A.b}); break;
+                case kWfProlong: a = row_dot_pref<TPR>(rb[it], col, val, Gather<T>{A.e}); break;
+                case kWfQApply:
+                    if constexpr (FLY) a = row_qfly_pref<TPR>(rb[it], dj[it], row, col, val, A.diag, k, dii[it], GatherCG<T>{in});
+                    else a = row_dot_pref<TPR>(rb[it], col, val, GatherCG<T>{in});
+                    break;
+                case kWfQB:
+                    if constexpr (FLY) a = row_qfly_pref<TPR>(rb[it], dj[it], row, col, val, A.diag, k, dii[it], Gather<T>{A.b});
+                    else a = row_dot_pref<TPR>(rb[it], col, val, Gather<T>{A.b});
+                    break;
+                default: break;
             }
         }
-        acc = group_sum<TPR>(acc);
-        if (live && lane == 0) {
+        acc[it] = group_sum<TPR>(a);
+    }
+#pragma unroll
+    for (int it = 0; it < kWfIter; ++it) {
+        const int row = r0 + it * RPB + static_cast<int>(threadIdx.x) / TPR;
+        if (row < r1 && lane == 0) {
             T r;
             switch (op) {
-                case kWfResid: r = __ldg(A.b + row) - acc; break;
-                case kWfQApply: r = __ldcg(aux + row) + acc; break;
-                case kWfQB: r = acc; break;
+                case kWfResid: r = __ldg(A.b + row) - acc[it]; break;
+                case kWfQApply: r = __ldcg(aux + row) + acc[it]; break;
+                case kWfQB: r = acc[it]; break;
                 case kWfJac: {
                     const T ui = __ldcg(in + row);
-                    r = ui + __ldg(A.jac + row) * (__ldg(A.b + row) - acc);
+                    r = ui + __ldg(A.jac + row) * (__ldg(A.b + row) - acc[it]);
                     break;
                 }
                 case kWfJac12: {
                     const T jr = __ldg(A.jac + row), br = __ldg(A.b + row);
                     const T u1 = jr * br;
-                    r = u1 + jr * (br - acc);
+                    r = u1 + jr * (br - acc[it]);
                     break;
                 }
                 case kWfJacZ: r = __ldg(A.jac + row) * __ldg(A.b + row); break;
-                case kWfProlong: r = __ldcg(in + row) + acc; break;
+                case kWfProlong: r = __ldcg(in + row) + acc[it]; break;
                 default: r = T(0); break;
             }
             out[row] = r;
@@ -265,34 +302,20 @@ __device__ __forceinline__ void wf_run(const WfArgs<T> &A, int ph, int blk) {
 }
 
 template <class T, int TPR, bool FLY>
-__global__ void __launch_bounds__(kWfThreads) k_wavefront(const WfArgs<T> A) {
-    __shared__ int s_next;
+__global__ void __launch_bounds__(kWfThreads, AMG_WF_MINB) k_wavefront(const WfArgs<T> A) {
     __shared__ unsigned s_target;
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (threadIdx.x == 0) {
-        s_target = ld_acquire_u32(A.ctrl + 2) + 1u;
-        s_next = AMG_WF_STATIC ? static_cast<int>(blockIdx.x) : atomicAdd(reinterpret_cast<int *>(A.ctrl), 1);
-    }
+    if (threadIdx.x == 0) s_target = ld_acquire_u32(A.ctrl + 2) + 1u;
     __syncthreads();
     const unsigned target = s_target;
-    int t = s_next;
-    while (t < A.ntask) {
-        __syncthreads();   // every thread has read s_next
-        if (threadIdx.x == 0)   // the next task, early
-            s_next = AMG_WF_STATIC ? t + static_cast<int>(gridDim.x) : atomicAdd(reinterpret_cast<int *>(A.ctrl), 1);
-        const int code = __ldg(A.order + t);
-        const int ph = code >> 24, blk = code & 0xffffff;
-        if (ph > 0 && threadIdx.x < 32)
-            wf_wait(A.flags + static_cast<size_t>(ph - 1) * A.nblk, __ldg(A.lohi + 2 * blk),
-                    __ldg(A.lohi + 2 * blk + 1), target, A.err);
-        __syncthreads();
-        wf_run<T, TPR, FLY>(A, ph, blk);
-        __syncthreads();
+    for (int t = blockIdx.x; t < A.ntask; t += gridDim.x) {
+        const int4 d = __ldg(A.task + t);
+        wf_task<T, TPR, FLY>(A, d, target);
+        __syncthreads();   // every row of the task is stored
         if (threadIdx.x == 0) {
             if (AMG_WF_FENCE) __threadfence();
-            st_release_u32(A.flags + static_cast<size_t>(ph) * A.nblk + blk, target);
+            st_release_u32(A.flags + static_cast<size_t>(d.x) * A.nblk + d.y, target);
         }
-        t = s_next;
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x == 0) {
@@ -300,7 +323,6 @@ __global__ void __launch_bounds__(kWfThreads) k_wavefront(const WfArgs<T> A) {
         const unsigned done = atomicAdd(A.ctrl + 1, 1u);
         if (done == gridDim.x - 1) {
             __threadfence();
-            *reinterpret_cast<volatile unsigned *>(A.ctrl) = 0u;
             *reinterpret_cast<volatile unsigned *>(A.ctrl + 1) = 0u;
             __threadfence();
             st_release_u32(A.ctrl + 2, target);
@@ -311,11 +333,11 @@ __global__ void __launch_bounds__(kWfThreads) k_wavefront(const WfArgs<T> A) {
 // Task order of an nphase-pass chain over nblk blocks: block k of pass p is
 // placed once pass p - 1 has been placed on blocks 0 .. H_k + lag, where
 // H_k = max_{k' <= k} hi_{k'} (so every block it reads from comes first).
-// Returns false if the order fails its own check (each task after the
-// tasks it waits on).
-inline bool wf_build_order(int nblk, const std::vector<int> &lohi, int nphase, int lag, std::vector<int> &order) {
-    order.clear();
-    if (nblk <= 0 || nphase <= 0 || nphase > kWfMaxPhases || nblk >= (1 << 24)) return false;
+// Writes one (pass, block, lo, hi) descriptor per task.  Returns false if
+// the order fails its own check (each task after the tasks it waits on).
+inline bool wf_build_order(int nblk, const std::vector<int> &lohi, int nphase, int lag, std::vector<int> &desc) {
+    desc.clear();
+    if (nblk <= 0 || nphase <= 0 || nphase > kWfMaxPhases) return false;
     std::vector<int> H(nblk);
     int m = 0;
     for (int k = 0; k < nblk; ++k) {
@@ -323,15 +345,17 @@ inline bool wf_build_order(int nblk, const std::vector<int> &lohi, int nphase, i
         H[k] = m;
     }
     std::vector<int> next(nphase, 0);
+    std::vector<int> order;
     order.reserve(static_cast<size_t>(nphase) * nblk);
+    auto code = [nblk](int p, int k) { return p * nblk + k; };
     while (next[nphase - 1] < nblk) {
-        if (next[0] < nblk) order.push_back(next[0]++);
+        if (next[0] < nblk) order.push_back(code(0, next[0]++));
         for (int p = 1; p < nphase; ++p) {
             while (next[p] < nblk) {
                 const int k = next[p];
                 const long long need = std::min<long long>(nblk, static_cast<long long>(H[k]) + 1 + lag);
                 if (next[p - 1] < need) break;
-                order.push_back((p << 24) | k);
+                order.push_back(code(p, k));
                 ++next[p];
             }
         }
@@ -339,18 +363,25 @@ inline bool wf_build_order(int nblk, const std::vector<int> &lohi, int nphase, i
     // check: position of every task after those of its dependencies
     std::vector<int> pos(static_cast<size_t>(nphase) * nblk, -1);
     for (size_t t = 0; t < order.size(); ++t) {
-        const int p = order[t] >> 24, k = order[t] & 0xffffff;
-        if (pos[static_cast<size_t>(p) * nblk + k] != -1) return false;
-        pos[static_cast<size_t>(p) * nblk + k] = static_cast<int>(t);
+        if (pos[order[t]] != -1) return false;
+        pos[order[t]] = static_cast<int>(t);
     }
     for (int p = 0; p < nphase; ++p)
         for (int k = 0; k < nblk; ++k) {
-            const int tk = pos[static_cast<size_t>(p) * nblk + k];
+            const int tk = pos[code(p, k)];
             if (tk < 0) return false;
             if (p == 0) continue;
             for (int j = lohi[2 * k]; j <= lohi[2 * k + 1]; ++j)
-                if (pos[static_cast<size_t>(p - 1) * nblk + j] > tk) return false;
+                if (pos[code(p - 1, j)] > tk) return false;
         }
+    desc.resize(4 * order.size());
+    for (size_t t = 0; t < order.size(); ++t) {
+        const int p = order[t] / nblk, k = order[t] % nblk;
+        desc[4 * t] = p;
+        desc[4 * t + 1] = k;
+        desc[4 * t + 2] = lohi[2 * k];
+        desc[4 * t + 3] = lohi[2 * k + 1];
+    }
     return true;
 }
 
