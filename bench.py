@@ -775,8 +775,21 @@ def run_kernel_only(args, wl):
             P.amg_destroy(c)
         return
     A = wl["matrix"]()
-    ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64)
+    wf = args.kernel_only in ("wf_pre", "wf_post")
+    ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64, fused_sweeps=1 if wf else 0)
     P.amg_setup(ctx, A)
+    if wf:
+        # the finest level's wavefront chain with the learned smoother
+        theta, _ = load_theta(wl.get("wide", False))
+        P.gnn_load_params(ctx, theta)
+        P.gnn_predict_coeffs(ctx)
+        kid = P.AMG_K_WF_PRE if args.kernel_only == "wf_pre" else P.AMG_K_WF_POST
+        b = P.amg_kernel_launch(ctx, kid, 0, args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": args.kernel_only, "workload": wl["workload"], "method_bytes_per_launch": b,
+                          "launches": args.steps}))
+        P.amg_destroy(ctx)
+        return
     if args.kernel_only == "step":
         # one bench step (GCIN inference + solve to 1e-8) after one untimed
         # step, for an ncu launch list of exactly one step

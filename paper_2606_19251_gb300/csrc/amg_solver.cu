@@ -1070,8 +1070,12 @@ static void L_outer(const DevMat &A, const double *b, const double *x, T *rT, do
 // ---------------------------------------------------------------------------
 // wavefront smoothing chains (wavefront.cuh) on levels too large for L2
 // ---------------------------------------------------------------------------
-constexpr int kWfMinBlocks = 64;   // smaller levels stay in L2 anyway: one kernel per pass
-constexpr int kWfMaxReach = 64;    // a block's columns reach at most this many blocks ahead
+#ifndef AMG_WF_MIN_NNZ
+#define AMG_WF_MIN_NNZ (1 << 20)
+#endif
+constexpr int kWfMinBlocks = 4096;   // smaller levels: one kernel per pass
+constexpr long long kWfMinNnz = AMG_WF_MIN_NNZ;
+constexpr int kWfMaxReach = 4096;    // a block's columns reach at most this many blocks ahead
 
 template <class T, int TPR, bool FLY>
 static int wf_occupancy() {
@@ -1099,8 +1103,8 @@ static int wf_blocks_per_sm(int tpr, bool fly) {
     }
 }
 
-// Which levels run their smoothing as wavefront chains, with the block
-// ranges of their columns and the task orders of every chain length.
+// Which levels run their smoothing as wavefront chains, with the group
+// ranges of their blocks' columns and the lag of every chain length.
 static int plan_wavefront(amg_ctx *c) {
     const int nlev = static_cast<int>(c->host.size());
     c->wfplan.assign(nlev, WfPlan{});
@@ -1111,45 +1115,29 @@ static int plan_wavefront(amg_ctx *c) {
         if (H.fast) continue;
         const int n = H.A.n_rows;
         const int tpr = pick_tpr(H.A.nnz(), n);
-        if (tpr > 4) continue;
-        const int brows = kWfIter * kWfThreads / tpr;
-        const int nblk = (n + brows - 1) / brows;
+        if (tpr > 4 || H.A.nnz() < kWfMinNnz) continue;
+        const int rpt = 32 / tpr;
+        const int nblk = (n + rpt - 1) / rpt;
         if (nblk < kWfMinBlocks) continue;
         WfPlan &W = c->wfplan[l];
-        W.lohi.assign(2 * static_cast<size_t>(nblk), 0);
-        int front = 0, reach = 0;
-        for (int k = 0; k < nblk; ++k) {
-            int lo = k, hi = k;
-            const int r1 = std::min(n, (k + 1) * brows);
-            for (int p = H.A.rp[k * brows]; p < H.A.rp[r1]; ++p) {
-                const int cb = H.A.col[p] / brows;
-                lo = std::min(lo, cb);
-                hi = std::max(hi, cb);
-            }
-            W.lohi[2 * k] = lo;
-            W.lohi[2 * k + 1] = hi;
-            front = std::max(front, hi);
-            reach = std::max(reach, front - k);
-        }
+        const int reach = wf_block_ranges(n, H.A.rp.data(), H.A.col.data(), rpt, W.lohi);
         if (reach > kWfMaxReach) {
             W = WfPlan{};
             continue;
         }
         W.grid = std::min(kWfCtasPerSM, f32 ? wf_blocks_per_sm<float>(tpr, true) : wf_blocks_per_sm<double>(tpr, false)) *
                  kNumSMs;
-        W.brows = brows;
-        W.nblk = nblk;
-        std::vector<int> desc;
-        bool ok = true;
-        W.off[1] = 0;
-        for (int np = 1; np <= kWfMaxPhases && ok; ++np) {
-            const int lag = static_cast<int>((static_cast<long long>(kWfLagPct) * W.grid + 100LL * np - 1) /
-                                             (100LL * np)) + 1;
-            ok = wf_build_order(nblk, W.lohi, np, lag, desc);
-            W.task.insert(W.task.end(), desc.begin(), desc.end());
-            W.off[np + 1] = static_cast<int>(W.task.size() / 4);
+        const long long warps = static_cast<long long>(W.grid) * (kWfThreads / 32);
+        for (int np = 1; np <= kWfMaxPhases; ++np) {
+            // a task's inputs were produced a grid of tasks earlier; and the lag
+            // exceeds a block's reach by a completion group (no task waits for
+            // a later-numbered one)
+            const long long by_grid = (static_cast<long long>(kWfLagPct) * warps + 100LL * np - 1) / (100LL * np);
+            W.lag[np] = static_cast<int>(std::max<long long>(by_grid, reach + kWfGroup + 1));
         }
-        if (!ok) return ctx_fail(c, "wavefront task order failed its dependency check"), AMG_ERR_ARG;
+        W.rpt = rpt;
+        W.nblk = nblk;
+        W.ngroup = (nblk + kWfGroup - 1) / kWfGroup;
         W.on = true;
     }
     return AMG_OK;
@@ -1206,7 +1194,9 @@ static WfChain<T> wf_chain_for(amg_ctx *c, int l, const T *b) {
     WfArgs<T> &a = ch.a;
     a.n = L.n;
     a.nblk = L.wf_nblk;
-    a.brows = L.wf_brows;
+    a.rpt = L.wf_rpt;
+    a.ngroup = L.wf_ngroup;
+    a.lohi = reinterpret_cast<const int2 *>(L.wf_lohi);
     a.rp = L.A.rp;
     a.col = L.A.col;
     a.a = mvals<T>(L.A);
@@ -1219,8 +1209,6 @@ static WfChain<T> wf_chain_for(amg_ctx *c, int l, const T *b) {
     a.pv = mvals<T>(L.P);
     a.b = b;
     for (int k = 0; k < kWfBufs; ++k) a.v[k] = reinterpret_cast<T *>(L.wf_buf + static_cast<size_t>(k) * L.n);
-    a.flags = L.wf_flags;
-    a.ctrl = L.wf_ctrl;
     a.err = c->dflag + 1;
     return ch;
 }
@@ -1231,11 +1219,13 @@ template <class T>
 static bool wf_launch(amg_ctx *c, int l, WfChain<T> &ch, cudaStream_t s) {
     DevLevel &L = c->lev[l];
     if (!ch.ok || ch.a.nphase < 1) return false;
-    const WfPlan &W = c->wfplan[l];
-    ch.a.ntask = W.off[ch.a.nphase + 1] - W.off[ch.a.nphase];
-    ch.a.task = reinterpret_cast<const int4 *>(L.wf_task) + W.off[ch.a.nphase];
+    const int P = ch.a.nphase;
+    ch.a.lag = L.wf_lag[P];
+    // counters of the chains of 1 .. P-1 passes come first: P (P - 1) / 2 groups' worth
+    ch.a.count = L.wf_count + static_cast<size_t>(P * (P - 1) / 2) * L.wf_ngroup;
+    ch.a.ctrl = L.wf_ctrl + 4 * P;
     const bool fly = std::is_same<T, float>::value && !c->q_nodes;
-    const int grid = std::max(1, std::min(L.wf_grid, ch.a.ntask));
+    const int grid = std::max(1, L.wf_grid);
     switch (L.A.tpr) {
         case 1: WfLaunch<T>::template go<1>(ch.a, grid, fly, s); break;
         case 2: WfLaunch<T>::template go<2>(ch.a, grid, fly, s); break;
@@ -1769,12 +1759,15 @@ static void layout(amg_ctx *c, Planner &pl) {
         const WfPlan &W = c->wfplan[l];
         L.wf = W.on;
         if (W.on) {
-            L.wf_brows = W.brows;
+            L.wf_rpt = W.rpt;
             L.wf_nblk = W.nblk;
+            L.wf_ngroup = W.ngroup;
             L.wf_grid = W.grid;
-            L.wf_task = pl.take<int>(W.task.size());
-            L.wf_flags = pl.take<unsigned>(static_cast<size_t>(kWfMaxPhases) * W.nblk);
-            L.wf_ctrl = pl.take<unsigned>(4);
+            std::copy(W.lag, W.lag + 9, L.wf_lag);
+            L.wf_lohi = pl.take<int>(W.lohi.size());
+            // counters of every chain length 1..8: (1 + 2 + ... + 8) x ngroup
+            L.wf_count = pl.take<unsigned>(static_cast<size_t>(kWfMaxPhases * (kWfMaxPhases + 1) / 2) * W.ngroup);
+            L.wf_ctrl = pl.take<unsigned>(4 * (kWfMaxPhases + 1));
             L.wf_buf = pl.take<double>(static_cast<size_t>(kWfBufs) * L.n);
             L.diag32 = pl.take<float>(L.n);
         }
@@ -1891,7 +1884,7 @@ static int upload(amg_ctx *c) {
         k_extract_diag<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag); AMG_COUNT();
         if (L.wf) {
             const WfPlan &W = c->wfplan[l];
-            CK(cudaMemcpyAsync(L.wf_task, W.task.data(), sizeof(int) * W.task.size(), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(L.wf_lohi, W.lohi.data(), sizeof(int) * W.lohi.size(), cudaMemcpyHostToDevice, s));
             launch_pdl(k_convert<double, float>, dim3(grid_for(L.n)), dim3(kBlock), 0, s, L.n,
                        static_cast<const double *>(L.diag), L.diag32);
         }

@@ -40,10 +40,11 @@ struct DevLevel {
     double *vw = nullptr;                      // w = M b of the current V-cycle
     // wavefront smoothing chains (levels too large for L2; wavefront.cuh)
     bool wf = false;
-    int wf_brows = 0, wf_nblk = 0, wf_grid = 0;
-    int *wf_task = nullptr;                    // task descriptors of 1..8-pass chains (4 ints each)
-    unsigned *wf_flags = nullptr;              // kWfMaxPhases x nblk completion epochs
-    unsigned *wf_ctrl = nullptr;               // finished CTAs, epoch
+    int wf_rpt = 0, wf_nblk = 0, wf_ngroup = 0, wf_grid = 0;
+    int wf_lag[9] = {};                        // lag (blocks) of a p-pass chain, p = 1..8
+    int *wf_lohi = nullptr;                    // per block: first and last group of its columns
+    unsigned *wf_count = nullptr;              // completed-task counters, p x ngroup for each p = 1..8
+    unsigned *wf_ctrl = nullptr;               // 4 words per chain length: finished warps, launch number
     double *wf_buf = nullptr;                  // kWfBufs chain vectors (n doubles of storage each)
     float *diag32 = nullptr;                   // a_ii in FP32 (pseudo-inverse values on the fly)
 };
@@ -51,10 +52,9 @@ struct DevLevel {
 // Host-side plan of a level's wavefront chains (built at upload).
 struct WfPlan {
     bool on = false;
-    int brows = 0, nblk = 0, grid = 0;
+    int rpt = 0, nblk = 0, ngroup = 0, grid = 0;
+    int lag[9] = {};
     std::vector<int> lohi;                     // 2 x nblk
-    std::vector<int> task;                     // descriptors of every chain length, back to back
-    int off[10] = {};                          // tasks off[p]..off[p+1]: a p-pass chain (p = 1..8)
 };
 
 enum : int { kRunning = 1, kStalled = 2 };

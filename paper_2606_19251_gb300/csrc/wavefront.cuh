@@ -16,23 +16,24 @@
 // from a_ij, a_ii, a_jj, s and the level's coefficients (Sec. 3.1), so a
 // pass of Q^-1 reads no stored values.
 //
-// Scheduling: the (pass, block) tasks of a chain are numbered on the host in
-// an order where every task comes after the tasks it depends on, each pass
-// trailing the previous one by `lag` blocks beyond its dependency front.
-// CTA c of the grid (no larger than the CTAs that fit on the GPU at once)
-// runs tasks c, c + grid, c + 2 grid, ... in that order, so a task only ever
-// waits for lower-numbered tasks, each of which its CTA reaches first: the
-// smallest unfinished task always has its inputs, and the chain cannot
-// deadlock.  Each task first issues the loads that depend on no other task
-// (row bounds, columns and values of its rows, and a_jj for the on-the-fly
-// values), then waits for the blocks it gathers from, then gathers.  A task
-// publishes its completion with a release store of the launch's epoch in a
-// per-(pass, block) flag; a dependent task polls the flags with acquire
-// loads.  Every wait is bounded: after kWfMaxPolls polls (or once another
-// wait has given up) the CTA records the failure in `err` and carries on,
-// so the kernel always ends and the host reports AMG_ERR_DEVICE_FLAG.
-// The last CTA to finish advances the epoch, so flags need no clearing
-// between launches.
+// Scheduling: a task is one warp's rows (32 / TPR rows) of one pass.  Tasks
+// are numbered round by round: round r holds block r of pass 0, block r - L
+// of pass 1, ..., block r - (P - 1) L of pass P - 1, with the lag L (in
+// blocks) larger than the distance from a block to the last block its
+// columns reach.  So a task only ever waits for lower-numbered tasks.  Warp
+// w of the grid (no larger than the warps that fit on the GPU at once) runs
+// tasks w, w + W, w + 2 W, ... in that order, so the smallest unfinished task
+// always has its inputs and the chain cannot deadlock; with L x P about the
+// number of warps, the tasks a task waits for were started a whole grid of
+// tasks earlier.  Completion is counted per (pass, group of kWfGroup
+// blocks): a finished task adds one to its group's counter with a release
+// fence; a dependent task polls the counters of the groups its columns fall
+// in with acquire loads until they reach launch number x tasks in the group
+// (counters only grow, one set per chain length, so nothing is cleared
+// between launches).  Every wait is bounded: after kWfMaxPolls polls (or
+// once another wait has given up) the warp records the failure in `err` and
+// carries on, so the kernel always ends and the host reports
+// AMG_ERR_DEVICE_FLAG.  The last warp to finish advances the launch number.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -54,35 +55,21 @@ enum WfOp : int {
 
 constexpr int kWfMaxPhases = 8;
 constexpr int kWfBufs = 8;                 // level-owned chain buffers
-constexpr int kWfThreads = 256;
-#ifndef AMG_WF_ITER
-#define AMG_WF_ITER 2
-#endif
+constexpr int kWfThreads = 256;            // 8 warps per CTA, each an independent worker
+constexpr int kWfGroup = 16;               // blocks (warp tasks) per completion counter
 #ifndef AMG_WF_LAG_PCT
-#define AMG_WF_LAG_PCT 200
+#define AMG_WF_LAG_PCT 100
 #endif
 #ifndef AMG_WF_CTAS_PER_SM
 #define AMG_WF_CTAS_PER_SM 8
 #endif
-constexpr int kWfIter = AMG_WF_ITER;       // row-group passes of a CTA per task
-// each pass trails the previous one by kWfLagPct % of a grid's worth of
-// tasks, so the tasks a task waits for were taken about a grid turnover
-// earlier and have usually finished
+// the passes trail each other by this percentage of a grid of warps' tasks
 constexpr int kWfLagPct = AMG_WF_LAG_PCT;
 constexpr int kWfCtasPerSM = AMG_WF_CTAS_PER_SM;
-#ifndef AMG_WF_SLEEP_NS
-#define AMG_WF_SLEEP_NS 32
-#endif
-#ifndef AMG_WF_FENCE
-#define AMG_WF_FENCE 1
-#endif
-#ifndef AMG_WF_MINB
-#define AMG_WF_MINB 1
-#endif
 constexpr unsigned kWfMaxPolls = 1u << 20; // bounded dependency wait (with back-off: >= ~0.1 s)
 
 template <class T> struct WfArgs {
-    int n = 0, nblk = 0, brows = 0, ntask = 0, nphase = 0;
+    int n = 0, nblk = 0, rpt = 0, nphase = 0, lag = 0, ngroup = 0;
     int op[kWfMaxPhases] = {}, in[kWfMaxPhases] = {}, aux[kWfMaxPhases] = {}, out[kWfMaxPhases] = {};
     const int *rp = nullptr, *col = nullptr;
     const T *a = nullptr;
@@ -94,9 +81,9 @@ template <class T> struct WfArgs {
     const T *pv = nullptr, *e = nullptr;   // prolongation P (n x n_c) and the coarse correction
     const T *b = nullptr;
     T *v[kWfBufs + 2] = {};         // chain buffers (n each), then two caller vectors
-    const int4 *task = nullptr;     // ntask descriptors: pass, block, first and last block it reads
-    unsigned *flags = nullptr;      // kWfMaxPhases x nblk completion epochs
-    unsigned *ctrl = nullptr;       // [1] CTAs finished, [2] epoch
+    const int2 *lohi = nullptr;     // per block: first and last group its rows' columns fall in
+    unsigned *count = nullptr;      // nphase x ngroup completed-task counters of this chain length
+    unsigned *ctrl = nullptr;       // [1] warps finished, [2] launch number of this chain length
     int *err = nullptr;             // set when a dependency wait gave up
 };
 
@@ -126,15 +113,18 @@ template <class T> struct JacBProd {   // gathered j_j b_j
     __device__ __forceinline__ T operator()(int j) const { return __ldg(jac + j) * __ldg(b + j); }
 };
 
-// Warp 0 waits until pass `ph` is complete (flag == target) on blocks lo..hi.
-__device__ __forceinline__ void wf_wait(const unsigned *f, int lo, int hi, unsigned target, int *err) {
+// The warp waits until every task of the previous pass in groups lo..hi is
+// done: counter >= launch number x tasks in the group.
+__device__ __forceinline__ void wf_wait(const unsigned *cnt, int lo, int hi, int nblk, unsigned target, int *err) {
     const int lane = threadIdx.x & 31;
     for (int base = lo; base <= hi; base += 32) {
-        const int k = base + lane;
-        bool ok = k > hi;
+        const int g = base + lane;
+        const bool mine = g <= hi;
+        const unsigned need = mine ? target * static_cast<unsigned>(min(kWfGroup, nblk - g * kWfGroup)) : 0u;
+        bool ok = !mine;
         unsigned polls = 0;
         while (true) {
-            if (!ok) ok = ld_acquire_u32(f + k) == target;
+            if (!ok) ok = ld_acquire_u32(cnt + g) >= need;
             if (__all_sync(0xffffffffu, ok)) break;
             // every lane takes the same decision (the flag read may differ by lane)
             const bool give_up = ++polls > kWfMaxPolls || ld_volatile_i32(err) != 0;
@@ -142,7 +132,7 @@ __device__ __forceinline__ void wf_wait(const unsigned *f, int lo, int hi, unsig
                 if (lane == 0) atomicOr(err, 1);
                 return;
             }
-            if (AMG_WF_SLEEP_NS > 0) __nanosleep(polls < 64 ? AMG_WF_SLEEP_NS : 8 * AMG_WF_SLEEP_NS);
+            if (polls > 8) __nanosleep(polls < 64 ? 32 : 256);
         }
     }
 }
@@ -198,15 +188,15 @@ __device__ __forceinline__ T row_qfly_pref(const RowBatch<T> &rb, const T (&dj)[
     return acc;
 }
 
-// One task: pass `ph` of the chain on the rows of block `blk`, after the
-// previous pass has finished on blocks lo..hi.  Each thread takes kWfIter
-// rows (row groups of TPR lanes): their matrix loads are issued before the
-// wait, their gathers after it, and the stores once every row is summed.
+// One task: pass `ph` on the rows of block `blk` (one warp, 32 / TPR rows):
+// the loads that depend on no other task (row bounds, the first batch of
+// columns and values, a_jj for the on-the-fly values), then the wait for the
+// previous pass on the groups the block's columns fall in, then the gathers,
+// the sums and the stores.
 template <class T, int TPR, bool FLY>
-__device__ __forceinline__ void wf_task(const WfArgs<T> &A, const int4 d, unsigned target) {
-    constexpr int RPB = kWfThreads / TPR;
-    const int ph = d.x, blk = d.y;
-    const int lane = threadIdx.x % TPR;
+__device__ __forceinline__ void wf_task(const WfArgs<T> &A, int ph, int blk, unsigned target) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % TPR;
     const int op = A.op[ph];
     const bool qpass = (op == kWfQApply || op == kWfQB);
     const bool qfly = FLY && qpass;
@@ -217,111 +207,99 @@ __device__ __forceinline__ void wf_task(const WfArgs<T> &A, const int4 d, unsign
         col = A.pcol;
         val = A.pv;
     }
-    const int r0 = blk * A.brows;
-    const int r1 = min(A.n, r0 + A.brows);
+    const int row = blk * A.rpt + lane / TPR;
+    const bool live = row < A.n;
+    const int2 lh = __ldg(A.lohi + blk);
+    RowBatch<T> rb;
+    row_prefetch<TPR>(rb, live, sub, rp, row, col, val);
+    T dj[4] = {T(0), T(0), T(0), T(0)};
+    T dii = T(1);
     WfCoef<T> k{};
-    if (qfly)
+    if (qfly) {
         k = WfCoef<T>{T(__ldg(A.coef)), T(__ldg(A.coef + 1)), T(__ldg(A.coef + 2)), T(__ldg(A.coef + 3)),
                       T(__ldg(A.coef + 4)), T(__ldg(A.coef + 5))};
-    // 1. loads that depend on no other task
-    RowBatch<T> rb[kWfIter];
-    T dj[kWfIter][4], dii[kWfIter];
-#pragma unroll
-    for (int it = 0; it < kWfIter; ++it) {
-        const int row = r0 + it * RPB + static_cast<int>(threadIdx.x) / TPR;
-        const bool live = row < r1;
-        row_prefetch<TPR>(rb[it], live, lane, rp, row, col, val);
-        dii[it] = T(1);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dj[it][j] = T(0);
-        if (qfly && live) {
-            dii[it] = __ldg(A.diag + row);
+        if (live) {
+            dii = __ldg(A.diag + row);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (rb[it].base + j * TPR < rb[it].e && rb[it].c[j] != row) dj[it][j] = __ldg(A.diag + rb[it].c[j]);
+                if (rb.base + j * TPR < rb.e && rb.c[j] != row) dj[j] = __ldg(A.diag + rb.c[j]);
         }
     }
-    // 2. the previous pass on the blocks this one gathers from
-    if (ph > 0 && threadIdx.x < 32) wf_wait(A.flags + static_cast<size_t>(ph - 1) * A.nblk, d.z, d.w, target, A.err);
-    __syncthreads();
-    // 3. gathers and sums of every row, then the stores
+    if (ph > 0) wf_wait(A.count + static_cast<size_t>(ph - 1) * A.ngroup, lh.x, lh.y, A.nblk, target, A.err);
     const T *in = A.v[A.in[ph]];
     const T *aux = A.v[A.aux[ph]];
     T *out = A.v[A.out[ph]];
-    T acc[kWfIter];
-#pragma unroll
-    for (int it = 0; it < kWfIter; ++it) {
-        const int row = r0 + it * RPB + static_cast<int>(threadIdx.x) / TPR;
-        T a = T(0);
-        if (row < r1) {
-            switch (op) {
-                case kWfResid:
-                case kWfJac: a = row_dot_pref<TPR>(rb[it], col, val, GatherCG<T>{in}); break;
-                case kWfJac12: a = row_dot_pref<TPR>(rb[it], col, val, JacBProd<T>{A.jac, A.b}); break;
-                case kWfProlong: a = row_dot_pref<TPR>(rb[it], col, val, Gather<T>{A.e}); break;
-                case kWfQApply:
-                    if constexpr (FLY) a = row_qfly_pref<TPR>(rb[it], dj[it], row, col, val, A.diag, k, dii[it], GatherCG<T>{in});
-                    else a = row_dot_pref<TPR>(rb[it], col, val, GatherCG<T>{in});
-                    break;
-                case kWfQB:
-                    if constexpr (FLY) a = row_qfly_pref<TPR>(rb[it], dj[it], row, col, val, A.diag, k, dii[it], Gather<T>{A.b});
-                    else a = row_dot_pref<TPR>(rb[it], col, val, Gather<T>{A.b});
-                    break;
-                default: break;
-            }
+    T acc = T(0);
+    if (live) {
+        switch (op) {
+            case kWfResid:
+            case kWfJac: acc = row_dot_pref<TPR>(rb, col, val, GatherCG<T>{in}); break;
+            case kWfJac12: acc = row_dot_pref<TPR>(rb, col, val, JacBProd<T>{A.jac, A.b}); break;
+            case kWfProlong: acc = row_dot_pref<TPR>(rb, col, val, Gather<T>{A.e}); break;
+            case kWfQApply:
+                if constexpr (FLY) acc = row_qfly_pref<TPR>(rb, dj, row, col, val, A.diag, k, dii, GatherCG<T>{in});
+                else acc = row_dot_pref<TPR>(rb, col, val, GatherCG<T>{in});
+                break;
+            case kWfQB:
+                if constexpr (FLY) acc = row_qfly_pref<TPR>(rb, dj, row, col, val, A.diag, k, dii, Gather<T>{A.b});
+                else acc = row_dot_pref<TPR>(rb, col, val, Gather<T>{A.b});
+                break;
+            default: break;
         }
-        acc[it] = group_sum<TPR>(a);
     }
-#pragma unroll
-    for (int it = 0; it < kWfIter; ++it) {
-        const int row = r0 + it * RPB + static_cast<int>(threadIdx.x) / TPR;
-        if (row < r1 && lane == 0) {
-            T r;
-            switch (op) {
-                case kWfResid: r = __ldg(A.b + row) - acc[it]; break;
-                case kWfQApply: r = __ldcg(aux + row) + acc[it]; break;
-                case kWfQB: r = acc[it]; break;
-                case kWfJac: {
-                    const T ui = __ldcg(in + row);
-                    r = ui + __ldg(A.jac + row) * (__ldg(A.b + row) - acc[it]);
-                    break;
-                }
-                case kWfJac12: {
-                    const T jr = __ldg(A.jac + row), br = __ldg(A.b + row);
-                    const T u1 = jr * br;
-                    r = u1 + jr * (br - acc[it]);
-                    break;
-                }
-                case kWfJacZ: r = __ldg(A.jac + row) * __ldg(A.b + row); break;
-                case kWfProlong: r = __ldcg(in + row) + acc[it]; break;
-                default: r = T(0); break;
+    acc = group_sum<TPR>(acc);
+    if (live && sub == 0) {
+        T r;
+        switch (op) {
+            case kWfResid: r = __ldg(A.b + row) - acc; break;
+            case kWfQApply: r = __ldcg(aux + row) + acc; break;
+            case kWfQB: r = acc; break;
+            case kWfJac: {
+                const T ui = __ldcg(in + row);
+                r = ui + __ldg(A.jac + row) * (__ldg(A.b + row) - acc);
+                break;
             }
-            out[row] = r;
+            case kWfJac12: {
+                const T jr = __ldg(A.jac + row), br = __ldg(A.b + row);
+                const T u1 = jr * br;
+                r = u1 + jr * (br - acc);
+                break;
+            }
+            case kWfJacZ: r = __ldg(A.jac + row) * __ldg(A.b + row); break;
+            case kWfProlong: r = __ldcg(in + row) + acc; break;
+            default: r = T(0); break;
         }
+        out[row] = r;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        atomicAdd(A.count + static_cast<size_t>(ph) * A.ngroup + blk / kWfGroup, 1u);
     }
 }
 
 template <class T, int TPR, bool FLY>
-__global__ void __launch_bounds__(kWfThreads, AMG_WF_MINB) k_wavefront(const WfArgs<T> A) {
-    __shared__ unsigned s_target;
+__global__ void __launch_bounds__(kWfThreads) k_wavefront(const WfArgs<T> A) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (threadIdx.x == 0) s_target = ld_acquire_u32(A.ctrl + 2) + 1u;
-    __syncthreads();
-    const unsigned target = s_target;
-    for (int t = blockIdx.x; t < A.ntask; t += gridDim.x) {
-        const int4 d = __ldg(A.task + t);
-        wf_task<T, TPR, FLY>(A, d, target);
-        __syncthreads();   // every row of the task is stored
-        if (threadIdx.x == 0) {
-            if (AMG_WF_FENCE) __threadfence();
-            st_release_u32(A.flags + static_cast<size_t>(d.x) * A.nblk + d.y, target);
-        }
+    const int lane = threadIdx.x & 31;
+    const int nw = static_cast<int>(gridDim.x) * (kWfThreads / 32);
+    const int w = static_cast<int>(blockIdx.x) * (kWfThreads / 32) + static_cast<int>(threadIdx.x >> 5);
+    unsigned target = 0;
+    if (lane == 0) target = ld_acquire_u32(A.ctrl + 2) + 1u;
+    target = __shfl_sync(0xffffffffu, target, 0);
+    const int P = A.nphase;
+    const long long ntick = static_cast<long long>(A.nblk + (P - 1) * A.lag) * P;
+    for (long long t = w; t < ntick; t += nw) {
+        const int ph = static_cast<int>(t % P);
+        const long long blk = t / P - static_cast<long long>(ph) * A.lag;
+        if (blk < 0 || blk >= A.nblk) continue;   // warp-uniform: the pipeline's fill and drain
+        wf_task<T, TPR, FLY>(A, ph, static_cast<int>(blk), target);
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         __threadfence();
         const unsigned done = atomicAdd(A.ctrl + 1, 1u);
-        if (done == gridDim.x - 1) {
+        if (done == static_cast<unsigned>(nw) - 1u) {
             __threadfence();
             *reinterpret_cast<volatile unsigned *>(A.ctrl + 1) = 0u;
             __threadfence();
@@ -330,59 +308,26 @@ __global__ void __launch_bounds__(kWfThreads, AMG_WF_MINB) k_wavefront(const WfA
     }
 }
 
-// Task order of an nphase-pass chain over nblk blocks: block k of pass p is
-// placed once pass p - 1 has been placed on blocks 0 .. H_k + lag, where
-// H_k = max_{k' <= k} hi_{k'} (so every block it reads from comes first).
-// Writes one (pass, block, lo, hi) descriptor per task.  Returns false if
-// the order fails its own check (each task after the tasks it waits on).
-inline bool wf_build_order(int nblk, const std::vector<int> &lohi, int nphase, int lag, std::vector<int> &desc) {
-    desc.clear();
-    if (nblk <= 0 || nphase <= 0 || nphase > kWfMaxPhases) return false;
-    std::vector<int> H(nblk);
-    int m = 0;
+// The group range of each block's columns (own group included) and the
+// largest distance, in blocks, from a block to the last block its columns
+// reach.
+inline int wf_block_ranges(int n, const int *rp, const int *col, int rpt, std::vector<int> &lohi) {
+    const int nblk = (n + rpt - 1) / rpt;
+    lohi.assign(2 * static_cast<size_t>(nblk), 0);
+    int reach = 0;
     for (int k = 0; k < nblk; ++k) {
-        m = std::max(m, lohi[2 * k + 1]);
-        H[k] = m;
-    }
-    std::vector<int> next(nphase, 0);
-    std::vector<int> order;
-    order.reserve(static_cast<size_t>(nphase) * nblk);
-    auto code = [nblk](int p, int k) { return p * nblk + k; };
-    while (next[nphase - 1] < nblk) {
-        if (next[0] < nblk) order.push_back(code(0, next[0]++));
-        for (int p = 1; p < nphase; ++p) {
-            while (next[p] < nblk) {
-                const int k = next[p];
-                const long long need = std::min<long long>(nblk, static_cast<long long>(H[k]) + 1 + lag);
-                if (next[p - 1] < need) break;
-                order.push_back(code(p, k));
-                ++next[p];
-            }
+        int lo = k, hi = k;
+        const int r1 = std::min(n, (k + 1) * rpt);
+        for (int p = rp[k * rpt]; p < rp[r1]; ++p) {
+            const int cb = col[p] / rpt;
+            lo = std::min(lo, cb);
+            hi = std::max(hi, cb);
         }
+        reach = std::max(reach, hi - k);
+        lohi[2 * k] = lo / kWfGroup;
+        lohi[2 * k + 1] = hi / kWfGroup;
     }
-    // check: position of every task after those of its dependencies
-    std::vector<int> pos(static_cast<size_t>(nphase) * nblk, -1);
-    for (size_t t = 0; t < order.size(); ++t) {
-        if (pos[order[t]] != -1) return false;
-        pos[order[t]] = static_cast<int>(t);
-    }
-    for (int p = 0; p < nphase; ++p)
-        for (int k = 0; k < nblk; ++k) {
-            const int tk = pos[code(p, k)];
-            if (tk < 0) return false;
-            if (p == 0) continue;
-            for (int j = lohi[2 * k]; j <= lohi[2 * k + 1]; ++j)
-                if (pos[code(p - 1, j)] > tk) return false;
-        }
-    desc.resize(4 * order.size());
-    for (size_t t = 0; t < order.size(); ++t) {
-        const int p = order[t] / nblk, k = order[t] % nblk;
-        desc[4 * t] = p;
-        desc[4 * t + 1] = k;
-        desc[4 * t + 2] = lohi[2 * k];
-        desc[4 * t + 3] = lohi[2 * k + 1];
-    }
-    return true;
+    return reach;
 }
 
 }  // namespace amg
