@@ -587,10 +587,59 @@ def run_gpu(args, wl, rank, world):
             "clocks": {k2: v for k2, v in clocks.items()},
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         }
+        if wl["workload"] == "band-delaunay-fv-2.5M":
+            line["c2_graded_50k"] = small_mesh_summary(P, dev, flush, stream, K, Wm)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline_sample(P, ctx, theta, wl, use_gnn, statistics.mean(cyc_gnn))
         print(json.dumps(line), flush=True)
     P.amg_destroy(ctx)
+
+
+def small_mesh_summary(P, dev, flush, stream, K, Wm):
+    """The same step on the 50k-point graded mesh (L2-resident; network
+    trained on the C3 batch), reported beside the headline."""
+    import torch
+    A = W.c2_matrix(0)
+    n = A.n_rows
+    theta, _ = load_theta(False)
+    ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev)
+    P.amg_setup(ctx, A)
+    P.gnn_load_params(ctx, theta)
+    P.gnn_predict_coeffs(ctx)
+    rhs = [torch.tensor(W.rhs_zero_mean(1000 + k, n), device=f"cuda:{dev}") for k in range(Wm + K)]
+    _, kept = P.amg_reroute(ctx, rhs[0].cpu().numpy(), 30)
+    use_gnn = kept == P.AMG_SMOOTHER_GNN
+    x = torch.zeros(n, dtype=torch.float64, device=f"cuda:{dev}")
+
+    def run(step, ks):
+        out = []
+        for k in ks:
+            flush.fill_(float(k))
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, hist = step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append((e0.elapsed_time(e1), len(hist) - 1, st))
+        return out
+
+    def gnn(k):
+        if use_gnn:
+            P.gnn_predict_coeffs(ctx)
+        return P.amg_solve_device(ctx, rhs[k], x, TOL)
+
+    run(gnn, range(Wm))
+    g = run(gnn, range(Wm, Wm + K))
+    P.amg_set_jacobi(ctx)
+    run(lambda k: P.amg_solve_device(ctx, rhs[k], x, TOL), range(Wm))
+    j = run(lambda k: P.amg_solve_device(ctx, rhs[k], x, TOL), range(Wm, Wm + K))
+    P.amg_destroy(ctx)
+    return {"n": n, "nnz": A.nnz, "kept_gnn": use_gnn,
+            "gnn_step_ms": statistics.mean(v[0] for v in g), "vcycles_gnn": statistics.mean(v[1] for v in g),
+            "jacobi_solve_ms": statistics.mean(v[0] for v in j), "vcycles_jacobi": statistics.mean(v[1] for v in j),
+            "status": sorted(set(v[2] for v in g) | set(v[2] for v in j))}
 
 
 def cpu_baseline_sample(P, ctx, theta, wl, use_gnn, n_cycles, sample_cycles=2):
@@ -627,11 +676,27 @@ def cpu_baseline_sample(P, ctx, theta, wl, use_gnn, n_cycles, sample_cycles=2):
     res = O.solve(h, f, tol=1e-8, max_iter=sample_cycles)
     t_cyc = (time.perf_counter() - t0) / max(1, res.n_vcycles)
     ms = (t_inf + t_cyc * n_cycles) * 1e3
-    return {"value": ms, "unit": "ms", "cores": torch.get_num_threads(), "kind": "oracle",
+    # one V-cycle iteration again on a single thread (the same arithmetic)
+    nthr = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        res1 = O.solve(h, f, tol=1e-8, max_iter=1)
+        t_cyc1 = (time.perf_counter() - t0) / max(1, res1.n_vcycles)
+    finally:
+        torch.set_num_threads(nthr)
+    return {"value": ms, "unit": "ms", "cores": nthr, "kind": "oracle",
             "sample": f"oracle GCIN inference over all {len(levels)} level graphs ({t_inf:.1f} s) + "
                       f"{res.n_vcycles} FP64 V-cycle iterations ({t_cyc:.2f} s each) on the same hierarchy and "
                       f"right-hand side, scaled to the GPU solve's {n_cycles:.1f} V-cycles",
-            "cpu_model": _cpu_model()}
+            "single_thread": {"s_per_vcycle_iteration": t_cyc1, "s_per_vcycle_iteration_all_cores": t_cyc,
+                              "solve_vcycles_only_ms": t_cyc1 * n_cycles * 1e3},
+            "nproc": os.cpu_count(), "cpu_model": _cpu_model()}
+
+
+# Arm CPU part numbers (implementer 0x41) of the host cores this may run on
+_ARM_PARTS = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+              "0xd49": "Arm Neoverse-N2", "0xd8f": "Arm Neoverse-V3"}
 
 
 def _cpu_model():
@@ -639,8 +704,11 @@ def _cpu_model():
         with open("/proc/cpuinfo") as f:
             for ln in f:
                 low = ln.lower()
-                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                if low.startswith("model name") or low.startswith("hardware"):
                     return ln.split(":", 1)[1].strip()
+                if low.startswith("cpu part"):
+                    part = ln.split(":", 1)[1].strip()
+                    return f"{_ARM_PARTS.get(part, 'Arm')} (CPU part {part})"
     except OSError:
         pass
     import platform
