@@ -731,7 +731,7 @@ __global__ void k_max_final(const double *__restrict__ partial, int np, double *
 __global__ void k_pinv_basis(int n, const int *__restrict__ rp, const int *__restrict__ col,
                              const double *__restrict__ a, const double *__restrict__ d,
                              const double *__restrict__ s_ptr, double *__restrict__ bx, double *__restrict__ bw,
-                             unsigned char *__restrict__ isd) {
+                             unsigned char *__restrict__ isd, float *__restrict__ bx32, float *__restrict__ bw32) {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= n) return;
     const double s = *s_ptr, di = d[i];
@@ -740,6 +740,8 @@ __global__ void k_pinv_basis(int n, const int *__restrict__ rp, const int *__res
         bx[p] = a[p] / s;
         bw[p] = 1.0 / (j == i ? di : di + d[j]);
         isd[p] = (j == i) ? 1 : 0;
+        bx32[p] = static_cast<float>(bx[p]);
+        bw32[p] = static_cast<float>(bw[p]);
     }
 }
 
@@ -796,25 +798,37 @@ struct AsmQ {
     long long start[kAsmMaxLevels + 1];       // cumulative entries; start[nlev] = total
     const unsigned char *isd[kAsmMaxLevels];
     const double *bx[kAsmMaxLevels], *bw[kAsmMaxLevels];
+    const float *bx32[kAsmMaxLevels], *bw32[kAsmMaxLevels];
     double *q64[kAsmMaxLevels];
     float *q32[kAsmMaxLevels];
     int row[kAsmMaxLevels];                   // coefficient row of the level
 };
 
-__global__ void k_assemble_q_all(AsmQ L, const float *__restrict__ dc) {
+// mode 0: the FP32 V-cycle's values only, in FP32 from the FP32 basis (the
+// FP64 values are assembled when something asks for them); mode 1: both from
+// the FP64 product; mode 2: the FP64 values only. Coefficient row l starts at
+// dc + cstride * l.
+__global__ void k_assemble_q_all(AsmQ L, const float *__restrict__ dc, int cstride, int mode) {
     const long long p = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
     if (p >= L.start[L.nlev]) return;
     int l = 0;
     while (p >= L.start[l + 1]) ++l;
     const long long e = p - L.start[l];
-    const float *cf = dc + 5 * L.row[l];
+    const float *cf = dc + cstride * L.row[l];
+    if (mode == 0) {
+        const float x = L.bx32[l][e];
+        const float f = L.isd[l][e] ? __fadd_rn(__fadd_rn(cf[0], __fmul_rn(cf[1], x)), __fmul_rn(__fmul_rn(cf[2], x), x))
+                                    : __fadd_rn(__fmul_rn(cf[3], x), __fmul_rn(__fmul_rn(cf[4], x), x));
+        L.q32[l][e] = __fmul_rn(f, L.bw32[l][e]);
+        return;
+    }
     const double c0 = cf[0], c1 = cf[1], c2 = cf[2], c3 = cf[3], c4 = cf[4];
     const double x = L.bx[l][e];
     const double f = L.isd[l][e] ? __dadd_rn(__dadd_rn(c0, __dmul_rn(c1, x)), __dmul_rn(__dmul_rn(c2, x), x))
                                  : __dadd_rn(__dmul_rn(c3, x), __dmul_rn(__dmul_rn(c4, x), x));
     const double q = __dmul_rn(f, L.bw[l][e]);
     L.q64[l][e] = q;
-    L.q32[l][e] = static_cast<float>(q);
+    if (mode == 1) L.q32[l][e] = static_cast<float>(q);
 }
 
 struct AsmMA {
@@ -1742,6 +1756,8 @@ static void layout(amg_ctx *c, Planner &pl) {
         L.bx = pl.take<double>(std::max(1, L.A.nnz));
         L.isd = pl.take<unsigned char>(std::max(1, L.A.nnz));
         L.bw = pl.take<double>(std::max(1, L.A.nnz));
+        L.bx32 = pl.take<float>(std::max(1, L.A.nnz));
+        L.bw32 = pl.take<float>(std::max(1, L.A.nnz));
         L.q64 = pl.take<double>(std::max(1, L.A.nnz));
         L.q32 = pl.take<float>(std::max(1, L.A.nnz));
         L.j64 = pl.take<double>(L.n);
@@ -1894,7 +1910,7 @@ static int upload(amg_ctx *c) {
         k_jacobi_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, c->opt.omega, L.j64, L.j32); AMG_COUNT();
         k_dinv_vals<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.diag, L.dinv64, L.dinv32); AMG_COUNT();
         k_pinv_basis<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.v64, L.diag, c->scal + l, L.bx,
-                                                      L.bw, L.isd); AMG_COUNT();
+                                                      L.bw, L.isd, L.bx32, L.bw32); AMG_COUNT();
     }
     c->jac_omega = c->opt.omega;
     CK(cudaMemcpyAsync(c->ell_ptr, c->h_ell_ptr.data(), sizeof(int) * c->h_ell_ptr.size(), cudaMemcpyHostToDevice, s));
@@ -2185,22 +2201,35 @@ namespace amg {
 // coefficients in device memory (G x 5 FP32, level order) without a host
 // round trip; the caller validates the coefficients after its own
 // synchronisation and selects the smoother.
-int enqueue_coeff_assembly(amg_ctx *c, const float *d_coef, cudaStream_t s) {
-    const int nlev = static_cast<int>(c->lev.size());
-    if (nlev - 1 > kAsmMaxLevels) return ctx_fail(c, "too many levels for the batched assembly"), AMG_ERR_ARG;
-    // all levels' Q^-1 in one launch, then all latency-optimised levels' M A
+static AsmQ asm_q_levels(const amg_ctx *c) {
     AsmQ Q{};
-    AsmMA M{};
-    for (int l = 0; l < nlev - 1; ++l) {
+    for (int l = 0; l + 1 < static_cast<int>(c->lev.size()); ++l) {
         const DevLevel &L = c->lev[l];
         const int k = Q.nlev++;
         Q.start[k + 1] = Q.start[k] + L.A.nnz;
         Q.isd[k] = L.isd;
         Q.bx[k] = L.bx;
         Q.bw[k] = L.bw;
+        Q.bx32[k] = L.bx32;
+        Q.bw32[k] = L.bw32;
         Q.q64[k] = L.q64;
         Q.q32[k] = L.q32;
         Q.row[k] = l;
+    }
+    return Q;
+}
+
+int enqueue_coeff_assembly(amg_ctx *c, const float *d_coef, cudaStream_t s) {
+    const int nlev = static_cast<int>(c->lev.size());
+    if (nlev - 1 > kAsmMaxLevels) return ctx_fail(c, "too many levels for the batched assembly"), AMG_ERR_ARG;
+    // all levels' Q^-1 in one launch, then all latency-optimised levels' M A;
+    // the FP32 V-cycle needs only the FP32 values (the coefficients stay in
+    // wcoef for an FP64 assembly on request)
+    const AsmQ Q = asm_q_levels(c);
+    const bool fp64 = c->opt.precision == AMG_FP64;
+    AsmMA M{};
+    for (int l = 0; l < nlev - 1; ++l) {
+        const DevLevel &L = c->lev[l];
         if (L.fast) {
             const int j = M.nlev++;
             M.start[j + 1] = M.start[j] + L.MA.nnz;
@@ -2216,11 +2245,12 @@ int enqueue_coeff_assembly(amg_ctx *c, const float *d_coef, cudaStream_t s) {
         }
     }
     if (Q.nlev > 0 && Q.start[Q.nlev] > 0) {
-        k_assemble_q_all<<<grid_for(Q.start[Q.nlev]), kBlock, 0, s>>>(Q, d_coef); AMG_COUNT();
+        k_assemble_q_all<<<grid_for(Q.start[Q.nlev]), kBlock, 0, s>>>(Q, d_coef, 5, fp64 ? 1 : 0); AMG_COUNT();
     }
     if (M.nlev > 0 && M.start[M.nlev] > 0) {
-        k_assemble_ma_all<<<grid_for(M.start[M.nlev]), kBlock, 0, s>>>(M, c->opt.precision == AMG_FP64 ? 1 : 0); AMG_COUNT();
+        k_assemble_ma_all<<<grid_for(M.start[M.nlev]), kBlock, 0, s>>>(M, fp64 ? 1 : 0); AMG_COUNT();
     }
+    c->q64_stale = !fp64;
     if (nlev > 1) {
         k_wf_coef<<<1, 32, 0, s>>>(nlev - 1, d_coef, c->scal, c->wcoef); AMG_COUNT();
     }
@@ -2254,6 +2284,7 @@ int set_coeffs_device(amg_ctx *c, const double *coef, int n_rows, cudaStream_t s
         }
         CK(cudaMemcpyAsync(c->wcoef, wc.data(), sizeof(float) * wc.size(), cudaMemcpyHostToDevice, s));
         c->q_nodes = false;
+        c->q64_stale = false;
     }
     CKL("assemble pseudo-inverse");
     // the solve kernels fetch matrix values ahead of their grid-dependency
@@ -2322,6 +2353,7 @@ int amg_set_node_coeffs(amg_ctx *c, const double *coef, long long n_values) {
     if (e != cudaSuccess) return ctx_cuda_check(c, e, "assemble per-node pseudo-inverse");
     c->have_q = true;
     c->q_nodes = true;   // the wavefront chains read the stored values
+    c->q64_stale = false;
     c->smoother = AMG_SMOOTHER_GNN;
     return AMG_OK;
 }
@@ -2333,6 +2365,16 @@ int amg_get_smoother(const amg_ctx *cc, int level, double *q_out) {
     CK(cudaSetDevice(c->opt.device));
     if (c->smoother == AMG_SMOOTHER_CHEB) return ctx_fail(c, "the Chebyshev smoother has no explicit Q^-1"), AMG_ERR_STATE;
     if (c->smoother == AMG_SMOOTHER_GNN) {
+        if (c->q64_stale) {
+            // the network's coefficients were assembled for the FP32 V-cycle
+            // only: form the FP64 values from the kept FP32 coefficients
+            const AsmQ Q = asm_q_levels(c);
+            if (Q.start[Q.nlev] > 0) {
+                k_assemble_q_all<<<grid_for(Q.start[Q.nlev]), kBlock, 0, c->stream>>>(Q, c->wcoef, 8, 2); AMG_COUNT();
+            }
+            CKL("assemble FP64 pseudo-inverse");
+            c->q64_stale = false;
+        }
         CK(cudaMemcpyAsync(q_out, L.q64, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     } else {

@@ -24,6 +24,7 @@ struct DevLevel {
     DevMat A, P, R;                            // P: n x n_{l+1}; R: n_{l+1} x n
     double *diag = nullptr;                    // a_ii (FP64)
     double *bx = nullptr, *bw = nullptr;       // pseudo-inverse basis a_ij/s and 1/a_ii or 1/(a_ii+a_jj)
+    float *bx32 = nullptr, *bw32 = nullptr;    // the same in FP32 (assembly for the FP32 V-cycle)
     unsigned char *isd = nullptr;              // 1 on the diagonal entries of A's pattern
     double *q64 = nullptr; float *q32 = nullptr;   // pseudo-inverse values on A's pattern
     double *j64 = nullptr; float *j32 = nullptr;   // omega / a_ii
@@ -129,6 +130,7 @@ struct amg_ctx {
     std::vector<int> h_ell_ptr, h_ell_row, h_ell_col;
     std::vector<double> h_ell_val;
     bool q_nodes = false;                      // Q^-1 from per-node coefficients (stored values only)
+    bool q64_stale = false;                    // only the FP32 Q^-1 was assembled (coefficients kept in wcoef)
     std::vector<amg::WfPlan> wfplan;           // per level
 };
 

@@ -1235,6 +1235,7 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
     g_launches.fetch_add(g->exec_kernels);
     c->have_q = true;
     c->q_nodes = false;
+    c->q64_stale = c->opt.precision != AMG_FP64;   // the graph assembled the FP32 values only
     c->smoother = AMG_SMOOTHER_GNN;
     int dflag = 0;
     const int G = g->batch.G;

@@ -66,6 +66,21 @@ def test_predict_coeffs_parity(name, seed):
         q = P.amg_get_smoother(ctx, 0)
         qref = O.pseudo_inverse_values(O.TMat.of(levels[0].A), c[0])
         assert rel(q, qref.numpy()) < 1e-12
+        # the FP32 V-cycle sweeps with the FP32 values assembled in the
+        # inference graph: two sweeps on every smoothed level against the
+        # oracle's FP64 sweeps with the same coefficients
+        h = O.OHierarchy.of(levels)
+        h.set_pseudo_inverse([list(r) for r in c[:len(levels) - 1]])
+        for l in range(len(levels) - 1):
+            n = levels[l].A.n_rows
+            b, u0 = W.rhs_uniform(40 + l, n), W.rhs_uniform(50 + l, n)
+            db, du = torch.tensor(b, device="cuda"), torch.tensor(u0, device="cuda")
+            P.amg_smooth_device(ctx, l, db, du, 2)
+            torch.cuda.synchronize()
+            u = torch.from_numpy(u0)
+            for _ in range(2):
+                u = O.sweep(h.levels[l], torch.from_numpy(b), u)
+            assert rel(du.cpu().numpy(), u.numpy()) < 2e-5, l
     finally:
         P.amg_destroy(ctx)
 
