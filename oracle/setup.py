@@ -36,6 +36,21 @@ the round: i joins C when it beats every undecided j in S_i u S_i^T
 with a strong dependency among the new C points becomes F.  Rounds repeat
 until no point is undecided.  Interpolation and Galerkin product as for RS.
 
+Block-local Ruge-Stueben split (device setup, coarsening "rs-blocks"; the
+domain-decomposed form of the paper's RS): the rows are cut into
+consecutive blocks of B rows and the classical first pass above runs on
+each block's induced strength subgraph independently (S and S^T restricted
+to pairs inside the block; its isolation rule applies to the restricted
+lists).  With one block (B >= n) this is the RS split itself.  B is the
+largest of 1024, 512, 256, 128 for which no block holds more than 16384
+strong pairs (128 always fits: 128 * 127 < 16384), so each block's graph
+fits one CTA's shared memory.  Strong connections between blocks are
+ignored by the blocks' passes, so a point can end F with strong
+dependencies but none on a C point (all its couplings leave its block; its
+interpolation row would be empty).  Repair (reading): every such point
+becomes C, all decided from the split the blocks produced.  "rs-blocks-h1"
+then adds the second pass below (random numbers as for PMIS).
+
 Optional second pass after PMIS (coarsening "pmis-h1"), a round-parallel form
 of the RS second pass: a pair (i, j) of F points with j in S_i violates when
 no C point is a strong dependency of both (S_i n S_j n C empty).  Each
@@ -115,6 +130,46 @@ def rs_split(n: int, S, ST) -> np.ndarray:
                 lam[k] -= 1
                 heapq.heappush(heap, (-int(lam[k]), int(k)))
     return (state == C_PT).astype(np.int64)
+
+
+RS_BLOCK_SIZES = (1024, 512, 256, 128)
+RS_BLOCK_MAX_PAIRS = 16384
+
+
+def rs_block_pairs(n: int, S, B: int) -> int:
+    """Largest number of strong pairs (i, j), j in S_i, inside one block of B rows."""
+    counts = np.zeros((n + B - 1) // B, dtype=np.int64)
+    for i in range(n):
+        counts[i // B] += sum(1 for j in S[i] if int(j) // B == i // B)
+    return int(counts.max()) if len(counts) else 0
+
+
+def rs_block_size(n: int, S) -> int:
+    """Block size of the block-local RS split (see the module notes)."""
+    for B in RS_BLOCK_SIZES:
+        if rs_block_pairs(n, S, B) <= RS_BLOCK_MAX_PAIRS:
+            return B
+    return RS_BLOCK_SIZES[-1]
+
+
+def block_rs_split(n: int, S, ST, B: int) -> np.ndarray:
+    """The RS first pass on each block's induced strength subgraph; 1 for C, 0 for F."""
+    split = np.zeros(n, dtype=np.int64)
+    for b0 in range(0, n, B):
+        b1 = min(n, b0 + B)
+        Sl = [np.array([int(j) - b0 for j in S[i] if b0 <= int(j) < b1], dtype=np.int64) for i in range(b0, b1)]
+        STl = [np.array([int(j) - b0 for j in ST[i] if b0 <= int(j) < b1], dtype=np.int64) for i in range(b0, b1)]
+        split[b0:b1] = rs_split(b1 - b0, Sl, STl)
+    return split
+
+
+def rs_repair(n: int, S, split) -> np.ndarray:
+    """F points with strong dependencies but no strong C point become C (all
+    decided from the given split)."""
+    split = np.array(split, dtype=np.int64, copy=True)
+    orphan = [i for i in range(n) if split[i] == 0 and len(S[i]) > 0 and not any(split[int(j)] for j in S[i])]
+    split[orphan] = C_PT
+    return split
 
 
 def pmis_split(n: int, S, ST, r) -> np.ndarray:
@@ -247,19 +302,25 @@ def build_hierarchy(A: CSR, theta: float = 0.25, max_levels: int = 10, max_coars
                     coarsening: str = "rs", seed: int = 0):
     """Setup-AMG-Hierarchy of Algorithm 1: list of Level, finest first.
     coarsening "rs" (the paper's), "pmis" or "pmis-h1" (PMIS then the
-    second pass; level l draws its random numbers from
-    uniform01(seed + l, n_l) for both)."""
+    second pass), "rs-blocks" or "rs-blocks-h1" (the block-local RS split,
+    then the second pass); level l draws its random numbers from
+    uniform01(seed + l, n_l)."""
+    if coarsening not in ("rs", "pmis", "pmis-h1", "rs-blocks", "rs-blocks-h1"):
+        raise ValueError(f"unknown coarsening {coarsening!r}")
     levels = [Level(A)]
     while len(levels) < max_levels and levels[-1].A.n_rows > max_coarse:
         Al = levels[-1].A
         S, ST = strength(Al, theta)
-        if coarsening in ("pmis", "pmis-h1"):
-            r = uniform01(seed + len(levels) - 1, Al.n_rows)
-            split = pmis_split(Al.n_rows, S, ST, r)
-            if coarsening == "pmis-h1":
-                split = second_pass(Al.n_rows, S, ST, split, r)
-        else:
+        if coarsening == "rs":
             split = rs_split(Al.n_rows, S, ST)
+        else:
+            r = uniform01(seed + len(levels) - 1, Al.n_rows)
+            if coarsening.startswith("pmis"):
+                split = pmis_split(Al.n_rows, S, ST, r)
+            else:
+                split = rs_repair(Al.n_rows, S, block_rs_split(Al.n_rows, S, ST, rs_block_size(Al.n_rows, S)))
+            if coarsening.endswith("-h1"):
+                split = second_pass(Al.n_rows, S, ST, split, r)
         nc = int(split.sum())
         if nc == 0 or nc > 0.9 * Al.n_rows:
             break

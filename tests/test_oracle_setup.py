@@ -339,3 +339,124 @@ def test_direct_interpolation_preserves_constants_on_every_level(kind):
         np.testing.assert_allclose(psum[sel], 1.0, atol=1e-12, err_msg=f"level {l}")
     # the check must reach rows with positive couplings to pin the lumping
     assert n_pos_rows >= 3, n_pos_rows
+
+
+# ---------------------------------------------------------------------------
+# block-local RS split (device setup's domain-decomposed RS first pass)
+# ---------------------------------------------------------------------------
+def test_block_rs_1d_hand_worked():
+    # Path of 4 (one block of B = 4): lambda = (1, 2, 2, 1); point 1 wins
+    # (largest lambda, lowest index), 0 and 2 become F, 2's F status raises
+    # lambda_3 to 2, then 3 becomes C: F C F C.  Blocks of 3 on 8 points:
+    # paths 0-1-2 and 3-4-5 give F C F, the pair 6-7 ties and keeps the lower
+    # index as C.
+    A = lap1d(8)
+    Sg, ST = S.strength(A, 0.25)
+    assert np.array_equal(S.block_rs_split(8, Sg, ST, 4), [0, 1, 0, 1, 0, 1, 0, 1])
+    assert np.array_equal(S.block_rs_split(8, Sg, ST, 3), [0, 1, 0, 0, 1, 0, 1, 0])
+
+
+@pytest.mark.parametrize("make", [lambda: W.poisson5(24), lambda: W.fv_mesh("graded", 1200, 4)[0],
+                                  lambda: W.fv_mesh("band", 1200, 5, max_aspect=100.0)[0]])
+def test_block_rs_one_block_is_the_rs_split(make):
+    A = make()
+    n = A.n_rows
+    Sg, ST = S.strength(A, 0.25)
+    assert np.array_equal(S.block_rs_split(n, Sg, ST, n), S.rs_split(n, Sg, ST))
+    assert np.array_equal(S.block_rs_split(n, Sg, ST, 4 * n), S.rs_split(n, Sg, ST))
+
+
+def _greedy_blocks_brute(n, Sg, ST, B):
+    """Independent restatement: per block, repeatedly take the undecided point
+    of largest lambda = |S^T n U| + 2 |S^T n F| (recounted from the states,
+    restricted to the block; ties to the lowest index) as C and its undecided
+    block dependents as F; block-isolated points start as F."""
+    out = np.zeros(n, dtype=np.int64)
+    for b0 in range(0, n, B):
+        b1 = min(n, b0 + B)
+        inb = lambda j: b0 <= int(j) < b1
+        st = {i: ("F" if not any(inb(j) for j in Sg[i]) and not any(inb(j) for j in ST[i]) else "U")
+              for i in range(b0, b1)}
+        while any(v == "U" for v in st.values()):
+            def lam(k):
+                return sum(1 if st[int(j)] == "U" else 2 if st[int(j)] == "F" else 0 for j in ST[k] if inb(j))
+            i = max((k for k in range(b0, b1) if st[k] == "U"), key=lambda k: (lam(k), -k))
+            st[i] = "C"
+            for j in ST[i]:
+                if inb(j) and st[int(j)] == "U":
+                    st[int(j)] = "F"
+        for i in range(b0, b1):
+            out[i] = 1 if st[i] == "C" else 0
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_block_rs_matches_brute_force_on_random_graphs(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(20, 60))
+    Sg = []
+    for i in range(n):
+        k = int(rng.integers(0, 6))
+        cand = np.unique(rng.integers(0, n, k))
+        Sg.append(np.array([j for j in cand if j != i], dtype=np.int64))
+    ST = [np.array([i for i in range(n) if j in set(Sg[i].tolist())], dtype=np.int64) for j in range(n)]
+    for B in (5, 16, n):
+        assert np.array_equal(S.block_rs_split(n, Sg, ST, B), _greedy_blocks_brute(n, Sg, ST, B)), B
+
+
+def test_block_size_rule_counts_pairs_inside_blocks():
+    # S_i = {j : 0 < |j - i| <= 10}: a block of B rows holds 20 B - 2 (10 + 9
+    # + ... + 1) = 20 B - 110 strong pairs, 20370 for B = 1024 (over the
+    # 16384 limit) and 10130 for B = 512.
+    n = 2048
+    Sg = [np.array([j for j in range(i - 10, i + 11) if j != i and 0 <= j < n], dtype=np.int64) for i in range(n)]
+    assert S.rs_block_pairs(n, Sg, 1024) == 20370
+    assert S.rs_block_pairs(n, Sg, 512) == 10130
+    assert S.rs_block_size(n, Sg) == 512
+    # a sparse mesh keeps the largest block
+    A = W.fv_mesh("graded", 1500, 4)[0]
+    Sm, _ = S.strength(A, 0.25)
+    assert S.rs_block_size(A.n_rows, Sm) == 1024
+
+
+def test_rs_repair_brute_force():
+    # a 1-D path of 7 cut into blocks of 2: blocks (0,1), (2,3), (4,5) keep
+    # their lower point as C (a tie), the last block {6} is block-isolated
+    # and F with S_6 = {5} (F): the repair makes 6 C and nothing else; the
+    # same with blocks of 3 (F C F, F C F, then {6})
+    A = lap1d(7)
+    Sg, ST = S.strength(A, 0.25)
+    b2 = S.block_rs_split(7, Sg, ST, 2)
+    assert np.array_equal(b2, [1, 0, 1, 0, 1, 0, 0])
+    assert np.array_equal(S.rs_repair(7, Sg, b2), [1, 0, 1, 0, 1, 0, 1])
+    b3 = S.block_rs_split(7, Sg, ST, 3)
+    assert np.array_equal(b3, [0, 1, 0, 0, 1, 0, 0])
+    assert np.array_equal(S.rs_repair(7, Sg, b3), [0, 1, 0, 0, 1, 0, 1])
+
+
+@pytest.mark.parametrize("kind", ["graded", "band"])
+def test_block_rs_hierarchy_close_to_rs(kind):
+    # only the block seams differ from the RS split: after the repair every
+    # F point with strong dependencies has a strong C point, the coarse grid
+    # stays within a few percent of the RS one and the V-cycle count within
+    # 25 % of RS's; with the second pass it needs no more V-cycles than RS
+    A, _ = W.fv_mesh(kind, 4000, 6, max_aspect=100.0)
+    from oracle import solve as O
+    Sg, ST = S.strength(A, 0.25)
+    n = A.n_rows
+    sp = S.rs_repair(n, Sg, S.block_rs_split(n, Sg, ST, 1024))
+    for i in range(n):
+        if sp[i] == 0 and len(Sg[i]):
+            assert any(sp[int(j)] for j in Sg[i]), i
+    out = {}
+    for mode in ("rs", "rs-blocks", "rs-blocks-h1"):
+        lv = S.build_hierarchy(A, coarsening=mode, seed=3)
+        h = O.OHierarchy.of(lv)
+        h.set_jacobi()
+        res = O.solve(h, W.rhs_uniform(2, A.n_rows), tol=1e-8)
+        assert res.status == O.OK
+        out[mode] = (lv[1].A.n_rows, res.n_vcycles)
+    nc_rs = out["rs"][0]
+    assert abs(out["rs-blocks"][0] - nc_rs) <= 0.05 * nc_rs, out
+    assert out["rs-blocks"][1] <= 1.25 * out["rs"][1], out
+    assert out["rs-blocks-h1"][1] <= out["rs"][1], out
