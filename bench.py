@@ -448,17 +448,16 @@ def run_gpu(args, wl, rank, world):
                "infer_ms": statistics.mean(hi), "kept_gnn": use_h, "status": sorted(set(v[1][0] for v in hs))}
         P.amg_destroy(ctx_h)
 
-    # the hierarchy built on the device (PMIS split and the round-parallel
-    # second pass, Galerkin products on the GB300; not the paper's RS
-    # coarsening): its setup time, then the same step on it with either smoother
-    # (its levels coarsen by about 0.45 each, so it gets 16 levels instead of 10
-    # to keep the dense coarsest level small)
-    ctx_d = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev, max_levels=16)
+    # the hierarchy built on the device (the block-local RS split with its
+    # seam repair, Galerkin products on the GB300): its setup time, then the
+    # same step on it with either smoother (12 levels allowed: the seams keep
+    # a few more points per level than the host RS)
+    ctx_d = P.amg_create(precision=P.AMG_FP32_IN_FP64, device=dev, max_levels=12)
     dsetup = []
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        P.amg_setup_device(ctx_d, A, 0, True)
+        P.amg_setup_device(ctx_d, A, 0, P.AMG_SPLIT_RS_BLOCKS)
         torch.cuda.synchronize()
         dsetup.append((time.perf_counter() - t0) * 1e3)
     dinfo = [P.amg_level_info(ctx_d, l) for l in range(P.amg_num_levels(ctx_d))]
@@ -477,7 +476,8 @@ def run_gpu(args, wl, rank, world):
     ds = [timed(dev_step, Wm + k) for k in range(K)]
     P.amg_set_jacobi(ctx_d)
     dj = [timed(lambda k: P.amg_solve_device(ctx_d, rhs_dev[k], x, TOL), Wm + k) for k in range(K)]
-    device_setup = {"coarsening": "PMIS + round-parallel second pass (device), max 16 levels", "setup_ms": dsetup[-1],
+    device_setup = {"coarsening": "block-local RS first pass + seam repair (device), max 12 levels",
+                    "setup_ms": dsetup[-1],
                     "setup_ms_first_call": dsetup[0], "levels": len(dinfo),
                     "operator_complexity": sum(i[1] for i in dinfo) / dinfo[0][1],
                     "gnn_step_ms": statistics.mean(v[0] for v in ds),
@@ -844,7 +844,8 @@ def run_kernel_only(args, wl):
         return
     A = wl["matrix"]()
     wf = args.kernel_only in ("wf_pre", "wf_post")
-    ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64, fused_sweeps=1 if wf else 0)
+    ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64, fused_sweeps=1 if wf else 0,
+                       max_levels=12 if args.kernel_only == "setup" else 10)
     P.amg_setup(ctx, A)
     if wf:
         # the finest level's wavefront chain with the learned smoother
@@ -898,12 +899,12 @@ def run_kernel_only(args, wl):
         P.amg_destroy(ctx)
         return
     if args.kernel_only == "setup":
-        # the device setup (PMIS + second pass), args.steps times
+        # the device setup (block-local RS split), args.steps times
         times = []
         for k in range(args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            P.amg_setup_device(ctx, A, 0, True)
+            P.amg_setup_device(ctx, A, 0, P.AMG_SPLIT_RS_BLOCKS)
             torch.cuda.synchronize()
             times.append((time.perf_counter() - t0) * 1e3)
         print(json.dumps({"kernel": "setup_device", "workload": wl["workload"], "ms": times}))

@@ -127,27 +127,42 @@ const char *amg_last_error(const amg_ctx *ctx);
  * Errors: AMG_ERR_ARG (non-square, bad CSR), AMG_ERR_NOT_SPD, AMG_ERR_CUDA. */
 int amg_setup(amg_ctx *ctx, const amg_csr *A);
 
+/* C/F split of amg_setup_device (flags; 0 = PMIS alone) */
+#define AMG_SPLIT_SECOND_PASS 1 /* then the round-parallel second pass         */
+#define AMG_SPLIT_RS_BLOCKS   2 /* block-local RS first pass instead of PMIS   */
+
 /* amg_setup with every level built on the device and the Ruge-Stueben first
- * pass replaced by its parallel form PMIS (De Sterck, Yang & Heys 2006) on
- * the same strength graph: measure lambda_i = |S_i^T| + r_i (FP64), points
- * with |S_i^T| = 0 start as F, then rounds in which every undecided point
- * that beats all undecided points of S_i u S_i^T (larger lambda, ties to the
- * lower index) becomes C and every undecided point with a strong dependency
- * on a new C point becomes F.  Level l draws r_i (i = 0 .. n_l - 1) as the
- * top 53 bits of output i + 1 of splitmix64 started at seed + l, times
- * 2^-53.  second_pass != 0 then runs rounds in which every F point j with a
- * strong F partner i (j in S_i) sharing no strong C point with it counts
- * those pairs v_j, and each such j that beats every such candidate in
- * S_j u S_j^T (v + r, ties to the lower index) becomes C, until every strong
- * F-F pair has a common strong C point (denser coarse levels, much faster
- * convergence with direct interpolation).  Direct interpolation, R = P^T and
+ * pass (Sec. 2.2, Sec. 4: classical RS, theta = 0.25) in a parallel form:
+ *  - AMG_SPLIT_RS_BLOCKS: the rows are cut into consecutive blocks of B rows
+ *    and the classical first pass (largest measure first, ties to the lowest
+ *    index) runs on each block's induced strength subgraph, one CTA per block
+ *    (B = the largest of 4096, 2048, ..., 128 with at most 32768 strong
+ *    pairs inside every block; with one block this is amg_setup's split); then
+ *    every F point with strong dependencies but none on a C point (its
+ *    couplings all leave its block) becomes C.  Numberings with locality (a
+ *    mesh order, RCM) keep the coarse grids within a few percent of RS;
+ *  - otherwise PMIS (De Sterck, Yang & Heys 2006) on the same strength
+ *    graph: measure lambda_i = |S_i^T| + r_i (FP64), points with
+ *    |S_i^T| = 0 start as F, then rounds in which every undecided point that
+ *    beats all undecided points of S_i u S_i^T (larger lambda, ties to the
+ *    lower index) becomes C and every undecided point with a strong
+ *    dependency on a new C point becomes F.
+ * Level l draws r_i (i = 0 .. n_l - 1) as the top 53 bits of output i + 1 of
+ * splitmix64 started at seed + l, times 2^-53.  AMG_SPLIT_SECOND_PASS then
+ * runs rounds in which every F point j with a strong F partner i (j in S_i)
+ * sharing no strong C point with it counts those pairs v_j, and each such j
+ * that beats every such candidate in S_j u S_j^T (v + r, ties to the lower
+ * index) becomes C, until every strong F-F pair has a common strong C point
+ * (denser coarse levels, fewer V-cycles).  split = 0 / 1 keep the PMIS
+ * meanings of the former second_pass flag.  Direct interpolation, R = P^T and
  * A_c = R (A P) as amg_setup, on the device; the hierarchy is then kept on
  * the host too (amg_get_level) and uploaded as by amg_setup.  A (host CSR) is
- * copied.  Same stopping rules and errors as amg_setup; AMG_ERR_CUDA also
- * covers device allocation failures.  With the second pass each level keeps
- * about half the points, so meshes of millions of rows need max_levels of
- * about 16 to keep the coarsest level within the dense solve's 4096 rows. */
-int amg_setup_device(amg_ctx *ctx, const amg_csr *A, unsigned long long seed, int second_pass);
+ * copied.  Same stopping rules and errors as amg_setup, AMG_ERR_ARG for an
+ * unknown split; AMG_ERR_CUDA also covers device allocation failures.  PMIS
+ * with the second pass keeps about half the points per level, so meshes of
+ * millions of rows need max_levels of about 16 to keep the coarsest level
+ * within the dense solve's 4096 rows. */
+int amg_setup_device(amg_ctx *ctx, const amg_csr *A, unsigned long long seed, int split);
 
 /* Load a caller-built hierarchy: A[0..n_levels-1] (finest first),
  * P[0..n_levels-2] (n_l x n_{l+1}) and R[0..n_levels-2] (n_{l+1} x n_l);

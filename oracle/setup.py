@@ -42,8 +42,8 @@ consecutive blocks of B rows and the classical first pass above runs on
 each block's induced strength subgraph independently (S and S^T restricted
 to pairs inside the block; its isolation rule applies to the restricted
 lists).  With one block (B >= n) this is the RS split itself.  B is the
-largest of 1024, 512, 256, 128 for which no block holds more than 16384
-strong pairs (128 always fits: 128 * 127 < 16384), so each block's graph
+largest of 4096, 2048, ..., 128 for which no block holds more than 32768
+strong pairs (128 always fits: 128 * 127 < 32768), so each block's graph
 fits one CTA's shared memory.  Strong connections between blocks are
 ignored by the blocks' passes, so a point can end F with strong
 dependencies but none on a C point (all its couplings leave its block; its
@@ -132,8 +132,8 @@ def rs_split(n: int, S, ST) -> np.ndarray:
     return (state == C_PT).astype(np.int64)
 
 
-RS_BLOCK_SIZES = (1024, 512, 256, 128)
-RS_BLOCK_MAX_PAIRS = 16384
+RS_BLOCK_SIZES = (4096, 2048, 1024, 512, 256, 128)
+RS_BLOCK_MAX_PAIRS = 32768
 
 
 def rs_block_pairs(n: int, S, B: int) -> int:

@@ -36,6 +36,8 @@ AMG_OUTER_REFINE = 0
 AMG_OUTER_PCG = 1
 AMG_GNN_FP32 = 0
 AMG_GNN_BF16 = 1
+AMG_SPLIT_SECOND_PASS = 1     # amg_setup_device: then the round-parallel second pass
+AMG_SPLIT_RS_BLOCKS = 2       # amg_setup_device: block-local RS first pass instead of PMIS
 AMG_GCIN_NUM_PARAMS = 55045        # GCIN width 64 (App. A.1)
 AMG_GCIN_NUM_PARAMS_H32 = 37189    # GCIN width 32 (App. B.3)
 
@@ -218,10 +220,12 @@ def amg_setup(ctx, A):
     return _check(ctx, lib().amg_setup(ctx, C.byref(m)))
 
 
-def amg_setup_device(ctx, A, seed=0, second_pass=True):
+def amg_setup_device(ctx, A, seed=0, split=AMG_SPLIT_SECOND_PASS):
+    """split: AMG_SPLIT_* flags (0 = PMIS alone; True / False keep their
+    former second-pass meaning)."""
     keep = []
     m = _csr(A, keep)
-    return _check(ctx, lib().amg_setup_device(ctx, C.byref(m), int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(second_pass))))
+    return _check(ctx, lib().amg_setup_device(ctx, C.byref(m), int(seed) & 0xFFFFFFFFFFFFFFFF, int(split)))
 
 
 def amg_load_hierarchy(ctx, A_list, P_list, R_list=None):

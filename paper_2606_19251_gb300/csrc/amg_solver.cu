@@ -2089,17 +2089,19 @@ int amg_setup(amg_ctx *c, const amg_csr *A) {
     return upload(c);
 }
 
-int amg_setup_device(amg_ctx *c, const amg_csr *A, unsigned long long seed, int second_pass) {
+int amg_setup_device(amg_ctx *c, const amg_csr *A, unsigned long long seed, int split) {
     if (!c) return AMG_ERR_ARG;
     c->err.clear();
+    if (split < 0 || split > (AMG_SPLIT_SECOND_PASS | AMG_SPLIT_RS_BLOCKS))
+        return ctx_fail(c, "unknown split"), AMG_ERR_ARG;
     HostCSR h;
     std::string why;
     if (!to_host(A, h, why) || !validate_csr(h, true, why)) return ctx_fail(c, "A: " + why), AMG_ERR_ARG;
     if (h.n_rows < 1) return ctx_fail(c, "empty matrix"), AMG_ERR_ARG;
     CK(cudaSetDevice(c->opt.device));
     std::vector<HostLevel> levels;
-    const int rc = device_build_hierarchy(h, c->opt.theta, c->opt.max_levels, c->opt.max_coarse, seed,
-                                          second_pass != 0, c->stream, levels, why);
+    const int rc = device_build_hierarchy(h, c->opt.theta, c->opt.max_levels, c->opt.max_coarse, seed, split,
+                                          c->stream, levels, why);
     if (rc) return ctx_fail(c, why), rc;
     if (levels.back().A.n_rows > kMaxCoarseDense)
         return ctx_fail(c, "coarsening stalled above 4096 rows: dense Cholesky refused"), AMG_ERR_ARG;

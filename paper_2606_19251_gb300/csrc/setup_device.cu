@@ -339,6 +339,216 @@ __global__ void k_cflag(int n, const int8_t *__restrict__ state, int *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// block-local Ruge-Stueben split
+// ---------------------------------------------------------------------------
+// Consecutive blocks of B rows each run the classical first pass on their
+// induced strength subgraph (pairs with both points in the block).  B is the
+// largest of 4096, 2048, ..., 128 for which no block holds more than
+// kRsMaxPairs strong pairs, so a block's two restricted adjacency lists fit
+// one CTA's shared memory (128 always fits: 128 * 127 < kRsMaxPairs).
+constexpr int kRsMaxPairs = 32768;
+constexpr int kRsMaxBlock = 4096;
+constexpr int kRsSizes = 5;          // B = 256 << k, k = 0 .. 4 counted; 128 always fits
+constexpr int kRsThreads = 128;
+
+// Strong pairs inside the row's block for B = 256 << k, summed per 256-row
+// CTA: part[kRsSizes c + k].
+__global__ void __launch_bounds__(kBlock) k_rs_pairs(int n, const int *__restrict__ S_rp,
+                                                     const int *__restrict__ S_col, int *__restrict__ part) {
+    __shared__ int red[kRsSizes][kBlock / 32];
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    int c[kRsSizes] = {};
+    if (i < n) {
+        for (int p = S_rp[i]; p < S_rp[i + 1]; ++p) {
+            const int j = S_col[p];
+#pragma unroll
+            for (int k = 0; k < kRsSizes; ++k) c[k] += (j >> (8 + k)) == (i >> (8 + k));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kRsSizes; ++k) {
+        const int v = warp_sum(c[k]);
+        if (threadIdx.x % 32 == 0) red[k][threadIdx.x / 32] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kRsSizes) {
+        int t = 0;
+        for (int w = 0; w < kBlock / 32; ++w) t += red[threadIdx.x][w];
+        part[kRsSizes * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// worst[k] = the largest block sum of part for B = 256 << k: groups of 2^k
+// consecutive CTAs (one CTA)
+__global__ void __launch_bounds__(kBlock) k_rs_pairs_max(int nparts, const int *__restrict__ part,
+                                                         int *__restrict__ worst) {
+    __shared__ int red[kRsSizes][kBlock / 32];
+    int m[kRsSizes] = {};
+    for (int g = threadIdx.x; g < nparts; g += kBlock) {
+#pragma unroll
+        for (int k = 0; k < kRsSizes; ++k) {
+            if (g % (1 << k)) continue;
+            int t = 0;
+            for (int q = g; q < min(g + (1 << k), nparts); ++q) t += part[kRsSizes * q + k];
+            m[k] = max(m[k], t);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kRsSizes; ++k) {
+        int v = m[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x % 32 == 0) red[k][threadIdx.x / 32] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kRsSizes) {
+        int t = 0;
+        for (int w = 0; w < kBlock / 32; ++w) t = max(t, red[threadIdx.x][w]);
+        worst[threadIdx.x] = t;
+    }
+}
+
+// exclusive scan of cnt[0 .. m) into ptr[0 .. m] by warp 0 (m <= 1024)
+__device__ void rs_warp_scan(const int *cnt, int *ptr, int m) {
+    const int lane = threadIdx.x % 32;
+    const int per = (m + 31) / 32, a = min(m, lane * per), e = min(m, a + per);
+    int tot = 0;
+    for (int k = a; k < e; ++k) tot += cnt[k];
+    int inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    int run = inc - tot;
+    for (int k = a; k < e; ++k) {
+        ptr[k] = run;
+        run += cnt[k];
+    }
+    if (lane == 31) ptr[m] = inc;
+}
+
+// One CTA per block of B rows.  Shared memory: the block's S and S^T rows
+// restricted to the block (local indices), lambda, the states and a list of
+// the points made F by the current selection.  Each step of the first pass
+// takes the undecided point of largest (lambda, -index) as C (the CTA-wide
+// maximum of (lambda + 1) << 16 | (65535 - k)); warp 0 then makes its
+// undecided block dependents F, raises lambda_k for every undecided k that a
+// new F point strongly depends on and lowers it for every undecided k the new
+// C point strongly depends on.  Those updates commute (the increments reach
+// only points that stay undecided), so lanes apply them in any order with
+// shared-memory atomics and the result is that of the sequential pass.  Each
+// step decides at least one point: at most B steps.
+__global__ void __launch_bounds__(kRsThreads) k_rs_block(int n, int B, int max_pairs, const int *__restrict__ S_rp,
+                                                         const int *__restrict__ S_col, const int *__restrict__ T_rp,
+                                                         const int *__restrict__ T_col, int8_t *__restrict__ state) {
+    extern __shared__ __align__(16) unsigned char rs_buf[];
+    int *sp = reinterpret_cast<int *>(rs_buf);          // B + 1
+    int *tp = sp + (B + 1);                              // B + 1
+    int *lam = tp + (B + 1);                             // B (first the S counts)
+    int *tcnt = lam + B;                                 // B
+    unsigned short *sc = reinterpret_cast<unsigned short *>(tcnt + B);   // max_pairs
+    unsigned short *tc = sc + max_pairs;                                  // max_pairs
+    unsigned short *newf = tc + max_pairs;                                // B
+    int8_t *st = reinterpret_cast<int8_t *>(newf + B);                    // B
+    const int b0 = blockIdx.x * B, m = min(B, n - b0), b1 = b0 + m;
+    const int lane = threadIdx.x % 32;
+    // restricted row lengths
+    for (int k = threadIdx.x; k < m; k += kRsThreads) {
+        const int i = b0 + k;
+        int cs = 0, ct = 0;
+        for (int p = S_rp[i]; p < S_rp[i + 1]; ++p) cs += (S_col[p] >= b0 && S_col[p] < b1);
+        for (int p = T_rp[i]; p < T_rp[i + 1]; ++p) ct += (T_col[p] >= b0 && T_col[p] < b1);
+        lam[k] = cs;
+        tcnt[k] = ct;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        rs_warp_scan(lam, sp, m);
+        rs_warp_scan(tcnt, tp, m);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += kRsThreads) {
+        const int i = b0 + k;
+        int q = sp[k];
+        for (int p = S_rp[i]; p < S_rp[i + 1]; ++p) {
+            const int j = S_col[p];
+            if (j >= b0 && j < b1) sc[q++] = static_cast<unsigned short>(j - b0);
+        }
+        q = tp[k];
+        for (int p = T_rp[i]; p < T_rp[i + 1]; ++p) {
+            const int j = T_col[p];
+            if (j >= b0 && j < b1) tc[q++] = static_cast<unsigned short>(j - b0);
+        }
+        const int ns = sp[k + 1] - sp[k], nt = tp[k + 1] - tp[k];
+        lam[k] = nt;
+        st[k] = (ns == 0 && nt == 0) ? kF : kU;
+    }
+    __syncthreads();
+    __shared__ unsigned red[kRsThreads / 32];
+    for (int step = 0; step <= m; ++step) {
+        unsigned best = 0;
+        for (int k = threadIdx.x; k < m; k += kRsThreads)
+            if (st[k] == kU) best = max(best, (static_cast<unsigned>(lam[k] + 1) << 16) | (65535u - k));
+        best = __reduce_max_sync(0xffffffffu, best);
+        if (lane == 0) red[threadIdx.x / 32] = best;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < kRsThreads / 32; ++w) best = max(best, red[w]);
+        if (best == 0) break;                                   // the same value in every thread
+        if (threadIdx.x < 32) {
+            const int i = 65535 - static_cast<int>(best & 0xFFFFu);
+            if (lane == 0) st[i] = kC;
+            __syncwarp();
+            // undecided block dependents of i become F
+            int nf = 0;
+            for (int q0 = tp[i]; q0 < tp[i + 1]; q0 += 32) {
+                const int q = q0 + lane;
+                const int j = q < tp[i + 1] ? tc[q] : 0;
+                const bool fresh = q < tp[i + 1] && st[j] == kU;
+                const unsigned mask = __ballot_sync(0xffffffffu, fresh);
+                if (fresh) {
+                    newf[nf + __popc(mask & ((1u << lane) - 1u))] = static_cast<unsigned short>(j);
+                    st[j] = kF;
+                }
+                nf += __popc(mask);
+            }
+            __syncwarp();
+            for (int e = lane; e < nf; e += 32) {
+                const int j = newf[e];
+                for (int q = sp[j]; q < sp[j + 1]; ++q)
+                    if (st[sc[q]] == kU) atomicAdd(lam + sc[q], 1);
+            }
+            for (int q = sp[i] + lane; q < sp[i + 1]; q += 32)
+                if (st[sc[q]] == kU) atomicSub(lam + sc[q], 1);
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < m; k += kRsThreads) state[b0 + k] = st[k] == kC ? kC : kF;
+}
+
+inline int rs_smem(int B, int max_pairs) {
+    return ((2 * (B + 1) + 2 * B) * 4 + 2 * max_pairs * 2 + B * 2 + B + 15) / 16 * 16;
+}
+
+// Repair after the block split: an F point with strong dependencies but none
+// on a C point (its strong couplings all leave its block) becomes C, all
+// decided from the split as it stands (mark, then apply).
+__global__ void k_rs_repair_mark(int n, const int *__restrict__ S_rp, const int *__restrict__ S_col,
+                                 const int8_t *__restrict__ state, int8_t *__restrict__ mark) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    bool m = state[i] == kF && S_rp[i + 1] > S_rp[i];
+    for (int p = S_rp[i]; p < S_rp[i + 1] && m; ++p) m = state[S_col[p]] != kC;
+    mark[i] = m ? 1 : 0;
+}
+
+__global__ void k_rs_repair_apply(int n, const int8_t *__restrict__ mark, int8_t *__restrict__ state) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n && mark[i]) state[i] = kC;
+}
+
+// ---------------------------------------------------------------------------
 // direct interpolation (one thread per row, the row's entry order)
 // ---------------------------------------------------------------------------
 __global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__restrict__ col,
@@ -742,7 +952,13 @@ void plan_products(HostLevel &H, Pool &pool, cudaStream_t s) {
 }
 
 void build(const HostCSR &A0, double theta, int max_levels, int max_coarse, unsigned long long seed,
-           bool second, cudaStream_t s, std::vector<HostLevel> &levels, Pool &pool) {
+           int split_mode, cudaStream_t s, std::vector<HostLevel> &levels, Pool &pool) {
+    const bool second = (split_mode & AMG_SPLIT_SECOND_PASS) != 0;
+    const bool rs_blocks = (split_mode & AMG_SPLIT_RS_BLOCKS) != 0;
+    if (rs_blocks)
+        check(cudaFuncSetAttribute(k_rs_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   rs_smem(kRsMaxBlock, kRsMaxPairs)),
+              "block split shared memory");
     DevCSR A;
     A.n_rows = A.n_cols = A0.n_rows;
     A.nnz = A0.nnz();
@@ -774,23 +990,48 @@ void build(const HostCSR &A0, double theta, int max_levels, int max_coarse, unsi
         check(cudaMemcpyAsync(cursor, T_rp, sizeof(int) * n, cudaMemcpyDeviceToDevice, s), "copy");
         int *T_col = need<int>(pool, nS);
         k_scatter_transpose<<<g, kBlock, 0, s>>>(n, S_rp, S_col, nullptr, cursor, T_col, nullptr); AMG_COUNT();
-        // PMIS rounds
-        double *lam = need<double>(pool, n);
         int8_t *state = need<int8_t>(pool, n);
         int8_t *newc = need<int8_t>(pool, n);
         int *remaining = need<int>(pool, 1);
-        k_pmis_init<<<g, kBlock, 0, s>>>(n, T_rp, seed_l, lam, state); AMG_COUNT();
         // rounds in batches of kBatch between read-backs: a round after the
         // split is complete decides nothing and changes nothing
         constexpr int kBatch = 4;
-        for (int round = 0;; round += kBatch) {
-            if (round > n) throw Fail{"PMIS split did not finish"};
-            for (int b = 0; b < kBatch; ++b) {
-                check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
-                k_pmis_select<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, lam, state, newc); AMG_COUNT();
-                k_pmis_update<<<g, kBlock, 0, s>>>(n, S_rp, S_col, newc, state, remaining); AMG_COUNT();
+        if (rs_blocks) {
+            // block size from the strong pairs inside the blocks, then the
+            // blocks' first passes and the repair of F points left without a
+            // strong C point
+            int *part = need<int>(pool, static_cast<long long>(kRsSizes) * g);
+            int *worst = need<int>(pool, kRsSizes);
+            k_rs_pairs<<<g, kBlock, 0, s>>>(n, S_rp, S_col, part); AMG_COUNT();
+            k_rs_pairs_max<<<1, kBlock, 0, s>>>(g, part, worst); AMG_COUNT();
+            int hw[kRsSizes] = {};
+            check(cudaMemcpyAsync(hw, worst, sizeof(hw), cudaMemcpyDeviceToHost, s), "read back");
+            check(cudaStreamSynchronize(s), "synchronise");
+            int B = 128, max_pairs = kRsMaxPairs;
+            for (int k = kRsSizes - 1; k >= 0; --k) {
+                if (hw[k] <= kRsMaxPairs) {
+                    B = 256 << k;
+                    max_pairs = std::max(1, hw[k]);
+                    break;
+                }
             }
-            if (read_one(remaining, s) == 0) break;
+            k_rs_block<<<(n + B - 1) / B, kRsThreads, rs_smem(B, max_pairs), s>>>(n, B, max_pairs, S_rp, S_col, T_rp,
+                                                                              T_col, state); AMG_COUNT();
+            k_rs_repair_mark<<<g, kBlock, 0, s>>>(n, S_rp, S_col, state, newc); AMG_COUNT();
+            k_rs_repair_apply<<<g, kBlock, 0, s>>>(n, newc, state); AMG_COUNT();
+            check(cudaGetLastError(), "block split");
+        } else {
+            double *lam = need<double>(pool, n);
+            k_pmis_init<<<g, kBlock, 0, s>>>(n, T_rp, seed_l, lam, state); AMG_COUNT();
+            for (int round = 0;; round += kBatch) {
+                if (round > n) throw Fail{"PMIS split did not finish"};
+                for (int b = 0; b < kBatch; ++b) {
+                    check(cudaMemsetAsync(remaining, 0, sizeof(int), s), "memset");
+                    k_pmis_select<<<g, kBlock, 0, s>>>(n, S_rp, S_col, T_rp, T_col, lam, state, newc); AMG_COUNT();
+                    k_pmis_update<<<g, kBlock, 0, s>>>(n, S_rp, S_col, newc, state, remaining); AMG_COUNT();
+                }
+                if (read_one(remaining, s) == 0) break;
+            }
         }
         if (second) {
             int *v = need<int>(pool, n);
@@ -859,11 +1100,11 @@ int device_plan_products(std::vector<HostLevel> &levels, const std::vector<char>
 }
 
 int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int max_coarse,
-                           unsigned long long seed, bool second_pass, cudaStream_t s,
+                           unsigned long long seed, int split_mode, cudaStream_t s,
                            std::vector<HostLevel> &levels, std::string &err) {
     Pool pool;
     try {
-        build(A0, theta, max_levels, max_coarse, seed, second_pass, s, levels, pool);
+        build(A0, theta, max_levels, max_coarse, seed, split_mode, s, levels, pool);
     } catch (const Fail &f) {
         cudaStreamSynchronize(s);
         err = "device setup: " + f.msg;

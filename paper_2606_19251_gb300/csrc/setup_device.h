@@ -1,5 +1,5 @@
 // AMG setup on the device (Sec. 2.2 with a parallel C/F split): strength
-// graph, PMIS splitting, direct interpolation, R = P^T and the Galerkin
+// graph, block-local RS or PMIS splitting, direct interpolation, R = P^T and the Galerkin
 // product A_c = R (A P), every level built by CUDA kernels.  The hierarchy is
 // returned as host CSR (the context keeps a host copy of every level).
 #pragma once
@@ -12,13 +12,16 @@
 
 namespace amg {
 
-// Setup-AMG-Hierarchy of Algorithm 1 on the device.  Level l draws its PMIS
-// random numbers r_i = top 53 bits of splitmix64(seed + l) output i + 1,
-// times 2^-53; second_pass adds the round-parallel second pass (every strong
-// F-F pair gets a common strong C point).  Same stopping rules as the host
-// RS setup.  Returns AMG_OK or AMG_ERR_CUDA (message in err).
+// Setup-AMG-Hierarchy of Algorithm 1 on the device.  split_mode is a set of
+// AMG_SPLIT_* flags: AMG_SPLIT_RS_BLOCKS takes the block-local RS first pass
+// (with the repair of F points left without a strong C point) instead of
+// PMIS; AMG_SPLIT_SECOND_PASS adds the round-parallel second pass (every
+// strong F-F pair gets a common strong C point).  Level l draws its random
+// numbers r_i = top 53 bits of splitmix64(seed + l) output i + 1, times
+// 2^-53.  Same stopping rules as the host RS setup.  Returns AMG_OK or
+// AMG_ERR_CUDA (message in err).
 int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int max_coarse,
-                           unsigned long long seed, bool second_pass, cudaStream_t s,
+                           unsigned long long seed, int split_mode, cudaStream_t s,
                            std::vector<HostLevel> &levels, std::string &err);
 
 // For every level l with which[l] set (R and A present), computed on the

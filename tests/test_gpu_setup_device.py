@@ -1,7 +1,8 @@
 """GPU parity of the device setup (every level built by CUDA kernels with the
-PMIS split, optionally followed by the round-parallel second pass; Sec. 2.2
-with parallel forms of the Ruge-Stueben passes) against the oracle's
-hierarchy of the same coarsening drawn from the same random numbers.
+block-local RS split or the PMIS split, optionally followed by the
+round-parallel second pass; Sec. 2.2 with parallel forms of the
+Ruge-Stueben passes) against the oracle's hierarchy of the same coarsening
+drawn from the same random numbers.
 
 Bars: integer work bit-exact (level count, sizes, the patterns of P and of
 every A_l, hence the C/F splits); P_0 bit-exact (the same operations in the
@@ -22,7 +23,8 @@ from tests.gpu_helpers import CASES, library_levels, oracle_hier, rel_err
 pytestmark = pytest.mark.gpu
 
 
-MODES = {"pmis": False, "pmis-h1": True}
+MODES = {"pmis": 0, "pmis-h1": P.AMG_SPLIT_SECOND_PASS, "rs-blocks": P.AMG_SPLIT_RS_BLOCKS,
+         "rs-blocks-h1": P.AMG_SPLIT_RS_BLOCKS | P.AMG_SPLIT_SECOND_PASS}
 
 
 def device_ctx(A, seed, precision=P.AMG_FP64, mode="pmis-h1", **kw):
@@ -145,5 +147,58 @@ def test_device_setup_edge_cases():
         assert P.amg_num_levels(ctx) == 1
         st, x, hist = P.amg_solve(ctx, np.ones(n), rtol=1e-12)
         assert st == P.AMG_OK and rel_err(x, 1.0 / D.val) < 1e-14
+    finally:
+        P.amg_destroy(ctx)
+
+
+def test_block_split_with_one_block_is_the_host_rs_setup():
+    # n = 3600 rows and every level's strong pairs fit one block: the device
+    # split is the classical first pass itself, so the hierarchy is amg_setup's
+    A = W.poisson5(60)
+    ref = OS.build_hierarchy(A, coarsening="rs")
+    ctx = device_ctx(A, 0, mode="rs-blocks")
+    host = P.amg_create(precision=P.AMG_FP64)
+    try:
+        assert_same_hierarchy(ctx, ref)
+        P.amg_setup(host, A)
+        for (a, p), (ah, ph) in zip(library_levels(ctx), library_levels(host)):
+            assert np.array_equal(a.col, ah.col) and rel_err(a.val, ah.val) < 1e-13
+            if p is not None:
+                assert np.array_equal(p.col, ph.col)
+    finally:
+        P.amg_destroy(ctx)
+        P.amg_destroy(host)
+
+
+def test_block_split_small_blocks_on_a_dense_band():
+    # a_ij = -1 for 0 < |i - j| <= 100: 200 strong pairs per row, so blocks
+    # of 256 rows and more hold more than 32768 pairs (256 * 200 - 2 (100 +
+    # 99 + ... + 1) = 41100) and the split runs on blocks of 128 rows (eight
+    # CTAs on level 0)
+    n, w = 1000, 100
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for j in range(max(0, i - w), min(n, i + w + 1)):
+            rows.append(i)
+            cols.append(j)
+            vals.append(2.0 * w + 1.0 if i == j else -1.0)
+    A = W._coo_to_csr(n, n, np.array(rows), np.array(cols), np.array(vals))
+    Sg, _ = OS.strength(A, 0.25)
+    assert OS.rs_block_size(n, Sg) == 128
+    for mode in ("rs-blocks", "rs-blocks-h1"):
+        levels = OS.build_hierarchy(A, coarsening=mode, seed=5)
+        ctx = device_ctx(A, 5, mode=mode)
+        try:
+            assert_same_hierarchy(ctx, levels)
+        finally:
+            P.amg_destroy(ctx)
+
+
+def test_unknown_split_refused():
+    ctx = P.amg_create(precision=P.AMG_FP64)
+    try:
+        for bad in (-1, 4):
+            with pytest.raises(P.AmgError):
+                P.amg_setup_device(ctx, W.poisson5(20), 0, bad)
     finally:
         P.amg_destroy(ctx)

@@ -406,17 +406,18 @@ def test_block_rs_matches_brute_force_on_random_graphs(seed):
 
 def test_block_size_rule_counts_pairs_inside_blocks():
     # S_i = {j : 0 < |j - i| <= 10}: a block of B rows holds 20 B - 2 (10 + 9
-    # + ... + 1) = 20 B - 110 strong pairs, 20370 for B = 1024 (over the
-    # 16384 limit) and 10130 for B = 512.
-    n = 2048
+    # + ... + 1) = 20 B - 110 strong pairs, 40850 for B = 2048 (over the
+    # 32768 limit) and 20370 for B = 1024.
+    n = 4096
     Sg = [np.array([j for j in range(i - 10, i + 11) if j != i and 0 <= j < n], dtype=np.int64) for i in range(n)]
+    assert S.rs_block_pairs(n, Sg, 4096) == 81810
+    assert S.rs_block_pairs(n, Sg, 2048) == 40850
     assert S.rs_block_pairs(n, Sg, 1024) == 20370
-    assert S.rs_block_pairs(n, Sg, 512) == 10130
-    assert S.rs_block_size(n, Sg) == 512
+    assert S.rs_block_size(n, Sg) == 1024
     # a sparse mesh keeps the largest block
     A = W.fv_mesh("graded", 1500, 4)[0]
     Sm, _ = S.strength(A, 0.25)
-    assert S.rs_block_size(A.n_rows, Sm) == 1024
+    assert S.rs_block_size(A.n_rows, Sm) == 4096
 
 
 def test_rs_repair_brute_force():
@@ -436,15 +437,16 @@ def test_rs_repair_brute_force():
 
 @pytest.mark.parametrize("kind", ["graded", "band"])
 def test_block_rs_hierarchy_close_to_rs(kind):
-    # only the block seams differ from the RS split: after the repair every
-    # F point with strong dependencies has a strong C point, the coarse grid
-    # stays within a few percent of the RS one and the V-cycle count within
-    # 25 % of RS's; with the second pass it needs no more V-cycles than RS
-    A, _ = W.fv_mesh(kind, 4000, 6, max_aspect=100.0)
+    # with a locality numbering (RCM: three blocks of 4096 rows) only the
+    # block seams differ from the RS split: after the repair every F point
+    # with strong dependencies has a strong C point, the coarse grid stays
+    # within a few percent of the RS one and the V-cycle count within 25 % of
+    # RS's; with the second pass it needs no more V-cycles than RS
+    A = W.renumber_rcm(W.fv_mesh(kind, 12000, 6, max_aspect=100.0)[0])
     from oracle import solve as O
     Sg, ST = S.strength(A, 0.25)
     n = A.n_rows
-    sp = S.rs_repair(n, Sg, S.block_rs_split(n, Sg, ST, 1024))
+    sp = S.rs_repair(n, Sg, S.block_rs_split(n, Sg, ST, 512))
     for i in range(n):
         if sp[i] == 0 and len(Sg[i]):
             assert any(sp[int(j)] for j in Sg[i]), i
