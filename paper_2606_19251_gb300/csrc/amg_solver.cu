@@ -462,6 +462,26 @@ __global__ void __launch_bounds__(kBlock) k_pcg_spmv_ell(Ell64 E, const double *
     block_partial(pq, partial);
 }
 
+// Entries of the warp slices from the CSR operator (one thread per slice
+// lane): entry k of lane l at ptr[s] + 32 k + l, padding with value 0 and
+// the lane's own row as column.
+__global__ void __launch_bounds__(kBlock) k_ell_fill(int nslice, const int *__restrict__ ptr,
+                                                     const int *__restrict__ row, const int *__restrict__ rp,
+                                                     const int *__restrict__ col, const double *__restrict__ val,
+                                                     int *__restrict__ ecol, double *__restrict__ evalv) {
+    const long long t = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
+    if (t >= 32LL * nslice) return;
+    const int sl = static_cast<int>(t >> 5), l = static_cast<int>(t & 31);
+    const int r = row[t];
+    const int p0 = ptr[sl], w = (ptr[sl + 1] - p0) >> 5;
+    const int a = r >= 0 ? rp[r] : 0, len = r >= 0 ? rp[r + 1] - a : 0;
+    for (int k = 0; k < w; ++k) {
+        const long long p = static_cast<long long>(p0) + 32LL * k + l;
+        ecol[p] = k < len ? col[a + k] : (r >= 0 ? r : 0);
+        evalv[p] = k < len ? val[a + k] : 0.0;
+    }
+}
+
 __global__ void __launch_bounds__(kBlock) k_sqnorm_partial(int n, const double *__restrict__ v,
                                                            double *__restrict__ partial) {
     pdl_wait_and_release();
@@ -1693,20 +1713,23 @@ static void layout_mat(Planner &pl, DevMat &m, const HostCSR &h) {
 
 // Warp slices of the finest level's FP64 operator (see Ell64): rows sorted
 // by length, longest first, within windows of kEllWindow rows (stable, so
-// equal lengths keep their order); padding entries have value 0 and point at
-// the lane's own row.
+// equal lengths keep their order: a counting sort per window), the slice
+// widths and offsets; k_ell_fill then copies the entries on the device.
 static void build_ell(amg_ctx *c) {
     const HostCSR &A = c->host[0].A;
     const int n = A.n_rows;
     const int nslice = (n + 31) / 32;
     std::vector<int> rows(static_cast<size_t>(nslice) * 32, -1);
+    std::vector<int> start;
     for (int w0 = 0; w0 < n; w0 += kEllWindow) {
         const int w1 = std::min(n, w0 + kEllWindow);
-        std::vector<int> idx(w1 - w0);
-        for (int i = w0; i < w1; ++i) idx[i - w0] = i;
-        std::stable_sort(idx.begin(), idx.end(),
-                         [&](int a, int b) { return A.rp[a + 1] - A.rp[a] > A.rp[b + 1] - A.rp[b]; });
-        std::copy(idx.begin(), idx.end(), rows.begin() + w0);
+        int maxlen = 0;
+        for (int i = w0; i < w1; ++i) maxlen = std::max(maxlen, A.rp[i + 1] - A.rp[i]);
+        // bucket of length len starts after all longer rows of the window
+        start.assign(static_cast<size_t>(maxlen) + 2, 0);
+        for (int i = w0; i < w1; ++i) ++start[maxlen - (A.rp[i + 1] - A.rp[i]) + 1];
+        for (int k = 1; k <= maxlen + 1; ++k) start[k] += start[k - 1];
+        for (int i = w0; i < w1; ++i) rows[w0 + start[maxlen - (A.rp[i + 1] - A.rp[i])]++] = i;
     }
     c->h_ell_ptr.assign(nslice + 1, 0);
     for (int sl = 0; sl < nslice; ++sl) {
@@ -1717,25 +1740,7 @@ static void build_ell(amg_ctx *c) {
         }
         c->h_ell_ptr[sl + 1] = c->h_ell_ptr[sl] + 32 * w;
     }
-    const size_t ne = static_cast<size_t>(c->h_ell_ptr[nslice]);
-    c->h_ell_col.assign(std::max<size_t>(1, ne), 0);
-    c->h_ell_val.assign(std::max<size_t>(1, ne), 0.0);
-    for (int sl = 0; sl < nslice; ++sl) {
-        const int p0 = c->h_ell_ptr[sl], w = (c->h_ell_ptr[sl + 1] - p0) / 32;
-        for (int l = 0; l < 32; ++l) {
-            const int r = rows[32 * sl + l];
-            const int len = r >= 0 ? A.rp[r + 1] - A.rp[r] : 0;
-            for (int k = 0; k < w; ++k) {
-                const size_t p = static_cast<size_t>(p0) + 32 * k + l;
-                if (k < len) {
-                    c->h_ell_col[p] = A.col[A.rp[r] + k];
-                    c->h_ell_val[p] = A.val[A.rp[r] + k];
-                } else {
-                    c->h_ell_col[p] = r >= 0 ? r : 0;
-                }
-            }
-        }
-    }
+    c->ell_entries = static_cast<long long>(c->h_ell_ptr[nslice]);
     c->h_ell_row.swap(rows);
     c->ell_nslice = nslice;
 }
@@ -1801,8 +1806,8 @@ static void layout(amg_ctx *c, Planner &pl) {
     const int n0 = c->host[0].A.n_rows;
     c->ell_ptr = pl.take<int>(c->h_ell_ptr.size());
     c->ell_row = pl.take<int>(c->h_ell_row.size());
-    c->ell_col = pl.take<int>(c->h_ell_col.size());
-    c->ell_val = pl.take<double>(c->h_ell_val.size());
+    c->ell_col = pl.take<int>(std::max(1LL, c->ell_entries));
+    c->ell_val = pl.take<double>(std::max(1LL, c->ell_entries));
     c->db = pl.take<double>(n0);
     c->dx = pl.take<double>(n0);
     c->pcg = pl.take<double>(5 * static_cast<size_t>(n0));
@@ -1915,9 +1920,11 @@ static int upload(amg_ctx *c) {
     c->jac_omega = c->opt.omega;
     CK(cudaMemcpyAsync(c->ell_ptr, c->h_ell_ptr.data(), sizeof(int) * c->h_ell_ptr.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->ell_row, c->h_ell_row.data(), sizeof(int) * c->h_ell_row.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->ell_col, c->h_ell_col.data(), sizeof(int) * c->h_ell_col.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->ell_val, c->h_ell_val.data(), sizeof(double) * c->h_ell_val.size(), cudaMemcpyHostToDevice,
-                       s));
+    {
+        const DevMat &A0 = c->lev[0].A;
+        k_ell_fill<<<grid_for(32LL * c->ell_nslice), kBlock, 0, s>>>(c->ell_nslice, c->ell_ptr, c->ell_row, A0.rp,
+                                                                      A0.col, A0.v64, c->ell_col, c->ell_val); AMG_COUNT();
+    }
     // coarsest level: dense FP64 Cholesky and the inverse factor
     const DevLevel &Lc = c->lev.back();
     const int nL = c->nL;
@@ -1931,9 +1938,7 @@ static int upload(amg_ctx *c) {
     CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->scales.data(), c->scal, sizeof(double) * nlev, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    c->h_ell_col = std::vector<int>();    // copied: the host slices are not kept
-    c->h_ell_val = std::vector<double>();
-    c->h_ell_row = std::vector<int>();
+    c->h_ell_row = std::vector<int>();    // copied: the host row order is not kept
     if (flag) {
         c->err = "coarsest-level matrix is not positive definite";
         free_device(c);

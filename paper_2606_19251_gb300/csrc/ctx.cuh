@@ -127,8 +127,8 @@ struct amg_ctx {
     int ell_nslice = 0;
     int *ell_ptr = nullptr, *ell_row = nullptr, *ell_col = nullptr;
     double *ell_val = nullptr;
-    std::vector<int> h_ell_ptr, h_ell_row, h_ell_col;
-    std::vector<double> h_ell_val;
+    long long ell_entries = 0;                 // 32 x the sum of the slice widths
+    std::vector<int> h_ell_ptr, h_ell_row;
     bool q_nodes = false;                      // Q^-1 from per-node coefficients (stored values only)
     bool q64_stale = false;                    // only the FP32 Q^-1 was assembled (coefficients kept in wcoef)
     std::vector<amg::WfPlan> wfplan;           // per level
