@@ -69,8 +69,8 @@ int ctx_cuda_check(amg_ctx *c, cudaError_t e, const char *what) {
 // kernels: row-group CSR family
 // ---------------------------------------------------------------------------
 // r = b - A u
-template <class T, int TPR>
-__global__ void __launch_bounds__(kBlock) k_resid(int n, const int *__restrict__ rp, const int *__restrict__ col,
+template <class T, int TPR, class CS = const int *>
+__global__ void __launch_bounds__(kBlock) k_resid(int n, const int *__restrict__ rp, CS col,
                                                   const T *__restrict__ a, const T *__restrict__ b,
                                                   const T *__restrict__ u, T *__restrict__ r) {
     const int g = blockIdx.x * kBlock + threadIdx.x;
@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int *__restrict__ 
 
 // u = (add ? u : 0) + M r   (pseudo-inverse application, Sec. 3.1;
 // also prolongation-correction u += P e with add = 1)
-template <class T, int TPR>
-__global__ void __launch_bounds__(kBlock) k_apply(int n, const int *__restrict__ rp, const int *__restrict__ col,
+template <class T, int TPR, class CS = const int *>
+__global__ void __launch_bounds__(kBlock) k_apply(int n, const int *__restrict__ rp, CS col,
                                                   const T *__restrict__ m, const T *__restrict__ r,
                                                   T *__restrict__ u, int add) {
     const int g = blockIdx.x * kBlock + threadIdx.x;
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kBlock) k_apply(int n, const int *__restrict__
 }
 
 // u_out = u_in + (omega/a_ii) (b - A u_in)   (relaxed Jacobi, Sec. 2.3)
-template <class T, int TPR>
-__global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict__ rp, const int *__restrict__ col,
+template <class T, int TPR, class CS = const int *>
+__global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict__ rp, CS col,
                                                    const T *__restrict__ a, const T *__restrict__ jac,
                                                    const T *__restrict__ b, const T *__restrict__ uin,
                                                    T *__restrict__ uout) {
@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(kBlock) k_ma_sweep(int n, const int *__restric
 }
 
 // First sweep from zero that also keeps w = M b: u = w = M b
-template <class T, int TPR>
-__global__ void __launch_bounds__(kBlock) k_apply_w(int n, const int *__restrict__ rp, const int *__restrict__ col,
+template <class T, int TPR, class CS = const int *>
+__global__ void __launch_bounds__(kBlock) k_apply_w(int n, const int *__restrict__ rp, CS col,
                                                     const T *__restrict__ m, const T *__restrict__ b,
                                                     T *__restrict__ u, T *__restrict__ w) {
     const int g = blockIdx.x * kBlock + threadIdx.x;
@@ -199,8 +199,8 @@ template <class T> struct JacB {   // gathered j_j b_j
 };
 
 // Two Jacobi sweeps from zero in one pass: u = j b + j (b - A (j b)), j = omega/a_ii
-template <class T, int TPR>
-__global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__restrict__ rp, const int *__restrict__ col,
+template <class T, int TPR, class CS = const int *>
+__global__ void __launch_bounds__(kBlock) k_jacobi_first2(int n, const int *__restrict__ rp, CS col,
                                                           const T *__restrict__ a, const T *__restrict__ jac,
                                                           const T *__restrict__ b, T *__restrict__ u) {
     const int g = blockIdx.x * kBlock + threadIdx.x;
@@ -231,8 +231,8 @@ __global__ void k_cheb_zero(int n, const T *__restrict__ dinv, const T *__restri
     u[i] = di;
 }
 
-template <class T, int TPR>
-__global__ void __launch_bounds__(kBlock) k_cheb_step(int n, const int *__restrict__ rp, const int *__restrict__ col,
+template <class T, int TPR, class CS = const int *>
+__global__ void __launch_bounds__(kBlock) k_cheb_step(int n, const int *__restrict__ rp, CS col,
                                                       const T *__restrict__ a, const T *__restrict__ dinv,
                                                       const T *__restrict__ b, const T *__restrict__ uin,
                                                       T *__restrict__ uout, T *__restrict__ d, T cd, T cr,
@@ -460,6 +460,21 @@ __global__ void __launch_bounds__(kBlock) k_pcg_spmv_ell(Ell64 E, const double *
         }
     }
     block_partial(pq, partial);
+}
+
+// d_p = col_p - i in 16 bits for row i; flag = 1 if some offset does not fit
+// (the level then keeps its full column indices)
+__global__ void k_col_delta(int n, const int *__restrict__ rp, const int *__restrict__ col, short *__restrict__ d,
+                            int *__restrict__ flag) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    bool wide = false;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int off = col[p] - i;
+        if (off < -32768 || off > 32767) wide = true;
+        else d[p] = static_cast<short>(off);
+    }
+    if (wide) atomicExch(flag, 1);
 }
 
 // Entries of the warp slices from the CSR operator (one thread per slice
@@ -977,8 +992,9 @@ template <> const float *jvals<float>(const DevLevel &L) { return L.j32; }
 template <class T> struct Launch {
     template <int TPR>
     static void resid(const DevMat &A, const T *b, const T *u, T *r, cudaStream_t s) {
-        launch_pdl(k_resid<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, A.nr, A.rp, A.col,
-                                                                                         mvals<T>(A), b, u, r);
+        const dim3 g(grid_for(static_cast<long long>(A.nr) * TPR));
+        if (A.dcol) launch_pdl(k_resid<T, TPR, ColDelta>, g, dim3(kBlock), 0, s, A.nr, A.rp, ColDelta{A.dcol}, mvals<T>(A), b, u, r);
+        else launch_pdl(k_resid<T, TPR>, g, dim3(kBlock), 0, s, A.nr, A.rp, static_cast<const int *>(A.col), mvals<T>(A), b, u, r);
     }
     template <int TPR>
     static void spmv(const DevMat &M, const T *x, T *y, cudaStream_t s) {
@@ -987,13 +1003,15 @@ template <class T> struct Launch {
     }
     template <int TPR>
     static void apply(const DevMat &M, const T *m, const T *r, T *u, int add, cudaStream_t s) {
-        launch_pdl(k_apply<T, TPR>, dim3(grid_for(static_cast<long long>(M.nr) * TPR)), dim3(kBlock), 0, s, M.nr, M.rp, M.col, m,
-                                                                                         r, u, add);
+        const dim3 g(grid_for(static_cast<long long>(M.nr) * TPR));
+        if (M.dcol) launch_pdl(k_apply<T, TPR, ColDelta>, g, dim3(kBlock), 0, s, M.nr, M.rp, ColDelta{M.dcol}, m, r, u, add);
+        else launch_pdl(k_apply<T, TPR>, g, dim3(kBlock), 0, s, M.nr, M.rp, static_cast<const int *>(M.col), m, r, u, add);
     }
     template <int TPR>
     static void jacobi(const DevMat &A, const T *jac, const T *b, const T *uin, T *uout, cudaStream_t s) {
-        launch_pdl(k_jacobi<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, 
-            A.nr, A.rp, A.col, mvals<T>(A), jac, b, uin, uout);
+        const dim3 g(grid_for(static_cast<long long>(A.nr) * TPR));
+        if (A.dcol) launch_pdl(k_jacobi<T, TPR, ColDelta>, g, dim3(kBlock), 0, s, A.nr, A.rp, ColDelta{A.dcol}, mvals<T>(A), jac, b, uin, uout);
+        else launch_pdl(k_jacobi<T, TPR>, g, dim3(kBlock), 0, s, A.nr, A.rp, static_cast<const int *>(A.col), mvals<T>(A), jac, b, uin, uout);
     }
     template <int TPR>
     static void ma_sweep(const DevMat &MA, const T *w, const T *uin, T *uout, cudaStream_t s) {
@@ -1002,8 +1020,9 @@ template <class T> struct Launch {
     }
     template <int TPR>
     static void apply_w(const DevMat &A, const T *m, const T *b, T *u, T *w, cudaStream_t s) {
-        launch_pdl(k_apply_w<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, A.nr, A.rp, A.col, m, b,
-                                                                                           u, w);
+        const dim3 g(grid_for(static_cast<long long>(A.nr) * TPR));
+        if (A.dcol) launch_pdl(k_apply_w<T, TPR, ColDelta>, g, dim3(kBlock), 0, s, A.nr, A.rp, ColDelta{A.dcol}, m, b, u, w);
+        else launch_pdl(k_apply_w<T, TPR>, g, dim3(kBlock), 0, s, A.nr, A.rp, static_cast<const int *>(A.col), m, b, u, w);
     }
     template <int TPR>
     static void resid_restrict(const DevMat &R, const DevMat &RA, const T *b, const T *u, T *bc, cudaStream_t s) {
@@ -1012,8 +1031,9 @@ template <class T> struct Launch {
     }
     template <int TPR>
     static void jacobi_first2(const DevMat &A, const T *jac, const T *b, T *u, cudaStream_t s) {
-        launch_pdl(k_jacobi_first2<T, TPR>, dim3(grid_for(static_cast<long long>(A.nr) * TPR)), dim3(kBlock), 0, s, 
-            A.nr, A.rp, A.col, mvals<T>(A), jac, b, u);
+        const dim3 g(grid_for(static_cast<long long>(A.nr) * TPR));
+        if (A.dcol) launch_pdl(k_jacobi_first2<T, TPR, ColDelta>, g, dim3(kBlock), 0, s, A.nr, A.rp, ColDelta{A.dcol}, mvals<T>(A), jac, b, u);
+        else launch_pdl(k_jacobi_first2<T, TPR>, g, dim3(kBlock), 0, s, A.nr, A.rp, static_cast<const int *>(A.col), mvals<T>(A), jac, b, u);
     }
     template <int TPR>
     static void outer(const DevMat &A, const double *b, const double *x, T *rT, double *partial, int nblk,
@@ -1035,8 +1055,13 @@ template <class T> struct ChebLaunch {
     template <int TPR>
     static void step(const DevLevel &L, const T *b, const T *uin, T *uout, T *d, T cd, T cr, int first,
                      cudaStream_t s) {
-        launch_pdl(k_cheb_step<T, TPR>, dim3(grid_for(static_cast<long long>(L.n) * TPR)), dim3(kBlock), 0, s, L.n,
-                   L.A.rp, L.A.col, mvals<T>(L.A), dinvvals<T>(L), b, uin, uout, d, cd, cr, first);
+        const dim3 g(grid_for(static_cast<long long>(L.n) * TPR));
+        if (L.A.dcol)
+            launch_pdl(k_cheb_step<T, TPR, ColDelta>, g, dim3(kBlock), 0, s, L.n, L.A.rp, ColDelta{L.A.dcol},
+                       mvals<T>(L.A), dinvvals<T>(L), b, uin, uout, d, cd, cr, first);
+        else
+            launch_pdl(k_cheb_step<T, TPR>, g, dim3(kBlock), 0, s, L.n, L.A.rp, static_cast<const int *>(L.A.col),
+                       mvals<T>(L.A), dinvvals<T>(L), b, uin, uout, d, cd, cr, first);
     }
 };
 
@@ -1756,6 +1781,9 @@ static void layout(amg_ctx *c, Planner &pl) {
         if (l < nlev - 1) {
             layout_mat(pl, L.P, H.P);
             layout_mat(pl, L.R, H.R);
+            // 16-bit column offsets for the two-pass (HBM-sized) levels; dropped
+            // after the upload if some offset does not fit
+            if (!H.fast) L.A.dcol = pl.take<short>(std::max(1, L.A.nnz));
         }
         L.diag = pl.take<double>(L.n);
         L.bx = pl.take<double>(std::max(1, L.A.nnz));
@@ -1818,6 +1846,7 @@ static void layout(amg_ctx *c, Planner &pl) {
     c->state = pl.take<SolveState>(1);
     c->hist = pl.take<double>(c->opt.max_iter + 1);
     c->dflag = pl.take<int>(4);
+    c->dcol_flag = pl.take<int>(nlev);
 }
 
 static int upload_mat(amg_ctx *c, const DevMat &m, const HostCSR &h, cudaStream_t s) {
@@ -1889,6 +1918,9 @@ static int upload(amg_ctx *c) {
         const HostLevel &H = c->host[l];
         int rc = upload_mat(c, L.A, H.A, s);
         if (rc) return rc;
+        if (L.A.dcol && L.A.nnz > 0) {
+            k_col_delta<<<grid_for(L.n), kBlock, 0, s>>>(L.n, L.A.rp, L.A.col, L.A.dcol, c->dcol_flag + l); AMG_COUNT();
+        }
         if (l < nlev - 1) {
             if ((rc = upload_mat(c, L.P, H.P, s))) return rc;
             if ((rc = upload_mat(c, L.R, H.R, s))) return rc;
@@ -1935,9 +1967,13 @@ static int upload(amg_ctx *c) {
     k_tri_inverse<<<grid_for(nL), kBlock, 0, s>>>(nL, c->Ldense, c->Linv, c->LinvT); AMG_COUNT();
     CKL("hierarchy setup kernels");
     int flag = 0;
+    std::vector<int> wide(nlev, 0);
     CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->scales.data(), c->scal, sizeof(double) * nlev, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(wide.data(), c->dcol_flag, sizeof(int) * nlev, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    for (int l = 0; l < nlev; ++l)
+        if (wide[l]) c->lev[l].A.dcol = nullptr;    // an offset past 16 bits: full indices
     c->h_ell_row = std::vector<int>();    // copied: the host row order is not kept
     if (flag) {
         c->err = "coarsest-level matrix is not positive definite";

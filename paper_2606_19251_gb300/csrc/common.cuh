@@ -78,29 +78,39 @@ __device__ __forceinline__ T row_dot(int lane, int p0, int e, const int *__restr
 // a V-cycle runs, so these loads overlap the previous kernel and only the
 // gathers of the vector it produced remain after the wait.
 template <class T> struct RowBatch {
-    int base = 0, e = 0;
+    int base = 0, e = 0, row = 0;
     int c[4] = {0, 0, 0, 0};
     T v[4] = {T(0), T(0), T(0), T(0)};
 };
 
-template <int TPR, class T>
+// Column indices of a square matrix stored as 16-bit offsets from the row
+// (j = i + d_p; used where every |j - i| < 2^15, e.g. a mesh in RCM order):
+// 2 instead of 4 bytes per entry on the HBM-bound passes.
+struct ColDelta {
+    const short *__restrict__ d;
+};
+__device__ __forceinline__ int col_at(const int *__restrict__ col, int p, int) { return __ldg(col + p); }
+__device__ __forceinline__ int col_at(const ColDelta &cd, int p, int row) { return row + static_cast<int>(__ldg(cd.d + p)); }
+
+template <int TPR, class T, class CS>
 __device__ __forceinline__ void row_prefetch(RowBatch<T> &rb, bool live, int lane, const int *__restrict__ rp,
-                                             int row, const int *__restrict__ col, const T *__restrict__ val) {
+                                             int row, const CS &col, const T *__restrict__ val) {
     if (!live) return;
     const int p0 = __ldg(rp + row);
     rb.e = __ldg(rp + row + 1);
     rb.base = p0 + lane;
+    rb.row = row;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int p = rb.base + j * TPR;
-        rb.c[j] = p < rb.e ? __ldg(col + p) : 0;
+        rb.c[j] = p < rb.e ? col_at(col, p, row) : 0;
         rb.v[j] = p < rb.e ? __ldg(val + p) : T(0);
     }
 }
 
 // row_dot with the first batch taken from a RowBatch (same entries, same order).
-template <int TPR, class T, class X>
-__device__ __forceinline__ T row_dot_pref(const RowBatch<T> &rb, const int *__restrict__ col,
+template <int TPR, class T, class CS, class X>
+__device__ __forceinline__ T row_dot_pref(const RowBatch<T> &rb, const CS &col,
                                           const T *__restrict__ val, const X &xg) {
     T acc = T(0);
     if (rb.base >= rb.e) return acc;
@@ -116,7 +126,7 @@ __device__ __forceinline__ T row_dot_pref(const RowBatch<T> &rb, const int *__re
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int p = base + j * TPR;
-            c[j] = p < rb.e ? __ldg(col + p) : 0;
+            c[j] = p < rb.e ? col_at(col, p, rb.row) : 0;
             v[j] = p < rb.e ? __ldg(val + p) : T(0);
         }
         T y[4];

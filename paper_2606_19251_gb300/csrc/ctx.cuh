@@ -15,6 +15,7 @@ namespace amg {
 struct DevMat {
     int nr = 0, nc = 0, nnz = 0, tpr = 2;
     int *rp = nullptr, *col = nullptr;
+    short *dcol = nullptr;                     // col - row in 16 bits (square levels whose offsets fit), or null
     double *v64 = nullptr;
     float *v32 = nullptr;
 };
@@ -106,6 +107,7 @@ struct amg_ctx {
     amg::SolveState *state = nullptr;
     double *hist = nullptr;                    // max_iter + 1
     int *dflag = nullptr;
+    int *dcol_flag = nullptr;                  // per level: 1 if a column offset does not fit 16 bits
     char *arena = nullptr;
     size_t arena_bytes = 0;
     cudaStream_t stream = nullptr;

@@ -3,6 +3,9 @@ the L2 cache (the HBM-bound path of Sec. 2.2 / Sec. 2.3 / Sec. 3.1):
 
 * a 700 x 700 5-point grid (490,000 rows, 2,447,200 entries: one lane per
   row, and an M A pair list too large for the single-pass sweep);
+* the same grid with one extra coupling between its first and last rows
+  (a column offset past 16 bits: the level keeps full column indices instead
+  of 16-bit offsets);
 * the finest levels of the 2.5M-node generalisation mesh (graded Delaunay
   with an anisotropic band).
 
@@ -34,9 +37,24 @@ class _Lv:
         self.R = OS.transpose(Pm) if Pm is not None else None
 
 
-@pytest.fixture(scope="module", params=["grid700", "c4"])
+def _far_coupled(m):
+    """poisson5(m) plus a_{0,n-1} = a_{n-1,0} = -0.5 (diagonals raised by 0.5)."""
+    A = W.poisson5(m)
+    n = A.n_rows
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    cols = np.asarray(A.col, dtype=np.int64)
+    vals = np.array(A.val, dtype=np.float64)
+    vals[(rows == cols) & ((rows == 0) | (rows == n - 1))] += 0.5
+    rows = np.concatenate([rows, [0, n - 1]])
+    cols = np.concatenate([cols, [n - 1, 0]])
+    vals = np.concatenate([vals, [-0.5, -0.5]])
+    return W._coo_to_csr(n, n, rows, cols, vals)
+
+
+@pytest.fixture(scope="module", params=["grid700", "grid700_far", "c4"])
 def hbm(request):
-    A = W.poisson5(700) if request.param == "grid700" else W.c4_matrix(0)
+    A = {"grid700": lambda: W.poisson5(700), "grid700_far": lambda: _far_coupled(700),
+         "c4": lambda: W.c4_matrix(0)}[request.param]()
     ctx0 = P.amg_create(precision=P.AMG_FP64)
     try:
         P.amg_setup(ctx0, A)
