@@ -30,7 +30,9 @@ layer 2..4 node linears, h and Theta^(l), rounded to bfloat16 (round to
 nearest, ties to even, from their FP32 values), everything else in FP64.  This
 is the arithmetic of a tensor-core evaluation with BF16 operands and exact (or
 FP32) accumulation; under autograd the rounding passes gradients straight
-through.
+through.  BF16 inference (bf16_acts=True as well): the activations x that enter
+the aggregation of layers 2..4 are rounded to bfloat16 too (the inference path
+stores them that way); the pooling of each layer reads the unrounded x.
 
 Flat parameter order (weights stored [in][out], row-major; then bias):
 conv1 W(2x64) b(64); conv2..4 W(64x64) b(64); IN1..4 gamma(64) beta(64);
@@ -125,12 +127,12 @@ def bf16_round(t: torch.Tensor) -> torch.Tensor:
     return t.to(torch.float32).to(torch.bfloat16).to(DT)
 
 
-def forward_graph(p: dict, g: Graph, keep=None, bf16_linears=False) -> torch.Tensor:
+def forward_graph(p: dict, g: Graph, keep=None, bf16_linears=False, bf16_acts=False) -> torch.Tensor:
     """Coefficients c (5,) for one graph."""
     x = g.features()
     pooled = []
     for l in range(1, N_LAYERS + 1):
-        h = g.aggregate(x)
+        h = g.aggregate(bf16_round(x) if bf16_acts and l >= 2 else x)
         Wl = p[f"conv{l}.W"]
         if bf16_linears and l >= 2:
             h, Wl = bf16_round(h), bf16_round(Wl)
@@ -146,15 +148,15 @@ def forward_graph(p: dict, g: Graph, keep=None, bf16_linears=False) -> torch.Ten
     return z @ p["h3.W"] + p["h3.b"]
 
 
-def forward(theta, graphs, bf16_linears=False) -> torch.Tensor:
+def forward(theta, graphs, bf16_linears=False, bf16_acts=False) -> torch.Tensor:
     """Batched inference (Algorithm 1 step 6): c[g] for every graph, shape (G, 5)."""
     theta = torch.as_tensor(theta, dtype=DT) if not isinstance(theta, torch.Tensor) else theta
     p = unpack(theta)
-    return torch.stack([forward_graph(p, g, bf16_linears=bf16_linears) for g in graphs])
+    return torch.stack([forward_graph(p, g, bf16_linears=bf16_linears, bf16_acts=bf16_acts) for g in graphs])
 
 
-def predict(theta, matrices, bf16_linears=False) -> np.ndarray:
+def predict(theta, matrices, bf16_linears=False, bf16_acts=False) -> np.ndarray:
     """Coefficients for a list of CSR matrices (no gradient)."""
     with torch.no_grad():
         return forward(torch.as_tensor(np.asarray(theta, dtype=np.float64)), [Graph(A) for A in matrices],
-                       bf16_linears).numpy()
+                       bf16_linears, bf16_acts).numpy()

@@ -85,8 +85,9 @@ def _rne_bf16_bits(t):
     return torch.from_numpy(u.astype(np.uint32).view(np.float32).astype(np.float64))
 
 
-def _library_forward(theta, A, bf16=False):
-    """Same network from library layers: dense A_hat, F.linear, F.instance_norm, F.layer_norm."""
+def _library_forward(theta, A, bf16=False, acts=False):
+    """Same network from library layers: dense A_hat, F.linear, F.instance_norm,
+    F.layer_norm (acts: the activations entering layers 2..4 rounded too)."""
     p = G.unpack(torch.from_numpy(theta))
     Ad = torch.from_numpy(A.to_dense())
     n = A.n_rows
@@ -94,7 +95,7 @@ def _library_forward(theta, A, bf16=False):
     x = torch.stack([torch.diagonal(Ad), deg], 1)
     pooled = []
     for l in range(1, 5):
-        h, Wt = Ad @ x, p[f"conv{l}.W"].T
+        h, Wt = Ad @ (_rne_bf16_bits(x) if acts and l > 1 else x), p[f"conv{l}.W"].T
         if bf16 and l > 1:
             h, Wt = _rne_bf16_bits(h), _rne_bf16_bits(Wt)
         y = Fn.linear(h, Wt, p[f"conv{l}.b"])
@@ -276,3 +277,19 @@ def test_relative_metric_after_n_cycles():
     hb = O.OHierarchy.of(levels)
     hb.set_pseudo_inverse([[3.0, 0, 0, 0, 0]] * len(levels))   # unstable smoother
     assert O.relative_metric(hb, hj, f, n_cycles=6) > 0.5
+
+
+@pytest.mark.parametrize("kind", ["uniform", "band"])
+def test_bf16_inference_mode_equals_library_layers(kind):
+    """BF16 inference also rounds the activations entering layers 2..4 (and
+    only those: the pooling reads the unrounded ones)."""
+    A = W.fv_mesh(kind, 600, 3, max_aspect=100.0)[0]
+    levels = S.build_hierarchy(A, max_coarse=20)
+    theta = W.gcin_init_params(1, last_scale=1.0)
+    c = G.predict(theta, [l.A for l in levels], bf16_linears=True, bf16_acts=True)
+    cl = G.predict(theta, [l.A for l in levels], bf16_linears=True)
+    for k, lv in enumerate(levels):
+        ref = _library_forward(theta, lv.A, bf16=True, acts=True).numpy()
+        np.testing.assert_allclose(c[k], ref, rtol=1e-10, atol=1e-12)
+    d = np.abs(c - cl).max() / np.abs(cl).max()
+    assert 1e-7 < d < 2e-2
