@@ -17,6 +17,7 @@
 // sigmoid, Linear 128->128 + ReLU, Linear 128->64 + ReLU, Linear 64->5.
 // Backward mirrors these steps; every parameter gradient is a fixed-order
 // sum of per-tile or per-graph partials, so gradients are bit-reproducible.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,8 +25,6 @@
 #include <string>
 #include <mutex>
 #include <vector>
-
-#include <cuda_bf16.h>
 
 #include "gcin.cuh"
 
@@ -104,6 +103,7 @@ static void batch_layout(GcinBatch &b, Planner &pl, bool backward) {
     b.head = pl.take<float>(G * kHeadScratch);
     b.c = pl.take<float>(G * 5);
     b.err = pl.take<int>(4);
+    b.wtile = pl.take<unsigned char>(static_cast<size_t>(kLayers - 1) * kHidden * kHidden * 2);
     if (backward) {
         b.dc = pl.take<float>(G * 5);
         b.dhead = pl.take<float>(G * kHeadGrad);
@@ -259,8 +259,8 @@ __device__ __forceinline__ void tile_stats(const float (*sY)[H + 1], int nn, flo
     }
 }
 
-// Layer 1: h = A_hat x0 (FP64 sums of the raw features, one thread per node,
-// entries in row order), y = h W + b (K = 2: FMA units); tile stats.
+// Layer 1: h = A_hat x0 (FP64 sums of the raw features, four threads per
+// node), y = h W + b (K = 2: FMA units); tile stats.
 template <int H>
 __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ rp, const int *__restrict__ col,
                                                         const double *__restrict__ w64, const double *__restrict__ x0,
@@ -271,19 +271,31 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
     __shared__ float sY[kTile][H + 1];
     __shared__ float sH[kTile][2];
     const int t = blockIdx.x, a = tstart[t], nn = tstart[t + 1] - a;
-    if (threadIdx.x < nn) {
-        const int i = a + threadIdx.x;
+    {
+        static_assert(kTile * 4 == kBlock, "four threads per node of a tile");
+        // four threads per node (kTile * 4 = kBlock), entries p0 + q, p0 + q + 4,
+        // ...; the four partial sums are added pairwise, the same in each lane
+        const int k = threadIdx.x >> 2, q = threadIdx.x & 3;
         double a0 = 0.0, a1 = 0.0;
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            const double wv = w64[p];
-            const int j = col[p];
-            a0 += wv * x0[2 * j];
-            a1 += wv * x0[2 * j + 1];
+        if (k < nn) {
+            const int i = a + k;
+            for (int p = rp[i] + q; p < rp[i + 1]; p += 4) {
+                const double wv = w64[p];
+                const double2 xj = reinterpret_cast<const double2 *>(x0)[col[p]];
+                a0 += wv * xj.x;
+                a1 += wv * xj.y;
+            }
         }
-        const float h0 = static_cast<float>(a0), hv1 = static_cast<float>(a1);
-        reinterpret_cast<float2 *>(h1)[i] = make_float2(h0, hv1);
-        sH[threadIdx.x][0] = h0;
-        sH[threadIdx.x][1] = hv1;
+        a0 += __shfl_xor_sync(0xffffffffu, a0, 1);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+        a0 += __shfl_xor_sync(0xffffffffu, a0, 2);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+        if (k < nn && q == 0) {
+            const float h0 = static_cast<float>(a0), hv1 = static_cast<float>(a1);
+            reinterpret_cast<float2 *>(h1)[a + k] = make_float2(h0, hv1);
+            sH[k][0] = h0;
+            sH[k][1] = hv1;
+        }
     }
     __syncthreads();
     // 64 nodes x H features: thread -> node k = tid / 4, features FT (tid % 4) .. + FT - 1
@@ -314,9 +326,9 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
 // eight H = 64 (or sixteen H = 32) feature rows in flight.  Called by a whole
 // warp (the loop runs to the longest row of the warp, shorter rows predicated
 // off).
-template <int H>
+template <int H, class XR = const float4 *>
 __device__ __forceinline__ float4 agg_rows(int p0, int p1, const int *__restrict__ col, const float *__restrict__ w,
-                                           const float4 *__restrict__ x4, int hl) {
+                                           const XR &x4, int hl) {
     constexpr int L = H / 4;
     float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
     const int deg = p1 - p0;
@@ -393,7 +405,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_lin_tile(const int *__restrict__
         const int i = a + (live ? k : k0);
         const int p0 = rp[i], p1 = live ? rp[i + 1] : p0;
         const float4 hv = agg_rows<H>(p0, p1, col, w, x4, hl);
-        if (live) reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * L + hl] = hv;
+        if (live && hout) reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * L + hl] = hv;
         float4 yv = b4;
 #pragma unroll 4
         for (int m = 0; m < H; ++m) {
@@ -472,7 +484,10 @@ __global__ void __launch_bounds__(kLanes * H) k_stats_combine(const int *__restr
 }
 
 // x = ReLU((y - mu) rstd gamma + beta); tile sum / max / argmax of x
-// (kBlock / H groups of H threads, one thread per feature).
+// (groups of H / 4 threads, four features per thread, kBlock / (H / 4) rows
+// at a time).  x is stored in
+// FP32 (x), in bfloat16 (xb: BF16 inference) or not at all (both null: the
+// last layer in inference); the pooling always reads the FP32 value.
 template <int H>
 __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__restrict__ tstart,
                                                                 const int *__restrict__ tgraph,
@@ -481,43 +496,64 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
                                                                 const float *__restrict__ rstd,
                                                                 const float *__restrict__ gamma,
                                                                 const float *__restrict__ beta, float *__restrict__ x,
+                                                                __nv_bfloat16 *__restrict__ xb,
                                                                 double *__restrict__ tsum, float *__restrict__ tmax,
                                                                 int *__restrict__ targ) {
-    constexpr int Q = kBlock / H;
+    constexpr int F = H / 4, Q = kBlock / F;   // threads per row (4 features each), rows at a time
     __shared__ double rs[Q][H];
     __shared__ float rm[Q][H];
     __shared__ int ri[Q][H];
     const int t = blockIdx.x, a = tstart[t], e = tstart[t + 1], g = tgraph[t];
-    const int f = threadIdx.x % H, q = threadIdx.x / H;
-    const float m = mu[g * H + f], r = rstd[g * H + f], ga = gamma[f], be = beta[f];
-    // FP32 partial sum of at most kTile / Q values per thread (GB300's FP64
+    const int f = 4 * (threadIdx.x % F), q = threadIdx.x / F;
+    const float4 m = *reinterpret_cast<const float4 *>(mu + g * H + f);
+    const float4 r = *reinterpret_cast<const float4 *>(rstd + g * H + f);
+    const float4 ga = *reinterpret_cast<const float4 *>(gamma + f);
+    const float4 be = *reinterpret_cast<const float4 *>(beta + f);
+    // FP32 partial sums of at most kTile / Q values per thread (GB300's FP64
     // pipe is narrow); the tile and graph sums are taken in FP64
-    float s = 0.f;
-    float mx = -INFINITY;
-    int mi = a;
-#pragma unroll 4
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    float mx[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    int mi[4] = {a, a, a, a};
     for (int i = a + q; i < e; i += Q) {
         const size_t o = static_cast<size_t>(i) * H + f;
-        const float v = fmaxf((y[o] - m) * r * ga + be, 0.f);
-        x[o] = v;
-        s += v;
-        if (v > mx) { mx = v; mi = i; }
+        const float4 yv = *reinterpret_cast<const float4 *>(y + o);
+        float v[4];
+        v[0] = fmaxf((yv.x - m.x) * r.x * ga.x + be.x, 0.f);
+        v[1] = fmaxf((yv.y - m.y) * r.y * ga.y + be.y, 0.f);
+        v[2] = fmaxf((yv.z - m.z) * r.z * ga.z + be.z, 0.f);
+        v[3] = fmaxf((yv.w - m.w) * r.w * ga.w + be.w, 0.f);
+        if (xb) {   // inference: the next aggregation's BF16 input
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+            *reinterpret_cast<uint2 *>(xb + o) =
+                make_uint2(*reinterpret_cast<unsigned *>(&lo), *reinterpret_cast<unsigned *>(&hi));
+        } else if (x) {
+            *reinterpret_cast<float4 *>(x + o) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            s[j] += v[j];
+            if (v[j] > mx[j]) { mx[j] = v[j]; mi[j] = i; }
+        }
     }
-    rs[q][f] = static_cast<double>(s);
-    rm[q][f] = mx;
-    ri[q][f] = mi;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        rs[q][f + j] = static_cast<double>(s[j]);
+        rm[q][f + j] = mx[j];
+        ri[q][f + j] = mi[j];
+    }
     __syncthreads();
-    if (q == 0) {
+    if (threadIdx.x < H) {
+        const int ff = threadIdx.x;
         double ts = 0.0;
         float bm = -INFINITY;
         int bi = a;
         for (int k = 0; k < Q; ++k) {
-            ts += rs[k][f];
-            if (rm[k][f] > bm || (rm[k][f] == bm && ri[k][f] < bi)) { bm = rm[k][f]; bi = ri[k][f]; }
+            ts += rs[k][ff];
+            if (rm[k][ff] > bm || (rm[k][ff] == bm && ri[k][ff] < bi)) { bm = rm[k][ff]; bi = ri[k][ff]; }
         }
-        tsum[static_cast<size_t>(t) * H + f] = ts;
-        tmax[static_cast<size_t>(t) * H + f] = bm;
-        targ[static_cast<size_t>(t) * H + f] = bi;
+        tsum[static_cast<size_t>(t) * H + ff] = ts;
+        tmax[static_cast<size_t>(t) * H + ff] = bm;
+        targ[static_cast<size_t>(t) * H + ff] = bi;
     }
 }
 
@@ -649,6 +685,9 @@ void gcin_prepare_device() {
     if (done[dev]) return;
     cudaFuncSetAttribute(k_agg_lin_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden>());
     cudaFuncSetAttribute(k_agg_lin_tc<kHidden32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden32>());
+    cudaFuncSetAttribute(k_agg_lin_tc<kHidden, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<kHidden>());
+    cudaFuncSetAttribute(k_agg_lin_tc<kHidden32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         tc_smem<kHidden32>());
     cudaFuncSetAttribute(k_bwd_lin_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcb_smem<kHidden>());
     cudaFuncSetAttribute(k_bwd_lin_tc<kHidden32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcb_smem<kHidden32>());
     done[dev] = true;
@@ -659,25 +698,40 @@ static void forward_impl(GcinBatch &b, const float *th, cudaStream_t s) {
     const ParamLayout &pl = host_layout(H);
     const int N = b.N, G = b.G, NT = b.NT;
     constexpr int CT = combine_threads<H>();
+    const bool xb16 = b.bf16 && b.infer;   // BF16 inference: activations stored in bfloat16
+    if (xb16) {
+        k_pack_wtile<H><<<kLayers - 1, kBlock, 0, s>>>(th + pl.convW[1], th + pl.convW[2], th + pl.convW[3],
+                                                      b.wtile); AMG_COUNT();
+    }
     k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
     for (int l = 0; l < kLayers; ++l) {
         if (l == 0) {
             k_layer1_tile<H><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + pl.convW[0], th + pl.convB[0],
                                                    b.tstart, b.h1, b.y[0], b.tmean, b.tm2); AMG_COUNT();
+        } else if (xb16) {
+            k_agg_lin_tc<H, true><<<(NT + 1) / 2, kBlock, tc_smem<H>(), s>>>(
+                b.rp, b.col, b.w, b.x[l - 1], nullptr, b.wtile + static_cast<size_t>(l - 1) * tc_b_bytes<H>(),
+                th + pl.convB[l], b.tstart, NT, nullptr, b.y[l], b.tmean, b.tm2, b.err, 0); AMG_COUNT();
         } else if (b.bf16) {
             k_agg_lin_tc<H><<<(NT + 1) / 2, kBlock, tc_smem<H>(), s>>>(b.rp, b.col, b.w, b.x[l - 1],
-                                                                     th + pl.convW[l], th + pl.convB[l], b.tstart,
-                                                                     NT, b.h[l], b.y[l], b.tmean, b.tm2, b.err,
-                                                                     0); AMG_COUNT();
+                                                                     th + pl.convW[l], nullptr, th + pl.convB[l],
+                                                                     b.tstart, NT, b.infer ? nullptr : b.h[l], b.y[l],
+                                                                     b.tmean, b.tm2, b.err, 0); AMG_COUNT();
         } else {
             k_agg_lin_tile<H><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w, b.x[l - 1], th + pl.convW[l],
-                                                    th + pl.convB[l], b.tstart, b.h[l], b.y[l], b.tmean,
-                                                    b.tm2); AMG_COUNT();
+                                                    th + pl.convB[l], b.tstart, b.infer ? nullptr : b.h[l], b.y[l],
+                                                    b.tmean, b.tm2); AMG_COUNT();
         }
         k_stats_combine<H><<<b.NC, CT, 0, s>>>(b.ctile, b.cnode, b.tstart, b.tmean, b.tm2, b.cmean, b.cm2, 0); AMG_COUNT();
         k_stats_combine<H><<<G, CT, 0, s>>>(b.gchunk, b.gptr, b.cnode, b.cmean, b.cm2, b.mu[l], b.rstd[l], 1); AMG_COUNT();
+        // inference keeps only what the next aggregation reads (bfloat16 with
+        // the tensor-core linears, nothing after the last layer)
+        const bool last = l == kLayers - 1;
+        const bool xbf = xb16 && kInferBF16Acts;
+        float *xo = (b.infer && (xbf || last)) ? nullptr : b.x[l];
+        __nv_bfloat16 *xbo = (xbf && !last) ? reinterpret_cast<__nv_bfloat16 *>(b.x[l]) : nullptr;
         k_norm_relu_pool_tile<H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
-                                                       th + pl.inG[l], th + pl.inB[l], b.x[l], b.tsum, b.tmax,
+                                                       th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum, b.tmax,
                                                        b.targ); AMG_COUNT();
         k_pool_combine<H><<<b.NC, CT, 0, s>>>(b.ctile, b.cnode, b.tsum, b.tmax, b.targ, nullptr, nullptr, l,
                                               b.csum, b.cmax, b.carg); AMG_COUNT();
@@ -1199,6 +1253,7 @@ int gnn_predict_coeffs(amg_ctx *c, double *c_out) {
         g->batch_version = c->hier_version;
     }
     g->batch.bf16 = (c->opt.gnn_precision == AMG_GNN_BF16) ? 1 : 0;
+    g->batch.infer = 1;
     g->batch.hidden = g->hidden;
     // forward + smoother assembly (straight from the device coefficients) run
     // as one CUDA graph, captured once per batch and arithmetic: ~40 small
@@ -1291,7 +1346,7 @@ int gcin_tc_selftest(int device, int no_commit, const float *x, const float *W, 
     if (e == cudaSuccess) e = cudaMemcpy(L.W, W, sizeof(float) * kHidden * kHidden, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L.b, bias, sizeof(float) * kHidden, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_agg_lin_tc<kHidden><<<1, kBlock, tc_smem<kHidden>()>>>(L.rp, L.col, L.w, L.x, L.W, L.b, L.ts, 2, L.h, L.y, L.tm, L.t2, L.err,
+        k_agg_lin_tc<kHidden><<<1, kBlock, tc_smem<kHidden>()>>>(L.rp, L.col, L.w, L.x, L.W, nullptr, L.b, L.ts, 2, L.h, L.y, L.tm, L.t2, L.err,
                                              no_commit ? 1 : 0); AMG_COUNT();
         e = cudaGetLastError();
     }

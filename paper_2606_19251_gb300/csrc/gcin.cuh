@@ -78,6 +78,8 @@ struct GcinBatch {
     int G = 0, N = 0, NT = 0;            // graphs, nodes, tiles
     int hidden = kHidden;                // GCIN width H of the parameters (64 or 32)
     int bf16 = 0;                        // layers 2..4 on tensor cores (BF16 operands, FP32 accumulation)
+    int infer = 0;                       // inference only: no h, x in bfloat16 with bf16 (nothing kept for a backward)
+    unsigned char *wtile = nullptr;      // layers 2..4: round(W)^T as BF16 tensor-core B tiles (bf16 inference)
     int *err = nullptr;                  // device error flag (tensor-core wait timeout)
     long long E = 0;
     int *rp = nullptr, *col = nullptr, *gptr = nullptr, *gid = nullptr;

@@ -26,9 +26,13 @@ constexpr int kTcRows = 128;                       // MMA M
 template <int H> constexpr int tc_a_bytes() { return kTcRows * H * 2; }        // BF16 A tile (16 / 8 KB)
 template <int H> constexpr int tc_b_bytes() { return H * H * 2; }              // BF16 B tile (8 / 2 KB)
 template <int H> constexpr int tc_y_bytes() { return kTcRows * (H + 1) * 4; }  // FP32 staging of y over the operands
-template <int H> constexpr int tc_smem() {
+template <int H> constexpr int tc_op_bytes() {
     return (tc_a_bytes<H>() + tc_b_bytes<H>() > tc_y_bytes<H>()) ? tc_a_bytes<H>() + tc_b_bytes<H>() : tc_y_bytes<H>();
 }
+// the CTA's adjacency entries (column, weight), staged once when they fit
+constexpr int kAggStage = 2048;
+constexpr bool kInferBF16Acts = true;   // BF16 inference stores the activations in bfloat16
+template <int H> constexpr int tc_smem() { return tc_op_bytes<H>() + kAggStage * 8; }
 // 8-row groups of a K-major tile of H-wide BF16 rows are H / 8 core matrices of 128 B apart
 template <int H> constexpr uint32_t tc_sbo() { return static_cast<uint32_t>(H / 8) * 128u; }
 
@@ -75,10 +79,90 @@ __device__ __forceinline__ bool tc_wait_bounded(uint32_t mbar) {
     return false;
 }
 
+// Sum over the entries of a row of w_p x_{col p}, 8 features per lane
+// (L = H / 8 lanes per row; FP32 feature rows gathered as two 16-byte loads,
+// or bfloat16 rows (BF) as one, widened exactly); otherwise as agg_rows.
+template <int H, bool BF>
+__device__ __forceinline__ void agg_rows8(int p0, int p1, const int *__restrict__ col, const float *__restrict__ w,
+                                          const void *__restrict__ xin, int hl, float (&h)[8]) {
+    constexpr int L = H / 8;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) h[f] = 0.f;
+    const int deg = p1 - p0;
+    int maxdeg = deg;
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
+    for (int base = 0; base < maxdeg; base += L) {
+        int cj = 0;
+        float wj = 0.f;
+        if (base + hl < deg) {
+            cj = col[p0 + base + hl];
+            wj = w[p0 + base + hl];
+        }
+        const int cnt = deg - base;
+        const int cmax = min(L, maxdeg - base);
+        for (int k = 0; k < cmax; k += 4) {
+            int c[4];
+            float wk[4];
+            float v[4][8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                c[j] = __shfl_sync(0xffffffffu, cj, (k + j) & (L - 1), L);
+                wk[j] = __shfl_sync(0xffffffffu, wj, (k + j) & (L - 1), L);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool on = k + j < cnt && k + j < cmax;
+                if (BF) {
+                    const uint4 r = on ? reinterpret_cast<const uint4 *>(xin)[static_cast<size_t>(c[j]) * L + hl]
+                                       : make_uint4(0u, 0u, 0u, 0u);
+                    const unsigned q[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        v[j][2 * m] = __uint_as_float(q[m] << 16);
+                        v[j][2 * m + 1] = __uint_as_float(q[m] & 0xFFFF0000u);
+                    }
+                } else {
+                    const float4 *row = reinterpret_cast<const float4 *>(xin) + (static_cast<size_t>(c[j]) * L + hl) * 2;
+                    const float4 a = on ? row[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 b = on ? row[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[j][0] = a.x; v[j][1] = a.y; v[j][2] = a.z; v[j][3] = a.w;
+                    v[j][4] = b.x; v[j][5] = b.y; v[j][6] = b.z; v[j][7] = b.w;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (k + j < cnt && k + j < cmax) {
+#pragma unroll
+                    for (int f = 0; f < 8; ++f) h[f] = fmaf(wk[j], v[j][f], h[f]);
+                }
+            }
+        }
+    }
+}
+
+// B tiles of the node linears of layers 2..4 for the bfloat16 inference
+// path: round(W)^T in the tile layout the MMA reads (block l - 1 packs layer
+// l), so each CTA copies 8 KB instead of converting W.
 template <int H>
+__global__ void __launch_bounds__(kBlock) k_pack_wtile(const float *__restrict__ W1, const float *__restrict__ W2,
+                                                       const float *__restrict__ W3, unsigned char *__restrict__ out) {
+    const float *W = blockIdx.x == 0 ? W1 : blockIdx.x == 1 ? W2 : W3;
+    unsigned char *dst = out + static_cast<size_t>(blockIdx.x) * tc_b_bytes<H>();
+    for (int e = threadIdx.x; e < H * H; e += kBlock) {
+        const int k = e / H, n = e % H;
+        *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off<H>(n, k)) = __float2bfloat16_rn(W[e]);
+    }
+}
+
+// XB (inference): x rows are bfloat16 (8 features per lane), the B tile comes
+// pre-packed from wt, and no h is kept.
+template <int H, bool XB = false>
 __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict__ rp, const int *__restrict__ col,
-                                                       const float *__restrict__ w, const float *__restrict__ x,
-                                                       const float *__restrict__ W, const float *__restrict__ bias,
+                                                       const float *__restrict__ w, const void *__restrict__ xin,
+                                                       const float *__restrict__ W,
+                                                       const unsigned char *__restrict__ wt,
+                                                       const float *__restrict__ bias,
                                                        const int *__restrict__ tstart, int NT,
                                                        float *__restrict__ hout, float *__restrict__ y,
                                                        float *__restrict__ tmean, float *__restrict__ tm2,
@@ -90,6 +174,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     unsigned char *sA = tc_smem, *sB = tc_smem + tc_a_bytes<H>();
     // y is staged over the A / B tiles once the MMAs that read them have completed
     float(*sY)[H + 1] = reinterpret_cast<float(*)[H + 1]>(tc_smem);
+    int *s_col = reinterpret_cast<int *>(tc_smem + tc_op_bytes<H>());
+    float *s_w = reinterpret_cast<float *>(s_col + kAggStage);
+    __shared__ int s_rp[kTcRows + 1];
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ int s_ok;
@@ -107,24 +194,68 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // B = W^T (row n = output feature, k = input feature), BF16
-    for (int e = threadIdx.x; e < H * H; e += kBlock) {
-        const int k = e / H, n = e % H;
-        *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off<H>(n, k)) = __float2bfloat16_rn(W[e]);
+    if (XB) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(wt);
+        for (int q = threadIdx.x; q < tc_b_bytes<H>() / 16; q += kBlock) reinterpret_cast<uint4 *>(sB)[q] = src[q];
+    } else {
+        for (int e = threadIdx.x; e < H * H; e += kBlock) {
+            const int k = e / H, n = e % H;
+            *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off<H>(n, k)) = __float2bfloat16_rn(W[e]);
+        }
     }
-    // A = h of the (up to) 128 nodes of tiles 2b, 2b + 1, BF16
+    // A = h of the (up to) 128 nodes of tiles 2b, 2b + 1, BF16.  The rows are
+    // consecutive, so their bounds and (when at most kAggStage) their entries
+    // come in with coalesced loads first; the gathers then wait on nothing else.
     const int t0 = 2 * blockIdx.x;
     const int t1 = min(t0 + 2, NT);
     const int a0 = tstart[t0], nn = tstart[t1] - a0;
-    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    for (int k = threadIdx.x; k <= nn; k += kBlock) s_rp[k] = rp[a0 + k];
+    __syncthreads();
+    const int e0 = s_rp[0], ne = s_rp[nn] - e0;
+    const bool staged = ne <= kAggStage;
+    if (staged) {
+        for (int p = threadIdx.x; p < ne; p += kBlock) {
+            s_col[p] = col[e0 + p];
+            s_w[p] = w[e0 + p];
+        }
+    }
+    __syncthreads();
+    const int *cs = staged ? s_col : col;
+    const float *ws = staged ? s_w : w;
+    const int off = staged ? e0 : 0;
+    if (XB) {
+        constexpr int L8 = H / 8, R8 = 32 / L8;
+        const int grp = lane / L8, hl = lane % L8;
+        for (int k0 = R8 * warp; k0 < kTcRows; k0 += R8 * (kBlock / 32)) {
+            const int k = k0 + grp;
+            const bool live = k < nn;
+            const int p0 = live ? s_rp[k] - off : 0, p1 = live ? s_rp[k + 1] - off : 0;
+            float hv[8];
+            agg_rows8<H, kInferBF16Acts>(p0, p1, cs, ws, xin, hl, hv);   // zero for rows past the tiles
+            // features 8 hl .. 8 hl + 7 are one 16-byte core-matrix row
+            uint4 pk;
+            __nv_bfloat162 t;
+            t = __floats2bfloat162_rn(hv[0], hv[1]);
+            pk.x = *reinterpret_cast<unsigned *>(&t);
+            t = __floats2bfloat162_rn(hv[2], hv[3]);
+            pk.y = *reinterpret_cast<unsigned *>(&t);
+            t = __floats2bfloat162_rn(hv[4], hv[5]);
+            pk.z = *reinterpret_cast<unsigned *>(&t);
+            t = __floats2bfloat162_rn(hv[6], hv[7]);
+            pk.w = *reinterpret_cast<unsigned *>(&t);
+            *reinterpret_cast<uint4 *>(sA + tc_off<H>(k, 8 * hl)) = pk;
+        }
+    }
     const int grp = lane / L, hl = lane % L;
-    for (int k0 = R * warp; k0 < kTcRows; k0 += R * (kBlock / 32)) {
+    const float4 *x4 = reinterpret_cast<const float4 *>(xin);
+    for (int k0 = R * warp; !XB && k0 < kTcRows; k0 += R * (kBlock / 32)) {
         const int k = k0 + grp;
         const bool live = k < nn;
         const int i = a0 + (live ? k : 0);
-        const int p0 = live ? rp[i] : 0, p1 = live ? rp[i + 1] : 0;
-        const float4 hv = agg_rows<H>(p0, p1, col, w, x4, hl);     // zero for rows past the tiles
+        const int p0 = live ? s_rp[k] - off : 0, p1 = live ? s_rp[k + 1] - off : 0;
+        const float4 hv = agg_rows<H>(p0, p1, cs, ws, x4, hl);     // zero for rows past the tiles
         const __nv_bfloat162 lo = __floats2bfloat162_rn(hv.x, hv.y), hi = __floats2bfloat162_rn(hv.z, hv.w);
-        if (live) {   // the rounded h the MMA sees (kept for the backward)
+        if (live && hout) {   // the rounded h the MMA sees (kept for the backward)
             const float2 rl = __bfloat1622float2(lo), rh = __bfloat1622float2(hi);
             reinterpret_cast<float4 *>(hout)[static_cast<size_t>(i) * L + hl] = make_float4(rl.x, rl.y, rh.x, rh.y);
         }
@@ -181,10 +312,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols) : "memory");
     if (!all_ok) return;
-    // y (coalesced) and the statistics of the two 64-node tiles
-    for (int e = threadIdx.x; e < nn * H; e += kBlock) {
-        const int k = e / H, f = e % H;
-        y[static_cast<size_t>(a0 + k) * H + f] = sY[k][f];
+    // y (coalesced, 16 bytes per store) and the statistics of the two 64-node tiles
+    for (int e = threadIdx.x; e < nn * (H / 4); e += kBlock) {
+        const int k = e / (H / 4), f = 4 * (e % (H / 4));
+        reinterpret_cast<float4 *>(y)[(static_cast<size_t>(a0 + k) * H + f) / 4] =
+            make_float4(sY[k][f], sY[k][f + 1], sY[k][f + 2], sY[k][f + 3]);
     }
     // the first tile may be a graph's ragged last tile: split at tstart[t0 + 1]
     const int n0 = tstart[t0 + 1] - a0;

@@ -2,8 +2,10 @@
 path (Sec. 3.3, Algorithm 1) against the FP64 oracle, through the C ABI.
 
 Bars: coefficients within 1e-5 relative (FP32 network vs FP64 oracle, same
-FP32-rounded parameters) or 2e-2 relative (BF16 tensor-core node linears with
-FP32 accumulation); network gradients within 1e-4 relative; V-cycle
+FP32-rounded parameters) or 2e-2 relative on the vector's scale (BF16
+tensor-core node linears with FP32 accumulation; in inference the
+activations are stored in BF16 too, 4e-3 per column of the oracle's BF16
+inference mode); network gradients within 1e-4 relative; V-cycle
 loss and dL/dc within 1e-10 (FP64 V-cycle) and 1e-4 per V-cycle of the loss
 (FP32 V-cycle) of the oracle's autograd, and within 1e-4 of central finite
 differences.
@@ -102,20 +104,24 @@ def test_predict_coeffs_full_size_c2():
 @pytest.mark.parametrize("seed", [0, 7])
 def test_predict_coeffs_parity_bf16(name, seed):
     """Tensor-core path (default): BF16 operands of the layer 2..4 linears,
-    FP32 accumulation; 2e-2 relative to the FP64 oracle."""
+    FP32 accumulation, activations between layers stored in BF16; 2e-2
+    relative to the FP64 oracle on the vector's scale (5e-2 per column), 4e-3
+    per column to the oracle's BF16 inference mode."""
     A = MATS[name]()
     theta = W.gcin_init_params(seed, last_scale=1.0)
     levels = OS.build_hierarchy(A)
     ref = OG.predict(f32(theta), [l.A for l in levels])
-    emu = OG.predict(f32(theta), [l.A for l in levels], bf16_linears=True)
+    emu = OG.predict(f32(theta), [l.A for l in levels], bf16_linears=True, bf16_acts=True)
     ctx = ctx_setup(A, P.AMG_FP32_IN_FP64)
     try:
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
-        assert rel_cols(c, ref) < 2e-2, rel_cols(c, ref)
-        # the tensor-core result is the BF16-operand network up to FP32
-        # accumulation and rare one-ulp rounding flips of h
-        assert rel_cols(c, emu) < 1e-3, rel_cols(c, emu)
+        assert rel(c, ref) < 2e-2 and rel_cols(c, ref) < 5e-2, (rel(c, ref), rel_cols(c, ref))
+        # the tensor-core result is the oracle's BF16 inference network up to
+        # FP32 accumulation and rare one-ulp rounding flips of h and x: a flip
+        # moves one activation by 2^-8 of itself, and a pooled maximum over a
+        # coarse level's few nodes by as much
+        assert rel_cols(c, emu) < 4e-3, rel_cols(c, emu)
     finally:
         P.amg_destroy(ctx)
 
@@ -130,9 +136,9 @@ def test_predict_coeffs_full_size_c2_bf16(seed):
     try:
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
-        assert rel_cols(c, ref) < 2e-2, rel_cols(c, ref)
-        emu = OG.predict(f32(theta), [l.A for l in levels], bf16_linears=True)
-        assert rel_cols(c, emu) < 1e-3, rel_cols(c, emu)
+        assert rel(c, ref) < 2e-2 and rel_cols(c, ref) < 5e-2, (rel(c, ref), rel_cols(c, ref))
+        emu = OG.predict(f32(theta), [l.A for l in levels], bf16_linears=True, bf16_acts=True)
+        assert rel_cols(c, emu) < 4e-3, rel_cols(c, emu)
         # repeated inference is deterministic (fixed-order reductions)
         assert np.array_equal(c, P.gnn_predict_coeffs(ctx))
     finally:

@@ -3,9 +3,11 @@ FP64 oracle at width 32, through the same C ABI as the width-64 network: the
 width follows from the length of the parameter vector.
 
 Bars as for width 64: coefficients within 1e-5 relative (FP32 node linears)
-or 2e-2 of the FP64 oracle and 1e-3 of the BF16-operand oracle (tcgen05 node
-linears, N = 32 MMAs); network gradients within 1e-4 (FP32) and 1e-2 (BF16)
-in norm; the clipped Adam step as in the width-64 test.
+or, for inference on the tensor cores (tcgen05 node linears, N = 32 MMAs,
+activations stored in BF16), 2e-2 of the FP64 oracle on the vector's scale
+(5e-2 per column) and 4e-3 of the oracle's BF16 inference mode; the
+training forward 1e-3 of the BF16-operand oracle; network gradients within
+1e-4 (FP32) and 1e-2 (BF16) in norm; the clipped Adam step as in the width-64 test.
 """
 import numpy as np
 import pytest
@@ -82,13 +84,13 @@ def test_predict_coeffs_parity_bf16(name, seed):
     theta = W.gcin_init_params(seed, last_scale=1.0, hidden=H)
     levels = OS.build_hierarchy(A)
     ref = OG.predict(f32(theta), [l.A for l in levels])
-    emu = OG.predict(f32(theta), [l.A for l in levels], bf16_linears=True)
+    emu = OG.predict(f32(theta), [l.A for l in levels], bf16_linears=True, bf16_acts=True)
     ctx = ctx_setup(A, P.AMG_FP32_IN_FP64)
     try:
         P.gnn_load_params(ctx, theta)
         c = P.gnn_predict_coeffs(ctx)
-        assert rel_cols(c, ref) < 2e-2, rel_cols(c, ref)
-        assert rel_cols(c, emu) < 1e-3, rel_cols(c, emu)
+        assert rel(c, ref) < 2e-2 and rel_cols(c, ref) < 5e-2, (rel(c, ref), rel_cols(c, ref))
+        assert rel_cols(c, emu) < 4e-3, rel_cols(c, emu)
     finally:
         P.amg_destroy(ctx)
 
@@ -109,7 +111,7 @@ def test_predict_full_size_c2_bf16_and_width_switch():
             cf = OG.predict(f32(theta), mats)
             # BF16 against FP64: 2e-2 on the vector's scale, ~3 % per column at most
             assert rel(c, cf) < 2e-2 and rel_cols(c, cf) < 5e-2, (rel(c, cf), rel_cols(c, cf))
-            assert rel_cols(c, OG.predict(f32(theta), mats, bf16_linears=True)) < 1e-3
+            assert rel_cols(c, OG.predict(f32(theta), mats, bf16_linears=True, bf16_acts=True)) < 4e-3
             assert np.array_equal(c, P.gnn_predict_coeffs(ctx))   # deterministic replay
     finally:
         P.amg_destroy(ctx)
