@@ -153,7 +153,11 @@ int gcin_batch_build(GcinBatch &b, int n_problems, amg_ctx *const *problems, cud
     std::vector<int> ctile, cnode, gchunk;
     for (int g = 0; g < b.G; ++g) {
         gchunk.push_back(static_cast<int>(ctile.size()));
-        for (int t = gtile[g]; t < gtile[g + 1]; t += kChunkTiles) {
+        // about sqrt(tiles) tiles per chunk: both reduction stages then loop
+        // over about as many parts per lane (at least kChunkTiles per chunk)
+        const int nt_g = gtile[g + 1] - gtile[g];
+        const int ct = std::max(kChunkTiles, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(nt_g)))));
+        for (int t = gtile[g]; t < gtile[g + 1]; t += ct) {
             ctile.push_back(t);
             cnode.push_back(tstart[t]);
         }

@@ -69,7 +69,7 @@ inline int hidden_of(long long n) { return n == kNumParams ? kHidden : n == kNum
 // cross a graph boundary; every reduction over a graph is a fixed-order
 // combination of per-tile partials (deterministic, no atomics).
 constexpr int kTile = 64;
-constexpr int kChunkTiles = 64;
+constexpr int kChunkTiles = 64;     // smallest chunk of the tile -> chunk -> graph reductions
 constexpr int kGradChunks = 64;      // tile chunks of the weight-gradient reduction
 
 // Per-node and per-tile buffers are sized for the widest network (64) and
