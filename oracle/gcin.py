@@ -30,9 +30,11 @@ layer 2..4 node linears, h and Theta^(l), rounded to bfloat16 (round to
 nearest, ties to even, from their FP32 values), everything else in FP64.  This
 is the arithmetic of a tensor-core evaluation with BF16 operands and exact (or
 FP32) accumulation; under autograd the rounding passes gradients straight
-through.  BF16 inference (bf16_acts=True as well): the activations x that enter
-the aggregation of layers 2..4 are rounded to bfloat16 too (the inference path
-stores them that way); the pooling of each layer reads the unrounded x.
+through.  BF16 inference (bf16_acts=True as well): the linear outputs y of
+layers 1..4 are stored in bfloat16 (the instance-norm statistics come from the
+unrounded y, the normalisation is applied to the rounded copy), and the
+activations x that enter the aggregation of layers 2..4 are rounded to
+bfloat16 too; the pooling of each layer reads the unrounded x.
 
 Flat parameter order (weights stored [in][out], row-major; then bias):
 conv1 W(2x64) b(64); conv2..4 W(64x64) b(64); IN1..4 gamma(64) beta(64);
@@ -110,10 +112,13 @@ class Graph:
         return torch.zeros(self.n, x.shape[1], dtype=DT).index_add(0, self.row, self.w[:, None] * x[self.col])
 
 
-def instance_norm(y: torch.Tensor, gamma, beta) -> torch.Tensor:
+def instance_norm(y: torch.Tensor, gamma, beta, applied_to=None) -> torch.Tensor:
+    """InstanceNorm with statistics of y, applied to y (or to `applied_to`, a
+    rounded copy of y in BF16 inference)."""
     mu = y.mean(dim=0)
     var = ((y - mu) ** 2).mean(dim=0)
-    return (y - mu) / torch.sqrt(var + EPS) * gamma + beta
+    v = y if applied_to is None else applied_to
+    return (v - mu) / torch.sqrt(var + EPS) * gamma + beta
 
 
 def layer_norm(z: torch.Tensor, gamma, beta) -> torch.Tensor:
@@ -137,7 +142,8 @@ def forward_graph(p: dict, g: Graph, keep=None, bf16_linears=False, bf16_acts=Fa
         if bf16_linears and l >= 2:
             h, Wl = bf16_round(h), bf16_round(Wl)
         y = h @ Wl + p[f"conv{l}.b"]
-        x = torch.relu(instance_norm(y, p[f"in{l}.gamma"], p[f"in{l}.beta"]))
+        x = torch.relu(instance_norm(y, p[f"in{l}.gamma"], p[f"in{l}.beta"],
+                                     applied_to=bf16_round(y) if bf16_acts else None))
         if keep is not None:
             keep.append((h, y, x))
         gl = torch.cat([x.mean(dim=0), x.max(dim=0).values])

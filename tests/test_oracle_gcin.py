@@ -99,7 +99,14 @@ def _library_forward(theta, A, bf16=False, acts=False):
         if bf16 and l > 1:
             h, Wt = _rne_bf16_bits(h), _rne_bf16_bits(Wt)
         y = Fn.linear(h, Wt, p[f"conv{l}.b"])
-        y = Fn.instance_norm(y.T.unsqueeze(0), weight=p[f"in{l}.gamma"], bias=p[f"in{l}.beta"], eps=1e-5)[0].T
+        if acts:
+            # statistics of y (as running statistics), the library's
+            # normalisation applied to the BF16-rounded y
+            y = Fn.instance_norm(_rne_bf16_bits(y).T.unsqueeze(0), running_mean=y.mean(0),
+                                 running_var=y.var(0, unbiased=False), weight=p[f"in{l}.gamma"],
+                                 bias=p[f"in{l}.beta"], use_input_stats=False, eps=1e-5)[0].T
+        else:
+            y = Fn.instance_norm(y.T.unsqueeze(0), weight=p[f"in{l}.gamma"], bias=p[f"in{l}.beta"], eps=1e-5)[0].T
         x = Fn.relu(y)
         g = torch.cat([x.mean(0), x.amax(0)])
         pooled.append(Fn.linear(g, p[f"ro{l}.W"].T, p[f"ro{l}.b"]))
@@ -281,8 +288,9 @@ def test_relative_metric_after_n_cycles():
 
 @pytest.mark.parametrize("kind", ["uniform", "band"])
 def test_bf16_inference_mode_equals_library_layers(kind):
-    """BF16 inference also rounds the activations entering layers 2..4 (and
-    only those: the pooling reads the unrounded ones)."""
+    """BF16 inference also rounds the linear outputs before the normalisation
+    (statistics from the unrounded ones) and the activations entering layers
+    2..4 (the pooling reads the unrounded ones)."""
     A = W.fv_mesh(kind, 600, 3, max_aspect=100.0)[0]
     levels = S.build_hierarchy(A, max_coarse=20)
     theta = W.gcin_init_params(1, last_scale=1.0)
