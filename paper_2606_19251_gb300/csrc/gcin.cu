@@ -265,7 +265,15 @@ __device__ __forceinline__ void tile_stats(const float (*sY)[H + 1], int nn, flo
 
 // Layer 1: h = A_hat x0 (FP64 sums of the raw features, four threads per
 // node), y = h W + b (K = 2: FMA units); tile stats.
-template <int H>
+// bfloat16 copy of four FP32 values (round to nearest even), as 8 bytes
+__device__ __forceinline__ uint2 bf16x4(float a, float b, float c, float d) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    return make_uint2(*reinterpret_cast<unsigned *>(&lo), *reinterpret_cast<unsigned *>(&hi));
+}
+
+// YB (BF16 inference): y stored in bfloat16 (the tile statistics still from
+// the FP32 values), no h1 kept.
+template <int H, bool YB = false>
 __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ rp, const int *__restrict__ col,
                                                         const double *__restrict__ w64, const double *__restrict__ x0,
                                                         const float *__restrict__ W, const float *__restrict__ bias,
@@ -296,7 +304,7 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
         a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
         if (k < nn && q == 0) {
             const float h0 = static_cast<float>(a0), hv1 = static_cast<float>(a1);
-            reinterpret_cast<float2 *>(h1)[a + k] = make_float2(h0, hv1);
+            if (!YB) reinterpret_cast<float2 *>(h1)[a + k] = make_float2(h0, hv1);
             sH[k][0] = h0;
             sH[k][1] = hv1;
         }
@@ -314,9 +322,15 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
             out[q] = fmaf(h0, W[f], fmaf(hv1, W[H + f], bias[f]));
             sY[k][f] = out[q];
         }
-        float4 *yo = reinterpret_cast<float4 *>(y + static_cast<size_t>(a + k) * H + f0);
+        if (YB) {
+            uint2 *yo = reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(y) + static_cast<size_t>(a + k) * H + f0);
 #pragma unroll
-        for (int q = 0; q < FT / 4; ++q) yo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+            for (int q = 0; q < FT / 4; ++q) yo[q] = bf16x4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+        } else {
+            float4 *yo = reinterpret_cast<float4 *>(y + static_cast<size_t>(a + k) * H + f0);
+#pragma unroll
+            for (int q = 0; q < FT / 4; ++q) yo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+        }
     }
     __syncthreads();
     tile_stats<H>(sY, nn, tmean + static_cast<size_t>(t) * H, tm2 + static_cast<size_t>(t) * H);
@@ -492,7 +506,7 @@ __global__ void __launch_bounds__(kLanes * H) k_stats_combine(const int *__restr
 // at a time).  x is stored in
 // FP32 (x), in bfloat16 (xb: BF16 inference) or not at all (both null: the
 // last layer in inference); the pooling always reads the FP32 value.
-template <int H>
+template <int H, bool YB = false>
 __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__restrict__ tstart,
                                                                 const int *__restrict__ tgraph,
                                                                 const float *__restrict__ y,
@@ -520,16 +534,21 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
     int mi[4] = {a, a, a, a};
     for (int i = a + q; i < e; i += Q) {
         const size_t o = static_cast<size_t>(i) * H + f;
-        const float4 yv = *reinterpret_cast<const float4 *>(y + o);
+        float4 yv;
+        if (YB) {   // bfloat16 y (BF16 inference), widened exactly
+            const uint2 u = *reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(y) + o);
+            yv = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                             __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+        } else {
+            yv = *reinterpret_cast<const float4 *>(y + o);
+        }
         float v[4];
         v[0] = fmaxf((yv.x - m.x) * r.x * ga.x + be.x, 0.f);
         v[1] = fmaxf((yv.y - m.y) * r.y * ga.y + be.y, 0.f);
         v[2] = fmaxf((yv.z - m.z) * r.z * ga.z + be.z, 0.f);
         v[3] = fmaxf((yv.w - m.w) * r.w * ga.w + be.w, 0.f);
         if (xb) {   // inference: the next aggregation's BF16 input
-            __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
-            *reinterpret_cast<uint2 *>(xb + o) =
-                make_uint2(*reinterpret_cast<unsigned *>(&lo), *reinterpret_cast<unsigned *>(&hi));
+            *reinterpret_cast<uint2 *>(xb + o) = bf16x4(v[0], v[1], v[2], v[3]);
         } else if (x) {
             *reinterpret_cast<float4 *>(x + o) = make_float4(v[0], v[1], v[2], v[3]);
         }
@@ -702,14 +721,19 @@ static void forward_impl(GcinBatch &b, const float *th, cudaStream_t s) {
     const ParamLayout &pl = host_layout(H);
     const int N = b.N, G = b.G, NT = b.NT;
     constexpr int CT = combine_threads<H>();
-    const bool xb16 = b.bf16 && b.infer;   // BF16 inference: activations stored in bfloat16
+    const bool xb16 = b.bf16 && b.infer;   // BF16 inference on the tensor cores
+    const bool xbf = xb16 && kInferBF16Acts;   // ... with y and x stored in bfloat16
     if (xb16) {
         k_pack_wtile<H><<<kLayers - 1, kBlock, 0, s>>>(th + pl.convW[1], th + pl.convW[2], th + pl.convW[3],
                                                       b.wtile); AMG_COUNT();
     }
     k_feat0<<<grid_for(N), kBlock, 0, s>>>(N, b.rp, b.col, b.w64, b.x0); AMG_COUNT();
     for (int l = 0; l < kLayers; ++l) {
-        if (l == 0) {
+        if (l == 0 && xbf) {
+            k_layer1_tile<H, true><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + pl.convW[0],
+                                                         th + pl.convB[0], b.tstart, nullptr, b.y[0], b.tmean,
+                                                         b.tm2); AMG_COUNT();
+        } else if (l == 0) {
             k_layer1_tile<H><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + pl.convW[0], th + pl.convB[0],
                                                    b.tstart, b.h1, b.y[0], b.tmean, b.tm2); AMG_COUNT();
         } else if (xb16) {
@@ -731,12 +755,17 @@ static void forward_impl(GcinBatch &b, const float *th, cudaStream_t s) {
         // inference keeps only what the next aggregation reads (bfloat16 with
         // the tensor-core linears, nothing after the last layer)
         const bool last = l == kLayers - 1;
-        const bool xbf = xb16 && kInferBF16Acts;
         float *xo = (b.infer && (xbf || last)) ? nullptr : b.x[l];
         __nv_bfloat16 *xbo = (xbf && !last) ? reinterpret_cast<__nv_bfloat16 *>(b.x[l]) : nullptr;
-        k_norm_relu_pool_tile<H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
-                                                       th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum, b.tmax,
-                                                       b.targ); AMG_COUNT();
+        if (xbf) {
+            k_norm_relu_pool_tile<H, true><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
+                                                                 th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum,
+                                                                 b.tmax, b.targ); AMG_COUNT();
+        } else {
+            k_norm_relu_pool_tile<H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
+                                                           th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum, b.tmax,
+                                                           b.targ); AMG_COUNT();
+        }
         k_pool_combine<H><<<b.NC, CT, 0, s>>>(b.ctile, b.cnode, b.tsum, b.tmax, b.targ, nullptr, nullptr, l,
                                               b.csum, b.cmax, b.carg); AMG_COUNT();
         k_pool_combine<H><<<G, CT, 0, s>>>(b.gchunk, b.gptr, b.csum, b.cmax, b.carg, b.pooled, b.argmax, l,

@@ -312,11 +312,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols) : "memory");
     if (!all_ok) return;
-    // y (coalesced, 16 bytes per store) and the statistics of the two 64-node tiles
+    // y (coalesced; bfloat16 in BF16 inference) and the statistics of the
+    // two 64-node tiles (from the FP32 values)
     for (int e = threadIdx.x; e < nn * (H / 4); e += kBlock) {
         const int k = e / (H / 4), f = 4 * (e % (H / 4));
-        reinterpret_cast<float4 *>(y)[(static_cast<size_t>(a0 + k) * H + f) / 4] =
-            make_float4(sY[k][f], sY[k][f + 1], sY[k][f + 2], sY[k][f + 3]);
+        const size_t o = static_cast<size_t>(a0 + k) * H + f;
+        if (XB && kInferBF16Acts) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(sY[k][f], sY[k][f + 1]);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(sY[k][f + 2], sY[k][f + 3]);
+            reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(y) + o)[0] =
+                make_uint2(*reinterpret_cast<unsigned *>(&lo), *reinterpret_cast<unsigned *>(&hi));
+        } else {
+            reinterpret_cast<float4 *>(y)[o / 4] = make_float4(sY[k][f], sY[k][f + 1], sY[k][f + 2], sY[k][f + 3]);
+        }
     }
     // the first tile may be a graph's ragged last tile: split at tstart[t0 + 1]
     const int n0 = tstart[t0 + 1] - a0;
