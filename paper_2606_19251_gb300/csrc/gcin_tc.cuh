@@ -141,6 +141,43 @@ __device__ __forceinline__ void agg_rows8(int p0, int p1, const int *__restrict_
     }
 }
 
+// agg_rows8 for bfloat16 rows with the CTA's entries staged in shared memory
+// as (column, weight) pairs: each lane reads the pair of the entry it adds
+// (lanes of one row read the same address) instead of receiving it by shuffles.
+template <int H>
+__device__ __forceinline__ void agg_rows8_staged(int p0, int p1, const int2 *cw, const uint4 *__restrict__ x8,
+                                                 int hl, float (&h)[8]) {
+    constexpr int L = H / 8;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) h[f] = 0.f;
+    const int deg = p1 - p0;
+    int maxdeg = deg;
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
+    for (int k = 0; k < maxdeg; k += 4) {
+        uint4 r[4];
+        float wk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool on = k + j < deg;
+            const int2 e = on ? cw[p0 + k + j] : make_int2(0, 0);
+            wk[j] = __int_as_float(e.y);
+            r[j] = on ? x8[static_cast<size_t>(e.x) * L + hl] : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (k + j < deg) {
+                const unsigned q[4] = {r[j].x, r[j].y, r[j].z, r[j].w};
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    h[2 * m] = fmaf(wk[j], __uint_as_float(q[m] << 16), h[2 * m]);
+                    h[2 * m + 1] = fmaf(wk[j], __uint_as_float(q[m] & 0xFFFF0000u), h[2 * m + 1]);
+                }
+            }
+        }
+    }
+}
+
 // B tiles of the node linears of layers 2..4 for the bfloat16 inference
 // path: round(W)^T in the tile layout the MMA reads (block l - 1 packs layer
 // l), so each CTA copies 8 KB instead of converting W.
@@ -176,6 +213,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     float(*sY)[H + 1] = reinterpret_cast<float(*)[H + 1]>(tc_smem);
     int *s_col = reinterpret_cast<int *>(tc_smem + tc_op_bytes<H>());
     float *s_w = reinterpret_cast<float *>(s_col + kAggStage);
+    int2 *s_cw = reinterpret_cast<int2 *>(s_col);   // the same bytes as (column, weight) pairs (XB)
     __shared__ int s_rp[kTcRows + 1];
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
@@ -215,8 +253,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     const bool staged = ne <= kAggStage;
     if (staged) {
         for (int p = threadIdx.x; p < ne; p += kBlock) {
-            s_col[p] = col[e0 + p];
-            s_w[p] = w[e0 + p];
+            if (XB && kInferBF16Acts) {
+                s_cw[p] = make_int2(col[e0 + p], __float_as_int(w[e0 + p]));
+            } else {
+                s_col[p] = col[e0 + p];
+                s_w[p] = w[e0 + p];
+            }
         }
     }
     __syncthreads();
@@ -231,7 +273,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
             const bool live = k < nn;
             const int p0 = live ? s_rp[k] - off : 0, p1 = live ? s_rp[k + 1] - off : 0;
             float hv[8];
-            agg_rows8<H, kInferBF16Acts>(p0, p1, cs, ws, xin, hl, hv);   // zero for rows past the tiles
+            if (kInferBF16Acts && staged)
+                agg_rows8_staged<H>(p0, p1, s_cw, reinterpret_cast<const uint4 *>(xin), hl, hv);
+            else
+                agg_rows8<H, kInferBF16Acts>(p0, p1, cs, ws, xin, hl, hv);   // zero for rows past the tiles
             // features 8 hl .. 8 hl + 7 are one 16-byte core-matrix row
             uint4 pk;
             __nv_bfloat162 t;
