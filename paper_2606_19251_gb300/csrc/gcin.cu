@@ -532,16 +532,28 @@ __global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__res
     float s[4] = {0.f, 0.f, 0.f, 0.f};
     float mx[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
     int mi[4] = {a, a, a, a};
-    for (int i = a + q; i < e; i += Q) {
-        const size_t o = static_cast<size_t>(i) * H + f;
-        float4 yv;
+    static_assert(kTile % Q == 0, "rows per thread");
+#pragma unroll
+    // every row's load first (predicated), so a thread's kTile / Q loads are in flight together
+    float4 yr[kTile / Q];
+#pragma unroll
+    for (int r4 = 0; r4 < kTile / Q; ++r4) {
+        const int i = a + q + r4 * Q;
+        const size_t o = static_cast<size_t>(i < e ? i : a) * H + f;
         if (YB) {   // bfloat16 y (BF16 inference), widened exactly
             const uint2 u = *reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(y) + o);
-            yv = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
-                             __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+            yr[r4] = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                                 __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
         } else {
-            yv = *reinterpret_cast<const float4 *>(y + o);
+            yr[r4] = *reinterpret_cast<const float4 *>(y + o);
         }
+    }
+#pragma unroll
+    for (int r4 = 0; r4 < kTile / Q; ++r4) {
+        const int i = a + q + r4 * Q;
+        if (i >= e) break;
+        const size_t o = static_cast<size_t>(i) * H + f;
+        const float4 yv = yr[r4];
         float v[4];
         v[0] = fmaxf((yv.x - m.x) * r.x * ga.x + be.x, 0.f);
         v[1] = fmaxf((yv.y - m.y) * r.y * ga.y + be.y, 0.f);
