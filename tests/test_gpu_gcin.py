@@ -20,7 +20,7 @@ from oracle import gcin as OG
 from oracle import setup as OS
 from oracle import solve as O
 from oracle import train as OT
-from tests.gpu_helpers import ctx_from_oracle, ctx_setup
+from tests.gpu_helpers import ctx_from_oracle, ctx_setup, library_levels
 
 pytestmark = pytest.mark.gpu
 
@@ -314,3 +314,24 @@ def test_network_backward_bf16():
         P.gcin_trainer_destroy(tr)
         for c_ in ctxs:
             P.amg_destroy(c_)
+
+
+def test_predict_on_dense_device_hierarchy():
+    """BF16 inference on the PMIS + second-pass device hierarchy, whose coarse
+    levels hold tens of entries per row: blocks of 128 rows there exceed the
+    aggregation's shared-memory staging and gather straight from global
+    memory; parity with the oracle's BF16 inference on the same levels."""
+    A = W.fv_mesh("graded", 6000, 4)[0]
+    theta = W.gcin_init_params(5, last_scale=1.0)
+    ctx = P.amg_create(precision=P.AMG_FP32_IN_FP64, max_levels=16)
+    try:
+        P.amg_setup_device(ctx, A, 0, P.AMG_SPLIT_SECOND_PASS)
+        mats = [a for a, _ in library_levels(ctx)]
+        dense = [int(np.diff(m.row_ptr)[:128].sum()) for m in mats[1:-1]]
+        assert max(dense) > 2048, dense            # some level takes the unstaged path
+        P.gnn_load_params(ctx, theta)
+        c = P.gnn_predict_coeffs(ctx)
+        emu = OG.predict(f32(theta), mats, bf16_linears=True, bf16_acts=True)
+        assert rel_cols(c, emu) < 4e-3, rel_cols(c, emu)
+    finally:
+        P.amg_destroy(ctx)
