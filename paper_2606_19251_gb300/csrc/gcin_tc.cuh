@@ -148,8 +148,11 @@ template <int H>
 __device__ __forceinline__ void agg_rows8_staged(int p0, int p1, const int2 *cw, const uint4 *__restrict__ x8,
                                                  int hl, float (&h)[8]) {
     constexpr int L = H / 8;
+    // feature pairs (2m, 2m + 1) accumulate with paired FP32 FMAs (each half
+    // rounds exactly as fmaf)
+    float2 acc[4];
 #pragma unroll
-    for (int f = 0; f < 8; ++f) h[f] = 0.f;
+    for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
     const int deg = p1 - p0;
     int maxdeg = deg;
 #pragma unroll
@@ -168,13 +171,18 @@ __device__ __forceinline__ void agg_rows8_staged(int p0, int p1, const int2 *cw,
         for (int j = 0; j < 4; ++j) {
             if (k + j < deg) {
                 const unsigned q[4] = {r[j].x, r[j].y, r[j].z, r[j].w};
+                const float2 w2 = make_float2(wk[j], wk[j]);
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    h[2 * m] = fmaf(wk[j], __uint_as_float(q[m] << 16), h[2 * m]);
-                    h[2 * m + 1] = fmaf(wk[j], __uint_as_float(q[m] & 0xFFFF0000u), h[2 * m + 1]);
-                }
+                for (int m = 0; m < 4; ++m)
+                    acc[m] = __ffma2_rn(w2, make_float2(__uint_as_float(q[m] << 16), __uint_as_float(q[m] & 0xFFFF0000u)),
+                                        acc[m]);
             }
         }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        h[2 * m] = acc[m].x;
+        h[2 * m + 1] = acc[m].y;
     }
 }
 
