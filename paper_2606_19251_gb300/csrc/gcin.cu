@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kLanes * H) k_stats_combine(const int *__restr
 // FP32 (x), in bfloat16 (xb: BF16 inference) or not at all (both null: the
 // last layer in inference); the pooling always reads the FP32 value.
 template <int H, bool YB = false>
-__global__ void __launch_bounds__(kBlock) k_norm_relu_pool_tile(const int *__restrict__ tstart,
+__global__ void __launch_bounds__(kBlock, 6) k_norm_relu_pool_tile(const int *__restrict__ tstart,
                                                                 const int *__restrict__ tgraph,
                                                                 const float *__restrict__ y,
                                                                 const float *__restrict__ mu,
