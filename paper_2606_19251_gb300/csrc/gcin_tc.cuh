@@ -32,7 +32,12 @@ template <int H> constexpr int tc_op_bytes() {
 // the CTA's adjacency entries (column, weight), staged once when they fit
 constexpr int kAggStage = 2048;
 constexpr bool kInferBF16Acts = true;   // BF16 inference stores the activations in bfloat16
-template <int H> constexpr int tc_smem() { return tc_op_bytes<H>() + kAggStage * 8; }
+// the staged entries sit after the A and B tiles and, like them, are dead
+// once the MMAs are issued, so the y staging may overlay all three
+template <int H> constexpr int tc_stage_off() { return tc_a_bytes<H>() + tc_b_bytes<H>(); }
+template <int H> constexpr int tc_smem() {
+    return (tc_stage_off<H>() + kAggStage * 8 > tc_y_bytes<H>()) ? tc_stage_off<H>() + kAggStage * 8 : tc_y_bytes<H>();
+}
 // 8-row groups of a K-major tile of H-wide BF16 rows are H / 8 core matrices of 128 B apart
 template <int H> constexpr uint32_t tc_sbo() { return static_cast<uint32_t>(H / 8) * 128u; }
 
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     unsigned char *sA = tc_smem, *sB = tc_smem + tc_a_bytes<H>();
     // y is staged over the A / B tiles once the MMAs that read them have completed
     float(*sY)[H + 1] = reinterpret_cast<float(*)[H + 1]>(tc_smem);
-    int *s_col = reinterpret_cast<int *>(tc_smem + tc_op_bytes<H>());
+    int *s_col = reinterpret_cast<int *>(tc_smem + tc_stage_off<H>());
     float *s_w = reinterpret_cast<float *>(s_col + kAggStage);
     int2 *s_cw = reinterpret_cast<int2 *>(s_col);   // the same bytes as (column, weight) pairs (XB)
     __shared__ int s_rp[kTcRows + 1];
@@ -337,24 +342,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_lin_tc(const int *__restrict_
     __syncthreads();
     const bool all_ok = s_ok != 0;
     if (all_ok && warp < 4) {
-        // warp w reads TMEM lanes 32 w .. 32 w + 31 (its rows), 32 columns at a time
+        // warp w reads TMEM lanes 32 w .. 32 w + 31 (its rows), 16 columns at a time
         const int row = 32 * warp + lane;
 #pragma unroll
-        for (int half = 0; half < H / 32; ++half) {
-            uint32_t r[32];
-            const uint32_t ta = taddr + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(32 * half);
+        for (int q16 = 0; q16 < H / 16; ++q16) {
+            uint32_t r[16];
+            const uint32_t ta = taddr + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(16 * q16);
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                  "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                 : "r"(ta)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int f = 0; f < 32; ++f) sY[row][32 * half + f] = __uint_as_float(r[f]) + bias[32 * half + f];
+            for (int f = 0; f < 16; ++f) sY[row][16 * q16 + f] = __uint_as_float(r[f]) + bias[16 * q16 + f];
         }
     }
     if (!all_ok) {
