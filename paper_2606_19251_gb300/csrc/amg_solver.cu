@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -1162,12 +1163,37 @@ static int wf_blocks_per_sm(int tpr, bool fly) {
     }
 }
 
+// Host copies of level l's columns and values where they are still only on
+// the device (levels built by amg_setup_device)
+static int ensure_host(amg_ctx *c, int l) {
+    HostLevel &H = c->host[l];
+    for (HostCSR *h : {&H.A, &H.P, &H.R}) {
+        if (!h->on_device()) continue;
+        CK(cudaSetDevice(c->opt.device));
+        const long long nz = h->nnz();
+        h->col.resize(nz);
+        h->val.resize(nz);
+        if (nz > 0) {
+            CK(cudaMemcpyAsync(h->col.data(), h->dcol, sizeof(int) * nz, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(h->val.data(), h->dval, sizeof(double) * nz, cudaMemcpyDeviceToHost, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        h->drp = h->dcol = nullptr;
+        h->dval = nullptr;
+    }
+    return AMG_OK;
+}
+
 // Which levels run their smoothing as wavefront chains, with the group
 // ranges of their blocks' columns and the lag of every chain length.
 static int plan_wavefront(amg_ctx *c) {
     const int nlev = static_cast<int>(c->host.size());
     c->wfplan.assign(nlev, WfPlan{});
     if (!c->opt.fused_sweeps) return AMG_OK;
+    for (int l = 0; l < nlev; ++l) {
+        const int rc = ensure_host(c, l);
+        if (rc) return rc;
+    }
     const bool f32 = (c->opt.precision != AMG_FP64);
     for (int l = 0; l < nlev - 1; ++l) {
         const HostLevel &H = c->host[l];
@@ -1849,11 +1875,14 @@ static void layout(amg_ctx *c, Planner &pl) {
     c->dcol_flag = pl.take<int>(nlev);
 }
 
+// from the host, or device to device for a level built on the device
 static int upload_mat(amg_ctx *c, const DevMat &m, const HostCSR &h, cudaStream_t s) {
-    CK(cudaMemcpyAsync(m.rp, h.rp.data(), sizeof(int) * (h.n_rows + 1), cudaMemcpyHostToDevice, s));
+    const bool dev = h.on_device();
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(m.rp, dev ? h.drp : h.rp.data(), sizeof(int) * (h.n_rows + 1), kind, s));
     if (h.nnz() > 0) {
-        CK(cudaMemcpyAsync(m.col, h.col.data(), sizeof(int) * h.nnz(), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(m.v64, h.val.data(), sizeof(double) * h.nnz(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.col, dev ? h.dcol : h.col.data(), sizeof(int) * h.nnz(), kind, s));
+        CK(cudaMemcpyAsync(m.v64, dev ? h.dval : h.val.data(), sizeof(double) * h.nnz(), kind, s));
         launch_pdl(k_convert<double, float>, dim3(grid_for(h.nnz())), dim3(kBlock), 0, s, m.nnz, m.v64, m.v32);
     }
     return AMG_OK;
@@ -1979,6 +2008,18 @@ static int upload(amg_ctx *c) {
         c->err = "coarsest-level matrix is not positive definite";
         free_device(c);
         return AMG_ERR_NOT_SPD;
+    }
+    // device-built levels now live in the arena: later host copies come from there
+    for (int l = 0; l < nlev; ++l) {
+        HostLevel &H = c->host[l];
+        const DevLevel &L = c->lev[l];
+        const std::pair<HostCSR *, const DevMat *> mats[3] = {{&H.A, &L.A}, {&H.P, &L.P}, {&H.R, &L.R}};
+        for (const auto &hm : mats) {
+            if (!hm.first->on_device()) continue;
+            hm.first->drp = hm.second->rp;
+            hm.first->dcol = hm.second->col;
+            hm.first->dval = hm.second->v64;
+        }
     }
     c->smoother = AMG_SMOOTHER_JACOBI;
     return AMG_OK;
@@ -2141,13 +2182,17 @@ int amg_setup_device(amg_ctx *c, const amg_csr *A, unsigned long long seed, int 
     if (h.n_rows < 1) return ctx_fail(c, "empty matrix"), AMG_ERR_ARG;
     CK(cudaSetDevice(c->opt.device));
     std::vector<HostLevel> levels;
+    std::shared_ptr<void> built;   // the levels' device memory until the upload has copied them
     const int rc = device_build_hierarchy(h, c->opt.theta, c->opt.max_levels, c->opt.max_coarse, seed, split,
-                                          c->stream, levels, why);
+                                          c->stream, levels, built, why);
     if (rc) return ctx_fail(c, why), rc;
     if (levels.back().A.n_rows > kMaxCoarseDense)
         return ctx_fail(c, "coarsening stalled above 4096 rows: dense Cholesky refused"), AMG_ERR_ARG;
+    levels[0].A = std::move(h);    // the input's host copy stands for level 0
     c->host = std::move(levels);
-    return upload(c);
+    const int urc = upload(c);     // device to device; the host copies of the coarse levels come on demand
+    if (urc) c->host.clear();      // their device memory goes with `built`
+    return urc;
 }
 
 int amg_num_levels(const amg_ctx *c) { return c ? static_cast<int>(c->lev.size()) : 0; }
@@ -2161,9 +2206,12 @@ int amg_level_info(const amg_ctx *c, int level, int *n, long long *nnz_A, long l
     return AMG_OK;
 }
 
-int amg_get_level(const amg_ctx *c, int level, int *A_rp, int *A_col, double *A_val, int *P_rp, int *P_col,
+int amg_get_level(const amg_ctx *cc, int level, int *A_rp, int *A_col, double *A_val, int *P_rp, int *P_col,
                   double *P_val) {
+    amg_ctx *c = const_cast<amg_ctx *>(cc);
     if (!c || level < 0 || level >= static_cast<int>(c->host.size())) return AMG_ERR_ARG;
+    const int hrc = ensure_host(c, level);
+    if (hrc) return hrc;
     const HostLevel &H = c->host[level];
     if (!A_rp || !A_col || !A_val) return AMG_ERR_ARG;
     std::copy(H.A.rp.begin(), H.A.rp.end(), A_rp);
@@ -2211,6 +2259,8 @@ int amg_set_chebyshev(amg_ctx *c, int degree) {
         const int nlev = static_cast<int>(c->lev.size());
         for (int l = 0; l < nlev - 1; ++l) {
             DevLevel &L = c->lev[l];
+            const int hrc = ensure_host(c, l);
+            if (hrc) return hrc;
             const double rho = power_estimate(c->host[l].A, 20);
             if (!(rho > 0.0) || !std::isfinite(rho)) return ctx_fail(c, "power estimate failed"), AMG_ERR_ARG;
             const double lo = rho / 30.0, hi = 1.1 * rho;
@@ -2424,6 +2474,8 @@ int amg_get_smoother(const amg_ctx *cc, int level, double *q_out) {
         std::vector<double> j(L.n);
         CK(cudaMemcpyAsync(j.data(), L.j64, sizeof(double) * L.n, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        const int hrc = ensure_host(c, level);
+        if (hrc) return hrc;
         const HostCSR &A = c->host[level].A;
         for (int i = 0; i < A.n_rows; ++i)
             for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) q_out[p] = (A.col[p] == i) ? j[i] : 0.0;

@@ -888,11 +888,30 @@ void download(const DevCSR &M, HostCSR &h, cudaStream_t s) {
     }
 }
 
+// a level described on the device (row pointers copied to the host too)
+void describe(const DevCSR &M, HostCSR &h, cudaStream_t s) {
+    h.n_rows = M.n_rows;
+    h.n_cols = M.n_cols;
+    h.rp.resize(M.n_rows + 1);
+    h.col.clear();
+    h.val.clear();
+    check(cudaMemcpyAsync(h.rp.data(), M.rp, sizeof(int) * (M.n_rows + 1), cudaMemcpyDeviceToHost, s), "download");
+    h.drp = M.rp;
+    h.dcol = M.col;
+    h.dval = M.val;
+}
+
 DevCSR upload_csr(const HostCSR &h, Pool &pool, cudaStream_t s) {
     DevCSR M;
     M.n_rows = h.n_rows;
     M.n_cols = h.n_cols;
     M.nnz = h.nnz();
+    if (h.on_device()) {   // already there
+        M.rp = const_cast<int *>(h.drp);
+        M.col = const_cast<int *>(h.dcol);
+        M.val = const_cast<double *>(h.dval);
+        return M;
+    }
     M.rp = need<int>(pool, M.n_rows + 1);
     M.col = need<int>(pool, M.nnz);
     M.val = need<double>(pool, M.nnz);
@@ -1071,12 +1090,13 @@ void build(const HostCSR &A0, double theta, int max_levels, int max_coarse, unsi
         dR.push_back(R);
         dA.push_back(Ac);
     }
+    // the levels stay in the pool; the host receives their row pointers
     levels.assign(dA.size(), HostLevel{});
     for (size_t l = 0; l < dA.size(); ++l) {
-        download(dA[l], levels[l].A, s);
+        describe(dA[l], levels[l].A, s);
         if (l + 1 < dA.size()) {
-            download(dP[l], levels[l].P, s);
-            download(dR[l], levels[l].R, s);
+            describe(dP[l], levels[l].P, s);
+            describe(dR[l], levels[l].R, s);
         }
     }
     check(cudaStreamSynchronize(s), "setup");
@@ -1101,16 +1121,17 @@ int device_plan_products(std::vector<HostLevel> &levels, const std::vector<char>
 
 int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int max_coarse,
                            unsigned long long seed, int split_mode, cudaStream_t s,
-                           std::vector<HostLevel> &levels, std::string &err) {
-    Pool pool;
+                           std::vector<HostLevel> &levels, std::shared_ptr<void> &keep, std::string &err) {
+    auto pool = std::make_shared<Pool>();
     try {
-        build(A0, theta, max_levels, max_coarse, seed, split_mode, s, levels, pool);
+        build(A0, theta, max_levels, max_coarse, seed, split_mode, s, levels, *pool);
     } catch (const Fail &f) {
         cudaStreamSynchronize(s);
         err = "device setup: " + f.msg;
         levels.clear();
         return AMG_ERR_CUDA;
     }
+    keep = pool;
     return AMG_OK;
 }
 

@@ -1,10 +1,10 @@
 // AMG setup on the device (Sec. 2.2 with a parallel C/F split): strength
 // graph, block-local RS or PMIS splitting, direct interpolation, R = P^T and the Galerkin
-// product A_c = R (A P), every level built by CUDA kernels.  The hierarchy is
-// returned as host CSR (the context keeps a host copy of every level).
+// product A_c = R (A P), every level built by CUDA kernels.
 #pragma once
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -20,9 +20,14 @@ namespace amg {
 // numbers r_i = top 53 bits of splitmix64(seed + l) output i + 1, times
 // 2^-53.  Same stopping rules as the host RS setup.  Returns AMG_OK or
 // AMG_ERR_CUDA (message in err).
+//
+// The levels stay on the device: every HostCSR of `levels` holds its row
+// pointers on the host and its columns and values only as device pointers
+// (drp, dcol, dval) into memory that `keep` owns; the caller copies them
+// where it needs them and then releases `keep`.
 int device_build_hierarchy(const HostCSR &A0, double theta, int max_levels, int max_coarse,
                            unsigned long long seed, int split_mode, cudaStream_t s,
-                           std::vector<HostLevel> &levels, std::string &err);
+                           std::vector<HostLevel> &levels, std::shared_ptr<void> &keep, std::string &err);
 
 // For every level l with which[l] set (R and A present), computed on the
 // device and stored into levels[l]: MA = the pattern of A A (columns sorted,

@@ -11,7 +11,14 @@ struct HostCSR {
     int n_rows = 0, n_cols = 0;
     std::vector<int> rp, col;
     std::vector<double> val;
-    long long nnz() const { return static_cast<long long>(col.size()); }
+    // Device-built levels: col and val stay on the device (drp, dcol, dval)
+    // until a host copy is asked for; rp is on the host as well.
+    const int *drp = nullptr, *dcol = nullptr;
+    const double *dval = nullptr;
+    bool on_device() const { return dcol != nullptr; }
+    long long nnz() const {
+        return on_device() ? static_cast<long long>(rp.back()) : static_cast<long long>(col.size());
+    }
 };
 
 struct HostLevel {
