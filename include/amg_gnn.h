@@ -155,8 +155,9 @@ int amg_setup(amg_ctx *ctx, const amg_csr *A);
  * index) becomes C, until every strong F-F pair has a common strong C point
  * (denser coarse levels, fewer V-cycles).  split = 0 / 1 keep the PMIS
  * meanings of the former second_pass flag.  Direct interpolation, R = P^T and
- * A_c = R (A P) as amg_setup, on the device; the hierarchy is then kept on
- * the host too (amg_get_level) and uploaded as by amg_setup.  A (host CSR) is
+ * A_c = R (A P) as amg_setup, on the device; the levels are copied device to
+ * device into the solve's memory and reach the host only when asked for
+ * (amg_get_level copies a level's entries once).  A (host CSR) is
  * copied.  Same stopping rules and errors as amg_setup, AMG_ERR_ARG for an
  * unknown split; AMG_ERR_CUDA also covers device allocation failures.  PMIS
  * with the second pass keeps about half the points per level, so meshes of
