@@ -202,3 +202,27 @@ def test_unknown_split_refused():
                 P.amg_setup_device(ctx, W.poisson5(20), 0, bad)
     finally:
         P.amg_destroy(ctx)
+
+
+def test_host_routines_on_device_built_levels():
+    """The device-built levels reach the host only on demand: the Chebyshev
+    interval (a host power estimate) and the Jacobi smoother export read
+    them, and must see the oracle's hierarchy of the same split."""
+    A = CASES["graded_5k"]()
+    levels = OS.build_hierarchy(A, coarsening="rs-blocks", seed=2)
+    ctx = device_ctx(A, 2, mode="rs-blocks")
+    try:
+        P.amg_set_chebyshev(ctx, 3)
+        for l in range(len(levels) - 1):
+            rho, theta, delta = P.amg_get_chebyshev(ctx, l)
+            ref = O.power_estimate(O.TMat.of(levels[l].A), 20)
+            assert abs(rho - ref) <= 1e-11 * ref          # A_l within 1e-13 of the oracle's
+        P.amg_set_jacobi(ctx)
+        for l in range(len(levels) - 1):
+            q = P.amg_get_smoother(ctx, l)
+            ref = O.jacobi_values(O.TMat.of(levels[l].A), 2.0 / 3.0).numpy()
+            assert rel_err(q, ref) < 1e-12
+        # the host copies, once made, equal the oracle's levels
+        assert_same_hierarchy(ctx, levels)
+    finally:
+        P.amg_destroy(ctx)
