@@ -271,8 +271,8 @@ __device__ __forceinline__ uint2 bf16x4(float a, float b, float c, float d) {
     return make_uint2(*reinterpret_cast<unsigned *>(&lo), *reinterpret_cast<unsigned *>(&hi));
 }
 
-// YB (BF16 inference): y stored in bfloat16 (the tile statistics still from
-// the FP32 values), no h1 kept.
+// YB (BF16 inference): y only feeds the tile statistics (FP32); h1 is stored
+// and the normalisation pass recomputes y from it.
 template <int H, bool YB = false>
 __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ rp, const int *__restrict__ col,
                                                         const double *__restrict__ w64, const double *__restrict__ x0,
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
         a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
         if (k < nn && q == 0) {
             const float h0 = static_cast<float>(a0), hv1 = static_cast<float>(a1);
-            if (!YB) reinterpret_cast<float2 *>(h1)[a + k] = make_float2(h0, hv1);
+            reinterpret_cast<float2 *>(h1)[a + k] = make_float2(h0, hv1);
             sH[k][0] = h0;
             sH[k][1] = hv1;
         }
@@ -322,11 +322,9 @@ __global__ void __launch_bounds__(kBlock) k_layer1_tile(const int *__restrict__ 
             out[q] = fmaf(h0, W[f], fmaf(hv1, W[H + f], bias[f]));
             sY[k][f] = out[q];
         }
-        if (YB) {
-            uint2 *yo = reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(y) + static_cast<size_t>(a + k) * H + f0);
-#pragma unroll
-            for (int q = 0; q < FT / 4; ++q) yo[q] = bf16x4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
-        } else {
+        // BF16 inference stores no y: the normalisation pass forms it again
+        // from h1 (8 bytes per node instead of 128)
+        if (!YB) {
             float4 *yo = reinterpret_cast<float4 *>(y + static_cast<size_t>(a + k) * H + f0);
 #pragma unroll
             for (int q = 0; q < FT / 4; ++q) yo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
@@ -506,7 +504,10 @@ __global__ void __launch_bounds__(kLanes * H) k_stats_combine(const int *__restr
 // at a time).  x is stored in
 // FP32 (x), in bfloat16 (xb: BF16 inference) or not at all (both null: the
 // last layer in inference); the pooling always reads the FP32 value.
-template <int H, bool YB = false>
+// YM: 0 FP32 y; 1 bfloat16 y (BF16 inference); 2 layer 1 in BF16 inference:
+// y = h1 W1 + b1 recomputed from the stored h1 with the same FMAs as
+// k_layer1_tile, rounded to bfloat16 as a stored y would be.
+template <int H, int YM = 0>
 __global__ void __launch_bounds__(kBlock, 6) k_norm_relu_pool_tile(const int *__restrict__ tstart,
                                                                 const int *__restrict__ tgraph,
                                                                 const float *__restrict__ y,
@@ -516,7 +517,10 @@ __global__ void __launch_bounds__(kBlock, 6) k_norm_relu_pool_tile(const int *__
                                                                 const float *__restrict__ beta, float *__restrict__ x,
                                                                 __nv_bfloat16 *__restrict__ xb,
                                                                 double *__restrict__ tsum, float *__restrict__ tmax,
-                                                                int *__restrict__ targ) {
+                                                                int *__restrict__ targ,
+                                                                const float *__restrict__ h1 = nullptr,
+                                                                const float *__restrict__ W1 = nullptr,
+                                                                const float *__restrict__ b1 = nullptr) {
     constexpr int F = H / 4, Q = kBlock / F;   // threads per row (4 features each), rows at a time
     __shared__ double rs[Q][H];
     __shared__ float rm[Q][H];
@@ -540,10 +544,17 @@ __global__ void __launch_bounds__(kBlock, 6) k_norm_relu_pool_tile(const int *__
     for (int r4 = 0; r4 < kTile / Q; ++r4) {
         const int i = a + q + r4 * Q;
         const size_t o = static_cast<size_t>(i < e ? i : a) * H + f;
-        if (YB) {   // bfloat16 y (BF16 inference), widened exactly
+        if (YM == 1) {   // bfloat16 y (BF16 inference), widened exactly
             const uint2 u = *reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(y) + o);
             yr[r4] = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
                                  __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+        } else if (YM == 2) {
+            const float2 hh = reinterpret_cast<const float2 *>(h1)[i < e ? i : a];
+            float yv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                yv[j] = __bfloat162float(__float2bfloat16_rn(fmaf(hh.x, W1[f + j], fmaf(hh.y, W1[H + f + j], b1[f + j]))));
+            yr[r4] = make_float4(yv[0], yv[1], yv[2], yv[3]);
         } else {
             yr[r4] = *reinterpret_cast<const float4 *>(y + o);
         }
@@ -743,7 +754,7 @@ static void forward_impl(GcinBatch &b, const float *th, cudaStream_t s) {
     for (int l = 0; l < kLayers; ++l) {
         if (l == 0 && xbf) {
             k_layer1_tile<H, true><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + pl.convW[0],
-                                                         th + pl.convB[0], b.tstart, nullptr, b.y[0], b.tmean,
+                                                         th + pl.convB[0], b.tstart, b.h1, b.y[0], b.tmean,
                                                          b.tm2); AMG_COUNT();
         } else if (l == 0) {
             k_layer1_tile<H><<<NT, kBlock, 0, s>>>(b.rp, b.col, b.w64, b.x0, th + pl.convW[0], th + pl.convB[0],
@@ -769,10 +780,15 @@ static void forward_impl(GcinBatch &b, const float *th, cudaStream_t s) {
         const bool last = l == kLayers - 1;
         float *xo = (b.infer && (xbf || last)) ? nullptr : b.x[l];
         __nv_bfloat16 *xbo = (xbf && !last) ? reinterpret_cast<__nv_bfloat16 *>(b.x[l]) : nullptr;
-        if (xbf) {
-            k_norm_relu_pool_tile<H, true><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
-                                                                 th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum,
-                                                                 b.tmax, b.targ); AMG_COUNT();
+        if (xbf && l == 0) {
+            k_norm_relu_pool_tile<H, 2><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
+                                                              th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum,
+                                                              b.tmax, b.targ, b.h1, th + pl.convW[0],
+                                                              th + pl.convB[0]); AMG_COUNT();
+        } else if (xbf) {
+            k_norm_relu_pool_tile<H, 1><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
+                                                              th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum,
+                                                              b.tmax, b.targ); AMG_COUNT();
         } else {
             k_norm_relu_pool_tile<H><<<NT, kBlock, 0, s>>>(b.tstart, b.tgraph, b.y[l], b.mu[l], b.rstd[l],
                                                            th + pl.inG[l], th + pl.inB[l], xo, xbo, b.tsum, b.tmax,
