@@ -3,14 +3,19 @@
 // (App. B.3): BF16 operands, FP32 accumulation in tensor memory.  One CTA
 // owns two consecutive statistic tiles of at most 64 nodes each (a graph's
 // last tile is ragged; up to 128 nodes = one M = 128 MMA tile):
-//   1. warps aggregate h_i = sum_j w_ij x_j (FP32, 32 / (H / 4) rows per
-//      warp) and store h in BF16 into the A tile (128 x H, K-major,
-//      canonical no-swizzle core-matrix layout);
-//      W^T goes to the B tile (H x H, K-major) in BF16;
+//   0. the CTA's row bounds and, when they fit, its entries are staged in
+//      shared memory with coalesced loads;
+//   1. warps aggregate h_i = sum_j w_ij x_j with FP32 sums (training: FP32
+//      rows, H / 4 lanes per row; BF16 inference: bfloat16 rows, H / 8 lanes
+//      per row, each lane reading its entry's (column, weight) pair) and store
+//      h in BF16 into the A tile (128 x H, K-major, canonical no-swizzle
+//      core-matrix layout); W^T goes to the B tile (H x H, K-major) in BF16
+//      (pre-packed once per inference in BF16 inference);
 //   2. one thread issues H / 16 x tcgen05.mma.kind::f16 (M 128, N H, K 16)
 //      into an H-column TMEM accumulator and commits to an mbarrier;
 //   3. warps 0..3 read their 32 TMEM lanes (rows) with tcgen05.ld, add the
-//      bias, and the CTA writes y and the two tiles' mean / M2 statistics.
+//      bias, and the CTA writes y (FP32, or bfloat16 in BF16 inference) and
+//      the two tiles' mean / M2 statistics (FP32).
 // The mbarrier wait is bounded; on timeout the kernel raises an error flag,
 // waits (bounded) once more, frees its TMEM columns and returns
 // (gcin_tc_selftest exercises that path with no_commit).
