@@ -2,7 +2,11 @@
 // C/F split.  Per level, all in CUDA kernels:
 //   strength     j in S_i iff j != i and -a_ij >= theta max_{k != i}(-a_ik)
 //                (that maximum > 0); S as CSR, S^T by counting + scatter
-//   PMIS split   (De Sterck, Yang & Heys 2006) lambda_i = |S_i^T| + r_i in
+//   block RS     (AMG_SPLIT_RS_BLOCKS) the classical RS first pass on each
+//                block of up to 4096 consecutive rows, one CTA per block with
+//                the block's strength subgraph in shared memory, then every
+//                F point left without a strong C point becomes C
+//   PMIS split   (otherwise; De Sterck, Yang & Heys 2006) lambda_i = |S_i^T| + r_i in
 //                FP64, r_i from splitmix64 (seed + level); points with
 //                |S_i^T| = 0 start as F; rounds of "undecided i beats every
 //                undecided j in S_i u S_i^T (ties: lower index) -> C, then
@@ -23,7 +27,8 @@
 //                (load <= 2/3), compacted and rank-sorted; each entry then
 //                summed over the row in ascending order (the Gustavson order)
 // Offsets come from a three-phase exclusive scan.  The same stopping rules as
-// the host setup; the finished hierarchy is copied to host CSR.
+// the host setup; the finished levels stay on the device (their row pointers
+// are copied to the host).
 //
 // Also here: the products the latency-optimised (small) levels use, for
 // hierarchies from either setup: the pattern of A A (that of M A, M = Q^-1 on
